@@ -1,0 +1,362 @@
+"""Benchmark of the co-sparse data term on GB300.
+
+One step = the whole hot path on one synthetic image: patches, codes and
+co-support bitmasks (cs_codes), exact scribble distances, sample tables, the
+pixel x sample likelihood sum and the label normalisation (cs_likelihood).
+Workload: 481x321 RGB, 5 labels x 2000 scribble samples, 7x7 patches,
+Omega 98x49 (1.544e9 pixel x sample pairs per step).
+
+Metric: pixel x sample likelihood pairs per second, whole job.
+  value  device time of the K timed steps (CUDA events around each step on
+         the launching stream; inputs resident in HBM; L2 flushed between
+         steps by writing a 256 MB buffer outside the timed events)
+  e2e    the same steps through the C ABI starting from pinned host buffers:
+         host->device copy of the inputs, the step, device->host copy of the
+         data term f_i (neglog), all inside the timed region
+Under torchrun (N > 1) every rank runs its own image (weak scaling, no
+collective on the data path); rank 0 prints the max-over-ranks line.
+
+--impl reference times the FP64 CPU oracle (the method's plain definition)
+on the host cores, on a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = 2
+WORKLOAD_NAME = "481x321 RGB, 5 labels x 2000 samples, 7x7 patches, Omega 98x49"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Per-SM, per-clock issue rates of the pipes the plain FP32 pair loop uses
+# (Blackwell SM: 128 FP32 lanes, 64 INT32 lanes, 16 special-function lanes for
+# ex2 and 16 for popc). The pair-rate ceiling of the plain form is the minimum
+# over pipes of (lanes per clock / algorithmic operations per pair), times
+# SM count and clock.
+PIPE_LANES = {"fp32": 128, "int32": 64, "mufu": 16, "popc": 16}
+
+
+def plain_pair_ops(Wk: int) -> dict:
+    """Algorithmic operations per pixel x sample pair of the plain form:
+    location 2 sub + mul + fma, colour 3 sub + mul + 2 fma, combine 3, running
+    max 1, exponent offset 1, sum 1 (FP32); Wk xor + (Wk - 1) add (INT32);
+    Wk popc; one ex2."""
+    return {"fp32": 16, "int32": 2 * Wk - 1, "popc": Wk, "mufu": 1}
+
+
+def alu_peak_pairs(Wk: int, sm_mhz: float, n_sm: int = 152) -> tuple[float, str]:
+    ops = plain_pair_ops(Wk)
+    rates = {k: PIPE_LANES[k] / v for k, v in ops.items()}
+    pipe = min(rates, key=rates.get)
+    return rates[pipe] * n_sm * sm_mhz * 1e6, pipe
+
+
+def run_reference(args):
+    """Oracle timed on the host cores on a bounded pixel sample per step."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1312_4746_gb300 import synth
+
+    oracle.build()
+    pr = synth.make_workload(WORKLOAD)
+    prm = pr.params
+    rng = np.random.default_rng(0)
+    P = pr.H * pr.W
+    n_pix = args.ref_pixels
+    cores = os.cpu_count()
+    times = []
+    for step in range(args.warmup + args.steps):
+        pix = np.sort(rng.choice(P, n_pix, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.data_term(pr, pix=pix)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    pairs = n_pix * pr.n_samples
+    value = pairs * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": "pixel x sample likelihood pairs/s",
+        "value": value, "unit": "pairs/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "sample_pixels_per_step": n_pix},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n_pix} random pixels x all {pr.n_samples} samples per step "
+                                   f"(codes of those pixels and of every sample included)"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def cpu_baseline(pr, budget_s=15.0):
+    """The oracle as it stands on a bounded pixel sample (about budget_s)."""
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(1)
+    P = pr.H * pr.W
+    n_pix = 256
+    pix = np.sort(rng.choice(P, n_pix, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.data_term(pr, pix=pix)
+    dt = time.perf_counter() - t0
+    # grow the sample to about budget_s of CPU work
+    n2 = int(min(P, max(n_pix, n_pix * budget_s / max(dt, 1e-3) * 0.8)))
+    pix = np.sort(rng.choice(P, n2, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.data_term(pr, pix=pix)
+    dt = time.perf_counter() - t0
+    return {"value": n2 * pr.n_samples / dt, "unit": "pairs/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{n2} random pixels x all {pr.n_samples} samples, {dt:.1f} s "
+                      f"(FP64 C oracle, OpenMP over pixels)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--form", default="fp32", choices=["fp32"])
+    ap.add_argument("--ref-pixels", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    from paper_1312_4746_gb300 import build as csbuild
+
+    csbuild.build()
+    import paper_1312_4746_gb300 as cs
+    from paper_1312_4746_gb300 import synth
+
+    # weak scaling: every rank gets its own image of the same shape
+    pr = synth.make_workload(WORKLOAD, seed=1000 + WORKLOAD + 7919 * rank)
+    P = pr.H * pr.W
+    k = pr.k
+    Wk = (k + 31) // 32
+    nl = pr.n_labels
+    ctx = cs.Context(local)
+    prm = cs.Params.from_synth(pr.params, precision=cs.FP32)
+
+    img = torch.from_numpy(pr.image).to(dev)
+    om = torch.from_numpy(pr.omega).to(dev)
+    mask = torch.from_numpy(pr.mask).to(dev)
+    smp = torch.from_numpy(pr.sample_pix).to(dev)
+    bits = torch.empty((P, Wk), dtype=torch.int32, device=dev)
+    out = {"neglog": torch.empty((nl, pr.H, pr.W), dtype=torch.float32, device=dev),
+           "post": torch.empty((nl, pr.H, pr.W), dtype=torch.float32, device=dev)}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    lib = cs.lib()
+
+    def step(img_d, om_d, mask_d, smp_d, out_d):
+        ctx.check(lib.cs_codes(ctx.handle, cs._ptr(img_d), pr.H, pr.W, cs._ptr(om_d), k,
+                               cs._ptr(mask_d), cs.ctypes.byref(prm), None, None,
+                               cs._ptr(bits), cs._stream()))
+        ctx.likelihood(img_d, bits, k, pr.label_off, smp_d, prm, out=out_d)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step(img, om, mask, smp, out)
+    ctx.sync()
+
+    # ---------------- device-timed region (inputs resident in HBM)
+    n_launch_per_step = 3 + 6  # codes: rownorm, codes, guard; likelihood: fill, seed, cols, rows, gather, sum
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step(img, om, mask, smp, out)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    ctx.profile(False)
+    ctx.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    sum_ms, sum_n = ctx.profile_read(cs.STAGE_SUM)
+    stage_ms = {name: ctx.profile_read(st)[0] / args.steps
+                for name, st in (("codes", cs.STAGE_CODES), ("dist", cs.STAGE_DIST),
+                                 ("gather", cs.STAGE_GATHER))}
+    stage_ms["sum"] = sum_ms / max(sum_n, 1)
+
+    # ---------------- end to end through the C ABI from pinned host buffers
+    h_img = torch.from_numpy(pr.image).pin_memory()
+    h_om = torch.from_numpy(pr.omega).pin_memory()
+    h_mask = torch.from_numpy(pr.mask).pin_memory()
+    h_smp = torch.from_numpy(pr.sample_pix).pin_memory()
+    h_out = torch.empty((nl, pr.H, pr.W), dtype=torch.float32).pin_memory()
+    d_img, d_om, d_mask, d_smp = (torch.empty_like(img), torch.empty_like(om),
+                                  torch.empty_like(mask), torch.empty_like(smp))
+    h2d = sum(t.numel() * t.element_size() for t in (h_img, h_om, h_mask, h_smp)) + 4 * (nl + 1)
+    d2h = h_out.numel() * 4
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e2e_ev[i][0].record(stream)
+        d_img.copy_(h_img, non_blocking=True)
+        d_om.copy_(h_om, non_blocking=True)
+        d_mask.copy_(h_mask, non_blocking=True)
+        d_smp.copy_(h_smp, non_blocking=True)
+        step(d_img, d_om, d_mask, d_smp, out)
+        h_out.copy_(out["neglog"], non_blocking=True)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+
+    pairs_rank = P * pr.n_samples
+    t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    dev_ms, e2e_ms = float(t[0]), float(t[1])
+    total_pairs = pairs_rank * world * args.steps
+    value = total_pairs / (dev_ms * 1e-3)
+    e2e_value = total_pairs / (e2e_ms * 1e-3)
+
+    if rank == 0:
+        peaks, src = _peaks()
+        clocks = clk.summary()
+        sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        peak, pipe = alu_peak_pairs(Wk, sm_mhz, torch.cuda.get_device_properties(dev).multi_processor_count)
+        achieved = pairs_rank / (stage_ms["sum"] * 1e-3)
+        line = {
+            "metric": "pixel x sample likelihood pairs/s", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "form": "plain FP32 (CUDA cores, popc TSM)",
+                       "mode": "per-sample", "pairs_per_step": pairs_rank,
+                       "l2": "flushed between steps (256 MB write outside the timed events)",
+                       "stage_ms": stage_ms},
+            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": n_launch_per_step * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "pairs/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "sum_plain_kernel", "binding_pipe": pipe,
+                         "peak_basis": f"{PIPE_LANES[pipe]} {pipe} lanes/SM/clk / "
+                                       f"{plain_pair_ops(Wk)[pipe]} ops per pair x SMs x "
+                                       f"{sm_mhz:.0f} MHz (median SM clock sampled under load)"},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(pr)
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

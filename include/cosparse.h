@@ -1,0 +1,200 @@
+/*
+ * cosparse.h - C ABI of the GB300 (sm_103a) co-sparse data-term library.
+ *
+ * The library computes the data term of "Co-Sparse Textural Similarity for
+ * Image Segmentation" (Nieuwenhuis, Hawe, Kleinsteuber, Cremers): for an RGB
+ * image, an analysis operator O, and scribble samples per label, the
+ * negative log-likelihood f_i(x) = -log P(I(x), s_x, x | l(x) = i) that the
+ * convex multilabel solver of Sec. 4 consumes (Eq. energy1).
+ *
+ * Conventions shared by every call
+ *  - Pointers marked DEVICE must point to memory on the context's device;
+ *    pointers marked HOST to ordinary (optionally pinned) host memory.
+ *  - The caller owns every input and output buffer. The context owns only
+ *    its scratch memory, the device error word and (for the surrogate) the
+ *    network weights.
+ *  - Buffers are dense, C-contiguous, row-major; pixel index = y * W + x.
+ *    Images are H x W x 3 float32 (RGB interleaved, HWC).
+ *  - Calls validate their arguments on the host first and return
+ *    CS_ERR_INVALID_ARG (or CS_ERR_UNSUPPORTED) before launching anything.
+ *    Otherwise the work is enqueued on `stream` (a cudaStream_t, NULL = the
+ *    legacy default stream) and the call returns without waiting, except
+ *    where a call says it synchronises.
+ *  - Errors detected on the device (a bounded wait that gave up, a full
+ *    guard list) are recorded in the context's device error word; read it
+ *    with cs_sync_status().
+ *  - No call throws, exits or aborts. cs_last_error() describes the most
+ *    recent failure on the context.
+ *  - One context may be used from one host thread at a time.
+ */
+#ifndef COSPARSE_H
+#define COSPARSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int cs_status;
+#define CS_OK 0
+#define CS_ERR_INVALID_ARG 1 /* bad shape, null pointer, empty label, ... */
+#define CS_ERR_CUDA 2        /* a CUDA runtime call failed */
+#define CS_ERR_NOMEM 3       /* scratch allocation failed */
+#define CS_ERR_TIMEOUT 4     /* a bounded device-side wait gave up */
+#define CS_ERR_UNSUPPORTED 5 /* valid but not implemented (e.g. patch side 13) */
+#define CS_ERR_DEVICE 6      /* the device error word was set */
+
+/* Likelihood forms (Sec. 3.1). */
+#define CS_MODE_PERSAMPLE 0  /* each sample carries k_rho * k_sigma * exp(-TSM/beta) */
+#define CS_MODE_FACTORISED 1 /* Eq. (joined): Parzen sum times the Eq. (post_text) softmax */
+
+/* Arithmetic forms. */
+#define CS_FP32 0 /* CUDA-core FP32 with exact integer distances and popc TSM */
+#define CS_BF16 1 /* tensor-core (tcgen05) TSM and colour dot products, FP32 accumulation */
+#define CS_FP8 2  /* as CS_BF16 with FP8 operands where they are exact */
+
+typedef struct cs_ctx cs_ctx;
+
+/*
+ * Scalar parameters. Fill with cs_params_default() and override fields.
+ *   p          patch side, odd, 3..9 (n = p*p window elements; Sec. 5 uses 9)
+ *   mode       CS_MODE_PERSAMPLE or CS_MODE_FACTORISED
+ *   precision  CS_FP32, CS_BF16 or CS_FP8
+ *   tau        co-support threshold: j is in Co(a) iff |a_j| <= tau, the
+ *              practical "close to zero" of Sec. 2 (default 0.1)
+ *   sigma_c2   variance of the Gaussian colour kernel per channel (Sec. 3.1: 1.3)
+ *   alpha      rho_i(x) = alpha * max(|x - x_v|, d_min)  (Sec. 3.1: alpha = 1.3)
+ *   d_min      floor on the nearest-scribble distance in pixels (default 1)
+ *   kappa_beta beta_i(x) = kappa_beta * rho_i(x): beta proportional to rho (Sec. 3.1)
+ */
+typedef struct {
+    int32_t p;
+    int32_t mode;
+    int32_t precision;
+    int32_t reserved;
+    double tau;
+    double sigma_c2;
+    double alpha;
+    double d_min;
+    double kappa_beta;
+} cs_params;
+
+void cs_params_default(cs_params* out);
+
+/* Library version string (static storage). */
+const char* cs_version(void);
+
+/*
+ * Create a context on CUDA device `device`. *out receives the context; the
+ * caller releases it with cs_destroy(). Allocates only the device error
+ * word; scratch memory is allocated on first use and grows as needed.
+ * Errors: CS_ERR_INVALID_ARG (out NULL or no such device), CS_ERR_CUDA.
+ */
+cs_status cs_create(cs_ctx** out, int device);
+void cs_destroy(cs_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none). Valid until the next call. */
+const char* cs_last_error(const cs_ctx* ctx);
+
+/*
+ * Wait for `stream`, then read and clear the device error word.
+ * Returns CS_OK, CS_ERR_DEVICE / CS_ERR_TIMEOUT (message in cs_last_error),
+ * or CS_ERR_CUDA if the stream reported a CUDA error. Synchronises.
+ */
+cs_status cs_sync_status(cs_ctx* ctx, void* stream);
+
+/*
+ * Patches, codes and co-support bitmasks for every pixel
+ * (Sec. 2: a = O s with s a zero-mean, unit-norm patch; Sec. 3.1: gray
+ * patch centred at x, multiplied element-wise by a Gaussian mask before the
+ * normalisation; Eq. 1: Co(a) = {j : a_j = 0}, read as |a_j| <= tau).
+ *
+ *   img     DEVICE H x W x 3 float32
+ *   omega   DEVICE k x n float32, row-major, n = p*p, window order t = dy*p + dx
+ *   mask    DEVICE n float32 (Gaussian weights)
+ *   codes   DEVICE P x k float32 or NULL          (P = H*W)
+ *   lead16  DEVICE P x 16 float32 or NULL (the first min(k,16) codes, 0-padded)
+ *   bitmask DEVICE P x ceil(k/32) uint32 or NULL: bit j of word j>>5 set iff
+ *           |a_j| <= tau; pad bits are 0.
+ *
+ * Patch rule: window pixels clamp to the image edge; gray = 0.299 R +
+ * 0.587 G + 0.114 B; v = mask * gray; s = (v - mean v) / ||v - mean v||, or
+ * s = 0 when v is constant. Bitmasks are bit-exact against this rule in
+ * double precision with sums taken in index order: entries whose FP32 value
+ * lies within a rigorous error bound of tau are recomputed that way on the
+ * device. `codes` and `lead16` carry the FP32 values.
+ * Errors: CS_ERR_INVALID_ARG (H, W < 1; k < 1 or k > 1024; null required
+ * pointer), CS_ERR_UNSUPPORTED (p not in 3..9 odd), CS_ERR_NOMEM, CS_ERR_CUDA.
+ */
+cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* omega, int k,
+                   const float* mask, const cs_params* prm, float* codes, float* lead16,
+                   uint32_t* bitmask, void* stream);
+
+/*
+ * Co-support bitmasks of given codes (Eq. 1): bit j of row q is set iff
+ * |codes[q*k + j]| <= tau, compared in double precision.
+ *   codes DEVICE P x k float32; bitmask DEVICE P x ceil(k/32) uint32.
+ */
+cs_status cs_cosupport(cs_ctx* ctx, const float* codes, int P, int k, double tau,
+                       uint32_t* bitmask, void* stream);
+
+/*
+ * Spatially varying likelihoods for every pixel and label (Sec. 3.1).
+ *
+ * Per-sample form (CS_MODE_PERSAMPLE):
+ *   L_i(x) = log (1/m_i) sum_j k_rho(x - x_ij) k_sigma(I(x) - I_ij)
+ *                                exp(-TSM(b_x, b_ij) / beta_i(x))
+ * Factorised form (CS_MODE_FACTORISED, Eq. joined = Eq. color x Eq. post_text):
+ *   L_i(x) = log (1/m_i) sum_j k_rho k_sigma + log softmax_i(-TSM(b_x, c_i) / beta_i(x))
+ * with k_rho(u) = exp(-|u|^2 / (2 rho^2)) / (2 pi rho^2),
+ * k_sigma(d) = exp(-|d|^2 / (2 sigma_c2)) / (2 pi sigma_c2)^(3/2),
+ * rho_i(x) = alpha * max(sqrt(D_i(x)), d_min), D_i(x) the squared distance
+ * to the nearest sample of label i (Sec. 3.1), beta_i = kappa_beta * rho_i,
+ * TSM the Hamming distance of co-support bitmasks (Eq. tsm_clean) and c_i
+ * the majority co-support of the label's samples (Eq. tex-rep).
+ *
+ *   img        DEVICE H x W x 3 float32
+ *   bitmask    DEVICE P x ceil(k/32) uint32 (from cs_codes)
+ *   label_off  HOST   n_labels + 1 int32, CSR offsets into sample_pix;
+ *              label_off[0] = 0 and every label needs >= 1 sample
+ *   sample_pix DEVICE label_off[n_labels] int32 pixel indices (y*W + x)
+ *   dist2      DEVICE n_labels x P int32 or NULL: D_i(x), exact
+ *   neglog     DEVICE n_labels x P float32: f_i(x) = -L_i(x) (Eq. energy1)
+ *   post       DEVICE n_labels x P float32 or NULL: label posteriors
+ *              exp(L_i) / sum_l exp(L_l) under a uniform label prior
+ * Errors: CS_ERR_INVALID_ARG (empty label, bad offsets, n_labels < 1 or
+ * > 64, null required pointer, non-positive sigma_c2/alpha/d_min/kappa_beta),
+ * CS_ERR_UNSUPPORTED (k > 256 with the tensor-core forms), CS_ERR_NOMEM,
+ * CS_ERR_CUDA.
+ */
+cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
+                        int k, int n_labels, const int32_t* label_off,
+                        const int32_t* sample_pix, const cs_params* prm, int32_t* dist2,
+                        float* neglog, float* post, void* stream);
+
+/*
+ * Stage timing. While enabled, every call records a pair of CUDA events on
+ * its stream around each stage it launches:
+ *   CS_STAGE_CODES   patches, codes, bitmasks and the FP64 guard pass
+ *   CS_STAGE_DIST    exact scribble distance transform
+ *   CS_STAGE_GATHER  sample tables and majority co-supports
+ *   CS_STAGE_SUM     the pixel x sample likelihood sum and label normalisation
+ * cs_profile_read waits for the recorded events of `stage`, returns their
+ * summed duration in milliseconds and the number of recorded launches, and
+ * forgets them. Synchronises on those events only.
+ */
+#define CS_STAGE_CODES 0
+#define CS_STAGE_DIST 1
+#define CS_STAGE_GATHER 2
+#define CS_STAGE_SUM 3
+#define CS_N_STAGES 4
+cs_status cs_profile_enable(cs_ctx* ctx, int on);
+cs_status cs_profile_read(cs_ctx* ctx, int stage, double* ms, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COSPARSE_H */

@@ -1,0 +1,238 @@
+"""GB300 (sm_103a) co-sparse data term: thin Python binding of libcosparse.so.
+
+Every step of the computation runs in the library's CUDA kernels behind the
+C ABI declared in ``include/cosparse.h``. This module only marshals
+arguments: it allocates outputs as torch CUDA tensors, passes raw device
+pointers and the current CUDA stream, and turns status codes into
+exceptions. There is no CPU fallback: if the library is missing, ``lib()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "_build", "libcosparse.so")
+
+CS_OK = 0
+CS_ERR_INVALID_ARG = 1
+CS_ERR_CUDA = 2
+CS_ERR_NOMEM = 3
+CS_ERR_TIMEOUT = 4
+CS_ERR_UNSUPPORTED = 5
+CS_ERR_DEVICE = 6
+
+MODE_PERSAMPLE = 0
+MODE_FACTORISED = 1
+FP32 = 0
+BF16 = 1
+FP8 = 2
+
+# every symbol include/cosparse.h declares
+EXPORTS = (
+    "cs_params_default",
+    "cs_version",
+    "cs_create",
+    "cs_destroy",
+    "cs_last_error",
+    "cs_sync_status",
+    "cs_codes",
+    "cs_cosupport",
+    "cs_likelihood",
+    "cs_profile_enable",
+    "cs_profile_read",
+)
+
+STAGE_CODES = 0
+STAGE_DIST = 1
+STAGE_GATHER = 2
+STAGE_SUM = 3
+
+
+class CsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"[cs status {status}] {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of cs_params (include/cosparse.h)."""
+
+    _fields_ = [
+        ("p", ctypes.c_int32),
+        ("mode", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("sigma_c2", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("d_min", ctypes.c_double),
+        ("kappa_beta", ctypes.c_double),
+    ]
+
+    @classmethod
+    def default(cls, **kw):
+        p = cls()
+        lib().cs_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    @classmethod
+    def from_synth(cls, sp, **kw):
+        """From a ``synth.Params`` dataclass."""
+        p = cls.default(p=sp.p, mode=sp.mode, tau=sp.tau, sigma_c2=sp.sigma_c2, alpha=sp.alpha,
+                        d_min=sp.d_min, kappa_beta=sp.kappa_beta)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load libcosparse.so (built in-tree by ``build.build()``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    so = path or SO_PATH
+    if not os.path.exists(so):
+        raise RuntimeError(
+            f"libcosparse.so not found at {so}: build it with "
+            "`python -m paper_1312_4746_gb300.build` (there is no CPU fallback)")
+    L = ctypes.CDLL(so)
+    V, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.cs_params_default.argtypes = [ctypes.POINTER(Params)]
+    L.cs_params_default.restype = None
+    L.cs_version.restype = ctypes.c_char_p
+    L.cs_create.argtypes = [ctypes.POINTER(V), I]
+    L.cs_destroy.argtypes = [V]
+    L.cs_destroy.restype = None
+    L.cs_last_error.argtypes = [V]
+    L.cs_last_error.restype = ctypes.c_char_p
+    L.cs_sync_status.argtypes = [V, V]
+    L.cs_codes.argtypes = [V, V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V]
+    L.cs_cosupport.argtypes = [V, V, I, I, D, V, V]
+    L.cs_likelihood.argtypes = [V, V, I, I, V, I, I, V, V, ctypes.POINTER(Params), V, V, V, V]
+    L.cs_profile_enable.argtypes = [V, I]
+    L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
+    for f in ("cs_create", "cs_sync_status", "cs_codes", "cs_cosupport", "cs_likelihood",
+              "cs_profile_enable", "cs_profile_read"):
+        getattr(L, f).restype = I
+    if path is None:
+        _lib = L
+    return L
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """Owns a cs_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = lib()
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self._lib.cs_create(ctypes.byref(h), device)
+        if st != CS_OK:
+            raise CsError(st, self._lib.cs_last_error(None).decode())
+        self.handle = h
+
+    def check(self, st):
+        if st != CS_OK:
+            raise CsError(st, self._lib.cs_last_error(self.handle).decode())
+
+    def sync(self):
+        """Wait for the current stream and raise on a device-side error."""
+        self.check(self._lib.cs_sync_status(self.handle, _stream()))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.cs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, on: bool = True):
+        self.check(self._lib.cs_profile_enable(self.handle, int(on)))
+
+    def profile_read(self, stage: int):
+        """(summed milliseconds, launches) of one stage since the last read."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int()
+        self.check(self._lib.cs_profile_read(self.handle, stage, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    # ------------------------------------------------------------------ calls
+
+    def codes(self, img, omega, mask, params: Params, want_codes=False, want_lead16=False,
+              want_bitmask=True):
+        """cs_codes: returns dict with 'bitmask' (P, Wk) int32 view of uint32
+        words, and optionally 'codes' (P, k) and 'lead16' (P, 16) float32."""
+        import torch
+
+        H, W = int(img.shape[0]), int(img.shape[1])
+        k = int(omega.shape[0])
+        P = H * W
+        dev = img.device
+        out = {}
+        out["codes"] = torch.empty((P, k), dtype=torch.float32, device=dev) if want_codes else None
+        out["lead16"] = torch.empty((P, 16), dtype=torch.float32, device=dev) if want_lead16 else None
+        out["bitmask"] = (torch.empty((P, (k + 31) // 32), dtype=torch.int32, device=dev)
+                          if want_bitmask else None)
+        self.check(self._lib.cs_codes(self.handle, _ptr(img), H, W, _ptr(omega), k, _ptr(mask),
+                                      ctypes.byref(params), _ptr(out["codes"]),
+                                      _ptr(out["lead16"]), _ptr(out["bitmask"]), _stream()))
+        return out
+
+    def cosupport(self, codes, tau, bitmask=None):
+        import torch
+
+        P, k = int(codes.shape[0]), int(codes.shape[1])
+        if bitmask is None:
+            bitmask = torch.empty((P, (k + 31) // 32), dtype=torch.int32, device=codes.device)
+        self.check(self._lib.cs_cosupport(self.handle, _ptr(codes), P, k, float(tau),
+                                          _ptr(bitmask), _stream()))
+        return bitmask
+
+    def likelihood(self, img, bitmask, k, label_off, sample_pix, params: Params,
+                   want_dist2=False, want_post=True, out=None):
+        """cs_likelihood: returns dict with 'neglog' (n, H, W), optionally
+        'post' and 'dist2'. ``label_off`` is a host array (numpy or list);
+        ``sample_pix`` a device int32 tensor."""
+        import numpy as np
+        import torch
+
+        H, W = int(img.shape[0]), int(img.shape[1])
+        off = np.ascontiguousarray(np.asarray(label_off, dtype=np.int32))
+        nl = len(off) - 1
+        dev = img.device
+        if out is None:
+            out = {
+                "neglog": torch.empty((nl, H, W), dtype=torch.float32, device=dev),
+                "post": torch.empty((nl, H, W), dtype=torch.float32, device=dev) if want_post else None,
+                "dist2": torch.empty((nl, H, W), dtype=torch.int32, device=dev) if want_dist2 else None,
+            }
+        self.check(self._lib.cs_likelihood(
+            self.handle, _ptr(img), H, W, _ptr(bitmask), int(k), nl,
+            ctypes.c_void_p(off.ctypes.data), _ptr(sample_pix), ctypes.byref(params),
+            _ptr(out.get("dist2")), _ptr(out["neglog"]), _ptr(out.get("post")), _stream()))
+        return out
+
+
+def version() -> str:
+    return lib().cs_version().decode()

@@ -1,0 +1,139 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/cosparse.h"
+
+// Device error word layout: err[0] = status code (0 = none), err[1] = detail.
+#define CS_DEVERR_GUARD_FULL 101  // co-support guard list overflowed
+#define CS_DEVERR_TIMEOUT 102     // bounded wait gave up
+#define CS_DEVERR_BAD_SAMPLE 103  // a sample index lies outside the image
+
+// Largest supported shapes.
+#define CS_MAX_K 1024
+#define CS_MAX_LABELS 64
+#define CS_MAX_SIDE 23170  // keeps W^2 + H^2 < 2^31 for the exact distances
+
+struct StageRecord {
+    int stage;
+    cudaEvent_t beg, end;
+};
+
+struct cs_ctx {
+    int device = 0;
+    std::string err;
+    char* scratch = nullptr;
+    size_t scratch_cap = 0;
+    int* d_err = nullptr;  // 2 ints
+    bool profiling = false;
+    std::vector<StageRecord> records;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+// Records events around one stage when profiling is on (RAII on the stream).
+struct StageTimer {
+    cs_ctx* ctx;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t beg = nullptr, end = nullptr;
+    StageTimer(cs_ctx* c, int s, cudaStream_t stream);
+    ~StageTimer();
+};
+
+// Bump allocator over a context's scratch buffer. First pass with base ==
+// nullptr measures the size; the second carves real pointers.
+struct Carve {
+    char* base;
+    size_t off = 0;
+    explicit Carve(char* b) : base(b) {}
+    template <class T>
+    T* take(size_t count, size_t align = 256) {
+        off = (off + align - 1) / align * align;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+cs_status cs_set_error(cs_ctx* ctx, cs_status code, const char* fmt, ...);
+cs_status cs_ensure_scratch(cs_ctx* ctx, size_t bytes);
+cs_status cs_check_launch(cs_ctx* ctx, const char* what);
+
+// ---- launchers (each enqueues kernels on `st`; returns cudaError_t) -------
+
+// Patches, codes, co-support bitmasks (FP32 with a rigorous guard band and
+// canonical FP64 recomputation of guarded entries).
+struct CodesArgs {
+    const float* img;
+    int H, W;
+    const float* omega;
+    int k;
+    const float* mask;
+    int p;
+    double tau;
+    float* codes;
+    float* lead16;
+    uint32_t* bitmask;
+    // scratch
+    float* rownorm;     // k
+    int2* guard;        // guard_cap entries
+    int guard_cap;
+    int* guard_count;   // 1 int
+    int* d_err;
+};
+cudaError_t launch_codes_f32(const CodesArgs& a, cudaStream_t st);
+cudaError_t launch_cosupport(const float* codes, long long P, int k, double tau, uint32_t* bitmask,
+                             cudaStream_t st);
+
+// Exact squared distance to the nearest scribble of every label.
+struct EdtArgs {
+    int H, W, n_labels;
+    const int32_t* d_label_off;  // device copy, n_labels + 1
+    const int32_t* sample_pix;
+    int n_samples;
+    int32_t* colbuf;  // scratch n_labels * P
+    int32_t* vbuf;    // scratch n_labels * P
+    int32_t* dist2;   // output n_labels * P
+    int* d_err;
+};
+cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st);
+
+// Per-sample tables (SoA) and the majority co-support of each label.
+struct SampleTables {
+    float* sx;
+    float* sy;
+    float* sr;
+    float* sg;
+    float* sb;
+    uint32_t* sbits;  // word-major: [Wk][S]
+    int32_t* spop;    // popcount of each sample's bitmask
+    uint32_t* rep;    // [n_labels][Wk]
+};
+cudaError_t launch_gather(const float* img, int H, int W, const uint32_t* bitmask, int k,
+                          int n_labels, const int32_t* d_label_off, const int32_t* sample_pix,
+                          int n_samples, bool want_rep, const SampleTables& t, cudaStream_t st);
+
+// Pixel x sample likelihood sum and label normalisation.
+struct SumArgs {
+    const float* img;
+    int H, W;
+    const uint32_t* bitmask;
+    int k, Wk;
+    int n_labels;
+    const int32_t* d_label_off;
+    int n_samples;
+    SampleTables t;
+    const int32_t* dist2;
+    float alpha, d_min, kappa_beta;
+    float sigma_c2;
+    int mode;
+    float* neglog;
+    float* post;
+};
+cudaError_t launch_sum_plain(const SumArgs& a, cudaStream_t st);

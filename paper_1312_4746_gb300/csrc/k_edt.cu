@@ -1,0 +1,191 @@
+// Exact squared distance from every pixel to the nearest scribble sample of
+// each label (Sec. 3.1: rho_i(x) = alpha |x - x_v|, x_v the closest scribble
+// location of label i).
+//
+// Separable exact transform in integers:
+//   1. seed planes: 0 at the label's sample pixels, INF elsewhere;
+//   2. column pass (one thread per label and column): vertical distance to
+//      the nearest seed in the same column, squared;
+//   3. row pass (one thread per label and row): lower envelope of the
+//      parabolas (x - q)^2 + g(q) over the columns q with finite g, built in
+//      one sweep and read back in a second; intersection abscissae are
+//      compared as exact rationals with 64-bit cross products, so the
+//      result equals the brute-force minimum bit for bit.
+// The sample gather builds SoA tables of every sample (location, colour,
+// co-support bitmask and its popcount) and, for the factorised form, the
+// majority co-support of each label (Eq. tex-rep: bit set iff 2 * count >= m).
+#include <cstdint>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int32_t INF = 0x7FFFFFFF;
+
+__device__ __forceinline__ int label_of(const int32_t* __restrict__ off, int n_labels, int s) {
+    int lo = 0, hi = n_labels - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= s)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void fill_kernel(int32_t* __restrict__ p, long long n, int32_t v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void seed_kernel(const int32_t* __restrict__ off, int n_labels,
+                            const int32_t* __restrict__ sample_pix, int n_samples, long long P,
+                            int32_t* __restrict__ g, int* __restrict__ d_err) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_samples) return;
+    const int pix = sample_pix[s];
+    if (pix < 0 || pix >= P) {  // reject out-of-image sample indices, never write them
+        if (atomicCAS(d_err, 0, CS_DEVERR_BAD_SAMPLE) == 0) d_err[1] = s;
+        return;
+    }
+    int i = label_of(off, n_labels, s);
+    g[(size_t)i * P + pix] = 0;
+}
+
+__global__ void cols_kernel(int H, int W, int n_labels, int32_t* __restrict__ g) {
+    long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= (long long)n_labels * W) return;
+    const int i = (int)(tid / W), x = (int)(tid % W);
+    int32_t* col = g + (size_t)i * H * W + x;
+    int last = -1;
+    for (int y = 0; y < H; ++y) {
+        int32_t v = col[(size_t)y * W];
+        if (v == 0) last = y;
+        col[(size_t)y * W] = last < 0 ? INF : y - last;  // 0 exactly at seeds
+    }
+    int next = -1;
+    for (int y = H - 1; y >= 0; --y) {
+        int32_t v = col[(size_t)y * W];
+        if (v == 0) next = y;
+        int32_t d = v;
+        if (next >= 0 && next - y < d) d = next - y;
+        col[(size_t)y * W] = d == INF ? INF : d * d;
+    }
+}
+
+__global__ void rows_kernel(int H, int W, int n_labels, const int32_t* __restrict__ g,
+                            int32_t* __restrict__ vbuf, int32_t* __restrict__ dist2) {
+    long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= (long long)n_labels * H) return;
+    const size_t row = (size_t)tid * W;  // label-major planes: row index i * H + y
+    const int32_t* f = g + row;
+    int32_t* v = vbuf + row;
+    int32_t* out = dist2 + row;
+    int kk = -1;
+    for (int q = 0; q < W; ++q) {
+        const int32_t fq = f[q];
+        if (fq == INF) continue;
+        const long long Fq = (long long)fq + (long long)q * q;
+        while (kk > 0) {
+            const int vk = v[kk], vp = v[kk - 1];
+            const long long Fv = (long long)f[vk] + (long long)vk * vk;
+            const long long Fp = (long long)f[vp] + (long long)vp * vp;
+            // drop v[kk] if its parabola is nowhere strictly below both neighbours:
+            // s(vk, q) <= z(vp, vk)  <=>  (Fq - Fv)(vk - vp) <= (Fv - Fp)(q - vk)
+            if ((Fq - Fv) * (long long)(vk - vp) <= (Fv - Fp) * (long long)(q - vk))
+                --kk;
+            else
+                break;
+        }
+        v[++kk] = q;
+    }
+    if (kk < 0) {  // no valid seed of this label (only possible after a bad sample index)
+        for (int x = 0; x < W; ++x) out[x] = INF;
+        return;
+    }
+    int j = 0;
+    for (int x = 0; x < W; ++x) {
+        while (j < kk) {
+            const int a = v[j], b = v[j + 1];
+            const long long Fa = (long long)f[a] + (long long)a * a;
+            const long long Fb = (long long)f[b] + (long long)b * b;
+            if (Fb - Fa < 2ll * x * (b - a))  // z(a, b) < x
+                ++j;
+            else
+                break;
+        }
+        const int a = v[j];
+        out[x] = (x - a) * (x - a) + f[a];
+    }
+}
+
+__global__ void gather_kernel(const float* __restrict__ img, int W, long long P,
+                              const uint32_t* __restrict__ bitmask, int Wk,
+                              const int32_t* __restrict__ sample_pix, int n_samples,
+                              SampleTables t) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_samples) return;
+    int pix = sample_pix[s];
+    if (pix < 0 || pix >= P) pix = 0;  // reported by seed_kernel; keep the tables finite
+    t.sx[s] = (float)(pix % W);
+    t.sy[s] = (float)(pix / W);
+    t.sr[s] = img[(size_t)pix * 3 + 0];
+    t.sg[s] = img[(size_t)pix * 3 + 1];
+    t.sb[s] = img[(size_t)pix * 3 + 2];
+    int pc = 0;
+    for (int w = 0; w < Wk; ++w) {
+        uint32_t b = bitmask[(size_t)pix * Wk + w];
+        t.sbits[(size_t)w * n_samples + s] = b;
+        pc += __popc(b);
+    }
+    t.spop[s] = pc;
+}
+
+// one thread per (label, code index j)
+__global__ void majority_kernel(const int32_t* __restrict__ off, int n_labels, int k, int Wk,
+                                int n_samples, const uint32_t* __restrict__ sbits,
+                                uint32_t* __restrict__ rep) {
+    int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= n_labels * Wk * 32) return;
+    const int i = tid / (Wk * 32), j = tid % (Wk * 32);
+    const int w = j >> 5, b = j & 31;
+    int cnt = 0;
+    const int m = off[i + 1] - off[i];
+    for (int s = off[i]; s < off[i + 1]; ++s) cnt += (sbits[(size_t)w * n_samples + s] >> b) & 1;
+    const bool set = (j < k) && (2 * cnt >= m);
+    const unsigned word = __ballot_sync(0xffffffffu, set);  // 32 consecutive j share a word
+    if (b == 0) rep[(size_t)i * Wk + w] = word;
+}
+
+}  // namespace
+
+cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
+    const long long P = (long long)a.H * a.W;
+    const long long n = P * a.n_labels;
+    fill_kernel<<<152 * 8, 256, 0, st>>>(a.colbuf, n, INF);
+    seed_kernel<<<(a.n_samples + 255) / 256, 256, 0, st>>>(a.d_label_off, a.n_labels,
+                                                           a.sample_pix, a.n_samples, P, a.colbuf,
+                                                           a.d_err);
+    long long ncol = (long long)a.n_labels * a.W;
+    cols_kernel<<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(a.H, a.W, a.n_labels, a.colbuf);
+    long long nrow = (long long)a.n_labels * a.H;
+    rows_kernel<<<(unsigned)((nrow + 63) / 64), 64, 0, st>>>(a.H, a.W, a.n_labels, a.colbuf,
+                                                             a.vbuf, a.dist2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const float* img, int H, int W, const uint32_t* bitmask, int k,
+                          int n_labels, const int32_t* d_label_off, const int32_t* sample_pix,
+                          int n_samples, bool want_rep, const SampleTables& t, cudaStream_t st) {
+    const int Wk = (k + 31) / 32;
+    gather_kernel<<<(n_samples + 255) / 256, 256, 0, st>>>(img, W, (long long)H * W, bitmask, Wk, sample_pix,
+                                                           n_samples, t);
+    if (want_rep) {
+        int nthr = n_labels * Wk * 32;
+        majority_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(d_label_off, n_labels, k, Wk,
+                                                            n_samples, t.sbits, t.rep);
+    }
+    return cudaGetLastError();
+}
