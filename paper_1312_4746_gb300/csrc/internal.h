@@ -98,7 +98,8 @@ struct EdtArgs {
     const int32_t* sample_pix;
     int n_samples;
     int32_t* colbuf;  // scratch n_labels * P
-    int32_t* vbuf;    // scratch n_labels * P
+    int32_t* vbuf;    // scratch n_labels * P (envelope rows, when not in shared memory)
+    int32_t* fbuf;    // scratch n_labels * P (envelope offsets, likewise)
     int32_t* dist2;   // output n_labels * P
     int* d_err;
 };

@@ -54,11 +54,12 @@ __global__ void __launch_bounds__(TILE* TILE)
                      float* __restrict__ lead16, uint32_t* __restrict__ bitmask,
                      int2* __restrict__ guard, int guard_cap, int* __restrict__ guard_count) {
     constexpr int N = P * P;
+    constexpr int NP = (N + 3) & ~3;  // operator rows padded to whole float4s
     constexpr int R = (P - 1) / 2;
     constexpr int TW = TILE + P - 1;
     __shared__ float s_gray[TW * TW];
     __shared__ float s_gabs[TW * TW];
-    __shared__ float s_om[32 * N];
+    __shared__ __align__(16) float s_om[32 * NP];
     __shared__ float s_w[N];
 
     const int tid = threadIdx.y * TILE + threadIdx.x;
@@ -80,7 +81,9 @@ __global__ void __launch_bounds__(TILE* TILE)
     const bool live = (y < H) && (x < W);
     const int pix = y * W + x;
 
-    float s[N];
+    float s[NP];
+#pragma unroll
+    for (int t = N; t < NP; ++t) s[t] = 0.f;
     float sum = 0.f, kc = 0.f, vabs = 0.f, e2 = 0.f;
 #pragma unroll
     for (int dy = 0; dy < P; ++dy)
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(TILE* TILE)
 #pragma unroll
     for (int t = 0; t < N; ++t) s[t] = __fmul_rn(s[t], inv);
     const float ds = whole ? 0.f : (2.f * dc / cn) * 1.0001f + 0.5f * (N + 7) * U32;
-    const float ebase = (ds + N * U32 * (1.f + ds)) * 1.25f;
+    const float ebase = (ds + (N + 1) * U32 * (1.f + ds)) * 1.25f;
 
     if (live && whole) guard_push(guard, guard_cap, guard_count, pix, -1);
 
@@ -123,14 +126,25 @@ __global__ void __launch_bounds__(TILE* TILE)
         const int j0 = w * 32;
         const int rows = min(32, k - j0);
         __syncthreads();
-        for (int i = tid; i < rows * N; i += TILE * TILE) s_om[i] = omega[(size_t)j0 * N + i];
+        for (int i = tid; i < 32 * NP; i += TILE * TILE) {
+            const int jj = i / NP, t = i % NP;
+            s_om[i] = (jj < rows && t < N) ? omega[(size_t)(j0 + jj) * N + t] : 0.f;
+        }
         __syncthreads();
         uint32_t word = 0;
         for (int jj = 0; jj < rows; ++jj) {
-            const float* om = s_om + jj * N;
-            float a = 0.f;
+            const float4* om = reinterpret_cast<const float4*>(s_om + jj * NP);
+            // two interleaved partial sums; the bound below holds for any order
+            float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-            for (int t = 0; t < N; ++t) a = fmaf(om[t], s[t], a);
+            for (int t4 = 0; t4 < NP / 4; ++t4) {
+                const float4 o = om[t4];
+                a0 = fmaf(o.x, s[4 * t4 + 0], a0);
+                a1 = fmaf(o.y, s[4 * t4 + 1], a1);
+                a0 = fmaf(o.z, s[4 * t4 + 2], a0);
+                a1 = fmaf(o.w, s[4 * t4 + 3], a1);
+            }
+            const float a = a0 + a1;
             const int j = j0 + jj;
             if (!live) continue;
             const float aa = fabsf(a);

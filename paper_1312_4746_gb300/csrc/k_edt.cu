@@ -4,16 +4,17 @@
 //
 // Separable exact transform in integers:
 //   1. seed planes: 0 at the label's sample pixels, INF elsewhere;
-//   2. column pass (one thread per label and column): vertical distance to
-//      the nearest seed in the same column, squared;
-//   3. row pass (one thread per label and row): lower envelope of the
-//      parabolas (x - q)^2 + g(q) over the columns q with finite g, built in
-//      one sweep and read back in a second; intersection abscissae are
-//      compared as exact rationals with 64-bit cross products, so the
-//      result equals the brute-force minimum bit for bit.
+//   2. row pass (one thread per label and row): horizontal distance h to the
+//      nearest seed in the same row;
+//   3. column pass (one thread per label and column, coalesced): lower
+//      envelope of the parabolas (y - q)^2 + h(q)^2 over the rows q with
+//      finite h, built in one sweep and read back in a second; intersection
+//      abscissae are compared as exact rationals with 64-bit cross products,
+//      so the result equals the brute-force minimum bit for bit.
 // The sample gather builds SoA tables of every sample (location, colour,
 // co-support bitmask and its popcount) and, for the factorised form, the
 // majority co-support of each label (Eq. tex-rep: bit set iff 2 * count >= m).
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -54,70 +55,91 @@ __global__ void seed_kernel(const int32_t* __restrict__ off, int n_labels,
     g[(size_t)i * P + pix] = 0;
 }
 
-__global__ void cols_kernel(int H, int W, int n_labels, int32_t* __restrict__ g) {
+// Pass 1 (one thread per label and row): horizontal distance to the nearest
+// seed of the same row, in place (0 exactly at seeds, INF if the row has none).
+__global__ void rows_binary_kernel(int H, int W, int n_labels, int32_t* __restrict__ g) {
     long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= (long long)n_labels * W) return;
-    const int i = (int)(tid / W), x = (int)(tid % W);
-    int32_t* col = g + (size_t)i * H * W + x;
+    if (tid >= (long long)n_labels * H) return;
+    int32_t* row = g + (size_t)tid * W;  // label-major planes: row index i * H + y
     int last = -1;
-    for (int y = 0; y < H; ++y) {
-        int32_t v = col[(size_t)y * W];
-        if (v == 0) last = y;
-        col[(size_t)y * W] = last < 0 ? INF : y - last;  // 0 exactly at seeds
+    for (int x = 0; x < W; ++x) {
+        const int32_t v = row[x];
+        if (v == 0) last = x;
+        row[x] = last < 0 ? INF : x - last;
     }
     int next = -1;
-    for (int y = H - 1; y >= 0; --y) {
-        int32_t v = col[(size_t)y * W];
-        if (v == 0) next = y;
-        int32_t d = v;
-        if (next >= 0 && next - y < d) d = next - y;
-        col[(size_t)y * W] = d == INF ? INF : d * d;
+    for (int x = W - 1; x >= 0; --x) {
+        const int32_t v = row[x];
+        if (v == 0) next = x;
+        if (next >= 0 && next - x < v) row[x] = next - x;
     }
 }
 
-__global__ void rows_kernel(int H, int W, int n_labels, const int32_t* __restrict__ g,
-                            int32_t* __restrict__ vbuf, int32_t* __restrict__ dist2) {
-    long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= (long long)n_labels * H) return;
-    const size_t row = (size_t)tid * W;  // label-major planes: row index i * H + y
-    const int32_t* f = g + row;
-    int32_t* v = vbuf + row;
-    int32_t* out = dist2 + row;
+// Pass 2 (one thread per label and column, coalesced across a warp): lower
+// envelope over y of the parabolas (y - q)^2 + h(q)^2. The stack of envelope
+// rows v[k] and their offsets F[k] = h(v_k)^2 + v_k^2 lives either in shared
+// memory (stride = threads per block) or in global scratch (stride = total
+// threads); intersections are compared as exact rationals in 64 bits.
+template <bool SHARED>
+__global__ void cols_envelope_kernel(int H, int W, int n_labels, const int32_t* __restrict__ h,
+                                     int32_t* __restrict__ gv, int32_t* __restrict__ gF,
+                                     int32_t* __restrict__ dist2) {
+    extern __shared__ int32_t smem[];
+    const long long nthr = (long long)n_labels * W;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= nthr) return;
+    const int i = (int)(tid / W), x = (int)(tid % W);
+    int32_t *v, *F;
+    long long stride;
+    if (SHARED) {
+        v = smem + threadIdx.x;
+        F = smem + (size_t)H * blockDim.x + threadIdx.x;
+        stride = blockDim.x;
+    } else {
+        v = gv + tid;
+        F = gF + tid;
+        stride = nthr;
+    }
+    const int32_t* col = h + (size_t)i * H * W + x;
+    int32_t* out = dist2 + (size_t)i * H * W + x;
     int kk = -1;
-    for (int q = 0; q < W; ++q) {
-        const int32_t fq = f[q];
-        if (fq == INF) continue;
-        const long long Fq = (long long)fq + (long long)q * q;
+    for (int q = 0; q < H; ++q) {
+        const int32_t hq = col[(size_t)q * W];
+        if (hq == INF) continue;
+        const int32_t Fq = hq * hq + q * q;
         while (kk > 0) {
-            const int vk = v[kk], vp = v[kk - 1];
-            const long long Fv = (long long)f[vk] + (long long)vk * vk;
-            const long long Fp = (long long)f[vp] + (long long)vp * vp;
-            // drop v[kk] if its parabola is nowhere strictly below both neighbours:
-            // s(vk, q) <= z(vp, vk)  <=>  (Fq - Fv)(vk - vp) <= (Fv - Fp)(q - vk)
-            if ((Fq - Fv) * (long long)(vk - vp) <= (Fv - Fp) * (long long)(q - vk))
+            const int vk = v[kk * stride], vp = v[(kk - 1) * stride];
+            const int32_t Fv = F[kk * stride], Fp = F[(kk - 1) * stride];
+            // drop v[kk] if s(vk, q) <= z(vp, vk)
+            if ((long long)(Fq - Fv) * (vk - vp) <= (long long)(Fv - Fp) * (q - vk))
                 --kk;
             else
                 break;
         }
-        v[++kk] = q;
+        ++kk;
+        v[kk * stride] = q;
+        F[kk * stride] = Fq;
     }
     if (kk < 0) {  // no valid seed of this label (only possible after a bad sample index)
-        for (int x = 0; x < W; ++x) out[x] = INF;
+        for (int y = 0; y < H; ++y) out[(size_t)y * W] = INF;
         return;
     }
     int j = 0;
-    for (int x = 0; x < W; ++x) {
+    int vj = v[0];
+    int32_t Fj = F[0];
+    for (int y = 0; y < H; ++y) {
         while (j < kk) {
-            const int a = v[j], b = v[j + 1];
-            const long long Fa = (long long)f[a] + (long long)a * a;
-            const long long Fb = (long long)f[b] + (long long)b * b;
-            if (Fb - Fa < 2ll * x * (b - a))  // z(a, b) < x
+            const int vn = v[(j + 1) * stride];
+            const int32_t Fn = F[(j + 1) * stride];
+            if ((long long)(Fn - Fj) < 2ll * y * (vn - vj)) {  // z(vj, vn) < y
                 ++j;
-            else
+                vj = vn;
+                Fj = Fn;
+            } else {
                 break;
+            }
         }
-        const int a = v[j];
-        out[x] = (x - a) * (x - a) + f[a];
+        out[(size_t)y * W] = (y - vj) * (y - vj) + (Fj - vj * vj);
     }
 }
 
@@ -168,11 +190,24 @@ cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
     seed_kernel<<<(a.n_samples + 255) / 256, 256, 0, st>>>(a.d_label_off, a.n_labels,
                                                            a.sample_pix, a.n_samples, P, a.colbuf,
                                                            a.d_err);
-    long long ncol = (long long)a.n_labels * a.W;
-    cols_kernel<<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(a.H, a.W, a.n_labels, a.colbuf);
-    long long nrow = (long long)a.n_labels * a.H;
-    rows_kernel<<<(unsigned)((nrow + 63) / 64), 64, 0, st>>>(a.H, a.W, a.n_labels, a.colbuf,
-                                                             a.vbuf, a.dist2);
+    const long long nrow = (long long)a.n_labels * a.H;
+    rows_binary_kernel<<<(unsigned)((nrow + 63) / 64), 64, 0, st>>>(a.H, a.W, a.n_labels,
+                                                                   a.colbuf);
+    const long long ncol = (long long)a.n_labels * a.W;
+    // shared-memory stacks when at least 16 columns fit in 200 KB
+    const size_t per_thread = (size_t)a.H * 2 * sizeof(int32_t);
+    int tb = (int)std::min<size_t>(64, (200u * 1024u) / per_thread);
+    if (tb >= 16) {
+        tb = tb / 16 * 16;
+        const size_t smem = per_thread * tb;
+        cudaFuncSetAttribute(cols_envelope_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cols_envelope_kernel<true><<<(unsigned)((ncol + tb - 1) / tb), tb, smem, st>>>(
+            a.H, a.W, a.n_labels, a.colbuf, nullptr, nullptr, a.dist2);
+    } else {
+        cols_envelope_kernel<false><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(
+            a.H, a.W, a.n_labels, a.colbuf, a.vbuf, a.fbuf, a.dist2);
+    }
     return cudaGetLastError();
 }
 
