@@ -338,9 +338,10 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
     const int S = label_off[n_labels];
     const int Wk = (k + 31) / 32;
 
-    auto layout = [&](Carve& c, int32_t** d_off, int32_t** colbuf, int32_t** vbuf,
-                      int32_t** fbuf, int32_t** d2, SampleTables* t) {
+    auto layout = [&](Carve& c, int32_t** d_off, uint32_t** seedbits, int32_t** colbuf,
+                      int32_t** vbuf, int32_t** fbuf, int32_t** d2, SampleTables* t) {
         *d_off = c.take<int32_t>(n_labels + 1);
+        *seedbits = c.take<uint32_t>((size_t)n_labels * H * ((W + 31) / 32));
         *colbuf = c.take<int32_t>(P * n_labels);
         *vbuf = c.take<int32_t>(P * n_labels);
         *fbuf = c.take<int32_t>(P * n_labels);
@@ -356,18 +357,19 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
         t->rep = c.take<uint32_t>((size_t)n_labels * Wk);
     };
     int32_t *d_off, *colbuf, *vbuf, *fbuf, *d2;
+    uint32_t* seedbits;
     SampleTables t{};
     Carve m(nullptr);
-    layout(m, &d_off, &colbuf, &vbuf, &fbuf, &d2, &t);
+    layout(m, &d_off, &seedbits, &colbuf, &vbuf, &fbuf, &d2, &t);
     s = cs_ensure_scratch(ctx, m.off);
     if (s) return s;
     Carve c(ctx->scratch);
-    layout(c, &d_off, &colbuf, &vbuf, &fbuf, &d2, &t);
+    layout(c, &d_off, &seedbits, &colbuf, &vbuf, &fbuf, &d2, &t);
 
     cudaError_t e = cudaMemcpyAsync(d_off, label_off, sizeof(int32_t) * (n_labels + 1),
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
-    EdtArgs ea{H, W, n_labels, d_off, sample_pix, S, colbuf, vbuf, fbuf, d2, ctx->d_err};
+    EdtArgs ea{H, W, n_labels, d_off, sample_pix, S, seedbits, colbuf, vbuf, fbuf, d2, ctx->d_err};
     {
         StageTimer tm(ctx, CS_STAGE_DIST, st);
         e = launch_edt(ea, st);

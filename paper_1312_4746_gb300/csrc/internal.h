@@ -97,7 +97,8 @@ struct EdtArgs {
     const int32_t* d_label_off;  // device copy, n_labels + 1
     const int32_t* sample_pix;
     int n_samples;
-    int32_t* colbuf;  // scratch n_labels * P
+    uint32_t* seedbits;  // scratch n_labels * H * ceil(W/32)
+    int32_t* colbuf;  // scratch n_labels * P (horizontal distances)
     int32_t* vbuf;    // scratch n_labels * P (envelope rows, when not in shared memory)
     int32_t* fbuf;    // scratch n_labels * P (envelope offsets, likewise)
     int32_t* dist2;   // output n_labels * P

@@ -164,16 +164,20 @@ __global__ void __launch_bounds__(TILE* TILE)
         for (int j = k; j < 16; ++j) lead16[(size_t)pix * 16 + j] = 0.f;
 }
 
-// Canonical double-precision recomputation of guarded entries: the patch and
-// code follow the exact operation order of the definition (gray, mask
-// product, sequential sums, division by the square root), with every
-// operation correctly rounded and no contraction.
+// Canonical double-precision recomputation of guarded entries, one warp per
+// entry: the patch and code follow the exact operation order of the
+// definition (gray, mask product, index-order sums, division by the square
+// root), with every operation correctly rounded and no contraction. The
+// element-wise steps run across the lanes; every sum runs on lane 0 in index
+// order, so the result is bit-identical to a sequential evaluation.
 __global__ void codes_guard_kernel(const float* __restrict__ img, int H, int W,
                                    const float* __restrict__ omega, int k,
                                    const float* __restrict__ mask, int p, double tau,
                                    const int2* __restrict__ guard, int guard_cap,
                                    const int* __restrict__ guard_count,
                                    uint32_t* __restrict__ bitmask, int* __restrict__ d_err) {
+    __shared__ double s_s[4][81];
+    __shared__ double s_ab[4];
     int cnt = *guard_count;
     if (cnt > guard_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && atomicCAS(d_err, 0, CS_DEVERR_GUARD_FULL) == 0)
@@ -181,39 +185,54 @@ __global__ void codes_guard_kernel(const float* __restrict__ img, int H, int W,
         cnt = guard_cap;
     }
     const int n = p * p, r = (p - 1) / 2, Wk = (k + 31) >> 5;
-    double s[81];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double* s = s_s[wib];
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int e = blockIdx.x * (blockDim.x >> 5) + wib; e < cnt; e += warps) {
         const int2 g = guard[e];
         const int y = g.x / W, x = g.x % W;
-        double mu = 0.0;
-        for (int dy = 0; dy < p; ++dy)
-            for (int dx = 0; dx < p; ++dx) {
-                int yy = min(max(y + dy - r, 0), H - 1), xx = min(max(x + dx - r, 0), W - 1);
-                const float* px = img + ((size_t)yy * W + xx) * 3;
-                double gr = __dadd_rn(__dadd_rn(__dmul_rn(0.299, (double)px[0]),
-                                                __dmul_rn(0.587, (double)px[1])),
-                                      __dmul_rn(0.114, (double)px[2]));
-                s[dy * p + dx] = __dmul_rn((double)mask[dy * p + dx], gr);
-            }
-        for (int t = 0; t < n; ++t) mu = __dadd_rn(mu, s[t]);
-        mu = __ddiv_rn(mu, (double)n);
-        double ss = 0.0;
-        for (int t = 0; t < n; ++t) {
-            s[t] = __dadd_rn(s[t], -mu);
-            ss = __dadd_rn(ss, __dmul_rn(s[t], s[t]));
+        for (int t = lane; t < n; t += 32) {
+            const int dy = t / p, dx = t % p;
+            const int yy = min(max(y + dy - r, 0), H - 1), xx = min(max(x + dx - r, 0), W - 1);
+            const float* px = img + ((size_t)yy * W + xx) * 3;
+            const double gr = __dadd_rn(__dadd_rn(__dmul_rn(0.299, (double)px[0]),
+                                                  __dmul_rn(0.587, (double)px[1])),
+                                        __dmul_rn(0.114, (double)px[2]));
+            s[t] = __dmul_rn((double)mask[t], gr);
         }
+        __syncwarp();
+        if (lane == 0) {
+            double mu = 0.0;
+            for (int t = 0; t < n; ++t) mu = __dadd_rn(mu, s[t]);
+            s_ab[wib] = __ddiv_rn(mu, (double)n);
+        }
+        __syncwarp();
+        const double mu = s_ab[wib];
+        for (int t = lane; t < n; t += 32) s[t] = __dadd_rn(s[t], -mu);
+        __syncwarp();
+        if (lane == 0) {
+            double ss = 0.0;
+            for (int t = 0; t < n; ++t) ss = __dadd_rn(ss, __dmul_rn(s[t], s[t]));
+            s_ab[wib] = ss;
+        }
+        __syncwarp();
+        const double ss = s_ab[wib];
         if (ss == 0.0) {
-            for (int t = 0; t < n; ++t) s[t] = 0.0;
+            for (int t = lane; t < n; t += 32) s[t] = 0.0;
         } else {
             const double nrm = __dsqrt_rn(ss);
-            for (int t = 0; t < n; ++t) s[t] = __ddiv_rn(s[t], nrm);
+            for (int t = lane; t < n; t += 32) s[t] = __ddiv_rn(s[t], nrm);
         }
+        __syncwarp();
+        // codes: one lane per code index, each an index-order dot product
         const int jlo = g.y < 0 ? 0 : g.y, jhi = g.y < 0 ? k : g.y + 1;
-        for (int j = jlo; j < jhi; ++j) {
+        for (int j = jlo + lane; j < jhi; j += 32) {
             double a = 0.0;
-            for (int t = 0; t < n; ++t) a = __dadd_rn(a, __dmul_rn((double)omega[(size_t)j * n + t], s[t]));
+            for (int t = 0; t < n; ++t)
+                a = __dadd_rn(a, __dmul_rn((double)omega[(size_t)j * n + t], s[t]));
             if (fabs(a) <= tau) atomicOr(bitmask + (size_t)g.x * Wk + (j >> 5), 1u << (j & 31));
         }
+        __syncwarp();
     }
 }
 
@@ -262,7 +281,7 @@ cudaError_t launch_codes_f32(const CodesArgs& a, cudaStream_t st) {
     }
     if (e != cudaSuccess) return e;
     if (!a.bitmask) return cudaSuccess;
-    codes_guard_kernel<<<152 * 2, 128, 0, st>>>(a.img, a.H, a.W, a.omega, a.k, a.mask, a.p, a.tau,
+    codes_guard_kernel<<<152 * 4, 128, 0, st>>>(a.img, a.H, a.W, a.omega, a.k, a.mask, a.p, a.tau,
                                                 a.guard, a.guard_cap, a.guard_count, a.bitmask,
                                                 a.d_err);
     return cudaGetLastError();

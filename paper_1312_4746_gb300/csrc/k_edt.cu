@@ -3,9 +3,9 @@
 // location of label i).
 //
 // Separable exact transform in integers:
-//   1. seed planes: 0 at the label's sample pixels, INF elsewhere;
-//   2. row pass (one thread per label and row): horizontal distance h to the
-//      nearest seed in the same row;
+//   1. seed bitmaps: one bit per pixel and label;
+//   2. row pass (one warp per label and row): horizontal distance h to the
+//      nearest seed in the same row, from bit scans of the bitmap words;
 //   3. column pass (one thread per label and column, coalesced): lower
 //      envelope of the parabolas (y - q)^2 + h(q)^2 over the rows q with
 //      finite h, built in one sweep and read back in a second; intersection
@@ -35,43 +35,52 @@ __device__ __forceinline__ int label_of(const int32_t* __restrict__ off, int n_l
     return lo;
 }
 
-__global__ void fill_kernel(int32_t* __restrict__ p, long long n, int32_t v) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        p[i] = v;
-}
-
+// Seed bitmap: bit (x & 31) of word [i][y][x >> 5] is set when (y, x) is a
+// sample of label i.
 __global__ void seed_kernel(const int32_t* __restrict__ off, int n_labels,
-                            const int32_t* __restrict__ sample_pix, int n_samples, long long P,
-                            int32_t* __restrict__ g, int* __restrict__ d_err) {
+                            const int32_t* __restrict__ sample_pix, int n_samples, int H, int W,
+                            uint32_t* __restrict__ bm, int* __restrict__ d_err) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_samples) return;
     const int pix = sample_pix[s];
-    if (pix < 0 || pix >= P) {  // reject out-of-image sample indices, never write them
+    if (pix < 0 || pix >= H * W) {  // reject out-of-image sample indices, never write them
         if (atomicCAS(d_err, 0, CS_DEVERR_BAD_SAMPLE) == 0) d_err[1] = s;
         return;
     }
-    int i = label_of(off, n_labels, s);
-    g[(size_t)i * P + pix] = 0;
+    const int i = label_of(off, n_labels, s);
+    const int y = pix / W, x = pix % W, Wb = (W + 31) >> 5;
+    atomicOr(bm + ((size_t)i * H + y) * Wb + (x >> 5), 1u << (x & 31));
 }
 
-// Pass 1 (one thread per label and row): horizontal distance to the nearest
-// seed of the same row, in place (0 exactly at seeds, INF if the row has none).
-__global__ void rows_binary_kernel(int H, int W, int n_labels, int32_t* __restrict__ g) {
-    long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= (long long)n_labels * H) return;
-    int32_t* row = g + (size_t)tid * W;  // label-major planes: row index i * H + y
-    int last = -1;
-    for (int x = 0; x < W; ++x) {
-        const int32_t v = row[x];
-        if (v == 0) last = x;
-        row[x] = last < 0 ? INF : x - last;
+// Pass 1 (one warp per label and row): horizontal distance to the nearest
+// seed of the same row (INF if the row has none), from the seed bitmap with
+// ballot-free bit scans; a forward sweep finds the last seed at or left of
+// each pixel, a backward sweep the next seed at or right of it.
+__global__ void rows_binary_kernel(int H, int W, int n_labels, const uint32_t* __restrict__ bm,
+                                   int32_t* __restrict__ h) {
+    const long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= (long long)n_labels * H) return;
+    const int Wb = (W + 31) >> 5;
+    const uint32_t* b = bm + (size_t)row * Wb;
+    int32_t* out = h + (size_t)row * W;
+    int carry = -1;  // last seed column seen so far
+    for (int c = 0; c < Wb; ++c) {
+        const uint32_t word = b[c];
+        const uint32_t le = word & (lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u));
+        const int last = le ? 32 * c + 31 - __clz(le) : carry;
+        const int x = 32 * c + lane;
+        if (x < W) out[x] = last < 0 ? INF : x - last;
+        if (word) carry = 32 * c + 31 - __clz(word);
     }
-    int next = -1;
-    for (int x = W - 1; x >= 0; --x) {
-        const int32_t v = row[x];
-        if (v == 0) next = x;
-        if (next >= 0 && next - x < v) row[x] = next - x;
+    carry = -1;  // next seed column seen so far (from the right)
+    for (int c = Wb - 1; c >= 0; --c) {
+        const uint32_t word = b[c];
+        const uint32_t ge = word & (0xFFFFFFFFu << lane);
+        const int next = ge ? 32 * c + __ffs(ge) - 1 : carry;
+        const int x = 32 * c + lane;
+        if (x < W && next >= 0 && next - x < out[x]) out[x] = next - x;
+        if (word) carry = 32 * c + __ffs(word) - 1;
     }
 }
 
@@ -103,22 +112,30 @@ __global__ void cols_envelope_kernel(int H, int W, int n_labels, const int32_t* 
     const int32_t* col = h + (size_t)i * H * W + x;
     int32_t* out = dist2 + (size_t)i * H * W + x;
     int kk = -1;
-    for (int q = 0; q < H; ++q) {
-        const int32_t hq = col[(size_t)q * W];
-        if (hq == INF) continue;
-        const int32_t Fq = hq * hq + q * q;
-        while (kk > 0) {
-            const int vk = v[kk * stride], vp = v[(kk - 1) * stride];
-            const int32_t Fv = F[kk * stride], Fp = F[(kk - 1) * stride];
-            // drop v[kk] if s(vk, q) <= z(vp, vk)
-            if ((long long)(Fq - Fv) * (vk - vp) <= (long long)(Fv - Fp) * (q - vk))
-                --kk;
-            else
-                break;
+    constexpr int PF = 16;  // rows of h fetched ahead (independent loads)
+    for (int q0 = 0; q0 < H; q0 += PF) {
+        int32_t hv[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) hv[u] = q0 + u < H ? col[(size_t)(q0 + u) * W] : INF;
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int q = q0 + u;
+            const int32_t hq = hv[u];
+            if (hq == INF) continue;
+            const int32_t Fq = hq * hq + q * q;
+            while (kk > 0) {
+                const int vk = v[kk * stride], vp = v[(kk - 1) * stride];
+                const int32_t Fv = F[kk * stride], Fp = F[(kk - 1) * stride];
+                // drop v[kk] if s(vk, q) <= z(vp, vk)
+                if ((long long)(Fq - Fv) * (vk - vp) <= (long long)(Fv - Fp) * (q - vk))
+                    --kk;
+                else
+                    break;
+            }
+            ++kk;
+            v[kk * stride] = q;
+            F[kk * stride] = Fq;
         }
-        ++kk;
-        v[kk * stride] = q;
-        F[kk * stride] = Fq;
     }
     if (kk < 0) {  // no valid seed of this label (only possible after a bad sample index)
         for (int y = 0; y < H; ++y) out[(size_t)y * W] = INF;
@@ -184,19 +201,19 @@ __global__ void majority_kernel(const int32_t* __restrict__ off, int n_labels, i
 }  // namespace
 
 cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
-    const long long P = (long long)a.H * a.W;
-    const long long n = P * a.n_labels;
-    fill_kernel<<<152 * 8, 256, 0, st>>>(a.colbuf, n, INF);
-    seed_kernel<<<(a.n_samples + 255) / 256, 256, 0, st>>>(a.d_label_off, a.n_labels,
-                                                           a.sample_pix, a.n_samples, P, a.colbuf,
-                                                           a.d_err);
+    const int Wb = (a.W + 31) / 32;
     const long long nrow = (long long)a.n_labels * a.H;
-    rows_binary_kernel<<<(unsigned)((nrow + 63) / 64), 64, 0, st>>>(a.H, a.W, a.n_labels,
-                                                                   a.colbuf);
+    cudaError_t e = cudaMemsetAsync(a.seedbits, 0, sizeof(uint32_t) * nrow * Wb, st);
+    if (e != cudaSuccess) return e;
+    seed_kernel<<<(a.n_samples + 255) / 256, 256, 0, st>>>(a.d_label_off, a.n_labels,
+                                                           a.sample_pix, a.n_samples, a.H, a.W,
+                                                           a.seedbits, a.d_err);
+    rows_binary_kernel<<<(unsigned)((nrow * 32 + 127) / 128), 128, 0, st>>>(
+        a.H, a.W, a.n_labels, a.seedbits, a.colbuf);
     const long long ncol = (long long)a.n_labels * a.W;
-    // shared-memory stacks when at least 16 columns fit in 200 KB
+    // shared-memory stacks when at least 16 columns fit in 100 KB
     const size_t per_thread = (size_t)a.H * 2 * sizeof(int32_t);
-    int tb = (int)std::min<size_t>(64, (200u * 1024u) / per_thread);
+    int tb = (int)std::min<size_t>(32, (100u * 1024u) / per_thread);
     if (tb >= 16) {
         tb = tb / 16 * 16;
         const size_t smem = per_thread * tb;
@@ -205,7 +222,7 @@ cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
         cols_envelope_kernel<true><<<(unsigned)((ncol + tb - 1) / tb), tb, smem, st>>>(
             a.H, a.W, a.n_labels, a.colbuf, nullptr, nullptr, a.dist2);
     } else {
-        cols_envelope_kernel<false><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(
+        cols_envelope_kernel<false><<<(unsigned)((ncol + 63) / 64), 64, 0, st>>>(
             a.H, a.W, a.n_labels, a.colbuf, a.vbuf, a.fbuf, a.dist2);
     }
     return cudaGetLastError();
