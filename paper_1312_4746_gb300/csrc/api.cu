@@ -150,6 +150,7 @@ cs_status cs_create(cs_ctx** out, int device) {
     cs_ctx* c = new cs_ctx();
     c->device = device;
     DeviceGuard g(device);
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_err, 2 * sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_err, 0, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -332,15 +333,31 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
     if (s) return s;
     if (k > 256)
         return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "%s: k=%d > 256 not supported yet", fn, k);
+    const bool tc_form = prm->precision != CS_FP32;
+    const bool tex8 = prm->precision == CS_FP8;
+    const bool persample = prm->mode == CS_MODE_PERSAMPLE;
+    if (tc_form && !tc_supported(k, tex8))
+        return cs_set_error(ctx, CS_ERR_UNSUPPORTED,
+                            "%s: k=%d too large for the %s tensor-core form", fn, k,
+                            tex8 ? "FP8" : "BF16");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const long long P = (long long)H * W;
     const int S = label_off[n_labels];
     const int Wk = (k + 31) / 32;
+    // label offsets and, for the tensor-core form, the first sample tile of each label
+    std::vector<int32_t> hoff(2 * (n_labels + 1));
+    for (int i = 0; i <= n_labels; ++i) hoff[i] = label_off[i];
+    hoff[n_labels + 1] = 0;
+    for (int i = 0; i < n_labels; ++i)
+        hoff[n_labels + 2 + i] =
+            hoff[n_labels + 1 + i] + tc_tiles_per_label(label_off[i + 1] - label_off[i]);
+    const int total_tiles = hoff[2 * n_labels + 1];
+    const size_t stage_bytes = tc_stage_bytes(k, tex8, persample);
 
     auto layout = [&](Carve& c, int32_t** d_off, uint32_t** seedbits, int32_t** colbuf,
                       int32_t** vbuf, int32_t** fbuf, int32_t** d2, SampleTables* t) {
-        *d_off = c.take<int32_t>(n_labels + 1);
+        *d_off = c.take<int32_t>(2 * (n_labels + 1));
         *seedbits = c.take<uint32_t>((size_t)n_labels * H * ((W + 31) / 32));
         *colbuf = c.take<int32_t>(P * n_labels);
         *vbuf = c.take<int32_t>(P * n_labels);
@@ -355,6 +372,7 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
         t->sbits = c.take<uint32_t>((size_t)Wk * S);
         t->spop = c.take<int32_t>(S);
         t->rep = c.take<uint32_t>((size_t)n_labels * Wk);
+        t->blob = c.take<uint8_t>(tc_form ? (size_t)total_tiles * stage_bytes : 0, 1024);
     };
     int32_t *d_off, *colbuf, *vbuf, *fbuf, *d2;
     uint32_t* seedbits;
@@ -366,7 +384,7 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
     Carve c(ctx->scratch);
     layout(c, &d_off, &seedbits, &colbuf, &vbuf, &fbuf, &d2, &t);
 
-    cudaError_t e = cudaMemcpyAsync(d_off, label_off, sizeof(int32_t) * (n_labels + 1),
+    cudaError_t e = cudaMemcpyAsync(d_off, hoff.data(), sizeof(int32_t) * hoff.size(),
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     EdtArgs ea{H, W, n_labels, d_off, sample_pix, S, seedbits, colbuf, vbuf, fbuf, d2, ctx->d_err};
@@ -400,7 +418,35 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
         a.mode = prm->mode;
         a.neglog = neglog;
         a.post = post;
-        e = launch_sum_plain(a, st);
+        if (!tc_form) {
+            e = launch_sum_plain(a, st);
+        } else {
+            TcLaunch L{};
+            L.img = img;
+            L.H = H;
+            L.W = W;
+            L.bitmask = bitmask;
+            L.k = k;
+            L.n_labels = n_labels;
+            L.d_label_off = d_off;
+            L.d_tile_off = d_off + n_labels + 1;
+            L.total_tiles = total_tiles;
+            L.n_samples = S;
+            L.t = t;
+            L.blob = t.blob;
+            L.dist2 = d2;
+            L.alpha = a.alpha;
+            L.d_min = a.d_min;
+            L.kappa_beta = a.kappa_beta;
+            L.sigma_c2 = a.sigma_c2;
+            L.neglog = neglog;
+            L.post = post;
+            L.d_err = ctx->d_err;
+            L.n_sm = ctx->n_sm;
+            L.tex8 = tex8;
+            L.persample = persample;
+            e = launch_sum_tc(L, st);
+        }
     }
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return cs_check_launch(ctx, fn);

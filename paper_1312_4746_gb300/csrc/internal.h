@@ -31,6 +31,7 @@ struct cs_ctx {
     char* scratch = nullptr;
     size_t scratch_cap = 0;
     int* d_err = nullptr;  // 2 ints
+    int n_sm = 148;
     bool profiling = false;
     std::vector<StageRecord> records;
     std::vector<cudaEvent_t> event_pool;
@@ -116,6 +117,7 @@ struct SampleTables {
     uint32_t* sbits;  // word-major: [Wk][S]
     int32_t* spop;    // popcount of each sample's bitmask
     uint32_t* rep;    // [n_labels][Wk]
+    uint8_t* blob;    // tensor-core sample tiles (ring-stage layout)
 };
 cudaError_t launch_gather(const float* img, int H, int W, const uint32_t* bitmask, int k,
                           int n_labels, const int32_t* d_label_off, const int32_t* sample_pix,
@@ -139,3 +141,30 @@ struct SumArgs {
     float* post;
 };
 cudaError_t launch_sum_plain(const SumArgs& a, cudaStream_t st);
+
+// Tensor-core (tcgen05) pixel x sample sum.
+struct TcLaunch {
+    const float* img;
+    int H, W;
+    const uint32_t* bitmask;
+    int k;
+    int n_labels;
+    const int32_t* d_label_off;
+    const int32_t* d_tile_off;
+    int total_tiles;
+    int n_samples;
+    SampleTables t;
+    uint8_t* blob;
+    const int32_t* dist2;
+    float alpha, d_min, kappa_beta, sigma_c2;
+    float* neglog;
+    float* post;
+    int* d_err;
+    int n_sm;
+    bool tex8;       // texture operands in FP8 (else BF16)
+    bool persample;  // per-sample texture kernel (else factorised)
+};
+size_t tc_stage_bytes(int k, bool tex8, bool persample);
+int tc_tiles_per_label(int m);
+bool tc_supported(int k, bool tex8);
+cudaError_t launch_sum_tc(const TcLaunch& L, cudaStream_t st);
