@@ -25,7 +25,8 @@
  *    with cs_sync_status().
  *  - No call throws, exits or aborts. cs_last_error() describes the most
  *    recent failure on the context.
- *  - One context may be used from one host thread at a time.
+ *  - One context may be used from one host thread at a time, and its calls
+ *    must be ordered on one stream: they share the context's scratch memory.
  */
 #ifndef COSPARSE_H
 #define COSPARSE_H
@@ -173,6 +174,21 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
                         int k, int n_labels, const int32_t* label_off,
                         const int32_t* sample_pix, const cs_params* prm, int32_t* dist2,
                         float* neglog, float* post, void* stream);
+
+/*
+ * The whole data term in one call: patches, codes and co-support bitmasks of
+ * every pixel (as cs_codes) followed by the likelihoods (as cs_likelihood).
+ * The scribble distance transform depends only on the samples; it runs on a
+ * context-owned stream concurrently with the codes and is joined (CUDA
+ * events) before the sum. Arguments as in cs_codes / cs_likelihood; bitmask
+ * (DEVICE P x ceil(k/32) uint32) and dist2 may be NULL, in which case they
+ * live in scratch. Capturable in a CUDA graph once a first call has sized
+ * the scratch (the call allocates only when the scratch must grow).
+ */
+cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float* omega, int k,
+                       const float* mask, int n_labels, const int32_t* label_off,
+                       const int32_t* sample_pix, const cs_params* prm, uint32_t* bitmask,
+                       int32_t* dist2, float* neglog, float* post, void* stream);
 
 /*
  * Stage timing. While enabled, every call records a pair of CUDA events on

@@ -40,6 +40,7 @@ EXPORTS = (
     "cs_codes",
     "cs_cosupport",
     "cs_likelihood",
+    "cs_data_term",
     "cs_profile_enable",
     "cs_profile_read",
 )
@@ -116,10 +117,11 @@ def lib(path: str | None = None):
     L.cs_codes.argtypes = [V, V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V]
     L.cs_cosupport.argtypes = [V, V, I, I, D, V, V]
     L.cs_likelihood.argtypes = [V, V, I, I, V, I, I, V, V, ctypes.POINTER(Params), V, V, V, V]
+    L.cs_data_term.argtypes = [V, V, I, I, V, I, V, I, V, V, ctypes.POINTER(Params), V, V, V, V, V]
     L.cs_profile_enable.argtypes = [V, I]
     L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     for f in ("cs_create", "cs_sync_status", "cs_codes", "cs_cosupport", "cs_likelihood",
-              "cs_profile_enable", "cs_profile_read"):
+              "cs_data_term", "cs_profile_enable", "cs_profile_read"):
         getattr(L, f).restype = I
     if path is None:
         _lib = L
@@ -231,6 +233,36 @@ class Context:
             self.handle, _ptr(img), H, W, _ptr(bitmask), int(k), nl,
             ctypes.c_void_p(off.ctypes.data), _ptr(sample_pix), ctypes.byref(params),
             _ptr(out.get("dist2")), _ptr(out["neglog"]), _ptr(out.get("post")), _stream()))
+        return out
+
+
+    def data_term(self, img, omega, mask, label_off, sample_pix, params: Params,
+                  want_bitmask=False, want_dist2=False, want_post=True, out=None):
+        """cs_data_term: codes, co-supports and likelihoods in one call.
+        Returns dict with 'neglog' (n, H, W) and optionally 'post', 'bitmask',
+        'dist2'. ``label_off`` is a host array; the other inputs are device
+        tensors."""
+        import numpy as np
+        import torch
+
+        H, W = int(img.shape[0]), int(img.shape[1])
+        k = int(omega.shape[0])
+        off = np.ascontiguousarray(np.asarray(label_off, dtype=np.int32))
+        nl = len(off) - 1
+        dev = img.device
+        if out is None:
+            out = {
+                "neglog": torch.empty((nl, H, W), dtype=torch.float32, device=dev),
+                "post": torch.empty((nl, H, W), dtype=torch.float32, device=dev) if want_post else None,
+                "dist2": torch.empty((nl, H, W), dtype=torch.int32, device=dev) if want_dist2 else None,
+                "bitmask": (torch.empty((H * W, (k + 31) // 32), dtype=torch.int32, device=dev)
+                            if want_bitmask else None),
+            }
+        self.check(self._lib.cs_data_term(
+            self.handle, _ptr(img), H, W, _ptr(omega), k, _ptr(mask), nl,
+            ctypes.c_void_p(off.ctypes.data), _ptr(sample_pix), ctypes.byref(params),
+            _ptr(out.get("bitmask")), _ptr(out.get("dist2")), _ptr(out["neglog"]),
+            _ptr(out.get("post")), _stream()))
         return out
 
 

@@ -152,10 +152,16 @@ cs_status cs_create(cs_ctx** out, int device) {
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_err, 2 * sizeof(int)) != cudaSuccess ||
-        cudaMemset(c->d_err, 0, 2 * sizeof(int)) != cudaSuccess) {
+        cudaMemset(c->d_err, 0, 2 * sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (c->d_err) cudaFree(c->d_err);
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
         delete c;
-        return cs_set_error(nullptr, CS_ERR_CUDA, "cs_create: cannot allocate the error word");
+        return cs_set_error(nullptr, CS_ERR_CUDA, "cs_create: cannot set up the context");
     }
     *out = c;
     return CS_OK;
@@ -172,6 +178,9 @@ void cs_destroy(cs_ctx* ctx) {
         cudaEventDestroy(r.end);
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
 }
 
@@ -205,7 +214,7 @@ cs_status cs_sync_status(cs_ctx* ctx, void* stream) {
     return cs_set_error(ctx, CS_ERR_DEVICE, "device error %d (detail %d)", h[0], h[1]);
 }
 
-// ---------------------------------------------------------------- cs_codes
+// ---------------------------------------------------------------- planning helpers
 
 static int guard_capacity(long long P, int k) {
     long long cap = P * (long long)k / 128 + 65536;
@@ -213,60 +222,224 @@ static int guard_capacity(long long P, int k) {
     return (int)cap;
 }
 
-cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* omega, int k,
-                   const float* mask, const cs_params* prm, float* codes, float* lead16,
-                   uint32_t* bitmask, void* stream) {
-    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_codes: ctx is NULL");
-    if (!img || !omega || !mask || !prm)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_codes: null input pointer");
+static cs_status check_image(cs_ctx* ctx, const char* fn, int H, int W, int k) {
     if (H < 1 || W < 1 || H > CS_MAX_SIDE || W > CS_MAX_SIDE)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_codes: bad image size %dx%d", W, H);
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: bad image size %dx%d", fn, W, H);
     if (k < 1 || k > CS_MAX_K)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_codes: k=%d outside 1..%d", k, CS_MAX_K);
-    if (!codes && !lead16 && !bitmask)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_codes: no output requested");
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: k=%d outside 1..%d", fn, k, CS_MAX_K);
+    return CS_OK;
+}
+
+static cs_status check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm) {
+    if (!prm) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: params is NULL", fn);
     if (prm->p < 1 || (prm->p & 1) == 0)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_codes: patch side %d is not odd", prm->p);
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: patch side %d is not odd", fn, prm->p);
     if (prm->p < 3 || prm->p > 9)
-        return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "cs_codes: patch side %d not in 3..9",
-                            prm->p);
+        return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "%s: patch side %d not in 3..9", fn, prm->p);
     if (!(prm->tau >= 0.0))
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_codes: tau must be >= 0");
-    DeviceGuard g(ctx->device);
-    long long P = (long long)H * W;
-    int cap = guard_capacity(P, k);
-    Carve m(nullptr);
-    m.take<float>(k);
-    m.take<int>(1);
-    m.take<int2>(cap);
-    if (!bitmask) m.take<uint32_t>(P * ((k + 31) / 32));
-    cs_status s = cs_ensure_scratch(ctx, m.off);
-    if (s) return s;
-    Carve c(ctx->scratch);
-    CodesArgs a{};
-    a.img = img;
-    a.H = H;
-    a.W = W;
-    a.omega = omega;
-    a.k = k;
-    a.mask = mask;
-    a.p = prm->p;
-    a.tau = prm->tau;
-    a.codes = codes;
-    a.lead16 = lead16;
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: tau must be >= 0", fn);
+    return CS_OK;
+}
+
+static cs_status check_labels(cs_ctx* ctx, const char* fn, int n_labels,
+                              const int32_t* label_off) {
+    if (n_labels < 1 || n_labels > CS_MAX_LABELS)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: n_labels=%d outside 1..%d", fn,
+                            n_labels, CS_MAX_LABELS);
+    if (!label_off) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: label_off is NULL", fn);
+    if (label_off[0] != 0)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: label_off[0] must be 0", fn);
+    for (int i = 0; i < n_labels; ++i)
+        if (label_off[i + 1] - label_off[i] < 1)
+            return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: label %d has no scribble samples",
+                                fn, i);
+    return CS_OK;
+}
+
+static cs_status check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k) {
+    if (!prm) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: params is NULL", fn);
+    if (!(prm->sigma_c2 > 0) || !(prm->alpha > 0) || !(prm->d_min > 0) || !(prm->kappa_beta > 0))
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG,
+                            "%s: sigma_c2, alpha, d_min and kappa_beta must be > 0", fn);
+    if (prm->mode != CS_MODE_PERSAMPLE && prm->mode != CS_MODE_FACTORISED)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown mode %d", fn, prm->mode);
+    if (prm->precision != CS_FP32 && prm->precision != CS_BF16 && prm->precision != CS_FP8)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown precision %d", fn,
+                            prm->precision);
+    if (k > 256)
+        return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "%s: k=%d > 256 not supported", fn, k);
+    if (prm->precision != CS_FP32 && !tc_supported(k, prm->precision == CS_FP8))
+        return cs_set_error(ctx, CS_ERR_UNSUPPORTED,
+                            "%s: k=%d too large for the %s tensor-core form", fn, k,
+                            prm->precision == CS_FP8 ? "FP8" : "BF16");
+    return CS_OK;
+}
+
+// Scratch layout of the codes stage.
+static void plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitmask) {
+    const int cap = guard_capacity(P, k);
     a.rownorm = c.take<float>(k);
     a.guard_count = c.take<int>(1);
     a.guard = c.take<int2>(cap);
     a.guard_cap = cap;
-    a.bitmask = bitmask ? bitmask : c.take<uint32_t>(P * ((k + 31) / 32));
-    a.d_err = ctx->d_err;
+    if (own_bitmask) a.bitmask = c.take<uint32_t>(P * ((k + 31) / 32));
+}
+
+// Everything the likelihood stage needs besides the caller's buffers.
+struct LikPlan {
+    int H, W, k, n_labels, S, total_tiles;
+    bool tc_form, tex8, persample;
+    size_t stage_bytes;
+    OffsetsParam offs;  // label offsets then first sample tile of each label
+    int32_t* d_off;
+    uint32_t* seedbits;
+    int32_t *colbuf, *vbuf, *fbuf, *d2;
+    SampleTables t;
+};
+
+static void plan_likelihood(LikPlan& L, int H, int W, int k, int n_labels,
+                            const int32_t* label_off, const cs_params* prm) {
+    L.H = H;
+    L.W = W;
+    L.k = k;
+    L.n_labels = n_labels;
+    L.S = label_off[n_labels];
+    L.tc_form = prm->precision != CS_FP32;
+    L.tex8 = prm->precision == CS_FP8;
+    L.persample = prm->mode == CS_MODE_PERSAMPLE;
+    for (int i = 0; i <= n_labels; ++i) L.offs.v[i] = label_off[i];
+    L.offs.v[n_labels + 1] = 0;
+    for (int i = 0; i < n_labels; ++i)
+        L.offs.v[n_labels + 2 + i] =
+            L.offs.v[n_labels + 1 + i] + tc_tiles_per_label(label_off[i + 1] - label_off[i]);
+    L.total_tiles = L.offs.v[2 * n_labels + 1];
+    L.stage_bytes = tc_stage_bytes(k, L.tex8, L.persample);
+}
+
+static void carve_likelihood(Carve& c, LikPlan& L, int32_t* dist2) {
+    const long long P = (long long)L.H * L.W;
+    const int n = L.n_labels, S = L.S, Wk = (L.k + 31) / 32;
+    L.d_off = c.take<int32_t>(2 * (n + 1));
+    L.seedbits = c.take<uint32_t>((size_t)n * L.H * ((L.W + 31) / 32));
+    L.colbuf = c.take<int32_t>(P * n);
+    L.vbuf = c.take<int32_t>(P * n);
+    L.fbuf = c.take<int32_t>(P * n);
+    int32_t* d2s = c.take<int32_t>(dist2 ? 0 : P * n);
+    L.d2 = dist2 ? dist2 : d2s;
+    L.t.sx = c.take<float>(S);
+    L.t.sy = c.take<float>(S);
+    L.t.sr = c.take<float>(S);
+    L.t.sg = c.take<float>(S);
+    L.t.sb = c.take<float>(S);
+    L.t.sbits = c.take<uint32_t>((size_t)Wk * S);
+    L.t.spop = c.take<int32_t>(S);
+    L.t.rep = c.take<uint32_t>((size_t)n * Wk);
+    L.t.blob = c.take<uint8_t>(L.tc_form ? (size_t)L.total_tiles * L.stage_bytes : 0, 1024);
+}
+
+static cudaError_t enqueue_codes(cs_ctx* ctx, const CodesArgs& a, cudaStream_t st) {
+    StageTimer tm(ctx, CS_STAGE_CODES, st);
+    return launch_codes_f32(a, st);
+}
+
+// Distance transform (on `side` when given, else on `st`), then gather and sum on `st`.
+static cudaError_t enqueue_distances(cs_ctx* ctx, const LikPlan& L, const int32_t* sample_pix,
+                                     cudaStream_t st) {
+    cudaError_t e = launch_set_offsets(L.offs, 2 * (L.n_labels + 1), L.d_off, st);
+    if (e != cudaSuccess) return e;
+    EdtArgs ea{L.H, L.W, L.n_labels, L.d_off, sample_pix, L.S, L.seedbits, L.colbuf,
+               L.vbuf, L.fbuf, L.d2, ctx->d_err};
+    StageTimer tm(ctx, CS_STAGE_DIST, st);
+    return launch_edt(ea, st);
+}
+
+static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
+                               const uint32_t* bitmask, const int32_t* sample_pix,
+                               const cs_params* prm, float* neglog, float* post,
+                               cudaStream_t st) {
     cudaError_t e;
     {
-        StageTimer tm(ctx, CS_STAGE_CODES, (cudaStream_t)stream);
-        e = launch_codes_f32(a, (cudaStream_t)stream);
+        StageTimer tm(ctx, CS_STAGE_GATHER, st);
+        e = launch_gather(img, L.H, L.W, bitmask, L.k, L.n_labels, L.d_off, sample_pix, L.S,
+                          !L.persample, L.t, st);
     }
-    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "cs_codes: %s", cudaGetErrorString(e));
-    return cs_check_launch(ctx, "cs_codes");
+    if (e != cudaSuccess) return e;
+    StageTimer tm(ctx, CS_STAGE_SUM, st);
+    if (!L.tc_form) {
+        SumArgs a{};
+        a.img = img;
+        a.H = L.H;
+        a.W = L.W;
+        a.bitmask = bitmask;
+        a.k = L.k;
+        a.Wk = (L.k + 31) / 32;
+        a.n_labels = L.n_labels;
+        a.d_label_off = L.d_off;
+        a.n_samples = L.S;
+        a.t = L.t;
+        a.dist2 = L.d2;
+        a.alpha = (float)prm->alpha;
+        a.d_min = (float)prm->d_min;
+        a.kappa_beta = (float)prm->kappa_beta;
+        a.sigma_c2 = (float)prm->sigma_c2;
+        a.mode = prm->mode;
+        a.neglog = neglog;
+        a.post = post;
+        return launch_sum_plain(a, st);
+    }
+    TcLaunch T{};
+    T.img = img;
+    T.H = L.H;
+    T.W = L.W;
+    T.bitmask = bitmask;
+    T.k = L.k;
+    T.n_labels = L.n_labels;
+    T.d_label_off = L.d_off;
+    T.d_tile_off = L.d_off + L.n_labels + 1;
+    T.total_tiles = L.total_tiles;
+    T.n_samples = L.S;
+    T.t = L.t;
+    T.blob = L.t.blob;
+    T.dist2 = L.d2;
+    T.alpha = (float)prm->alpha;
+    T.d_min = (float)prm->d_min;
+    T.kappa_beta = (float)prm->kappa_beta;
+    T.sigma_c2 = (float)prm->sigma_c2;
+    T.neglog = neglog;
+    T.post = post;
+    T.d_err = ctx->d_err;
+    T.n_sm = ctx->n_sm;
+    T.tex8 = L.tex8;
+    T.persample = L.persample;
+    return launch_sum_tc(T, st);
+}
+
+// ---------------------------------------------------------------- entry points
+
+cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* omega, int k,
+                   const float* mask, const cs_params* prm, float* codes, float* lead16,
+                   uint32_t* bitmask, void* stream) {
+    const char* fn = "cs_codes";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!img || !omega || !mask)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null input pointer", fn);
+    if (!codes && !lead16 && !bitmask)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: no output requested", fn);
+    cs_status s = check_image(ctx, fn, H, W, k);
+    if (!s) s = check_patch(ctx, fn, prm);
+    if (s) return s;
+    DeviceGuard g(ctx->device);
+    const long long P = (long long)H * W;
+    CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, codes, lead16, bitmask};
+    Carve m(nullptr);
+    plan_codes(m, a, P, k, !bitmask);
+    if ((s = cs_ensure_scratch(ctx, m.off))) return s;
+    Carve c(ctx->scratch);
+    plan_codes(c, a, P, k, !bitmask);
+    a.d_err = ctx->d_err;
+    cudaError_t e = enqueue_codes(ctx, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return cs_check_launch(ctx, fn);
 }
 
 cs_status cs_cosupport(cs_ctx* ctx, const float* codes, int P, int k, double tau,
@@ -285,36 +458,6 @@ cs_status cs_cosupport(cs_ctx* ctx, const float* codes, int P, int k, double tau
     return cs_check_launch(ctx, "cs_cosupport");
 }
 
-// ---------------------------------------------------------------- cs_likelihood
-
-static cs_status check_labels(cs_ctx* ctx, const char* fn, int n_labels,
-                              const int32_t* label_off) {
-    if (n_labels < 1 || n_labels > CS_MAX_LABELS)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: n_labels=%d outside 1..%d", fn,
-                            n_labels, CS_MAX_LABELS);
-    if (!label_off) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: label_off is NULL", fn);
-    if (label_off[0] != 0)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: label_off[0] must be 0", fn);
-    for (int i = 0; i < n_labels; ++i)
-        if (label_off[i + 1] - label_off[i] < 1)
-            return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: label %d has no scribble samples",
-                                fn, i);
-    return CS_OK;
-}
-
-static cs_status check_params(cs_ctx* ctx, const char* fn, const cs_params* prm) {
-    if (!prm) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: params is NULL", fn);
-    if (!(prm->sigma_c2 > 0) || !(prm->alpha > 0) || !(prm->d_min > 0) || !(prm->kappa_beta > 0))
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG,
-                            "%s: sigma_c2, alpha, d_min and kappa_beta must be > 0", fn);
-    if (prm->mode != CS_MODE_PERSAMPLE && prm->mode != CS_MODE_FACTORISED)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown mode %d", fn, prm->mode);
-    if (prm->precision != CS_FP32 && prm->precision != CS_BF16 && prm->precision != CS_FP8)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown precision %d", fn,
-                            prm->precision);
-    return CS_OK;
-}
-
 cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
                         int k, int n_labels, const int32_t* label_off,
                         const int32_t* sample_pix, const cs_params* prm, int32_t* dist2,
@@ -323,131 +466,61 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
     if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
     if (!img || !bitmask || !sample_pix || !neglog)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
-    if (H < 1 || W < 1 || H > CS_MAX_SIDE || W > CS_MAX_SIDE)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: bad image size %dx%d", fn, W, H);
-    if (k < 1 || k > CS_MAX_K)
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: k=%d outside 1..%d", fn, k, CS_MAX_K);
-    cs_status s = check_labels(ctx, fn, n_labels, label_off);
+    cs_status s = check_image(ctx, fn, H, W, k);
+    if (!s) s = check_labels(ctx, fn, n_labels, label_off);
+    if (!s) s = check_params(ctx, fn, prm, k);
     if (s) return s;
-    s = check_params(ctx, fn, prm);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    LikPlan L{};
+    plan_likelihood(L, H, W, k, n_labels, label_off, prm);
+    Carve m(nullptr);
+    carve_likelihood(m, L, dist2);
+    if ((s = cs_ensure_scratch(ctx, m.off))) return s;
+    Carve c(ctx->scratch);
+    carve_likelihood(c, L, dist2);
+    cudaError_t e = enqueue_distances(ctx, L, sample_pix, st);
+    if (e == cudaSuccess) e = enqueue_sum(ctx, L, img, bitmask, sample_pix, prm, neglog, post, st);
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return cs_check_launch(ctx, fn);
+}
+
+cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float* omega, int k,
+                       const float* mask, int n_labels, const int32_t* label_off,
+                       const int32_t* sample_pix, const cs_params* prm, uint32_t* bitmask,
+                       int32_t* dist2, float* neglog, float* post, void* stream) {
+    const char* fn = "cs_data_term";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!img || !omega || !mask || !sample_pix || !neglog)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
+    cs_status s = check_image(ctx, fn, H, W, k);
+    if (!s) s = check_patch(ctx, fn, prm);
+    if (!s) s = check_labels(ctx, fn, n_labels, label_off);
+    if (!s) s = check_params(ctx, fn, prm, k);
     if (s) return s;
-    if (k > 256)
-        return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "%s: k=%d > 256 not supported yet", fn, k);
-    const bool tc_form = prm->precision != CS_FP32;
-    const bool tex8 = prm->precision == CS_FP8;
-    const bool persample = prm->mode == CS_MODE_PERSAMPLE;
-    if (tc_form && !tc_supported(k, tex8))
-        return cs_set_error(ctx, CS_ERR_UNSUPPORTED,
-                            "%s: k=%d too large for the %s tensor-core form", fn, k,
-                            tex8 ? "FP8" : "BF16");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const long long P = (long long)H * W;
-    const int S = label_off[n_labels];
-    const int Wk = (k + 31) / 32;
-    // label offsets and, for the tensor-core form, the first sample tile of each label
-    std::vector<int32_t> hoff(2 * (n_labels + 1));
-    for (int i = 0; i <= n_labels; ++i) hoff[i] = label_off[i];
-    hoff[n_labels + 1] = 0;
-    for (int i = 0; i < n_labels; ++i)
-        hoff[n_labels + 2 + i] =
-            hoff[n_labels + 1 + i] + tc_tiles_per_label(label_off[i + 1] - label_off[i]);
-    const int total_tiles = hoff[2 * n_labels + 1];
-    const size_t stage_bytes = tc_stage_bytes(k, tex8, persample);
-
-    auto layout = [&](Carve& c, int32_t** d_off, uint32_t** seedbits, int32_t** colbuf,
-                      int32_t** vbuf, int32_t** fbuf, int32_t** d2, SampleTables* t) {
-        *d_off = c.take<int32_t>(2 * (n_labels + 1));
-        *seedbits = c.take<uint32_t>((size_t)n_labels * H * ((W + 31) / 32));
-        *colbuf = c.take<int32_t>(P * n_labels);
-        *vbuf = c.take<int32_t>(P * n_labels);
-        *fbuf = c.take<int32_t>(P * n_labels);
-        int32_t* d2s = c.take<int32_t>(dist2 ? 0 : P * n_labels);
-        *d2 = dist2 ? dist2 : d2s;
-        t->sx = c.take<float>(S);
-        t->sy = c.take<float>(S);
-        t->sr = c.take<float>(S);
-        t->sg = c.take<float>(S);
-        t->sb = c.take<float>(S);
-        t->sbits = c.take<uint32_t>((size_t)Wk * S);
-        t->spop = c.take<int32_t>(S);
-        t->rep = c.take<uint32_t>((size_t)n_labels * Wk);
-        t->blob = c.take<uint8_t>(tc_form ? (size_t)total_tiles * stage_bytes : 0, 1024);
-    };
-    int32_t *d_off, *colbuf, *vbuf, *fbuf, *d2;
-    uint32_t* seedbits;
-    SampleTables t{};
+    CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, nullptr, nullptr, bitmask};
+    LikPlan L{};
+    plan_likelihood(L, H, W, k, n_labels, label_off, prm);
     Carve m(nullptr);
-    layout(m, &d_off, &seedbits, &colbuf, &vbuf, &fbuf, &d2, &t);
-    s = cs_ensure_scratch(ctx, m.off);
-    if (s) return s;
+    plan_codes(m, a, P, k, !bitmask);
+    carve_likelihood(m, L, dist2);
+    if ((s = cs_ensure_scratch(ctx, m.off))) return s;
     Carve c(ctx->scratch);
-    layout(c, &d_off, &seedbits, &colbuf, &vbuf, &fbuf, &d2, &t);
-
-    cudaError_t e = cudaMemcpyAsync(d_off, hoff.data(), sizeof(int32_t) * hoff.size(),
-                                    cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
-    EdtArgs ea{H, W, n_labels, d_off, sample_pix, S, seedbits, colbuf, vbuf, fbuf, d2, ctx->d_err};
-    {
-        StageTimer tm(ctx, CS_STAGE_DIST, st);
-        e = launch_edt(ea, st);
-    }
-    if (e == cudaSuccess) {
-        StageTimer tm(ctx, CS_STAGE_GATHER, st);
-        e = launch_gather(img, H, W, bitmask, k, n_labels, d_off, sample_pix, S,
-                          prm->mode == CS_MODE_FACTORISED, t, st);
-    }
-    if (e == cudaSuccess) {
-        StageTimer tm(ctx, CS_STAGE_SUM, st);
-        SumArgs a{};
-        a.img = img;
-        a.H = H;
-        a.W = W;
-        a.bitmask = bitmask;
-        a.k = k;
-        a.Wk = Wk;
-        a.n_labels = n_labels;
-        a.d_label_off = d_off;
-        a.n_samples = S;
-        a.t = t;
-        a.dist2 = d2;
-        a.alpha = (float)prm->alpha;
-        a.d_min = (float)prm->d_min;
-        a.kappa_beta = (float)prm->kappa_beta;
-        a.sigma_c2 = (float)prm->sigma_c2;
-        a.mode = prm->mode;
-        a.neglog = neglog;
-        a.post = post;
-        if (!tc_form) {
-            e = launch_sum_plain(a, st);
-        } else {
-            TcLaunch L{};
-            L.img = img;
-            L.H = H;
-            L.W = W;
-            L.bitmask = bitmask;
-            L.k = k;
-            L.n_labels = n_labels;
-            L.d_label_off = d_off;
-            L.d_tile_off = d_off + n_labels + 1;
-            L.total_tiles = total_tiles;
-            L.n_samples = S;
-            L.t = t;
-            L.blob = t.blob;
-            L.dist2 = d2;
-            L.alpha = a.alpha;
-            L.d_min = a.d_min;
-            L.kappa_beta = a.kappa_beta;
-            L.sigma_c2 = a.sigma_c2;
-            L.neglog = neglog;
-            L.post = post;
-            L.d_err = ctx->d_err;
-            L.n_sm = ctx->n_sm;
-            L.tex8 = tex8;
-            L.persample = persample;
-            e = launch_sum_tc(L, st);
-        }
-    }
+    plan_codes(c, a, P, k, !bitmask);
+    carve_likelihood(c, L, dist2);
+    a.d_err = ctx->d_err;
+    // fork: the distance transform depends only on the scribbles and runs on
+    // the context's side stream while the codes run on the caller's stream
+    cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    if (e == cudaSuccess) e = enqueue_distances(ctx, L, sample_pix, ctx->side);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+    if (e == cudaSuccess) e = enqueue_codes(ctx, a, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join, 0);
+    if (e == cudaSuccess) e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return cs_check_launch(ctx, fn);
 }

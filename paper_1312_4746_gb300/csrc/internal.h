@@ -32,6 +32,8 @@ struct cs_ctx {
     size_t scratch_cap = 0;
     int* d_err = nullptr;  // 2 ints
     int n_sm = 148;
+    cudaStream_t side = nullptr;  // distance transform overlapping the codes
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool profiling = false;
     std::vector<StageRecord> records;
     std::vector<cudaEvent_t> event_pool;
@@ -106,6 +108,13 @@ struct EdtArgs {
     int* d_err;
 };
 cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st);
+
+// Small host arrays passed by value (no pageable copy, so calls can be
+// captured in a CUDA graph): label offsets and first sample tile per label.
+struct OffsetsParam {
+    int32_t v[2 * (CS_MAX_LABELS + 1)];
+};
+cudaError_t launch_set_offsets(const OffsetsParam& p, int n, int32_t* dst, cudaStream_t st);
 
 // Per-sample tables (SoA) and the majority co-support of each label.
 struct SampleTables {

@@ -198,7 +198,16 @@ __global__ void majority_kernel(const int32_t* __restrict__ off, int n_labels, i
     if (b == 0) rep[(size_t)i * Wk + w] = word;
 }
 
+__global__ void set_offsets_kernel(OffsetsParam p, int n, int32_t* __restrict__ dst) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = p.v[i];
+}
+
 }  // namespace
+
+cudaError_t launch_set_offsets(const OffsetsParam& p, int n, int32_t* dst, cudaStream_t st) {
+    set_offsets_kernel<<<1, 128, 0, st>>>(p, n, dst);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
     const int Wb = (a.W + 31) / 32;

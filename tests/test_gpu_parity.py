@@ -180,3 +180,24 @@ def test_workload2_sampled(env):
     assert np.array_equal(got["dist2"][:, pix], ref["dist2"])
     assert _rel(got["L"][:, pix], ref["L"]) <= REL_TOL
     assert np.max(np.abs(got["post"][:, pix] - ref["post"])) < 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_data_term_entry(env, precision):
+    """cs_data_term (distance transform overlapped with the codes on a side
+    stream) gives exactly what cs_codes followed by cs_likelihood gives."""
+    cs, ctx, torch = env
+    pr = synth.make_workload(1)
+    prm = cs.Params.from_synth(pr.params, precision=precision)
+    img, om, mask = _dev(torch, pr.image), _dev(torch, pr.omega), _dev(torch, pr.mask)
+    smp = _dev(torch, pr.sample_pix)
+    one = ctx.data_term(img, om, mask, pr.label_off, smp, prm, want_bitmask=True, want_dist2=True)
+    c = ctx.codes(img, om, mask, prm)
+    two = ctx.likelihood(img, c["bitmask"], pr.k, pr.label_off, smp, prm, want_dist2=True)
+    ctx.sync()
+    assert torch.equal(one["bitmask"], c["bitmask"])
+    assert torch.equal(one["dist2"], two["dist2"])
+    assert torch.equal(one["neglog"], two["neglog"])
+    ref = oracle.data_term(pr, want_dist2=True)
+    assert np.array_equal(one["bitmask"].cpu().numpy().view(np.uint32), ref["bits_px"])
+    assert np.array_equal(one["dist2"].cpu().numpy().reshape(pr.n_labels, -1), ref["dist2"])
