@@ -127,6 +127,7 @@ struct SampleTables {
     int32_t* spop;    // popcount of each sample's bitmask
     uint32_t* rep;    // [n_labels][Wk]
     uint8_t* blob;    // tensor-core sample tiles (ring-stage layout)
+    int2* tile_xy;    // tensor-core sample tile coordinates
 };
 cudaError_t launch_gather(const float* img, int H, int W, const uint32_t* bitmask, int k,
                           int n_labels, const int32_t* d_label_off, const int32_t* sample_pix,
@@ -164,6 +165,7 @@ struct TcLaunch {
     int n_samples;
     SampleTables t;
     uint8_t* blob;
+    int2* tile_xy;
     const int32_t* dist2;
     float alpha, d_min, kappa_beta, sigma_c2;
     float* neglog;
@@ -173,7 +175,7 @@ struct TcLaunch {
     bool tex8;       // texture operands in FP8 (else BF16)
     bool persample;  // per-sample texture kernel (else factorised)
 };
-size_t tc_stage_bytes(int k, bool tex8, bool persample);
+size_t tc_copy_bytes(int k, bool tex8, bool persample);
 int tc_tiles_per_label(int m);
 bool tc_supported(int k, bool tex8);
 cudaError_t launch_sum_tc(const TcLaunch& L, cudaStream_t st);
