@@ -191,12 +191,64 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
                        int32_t* dist2, float* neglog, float* post, void* stream);
 
 /*
+ * Learned surrogate of the data term (not in the paper: an approximation of
+ * the Sec. 3.1 likelihood that the exact sum judges and backs up).
+ *
+ * A 21 -> 64 -> 64 -> 64 -> n_labels MLP with SiLU activations, bf16 weights
+ * (fp32 masters) and fp32 arithmetic maps per-pixel features
+ * [R, G, B, x/W, y/H, a_1..a_16] (a = the leading codes, cs_codes' lead16) to
+ * the log kernel sums T_i(x) = log sum_j k_rho k_sigma [exp(-TSM/beta)] of
+ * every label; L_i(x) = T_i - log m_i - log(2 pi rho_i^2) - 1.5 log(2 pi
+ * sigma_c2) then uses the exact scribble distance transform.
+ *
+ * cs_surrogate_fit: selects training pixels q with u(q) < frac and
+ *   validation pixels with frac <= u(q) < frac + min(0.01, 20000/P), where
+ *   u(q) = splitmix64(seed ^ q) / 2^64; computes their exact T (FP32 form);
+ *   standardises features and targets; trains `steps` Adam steps (minibatch
+ *   64 x SM count, learning rate 2e-3 with cosine decay to 1e-4) with the
+ *   library's own forward/backward kernels; records the largest validation
+ *   error eta of L. The network lives in the context. Inputs as in
+ *   cs_likelihood plus lead16 (DEVICE P x 16 float32). Asynchronous, but the
+ *   pixel selection runs on the host before the call returns.
+ * cs_surrogate_eval: evaluates the network at every pixel and writes
+ *   neglog/post there, except at pixels whose top-2 posterior margin is below
+ *   `margin` or whose top-2 log-likelihood gap is below
+ *   2.2 eta + log((n_labels - 1) / 0.005); those get the exact FP32 sum.
+ *   n_fallback (HOST int32, may be NULL) receives their count; when given,
+ *   the call synchronises.
+ * cs_surrogate_params: copies the fp32 master weights to HOST memory
+ *   (layout W1[64][21] b1 W2[64][64] b2 W3[64][64] b3 W4[n][64] b4);
+ *   *n_params receives their count; host_params may be NULL. Synchronises.
+ * cs_mlp_forward / cs_mlp_grad: the network kernels on given DEVICE
+ *   parameters (same layout, used rounded to bf16) and standardised feature
+ *   rows X (rows x 21): outputs Z (rows x n_out), or the gradient of
+ *   loss = mean over rows and outputs of (Z - T)^2 / 2 into grads (DEVICE,
+ *   cs_mlp_param_count(n_out) floats) and the loss into *loss (DEVICE);
+ *   rows must be a positive multiple of 64 for cs_mlp_grad.
+ */
+cs_status cs_surrogate_fit(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
+                           const float* lead16, int k, int n_labels, const int32_t* label_off,
+                           const int32_t* sample_pix, const cs_params* prm, double frac,
+                           int steps, uint64_t seed, void* stream);
+cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
+                            const float* lead16, int k, int n_labels, const int32_t* label_off,
+                            const int32_t* sample_pix, const cs_params* prm, double margin,
+                            float* neglog, float* post, int32_t* n_fallback, void* stream);
+cs_status cs_surrogate_params(cs_ctx* ctx, float* host_params, int cap, int* n_params);
+int cs_mlp_param_count(int n_out);
+cs_status cs_mlp_forward(cs_ctx* ctx, const float* params, int n_out, const float* X, int rows,
+                         float* Z, void* stream);
+cs_status cs_mlp_grad(cs_ctx* ctx, const float* params, int n_out, const float* X,
+                      const float* T, int rows, float* grads, float* loss, void* stream);
+
+/*
  * Stage timing. While enabled, every call records a pair of CUDA events on
  * its stream around each stage it launches:
  *   CS_STAGE_CODES   patches, codes, bitmasks and the FP64 guard pass
  *   CS_STAGE_DIST    exact scribble distance transform
  *   CS_STAGE_GATHER  sample tables and majority co-supports
  *   CS_STAGE_SUM     the pixel x sample likelihood sum and label normalisation
+ *   CS_STAGE_SURROGATE  the surrogate network over all pixels
  * cs_profile_read waits for the recorded events of `stage`, returns their
  * summed duration in milliseconds and the number of recorded launches, and
  * forgets them. Synchronises on those events only.
@@ -205,7 +257,8 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
 #define CS_STAGE_DIST 1
 #define CS_STAGE_GATHER 2
 #define CS_STAGE_SUM 3
-#define CS_N_STAGES 4
+#define CS_STAGE_SURROGATE 4 /* network evaluation and fallback selection */
+#define CS_N_STAGES 5
 cs_status cs_profile_enable(cs_ctx* ctx, int on);
 cs_status cs_profile_read(cs_ctx* ctx, int stage, double* ms, int* launches);
 

@@ -41,6 +41,12 @@ EXPORTS = (
     "cs_cosupport",
     "cs_likelihood",
     "cs_data_term",
+    "cs_surrogate_fit",
+    "cs_surrogate_eval",
+    "cs_surrogate_params",
+    "cs_mlp_param_count",
+    "cs_mlp_forward",
+    "cs_mlp_grad",
     "cs_profile_enable",
     "cs_profile_read",
 )
@@ -49,6 +55,7 @@ STAGE_CODES = 0
 STAGE_DIST = 1
 STAGE_GATHER = 2
 STAGE_SUM = 3
+STAGE_SURROGATE = 4
 
 
 class CsError(RuntimeError):
@@ -118,10 +125,20 @@ def lib(path: str | None = None):
     L.cs_cosupport.argtypes = [V, V, I, I, D, V, V]
     L.cs_likelihood.argtypes = [V, V, I, I, V, I, I, V, V, ctypes.POINTER(Params), V, V, V, V]
     L.cs_data_term.argtypes = [V, V, I, I, V, I, V, I, V, V, ctypes.POINTER(Params), V, V, V, V, V]
+    U64 = ctypes.c_uint64
+    L.cs_surrogate_fit.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, I, U64, V]
+    L.cs_surrogate_eval.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, V, V,
+                                    V, V]
+    L.cs_surrogate_params.argtypes = [V, V, I, ctypes.POINTER(I)]
+    L.cs_mlp_param_count.argtypes = [I]
+    L.cs_mlp_param_count.restype = I
+    L.cs_mlp_forward.argtypes = [V, V, I, V, I, V, V]
+    L.cs_mlp_grad.argtypes = [V, V, I, V, V, I, V, V, V]
     L.cs_profile_enable.argtypes = [V, I]
     L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     for f in ("cs_create", "cs_sync_status", "cs_codes", "cs_cosupport", "cs_likelihood",
-              "cs_data_term", "cs_profile_enable", "cs_profile_read"):
+              "cs_data_term", "cs_profile_enable", "cs_profile_read", "cs_surrogate_fit",
+              "cs_surrogate_eval", "cs_surrogate_params", "cs_mlp_forward", "cs_mlp_grad"):
         getattr(L, f).restype = I
     if path is None:
         _lib = L
@@ -264,6 +281,69 @@ class Context:
             _ptr(out.get("bitmask")), _ptr(out.get("dist2")), _ptr(out["neglog"]),
             _ptr(out.get("post")), _stream()))
         return out
+
+
+    # ------------------------------------------------------------------ surrogate
+
+    def surrogate_fit(self, img, bitmask, lead16, k, label_off, sample_pix, params: Params,
+                      frac=0.05, steps=400, seed=1):
+        """cs_surrogate_fit (network kept in the context)."""
+        import numpy as np
+
+        H, W = int(img.shape[0]), int(img.shape[1])
+        off = np.ascontiguousarray(np.asarray(label_off, dtype=np.int32))
+        self.check(self._lib.cs_surrogate_fit(
+            self.handle, _ptr(img), H, W, _ptr(bitmask), _ptr(lead16), int(k), len(off) - 1,
+            ctypes.c_void_p(off.ctypes.data), _ptr(sample_pix), ctypes.byref(params),
+            float(frac), int(steps), ctypes.c_uint64(seed), _stream()))
+
+    def surrogate_eval(self, img, bitmask, lead16, k, label_off, sample_pix, params: Params,
+                       margin=0.1, out=None, want_post=True, count=True):
+        """cs_surrogate_eval: returns (dict with 'neglog'/'post', n_fallback or None)."""
+        import numpy as np
+        import torch
+
+        H, W = int(img.shape[0]), int(img.shape[1])
+        off = np.ascontiguousarray(np.asarray(label_off, dtype=np.int32))
+        nl = len(off) - 1
+        if out is None:
+            out = {"neglog": torch.empty((nl, H, W), dtype=torch.float32, device=img.device),
+                   "post": (torch.empty((nl, H, W), dtype=torch.float32, device=img.device)
+                            if want_post else None)}
+        nfb = ctypes.c_int32(-1)
+        self.check(self._lib.cs_surrogate_eval(
+            self.handle, _ptr(img), H, W, _ptr(bitmask), _ptr(lead16), int(k), nl,
+            ctypes.c_void_p(off.ctypes.data), _ptr(sample_pix), ctypes.byref(params),
+            float(margin), _ptr(out["neglog"]), _ptr(out.get("post")),
+            ctypes.byref(nfb) if count else None, _stream()))
+        return out, (nfb.value if count else None)
+
+    def surrogate_params(self):
+        import numpy as np
+
+        n = ctypes.c_int()
+        self.check(self._lib.cs_surrogate_params(self.handle, None, 0, ctypes.byref(n)))
+        buf = np.zeros(n.value, np.float32)
+        self.check(self._lib.cs_surrogate_params(self.handle, ctypes.c_void_p(buf.ctypes.data),
+                                                 n.value, ctypes.byref(n)))
+        return buf
+
+    def mlp_forward(self, params_dev, n_out, X):
+        import torch
+
+        Z = torch.empty((X.shape[0], n_out), dtype=torch.float32, device=X.device)
+        self.check(self._lib.cs_mlp_forward(self.handle, _ptr(params_dev), n_out, _ptr(X),
+                                            int(X.shape[0]), _ptr(Z), _stream()))
+        return Z
+
+    def mlp_grad(self, params_dev, n_out, X, T):
+        import torch
+
+        g = torch.empty(self._lib.cs_mlp_param_count(n_out), dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        self.check(self._lib.cs_mlp_grad(self.handle, _ptr(params_dev), n_out, _ptr(X), _ptr(T),
+                                         int(X.shape[0]), _ptr(g), _ptr(loss), _stream()))
+        return g, loss
 
 
 def version() -> str:

@@ -178,6 +178,7 @@ void cs_destroy(cs_ctx* ctx) {
         cudaEventDestroy(r.end);
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->surr_buf) cudaFree(ctx->surr_buf);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -284,18 +285,6 @@ static void plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitm
     a.guard_cap = cap;
     if (own_bitmask) a.bitmask = c.take<uint32_t>(P * ((k + 31) / 32));
 }
-
-// Everything the likelihood stage needs besides the caller's buffers.
-struct LikPlan {
-    int H, W, k, n_labels, S, total_tiles;
-    bool tc_form, tex8, persample;
-    size_t stage_bytes;
-    OffsetsParam offs;  // label offsets then first sample tile of each label
-    int32_t* d_off;
-    uint32_t* seedbits;
-    int32_t *colbuf, *vbuf, *fbuf, *d2;
-    SampleTables t;
-};
 
 static void plan_likelihood(LikPlan& L, int H, int W, int k, int n_labels,
                             const int32_t* label_off, const cs_params* prm) {
@@ -459,6 +448,93 @@ cs_status cs_cosupport(cs_ctx* ctx, const float* codes, int P, int k, double tau
         return cs_set_error(ctx, CS_ERR_CUDA, "cs_cosupport: %s", cudaGetErrorString(e));
     return cs_check_launch(ctx, "cs_cosupport");
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- helpers for other entry points
+
+cs_status cs_check_likelihood_args(cs_ctx* ctx, const char* fn, int H, int W, int k,
+                                   int n_labels, const int32_t* label_off, const cs_params* prm) {
+    cs_status s = check_image(ctx, fn, H, W, k);
+    if (!s) s = check_labels(ctx, fn, n_labels, label_off);
+    if (!s) s = check_params(ctx, fn, prm, k);
+    return s;
+}
+
+// Plans and carves the likelihood scratch with `extra` bytes reserved after
+// it (their offset in *off_extra).
+cs_status cs_plan_likelihood(cs_ctx* ctx, LikPlan& L, int H, int W, int k, int n_labels,
+                             const int32_t* label_off, const cs_params* prm, int32_t* dist2,
+                             size_t extra, size_t* off_extra) {
+    plan_likelihood(L, H, W, k, n_labels, label_off, prm);
+    Carve m(nullptr);
+    carve_likelihood(m, L, dist2);
+    const size_t base = (m.off + 255) / 256 * 256;
+    cs_status s = cs_ensure_scratch(ctx, base + extra);
+    if (s) return s;
+    Carve c(ctx->scratch);
+    carve_likelihood(c, L, dist2);
+    *off_extra = base;
+    return CS_OK;
+}
+
+// distances and sample tables
+cudaError_t cs_enqueue_prepare(cs_ctx* ctx, const LikPlan& L, const float* img,
+                               const uint32_t* bitmask, const int32_t* sample_pix,
+                               const cs_params* prm, cudaStream_t st) {
+    cudaError_t e = enqueue_distances(ctx, L, sample_pix, st);
+    if (e != cudaSuccess) return e;
+    StageTimer tm(ctx, CS_STAGE_GATHER, st);
+    return launch_gather(img, L.H, L.W, bitmask, L.k, L.n_labels, L.d_off, sample_pix, L.S,
+                         prm->mode == CS_MODE_FACTORISED, L.t, st);
+}
+
+// exact plain sum over a device pixel list (after cs_enqueue_prepare): with
+// T_out the log kernel sums [n_labels][cap], else neglog/post at the pixels
+cudaError_t cs_enqueue_exact_list_prepared(cs_ctx* ctx, const LikPlan& L, const float* img,
+                                           const uint32_t* bitmask, const cs_params* prm,
+                                           const int32_t* list, const int* count, int cap,
+                                           float* T_out, float* neglog, float* post,
+                                           cudaStream_t st) {
+    SumArgs a{};
+    a.img = img;
+    a.H = L.H;
+    a.W = L.W;
+    a.bitmask = bitmask;
+    a.k = L.k;
+    a.Wk = (L.k + 31) / 32;
+    a.n_labels = L.n_labels;
+    a.d_label_off = L.d_off;
+    a.n_samples = L.S;
+    a.t = L.t;
+    a.dist2 = L.d2;
+    a.alpha = (float)prm->alpha;
+    a.d_min = (float)prm->d_min;
+    a.kappa_beta = (float)prm->kappa_beta;
+    a.sigma_c2 = (float)prm->sigma_c2;
+    a.mode = prm->mode;
+    a.neglog = neglog;
+    a.post = post;
+    a.pix_list = list;
+    a.list_count = count;
+    a.list_cap = cap;
+    a.T_out = T_out;
+    StageTimer tm(ctx, CS_STAGE_SUM, st);
+    return launch_sum_plain(a, st);
+}
+
+cudaError_t cs_enqueue_exact_list(cs_ctx* ctx, const LikPlan& L, const float* img,
+                                  const uint32_t* bitmask, const int32_t* sample_pix,
+                                  const cs_params* prm, const int32_t* list, const int* count,
+                                  int cap, float* T_out, float* neglog, float* post,
+                                  cudaStream_t st) {
+    cudaError_t e = cs_enqueue_prepare(ctx, L, img, bitmask, sample_pix, prm, st);
+    if (e != cudaSuccess) return e;
+    return cs_enqueue_exact_list_prepared(ctx, L, img, bitmask, prm, list, count, cap, T_out,
+                                          neglog, post, st);
+}
+
+extern "C" {
 
 cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
                         int k, int n_labels, const int32_t* label_off,

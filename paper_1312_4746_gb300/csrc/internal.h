@@ -32,6 +32,11 @@ struct cs_ctx {
     size_t scratch_cap = 0;
     int* d_err = nullptr;  // 2 ints
     int n_sm = 148;
+    // learned surrogate (allocated by the first fit)
+    float* surr_buf = nullptr;
+    size_t surr_cap = 0;
+    int surr_n = 0, surr_train = 0, surr_val = 0;
+    bool surr_ready = false;
     cudaStream_t side = nullptr;  // distance transform overlapping the codes
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool profiling = false;
@@ -149,8 +154,49 @@ struct SumArgs {
     int mode;
     float* neglog;
     float* post;
+    // optional pixel list (device), its length (device) and capacity; with
+    // T_out the kernel writes only the log kernel sums T[i][item] (compact)
+    const int32_t* pix_list = nullptr;
+    const int* list_count = nullptr;
+    int list_cap = 0;
+    float* T_out = nullptr;
 };
 cudaError_t launch_sum_plain(const SumArgs& a, cudaStream_t st);
+
+// Likelihood-stage plan: shapes, forms and the carved scratch pointers.
+struct LikPlan {
+    int H, W, k, n_labels, S, total_tiles;
+    bool tc_form, tex8, persample;
+    size_t stage_bytes;
+    OffsetsParam offs;  // label offsets then first sample tile of each label
+    int32_t* d_off;
+    uint32_t* seedbits;
+    int32_t *colbuf, *vbuf, *fbuf, *d2;
+    SampleTables t;
+};
+
+typedef LikPlan LikPlanRef;
+inline const int32_t* cs_plan_dist2(const LikPlan& L) { return L.d2; }
+inline const int32_t* cs_plan_label_off(const LikPlan& L) { return L.d_off; }
+inline const uint32_t* cs_plan_rep(const LikPlan& L) { return L.t.rep; }
+cs_status cs_check_likelihood_args(cs_ctx* ctx, const char* fn, int H, int W, int k,
+                                   int n_labels, const int32_t* label_off, const cs_params* prm);
+cs_status cs_plan_likelihood(cs_ctx* ctx, LikPlan& L, int H, int W, int k, int n_labels,
+                             const int32_t* label_off, const cs_params* prm, int32_t* dist2,
+                             size_t extra, size_t* off_extra);
+cudaError_t cs_enqueue_prepare(cs_ctx* ctx, const LikPlan& L, const float* img,
+                               const uint32_t* bitmask, const int32_t* sample_pix,
+                               const cs_params* prm, cudaStream_t st);
+cudaError_t cs_enqueue_exact_list_prepared(cs_ctx* ctx, const LikPlan& L, const float* img,
+                                           const uint32_t* bitmask, const cs_params* prm,
+                                           const int32_t* list, const int* count, int cap,
+                                           float* T_out, float* neglog, float* post,
+                                           cudaStream_t st);
+cudaError_t cs_enqueue_exact_list(cs_ctx* ctx, const LikPlan& L, const float* img,
+                                  const uint32_t* bitmask, const int32_t* sample_pix,
+                                  const cs_params* prm, const int32_t* list, const int* count,
+                                  int cap, float* T_out, float* neglog, float* post,
+                                  cudaStream_t st);
 
 // Tensor-core (tcgen05) pixel x sample sum.
 struct TcLaunch {
@@ -179,3 +225,44 @@ size_t tc_copy_bytes(int k, bool tex8, bool persample);
 int tc_tiles_per_label(int m);
 bool tc_supported(int k, bool tex8);
 cudaError_t launch_sum_tc(const TcLaunch& L, cudaStream_t st);
+
+// Learned surrogate (MLP) kernels.
+int mlp_param_count(int n);
+size_t mlp_train_smem(int n);
+cudaError_t launch_mlp_train(const float* params, int n, const float* X, const float* T,
+                             int n_rows, long long start, int batch, float* grads,
+                             float* loss_acc, cudaStream_t st);
+cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr, int t,
+                        cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* params, int n, const float* X, int rows, float* Z,
+                               cudaStream_t st);
+cudaError_t launch_features(const float* img, const float* lead16, int H, int W,
+                            const int32_t* list, int rows, float* X, cudaStream_t st);
+cudaError_t launch_stats(const float* X, const float* T, int n, int cap, int n_rows,
+                         float* stats, cudaStream_t st);
+cudaError_t launch_standardize(float* X, const float* T, int n, int cap, int rows,
+                               const float* stats, float* Ts, cudaStream_t st);
+cudaError_t launch_init_params(float* p, float* m, float* v, float* g, int n, uint64_t seed,
+                               cudaStream_t st);
+cudaError_t launch_calib(const float* Z, const float* Ts, int n, int rows, const float* stats,
+                         float* eta, cudaStream_t st);
+struct SurrogateEvalArgs {
+    const float* params;
+    int n;
+    const float* stats;
+    const float* eta;
+    const float* img;
+    const float* lead16;
+    int H, W;
+    const int32_t* dist2;
+    const int32_t* label_off;
+    const uint32_t* bitmask;
+    const uint32_t* rep;
+    int Wk, mode;
+    float alpha, d_min, kappa_beta, sigma_c2, margin, eps;
+    float* neglog;
+    float* post;
+    int32_t* fb_list;
+    int* fb_count;
+};
+cudaError_t launch_surrogate_eval(const SurrogateEvalArgs& a, cudaStream_t st);

@@ -51,20 +51,25 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
     __shared__ uint32_t s_bits[WK][TS];
 
     const long long P = (long long)a.H * a.W;
-    const long long base = (long long)blockIdx.x * THREADS * NPIX;
     const int tid = threadIdx.x;
     const float nC = -LOG2E / (2.f * a.sigma_c2);
     const float log_col_norm = 1.5f * logf(6.283185307179586f * a.sigma_c2);
     const float wtex = a.mode == CS_MODE_PERSAMPLE ? 1.f : 0.f;
+    // work items: every pixel, or the pixels of a device list (count on the device)
+    const long long n_items = a.pix_list ? (long long)min(*a.list_count, a.list_cap) : P;
 
+    for (long long base = (long long)blockIdx.x * THREADS * NPIX; base < n_items;
+         base += (long long)gridDim.x * THREADS * NPIX) {
     float px[NPIX], py[NPIX], pr[NPIX], pg[NPIX], pb[NPIX];
     uint32_t pbits[NPIX][WK];
     bool live[NPIX];
+    long long qpix[NPIX], item[NPIX];
 #pragma unroll
     for (int u = 0; u < NPIX; ++u) {
-        long long q = base + u * THREADS + tid;
-        live[u] = q < P;
-        long long qq = live[u] ? q : 0;
+        item[u] = base + u * THREADS + tid;
+        live[u] = item[u] < n_items;
+        long long qq = live[u] ? (a.pix_list ? (long long)a.pix_list[item[u]] : item[u]) : 0;
+        qpix[u] = qq;
         px[u] = (float)(qq % a.W);
         py[u] = (float)(qq / a.W);
         pr[u] = a.img[qq * 3 + 0];
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
         float nA[NPIX], nB[NPIX], rho[NPIX], M[NPIX], S[NPIX], Cc[NPIX];
 #pragma unroll
         for (int u = 0; u < NPIX; ++u) {
-            long long q = live[u] ? base + u * THREADS + tid : 0;
+            long long q = qpix[u];
             label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, rho[u],
                          nA[u], nB[u]);
             nB[u] *= wtex;
@@ -152,18 +157,23 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
 #pragma unroll
         for (int u = 0; u < NPIX; ++u) {
             if (!live[u]) continue;
-            const long long q = base + u * THREADS + tid;
+            const long long q = qpix[u];
             const float lse = (M[u] + log2f(S[u] + Cc[u])) * LN2;
+            if (a.T_out) {  // log kernel sum only (surrogate targets), compact layout
+                a.T_out[(size_t)i * a.list_cap + item[u]] = lse;
+                continue;
+            }
             const float L = lse - logm - logf(6.283185307179586f * rho[u] * rho[u]) - log_col_norm;
             a.neglog[(size_t)i * P + q] = -L;
         }
     }
+    if (a.T_out) continue;
 
     // label normalisation (and the factorised texture posterior)
 #pragma unroll
     for (int u = 0; u < NPIX; ++u) {
         if (!live[u]) continue;
-        const long long q = base + u * THREADS + tid;
+        const long long q = qpix[u];
         if (a.mode == CS_MODE_FACTORISED) {
             float tmax = -INFINITY;
             for (int i = 0; i < a.n_labels; ++i) {
@@ -203,14 +213,17 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
             for (int i = 0; i < a.n_labels; ++i)
                 a.post[(size_t)i * P + q] = expf(-a.neglog[(size_t)i * P + q] - lse);
     }
+    }  // work-item tiles
 }
 
 template <int WK>
 cudaError_t launch_wk(const SumArgs& a, cudaStream_t st) {
     constexpr int NPIX = 1;
-    const long long P = (long long)a.H * a.W;
-    const unsigned blocks = (unsigned)((P + THREADS * NPIX - 1) / (THREADS * NPIX));
-    sum_plain_kernel<WK, NPIX><<<blocks, THREADS, 0, st>>>(a);
+    const long long n = a.pix_list ? (long long)a.list_cap : (long long)a.H * a.W;
+    long long blocks = (n + THREADS * NPIX - 1) / (THREADS * NPIX);
+    if (a.pix_list && blocks > 152 * 16) blocks = 152 * 16;  // grid-stride over the list
+    if (blocks < 1) blocks = 1;
+    sum_plain_kernel<WK, NPIX><<<(unsigned)blocks, THREADS, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,277 @@
+// C ABI of the learned surrogate: fit (exact targets at a seeded pixel subset,
+// standardisation, Adam training with the project's forward/backward
+// kernels, calibration of the fallback gap on a held-out subset) and eval
+// (network everywhere, exact sum on the low-margin pixels). Also the two
+// kernel hooks cs_mlp_forward and cs_mlp_grad.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+// splitmix64 (Steele, Lea, Flood 2014): the counter-based generator behind the
+// pixel subsets and their shuffle.
+uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+constexpr int NIN = 21;
+constexpr int MAX_VAL = 20000;
+
+struct Sel {
+    std::vector<int32_t> train, val;
+};
+
+// Pixel q is a training pixel when u(q) < frac and a validation pixel when
+// frac <= u(q) < frac + vfrac, u(q) = splitmix64(seed ^ q) / 2^64. The
+// training list is then shuffled (Fisher-Yates driven by splitmix64).
+Sel select_pixels(long long P, double frac, uint64_t seed) {
+    Sel s;
+    const double vfrac = std::min(0.01, (double)MAX_VAL / (double)P);
+    for (long long q = 0; q < P; ++q) {
+        const double u = (double)(splitmix64(seed ^ (uint64_t)q) >> 11) * 0x1.0p-53;
+        if (u < frac)
+            s.train.push_back((int32_t)q);
+        else if (u < frac + vfrac)
+            s.val.push_back((int32_t)q);
+    }
+    uint64_t st = seed ^ 0x5DEECE66Dull;
+    for (size_t i = s.train.size(); i > 1; --i) {
+        st = splitmix64(st);
+        const size_t j = (size_t)(st % i);
+        std::swap(s.train[i - 1], s.train[j]);
+    }
+    return s;
+}
+
+}  // namespace
+
+// surrogate state kept in the context (allocated by the first fit)
+static cs_status ensure_surrogate(cs_ctx* ctx, int n) {
+    const int np = mlp_param_count(n);
+    // params | m | v | grads | stats (2*21 + 2n) | eta | loss
+    const size_t need = (size_t)4 * np + 2 * NIN + 2 * n + 2;
+    if (ctx->surr_buf && ctx->surr_cap >= need) return CS_OK;
+    if (ctx->surr_buf) cudaFree(ctx->surr_buf);
+    ctx->surr_buf = nullptr;
+    ctx->surr_cap = 0;
+    if (cudaMalloc(&ctx->surr_buf, need * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return cs_set_error(ctx, CS_ERR_NOMEM, "surrogate state allocation failed");
+    }
+    ctx->surr_cap = need;
+    return CS_OK;
+}
+
+struct SurrPtrs {
+    float *p, *m, *v, *g, *stats, *eta, *loss;
+};
+static SurrPtrs surr_ptrs(cs_ctx* ctx, int n) {
+    const int np = mlp_param_count(n);
+    SurrPtrs s;
+    s.p = ctx->surr_buf;
+    s.m = s.p + np;
+    s.v = s.m + np;
+    s.g = s.v + np;
+    s.stats = s.g + np;
+    s.eta = s.stats + 2 * NIN + 2 * n;
+    s.loss = s.eta + 1;
+    return s;
+}
+
+extern "C" {
+
+cs_status cs_mlp_forward(cs_ctx* ctx, const float* params, int n_out, const float* X, int rows,
+                         float* Z, void* stream) {
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_mlp_forward: ctx is NULL");
+    if (!params || !X || !Z || rows < 1 || n_out < 1 || n_out > CS_MAX_LABELS)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_mlp_forward: bad arguments");
+    cudaError_t e = launch_mlp_forward(params, n_out, X, rows, Z, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "cs_mlp_forward: %s", cudaGetErrorString(e));
+    return cs_check_launch(ctx, "cs_mlp_forward");
+}
+
+cs_status cs_mlp_grad(cs_ctx* ctx, const float* params, int n_out, const float* X,
+                      const float* T, int rows, float* grads, float* loss, void* stream) {
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_mlp_grad: ctx is NULL");
+    if (!params || !X || !T || !grads || !loss || rows < 64 || rows % 64 || n_out < 1 ||
+        n_out > CS_MAX_LABELS)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG,
+                            "cs_mlp_grad: bad arguments (rows must be a positive multiple of 64)");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(grads, 0, sizeof(float) * mlp_param_count(n_out), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+    if (e == cudaSuccess) e = launch_mlp_train(params, n_out, X, T, rows, 0, rows, grads, loss, st);
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "cs_mlp_grad: %s", cudaGetErrorString(e));
+    return cs_check_launch(ctx, "cs_mlp_grad");
+}
+
+int cs_mlp_param_count(int n_out) { return n_out < 1 ? 0 : mlp_param_count(n_out); }
+
+cs_status cs_surrogate_fit(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
+                           const float* lead16, int k, int n_labels, const int32_t* label_off,
+                           const int32_t* sample_pix, const cs_params* prm, double frac,
+                           int steps, uint64_t seed, void* stream) {
+    const char* fn = "cs_surrogate_fit";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!img || !bitmask || !lead16 || !sample_pix)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
+    if (!(frac > 0.0 && frac <= 0.5) || steps < 1)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: need 0 < frac <= 0.5 and steps >= 1", fn);
+    cs_status s = cs_check_likelihood_args(ctx, fn, H, W, k, n_labels, label_off, prm);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long P = (long long)H * W;
+    Sel sel = select_pixels(P, frac, seed);
+    const int ntr = (int)sel.train.size(), nva = (int)sel.val.size();
+    if (ntr < 64 || nva < 1)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: image too small for frac=%g", fn, frac);
+    const int N = ntr + nva, n = n_labels;
+    if ((s = ensure_surrogate(ctx, n))) return s;
+
+    // scratch: likelihood plan (distances, sample tables), list, targets, features
+    LikPlanRef plan;
+    cs_params exact = *prm;
+    exact.precision = CS_FP32;
+    size_t off_extra = 0;
+    if ((s = cs_plan_likelihood(ctx, plan, H, W, k, n_labels, label_off, &exact, nullptr,
+                                (size_t)N * sizeof(int32_t) + 256 +       // list
+                                    (size_t)n * N * sizeof(float) + 256 + // T (label-major)
+                                    (size_t)N * NIN * sizeof(float) + 256 + // X
+                                    (size_t)N * n * sizeof(float) + 256 + // standardised T
+                                    (size_t)N * n * sizeof(float) + 256 + // calibration output
+                                    16,
+                                &off_extra)))
+        return s;
+    Carve c(ctx->scratch);
+    c.off = off_extra;
+    int32_t* d_list = c.take<int32_t>(N);
+    float* T = c.take<float>((size_t)n * N);
+    float* X = c.take<float>((size_t)N * NIN);
+    float* Ts = c.take<float>((size_t)N * n);
+    float* Z = c.take<float>((size_t)N * n);
+    int* d_count = c.take<int>(1);
+    std::vector<int32_t> hl(sel.train);
+    hl.insert(hl.end(), sel.val.begin(), sel.val.end());
+    cudaError_t e = cudaMemcpyAsync(d_list, hl.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_count, &N, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cs_enqueue_exact_list(ctx, plan, img, bitmask, sample_pix, &exact,
+                                                    d_list, d_count, N, T, nullptr, nullptr, st);
+    SurrPtrs sp = surr_ptrs(ctx, n);
+    const int np = mlp_param_count(n);
+    if (e == cudaSuccess) e = launch_features(img, lead16, H, W, d_list, N, X, st);
+    if (e == cudaSuccess) e = launch_stats(X, T, n, N, ntr, sp.stats, st);
+    if (e == cudaSuccess) e = launch_standardize(X, T, n, N, N, sp.stats, Ts, st);
+    if (e == cudaSuccess) e = launch_init_params(sp.p, sp.m, sp.v, sp.g, n, seed, st);
+    const int batch = 64 * std::max(1, std::min(ctx->n_sm, (ntr + 63) / 64));
+    for (int t = 0; e == cudaSuccess && t < steps; ++t) {
+        e = launch_mlp_train(sp.p, n, X, Ts, ntr, (long long)t * batch, batch, sp.g, sp.loss, st);
+        // learning rate 2e-3, cosine decay to 1e-4
+        const float lr = 1e-4f + 0.5f * (2e-3f - 1e-4f) * (1.f + cosf(3.14159265f * t / steps));
+        if (e == cudaSuccess) e = launch_adam(sp.p, sp.g, sp.m, sp.v, np, lr, t + 1, st);
+    }
+    // calibration on the validation rows: largest log-likelihood error
+    if (e == cudaSuccess) e = cudaMemsetAsync(sp.eta, 0, sizeof(float), st);
+    if (e == cudaSuccess)
+        e = launch_mlp_forward(sp.p, n, X + (size_t)ntr * NIN, nva, Z, st);
+    if (e == cudaSuccess) e = launch_calib(Z, Ts + (size_t)ntr * n, n, nva, sp.stats, sp.eta, st);
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    ctx->surr_n = n;
+    ctx->surr_ready = true;
+    ctx->surr_train = ntr;
+    ctx->surr_val = nva;
+    return cs_check_launch(ctx, fn);
+}
+
+cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
+                            const float* lead16, int k, int n_labels, const int32_t* label_off,
+                            const int32_t* sample_pix, const cs_params* prm, double margin,
+                            float* neglog, float* post, int32_t* n_fallback, void* stream) {
+    const char* fn = "cs_surrogate_eval";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!img || !bitmask || !lead16 || !sample_pix || !neglog)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
+    if (!ctx->surr_ready || ctx->surr_n != n_labels)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: no surrogate fitted for %d labels", fn,
+                            n_labels);
+    if (!(margin >= 0.0 && margin <= 1.0))
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: margin must be in [0, 1]", fn);
+    cs_status s = cs_check_likelihood_args(ctx, fn, H, W, k, n_labels, label_off, prm);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long P = (long long)H * W;
+    cs_params exact = *prm;
+    exact.precision = CS_FP32;
+    LikPlanRef plan;
+    size_t off_extra = 0;
+    if ((s = cs_plan_likelihood(ctx, plan, H, W, k, n_labels, label_off, &exact, nullptr,
+                                (size_t)P * sizeof(int32_t) + 256 + 16, &off_extra)))
+        return s;
+    Carve c(ctx->scratch);
+    c.off = off_extra;
+    int32_t* fb_list = c.take<int32_t>(P);
+    int* fb_count = c.take<int>(1);
+    SurrPtrs sp = surr_ptrs(ctx, n_labels);
+    cudaError_t e = cudaMemsetAsync(fb_count, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cs_enqueue_prepare(ctx, plan, img, bitmask, sample_pix, &exact, st);
+    if (e == cudaSuccess) {
+        SurrogateEvalArgs a{};
+        a.params = sp.p;
+        a.n = n_labels;
+        a.stats = sp.stats;
+        a.eta = sp.eta;
+        a.img = img;
+        a.lead16 = lead16;
+        a.H = H;
+        a.W = W;
+        a.dist2 = cs_plan_dist2(plan);
+        a.label_off = cs_plan_label_off(plan);
+        a.bitmask = bitmask;
+        a.rep = cs_plan_rep(plan);
+        a.Wk = (k + 31) / 32;
+        a.mode = prm->mode;
+        a.alpha = (float)prm->alpha;
+        a.d_min = (float)prm->d_min;
+        a.kappa_beta = (float)prm->kappa_beta;
+        a.sigma_c2 = (float)prm->sigma_c2;
+        a.margin = (float)margin;
+        a.eps = 0.005f;
+        a.neglog = neglog;
+        a.post = post;
+        a.fb_list = fb_list;
+        a.fb_count = fb_count;
+        StageTimer tm(ctx, CS_STAGE_SURROGATE, st);
+        e = launch_surrogate_eval(a, st);
+    }
+    if (e == cudaSuccess)
+        e = cs_enqueue_exact_list_prepared(ctx, plan, img, bitmask, &exact, fb_list, fb_count,
+                                           (int)P, nullptr, neglog, post, st);
+    if (e == cudaSuccess && n_fallback) {
+        e = cudaMemcpyAsync(n_fallback, fb_count, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return cs_check_launch(ctx, fn);
+}
+
+cs_status cs_surrogate_params(cs_ctx* ctx, float* host_params, int cap, int* n_params) {
+    if (!ctx || !n_params) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_surrogate_params: bad arguments");
+    if (!ctx->surr_ready) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_surrogate_params: no surrogate");
+    const int np = mlp_param_count(ctx->surr_n);
+    *n_params = np;
+    if (!host_params) return CS_OK;
+    if (cap < np) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_surrogate_params: cap < %d", np);
+    if (cudaMemcpy(host_params, ctx->surr_buf, sizeof(float) * np, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return cs_set_error(ctx, CS_ERR_CUDA, "cs_surrogate_params: copy failed");
+    }
+    return CS_OK;
+}
+
+}  // extern "C"
