@@ -302,6 +302,8 @@ static void plan_likelihood(LikPlan& L, int H, int W, int k, int n_labels,
         L.offs.v[n_labels + 2 + i] =
             L.offs.v[n_labels + 1 + i] + tc_tiles_per_label(label_off[i + 1] - label_off[i]);
     L.total_tiles = L.offs.v[2 * n_labels + 1];
+    L.n_chunks = 0;
+    for (int i = 0; i < n_labels; ++i) L.n_chunks += (label_off[i + 1] - label_off[i] + 4095) / 4096;
     L.stage_bytes = tc_copy_bytes(k, L.tex8, L.persample);
 }
 
@@ -324,7 +326,8 @@ static void carve_likelihood(Carve& c, LikPlan& L, int32_t* dist2) {
     L.t.spop = c.take<int32_t>(S);
     L.t.rep = c.take<uint32_t>((size_t)n * Wk);
     L.t.blob = c.take<uint8_t>(L.tc_form ? (size_t)L.total_tiles * L.stage_bytes : 0, 1024);
-    L.t.tile_xy = c.take<int2>(L.tc_form ? (size_t)L.total_tiles * 128 : 0);
+    L.t.tile_c = c.take<int2>(L.tc_form ? (size_t)L.total_tiles : 0);
+    L.t.perm = c.take<int32_t>(L.tc_form ? (size_t)S : 0);
 }
 
 static cudaError_t enqueue_codes(cs_ctx* ctx, const CodesArgs& a, cudaStream_t st) {
@@ -390,7 +393,7 @@ static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
     T.n_samples = L.S;
     T.t = L.t;
     T.blob = L.t.blob;
-    T.tile_xy = L.t.tile_xy;
+    T.n_chunks = L.n_chunks;
     T.dist2 = L.d2;
     T.alpha = (float)prm->alpha;
     T.d_min = (float)prm->d_min;

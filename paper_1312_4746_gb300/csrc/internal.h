@@ -132,7 +132,8 @@ struct SampleTables {
     int32_t* spop;    // popcount of each sample's bitmask
     uint32_t* rep;    // [n_labels][Wk]
     uint8_t* blob;    // tensor-core sample tiles (ring-stage layout)
-    int2* tile_xy;    // tensor-core sample tile coordinates
+    int2* tile_c;     // tensor-core sample tile anchors
+    int32_t* perm;    // tensor-core sample order (Morton order in chunks of 4096)
 };
 cudaError_t launch_gather(const float* img, int H, int W, const uint32_t* bitmask, int k,
                           int n_labels, const int32_t* d_label_off, const int32_t* sample_pix,
@@ -165,7 +166,7 @@ cudaError_t launch_sum_plain(const SumArgs& a, cudaStream_t st);
 
 // Likelihood-stage plan: shapes, forms and the carved scratch pointers.
 struct LikPlan {
-    int H, W, k, n_labels, S, total_tiles;
+    int H, W, k, n_labels, S, total_tiles, n_chunks;
     bool tc_form, tex8, persample;
     size_t stage_bytes;
     OffsetsParam offs;  // label offsets then first sample tile of each label
@@ -211,7 +212,7 @@ struct TcLaunch {
     int n_samples;
     SampleTables t;
     uint8_t* blob;
-    int2* tile_xy;
+    int n_chunks;  // Morton-sort chunks (4096 samples) over all labels
     const int32_t* dist2;
     float alpha, d_min, kappa_beta, sigma_c2;
     float* neglog;

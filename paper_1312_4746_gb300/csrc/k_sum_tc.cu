@@ -2,21 +2,29 @@
 // of Sec. 3.1 Eq. (color) x Eq. (post_text) (per-sample or factorised).
 //
 // Per pixel x and label i (log2 units, C = log2(e) / (2 sigma_c2),
-// Bt = log2(e) / beta_i(x), nA = -log2(e) / (2 rho_i(x)^2)), with x' and
-// x_j' the pixel and sample positions relative to the pixel tile's origin:
+// Bt = log2(e) / beta_i(x), nA = -log2(e) / (2 rho_i(x)^2)):
 //   e_j = nA |x - x_j|^2 - C |I - I_j|^2 - Bt TSM(b_x, b_j)
-//       = Bt D1_j + nA Dl_j + R0,
+//       = Bt D1_j + nA (Dl_j + K) + R0,
 //   D1_j = sum_t (2 b_x,t - 1) b_j,t  +  (1/Bt) (2 C I.I_j - C |I_j|^2)
-//   Dl_j = -2 x'.x_j' + |x_j'|^2,   R0 = -Bt |b_x| - C |I|^2 + nA |x'|^2.
+//   Dl_j = -2 x'.s_j - 2 delta.s_j + |s_j|^2,   R0 = -Bt |b_x| - C |I|^2,
+//   K = |x'|^2 + |delta|^2 + 2 x'.delta,
+// where x' = x - o (o the pixel tile's origin), s_j = x_j - c (c the first
+// sample of the sample tile, its anchor) and delta = o - c, so that
+// |x - x_j|^2 = |x' - s_j + delta|^2 = Dl_j + K.
 // The texture sum is an exact integer (2 b_x.b_j - |b_j|, so TSM = |b_x| minus
 // it) from an FP8 (e4m3, values 0 and +-1) or BF16 MMA; the colour part is a
 // 16-wide BF16 MMA over hi/lo splits of both factors (relative error about
 // 2^-17) into the same FP32 accumulator. Dl is a second 16-wide BF16 MMA whose
-// operands are exact small integers (x' < 16 x 8; x_j' = 128 h + l with
-// |h| < 256, 0 <= l < 128; |x_j'|^2 in four exact BF16 pieces), so Dl and
-// hence the squared distance are exact whenever |x_j'|^2 < 2^24 - every
-// sample near enough to matter. In the factorised form D1 is the colour
-// part alone with Bt = 1.
+// operands are exact small integers: x' < 16 x 8; s = 128 h + l and
+// delta = 128 dh + dl with |h|, |dh| < 256 and 0 <= l, dl < 128 (the cross
+// term delta.s as four products of pieces); |s|^2 in four exact BF16 pieces.
+// The samples of each label are sorted in Morton order in chunks of 4096, so
+// a sample tile spans a small region; then every partial sum of Dl for a
+// sample near the pixel stays below 2^24 and the squared distance is exact
+// (it is exact whenever the tile spans less than ~2300 pixels). The
+// B operand of Dl is precomputed per sample tile; the producer writes only
+// the A operand's delta entries per stage. In the factorised form D1 is the
+// colour part alone with Bt = 1.
 //
 // All full exponents are <= 0. The first chunk of 16 samples each warp sees
 // for a label fixes a reference maximum M; later terms can then exceed it by
@@ -26,9 +34,9 @@
 //
 // One persistent CTA per SM; a pixel tile is 16 x 8 pixels (one TMEM lane
 // each), a sample tile 128 samples (one TMEM column each).
-//   warp 16      producer: per stage, writes the location slab for the
-//                current pixel tile (generic stores + proxy fence) and
-//                bulk-copies (TMA) the pre-laid-out texture and colour slabs
+//   warp 16      producer: per stage, bulk-copies (TMA) the pre-laid-out
+//                texture, colour and location slabs of a sample tile and
+//                writes the pixel-side location slab (x' and delta entries)
 //   warp 17      MMA issuer: D1 <- texture slabs + colour slab,
 //                Dl <- location slab; TMEM double-buffered (4 x 128 columns)
 //   warps 0..15  epilogue: warp w reads lanes 32 (w % 4) .. +31 and columns
@@ -71,7 +79,7 @@ struct TcArgs {
     const int32_t* d_label_off;
     const int32_t* d_tile_off;  // first sample tile of each label, n_labels + 1
     const uint8_t* blob;        // total_tiles x copy_bytes: texture slabs + colour slab
-    const int2* tile_xy;        // total_tiles x 128 sample coordinates (padded: INT_MIN)
+    const int2* tile_c;         // anchor (first sample position) of each sample tile
     const uint32_t* rep;        // majority co-supports (factorised form)
     const int32_t* dist2;
     float alpha, d_min, kappa_beta, sigma_c2;
@@ -85,17 +93,16 @@ template <bool TEX8, int KS, bool PERSAMPLE>
 struct Cfg {
     static constexpr int tex_bytes = PERSAMPLE ? KS * 4096 : 0;
     static constexpr int col_off = tex_bytes;
-    static constexpr int loc_off = tex_bytes + 4096;
-    static constexpr int copy_bytes = tex_bytes + 4096;      // bulk-copied part of a stage
-    static constexpr int stage_bytes = tex_bytes + 2 * 4096; // + location slab
+    static constexpr int bloc_off = tex_bytes + 4096;         // sample-side location slab
+    static constexpr int aloc_off = tex_bytes + 2 * 4096;     // pixel-side location slab
+    static constexpr int copy_bytes = tex_bytes + 2 * 4096;   // bulk-copied part of a stage
+    static constexpr int stage_bytes = tex_bytes + 3 * 4096;
     // shared memory map
     static constexpr int ring_off = 0;
     static constexpr int atex_off = ring_off + STAGES * stage_bytes;
-    static constexpr int aloc_off = atex_off + tex_bytes;
-    static constexpr int acol_off = aloc_off + 4096;
+    static constexpr int acol_off = atex_off + tex_bytes;
     static constexpr int xchg_off = acol_off + 2 * 4096;              // [4][EPQ-1][4][32] float4
-    static constexpr int ls_off = xchg_off + 4 * (EPQ - 1) * 4 * 32 * 16;  // [64 labels][128] float
-    static constexpr int bar_off = ls_off + CS_MAX_LABELS * BM * 4;
+    static constexpr int bar_off = xchg_off + 4 * (EPQ - 1) * 4 * 32 * 16;
     static constexpr int n_bars = 2 * STAGES + 2 + 2 + 2 + 2 + 2 + 16;
     static constexpr int misc_off = bar_off + n_bars * 8;
     // at least 120 KB so that two CTAs never share an SM (each holds all 512 TMEM columns)
@@ -150,32 +157,19 @@ __device__ __forceinline__ int tiles_of(const int32_t* tile_off, int i) {
     return tile_off[i + 1] - tile_off[i];
 }
 
-// One row of the location operand of a sample at (x, y) relative to origin
-// (ox, oy): [h_x, l_x, h_y, l_y, q0, q1, q2, q3, 0...] with x' = 128 h + l and
-// |x'|^2 = q0 + q1 + q2 + q3 exactly (bf16 pieces). Padding rows put 2^30 in
-// q0 so that their exponents vanish.
-__device__ __forceinline__ void loc_row_b(int2 s, int ox, int oy, uint4& lo, uint4& hi) {
-    if (s.x == INT_MIN) {
-        lo = make_uint4(0, 0, pack2(bf16_bits(1073741824.f), 0), 0);
-        hi = make_uint4(0, 0, 0, 0);
-        return;
-    }
-    const int dx = s.x - ox, dy = s.y - oy;
-    const int hx = dx >> 7, lx = dx & 127, hy = dy >> 7, ly = dy & 127;
-    // q < 2^30: each piece is an integer with at most 8 significant bits, and
-    // the integer remainders shrink by 2^-8 per step, so four pieces are exact
-    int rem = dx * dx + dy * dy;
-    uint16_t qp[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const __nv_bfloat16 b = __float2bfloat16_rn((float)rem);
-        qp[u] = __bfloat16_as_ushort(b);
-        rem -= (int)__bfloat162float(b);
-    }
-    lo = make_uint4(pack2(bf16_bits((float)hx), bf16_bits((float)lx)),
-                    pack2(bf16_bits((float)hy), bf16_bits((float)ly)), pack2(qp[0], qp[1]),
-                    pack2(qp[2], qp[3]));
-    hi = make_uint4(0, 0, 0, 0);
+// Pixel-side location row for tile-relative position (px, py) and offset
+// (dx, dy) = o - c: [-256 px, -2 px, -256 py, -2 py, -32768 dhx, -256 dhx,
+// -256 dlx, -2 dlx, (same for y), 1, 1, 1, 1] with d = 128 dh + dl.
+__device__ __forceinline__ void loc_row_a(int px, int py, int dx, int dy, uint4& lo, uint4& hi) {
+    const int dhx = dx >> 7, dlx = dx & 127, dhy = dy >> 7, dly = dy & 127;
+    const uint16_t one = bf16_bits(1.f);
+    lo = make_uint4(pack2(bf16_bits(-256.f * px), bf16_bits(-2.f * px)),
+                    pack2(bf16_bits(-256.f * py), bf16_bits(-2.f * py)),
+                    pack2(bf16_bits(-32768.f * dhx), bf16_bits(-256.f * dhx)),
+                    pack2(bf16_bits(-256.f * dlx), bf16_bits(-2.f * dlx)));
+    hi = make_uint4(pack2(bf16_bits(-32768.f * dhy), bf16_bits(-256.f * dhy)),
+                    pack2(bf16_bits(-256.f * dly), bf16_bits(-2.f * dly)), pack2(one, one),
+                    pack2(one, one));
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
@@ -184,10 +178,8 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ring = smem + C::ring_off;
     uint8_t* atex = smem + C::atex_off;
-    uint8_t* aloc = smem + C::aloc_off;
     uint8_t* acol = smem + C::acol_off;
     float4* xchg = reinterpret_cast<float4*>(smem + C::xchg_off);
-    float* Ls = reinterpret_cast<float*>(smem + C::ls_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::bar_off);
     uint64_t* full = bars;                    // [STAGES] producer arrival + TMA bytes
     uint64_t* empty = bars + STAGES;          // [STAGES] MMA commit
@@ -221,18 +213,6 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    // pixel-side location operand, the same for every tile: row r holds
-    // x' = (r % 16, r / 16): [-256 x'_x, -2 x'_x, -256 x'_y, -2 x'_y, 1, 1, 1, 1, 0...]
-    if (threadIdx.x < BM) {
-        const int r = threadIdx.x, px = r % TW, py = r / TW;
-        const uint16_t one = bf16_bits(1.f);
-        const uint4 lo = make_uint4(pack2(bf16_bits(-256.f * px), bf16_bits(-2.f * px)),
-                                    pack2(bf16_bits(-256.f * py), bf16_bits(-2.f * py)),
-                                    pack2(one, one), pack2(one, one));
-        *reinterpret_cast<uint4*>(aloc + tc::slab_off(r, 0)) = lo;
-        *reinterpret_cast<uint4*>(aloc + tc::slab_off(r, 16)) = make_uint4(0, 0, 0, 0);
-        tc::fence_proxy_async_smem();
-    }
     if (warp == 0) {
         tc::tmem_alloc(tmem_base_s, TMEM_COLS);
         tc::tmem_relinquish();
@@ -256,14 +236,14 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     ok = wait_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1);
                     if (!ok) break;
                     uint8_t* st = ring + s * C::stage_bytes;
-                    const int2* xy = a.tile_xy + (size_t)(t0 + t) * BN;
+                    const int2 c = a.tile_c[t0 + t];
 #pragma unroll
-                    for (int u = 0; u < BN / 32; ++u) {
+                    for (int u = 0; u < BM / 32; ++u) {
                         const int r = u * 32 + lane;
                         uint4 lo, hi;
-                        loc_row_b(xy[r], ox, oy, lo, hi);
-                        *reinterpret_cast<uint4*>(st + C::loc_off + tc::slab_off(r, 0)) = lo;
-                        *reinterpret_cast<uint4*>(st + C::loc_off + tc::slab_off(r, 16)) = hi;
+                        loc_row_a(r % TW, r / TW, ox - c.x, oy - c.y, lo, hi);
+                        *reinterpret_cast<uint4*>(st + C::aloc_off + tc::slab_off(r, 0)) = lo;
+                        *reinterpret_cast<uint4*>(st + C::aloc_off + tc::slab_off(r, 16)) = hi;
                     }
                     tc::fence_proxy_async_smem();
                     __syncwarp();
@@ -315,8 +295,8 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                         }
                         tc::mma_bf16(d1, tc::smem_desc(acol + cb * 4096),
                                      tc::smem_desc(st + C::col_off), C::id_bf16, PERSAMPLE ? 1 : 0);
-                        tc::mma_bf16(dl, tc::smem_desc(aloc), tc::smem_desc(st + C::loc_off),
-                                     C::id_bf16, 0);
+                        tc::mma_bf16(dl, tc::smem_desc(st + C::aloc_off),
+                                     tc::smem_desc(st + C::bloc_off), C::id_bf16, 0);
                         tc::mma_commit(empty + s);
                         tc::mma_commit(tmem_full + b);
                         last = it;
@@ -345,7 +325,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             const long long pix = live ? (long long)y * a.W + x : 0;
             const float IR = a.img[pix * 3 + 0], IG = a.img[pix * 3 + 1], IB = a.img[pix * 3 + 2];
             const float I2 = fmaf(IR, IR, fmaf(IG, IG, IB * IB));
-            const float p2 = (float)(rx * rx + ry * ry);
+            const int ox = (pt % a.ntx) * TW, oy = (pt / a.ntx) * TH;
             uint32_t bx[8];
             int popx = 0;
 #pragma unroll
@@ -396,7 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 const float nA = -LOG2E / (2.f * rho * rho);
                 const float Bt = PERSAMPLE ? LOG2E / (a.kappa_beta * rho) : 1.f;
                 const float g = PERSAMPLE ? (a.kappa_beta * rho) / LOG2E : 1.f;
-                const float R0 = (PERSAMPLE ? -Bt * (float)popx : 0.f) - Cc * I2 + nA * p2;
+                const float R0 = (PERSAMPLE ? -Bt * (float)popx : 0.f) - Cc * I2;
                 // colour operand row (16 bf16): this warp writes half hf (hf < 2)
                 const int cb = (int)(li & 1);
                 ok = wait_warp(acol_empty + cb, (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag, a.d_err, 8);
@@ -420,7 +400,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
 
                 const int m_i = a.d_label_off[i + 1] - a.d_label_off[i];
                 const float lim = SAFE - log2f((float)m_i);
-                const int nt = tiles_of(a.d_tile_off, i);
+                const int nt = tiles_of(a.d_tile_off, i), t0 = a.d_tile_off[i];
                 float M = -INFINITY, S = 0.f, Ccomp = 0.f;
                 bool fixed = false;  // warp-uniform: reference maximum fixed
                 for (int t = 0; t < nt; ++t, ++it) {
@@ -429,6 +409,12 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     if (!ok) break;
                     tc::fence_after_sync();
                     const int nvalid = min(BN, m_i - t * BN);
+                    // per-tile location constant nA (|x'|^2 + |delta|^2 + 2 x'.delta)
+                    const int2 c = a.tile_c[t0 + t];
+                    const long long dX = ox - c.x, dY = oy - c.y;
+                    const long long Kq = (long long)(rx * rx + ry * ry) + dX * dX + dY * dY +
+                                         2ll * (rx * dX + ry * dY);
+                    const float nK = nA * (float)Kq;
 #pragma unroll
                     for (int c = 0; c < CPW / 16; ++c) {
                         const int col0 = hf * CPW + 16 * c;
@@ -440,7 +426,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                         if (col0 >= nvalid) continue;  // warp-uniform: padding only
                         float ts = 0.f;
                         if (fixed) {
-                            const float nM = -M;
+                            const float nM = nK - M;
 #pragma unroll
                             for (int u = 0; u < 16; ++u) {
                                 const float v = fmaf(nA, __uint_as_float(rl[u]),
@@ -452,7 +438,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                             float m = -INFINITY;
 #pragma unroll
                             for (int u = 0; u < 16; ++u) {
-                                e[u] = fmaf(nA, __uint_as_float(rl[u]), Bt * __uint_as_float(r1[u]));
+                                e[u] = fmaf(nA, __uint_as_float(rl[u]), fmaf(Bt, __uint_as_float(r1[u]), nK));
                                 m = fmaxf(m, e[u]);
                             }
                             if (m > M + LAZY || M == -INFINITY) {
@@ -502,8 +488,11 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                         Cm += v.z * sc;
                     }
                     const float lse2 = R0 + Mm + log2f(Sm + Cm);
-                    Ls[i * BM + r] = lse2 * LN2 - logf((float)m_i) -
-                                     logf(6.283185307179586f * rho * rho) - log_col_norm;
+                    // -L into the output plane; normalised once all labels are done
+                    if (live)
+                        a.neglog[(size_t)i * P + pix] = -(lse2 * LN2 - logf((float)m_i) -
+                                                          logf(6.283185307179586f * rho * rho) -
+                                                          log_col_norm);
                 }
             }
             if (!ok) break;
@@ -529,19 +518,17 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                         const float rho = a.alpha * fmaxf(sqrtf((float)a.dist2[(size_t)i * P + pix]), a.d_min);
                         int h = 0;
                         for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[i * a.Wk + w]);
-                        Ls[i * BM + r] += (-LOG2E * (float)h / (a.kappa_beta * rho) - tl) * LN2;
+                        a.neglog[(size_t)i * P + pix] -= (-LOG2E * (float)h / (a.kappa_beta * rho) - tl) * LN2;
                     }
                 }
                 float lmax = -INFINITY;
-                for (int i = 0; i < a.n_labels; ++i) lmax = fmaxf(lmax, Ls[i * BM + r]);
+                for (int i = 0; i < a.n_labels; ++i) lmax = fmaxf(lmax, -a.neglog[(size_t)i * P + pix]);
                 float ls = 0.f;
-                for (int i = 0; i < a.n_labels; ++i) ls += expf(Ls[i * BM + r] - lmax);
+                for (int i = 0; i < a.n_labels; ++i) ls += expf(-a.neglog[(size_t)i * P + pix] - lmax);
                 const float lse = lmax + logf(ls);
-                for (int i = 0; i < a.n_labels; ++i) {
-                    const float L = Ls[i * BM + r];
-                    a.neglog[(size_t)i * P + pix] = -L;
-                    if (a.post) a.post[(size_t)i * P + pix] = expf(L - lse);
-                }
+                if (a.post)
+                    for (int i = 0; i < a.n_labels; ++i)
+                        a.post[(size_t)i * P + pix] = expf(-a.neglog[(size_t)i * P + pix] - lse);
             }
         }
     }
@@ -553,15 +540,83 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
     }
 }
 
+// Morton order of each label's samples in chunks of 4096 (one block per
+// chunk, bitonic sort of (key, index) pairs in shared memory): consecutive
+// 128-sample tiles then cover compact regions.
+__device__ __forceinline__ uint32_t morton16(uint32_t v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) morton_sort_kernel(const int32_t* __restrict__ label_off,
+                                                           int n_labels, SampleTables t,
+                                                           int32_t* __restrict__ perm) {
+    __shared__ uint32_t key[4096];
+    __shared__ int32_t idx[4096];
+    // chunk -> (label, first sample, count)
+    int b = blockIdx.x, i = 0, start = 0, cnt = 0;
+    for (; i < n_labels; ++i) {
+        const int m = label_off[i + 1] - label_off[i];
+        const int nch = (m + 4095) / 4096;
+        if (b < nch) {
+            start = label_off[i] + b * 4096;
+            cnt = min(4096, label_off[i + 1] - start);
+            break;
+        }
+        b -= nch;
+    }
+    if (i == n_labels) return;
+    int n2 = 1;
+    while (n2 < cnt) n2 <<= 1;
+    for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+        if (e < cnt) {
+            const int sidx = start + e;
+            key[e] = morton16((uint32_t)t.sx[sidx]) | (morton16((uint32_t)t.sy[sidx]) << 1);
+            idx[e] = sidx;
+        } else {
+            key[e] = 0xFFFFFFFFu;
+            idx[e] = 0x7FFFFFFF;
+        }
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= n2; kk <<= 1)
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+                const int partner = e ^ jj;
+                if (partner > e) {
+                    const bool up = (e & kk) == 0;
+                    const uint32_t ka = key[e], kb = key[partner];
+                    const int ia = idx[e], ib = idx[partner];
+                    const bool gt = ka > kb || (ka == kb && ia > ib);
+                    if (gt == up) {
+                        key[e] = kb;
+                        key[partner] = ka;
+                        idx[e] = ib;
+                        idx[partner] = ia;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) perm[start + e] = idx[e];
+}
+
 // Sample tiles laid out as the bulk-copied part of a ring stage: texture
-// slabs (b_j in {0, 1}) and the colour slab (hi/lo bf16 of I_j and of
-// -C |I_j|^2); padded rows are zero. Coordinates go to tile_xy (padding:
-// INT_MIN).
+// slabs (b_j in {0, 1}), the colour slab (hi/lo bf16 of I_j and of
+// -C |I_j|^2) and the sample-side location slab ([h, l] of s = x_j - c per
+// axis, repeated as the pixel side's four cross products need, then |s|^2 in
+// four exact bf16 pieces); padded rows are zero except |s|^2 = 2^30, which
+// makes their exponents vanish. tile_c receives each tile's anchor c.
 template <bool TEX8, int KS, bool PERSAMPLE>
 __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
                                    const int32_t* __restrict__ tile_off, int n_labels,
                                    int total_tiles, SampleTables t, int n_samples, int k,
-                                   float Cc, uint8_t* __restrict__ blob, int2* __restrict__ tile_xy) {
+                                   float Cc, const int32_t* __restrict__ perm,
+                                   uint8_t* __restrict__ blob, int2* __restrict__ tile_c) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= (long long)total_tiles * BN) return;
@@ -572,8 +627,13 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
         if (tile_off[mid] <= tile) lo = mid; else hi = mid - 1;
     }
     const int i = lo;
-    const int s = label_off[i] + (tile - tile_off[i]) * BN + r;
-    const bool valid = s < label_off[i + 1];
+    const int first = label_off[i] + (tile - tile_off[i]) * BN;
+    const int pos = first + r;
+    const bool valid = pos < label_off[i + 1];
+    const int s = valid ? perm[pos] : 0;
+    const int s0 = perm[first];
+    const int cx = (int)t.sx[s0], cy = (int)t.sy[s0];
+    if (r == 0) tile_c[tile] = make_int2(cx, cy);
     uint8_t* st = blob + (size_t)tile * C::copy_bytes;
     if (PERSAMPLE) {
         for (int sl = 0; sl < KS; ++sl) {
@@ -603,6 +663,7 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
         }
     }
     uint32_t pw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t lw[8] = {0, 0, 0, 0, 0, 0, pack2(bf16_bits(1073741824.f), 0), 0};
     if (valid) {
         const float R = t.sr[s], G = t.sg[s], B = t.sb[s];
         const float qv = -Cc * fmaf(R, R, fmaf(G, G, B * B));
@@ -615,22 +676,38 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
         pw[2] = pack2(hg, lg); pw[3] = pack2(hg, lg);
         pw[4] = pack2(hb, lb); pw[5] = pack2(hb, lb);
         pw[6] = pack2(hq, lq); pw[7] = pack2(hq, lq);
+        const int dx = (int)t.sx[s] - cx, dy = (int)t.sy[s] - cy;
+        const uint32_t hxl = pack2(bf16_bits((float)(dx >> 7)), bf16_bits((float)(dx & 127)));
+        const uint32_t hyl = pack2(bf16_bits((float)(dy >> 7)), bf16_bits((float)(dy & 127)));
+        // |s|^2 < 2^30 in four integer pieces of at most 8 significant bits
+        int rem = dx * dx + dy * dy;
+        uint16_t qp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __nv_bfloat16 bq = __float2bfloat16_rn((float)rem);
+            qp[u] = __bfloat16_as_ushort(bq);
+            rem -= (int)__bfloat162float(bq);
+        }
+        lw[0] = hxl; lw[1] = hyl; lw[2] = hxl; lw[3] = hxl;
+        lw[4] = hyl; lw[5] = hyl; lw[6] = pack2(qp[0], qp[1]); lw[7] = pack2(qp[2], qp[3]);
     }
     *reinterpret_cast<uint4*>(st + C::col_off + tc::slab_off(r, 0)) = make_uint4(pw[0], pw[1], pw[2], pw[3]);
     *reinterpret_cast<uint4*>(st + C::col_off + tc::slab_off(r, 16)) = make_uint4(pw[4], pw[5], pw[6], pw[7]);
-    tile_xy[(size_t)tile * BN + r] =
-        valid ? make_int2((int)t.sx[s], (int)t.sy[s]) : make_int2(INT_MIN, INT_MIN);
+    *reinterpret_cast<uint4*>(st + C::bloc_off + tc::slab_off(r, 0)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    *reinterpret_cast<uint4*>(st + C::bloc_off + tc::slab_off(r, 16)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
 cudaError_t run(const TcLaunch& L, cudaStream_t st) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
+    static_assert(C::smem_bytes <= 227 * 1024, "shared memory budget");
     const int total_tiles = L.total_tiles;
     const float Cc = 1.4426950408889634f / (2.f * L.sigma_c2);
+    morton_sort_kernel<<<L.n_chunks, 1024, 0, st>>>(L.d_label_off, L.n_labels, L.t, L.t.perm);
     build_tiles_kernel<TEX8, KS, PERSAMPLE>
         <<<(unsigned)(((long long)total_tiles * BN + 127) / 128), 128, 0, st>>>(
             L.d_label_off, L.d_tile_off, L.n_labels, total_tiles, L.t, L.n_samples, L.k, Cc,
-            L.blob, L.tile_xy);
+            L.t.perm, L.blob, L.t.tile_c);
     TcArgs a{};
     a.img = L.img;
     a.H = L.H;
@@ -642,7 +719,7 @@ cudaError_t run(const TcLaunch& L, cudaStream_t st) {
     a.d_label_off = L.d_label_off;
     a.d_tile_off = L.d_tile_off;
     a.blob = L.blob;
-    a.tile_xy = L.tile_xy;
+    a.tile_c = L.t.tile_c;
     a.rep = L.t.rep;
     a.dist2 = L.dist2;
     a.alpha = L.alpha;
@@ -681,7 +758,7 @@ cudaError_t run_ks(const TcLaunch& L, int ks, cudaStream_t st) {
 
 size_t tc_copy_bytes(int k, bool tex8, bool persample) {
     const int ks = tex8 ? (k + 31) / 32 : (k + 15) / 16;
-    return (size_t)(persample ? ks * 4096 : 0) + 4096;
+    return (size_t)(persample ? ks * 4096 : 0) + 2 * 4096;
 }
 
 int tc_tiles_per_label(int m) { return (m + BN - 1) / BN; }
