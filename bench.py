@@ -111,24 +111,30 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Per-SM, per-clock issue rates of the pipes the plain FP32 pair loop uses
-# (Blackwell SM: 128 FP32 lanes, 64 INT32 lanes, 16 special-function lanes for
-# ex2 and 16 for popc). The pair-rate ceiling of the plain form is the minimum
-# over pipes of (lanes per clock / algorithmic operations per pair), times
-# SM count and clock.
-PIPE_LANES = {"fp32": 128, "int32": 64, "mufu": 16, "popc": 16}
+# Nominal per-SM, per-clock rates of the pipes the pair loops use on GB300
+# (152 SMs): 128 FP32 lanes, 64 INT32, 16 popc and 32 ex2 (special-function)
+# results per clock. A probe of chained FFMA / popc / ex2 on the box measured
+# 117, 15.2 and 30.3 per clock, consistent with these.
+PIPE_LANES = {"fp32": 128, "int32": 64, "mufu": 32, "popc": 16}
 
 
-def plain_pair_ops(Wk: int) -> dict:
-    """Algorithmic operations per pixel x sample pair of the plain form:
-    location 2 sub + mul + fma, colour 3 sub + mul + 2 fma, combine 3, running
-    max 1, exponent offset 1, sum 1 (FP32); Wk xor + (Wk - 1) add (INT32);
-    Wk popc; one ex2."""
-    return {"fp32": 16, "int32": 2 * Wk - 1, "popc": Wk, "mufu": 1}
+def pair_ops(form: str, Wk: int) -> dict:
+    """Algorithmic operations per pixel x sample pair.
+
+    fp32 (CUDA cores): location 2 sub + mul + fma, colour 3 sub + mul + 2 fma,
+    combine 3, running max, exponent offset and sum (16 FP32); Wk xor and
+    Wk - 1 adds (INT32); Wk popc; one ex2.
+    tensor-core forms: the dot products run on the tensor cores; the CUDA
+    cores do 2 FFMA (texture/colour scale, location scale) and one add per
+    pair (3 FP32) and one ex2.
+    """
+    if form == "fp32":
+        return {"fp32": 16, "int32": 2 * Wk - 1, "popc": Wk, "mufu": 1}
+    return {"fp32": 3, "mufu": 1}
 
 
-def alu_peak_pairs(Wk: int, sm_mhz: float, n_sm: int = 152) -> tuple[float, str]:
-    ops = plain_pair_ops(Wk)
+def alu_peak_pairs(form: str, Wk: int, sm_mhz: float, n_sm: int = 152) -> tuple[float, str]:
+    ops = pair_ops(form, Wk)
     rates = {k: PIPE_LANES[k] / v for k, v in ops.items()}
     pipe = min(rates, key=rates.get)
     return rates[pipe] * n_sm * sm_mhz * 1e6, pipe
@@ -199,13 +205,89 @@ def cpu_baseline(pr, budget_s=15.0):
                       f"(FP64 C oracle, OpenMP over pixels)"}
 
 
+FORMS = {"fp32": 0, "bf16": 1, "fp8": 2}
+FORM_NAMES = {"fp32": "plain FP32 (CUDA cores, popc TSM)",
+              "bf16": "tensor cores (tcgen05): BF16 exact texture dot, split-BF16 colour, exact location",
+              "fp8": "tensor cores (tcgen05): FP8 exact texture dot, split-BF16 colour, exact location"}
+# kernels one step launches (cs_data_term, per-sample form): offsets, seed,
+# row scan, column envelope; row norms, codes, guard; gather; then either the
+# plain sum, or Morton sort, tile build and the tcgen05 sum
+LAUNCHES = {"fp32": 9, "bf16": 11, "fp8": 11}
+
+
+def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=None):
+    """Device time (ms) of `steps` data-term steps with inputs resident, the
+    per-stage times, and the end-to-end time from pinned host buffers."""
+    P = pr.H * pr.W
+    nl = pr.n_labels
+    prm = cs.Params.from_synth(pr.params, precision=FORMS[form])
+    img = torch.from_numpy(pr.image).to(dev)
+    om = torch.from_numpy(pr.omega).to(dev)
+    mask = torch.from_numpy(pr.mask).to(dev)
+    smp = torch.from_numpy(pr.sample_pix).to(dev)
+    out = {"neglog": torch.empty((nl, pr.H, pr.W), dtype=torch.float32, device=dev),
+           "post": torch.empty((nl, pr.H, pr.W), dtype=torch.float32, device=dev)}
+
+    def step(img_d, om_d, mask_d, smp_d):
+        ctx.data_term(img_d, om_d, mask_d, pr.label_off, smp_d, prm, out=out)
+
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        step(img, om, mask, smp)
+    ctx.sync()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    for i in range(steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        step(img, om, mask, smp)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    ctx.sync()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    stage = {}
+    for name, st in (("codes", cs.STAGE_CODES), ("dist", cs.STAGE_DIST),
+                     ("gather", cs.STAGE_GATHER), ("sum", cs.STAGE_SUM)):
+        ms, n = ctx.profile_read(st)
+        stage[name] = ms / max(n, 1)
+    # end to end through the C ABI from pinned host buffers
+    h_img = torch.from_numpy(pr.image).pin_memory()
+    h_om = torch.from_numpy(pr.omega).pin_memory()
+    h_mask = torch.from_numpy(pr.mask).pin_memory()
+    h_smp = torch.from_numpy(pr.sample_pix).pin_memory()
+    h_out = torch.empty((nl, pr.H, pr.W), dtype=torch.float32).pin_memory()
+    d_img, d_om, d_mask, d_smp = (torch.empty_like(img), torch.empty_like(om),
+                                  torch.empty_like(mask), torch.empty_like(smp))
+    h2d = sum(t.numel() * t.element_size() for t in (h_img, h_om, h_mask, h_smp)) + 4 * (nl + 1)
+    d2h = h_out.numel() * 4
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(float(i))
+        e2e_ev[i][0].record(stream)
+        d_img.copy_(h_img, non_blocking=True)
+        d_om.copy_(h_om, non_blocking=True)
+        d_mask.copy_(h_mask, non_blocking=True)
+        d_smp.copy_(h_smp, non_blocking=True)
+        step(d_img, d_om, d_mask, d_smp)
+        h_out.copy_(out["neglog"], non_blocking=True)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    return dev_ms, e2e_ms, stage, h2d, d2h
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--form", default="fp32", choices=["fp32"])
+    ap.add_argument("--form", default="fp8", choices=list(FORMS))
     ap.add_argument("--ref-pixels", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -234,120 +316,73 @@ def main():
     # weak scaling: every rank gets its own image of the same shape
     pr = synth.make_workload(WORKLOAD, seed=1000 + WORKLOAD + 7919 * rank)
     P = pr.H * pr.W
-    k = pr.k
-    Wk = (k + 31) // 32
-    nl = pr.n_labels
+    Wk = (pr.k + 31) // 32
     ctx = cs.Context(local)
-    prm = cs.Params.from_synth(pr.params, precision=cs.FP32)
-
-    img = torch.from_numpy(pr.image).to(dev)
-    om = torch.from_numpy(pr.omega).to(dev)
-    mask = torch.from_numpy(pr.mask).to(dev)
-    smp = torch.from_numpy(pr.sample_pix).to(dev)
-    bits = torch.empty((P, Wk), dtype=torch.int32, device=dev)
-    out = {"neglog": torch.empty((nl, pr.H, pr.W), dtype=torch.float32, device=dev),
-           "post": torch.empty((nl, pr.H, pr.W), dtype=torch.float32, device=dev)}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    lib = cs.lib()
-
-    def step(img_d, om_d, mask_d, smp_d, out_d):
-        ctx.check(lib.cs_codes(ctx.handle, cs._ptr(img_d), pr.H, pr.W, cs._ptr(om_d), k,
-                               cs._ptr(mask_d), cs.ctypes.byref(prm), None, None,
-                               cs._ptr(bits), cs._stream()))
-        ctx.likelihood(img_d, bits, k, pr.label_off, smp_d, prm, out=out_d)
-
-    for _ in range(args.warmup):
-        flush.fill_(1.0)
-        step(img, om, mask, smp, out)
-    ctx.sync()
-
-    # ---------------- device-timed region (inputs resident in HBM)
-    n_launch_per_step = 3 + 6  # codes: rownorm, codes, guard; likelihood: fill, seed, cols, rows, gather, sum
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    ctx.profile(True)
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            evs[i][0].record(stream)
-            step(img, om, mask, smp, out)
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-    ctx.profile(False)
-    ctx.sync()
-    if world > 1:
-        torch.distributed.barrier()
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    sum_ms, sum_n = ctx.profile_read(cs.STAGE_SUM)
-    stage_ms = {name: ctx.profile_read(st)[0] / args.steps
-                for name, st in (("codes", cs.STAGE_CODES), ("dist", cs.STAGE_DIST),
-                                 ("gather", cs.STAGE_GATHER))}
-    stage_ms["sum"] = sum_ms / max(sum_n, 1)
-
-    # ---------------- end to end through the C ABI from pinned host buffers
-    h_img = torch.from_numpy(pr.image).pin_memory()
-    h_om = torch.from_numpy(pr.omega).pin_memory()
-    h_mask = torch.from_numpy(pr.mask).pin_memory()
-    h_smp = torch.from_numpy(pr.sample_pix).pin_memory()
-    h_out = torch.empty((nl, pr.H, pr.W), dtype=torch.float32).pin_memory()
-    d_img, d_om, d_mask, d_smp = (torch.empty_like(img), torch.empty_like(om),
-                                  torch.empty_like(mask), torch.empty_like(smp))
-    h2d = sum(t.numel() * t.element_size() for t in (h_img, h_om, h_mask, h_smp)) + 4 * (nl + 1)
-    d2h = h_out.numel() * 4
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        e2e_ev[i][0].record(stream)
-        d_img.copy_(h_img, non_blocking=True)
-        d_om.copy_(h_om, non_blocking=True)
-        d_mask.copy_(h_mask, non_blocking=True)
-        d_smp.copy_(h_smp, non_blocking=True)
-        step(d_img, d_om, d_mask, d_smp, out)
-        h_out.copy_(out["neglog"], non_blocking=True)
-        e2e_ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-
     pairs_rank = P * pr.n_samples
-    t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
+
+    forms = [args.form] + [f for f in ("fp32",) if f != args.form]
+    res = {}
     if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    dev_ms, e2e_ms = float(t[0]), float(t[1])
+        torch.distributed.barrier()
+    with ClockSampler(local) as clk:
+        for form in forms:
+            res[form] = measure(ctx, cs, torch, pr, form, args.steps, args.warmup, dev, stream,
+                                flush)
+    if world > 1:
+        torch.distributed.barrier()
+
+    def reduce_max(vals):
+        t = torch.tensor(vals, dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return [float(v) for v in t]
+
+    head = args.form
+    dev_ms, e2e_ms = reduce_max([res[head][0], res[head][1]])
     total_pairs = pairs_rank * world * args.steps
     value = total_pairs / (dev_ms * 1e-3)
     e2e_value = total_pairs / (e2e_ms * 1e-3)
-
     if rank == 0:
         peaks, src = _peaks()
         clocks = clk.summary()
         sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-        peak, pipe = alu_peak_pairs(Wk, sm_mhz, torch.cuda.get_device_properties(dev).multi_processor_count)
-        achieved = pairs_rank / (stage_ms["sum"] * 1e-3)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        forms_out = {}
+        for form in forms:
+            d_ms, e_ms, stage, h2d, d2h = res[form]
+            peak, pipe = alu_peak_pairs(form, Wk, sm_mhz, n_sm)
+            achieved = pairs_rank / (stage["sum"] * 1e-3)
+            forms_out[form] = {
+                "form": FORM_NAMES[form], "pairs_per_s": pairs_rank * args.steps / (d_ms * 1e-3),
+                "ms_per_step": d_ms / args.steps, "stage_ms": stage,
+                "sum_kernel_pairs_per_s": achieved, "sum_kernel_peak": peak,
+                "sum_kernel_frac": achieved / peak, "binding_pipe": pipe}
+        d_ms, e_ms, stage, h2d, d2h = res[head]
+        peak, pipe = alu_peak_pairs(head, Wk, sm_mhz, n_sm)
+        achieved = pairs_rank / (stage["sum"] * 1e-3)
+        kernel = "sum_plain_kernel" if head == "fp32" else "sum_tc_kernel"
         line = {
             "metric": "pixel x sample likelihood pairs/s", "value": value, "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "form": "plain FP32 (CUDA cores, popc TSM)",
-                       "mode": "per-sample", "pairs_per_step": pairs_rank,
+            "vs_baseline": None, "dtype": "f32" if head == "fp32" else head + "+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "form": FORM_NAMES[head], "mode": "per-sample",
+                       "pairs_per_step": pairs_rank,
                        "l2": "flushed between steps (256 MB write outside the timed events)",
-                       "stage_ms": stage_ms},
+                       "stage_ms": stage},
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": n_launch_per_step * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "pairs/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "sum_plain_kernel", "binding_pipe": pipe,
-                         "peak_basis": f"{PIPE_LANES[pipe]} {pipe} lanes/SM/clk / "
-                                       f"{plain_pair_ops(Wk)[pipe]} ops per pair x SMs x "
+            "gpu_launches": LAUNCHES[head] * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": kernel,
+                         "binding_pipe": pipe,
+                         "peak_basis": f"{PIPE_LANES[pipe]} {pipe} results/SM/clk / "
+                                       f"{pair_ops(head, Wk)[pipe]} per pair x {n_sm} SMs x "
                                        f"{sm_mhz:.0f} MHz (median SM clock sampled under load)"},
+            "forms": forms_out,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:

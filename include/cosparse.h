@@ -235,6 +235,14 @@ cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const u
                             const int32_t* sample_pix, const cs_params* prm, double margin,
                             float* neglog, float* post, int32_t* n_fallback, void* stream);
 cs_status cs_surrogate_params(cs_ctx* ctx, float* host_params, int cap, int* n_params);
+/*
+ * cs_surrogate_info: HOST copies of the standardisation statistics
+ * (mu_x[21], sd_x[21], mu_t[n], sd_t[n]; cap >= 42 + 2n floats, may be NULL),
+ * the calibrated validation error eta (nats), the last training step's loss
+ * and the training / validation pixel counts. Synchronises.
+ */
+cs_status cs_surrogate_info(cs_ctx* ctx, float* host_stats, int cap, float* eta, float* loss,
+                            int* n_train, int* n_val);
 int cs_mlp_param_count(int n_out);
 cs_status cs_mlp_forward(cs_ctx* ctx, const float* params, int n_out, const float* X, int rows,
                          float* Z, void* stream);

@@ -44,6 +44,7 @@ EXPORTS = (
     "cs_surrogate_fit",
     "cs_surrogate_eval",
     "cs_surrogate_params",
+    "cs_surrogate_info",
     "cs_mlp_param_count",
     "cs_mlp_forward",
     "cs_mlp_grad",
@@ -130,6 +131,7 @@ def lib(path: str | None = None):
     L.cs_surrogate_eval.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, V, V,
                                     V, V]
     L.cs_surrogate_params.argtypes = [V, V, I, ctypes.POINTER(I)]
+    L.cs_surrogate_info.argtypes = [V, V, I, V, V, ctypes.POINTER(I), ctypes.POINTER(I)]
     L.cs_mlp_param_count.argtypes = [I]
     L.cs_mlp_param_count.restype = I
     L.cs_mlp_forward.argtypes = [V, V, I, V, I, V, V]
@@ -138,7 +140,8 @@ def lib(path: str | None = None):
     L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     for f in ("cs_create", "cs_sync_status", "cs_codes", "cs_cosupport", "cs_likelihood",
               "cs_data_term", "cs_profile_enable", "cs_profile_read", "cs_surrogate_fit",
-              "cs_surrogate_eval", "cs_surrogate_params", "cs_mlp_forward", "cs_mlp_grad"):
+              "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_mlp_forward",
+              "cs_mlp_grad"):
         getattr(L, f).restype = I
     if path is None:
         _lib = L
@@ -327,6 +330,23 @@ class Context:
         self.check(self._lib.cs_surrogate_params(self.handle, ctypes.c_void_p(buf.ctypes.data),
                                                  n.value, ctypes.byref(n)))
         return buf
+
+    def surrogate_info(self, n_labels):
+        """(stats mu_x, sd_x, mu_t, sd_t; eta; last loss; n_train; n_val)."""
+        import numpy as np
+
+        st = np.zeros(42 + 2 * n_labels, np.float32)
+        eta = ctypes.c_float()
+        loss = ctypes.c_float()
+        ntr = ctypes.c_int()
+        nva = ctypes.c_int()
+        self.check(self._lib.cs_surrogate_info(self.handle, ctypes.c_void_p(st.ctypes.data), st.size,
+                                               ctypes.byref(eta), ctypes.byref(loss),
+                                               ctypes.byref(ntr), ctypes.byref(nva)))
+        n = n_labels
+        return {"mu_x": st[:21], "sd_x": st[21:42], "mu_t": st[42:42 + n],
+                "sd_t": st[42 + n:42 + 2 * n], "eta": eta.value, "loss": loss.value,
+                "n_train": ntr.value, "n_val": nva.value}
 
     def mlp_forward(self, params_dev, n_out, X):
         import torch

@@ -171,7 +171,9 @@ cs_status cs_surrogate_fit(cs_ctx* ctx, const float* img, int H, int W, const ui
     if (e == cudaSuccess) e = launch_init_params(sp.p, sp.m, sp.v, sp.g, n, seed, st);
     const int batch = 64 * std::max(1, std::min(ctx->n_sm, (ntr + 63) / 64));
     for (int t = 0; e == cudaSuccess && t < steps; ++t) {
-        e = launch_mlp_train(sp.p, n, X, Ts, ntr, (long long)t * batch, batch, sp.g, sp.loss, st);
+        if (t == steps - 1) e = cudaMemsetAsync(sp.loss, 0, sizeof(float), st);  // last-step loss
+        if (e == cudaSuccess)
+            e = launch_mlp_train(sp.p, n, X, Ts, ntr, (long long)t * batch, batch, sp.g, sp.loss, st);
         // learning rate 2e-3, cosine decay to 1e-4
         const float lr = 1e-4f + 0.5f * (2e-3f - 1e-4f) * (1.f + cosf(3.14159265f * t / steps));
         if (e == cudaSuccess) e = launch_adam(sp.p, sp.g, sp.m, sp.v, np, lr, t + 1, st);
@@ -271,6 +273,27 @@ cs_status cs_surrogate_params(cs_ctx* ctx, float* host_params, int cap, int* n_p
         cudaGetLastError();
         return cs_set_error(ctx, CS_ERR_CUDA, "cs_surrogate_params: copy failed");
     }
+    return CS_OK;
+}
+
+cs_status cs_surrogate_info(cs_ctx* ctx, float* host_stats, int cap, float* eta, float* loss,
+                            int* n_train, int* n_val) {
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_surrogate_info: ctx is NULL");
+    if (!ctx->surr_ready) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_surrogate_info: no surrogate");
+    const int n = ctx->surr_n;
+    SurrPtrs sp = surr_ptrs(ctx, n);
+    if (host_stats) {
+        if (cap < 2 * NIN + 2 * n)
+            return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_surrogate_info: cap < %d", 2 * NIN + 2 * n);
+        if (cudaMemcpy(host_stats, sp.stats, sizeof(float) * (2 * NIN + 2 * n), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return cs_set_error(ctx, CS_ERR_CUDA, "cs_surrogate_info: copy failed");
+    }
+    if (eta && cudaMemcpy(eta, sp.eta, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cs_set_error(ctx, CS_ERR_CUDA, "cs_surrogate_info: copy failed");
+    if (loss && cudaMemcpy(loss, sp.loss, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cs_set_error(ctx, CS_ERR_CUDA, "cs_surrogate_info: copy failed");
+    if (n_train) *n_train = ctx->surr_train;
+    if (n_val) *n_val = ctx->surr_val;
     return CS_OK;
 }
 
