@@ -403,14 +403,16 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 const int nt = tiles_of(a.d_tile_off, i), t0 = a.d_tile_off[i];
                 float M = -INFINITY, S = 0.f, Ccomp = 0.f;
                 bool fixed = false;  // warp-uniform: reference maximum fixed
+                int2 c_next = a.tile_c[t0];  // anchors fetched one tile ahead
                 for (int t = 0; t < nt; ++t, ++it) {
+                    const int2 c = c_next;
+                    if (t + 1 < nt) c_next = a.tile_c[t0 + t + 1];
                     const int b = (int)(it & 1);
                     ok = wait_warp(tmem_full + b, (uint32_t)((it >> 1) & 1), abort_flag, a.d_err, 10);
                     if (!ok) break;
                     tc::fence_after_sync();
                     const int nvalid = min(BN, m_i - t * BN);
                     // per-tile location constant nA (|x'|^2 + |delta|^2 + 2 x'.delta)
-                    const int2 c = a.tile_c[t0 + t];
                     const long long dX = ox - c.x, dY = oy - c.y;
                     const long long Kq = (long long)(rx * rx + ry * ry) + dX * dX + dY * dY +
                                          2ll * (rx * dX + ry * dY);
