@@ -134,6 +134,35 @@ cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* ome
                    uint32_t* bitmask, void* stream);
 
 /*
+ * cs_codes_noalloc: what cs_codes computes, for callers that cannot allocate
+ * device memory. The paper has no counterpart; this exists for callers such
+ * as code running while a CUDA graph is being captured (allocation would
+ * break the capture), applications whose device memory is entirely owned by
+ * another allocator or a fixed budget, and latency-critical loops where
+ * cudaMalloc / cudaFree would synchronise the device.
+ *
+ * It needs no context and allocates nothing: its scratch (operator row norms,
+ * the guard counter and a list of up to 2^20 guarded entries) is a fixed
+ * ~8 MB array in device memory that every GPU which loads the library holds
+ * until the process exits. The caller passes inputs and outputs as for
+ * cs_codes (bitmask required), plus dev_status: DEVICE 2 x int32, cleared by
+ * the call and set to a nonzero code (and a count) if more entries needed the
+ * exact double-precision recheck than the scratch holds (the bitmask is then
+ * not guaranteed exact). Limits: H * W <= 2^20 pixels, k <= 1024; larger
+ * requests return CS_ERR_INVALID_ARG before anything is launched.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents: calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller. Failures are reported
+ * through cs_last_error(NULL).
+ */
+cs_status cs_codes_noalloc(const float* img, int H, int W, const float* omega, int k,
+                           const float* mask, const cs_params* prm, float* codes, float* lead16,
+                           uint32_t* bitmask, int32_t* dev_status, void* stream);
+
+/*
  * Co-support bitmasks of given codes (Eq. 1): bit j of row q is set iff
  * |codes[q*k + j]| <= tau, compared in double precision.
  *   codes DEVICE P x k float32; bitmask DEVICE P x ceil(k/32) uint32.

@@ -38,6 +38,7 @@ EXPORTS = (
     "cs_last_error",
     "cs_sync_status",
     "cs_codes",
+    "cs_codes_noalloc",
     "cs_cosupport",
     "cs_likelihood",
     "cs_data_term",
@@ -124,6 +125,8 @@ def lib(path: str | None = None):
     L.cs_sync_status.argtypes = [V, V]
     L.cs_codes.argtypes = [V, V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V]
     L.cs_cosupport.argtypes = [V, V, I, I, D, V, V]
+    L.cs_codes_noalloc.argtypes = [V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V, V]
+    L.cs_codes_noalloc.restype = I
     L.cs_likelihood.argtypes = [V, V, I, I, V, I, I, V, V, ctypes.POINTER(Params), V, V, V, V]
     L.cs_data_term.argtypes = [V, V, I, I, V, I, V, I, V, V, ctypes.POINTER(Params), V, V, V, V, V]
     U64 = ctypes.c_uint64
