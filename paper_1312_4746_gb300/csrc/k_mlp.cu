@@ -30,7 +30,6 @@
 namespace {
 
 constexpr int NIN = 21, HID = 64, BS = 64, SP = BS + 1;  // SP: padded sample stride
-constexpr float LOG2E = 1.4426950408889634f;
 
 __host__ __device__ constexpr int off_W1() { return 0; }
 __host__ __device__ constexpr int off_b1() { return HID * NIN; }

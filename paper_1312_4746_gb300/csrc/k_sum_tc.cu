@@ -34,14 +34,15 @@
 //
 // One persistent CTA per SM; a pixel tile is 16 x 8 pixels (one TMEM lane
 // each), a sample tile 128 samples (one TMEM column each).
-//   warp 16      producer: per stage, bulk-copies (TMA) the pre-laid-out
+//   warp 8       producer: per stage, bulk-copies (TMA) the pre-laid-out
 //                texture, colour and location slabs of a sample tile and
 //                writes the pixel-side location slab (x' and delta entries)
-//   warp 17      MMA issuer: D1 <- texture slabs + colour slab,
+//   warp 9       MMA issuer: D1 <- texture slabs + colour slab,
 //                Dl <- location slab; TMEM double-buffered (4 x 128 columns)
-//   warps 0..15  epilogue: warp w reads lanes 32 (w % 4) .. +31 and columns
-//                32 (w / 4) .. +31 of each tile, merges the four column
-//                quarters per label and normalises over labels.
+//   warps 0..7   epilogue: warp w reads lanes 32 (w % 4) .. +31 and columns
+//                64 (w / 4) .. +63 of each tile (two 32-column loads, the
+//                second in flight while the first is consumed), merges the
+//                two column halves per label and normalises over labels.
 // Every mbarrier wait is bounded by the global timer; on expiry the CTA sets
 // the device error word, stops issuing, drains its copies and MMAs, frees its
 // tensor memory and exits.
@@ -57,10 +58,10 @@ namespace {
 constexpr int BM = 128, BN = 128;
 constexpr int TW = 16, TH = 8;          // pixel tile 16 x 8
 constexpr int STAGES = 3;
-constexpr int EPQ = 4;                  // epilogue warps per TMEM lane quadrant
-constexpr int EPI_WARPS = 4 * EPQ;      // 16
-constexpr int CPW = BN / EPQ;           // columns per epilogue warp per tile (32)
-constexpr int PRODUCER = EPI_WARPS;     // warp 16
+constexpr int EPQ = 2;                  // epilogue warps per TMEM lane quadrant
+constexpr int EPI_WARPS = 4 * EPQ;      // 8
+constexpr int CPW = BN / EPQ;           // columns per epilogue warp per tile (64)
+constexpr int PRODUCER = EPI_WARPS;     // warp 8
 constexpr int MMA_WARP = EPI_WARPS + 1;
 constexpr int THREADS = (EPI_WARPS + 2) * 32;
 constexpr uint32_t TMEM_COLS = 512;     // D1[2] at 0, 128; Dl[2] at 256, 384
@@ -170,6 +171,59 @@ __device__ __forceinline__ void loc_row_a(int px, int py, int dx, int dy, uint4&
     hi = make_uint4(pack2(bf16_bits(-32768.f * dhy), bf16_bits(-256.f * dhy)),
                     pack2(bf16_bits(-256.f * dly), bf16_bits(-2.f * dly)), pack2(one, one),
                     pack2(one, one));
+}
+
+// Online log-sum-exp over 16 columns (nv of them valid) of one pixel row:
+// exponents e = nA Dl + Bt D1 + nK (log2 units). With a fixed reference
+// maximum M (see the file header) and a full chunk, four independent sums
+// of 2^(e - M); otherwise the general path with the running maximum (lazy
+// rescale) until the reference can be fixed. TwoSum-compensated into (S, C).
+__device__ __forceinline__ void lse16(const uint32_t (&r1)[16], const uint32_t (&rl)[16], int nv,
+                                      float nA, float Bt, float nK, float R0, float lim,
+                                      float& M, float& S, float& Cc, bool& fixed) {
+    float ts;
+    if (fixed && nv >= 16) {
+        const float nM = nK - M;
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) {
+            t0 += ex2f(fmaf(nA, __uint_as_float(rl[u + 0]), fmaf(Bt, __uint_as_float(r1[u + 0]), nM)));
+            t1 += ex2f(fmaf(nA, __uint_as_float(rl[u + 1]), fmaf(Bt, __uint_as_float(r1[u + 1]), nM)));
+            t2 += ex2f(fmaf(nA, __uint_as_float(rl[u + 2]), fmaf(Bt, __uint_as_float(r1[u + 2]), nM)));
+            t3 += ex2f(fmaf(nA, __uint_as_float(rl[u + 3]), fmaf(Bt, __uint_as_float(r1[u + 3]), nM)));
+        }
+        ts = (t0 + t1) + (t2 + t3);
+    } else {
+        // first pass: maximum over the valid columns; second pass: the sum
+        float m = -INFINITY;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const float v = fmaf(nA, __uint_as_float(rl[u]), fmaf(Bt, __uint_as_float(r1[u]), nK));
+            if (u < nv) m = fmaxf(m, v);
+        }
+        if (!fixed && (m > M + LAZY || M == -INFINITY)) {
+            const float sc = ex2f(M - m);
+            S *= sc;
+            Cc *= sc;
+            M = m;
+        }
+        const float nM = nK - M;
+        float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; u += 2) {
+            const float v0 = fmaf(nA, __uint_as_float(rl[u]), fmaf(Bt, __uint_as_float(r1[u]), nM));
+            const float v1 = fmaf(nA, __uint_as_float(rl[u + 1]), fmaf(Bt, __uint_as_float(r1[u + 1]), nM));
+            t0 += u < nv ? ex2f(v0) : 0.f;
+            t1 += u + 1 < nv ? ex2f(v1) : 0.f;
+        }
+        ts = t0 + t1;
+        // every later exponent is <= -R0, i.e. at most -(M + R0) above M
+        if (!fixed) fixed = __all_sync(0xffffffffu, -(M + R0) <= lim);
+    }
+    const float sn = S + ts;
+    const float bb = sn - S;
+    Cc += (S - (sn - bb)) + (ts - bb);
+    S = sn;
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
@@ -326,40 +380,42 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             const float IR = a.img[pix * 3 + 0], IG = a.img[pix * 3 + 1], IB = a.img[pix * 3 + 2];
             const float I2 = fmaf(IR, IR, fmaf(IG, IG, IB * IB));
             const int ox = (pt % a.ntx) * TW, oy = (pt / a.ntx) * TH;
-            uint32_t bx[8];
+            const uint32_t* bxp = a.bitmask + pix * a.Wk;  // this pixel's co-support words
             int popx = 0;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                bx[w] = (w < a.Wk && live) ? a.bitmask[pix * a.Wk + w] : 0u;
-                popx += __popc(bx[w]);
-            }
+            if (live)
+                for (int w = 0; w < a.Wk; ++w) popx += __popc(bxp[w]);
             // texture operand rows: this warp writes slabs sl = hf, hf + EPQ, ...
             if (PERSAMPLE) {
                 ok = wait_warp(atex_empty, (uint32_t)((lpt & 1) ^ 1), abort_flag, a.d_err, 7);
                 if (!ok) break;
                 for (int sl = hf; sl < KS; sl += EPQ) {
+                    // FP8: slab sl holds codes 32 sl .. 32 sl + 31 (bitmask word sl);
+                    // BF16: codes 16 sl .. 16 sl + 15 (half of word sl / 2)
+                    const int wi = TEX8 ? sl : sl >> 1;
+                    const uint32_t word = live && wi < a.Wk ? bxp[wi] : 0u;
+                    const int j0 = TEX8 ? 32 * sl : 16 * sl;
+                    const int valid = live ? min(max(a.k - j0, 0), TEX8 ? 32 : 16) : 0;
+                    const uint32_t bits = TEX8 ? word : (word >> (16 * (sl & 1))) & 0xFFFFu;
                     uint32_t wv[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        uint32_t word = 0;
+                        uint32_t packed = 0;
                         if (TEX8) {
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
-                                const int j = 32 * sl + 4 * c + e;
-                                uint32_t v = 0;
-                                if (live && j < a.k) v = ((bx[j >> 5] >> (j & 31)) & 1u) ? 0x38u : 0xB8u;
-                                word |= v << (8 * e);
+                                const int jj = 4 * c + e;
+                                const uint32_t v = jj < valid ? (((bits >> jj) & 1u) ? 0x38u : 0xB8u) : 0u;
+                                packed |= v << (8 * e);
                             }
                         } else {
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
-                                const int j = 16 * sl + 2 * c + e;
-                                uint32_t v = 0;
-                                if (live && j < a.k) v = ((bx[j >> 5] >> (j & 31)) & 1u) ? 0x3F80u : 0xBF80u;
-                                word |= v << (16 * e);
+                                const int jj = 2 * c + e;
+                                const uint32_t v = jj < valid ? (((bits >> jj) & 1u) ? 0x3F80u : 0xBF80u) : 0u;
+                                packed |= v << (16 * e);
                             }
                         }
-                        wv[c] = word;
+                        wv[c] = packed;
                     }
                     uint8_t* base = atex + sl * 4096;
                     *reinterpret_cast<uint4*>(base + tc::slab_off(r, 0)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
@@ -412,60 +468,47 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     if (!ok) break;
                     tc::fence_after_sync();
                     const int nvalid = min(BN, m_i - t * BN);
-                    // per-tile location constant nA (|x'|^2 + |delta|^2 + 2 x'.delta)
-                    const long long dX = ox - c.x, dY = oy - c.y;
-                    const long long Kq = (long long)(rx * rx + ry * ry) + dX * dX + dY * dY +
-                                         2ll * (rx * dX + ry * dY);
-                    const float nK = nA * (float)Kq;
-#pragma unroll
-                    for (int c = 0; c < CPW / 16; ++c) {
-                        const int col0 = hf * CPW + 16 * c;
-                        uint32_t r1[16], rl[16];
-                        const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
-                        tc::tmem_ld16(lanebase + (uint32_t)(b * BN + col0), r1);
-                        tc::tmem_ld16(lanebase + 256u + (uint32_t)(b * BN + col0), rl);
+                    // per-tile location constant nA |x' + delta|^2, delta = o - c
+                    const float kx = (float)(rx + ox - c.x), ky = (float)(ry + oy - c.y);
+                    const float nK = nA * fmaf(kx, kx, ky * ky);
+                    const int cbase = hf * CPW;
+                    const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
+                    if (cbase < nvalid) {  // warp-uniform
+                        // four 16-column chunks; the next one loads while this one is consumed
+                        const int nch = min(CPW / 16, (nvalid - cbase + 15) / 16);  // warp-uniform
+                        uint32_t x1[16], xl[16], y1[16], yl[16];
+                        tc::tmem_ld16(lb, x1);
+                        tc::tmem_ld16(lb + 256u, xl);
                         tc::tmem_ld_wait();
-                        if (col0 >= nvalid) continue;  // warp-uniform: padding only
-                        float ts = 0.f;
-                        if (fixed) {
-                            const float nM = nK - M;
 #pragma unroll
-                            for (int u = 0; u < 16; ++u) {
-                                const float v = fmaf(nA, __uint_as_float(rl[u]),
-                                                     fmaf(Bt, __uint_as_float(r1[u]), nM));
-                                ts += ex2f(v);
+                        for (int ch = 0; ch < CPW / 16; ch += 2) {
+                            if (ch < nch) {
+                                if (ch + 1 < nch) {
+                                    tc::tmem_ld16(lb + 16u * (ch + 1), y1);
+                                    tc::tmem_ld16(lb + 256u + 16u * (ch + 1), yl);
+                                }
+                                lse16(x1, xl, nvalid - cbase - 16 * ch, nA, Bt, nK, R0, lim, M, S,
+                                      Ccomp, fixed);
+                                if (ch + 1 < nch) tc::tmem_ld_wait();
                             }
-                        } else {
-                            float e[16];
-                            float m = -INFINITY;
-#pragma unroll
-                            for (int u = 0; u < 16; ++u) {
-                                e[u] = fmaf(nA, __uint_as_float(rl[u]), fmaf(Bt, __uint_as_float(r1[u]), nK));
-                                m = fmaxf(m, e[u]);
+                            if (ch + 1 < nch) {
+                                if (ch + 2 < nch) {
+                                    tc::tmem_ld16(lb + 16u * (ch + 2), x1);
+                                    tc::tmem_ld16(lb + 256u + 16u * (ch + 2), xl);
+                                }
+                                lse16(y1, yl, nvalid - cbase - 16 * (ch + 1), nA, Bt, nK, R0, lim, M,
+                                      S, Ccomp, fixed);
+                                if (ch + 2 < nch) tc::tmem_ld_wait();
                             }
-                            if (m > M + LAZY || M == -INFINITY) {
-                                const float sc = ex2f(M - m);
-                                S *= sc;
-                                Ccomp *= sc;
-                                M = m;
-                            }
-#pragma unroll
-                            for (int u = 0; u < 16; ++u) ts += ex2f(e[u] - M);
-                            // all later terms are <= -R0 in the frame of M
-                            fixed = __all_sync(0xffffffffu, -(M + R0) <= lim);
                         }
-                        const float sn = S + ts;
-                        const float bb = sn - S;
-                        Ccomp += (S - (sn - bb)) + (ts - bb);
-                        S = sn;
                     }
                     tc::fence_before_sync();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(tmem_empty + b);
                 }
                 if (!ok) break;
-                // merge the EPQ column quarters of each pixel. Four exchange
-                // buffers: a quarter can run at most two sample tiles ahead of
+                // merge the EPQ column parts of each pixel. Four exchange
+                // buffers: a part can run at most two sample tiles ahead of
                 // another (tensor memory is double-buffered and every label has
                 // at least one tile), so buffer li & 3 is free when rewritten.
                 const int xbuf = (int)(li & 3);
@@ -498,28 +541,28 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 }
             }
             if (!ok) break;
-            // label normalisation (and the factorised texture posterior) by quarter 0
+            // label normalisation (and the factorised texture posterior) by part 0
             if (hf == 0 && live) {
                 if (!PERSAMPLE) {
                     float tmax = -INFINITY;
                     for (int i = 0; i < a.n_labels; ++i) {
                         const float rho = a.alpha * fmaxf(sqrtf((float)a.dist2[(size_t)i * P + pix]), a.d_min);
                         int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[i * a.Wk + w]);
+                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ a.rep[i * a.Wk + w]);
                         tmax = fmaxf(tmax, -LOG2E * (float)h / (a.kappa_beta * rho));
                     }
                     float ts = 0.f;
                     for (int i = 0; i < a.n_labels; ++i) {
                         const float rho = a.alpha * fmaxf(sqrtf((float)a.dist2[(size_t)i * P + pix]), a.d_min);
                         int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[i * a.Wk + w]);
+                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ a.rep[i * a.Wk + w]);
                         ts += ex2f(-LOG2E * (float)h / (a.kappa_beta * rho) - tmax);
                     }
                     const float tl = tmax + log2f(ts);
                     for (int i = 0; i < a.n_labels; ++i) {
                         const float rho = a.alpha * fmaxf(sqrtf((float)a.dist2[(size_t)i * P + pix]), a.d_min);
                         int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[i * a.Wk + w]);
+                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ a.rep[i * a.Wk + w]);
                         a.neglog[(size_t)i * P + pix] -= (-LOG2E * (float)h / (a.kappa_beta * rho) - tl) * LN2;
                     }
                 }
