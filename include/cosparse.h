@@ -243,6 +243,8 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
  *   neglog/post there, except at pixels whose top-2 posterior margin is below
  *   `margin` or whose top-2 log-likelihood gap is below
  *   2.2 eta + log((n_labels - 1) / 0.005); those get the exact FP32 sum.
+ *   A negative margin disables the fallback: the network answers every pixel
+ *   (an approximation with no error guarantee, for speed/accuracy studies).
  *   n_fallback (HOST int32, may be NULL) receives their count; when given,
  *   the call synchronises.
  * cs_surrogate_params: copies the fp32 master weights to HOST memory

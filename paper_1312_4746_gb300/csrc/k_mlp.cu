@@ -457,7 +457,8 @@ __global__ void __launch_bounds__(BS) surrogate_eval_kernel(
     // a gap g guarantees a max probability error <= eps when every logit is
     // within eta of the truth: (n - 1) exp(-(g - 2 eta)) <= eps
     const float gap_min = 2.2f * (*eta) + logf(fmaxf((float)(n - 1), 1.f) / eps);
-    const bool fb = (p1 - p2 < margin) || (n > 1 && m1 - m2 < gap_min);
+    // margin < 0: the network answers every pixel (no exact fallback)
+    const bool fb = margin >= 0.f && ((p1 - p2 < margin) || (n > 1 && m1 - m2 < gap_min));
     if (fb) {
         const int idx = atomicAdd(fb_count, 1);
         if (idx < P) fb_list[idx] = (int32_t)q;

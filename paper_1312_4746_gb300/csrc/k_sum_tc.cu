@@ -34,15 +34,15 @@
 //
 // One persistent CTA per SM; a pixel tile is 16 x 8 pixels (one TMEM lane
 // each), a sample tile 128 samples (one TMEM column each).
-//   warp 8       producer: per stage, bulk-copies (TMA) the pre-laid-out
+//   warp 16      producer: per stage, bulk-copies (TMA) the pre-laid-out
 //                texture, colour and location slabs of a sample tile and
 //                writes the pixel-side location slab (x' and delta entries)
-//   warp 9       MMA issuer: D1 <- texture slabs + colour slab,
+//   warp 17      MMA issuer: D1 <- texture slabs + colour slab,
 //                Dl <- location slab; TMEM double-buffered (4 x 128 columns)
-//   warps 0..7   epilogue: warp w reads lanes 32 (w % 4) .. +31 and columns
-//                64 (w / 4) .. +63 of each tile (two 32-column loads, the
-//                second in flight while the first is consumed), merges the
-//                two column halves per label and normalises over labels.
+//   warps 0..15  epilogue: warp w reads lanes 32 (w % 4) .. +31 and columns
+//                32 (w / 4) .. +31 of each tile (two 16-column loads),
+//                merges the four column parts per label and normalises
+//                over labels.
 // Every mbarrier wait is bounded by the global timer; on expiry the CTA sets
 // the device error word, stops issuing, drains its copies and MMAs, frees its
 // tensor memory and exits.
@@ -58,10 +58,10 @@ namespace {
 constexpr int BM = 128, BN = 128;
 constexpr int TW = 16, TH = 8;          // pixel tile 16 x 8
 constexpr int STAGES = 3;
-constexpr int EPQ = 2;                  // epilogue warps per TMEM lane quadrant
-constexpr int EPI_WARPS = 4 * EPQ;      // 8
-constexpr int CPW = BN / EPQ;           // columns per epilogue warp per tile (64)
-constexpr int PRODUCER = EPI_WARPS;     // warp 8
+constexpr int EPQ = 4;                  // epilogue warps per TMEM lane quadrant
+constexpr int EPI_WARPS = 4 * EPQ;      // 16
+constexpr int CPW = BN / EPQ;           // columns per epilogue warp per tile (32)
+constexpr int PRODUCER = EPI_WARPS;     // warp 16
 constexpr int MMA_WARP = EPI_WARPS + 1;
 constexpr int THREADS = (EPI_WARPS + 2) * 32;
 constexpr uint32_t TMEM_COLS = 512;     // D1[2] at 0, 128; Dl[2] at 256, 384
@@ -474,31 +474,15 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     const int cbase = hf * CPW;
                     const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
                     if (cbase < nvalid) {  // warp-uniform
-                        // four 16-column chunks; the next one loads while this one is consumed
-                        const int nch = min(CPW / 16, (nvalid - cbase + 15) / 16);  // warp-uniform
-                        uint32_t x1[16], xl[16], y1[16], yl[16];
-                        tc::tmem_ld16(lb, x1);
-                        tc::tmem_ld16(lb + 256u, xl);
-                        tc::tmem_ld_wait();
+                        uint32_t x1[16], xl[16];
 #pragma unroll
-                        for (int ch = 0; ch < CPW / 16; ch += 2) {
-                            if (ch < nch) {
-                                if (ch + 1 < nch) {
-                                    tc::tmem_ld16(lb + 16u * (ch + 1), y1);
-                                    tc::tmem_ld16(lb + 256u + 16u * (ch + 1), yl);
-                                }
+                        for (int ch = 0; ch < CPW / 16; ++ch) {
+                            if (cbase + 16 * ch < nvalid) {  // warp-uniform
+                                tc::tmem_ld16(lb + 16u * ch, x1);
+                                tc::tmem_ld16(lb + 256u + 16u * ch, xl);
+                                tc::tmem_ld_wait();
                                 lse16(x1, xl, nvalid - cbase - 16 * ch, nA, Bt, nK, R0, lim, M, S,
                                       Ccomp, fixed);
-                                if (ch + 1 < nch) tc::tmem_ld_wait();
-                            }
-                            if (ch + 1 < nch) {
-                                if (ch + 2 < nch) {
-                                    tc::tmem_ld16(lb + 16u * (ch + 2), x1);
-                                    tc::tmem_ld16(lb + 256u + 16u * (ch + 2), xl);
-                                }
-                                lse16(y1, yl, nvalid - cbase - 16 * (ch + 1), nA, Bt, nK, R0, lim, M,
-                                      S, Ccomp, fixed);
-                                if (ch + 2 < nch) tc::tmem_ld_wait();
                             }
                         }
                     }

@@ -202,8 +202,8 @@ cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const u
     if (!ctx->surr_ready || ctx->surr_n != n_labels)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: no surrogate fitted for %d labels", fn,
                             n_labels);
-    if (!(margin >= 0.0 && margin <= 1.0))
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: margin must be in [0, 1]", fn);
+    if (!(margin <= 1.0))
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: margin must be <= 1", fn);
     cs_status s = cs_check_likelihood_args(ctx, fn, H, W, k, n_labels, label_off, prm);
     if (s) return s;
     cudaStream_t st = (cudaStream_t)stream;
