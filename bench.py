@@ -205,6 +205,11 @@ def cpu_baseline(pr, budget_s=15.0):
                       f"(FP64 C oracle, OpenMP over pixels)"}
 
 
+# DRAM bytes per launch of the sum kernels on this workload
+# (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
+# kernels as they are now)
+TRAFFIC = {"sum_tc_kernel": 9.47e6, "sum_plain_kernel": 7.83e6}
+
 FORMS = {"fp32": 0, "bf16": 1, "fp8": 2}
 FORM_NAMES = {"fp32": "plain FP32 (CUDA cores, popc TSM)",
               "bf16": "tensor cores (tcgen05): BF16 exact texture dot, split-BF16 colour, exact location",
@@ -377,7 +382,7 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": LAUNCHES[head] * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": kernel,
+                         "frac": achieved / peak, "traffic": TRAFFIC.get(kernel), "kernel": kernel,
                          "binding_pipe": pipe,
                          "peak_basis": f"{PIPE_LANES[pipe]} {pipe} results/SM/clk / "
                                        f"{pair_ops(head, Wk)[pipe]} per pair x {n_sm} SMs x "
