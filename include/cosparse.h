@@ -220,6 +220,84 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
                        int32_t* dist2, float* neglog, float* post, void* stream);
 
 /*
+ * Batches of images (the same operator, patch mask and parameters for all;
+ * every image with its own size, labels and scribbles).
+ *
+ * The paper segments one image at a time (Sec. 4-5); a batch is this
+ * library's way to fill the GPU with many of them. A batch is planned once
+ * (cs_batch_create) and run any number of times (cs_batch_run): each run
+ * re-reads the images' and scribbles' current contents from the buffers named
+ * at creation and rewrites the outputs, so a serving loop refills the same
+ * input buffers and runs again. One run:
+ *  - per image, on one of n_streams context-independent streams (round robin
+ *    in processing order): exact scribble distances, codes and co-support
+ *    bitmasks, sample tables and, for the tensor-core forms, the image's
+ *    sample tiles and descriptor;
+ *  - tensor-core forms: ONE persistent tcgen05 launch over the work items
+ *    (image, 16 x 8 pixel tile) of all images, in processing order; CTA c
+ *    takes items c, c + 152, ... (plain FP32 form: one sum launch per image
+ *    on its stream).
+ * Processing order: by decreasing pixel x sample pairs (order 0), so that
+ * the persistent launch ends with the cheapest items, or as given (order 1).
+ * Results are bit-identical to cs_data_term on each image alone.
+ */
+typedef struct {
+    const float* img;          /* DEVICE H x W x 3 float32 */
+    int32_t H, W;
+    int32_t n_labels;          /* 1 .. 64 */
+    int32_t reserved;          /* must be 0 */
+    const int32_t* label_off;  /* HOST n_labels + 1, read by cs_batch_create only */
+    const int32_t* sample_pix; /* DEVICE label_off[n_labels] int32 pixel indices */
+    uint32_t* bitmask;         /* DEVICE P x ceil(k/32) out, or NULL (batch memory) */
+    int32_t* dist2;            /* DEVICE n_labels x P out, or NULL (batch memory) */
+    float* neglog;             /* DEVICE n_labels x P out, required */
+    float* post;               /* DEVICE n_labels x P out, or NULL */
+} cs_image;
+
+#define CS_BATCH_GRAPH 1    /* capture the run into a CUDA graph after the first run; replay it */
+#define CS_BATCH_AUTOTUNE 2 /* first run times each (n_streams, order) candidate (synchronises) */
+
+typedef struct cs_batch cs_batch;
+
+/*
+ * Validates every image (as cs_data_term would), sizes and allocates the
+ * batch's own device memory (it does not use the context's scratch) and
+ * fixes the plan. `images` and every label_off array are copied; the device
+ * buffers they name must stay valid until cs_batch_destroy. k, omega, mask
+ * and prm as in cs_codes / cs_likelihood. flags: CS_BATCH_GRAPH,
+ * CS_BATCH_AUTOTUNE (or 0). A tuned configuration is remembered by the
+ * context for batches with the same shapes; with the environment variable
+ * CS_TUNE_CACHE naming a file it is also read from / appended to that file.
+ * Errors: as cs_data_term for the image at fault (the message names its
+ * index), CS_ERR_INVALID_ARG for n_images < 1 or > 4096, CS_ERR_NOMEM.
+ */
+cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, const float* omega,
+                          int k, const float* mask, const cs_params* prm, int flags,
+                          cs_batch** out);
+
+/* Enqueues one run of the batch on `stream` (ordered after the stream's prior
+ * work; the outputs are complete when the stream reaches this point). The
+ * first run with CS_BATCH_AUTOTUNE synchronises. Not reentrant: runs of one
+ * batch must be ordered on one stream. */
+cs_status cs_batch_run(cs_batch* b, void* stream);
+
+/* The configuration in use: streams, order (0 = by decreasing cost,
+ * 1 = given), total pixel x sample pairs per run, and the tuned run time in
+ * milliseconds (-1 when not tuned). Any output pointer may be NULL. */
+cs_status cs_batch_config(const cs_batch* b, int32_t* n_streams, int32_t* order, double* pairs,
+                          double* tuned_ms);
+
+/* Frees the batch (waits for its streams first). NULL is a no-op. */
+void cs_batch_destroy(cs_batch* b);
+
+/* One-shot batch: create (no flags), run on `stream`, destroy. The batch
+ * memory is freed only after the run completes (the call synchronises the
+ * stream). */
+cs_status cs_batch_data_term(cs_ctx* ctx, const cs_image* images, int n_images,
+                             const float* omega, int k, const float* mask, const cs_params* prm,
+                             void* stream);
+
+/*
  * Learned surrogate of the data term (not in the paper: an approximation of
  * the Sec. 3.1 likelihood that the exact sum judges and backs up).
  *

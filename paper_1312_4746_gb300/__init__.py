@@ -42,6 +42,11 @@ EXPORTS = (
     "cs_cosupport",
     "cs_likelihood",
     "cs_data_term",
+    "cs_batch_create",
+    "cs_batch_run",
+    "cs_batch_config",
+    "cs_batch_destroy",
+    "cs_batch_data_term",
     "cs_surrogate_fit",
     "cs_surrogate_eval",
     "cs_surrogate_params",
@@ -99,6 +104,27 @@ class Params(ctypes.Structure):
         return p
 
 
+class Image(ctypes.Structure):
+    """Mirror of cs_image (include/cosparse.h)."""
+
+    _fields_ = [
+        ("img", ctypes.c_void_p),
+        ("H", ctypes.c_int32),
+        ("W", ctypes.c_int32),
+        ("n_labels", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("label_off", ctypes.c_void_p),
+        ("sample_pix", ctypes.c_void_p),
+        ("bitmask", ctypes.c_void_p),
+        ("dist2", ctypes.c_void_p),
+        ("neglog", ctypes.c_void_p),
+        ("post", ctypes.c_void_p),
+    ]
+
+
+BATCH_GRAPH = 1
+BATCH_AUTOTUNE = 2
+
 _lib = None
 
 
@@ -129,6 +155,15 @@ def lib(path: str | None = None):
     L.cs_codes_noalloc.restype = I
     L.cs_likelihood.argtypes = [V, V, I, I, V, I, I, V, V, ctypes.POINTER(Params), V, V, V, V]
     L.cs_data_term.argtypes = [V, V, I, I, V, I, V, I, V, V, ctypes.POINTER(Params), V, V, V, V, V]
+    L.cs_batch_create.argtypes = [V, ctypes.POINTER(Image), I, V, I, V, ctypes.POINTER(Params), I,
+                                  ctypes.POINTER(V)]
+    L.cs_batch_run.argtypes = [V, V]
+    L.cs_batch_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(D), ctypes.POINTER(D)]
+    L.cs_batch_destroy.argtypes = [V]
+    L.cs_batch_destroy.restype = None
+    L.cs_batch_data_term.argtypes = [V, ctypes.POINTER(Image), I, V, I, V, ctypes.POINTER(Params),
+                                     V]
     U64 = ctypes.c_uint64
     L.cs_surrogate_fit.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, I, U64, V]
     L.cs_surrogate_eval.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, V, V,
@@ -144,7 +179,8 @@ def lib(path: str | None = None):
     for f in ("cs_create", "cs_sync_status", "cs_codes", "cs_cosupport", "cs_likelihood",
               "cs_data_term", "cs_profile_enable", "cs_profile_read", "cs_surrogate_fit",
               "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_mlp_forward",
-              "cs_mlp_grad"):
+              "cs_mlp_grad", "cs_batch_create", "cs_batch_run", "cs_batch_config",
+              "cs_batch_data_term"):
         getattr(L, f).restype = I
     if path is None:
         _lib = L
@@ -288,6 +324,23 @@ class Context:
             _ptr(out.get("post")), _stream()))
         return out
 
+    # ------------------------------------------------------------------ batches
+
+    def batch(self, images, omega, mask, params: Params, flags=0, want_post=True,
+              want_bitmask=False, want_dist2=False):
+        """cs_batch_create over ``images``: a list of dicts with device tensors
+        'img' (H, W, 3) and 'sample_pix', and host 'label_off'. Outputs are
+        allocated here (torch) and returned with the batch."""
+        return Batch(self, images, omega, mask, params, flags, want_post, want_bitmask, want_dist2)
+
+    def batch_data_term(self, images, omega, mask, params: Params, want_post=True):
+        """cs_batch_data_term (one-shot; synchronises the current stream)."""
+        arr, outs, keep = _batch_descs(images, int(omega.shape[0]), want_post, False, False)
+        self.check(self._lib.cs_batch_data_term(
+            self.handle, arr, len(images), _ptr(omega), int(omega.shape[0]), _ptr(mask),
+            ctypes.byref(params), _stream()))
+        return outs
+
 
     # ------------------------------------------------------------------ surrogate
 
@@ -367,6 +420,71 @@ class Context:
         self.check(self._lib.cs_mlp_grad(self.handle, _ptr(params_dev), n_out, _ptr(X), _ptr(T),
                                          int(X.shape[0]), _ptr(g), _ptr(loss), _stream()))
         return g, loss
+
+
+def _batch_descs(images, k, want_post, want_bitmask, want_dist2):
+    import numpy as np
+    import torch
+
+    n = len(images)
+    arr = (Image * n)()
+    outs, keep = [], []
+    for i, d in enumerate(images):
+        img = d["img"]
+        H, W = int(img.shape[0]), int(img.shape[1])
+        off = np.ascontiguousarray(np.asarray(d["label_off"], dtype=np.int32))
+        nl = len(off) - 1
+        dev = img.device
+        o = {"neglog": torch.empty((nl, H, W), dtype=torch.float32, device=dev),
+             "post": torch.empty((nl, H, W), dtype=torch.float32, device=dev) if want_post else None,
+             "dist2": torch.empty((nl, H, W), dtype=torch.int32, device=dev) if want_dist2 else None,
+             "bitmask": (torch.empty((H * W, (k + 31) // 32), dtype=torch.int32, device=dev)
+                         if want_bitmask else None)}
+        arr[i] = Image(img.data_ptr(), H, W, nl, 0, off.ctypes.data, d["sample_pix"].data_ptr(),
+                       _ptr(o["bitmask"]), _ptr(o["dist2"]), o["neglog"].data_ptr(), _ptr(o["post"]))
+        outs.append(o)
+        keep.append(off)
+    return arr, outs, keep
+
+
+class Batch:
+    """A planned batch (cs_batch): ``run()`` recomputes every image's outputs
+    from the current contents of the input tensors named at creation."""
+
+    def __init__(self, ctx: Context, images, omega, mask, params, flags, want_post, want_bitmask,
+                 want_dist2):
+        self.ctx = ctx
+        self._inputs = (images, omega, mask)  # keep the device buffers alive
+        arr, self.outputs, keep = _batch_descs(images, int(omega.shape[0]), want_post,
+                                               want_bitmask, want_dist2)
+        h = ctypes.c_void_p()
+        ctx.check(ctx._lib.cs_batch_create(
+            ctx.handle, arr, len(images), _ptr(omega), int(omega.shape[0]), _ptr(mask),
+            ctypes.byref(params), int(flags), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self):
+        self.ctx.check(self.ctx._lib.cs_batch_run(self.handle, _stream()))
+        return self.outputs
+
+    def config(self):
+        ns, om = ctypes.c_int32(), ctypes.c_int32()
+        pairs, tms = ctypes.c_double(), ctypes.c_double()
+        self.ctx.check(self.ctx._lib.cs_batch_config(self.handle, ctypes.byref(ns), ctypes.byref(om),
+                                                     ctypes.byref(pairs), ctypes.byref(tms)))
+        return {"n_streams": ns.value, "order": om.value, "pairs": pairs.value,
+                "tuned_ms": tms.value}
+
+    def close(self):
+        if self.handle:
+            self.ctx._lib.cs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> str:

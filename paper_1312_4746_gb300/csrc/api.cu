@@ -47,19 +47,6 @@ cs_status cs_ensure_scratch(cs_ctx* ctx, size_t bytes) {
     return CS_OK;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 static cudaEvent_t pool_get(cs_ctx* ctx) {
     if (!ctx->event_pool.empty()) {
         cudaEvent_t e = ctx->event_pool.back();
@@ -215,6 +202,8 @@ cs_status cs_sync_status(cs_ctx* ctx, void* stream) {
     return cs_set_error(ctx, CS_ERR_DEVICE, "device error %d (detail %d)", h[0], h[1]);
 }
 
+}  // extern "C"
+
 // ---------------------------------------------------------------- planning helpers
 
 static int guard_capacity(long long P, int k) {
@@ -223,7 +212,7 @@ static int guard_capacity(long long P, int k) {
     return (int)cap;
 }
 
-static cs_status check_image(cs_ctx* ctx, const char* fn, int H, int W, int k) {
+cs_status cs_check_image(cs_ctx* ctx, const char* fn, int H, int W, int k) {
     if (H < 1 || W < 1 || H > CS_MAX_SIDE || W > CS_MAX_SIDE)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: bad image size %dx%d", fn, W, H);
     if (k < 1 || k > CS_MAX_K)
@@ -231,7 +220,7 @@ static cs_status check_image(cs_ctx* ctx, const char* fn, int H, int W, int k) {
     return CS_OK;
 }
 
-static cs_status check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm) {
+cs_status cs_check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm) {
     if (!prm) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: params is NULL", fn);
     if (prm->p < 1 || (prm->p & 1) == 0)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: patch side %d is not odd", fn, prm->p);
@@ -242,7 +231,7 @@ static cs_status check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm) 
     return CS_OK;
 }
 
-static cs_status check_labels(cs_ctx* ctx, const char* fn, int n_labels,
+cs_status cs_check_labels(cs_ctx* ctx, const char* fn, int n_labels,
                               const int32_t* label_off) {
     if (n_labels < 1 || n_labels > CS_MAX_LABELS)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: n_labels=%d outside 1..%d", fn,
@@ -257,7 +246,7 @@ static cs_status check_labels(cs_ctx* ctx, const char* fn, int n_labels,
     return CS_OK;
 }
 
-static cs_status check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k) {
+cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k) {
     if (!prm) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: params is NULL", fn);
     if (!(prm->sigma_c2 > 0) || !(prm->alpha > 0) || !(prm->d_min > 0) || !(prm->kappa_beta > 0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG,
@@ -277,7 +266,7 @@ static cs_status check_params(cs_ctx* ctx, const char* fn, const cs_params* prm,
 }
 
 // Scratch layout of the codes stage.
-static void plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitmask) {
+void cs_plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitmask) {
     const int cap = guard_capacity(P, k);
     a.rownorm = c.take<float>(k);
     a.guard_count = c.take<int>(1);
@@ -286,7 +275,7 @@ static void plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitm
     if (own_bitmask) a.bitmask = c.take<uint32_t>(P * ((k + 31) / 32));
 }
 
-static void plan_likelihood(LikPlan& L, int H, int W, int k, int n_labels,
+void cs_lik_plan(LikPlan& L, int H, int W, int k, int n_labels,
                             const int32_t* label_off, const cs_params* prm) {
     L.H = H;
     L.W = W;
@@ -307,7 +296,7 @@ static void plan_likelihood(LikPlan& L, int H, int W, int k, int n_labels,
     L.stage_bytes = tc_copy_bytes(k, L.tex8, L.persample);
 }
 
-static void carve_likelihood(Carve& c, LikPlan& L, int32_t* dist2) {
+void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2) {
     const long long P = (long long)L.H * L.W;
     const int n = L.n_labels, S = L.S, Wk = (L.k + 31) / 32;
     L.d_off = c.take<int32_t>(2 * (n + 1));
@@ -328,6 +317,7 @@ static void carve_likelihood(Carve& c, LikPlan& L, int32_t* dist2) {
     L.t.blob = c.take<uint8_t>(L.tc_form ? (size_t)L.total_tiles * L.stage_bytes : 0, 1024);
     L.t.tile_c = c.take<int2>(L.tc_form ? (size_t)L.total_tiles : 0);
     L.t.perm = c.take<int32_t>(L.tc_form ? (size_t)S : 0);
+    L.desc = c.take<TcImage>(L.tc_form ? 1 : 0);
 }
 
 static cudaError_t enqueue_codes(cs_ctx* ctx, const CodesArgs& a, cudaStream_t st) {
@@ -346,40 +336,32 @@ static cudaError_t enqueue_distances(cs_ctx* ctx, const LikPlan& L, const int32_
     return launch_edt(ea, st);
 }
 
-static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
-                               const uint32_t* bitmask, const int32_t* sample_pix,
-                               const cs_params* prm, float* neglog, float* post,
-                               cudaStream_t st) {
-    cudaError_t e;
-    {
-        StageTimer tm(ctx, CS_STAGE_GATHER, st);
-        e = launch_gather(img, L.H, L.W, bitmask, L.k, L.n_labels, L.d_off, sample_pix, L.S,
-                          !L.persample, L.t, st);
-    }
-    if (e != cudaSuccess) return e;
-    StageTimer tm(ctx, CS_STAGE_SUM, st);
-    if (!L.tc_form) {
-        SumArgs a{};
-        a.img = img;
-        a.H = L.H;
-        a.W = L.W;
-        a.bitmask = bitmask;
-        a.k = L.k;
-        a.Wk = (L.k + 31) / 32;
-        a.n_labels = L.n_labels;
-        a.d_label_off = L.d_off;
-        a.n_samples = L.S;
-        a.t = L.t;
-        a.dist2 = L.d2;
-        a.alpha = (float)prm->alpha;
-        a.d_min = (float)prm->d_min;
-        a.kappa_beta = (float)prm->kappa_beta;
-        a.sigma_c2 = (float)prm->sigma_c2;
-        a.mode = prm->mode;
-        a.neglog = neglog;
-        a.post = post;
-        return launch_sum_plain(a, st);
-    }
+SumArgs cs_sum_args(const LikPlan& L, const float* img, const uint32_t* bitmask,
+                    const cs_params* prm, float* neglog, float* post) {
+    SumArgs a{};
+    a.img = img;
+    a.H = L.H;
+    a.W = L.W;
+    a.bitmask = bitmask;
+    a.k = L.k;
+    a.Wk = (L.k + 31) / 32;
+    a.n_labels = L.n_labels;
+    a.d_label_off = L.d_off;
+    a.n_samples = L.S;
+    a.t = L.t;
+    a.dist2 = L.d2;
+    a.alpha = (float)prm->alpha;
+    a.d_min = (float)prm->d_min;
+    a.kappa_beta = (float)prm->kappa_beta;
+    a.sigma_c2 = (float)prm->sigma_c2;
+    a.mode = prm->mode;
+    a.neglog = neglog;
+    a.post = post;
+    return a;
+}
+
+TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uint32_t* bitmask,
+                      const cs_params* prm, float* neglog, float* post) {
     TcLaunch T{};
     T.img = img;
     T.H = L.H;
@@ -405,8 +387,28 @@ static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
     T.n_sm = ctx->n_sm;
     T.tex8 = L.tex8;
     T.persample = L.persample;
-    return launch_sum_tc(T, st);
+    T.desc = L.desc;
+    T.first_item = 0;
+    return T;
 }
+
+static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
+                               const uint32_t* bitmask, const int32_t* sample_pix,
+                               const cs_params* prm, float* neglog, float* post,
+                               cudaStream_t st) {
+    cudaError_t e;
+    {
+        StageTimer tm(ctx, CS_STAGE_GATHER, st);
+        e = launch_gather(img, L.H, L.W, bitmask, L.k, L.n_labels, L.d_off, sample_pix, L.S,
+                          !L.persample, L.t, st);
+    }
+    if (e != cudaSuccess) return e;
+    StageTimer tm(ctx, CS_STAGE_SUM, st);
+    if (!L.tc_form) return launch_sum_plain(cs_sum_args(L, img, bitmask, prm, neglog, post), st);
+    return launch_sum_tc(cs_tc_launch(ctx, L, img, bitmask, prm, neglog, post), st);
+}
+
+extern "C" {
 
 // ---------------------------------------------------------------- entry points
 
@@ -419,17 +421,17 @@ cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* ome
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null input pointer", fn);
     if (!codes && !lead16 && !bitmask)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: no output requested", fn);
-    cs_status s = check_image(ctx, fn, H, W, k);
-    if (!s) s = check_patch(ctx, fn, prm);
+    cs_status s = cs_check_image(ctx, fn, H, W, k);
+    if (!s) s = cs_check_patch(ctx, fn, prm);
     if (s) return s;
     DeviceGuard g(ctx->device);
     const long long P = (long long)H * W;
     CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, codes, lead16, bitmask};
     Carve m(nullptr);
-    plan_codes(m, a, P, k, !bitmask);
+    cs_plan_codes(m, a, P, k, !bitmask);
     if ((s = cs_ensure_scratch(ctx, m.off))) return s;
     Carve c(ctx->scratch);
-    plan_codes(c, a, P, k, !bitmask);
+    cs_plan_codes(c, a, P, k, !bitmask);
     a.d_err = ctx->d_err;
     cudaError_t e = enqueue_codes(ctx, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
@@ -458,9 +460,9 @@ cs_status cs_cosupport(cs_ctx* ctx, const float* codes, int P, int k, double tau
 
 cs_status cs_check_likelihood_args(cs_ctx* ctx, const char* fn, int H, int W, int k,
                                    int n_labels, const int32_t* label_off, const cs_params* prm) {
-    cs_status s = check_image(ctx, fn, H, W, k);
-    if (!s) s = check_labels(ctx, fn, n_labels, label_off);
-    if (!s) s = check_params(ctx, fn, prm, k);
+    cs_status s = cs_check_image(ctx, fn, H, W, k);
+    if (!s) s = cs_check_labels(ctx, fn, n_labels, label_off);
+    if (!s) s = cs_check_params(ctx, fn, prm, k);
     return s;
 }
 
@@ -469,14 +471,14 @@ cs_status cs_check_likelihood_args(cs_ctx* ctx, const char* fn, int H, int W, in
 cs_status cs_plan_likelihood(cs_ctx* ctx, LikPlan& L, int H, int W, int k, int n_labels,
                              const int32_t* label_off, const cs_params* prm, int32_t* dist2,
                              size_t extra, size_t* off_extra) {
-    plan_likelihood(L, H, W, k, n_labels, label_off, prm);
+    cs_lik_plan(L, H, W, k, n_labels, label_off, prm);
     Carve m(nullptr);
-    carve_likelihood(m, L, dist2);
+    cs_lik_carve(m, L, dist2);
     const size_t base = (m.off + 255) / 256 * 256;
     cs_status s = cs_ensure_scratch(ctx, base + extra);
     if (s) return s;
     Carve c(ctx->scratch);
-    carve_likelihood(c, L, dist2);
+    cs_lik_carve(c, L, dist2);
     *off_extra = base;
     return CS_OK;
 }
@@ -499,25 +501,7 @@ cudaError_t cs_enqueue_exact_list_prepared(cs_ctx* ctx, const LikPlan& L, const 
                                            const int32_t* list, const int* count, int cap,
                                            float* T_out, float* neglog, float* post,
                                            cudaStream_t st) {
-    SumArgs a{};
-    a.img = img;
-    a.H = L.H;
-    a.W = L.W;
-    a.bitmask = bitmask;
-    a.k = L.k;
-    a.Wk = (L.k + 31) / 32;
-    a.n_labels = L.n_labels;
-    a.d_label_off = L.d_off;
-    a.n_samples = L.S;
-    a.t = L.t;
-    a.dist2 = L.d2;
-    a.alpha = (float)prm->alpha;
-    a.d_min = (float)prm->d_min;
-    a.kappa_beta = (float)prm->kappa_beta;
-    a.sigma_c2 = (float)prm->sigma_c2;
-    a.mode = prm->mode;
-    a.neglog = neglog;
-    a.post = post;
+    SumArgs a = cs_sum_args(L, img, bitmask, prm, neglog, post);
     a.pix_list = list;
     a.list_count = count;
     a.list_cap = cap;
@@ -547,19 +531,19 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
     if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
     if (!img || !bitmask || !sample_pix || !neglog)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
-    cs_status s = check_image(ctx, fn, H, W, k);
-    if (!s) s = check_labels(ctx, fn, n_labels, label_off);
-    if (!s) s = check_params(ctx, fn, prm, k);
+    cs_status s = cs_check_image(ctx, fn, H, W, k);
+    if (!s) s = cs_check_labels(ctx, fn, n_labels, label_off);
+    if (!s) s = cs_check_params(ctx, fn, prm, k);
     if (s) return s;
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     LikPlan L{};
-    plan_likelihood(L, H, W, k, n_labels, label_off, prm);
+    cs_lik_plan(L, H, W, k, n_labels, label_off, prm);
     Carve m(nullptr);
-    carve_likelihood(m, L, dist2);
+    cs_lik_carve(m, L, dist2);
     if ((s = cs_ensure_scratch(ctx, m.off))) return s;
     Carve c(ctx->scratch);
-    carve_likelihood(c, L, dist2);
+    cs_lik_carve(c, L, dist2);
     cudaError_t e = enqueue_distances(ctx, L, sample_pix, st);
     if (e == cudaSuccess) e = enqueue_sum(ctx, L, img, bitmask, sample_pix, prm, neglog, post, st);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
@@ -574,24 +558,24 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
     if (!img || !omega || !mask || !sample_pix || !neglog)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
-    cs_status s = check_image(ctx, fn, H, W, k);
-    if (!s) s = check_patch(ctx, fn, prm);
-    if (!s) s = check_labels(ctx, fn, n_labels, label_off);
-    if (!s) s = check_params(ctx, fn, prm, k);
+    cs_status s = cs_check_image(ctx, fn, H, W, k);
+    if (!s) s = cs_check_patch(ctx, fn, prm);
+    if (!s) s = cs_check_labels(ctx, fn, n_labels, label_off);
+    if (!s) s = cs_check_params(ctx, fn, prm, k);
     if (s) return s;
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const long long P = (long long)H * W;
     CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, nullptr, nullptr, bitmask};
     LikPlan L{};
-    plan_likelihood(L, H, W, k, n_labels, label_off, prm);
+    cs_lik_plan(L, H, W, k, n_labels, label_off, prm);
     Carve m(nullptr);
-    plan_codes(m, a, P, k, !bitmask);
-    carve_likelihood(m, L, dist2);
+    cs_plan_codes(m, a, P, k, !bitmask);
+    cs_lik_carve(m, L, dist2);
     if ((s = cs_ensure_scratch(ctx, m.off))) return s;
     Carve c(ctx->scratch);
-    plan_codes(c, a, P, k, !bitmask);
-    carve_likelihood(c, L, dist2);
+    cs_plan_codes(c, a, P, k, !bitmask);
+    cs_lik_carve(c, L, dist2);
     a.d_err = ctx->d_err;
     // fork: the distance transform depends only on the scribbles and runs on
     // the context's side stream while the codes run on the caller's stream

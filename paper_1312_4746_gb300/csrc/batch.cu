@@ -1,0 +1,413 @@
+// Batches of images: per-image preparation on several streams, one
+// persistent tensor-core sum launch over all images' pixel tiles, optional
+// CUDA-graph capture of the whole run and a small autotuner over the launch
+// configuration (number of streams, processing order).
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int MAX_STREAMS = 8;
+constexpr int MAX_IMAGES = 4096;
+
+struct BatchImage {
+    cs_image d;
+    std::vector<int32_t> off;  // host copy of label_off
+    CodesArgs codes;
+    LikPlan L;
+    double pairs;
+};
+
+// Tuned configurations, shared by all contexts of the process and keyed by
+// the batch's shape signature (device name included).
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, int>> g_tuned;
+bool g_tune_file_loaded = false;
+
+const char* tune_file() {
+    const char* f = std::getenv("CS_TUNE_CACHE");
+    return (f && *f) ? f : nullptr;
+}
+
+void load_tune_file() {
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char* f = tune_file();
+    if (!f) return;
+    std::ifstream in(f);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        std::string sig;
+        int s = 0, o = 0;
+        if (ls >> sig >> s >> o && s >= 1 && s <= MAX_STREAMS && (o == 0 || o == 1))
+            g_tuned[sig] = {s, o};
+    }
+}
+
+void store_tune(const std::string& sig, int s, int o, double ms) {
+    g_tuned[sig] = {s, o};
+    const char* f = tune_file();
+    if (!f) return;
+    std::ofstream out(f, std::ios::app);
+    out << sig << " " << s << " " << o << " " << ms << "\n";
+}
+
+}  // namespace
+
+struct cs_batch {
+    cs_ctx* ctx = nullptr;
+    std::vector<BatchImage> im;
+    const float* omega = nullptr;
+    const float* mask = nullptr;
+    int k = 0;
+    cs_params prm{};
+    int flags = 0;
+    bool tc = false;
+    char* mem = nullptr;
+    TcImage* descs = nullptr;
+    int n_streams = 4, order_mode = 0;
+    std::vector<int> order;       // image index at each processing position
+    std::vector<int> first_item;  // first work item at each processing position
+    int n_items = 0;
+    double pairs = 0, tuned_ms = -1;
+    bool tuned = false, ran = false;
+    std::string sig;
+    cudaStream_t streams[MAX_STREAMS] = {};
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[MAX_STREAMS] = {};
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void set_order(cs_batch* b, int n_streams, int order_mode) {
+    const int n = (int)b->im.size();
+    b->n_streams = n_streams;
+    b->order_mode = order_mode;
+    b->order.resize(n);
+    for (int i = 0; i < n; ++i) b->order[i] = i;
+    if (order_mode == 0)
+        std::stable_sort(b->order.begin(), b->order.end(),
+                         [&](int x, int y) { return b->im[x].pairs > b->im[y].pairs; });
+    b->first_item.resize(n);
+    int items = 0;
+    for (int s = 0; s < n; ++s) {
+        b->first_item[s] = items;
+        const BatchImage& m = b->im[b->order[s]];
+        items += tc_pixel_tiles(m.L.H, m.L.W);
+    }
+    b->n_items = items;
+}
+
+// Enqueues one run on `st`: fork to the batch streams, per-image work, join,
+// then the multi-image sum. No allocation, no host synchronisation.
+static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
+    cs_ctx* ctx = b->ctx;
+    const int S = b->n_streams;
+    cudaError_t e = cudaEventRecord(b->ev_fork, st);
+    for (int j = 0; e == cudaSuccess && j < S; ++j) e = cudaStreamWaitEvent(b->streams[j], b->ev_fork, 0);
+    for (int s = 0; e == cudaSuccess && s < (int)b->order.size(); ++s) {
+        BatchImage& m = b->im[b->order[s]];
+        cudaStream_t ss = b->streams[s % S];
+        const LikPlan& L = m.L;
+        e = launch_set_offsets(L.offs, 2 * (L.n_labels + 1), L.d_off, ss);
+        if (e == cudaSuccess) {
+            EdtArgs ea{L.H, L.W, L.n_labels, L.d_off, m.d.sample_pix, L.S, L.seedbits, L.colbuf,
+                       L.vbuf, L.fbuf, L.d2, ctx->d_err};
+            e = launch_edt(ea, ss);
+        }
+        if (e == cudaSuccess) e = launch_codes_f32(m.codes, ss);
+        if (e == cudaSuccess)
+            e = launch_gather(m.d.img, L.H, L.W, m.codes.bitmask, L.k, L.n_labels, L.d_off,
+                              m.d.sample_pix, L.S, !L.persample, L.t, ss);
+        if (e != cudaSuccess) break;
+        if (b->tc) {
+            TcLaunch T = cs_tc_launch(ctx, L, m.d.img, m.codes.bitmask, &b->prm, m.d.neglog,
+                                      m.d.post);
+            T.desc = b->descs + s;
+            T.first_item = b->first_item[s];
+            e = launch_tc_prepare(T, ss);
+        } else {
+            e = launch_sum_plain(cs_sum_args(L, m.d.img, m.codes.bitmask, &b->prm, m.d.neglog,
+                                             m.d.post), ss);
+        }
+    }
+    for (int j = 0; j < S; ++j) {
+        // always join every forked stream, even after an error
+        cudaError_t e2 = cudaEventRecord(b->ev_join[j], b->streams[j]);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, b->ev_join[j], 0);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && b->tc) {
+        TcSumParams p{b->k,
+                      b->prm.precision == CS_FP8,
+                      b->prm.mode == CS_MODE_PERSAMPLE,
+                      (float)b->prm.alpha,
+                      (float)b->prm.d_min,
+                      (float)b->prm.kappa_beta,
+                      (float)b->prm.sigma_c2,
+                      ctx->d_err,
+                      ctx->n_sm};
+        e = launch_tc_sum(b->descs, (int)b->order.size(), b->n_items, p, st);
+    }
+    return e;
+}
+
+static cs_status cuda_fail(cs_batch* b, const char* fn, cudaError_t e) {
+    cudaGetLastError();
+    return cs_set_error(b->ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+}
+
+static void drop_graph(cs_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+// Captures one run into a graph (on the batch's private stream).
+static cudaError_t capture(cs_batch* b) {
+    drop_graph(b);
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t er = enqueue_run(b, b->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (er != cudaSuccess) e = er;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) b->exec = nullptr;
+    return e;
+}
+
+// Times every (streams, order) candidate on `st` and keeps the fastest.
+static cudaError_t autotune(cs_batch* b, cudaStream_t st) {
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const int cand_s[] = {1, 2, 4, 8};
+    int best_s = b->n_streams, best_o = b->order_mode;
+    float best = -1.f;
+    for (int o = 0; e == cudaSuccess && o < 2; ++o)
+        for (int si = 0; e == cudaSuccess && si < 4; ++si) {
+            set_order(b, cand_s[si], o);
+            e = enqueue_run(b, st);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+            for (int r = 0; e == cudaSuccess && r < 2; ++r) e = enqueue_run(b, st);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e == cudaSuccess && (best < 0.f || ms < best)) {
+                best = ms;
+                best_s = cand_s[si];
+                best_o = o;
+            }
+        }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    set_order(b, best_s, best_o);
+    if (e == cudaSuccess) {
+        b->tuned = true;
+        b->tuned_ms = best / 2.0;
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        store_tune(b->sig, best_s, best_o, b->tuned_ms);
+    }
+    return e;
+}
+
+extern "C" {
+
+void cs_batch_destroy(cs_batch* b) {
+    if (!b) return;
+    {
+        DeviceGuard g(b->ctx->device);
+        for (int j = 0; j < MAX_STREAMS; ++j)
+            if (b->streams[j]) cudaStreamSynchronize(b->streams[j]);
+        if (b->cap) cudaStreamSynchronize(b->cap);
+        drop_graph(b);
+        for (int j = 0; j < MAX_STREAMS; ++j) {
+            if (b->streams[j]) cudaStreamDestroy(b->streams[j]);
+            if (b->ev_join[j]) cudaEventDestroy(b->ev_join[j]);
+        }
+        if (b->cap) cudaStreamDestroy(b->cap);
+        if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+        if (b->mem) cudaFree(b->mem);
+    }
+    delete b;
+}
+
+cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, const float* omega,
+                          int k, const float* mask, const cs_params* prm, int flags,
+                          cs_batch** out) {
+    const char* fn = "cs_batch_create";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!out) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: out is NULL", fn);
+    *out = nullptr;
+    if (!images || !omega || !mask)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
+    if (n_images < 1 || n_images > MAX_IMAGES)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: n_images=%d outside 1..%d", fn,
+                            n_images, MAX_IMAGES);
+    if (flags & ~(CS_BATCH_GRAPH | CS_BATCH_AUTOTUNE))
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown flags 0x%x", fn, flags);
+    cs_status s = cs_check_patch(ctx, fn, prm);
+    if (s) return s;
+    char where[64];
+    for (int i = 0; i < n_images; ++i) {
+        const cs_image& d = images[i];
+        snprintf(where, sizeof(where), "%s: image %d", fn, i);
+        if (!d.img || !d.sample_pix || !d.neglog)
+            return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", where);
+        if (d.reserved != 0)
+            return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: reserved field must be 0", where);
+        if ((s = cs_check_image(ctx, where, d.H, d.W, k))) return s;
+        if ((s = cs_check_labels(ctx, where, d.n_labels, d.label_off))) return s;
+    }
+    if ((s = cs_check_params(ctx, fn, prm, k))) return s;
+
+    cs_batch* b = new cs_batch();
+    b->ctx = ctx;
+    b->omega = omega;
+    b->mask = mask;
+    b->k = k;
+    b->prm = *prm;
+    b->flags = flags;
+    b->tc = prm->precision != CS_FP32;
+    b->im.resize(n_images);
+    std::ostringstream sig;
+    cudaDeviceProp dp{};
+    DeviceGuard g(ctx->device);
+    cudaGetDeviceProperties(&dp, ctx->device);
+    for (char* c = dp.name; *c; ++c)
+        if (*c == ' ') *c = '_';
+    sig << dp.name << ":k" << k << "p" << prm->p << "m" << prm->mode << "f" << prm->precision
+        << ":n" << n_images;
+    for (int i = 0; i < n_images; ++i) {
+        BatchImage& m = b->im[i];
+        m.d = images[i];
+        m.off.assign(images[i].label_off, images[i].label_off + images[i].n_labels + 1);
+        m.d.label_off = m.off.data();
+        const long long P = (long long)m.d.H * m.d.W;
+        m.pairs = (double)P * m.off[m.d.n_labels];
+        b->pairs += m.pairs;
+        sig << ":" << m.d.W << "x" << m.d.H << "x" << m.d.n_labels << "x" << m.off[m.d.n_labels];
+    }
+    // the signature is hashed so that cache lines stay short
+    {
+        const std::string full = sig.str();
+        uint64_t h = 1469598103934665603ull;  // FNV-1a
+        for (unsigned char c : full) h = (h ^ c) * 1099511628211ull;
+        char buf[32];
+        snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)h);
+        b->sig = std::string(dp.name) + ":" + buf;
+    }
+    // memory: per image the codes scratch and the likelihood scratch, then the descriptors
+    auto carve_all = [&](Carve& c) {
+        for (int i = 0; i < n_images; ++i) {
+            BatchImage& m = b->im[i];
+            const long long P = (long long)m.d.H * m.d.W;
+            m.codes = CodesArgs{m.d.img, m.d.H, m.d.W, omega, k, mask, prm->p, prm->tau,
+                                nullptr, nullptr, m.d.bitmask};
+            cs_plan_codes(c, m.codes, P, k, !m.d.bitmask);
+            m.codes.d_err = ctx->d_err;
+            cs_lik_plan(m.L, m.d.H, m.d.W, k, m.d.n_labels, m.off.data(), prm);
+            cs_lik_carve(c, m.L, m.d.dist2);
+        }
+        b->descs = c.take<TcImage>(b->tc ? (size_t)n_images : 0);
+    };
+    Carve m0(nullptr);
+    carve_all(m0);
+    cudaError_t e = cudaMalloc(&b->mem, m0.off + 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->mem = nullptr;
+        cs_batch_destroy(b);
+        return cs_set_error(ctx, CS_ERR_NOMEM, "%s: cannot allocate %zu bytes", fn, m0.off);
+    }
+    Carve c(b->mem);
+    carve_all(c);
+    for (int j = 0; e == cudaSuccess && j < MAX_STREAMS; ++j) {
+        e = cudaStreamCreateWithFlags(&b->streams[j], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[j], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cs_status r = cuda_fail(b, fn, e);
+        cs_batch_destroy(b);
+        return r;
+    }
+    int ns = 4, om = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        load_tune_file();
+        auto it = g_tuned.find(b->sig);
+        if (it != g_tuned.end()) {
+            ns = it->second.first;
+            om = it->second.second;
+            b->tuned = true;  // configuration known: no tuning at the first run
+        }
+    }
+    set_order(b, ns, om);
+    *out = b;
+    return CS_OK;
+}
+
+cs_status cs_batch_run(cs_batch* b, void* stream) {
+    if (!b) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_batch_run: batch is NULL");
+    const char* fn = "cs_batch_run";
+    DeviceGuard g(b->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if ((b->flags & CS_BATCH_AUTOTUNE) && !b->tuned) {
+        e = autotune(b, st);
+        if (e != cudaSuccess) return cuda_fail(b, fn, e);
+    }
+    if (b->exec) {
+        e = cudaGraphLaunch(b->exec, st);
+    } else {
+        e = enqueue_run(b, st);
+        // the first direct run has loaded every kernel; later runs replay a graph
+        if (e == cudaSuccess && (b->flags & CS_BATCH_GRAPH)) e = capture(b);
+    }
+    if (e != cudaSuccess) return cuda_fail(b, fn, e);
+    b->ran = true;
+    return cs_check_launch(b->ctx, fn);
+}
+
+cs_status cs_batch_config(const cs_batch* b, int32_t* n_streams, int32_t* order, double* pairs,
+                          double* tuned_ms) {
+    if (!b) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_batch_config: batch is NULL");
+    if (n_streams) *n_streams = b->n_streams;
+    if (order) *order = b->order_mode;
+    if (pairs) *pairs = b->pairs;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    return CS_OK;
+}
+
+cs_status cs_batch_data_term(cs_ctx* ctx, const cs_image* images, int n_images,
+                             const float* omega, int k, const float* mask, const cs_params* prm,
+                             void* stream) {
+    cs_batch* b = nullptr;
+    cs_status s = cs_batch_create(ctx, images, n_images, omega, k, mask, prm, 0, &b);
+    if (s) return s;
+    s = cs_batch_run(b, stream);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    cs_batch_destroy(b);
+    if (s) return s;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cs_set_error(ctx, CS_ERR_CUDA, "cs_batch_data_term: %s", cudaGetErrorString(e));
+    }
+    return CS_OK;
+}
+
+}  // extern "C"

@@ -54,6 +54,20 @@ struct StageTimer {
     ~StageTimer();
 };
 
+// Makes `dev` current for the scope (restores the previous device).
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 // Bump allocator over a context's scratch buffer. First pass with base ==
 // nullptr measures the size; the second carves real pointers.
 struct Carve {
@@ -164,6 +178,8 @@ struct SumArgs {
 };
 cudaError_t launch_sum_plain(const SumArgs& a, cudaStream_t st);
 
+struct TcImage;
+
 // Likelihood-stage plan: shapes, forms and the carved scratch pointers.
 struct LikPlan {
     int H, W, k, n_labels, S, total_tiles, n_chunks;
@@ -174,6 +190,7 @@ struct LikPlan {
     uint32_t* seedbits;
     int32_t *colbuf, *vbuf, *fbuf, *d2;
     SampleTables t;
+    TcImage* desc;  // tensor-core form: descriptor slot
 };
 
 typedef LikPlan LikPlanRef;
@@ -200,6 +217,30 @@ cudaError_t cs_enqueue_exact_list(cs_ctx* ctx, const LikPlan& L, const float* im
                                   cudaStream_t st);
 
 // Tensor-core (tcgen05) pixel x sample sum.
+// One image of a sum launch; the launch reads an array of these from device
+// memory, ordered by first_item, and processes items (image, pixel tile).
+struct TcImage {
+    const float* img;
+    const uint32_t* bitmask;
+    const int32_t* dist2;
+    const int32_t* label_off;  // n_labels + 1
+    const int32_t* tile_off;   // first sample tile of each label, n_labels + 1
+    const uint8_t* blob;       // sample tiles in ring-stage layout
+    const int2* tile_c;        // sample tile anchors
+    const uint32_t* rep;       // majority co-supports (factorised form)
+    float* neglog;
+    float* post;
+    int H, W, ntx, n_labels;
+    int first_item;  // work-item index of this image's first pixel tile
+    int pad[3];
+};
+struct TcSumParams {
+    int k;
+    bool tex8, persample;
+    float alpha, d_min, kappa_beta, sigma_c2;
+    int* d_err;
+    int n_sm;
+};
 struct TcLaunch {
     const float* img;
     int H, W;
@@ -221,11 +262,34 @@ struct TcLaunch {
     int n_sm;
     bool tex8;       // texture operands in FP8 (else BF16)
     bool persample;  // per-sample texture kernel (else factorised)
+    TcImage* desc;   // device slot receiving this image's descriptor
+    int first_item;  // its first work item in the sum launch
 };
 size_t tc_copy_bytes(int k, bool tex8, bool persample);
 int tc_tiles_per_label(int m);
+int tc_pixel_tiles(int H, int W);
 bool tc_supported(int k, bool tex8);
+// Morton sort and sample tiles of one image; writes *L.desc.
+cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st);
+// One persistent launch over the items of n_images prepared images.
+cudaError_t launch_tc_sum(const TcImage* descs, int n_images, int n_items, const TcSumParams& p,
+                          cudaStream_t st);
+// Both, for a single image (L.desc must be set).
 cudaError_t launch_sum_tc(const TcLaunch& L, cudaStream_t st);
+
+// Validation and planning helpers shared by the entry points.
+cs_status cs_check_image(cs_ctx* ctx, const char* fn, int H, int W, int k);
+cs_status cs_check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm);
+cs_status cs_check_labels(cs_ctx* ctx, const char* fn, int n_labels, const int32_t* label_off);
+cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k);
+void cs_plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitmask);
+void cs_lik_plan(LikPlan& L, int H, int W, int k, int n_labels, const int32_t* label_off,
+                        const cs_params* prm);
+void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2);
+SumArgs cs_sum_args(const LikPlan& L, const float* img, const uint32_t* bitmask,
+                    const cs_params* prm, float* neglog, float* post);
+TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uint32_t* bitmask,
+                      const cs_params* prm, float* neglog, float* post);
 
 // Learned surrogate (MLP) kernels.
 int mlp_param_count(int n);

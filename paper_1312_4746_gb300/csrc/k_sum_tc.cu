@@ -49,6 +49,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 #include "tc_ptx.cuh"
@@ -72,23 +73,22 @@ constexpr float LAZY = 8.f;                  // slow path: rescale once the max 
 constexpr float SAFE = 120.f;                // fixed-reference range limit (log2)
 
 struct TcArgs {
-    const float* img;
-    int H, W;
-    const uint32_t* bitmask;
+    const TcImage* images;  // n_images descriptors, ordered by first_item
+    int n_images, n_items;  // work items: (image, pixel tile) pairs
     int k, Wk;
-    int n_labels;
-    const int32_t* d_label_off;
-    const int32_t* d_tile_off;  // first sample tile of each label, n_labels + 1
-    const uint8_t* blob;        // total_tiles x copy_bytes: texture slabs + colour slab
-    const int2* tile_c;         // anchor (first sample position) of each sample tile
-    const uint32_t* rep;        // majority co-supports (factorised form)
-    const int32_t* dist2;
     float alpha, d_min, kappa_beta, sigma_c2;
-    float* neglog;
-    float* post;
     int* d_err;
-    int ntx, n_ptiles;
 };
+
+// Image of work item g: the last descriptor whose first item is <= g.
+__device__ __forceinline__ int image_of(const TcArgs& a, int g) {
+    int lo = 0, hi = a.n_images - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.images[mid].first_item <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 template <bool TEX8, int KS, bool PERSAMPLE>
 struct Cfg {
@@ -248,7 +248,6 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::misc_off + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long P = (long long)a.H * a.W;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -278,19 +277,21 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
 
     if (warp == PRODUCER) {
         // ------------------------------------------------------------ producer
-        long long it = 0;
+        uint32_t it = 0;  // tiles issued by this CTA (< 2^32 in any launch)
         bool ok = true;
-        for (int pt = blockIdx.x; ok && pt < a.n_ptiles; pt += gridDim.x) {
-            const int ox = (pt % a.ntx) * TW, oy = (pt / a.ntx) * TH;
-            for (int i = 0; ok && i < a.n_labels; ++i) {
-                const int t0 = a.d_tile_off[i], nt = tiles_of(a.d_tile_off, i);
+        for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x) {
+            const TcImage& im = a.images[image_of(a, g)];
+            const int pt = g - im.first_item;
+            const int ox = (pt % im.ntx) * TW, oy = (pt / im.ntx) * TH;
+            for (int i = 0; ok && i < im.n_labels; ++i) {
+                const int t0 = im.tile_off[i], nt = tiles_of(im.tile_off, i);
                 for (int t = 0; ok && t < nt; ++t, ++it) {
                     const int s = (int)(it % STAGES);
                     const uint32_t ph = (uint32_t)((it / STAGES) & 1);
                     ok = wait_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1);
                     if (!ok) break;
                     uint8_t* st = ring + s * C::stage_bytes;
-                    const int2 c = a.tile_c[t0 + t];
+                    const int2 c = im.tile_c[t0 + t];
 #pragma unroll
                     for (int u = 0; u < BM / 32; ++u) {
                         const int r = u * 32 + lane;
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     __syncwarp();
                     if (lane == 0) {
                         tc::mbar_arrive_expect_tx(full + s, C::copy_bytes);
-                        tc::bulk_g2s(st, a.blob + (size_t)(t0 + t) * C::copy_bytes, C::copy_bytes,
+                        tc::bulk_g2s(st, im.blob + (size_t)(t0 + t) * C::copy_bytes, C::copy_bytes,
                                      full + s);
                     }
                 }
@@ -311,21 +312,22 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
         }
         // drain: copies still in flight must land before the CTA exits
         if (lane == 0)
-            for (long long d = (it > STAGES ? it - STAGES : 0); d < it; ++d)
+            for (uint32_t d = (it > STAGES ? it - STAGES : 0); d < it; ++d)
                 tc::mbar_wait(full + (int)(d % STAGES), (uint32_t)((d / STAGES) & 1),
                               tc::globaltimer() + WAIT_NS);
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            long long it = 0, li = 0, lpt = 0;
+            uint32_t it = 0, li = 0, lpt = 0;
             bool ok = true;
             long long last = -1;
-            for (int pt = blockIdx.x; ok && pt < a.n_ptiles; pt += gridDim.x, ++lpt) {
+            for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x, ++lpt) {
+                const TcImage& im = a.images[image_of(a, g)];
                 ok = wait_bar(atex_full, (uint32_t)(lpt & 1), abort_flag, a.d_err, 3);
-                for (int i = 0; ok && i < a.n_labels; ++i, ++li) {
+                for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
                     const int cb = (int)(li & 1);
                     ok = wait_bar(acol_full + cb, (uint32_t)((li >> 1) & 1), abort_flag, a.d_err, 4);
-                    const int nt = tiles_of(a.d_tile_off, i);
+                    const int nt = tiles_of(im.tile_off, i);
                     for (int t = 0; ok && t < nt; ++t, ++it) {
                         const int s = (int)(it % STAGES), b = (int)(it & 1);
                         ok = wait_bar(full + s, (uint32_t)((it / STAGES) & 1), abort_flag, a.d_err, 5) &&
@@ -371,16 +373,20 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
         const int rx = r % TW, ry = r / TW;
         const float Cc = LOG2E / (2.f * a.sigma_c2);
         const float log_col_norm = 1.5f * logf(6.283185307179586f * a.sigma_c2);
-        long long it = 0, li = 0, lpt = 0;
+        uint32_t it = 0, li = 0, lpt = 0;
         bool ok = true;
-        for (int pt = blockIdx.x; ok && pt < a.n_ptiles; pt += gridDim.x, ++lpt) {
-            const int x = (pt % a.ntx) * TW + rx, y = (pt / a.ntx) * TH + ry;
-            const bool live = x < a.W && y < a.H;
-            const long long pix = live ? (long long)y * a.W + x : 0;
-            const float IR = a.img[pix * 3 + 0], IG = a.img[pix * 3 + 1], IB = a.img[pix * 3 + 2];
+        for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x, ++lpt) {
+            const TcImage& im = a.images[image_of(a, g)];
+            const int pt = g - im.first_item;
+            const long long P = (long long)im.H * im.W;
+            const int x = (pt % im.ntx) * TW + rx, y = (pt / im.ntx) * TH + ry;
+            const bool live = x < im.W && y < im.H;
+            const int pix = live ? y * im.W + x : 0;  // < 2^31 (side <= 23170)
+            const float* Ip = im.img + (size_t)pix * 3;
+            const float IR = Ip[0], IG = Ip[1], IB = Ip[2];
             const float I2 = fmaf(IR, IR, fmaf(IG, IG, IB * IB));
-            const int ox = (pt % a.ntx) * TW, oy = (pt / a.ntx) * TH;
-            const uint32_t* bxp = a.bitmask + pix * a.Wk;  // this pixel's co-support words
+            const int ox = (pt % im.ntx) * TW, oy = (pt / im.ntx) * TH;
+            const uint32_t* bxp = im.bitmask + (size_t)pix * a.Wk;  // this pixel's co-support words
             int popx = 0;
             if (live)
                 for (int w = 0; w < a.Wk; ++w) popx += __popc(bxp[w]);
@@ -426,8 +432,8 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(atex_full);
 
-            for (int i = 0; ok && i < a.n_labels; ++i, ++li) {
-                const int D = live ? a.dist2[(size_t)i * P + pix] : 0;
+            for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
+                const int D = live ? im.dist2[(size_t)i * P + pix] : 0;
                 const float rho = a.alpha * fmaxf(sqrtf((float)D), a.d_min);
                 const float nA = -LOG2E / (2.f * rho * rho);
                 const float Bt = PERSAMPLE ? LOG2E / (a.kappa_beta * rho) : 1.f;
@@ -454,15 +460,15 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(acol_full + cb);
 
-                const int m_i = a.d_label_off[i + 1] - a.d_label_off[i];
+                const int m_i = im.label_off[i + 1] - im.label_off[i];
                 const float lim = SAFE - log2f((float)m_i);
-                const int nt = tiles_of(a.d_tile_off, i), t0 = a.d_tile_off[i];
+                const int nt = tiles_of(im.tile_off, i), t0 = im.tile_off[i];
                 float M = -INFINITY, S = 0.f, Ccomp = 0.f;
                 bool fixed = false;  // warp-uniform: reference maximum fixed
-                int2 c_next = a.tile_c[t0];  // anchors fetched one tile ahead
+                int2 c_next = im.tile_c[t0];  // anchors fetched one tile ahead
                 for (int t = 0; t < nt; ++t, ++it) {
                     const int2 c = c_next;
-                    if (t + 1 < nt) c_next = a.tile_c[t0 + t + 1];
+                    if (t + 1 < nt) c_next = im.tile_c[t0 + t + 1];
                     const int b = (int)(it & 1);
                     ok = wait_warp(tmem_full + b, (uint32_t)((it >> 1) & 1), abort_flag, a.d_err, 10);
                     if (!ok) break;
@@ -519,7 +525,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     const float lse2 = R0 + Mm + log2f(Sm + Cm);
                     // -L into the output plane; normalised once all labels are done
                     if (live)
-                        a.neglog[(size_t)i * P + pix] = -(lse2 * LN2 - logf((float)m_i) -
+                        im.neglog[(size_t)i * P + pix] = -(lse2 * LN2 - logf((float)m_i) -
                                                           logf(6.283185307179586f * rho * rho) -
                                                           log_col_norm);
                 }
@@ -529,35 +535,35 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             if (hf == 0 && live) {
                 if (!PERSAMPLE) {
                     float tmax = -INFINITY;
-                    for (int i = 0; i < a.n_labels; ++i) {
-                        const float rho = a.alpha * fmaxf(sqrtf((float)a.dist2[(size_t)i * P + pix]), a.d_min);
+                    for (int i = 0; i < im.n_labels; ++i) {
+                        const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
                         int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ a.rep[i * a.Wk + w]);
+                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
                         tmax = fmaxf(tmax, -LOG2E * (float)h / (a.kappa_beta * rho));
                     }
                     float ts = 0.f;
-                    for (int i = 0; i < a.n_labels; ++i) {
-                        const float rho = a.alpha * fmaxf(sqrtf((float)a.dist2[(size_t)i * P + pix]), a.d_min);
+                    for (int i = 0; i < im.n_labels; ++i) {
+                        const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
                         int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ a.rep[i * a.Wk + w]);
+                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
                         ts += ex2f(-LOG2E * (float)h / (a.kappa_beta * rho) - tmax);
                     }
                     const float tl = tmax + log2f(ts);
-                    for (int i = 0; i < a.n_labels; ++i) {
-                        const float rho = a.alpha * fmaxf(sqrtf((float)a.dist2[(size_t)i * P + pix]), a.d_min);
+                    for (int i = 0; i < im.n_labels; ++i) {
+                        const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
                         int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ a.rep[i * a.Wk + w]);
-                        a.neglog[(size_t)i * P + pix] -= (-LOG2E * (float)h / (a.kappa_beta * rho) - tl) * LN2;
+                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
+                        im.neglog[(size_t)i * P + pix] -= (-LOG2E * (float)h / (a.kappa_beta * rho) - tl) * LN2;
                     }
                 }
                 float lmax = -INFINITY;
-                for (int i = 0; i < a.n_labels; ++i) lmax = fmaxf(lmax, -a.neglog[(size_t)i * P + pix]);
+                for (int i = 0; i < im.n_labels; ++i) lmax = fmaxf(lmax, -im.neglog[(size_t)i * P + pix]);
                 float ls = 0.f;
-                for (int i = 0; i < a.n_labels; ++i) ls += expf(-a.neglog[(size_t)i * P + pix] - lmax);
+                for (int i = 0; i < im.n_labels; ++i) ls += expf(-im.neglog[(size_t)i * P + pix] - lmax);
                 const float lse = lmax + logf(ls);
-                if (a.post)
-                    for (int i = 0; i < a.n_labels; ++i)
-                        a.post[(size_t)i * P + pix] = expf(-a.neglog[(size_t)i * P + pix] - lse);
+                if (im.post)
+                    for (int i = 0; i < im.n_labels; ++i)
+                        im.post[(size_t)i * P + pix] = expf(-im.neglog[(size_t)i * P + pix] - lse);
             }
         }
     }
@@ -645,9 +651,11 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
                                    const int32_t* __restrict__ tile_off, int n_labels,
                                    int total_tiles, SampleTables t, int n_samples, int k,
                                    float Cc, const int32_t* __restrict__ perm,
-                                   uint8_t* __restrict__ blob, int2* __restrict__ tile_c) {
+                                   uint8_t* __restrict__ blob, int2* __restrict__ tile_c,
+                                   TcImage desc, TcImage* __restrict__ desc_dst) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (gid == 0) *desc_dst = desc;  // this image's descriptor for the sum launch
     if (gid >= (long long)total_tiles * BN) return;
     const int tile = (int)(gid / BN), r = (int)(gid % BN);
     int lo = 0, hi = n_labels - 1;  // label of this tile
@@ -727,60 +735,82 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
-cudaError_t run(const TcLaunch& L, cudaStream_t st) {
-    using C = Cfg<TEX8, KS, PERSAMPLE>;
-    static_assert(C::smem_bytes <= 227 * 1024, "shared memory budget");
+cudaError_t prepare(const TcLaunch& L, cudaStream_t st) {
     const int total_tiles = L.total_tiles;
     const float Cc = 1.4426950408889634f / (2.f * L.sigma_c2);
+    TcImage d{};
+    d.img = L.img;
+    d.bitmask = L.bitmask;
+    d.dist2 = L.dist2;
+    d.label_off = L.d_label_off;
+    d.tile_off = L.d_tile_off;
+    d.blob = L.blob;
+    d.tile_c = L.t.tile_c;
+    d.rep = L.t.rep;
+    d.neglog = L.neglog;
+    d.post = L.post;
+    d.H = L.H;
+    d.W = L.W;
+    d.ntx = (L.W + TW - 1) / TW;
+    d.n_labels = L.n_labels;
+    d.first_item = L.first_item;
     morton_sort_kernel<<<L.n_chunks, 1024, 0, st>>>(L.d_label_off, L.n_labels, L.t, L.t.perm);
     build_tiles_kernel<TEX8, KS, PERSAMPLE>
         <<<(unsigned)(((long long)total_tiles * BN + 127) / 128), 128, 0, st>>>(
             L.d_label_off, L.d_tile_off, L.n_labels, total_tiles, L.t, L.n_samples, L.k, Cc,
-            L.t.perm, L.blob, L.t.tile_c);
+            L.t.perm, L.blob, L.t.tile_c, d, L.desc);
+    return cudaGetLastError();
+}
+
+template <bool TEX8, int KS, bool PERSAMPLE>
+cudaError_t sum(const TcImage* descs, int n_images, int n_items, const TcSumParams& p,
+                cudaStream_t st) {
+    using C = Cfg<TEX8, KS, PERSAMPLE>;
+    static_assert(C::smem_bytes <= 227 * 1024, "shared memory budget");
     TcArgs a{};
-    a.img = L.img;
-    a.H = L.H;
-    a.W = L.W;
-    a.bitmask = L.bitmask;
-    a.k = L.k;
-    a.Wk = (L.k + 31) / 32;
-    a.n_labels = L.n_labels;
-    a.d_label_off = L.d_label_off;
-    a.d_tile_off = L.d_tile_off;
-    a.blob = L.blob;
-    a.tile_c = L.t.tile_c;
-    a.rep = L.t.rep;
-    a.dist2 = L.dist2;
-    a.alpha = L.alpha;
-    a.d_min = L.d_min;
-    a.kappa_beta = L.kappa_beta;
-    a.sigma_c2 = L.sigma_c2;
-    a.neglog = L.neglog;
-    a.post = L.post;
-    a.d_err = L.d_err;
-    a.ntx = (L.W + TW - 1) / TW;
-    a.n_ptiles = a.ntx * ((L.H + TH - 1) / TH);
+    a.images = descs;
+    a.n_images = n_images;
+    a.n_items = n_items;
+    a.k = p.k;
+    a.Wk = (p.k + 31) / 32;
+    a.alpha = p.alpha;
+    a.d_min = p.d_min;
+    a.kappa_beta = p.kappa_beta;
+    a.sigma_c2 = p.sigma_c2;
+    a.d_err = p.d_err;
     cudaError_t e = cudaFuncSetAttribute(sum_tc_kernel<TEX8, KS, PERSAMPLE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
     if (e != cudaSuccess) return e;
-    const int grid = a.n_ptiles < L.n_sm ? a.n_ptiles : L.n_sm;
+    const int grid = n_items < p.n_sm ? n_items : p.n_sm;
     sum_tc_kernel<TEX8, KS, PERSAMPLE><<<grid, THREADS, C::smem_bytes, st>>>(a);
     return cudaGetLastError();
 }
 
-template <bool TEX8, bool PERSAMPLE>
-cudaError_t run_ks(const TcLaunch& L, int ks, cudaStream_t st) {
+// Dispatch on (texture format, texture slabs, per-sample form).
+template <class F>
+cudaError_t dispatch(int k, bool tex8, bool persample, F&& f) {
+    if (!tc_supported(k, tex8)) return cudaErrorInvalidValue;
+    if (!persample) return f(std::integral_constant<bool, true>{}, std::integral_constant<int, 1>{},
+                             std::integral_constant<bool, false>{});
+    const int ks = tex8 ? (k + 31) / 32 : (k + 15) / 16;
+#define CS_TC_CASE(N)                                                                        \
+    case N:                                                                                  \
+        return tex8 ? f(std::integral_constant<bool, true>{}, std::integral_constant<int, N>{}, \
+                        std::integral_constant<bool, true>{})                                \
+                    : f(std::integral_constant<bool, false>{}, std::integral_constant<int, N>{}, \
+                        std::integral_constant<bool, true>{});
     switch (ks) {
-        case 1: return run<TEX8, 1, PERSAMPLE>(L, st);
-        case 2: return run<TEX8, 2, PERSAMPLE>(L, st);
-        case 3: return run<TEX8, 3, PERSAMPLE>(L, st);
-        case 4: return run<TEX8, 4, PERSAMPLE>(L, st);
-        case 5: return run<TEX8, 5, PERSAMPLE>(L, st);
-        case 6: return run<TEX8, 6, PERSAMPLE>(L, st);
-        case 7: return run<TEX8, 7, PERSAMPLE>(L, st);
-        case 8: return run<TEX8, 8, PERSAMPLE>(L, st);
+        CS_TC_CASE(1)
+        CS_TC_CASE(2)
+        CS_TC_CASE(3)
+        CS_TC_CASE(4)
+        CS_TC_CASE(5)
+        CS_TC_CASE(6)
+        CS_TC_CASE(7)
+        CS_TC_CASE(8)
         default: return cudaErrorInvalidValue;
     }
+#undef CS_TC_CASE
 }
 
 }  // namespace
@@ -794,9 +824,29 @@ int tc_tiles_per_label(int m) { return (m + BN - 1) / BN; }
 
 bool tc_supported(int k, bool tex8) { return tex8 ? k <= 256 : k <= 128; }
 
+int tc_pixel_tiles(int H, int W) { return ((W + TW - 1) / TW) * ((H + TH - 1) / TH); }
+
+cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st) {
+    return dispatch(L.k, L.tex8, L.persample, [&](auto t8, auto ks, auto ps) {
+        return prepare<decltype(t8)::value, decltype(ks)::value, decltype(ps)::value>(L, st);
+    });
+}
+
+cudaError_t launch_tc_sum(const TcImage* descs, int n_images, int n_items, const TcSumParams& p,
+                          cudaStream_t st) {
+    if (n_images < 1 || n_items < 1) return cudaErrorInvalidValue;
+    return dispatch(p.k, p.tex8, p.persample, [&](auto t8, auto ks, auto ps) {
+        return sum<decltype(t8)::value, decltype(ks)::value, decltype(ps)::value>(
+            descs, n_images, n_items, p, st);
+    });
+}
+
 cudaError_t launch_sum_tc(const TcLaunch& L, cudaStream_t st) {
-    if (!tc_supported(L.k, L.tex8)) return cudaErrorInvalidValue;
-    if (!L.persample) return run_ks<true, false>(L, 1, st);
-    const int ks = L.tex8 ? (L.k + 31) / 32 : (L.k + 15) / 16;
-    return L.tex8 ? run_ks<true, true>(L, ks, st) : run_ks<false, true>(L, ks, st);
+    TcLaunch one = L;
+    one.first_item = 0;
+    cudaError_t e = launch_tc_prepare(one, st);
+    if (e != cudaSuccess) return e;
+    TcSumParams p{L.k, L.tex8, L.persample, L.alpha, L.d_min, L.kappa_beta, L.sigma_c2, L.d_err,
+                  L.n_sm};
+    return launch_tc_sum(L.desc, 1, tc_pixel_tiles(L.H, L.W), p, st);
 }

@@ -58,3 +58,23 @@ def test_create_bad_device_no_gpu(L):
     h = ctypes.c_void_p()
     assert L.cs_create(ctypes.byref(h), 9999) == cs.CS_ERR_INVALID_ARG
     assert not h.value
+
+
+def test_batch_null_args_no_gpu(L):
+    p = cs.Params.default()
+    b = ctypes.c_void_p()
+    imgs = (cs.Image * 1)()
+    assert L.cs_batch_create(None, imgs, 1, None, 8, None, ctypes.byref(p), 0,
+                             ctypes.byref(b)) == cs.CS_ERR_INVALID_ARG
+    assert b"ctx" in L.cs_last_error(None)
+    assert L.cs_batch_run(None, None) == cs.CS_ERR_INVALID_ARG
+    assert L.cs_batch_config(None, None, None, None, None) == cs.CS_ERR_INVALID_ARG
+    assert L.cs_batch_data_term(None, imgs, 1, None, 8, None, ctypes.byref(p),
+                                None) == cs.CS_ERR_INVALID_ARG
+    L.cs_batch_destroy(None)  # no-op
+
+
+def test_image_struct_layout():
+    # cs_image: pointer, 4 x int32, then six pointers (64-bit ABI)
+    assert ctypes.sizeof(cs.Image) == 8 + 16 + 6 * 8
+    assert cs.Image.label_off.offset == 24
