@@ -56,13 +56,25 @@ typedef int cs_status;
 #define CS_BF16 1 /* tensor-core (tcgen05) TSM and colour dot products, FP32 accumulation */
 #define CS_FP8 2  /* as CS_BF16 with FP8 operands where they are exact */
 
+/* Forms of the operator product (codes). */
+#define CS_CODES_AUTO 0 /* tensor cores when supported (k <= 256), else FP32 */
+#define CS_CODES_FP32 1 /* CUDA-core FP32 dot products */
+#define CS_CODES_TC 2   /* tcgen05 GEMM, split-BF16 operands, FP32 accumulation */
+
 typedef struct cs_ctx cs_ctx;
 
 /*
  * Scalar parameters. Fill with cs_params_default() and override fields.
  *   p          patch side, odd, 3..9 (n = p*p window elements; Sec. 5 uses 9)
  *   mode       CS_MODE_PERSAMPLE or CS_MODE_FACTORISED
- *   precision  CS_FP32, CS_BF16 or CS_FP8
+ *   precision  CS_FP32, CS_BF16 or CS_FP8 (the pixel x sample sum)
+ *   codes_form the operator product (Sec. 2, a = O s): CS_CODES_AUTO (the
+ *              tensor-core form when k <= 256, else FP32), CS_CODES_FP32
+ *              (CUDA cores) or CS_CODES_TC (tcgen05 GEMM over three-piece
+ *              BF16 splits of O and s, FP32 accumulation). Co-support
+ *              bitmasks are bit-exact in every form (guard band + canonical
+ *              FP64); the codes returned by cs_codes are within a few 1e-6
+ *              |O_j| of the exact values in either form.
  *   tau        co-support threshold: j is in Co(a) iff |a_j| <= tau, the
  *              practical "close to zero" of Sec. 2 (default 0.1)
  *   sigma_c2   variance of the Gaussian colour kernel per channel (Sec. 3.1: 1.3)
@@ -74,7 +86,7 @@ typedef struct {
     int32_t p;
     int32_t mode;
     int32_t precision;
-    int32_t reserved;
+    int32_t codes_form;
     double tau;
     double sigma_c2;
     double alpha;
@@ -149,7 +161,10 @@ cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* ome
  * the call and set to a nonzero code (and a count) if more entries needed the
  * exact double-precision recheck than the scratch holds (the bitmask is then
  * not guaranteed exact). Limits: H * W <= 2^20 pixels, k <= 1024; larger
- * requests return CS_ERR_INVALID_ARG before anything is launched.
+ * requests return CS_ERR_INVALID_ARG before anything is launched. It always
+ * computes the FP32 CUDA-core form of the codes (the codes cs_codes returns
+ * with codes_form = CS_CODES_FP32); codes_form = CS_CODES_TC returns
+ * CS_ERR_UNSUPPORTED.
  *
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -28,6 +28,9 @@ MODE_FACTORISED = 1
 FP32 = 0
 BF16 = 1
 FP8 = 2
+CODES_AUTO = 0
+CODES_FP32 = 1
+CODES_TC = 2
 
 # every symbol include/cosparse.h declares
 EXPORTS = (
@@ -78,7 +81,7 @@ class Params(ctypes.Structure):
         ("p", ctypes.c_int32),
         ("mode", ctypes.c_int32),
         ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("codes_form", ctypes.c_int32),
         ("tau", ctypes.c_double),
         ("sigma_c2", ctypes.c_double),
         ("alpha", ctypes.c_double),

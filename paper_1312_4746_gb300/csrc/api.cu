@@ -228,6 +228,22 @@ cs_status cs_check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm) {
         return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "%s: patch side %d not in 3..9", fn, prm->p);
     if (!(prm->tau >= 0.0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: tau must be >= 0", fn);
+    if (prm->codes_form != CS_CODES_AUTO && prm->codes_form != CS_CODES_FP32 &&
+        prm->codes_form != CS_CODES_TC)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown codes_form %d", fn,
+                            prm->codes_form);
+    return CS_OK;
+}
+
+bool cs_codes_use_tc(const cs_params* prm, int k) {
+    if (prm->codes_form == CS_CODES_FP32) return false;
+    return codes_tc_supported(k, prm->p);
+}
+
+cs_status cs_check_codes_form(cs_ctx* ctx, const char* fn, const cs_params* prm, int k) {
+    if (prm->codes_form == CS_CODES_TC && !codes_tc_supported(k, prm->p))
+        return cs_set_error(ctx, CS_ERR_UNSUPPORTED,
+                            "%s: the tensor-core codes form supports k <= 256 (k=%d)", fn, k);
     return CS_OK;
 }
 
@@ -273,6 +289,7 @@ void cs_plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitmask)
     a.guard = c.take<int2>(cap);
     a.guard_cap = cap;
     if (own_bitmask) a.bitmask = c.take<uint32_t>(P * ((k + 31) / 32));
+    a.omega_blob = a.tc ? c.take<uint8_t>(codes_tc_blob_bytes(k, a.p), 1024) : nullptr;
 }
 
 void cs_lik_plan(LikPlan& L, int H, int W, int k, int n_labels,
@@ -322,7 +339,7 @@ void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2) {
 
 static cudaError_t enqueue_codes(cs_ctx* ctx, const CodesArgs& a, cudaStream_t st) {
     StageTimer tm(ctx, CS_STAGE_CODES, st);
-    return launch_codes_f32(a, st);
+    return launch_codes(a, st);
 }
 
 // Distance transform (on `side` when given, else on `st`), then gather and sum on `st`.
@@ -423,10 +440,12 @@ cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* ome
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: no output requested", fn);
     cs_status s = cs_check_image(ctx, fn, H, W, k);
     if (!s) s = cs_check_patch(ctx, fn, prm);
+    if (!s) s = cs_check_codes_form(ctx, fn, prm, k);
     if (s) return s;
     DeviceGuard g(ctx->device);
     const long long P = (long long)H * W;
     CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, codes, lead16, bitmask};
+    a.tc = cs_codes_use_tc(prm, k);
     Carve m(nullptr);
     cs_plan_codes(m, a, P, k, !bitmask);
     if ((s = cs_ensure_scratch(ctx, m.off))) return s;
@@ -560,6 +579,7 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
     cs_status s = cs_check_image(ctx, fn, H, W, k);
     if (!s) s = cs_check_patch(ctx, fn, prm);
+    if (!s) s = cs_check_codes_form(ctx, fn, prm, k);
     if (!s) s = cs_check_labels(ctx, fn, n_labels, label_off);
     if (!s) s = cs_check_params(ctx, fn, prm, k);
     if (s) return s;
@@ -567,6 +587,7 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     cudaStream_t st = (cudaStream_t)stream;
     const long long P = (long long)H * W;
     CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, nullptr, nullptr, bitmask};
+    a.tc = cs_codes_use_tc(prm, k);
     LikPlan L{};
     cs_lik_plan(L, H, W, k, n_labels, label_off, prm);
     Carve m(nullptr);

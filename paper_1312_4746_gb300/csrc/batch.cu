@@ -125,7 +125,7 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
                        L.vbuf, L.fbuf, L.d2, ctx->d_err};
             e = launch_edt(ea, ss);
         }
-        if (e == cudaSuccess) e = launch_codes_f32(m.codes, ss);
+        if (e == cudaSuccess) e = launch_codes(m.codes, ss);
         if (e == cudaSuccess)
             e = launch_gather(m.d.img, L.H, L.W, m.codes.bitmask, L.k, L.n_labels, L.d_off,
                               m.d.sample_pix, L.S, !L.persample, L.t, ss);
@@ -259,6 +259,7 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
     if (flags & ~(CS_BATCH_GRAPH | CS_BATCH_AUTOTUNE))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown flags 0x%x", fn, flags);
     cs_status s = cs_check_patch(ctx, fn, prm);
+    if (!s) s = cs_check_codes_form(ctx, fn, prm, k);
     if (s) return s;
     char where[64];
     for (int i = 0; i < n_images; ++i) {
@@ -316,6 +317,7 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
             const long long P = (long long)m.d.H * m.d.W;
             m.codes = CodesArgs{m.d.img, m.d.H, m.d.W, omega, k, mask, prm->p, prm->tau,
                                 nullptr, nullptr, m.d.bitmask};
+            m.codes.tc = cs_codes_use_tc(prm, k);
             cs_plan_codes(c, m.codes, P, k, !m.d.bitmask);
             m.codes.d_err = ctx->d_err;
             cs_lik_plan(m.L, m.d.H, m.d.W, k, m.d.n_labels, m.off.data(), prm);

@@ -108,8 +108,15 @@ struct CodesArgs {
     int guard_cap;
     int* guard_count;   // 1 int
     int* d_err;
+    // tensor-core form: operator hi/lo parts in the B-operand layout
+    bool tc = false;
+    uint8_t* omega_blob = nullptr;
 };
-cudaError_t launch_codes_f32(const CodesArgs& a, cudaStream_t st);
+// FP32 CUDA-core codes, or (a.tc) the tcgen05 split-BF16 GEMM; both followed
+// by the canonical FP64 recompute of guarded entries.
+cudaError_t launch_codes(const CodesArgs& a, cudaStream_t st);
+bool codes_tc_supported(int k, int p);
+size_t codes_tc_blob_bytes(int k, int p);
 cudaError_t launch_cosupport(const float* codes, long long P, int k, double tau, uint32_t* bitmask,
                              cudaStream_t st);
 
@@ -283,6 +290,8 @@ cs_status cs_check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm);
 cs_status cs_check_labels(cs_ctx* ctx, const char* fn, int n_labels, const int32_t* label_off);
 cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k);
 void cs_plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitmask);
+bool cs_codes_use_tc(const cs_params* prm, int k);
+cs_status cs_check_codes_form(cs_ctx* ctx, const char* fn, const cs_params* prm, int k);
 void cs_lik_plan(LikPlan& L, int H, int W, int k, int n_labels, const int32_t* label_off,
                         const cs_params* prm);
 void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2);

@@ -21,9 +21,12 @@
 //   a_j = sum_t O_jt s_t:   |da_j| <= ||O_j||_2 (||ds|| + n u (1 + ||ds||))
 // The bound is multiplied by 1.25 and widened by tau's FP32 rounding. A
 // patch with ||c|| <= 4||dc|| (nearly flat) is recomputed whole.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -164,76 +167,369 @@ __global__ void __launch_bounds__(TILE* TILE)
         for (int j = k; j < 16; ++j) lead16[(size_t)pix * 16 + j] = 0.f;
 }
 
-// Canonical double-precision recomputation of guarded entries, one warp per
-// entry: the patch and code follow the exact operation order of the
+// Canonical double-precision recomputation of guarded entries, one thread
+// per entry: the patch and code follow the exact operation order of the
 // definition (gray, mask product, index-order sums, division by the square
-// root), with every operation correctly rounded and no contraction. The
-// element-wise steps run across the lanes; every sum runs on lane 0 in index
-// order, so the result is bit-identical to a sequential evaluation.
-__global__ void codes_guard_kernel(const float* __restrict__ img, int H, int W,
-                                   const float* __restrict__ omega, int k,
-                                   const float* __restrict__ mask, int p, double tau,
-                                   const int2* __restrict__ guard, int guard_cap,
-                                   const int* __restrict__ guard_count,
-                                   uint32_t* __restrict__ bitmask, int* __restrict__ d_err) {
-    __shared__ double s_s[4][81];
-    __shared__ double s_ab[4];
+// root), with every operation correctly rounded and no contraction, so the
+// result is bit-identical to a sequential evaluation. An entry (pixel, j)
+// recomputes code j; (pixel, -1) recomputes every code of a nearly flat
+// patch. Guarded bits were left clear by the codes kernel and are set here.
+__device__ __forceinline__ double canon_v(const float* __restrict__ img, int H, int W,
+                                          const float* __restrict__ mask, int p, int y, int x,
+                                          int t) {
+    const int r = (p - 1) / 2, dy = t / p, dx = t % p;
+    const int yy = min(max(y + dy - r, 0), H - 1), xx = min(max(x + dx - r, 0), W - 1);
+    const float* px = img + ((size_t)yy * W + xx) * 3;
+    const double gr = __dadd_rn(__dadd_rn(__dmul_rn(0.299, (double)px[0]),
+                                          __dmul_rn(0.587, (double)px[1])),
+                                __dmul_rn(0.114, (double)px[2]));
+    return __dmul_rn((double)mask[t], gr);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) codes_guard_kernel(
+    const float* __restrict__ img, int H, int W, const float* __restrict__ omega, int k,
+    const float* __restrict__ mask, double tau, const int2* __restrict__ guard, int guard_cap,
+    const int* __restrict__ guard_count, uint32_t* __restrict__ bitmask, int* __restrict__ d_err) {
+    constexpr int N = P * P;
     int cnt = *guard_count;
     if (cnt > guard_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && atomicCAS(d_err, 0, CS_DEVERR_GUARD_FULL) == 0)
             d_err[1] = cnt;
         cnt = guard_cap;
     }
-    const int n = p * p, r = (p - 1) / 2, Wk = (k + 31) >> 5;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double* s = s_s[wib];
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int e = blockIdx.x * (blockDim.x >> 5) + wib; e < cnt; e += warps) {
+    const int Wk = (k + 31) >> 5;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
         const int2 g = guard[e];
         const int y = g.x / W, x = g.x % W;
-        for (int t = lane; t < n; t += 32) {
-            const int dy = t / p, dx = t % p;
-            const int yy = min(max(y + dy - r, 0), H - 1), xx = min(max(x + dx - r, 0), W - 1);
-            const float* px = img + ((size_t)yy * W + xx) * 3;
-            const double gr = __dadd_rn(__dadd_rn(__dmul_rn(0.299, (double)px[0]),
-                                                  __dmul_rn(0.587, (double)px[1])),
-                                        __dmul_rn(0.114, (double)px[2]));
-            s[t] = __dmul_rn((double)mask[t], gr);
+        // the element-wise steps are independent across t (unrolled, in
+        // registers); only the index-order sums form dependent chains
+        double s[N];
+#pragma unroll
+        for (int t = 0; t < N; ++t) s[t] = canon_v(img, H, W, mask, P, y, x, t);
+        double mu = 0.0;
+#pragma unroll
+        for (int t = 0; t < N; ++t) mu = __dadd_rn(mu, s[t]);
+        mu = __ddiv_rn(mu, (double)N);
+        double ss = 0.0;
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            s[t] = __dadd_rn(s[t], -mu);
+            ss = __dadd_rn(ss, __dmul_rn(s[t], s[t]));
         }
-        __syncwarp();
-        if (lane == 0) {
-            double mu = 0.0;
-            for (int t = 0; t < n; ++t) mu = __dadd_rn(mu, s[t]);
-            s_ab[wib] = __ddiv_rn(mu, (double)n);
-        }
-        __syncwarp();
-        const double mu = s_ab[wib];
-        for (int t = lane; t < n; t += 32) s[t] = __dadd_rn(s[t], -mu);
-        __syncwarp();
-        if (lane == 0) {
-            double ss = 0.0;
-            for (int t = 0; t < n; ++t) ss = __dadd_rn(ss, __dmul_rn(s[t], s[t]));
-            s_ab[wib] = ss;
-        }
-        __syncwarp();
-        const double ss = s_ab[wib];
         if (ss == 0.0) {
-            for (int t = lane; t < n; t += 32) s[t] = 0.0;
+#pragma unroll
+            for (int t = 0; t < N; ++t) s[t] = 0.0;
         } else {
             const double nrm = __dsqrt_rn(ss);
-            for (int t = lane; t < n; t += 32) s[t] = __ddiv_rn(s[t], nrm);
+#pragma unroll
+            for (int t = 0; t < N; ++t) s[t] = __ddiv_rn(s[t], nrm);
         }
-        __syncwarp();
-        // codes: one lane per code index, each an index-order dot product
         const int jlo = g.y < 0 ? 0 : g.y, jhi = g.y < 0 ? k : g.y + 1;
-        for (int j = jlo + lane; j < jhi; j += 32) {
+        for (int j = jlo; j < jhi; ++j) {
+            const float* oj = omega + (size_t)j * N;
             double a = 0.0;
-            for (int t = 0; t < n; ++t)
-                a = __dadd_rn(a, __dmul_rn((double)omega[(size_t)j * n + t], s[t]));
+#pragma unroll
+            for (int t = 0; t < N; ++t) a = __dadd_rn(a, __dmul_rn((double)oj[t], s[t]));
             if (fabs(a) <= tau) atomicOr(bitmask + (size_t)g.x * Wk + (j >> 5), 1u << (j & 31));
         }
-        __syncwarp();
     }
+}
+
+// ---------------------------------------------------------------- tensor-core codes
+//
+// codes_tc_kernel: the operator product as a tcgen05 GEMM. One CTA per
+// 16 x 8 pixel tile (one thread and one TMEM lane per pixel). The patch is
+// built and normalised in FP32 exactly as in codes_f32_kernel (same bound on
+// ||ds||) and split into three bf16 pieces, s = s1 + s2 + s3 + r with
+// |s2| <= 2^-8 |s|, |s3| <= 2^-16 |s|, |r| <= 2^-24 |s| (each piece the
+// bf16 rounding of the exact FP32 remainder); the operator is split the same
+// way (O1 + O2 + O3 + q) by omega_split_kernel into the B-operand layout and
+// arrives by one bulk (TMA) copy. Six MMA groups accumulate, smallest first,
+// O3 s1 + O2 s2 + O1 s3, then O2 s1 + O1 s2, then O1 s1 into FP32 tensor
+// memory. Omitted products and residuals contribute at most
+// 4.1 * 2^-24 sum_t |O_jt| |s_t|; for the accumulation, each MMA instruction
+// is taken to add a relative error of at most 2^-21 of the magnitudes summed
+// so far (a margin of 8 over one round-to-nearest; the bf16 x bf16 products
+// themselves are exact in FP32), so the KS instructions of the last group
+// dominate: KS 2^-21 (1 + 2^-6) plus 5 KS 2^-21 2^-7 for the earlier ones.
+// With sum_t |O_jt| |s_t| <= ||O_j|| ||s|| and ||s|| <= 1 + ||ds||, entries
+// closer to tau than the bound go to the same guard list and canonical FP64
+// recompute as the FP32 form.
+constexpr int CT_W = 16, CT_H = 8;  // pixel tile: 128 pixels
+constexpr uint64_t CT_WAIT_NS = 1000000000ull;
+
+__host__ __device__ constexpr int ct_ks(int p) { return (p * p + 15) / 16; }
+__host__ __device__ constexpr int ct_np(int k) { return (k + 15) / 16 * 16; }
+__host__ __device__ constexpr uint32_t ct_cols(int np) {
+    return np <= 32 ? 32u : np <= 64 ? 64u : np <= 128 ? 128u : 256u;
+}
+
+// Operator pieces in the B-operand layout: 3 KS slabs of np rows x 16 bf16
+// (slab piece * KS + s holds piece `piece` of columns 16 s .. 16 s + 15).
+__global__ void omega_split_kernel(const float* __restrict__ omega, int k, int n, int ks, int np,
+                                   uint8_t* __restrict__ blob) {
+    const int total = 3 * ks * np * 16;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i % 16, j = (i / 16) % np, sl = i / (16 * np);
+        const int piece = sl / ks, t = 16 * (sl % ks) + e;
+        float rem = (j < k && t < n) ? omega[(size_t)j * n + t] : 0.f;
+        uint16_t v = 0;
+        for (int q = 0; q <= piece; ++q) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(rem);
+            v = __bfloat16_as_ushort(b);
+            rem -= __bfloat162float(b);  // exact in FP32
+        }
+        *reinterpret_cast<uint16_t*>(blob + (size_t)sl * np * 32 + tc::slab_off(j, 2 * e)) = v;
+    }
+}
+
+__device__ __forceinline__ void ct_set_error(int* d_err, int site) {
+    if (atomicCAS(d_err, 0, CS_DEVERR_TIMEOUT) == 0) d_err[1] = site;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128, 4) codes_tc_kernel(
+    const float* __restrict__ img, int H, int W, const uint8_t* __restrict__ blob, int k, int np,
+    const float* __restrict__ mask, const float* __restrict__ rownorm, float tau_f,
+    float tau_slack, float* __restrict__ codes, float* __restrict__ lead16,
+    uint32_t* __restrict__ bitmask, int2* __restrict__ guard, int guard_cap,
+    int* __restrict__ guard_count, int* __restrict__ d_err) {
+    constexpr int N = P * P, R = (P - 1) / 2, KS = ct_ks(P);
+    constexpr int GW = CT_W + P - 1, GH = CT_H + P - 1;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sa = smem;                                  // A: 3 KS slabs x 4096 B
+    uint8_t* sb = smem + 3 * KS * 4096;                  // B: 3 KS slabs x np x 32 B
+    uint8_t* misc = sb + 3 * KS * np * 32;               // 32-byte aligned
+    uint64_t* bars = reinterpret_cast<uint64_t*>(misc);  // [0] B copy, [1] MMA
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(misc + 16);
+    int* s_flag = reinterpret_cast<int*>(misc + 20);
+    float* s_gray = reinterpret_cast<float*>(misc + 32);
+    float* s_gabs = s_gray + GW * GH;
+    float* s_w = s_gabs + GW * GH;
+    float* s_rn = s_w + N;                               // row norms, np
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t ncols = ct_cols(np);
+    const uint32_t b_bytes = (uint32_t)(3 * KS * np * 32);
+    if (tid == 0) {
+        tc::mbar_init(bars + 0, 1);
+        tc::mbar_init(bars + 1, 1);
+        tc::fence_mbar_init();
+        tc::mbar_arrive_expect_tx(bars + 0, b_bytes);
+        tc::bulk_g2s(sb, blob, b_bytes, bars + 0);
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(s_tmem, ncols);
+        tc::tmem_relinquish();
+    }
+    const int x0 = blockIdx.x * CT_W, y0 = blockIdx.y * CT_H;
+    for (int i = tid; i < GW * GH; i += 128) {
+        const int ly = i / GW, lx = i % GW;
+        const int yy = min(max(y0 + ly - R, 0), H - 1), xx = min(max(x0 + lx - R, 0), W - 1);
+        const float* px = img + ((size_t)yy * W + xx) * 3;
+        const float r = px[0], g = px[1], b = px[2];
+        s_gray[i] = __fadd_rn(__fadd_rn(__fmul_rn(0.299f, r), __fmul_rn(0.587f, g)),
+                              __fmul_rn(0.114f, b));
+        s_gabs[i] = (0.299f * fabsf(r) + 0.587f * fabsf(g) + 0.114f * fabsf(b)) * (1.f + 4 * U32);
+    }
+    for (int i = tid; i < N; i += 128) s_w[i] = mask[i];
+    for (int i = tid; i < np; i += 128) s_rn[i] = i < k ? rownorm[i] : 0.f;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *s_tmem;
+
+    // ---- patch, bound and A operand (row tid) -------------------------------
+    const int tx = tid % CT_W, ty = tid / CT_W;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool live = x < W && y < H;
+    const int pix = live ? y * W + x : 0;
+    float sum = 0.f, kc = 0.f, vabs = 0.f, e2 = 0.f;
+#pragma unroll
+    for (int dy = 0; dy < P; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < P; ++dx) {
+            const int t = dy * P + dx, li = (ty + dy) * GW + tx + dx;
+            const float v = __fmul_rn(s_w[t], s_gray[li]);
+            const float yk = __fsub_rn(v, kc);
+            const float tk = __fadd_rn(sum, yk);
+            kc = __fsub_rn(__fsub_rn(tk, sum), yk);
+            sum = tk;
+            vabs += fabsf(v);
+            const float ew = fabsf(s_w[t]) * s_gabs[li];
+            e2 = fmaf(ew, ew, e2);
+        }
+    const float mu = __fdiv_rn(sum, (float)N);
+    float ss = 0.f;
+#pragma unroll
+    for (int dy = 0; dy < P; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < P; ++dx) {
+            const int t = dy * P + dx, li = (ty + dy) * GW + tx + dx;
+            const float c = __fsub_rn(__fmul_rn(s_w[t], s_gray[li]), mu);
+            ss = fmaf(c, c, ss);
+        }
+    const float cn = sqrtf(ss);
+    const float dc = (2.f * 5.1f * U32) * sqrtf(e2) * 1.0001f +
+                     3.1f * U32 * vabs * rsqrtf((float)N) * 1.0001f + U32 * cn;
+    const bool whole = !(cn > 4.f * dc);
+    const float inv = whole ? 0.f : __frcp_rn(cn);
+    const float ds = whole ? 0.f : (2.f * dc / cn) * 1.0001f + 0.5f * (N + 7) * U32;
+    constexpr float EPS_TC = 4.1f * 5.9604645e-08f + KS * 4.76837158203125e-07f * 1.016f +
+                             5 * KS * 4.76837158203125e-07f * 0.0079f;
+    const float ebase = (ds + EPS_TC * (1.f + ds)) * 1.25f;
+#pragma unroll
+    for (int sl = 0; sl < KS; ++sl) {
+        uint32_t w1[8], w2[8], w3[8];
+#pragma unroll
+        for (int e2i = 0; e2i < 8; ++e2i) {
+            uint32_t p1 = 0, p2 = 0, p3 = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = 16 * sl + 2 * e2i + h;
+                float v = 0.f;
+                if (t < N && live) {
+                    const int li = (ty + t / P) * GW + tx + t % P;
+                    v = __fmul_rn(__fsub_rn(__fmul_rn(s_w[t], s_gray[li]), mu), inv);
+                }
+                const __nv_bfloat16 b1 = __float2bfloat16_rn(v);
+                const float r1 = v - __bfloat162float(b1);
+                const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+                const float r2 = r1 - __bfloat162float(b2);
+                const __nv_bfloat16 b3 = __float2bfloat16_rn(r2);
+                p1 |= (uint32_t)__bfloat16_as_ushort(b1) << (16 * h);
+                p2 |= (uint32_t)__bfloat16_as_ushort(b2) << (16 * h);
+                p3 |= (uint32_t)__bfloat16_as_ushort(b3) << (16 * h);
+            }
+            w1[e2i] = p1;
+            w2[e2i] = p2;
+            w3[e2i] = p3;
+        }
+        uint8_t* a1 = sa + sl * 4096;
+        uint8_t* a2 = sa + (KS + sl) * 4096;
+        uint8_t* a3 = sa + (2 * KS + sl) * 4096;
+        *reinterpret_cast<uint4*>(a1 + tc::slab_off(tid, 0)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4*>(a1 + tc::slab_off(tid, 16)) = make_uint4(w1[4], w1[5], w1[6], w1[7]);
+        *reinterpret_cast<uint4*>(a2 + tc::slab_off(tid, 0)) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        *reinterpret_cast<uint4*>(a2 + tc::slab_off(tid, 16)) = make_uint4(w2[4], w2[5], w2[6], w2[7]);
+        *reinterpret_cast<uint4*>(a3 + tc::slab_off(tid, 0)) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+        *reinterpret_cast<uint4*>(a3 + tc::slab_off(tid, 16)) = make_uint4(w3[4], w3[5], w3[6], w3[7]);
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+
+    // ---- MMA (one thread) ---------------------------------------------------
+    if (tid == 0) {
+        int flag = 0;
+        if (tc::mbar_wait(bars + 0, 0, tc::globaltimer() + CT_WAIT_NS)) {
+            tc::fence_after_sync();
+            const uint32_t id = tc::idesc(128, np, 1, 1);
+            // (operator piece, patch piece), smallest products first
+            const int order[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
+#pragma unroll
+            for (int gi = 0; gi < 6; ++gi)
+#pragma unroll
+                for (int sl = 0; sl < KS; ++sl)
+                    tc::mma_bf16(tmem, tc::smem_desc(sa + (order[gi][1] * KS + sl) * 4096),
+                                 tc::smem_desc(sb + (order[gi][0] * KS + sl) * np * 32), id,
+                                 gi > 0 || sl > 0);
+            tc::mma_commit(bars + 1);
+            flag = 1;
+        } else {
+            ct_set_error(d_err, 21);
+            // the copy must land before the CTA may exit
+            tc::mbar_wait(bars + 0, 0, tc::globaltimer() + CT_WAIT_NS);
+        }
+        *s_flag = flag;
+    }
+    __syncthreads();
+    bool ok = *s_flag != 0;
+    if (ok && !tc::mbar_wait(bars + 1, 0, tc::globaltimer() + CT_WAIT_NS)) {
+        ok = false;
+        ct_set_error(d_err, 22);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    tc::fence_after_sync();
+
+    // ---- epilogue: thresholds, guard list, outputs -------------------------
+    if (ok) {
+        const int Wk = (k + 31) >> 5;
+        const uint32_t lrow = tmem + ((uint32_t)(32 * warp) << 16);
+        uint32_t word = 0;
+        for (int c = 0; c < np / 16; ++c) {
+            uint32_t v[16];
+            tc::tmem_ld16(lrow + 16u * c, v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int j = 16 * c + e;
+                if (j < k && live) {
+                    const float a = __uint_as_float(v[e]);
+                    const float aa = fabsf(a);
+                    const float E = s_rn[j] * ebase + tau_slack;
+                    if (!whole) {
+                        if (fabsf(aa - tau_f) <= E)
+                            guard_push(guard, guard_cap, guard_count, pix, j);
+                        else if (aa <= tau_f)
+                            word |= 1u << (j & 31);
+                    }
+                    if (codes) codes[(size_t)pix * k + j] = a;
+                    if (lead16 && j < 16) lead16[(size_t)pix * 16 + j] = a;
+                }
+            }
+            if ((c & 1) || c == np / 16 - 1) {
+                if (live && bitmask) bitmask[(size_t)pix * Wk + (c >> 1)] = word;
+                word = 0;
+            }
+        }
+        if (live && whole) guard_push(guard, guard_cap, guard_count, pix, -1);
+        if (live && lead16)
+            for (int j = k; j < 16; ++j) lead16[(size_t)pix * 16 + j] = 0.f;
+    } else if (tid == 0 && *s_flag) {
+        // MMAs still in flight: they must finish before the tensor memory is freed
+        tc::mbar_wait(bars + 1, 0, tc::globaltimer() + CT_WAIT_NS);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, ncols);
+    }
+}
+
+template <int P>
+size_t ct_smem(int np) {
+    constexpr int N = P * P, KS = ct_ks(P), GW = CT_W + P - 1, GH = CT_H + P - 1;
+    size_t b = 3 * KS * 4096 + 3 * KS * (size_t)np * 32 + 32 + 4 * (2 * GW * GH + N + np);
+    b = (b + 15) / 16 * 16;
+    // at most 512 / ncols CTAs per SM, so that tensor-memory allocations never wait
+    const int per_sm = 512 / (int)ct_cols(np);
+    if (per_sm < 16) {
+        const size_t floor_b = 233472 / (per_sm + 1) - 1024 + 16;
+        if (b < floor_b) b = floor_b;
+    }
+    return b;
+}
+
+template <int P>
+cudaError_t launch_tc_p(const CodesArgs& a, cudaStream_t st) {
+    const int np = ct_np(a.k);
+    const size_t smem = ct_smem<P>(np);
+    cudaError_t e = cudaFuncSetAttribute(codes_tc_kernel<P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int total = 3 * ct_ks(P) * np * 16;
+    omega_split_kernel<<<(total + 255) / 256, 256, 0, st>>>(a.omega, a.k, P * P, ct_ks(P), np,
+                                                           a.omega_blob);
+    const float tau_f = (float)a.tau;
+    const float slack = fabsf(tau_f - (float)a.tau) + 2.f * U32 * tau_f + 1e-12f;
+    dim3 grd((a.W + CT_W - 1) / CT_W, (a.H + CT_H - 1) / CT_H);
+    codes_tc_kernel<P><<<grd, 128, smem, st>>>(a.img, a.H, a.W, a.omega_blob, a.k, np, a.mask,
+                                               a.rownorm, tau_f, slack, a.codes, a.lead16,
+                                               a.bitmask, a.guard, a.guard_cap, a.guard_count,
+                                               a.d_err);
+    return cudaGetLastError();
 }
 
 __global__ void cosupport_kernel(const float* __restrict__ codes, long long total, int k,
@@ -268,22 +564,48 @@ cudaError_t launch_p(const CodesArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_codes_f32(const CodesArgs& a, cudaStream_t st) {
+bool codes_tc_supported(int k, int p) { return k >= 1 && k <= 256 && p >= 3 && p <= 9 && (p & 1); }
+
+size_t codes_tc_blob_bytes(int k, int p) { return (size_t)3 * ct_ks(p) * ct_np(k) * 32; }
+
+cudaError_t launch_codes(const CodesArgs& a, cudaStream_t st) {
     const int n = a.p * a.p;
     rownorm_kernel<<<(a.k + 127) / 128, 128, 0, st>>>(a.omega, a.k, n, a.rownorm, a.guard_count);
     cudaError_t e;
-    switch (a.p) {
-        case 3: e = launch_p<3>(a, st); break;
-        case 5: e = launch_p<5>(a, st); break;
-        case 7: e = launch_p<7>(a, st); break;
-        case 9: e = launch_p<9>(a, st); break;
-        default: return cudaErrorInvalidValue;
+    if (a.tc) {
+        if (!a.omega_blob || !codes_tc_supported(a.k, a.p)) return cudaErrorInvalidValue;
+        switch (a.p) {
+            case 3: e = launch_tc_p<3>(a, st); break;
+            case 5: e = launch_tc_p<5>(a, st); break;
+            case 7: e = launch_tc_p<7>(a, st); break;
+            case 9: e = launch_tc_p<9>(a, st); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (a.p) {
+            case 3: e = launch_p<3>(a, st); break;
+            case 5: e = launch_p<5>(a, st); break;
+            case 7: e = launch_p<7>(a, st); break;
+            case 9: e = launch_p<9>(a, st); break;
+            default: return cudaErrorInvalidValue;
+        }
     }
     if (e != cudaSuccess) return e;
     if (!a.bitmask) return cudaSuccess;
-    codes_guard_kernel<<<152 * 4, 128, 0, st>>>(a.img, a.H, a.W, a.omega, a.k, a.mask, a.p, a.tau,
-                                                a.guard, a.guard_cap, a.guard_count, a.bitmask,
-                                                a.d_err);
+#define CS_GUARD(PP)                                                                        \
+    case PP:                                                                                \
+        codes_guard_kernel<PP><<<152 * 4, 128, 0, st>>>(a.img, a.H, a.W, a.omega, a.k, a.mask, \
+                                                        a.tau, a.guard, a.guard_cap,          \
+                                                        a.guard_count, a.bitmask, a.d_err);   \
+        break;
+    switch (a.p) {
+        CS_GUARD(3)
+        CS_GUARD(5)
+        CS_GUARD(7)
+        CS_GUARD(9)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CS_GUARD
     return cudaGetLastError();
 }
 

@@ -79,6 +79,10 @@ extern "C" cs_status cs_codes_noalloc(const float* img, int H, int W, const floa
         return cs_set_error(nullptr, CS_ERR_UNSUPPORTED, "%s: patch side %d not in 3..9", fn, prm->p);
     if (!(prm->tau >= 0.0))
         return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: tau must be >= 0", fn);
+    // the fixed scratch holds no operator operand tiles: FP32 CUDA-core codes only
+    if (prm->codes_form == CS_CODES_TC)
+        return cs_set_error(nullptr, CS_ERR_UNSUPPORTED, "%s: computes the FP32 codes form only",
+                            fn);
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) {
         cudaGetLastError();
@@ -99,7 +103,7 @@ extern "C" cs_status cs_codes_noalloc(const float* img, int H, int W, const floa
         a.guard = reinterpret_cast<int2*>(scratch + OFF_GUARD);
         a.guard_cap = NOALLOC_GUARD_CAP;
         a.d_err = dev_status;
-        e = launch_codes_f32(a, st);
+        e = launch_codes(a, st);  // FP32 form (a.tc is false)
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess)

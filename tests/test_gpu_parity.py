@@ -29,9 +29,9 @@ def _dev(torch, a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
 
 
-def _run(env, pr, mode=None, want_codes=False, precision=0):
+def _run(env, pr, mode=None, want_codes=False, precision=0, codes_form=0):
     cs, ctx, torch = env
-    prm = cs.Params.from_synth(pr.params, precision=precision)
+    prm = cs.Params.from_synth(pr.params, precision=precision, codes_form=codes_form)
     if mode is not None:
         prm.mode = mode
     img = _dev(torch, pr.image)
@@ -82,17 +82,46 @@ def test_workload1_full(env, mode):
 def test_ragged_shapes(env, H, W, nl, m, p, k, seed):
     pr = synth.make_problem(H, W, nl, m, p=p, k=k, seed=seed, cap_frac=0.9)
     for mode in (0, 1):
-        got = _run(env, pr, mode=mode)
+        got = _run(env, pr, mode=mode)  # tensor-core codes (k <= 256)
         ref = oracle.data_term(pr, mode=mode, want_dist2=True)
         _check_all(pr, got, ref)
+    got = _run(env, pr, codes_form=1)  # FP32 CUDA-core codes
+    assert np.array_equal(got["bits"], ref["bits_px"]), "bitmask mismatch (FP32 codes)"
 
 
-def test_codes_values(env):
-    """FP32 codes within their error bound of the FP64 codes."""
+@pytest.mark.parametrize("codes_form,bound", [(1, 2e-5), (2, 1e-5)])
+def test_codes_values(env, codes_form, bound):
+    """Codes within their form's error bound of the FP64 codes (unit-norm
+    operator rows): FP32 dot products, or the tensor-core GEMM over
+    three-piece BF16 splits (about 2.3e-6 from splits and accumulation plus
+    the FP32 patch error)."""
     pr = synth.make_problem(40, 44, 2, 10, p=7, k=98, seed=8)
-    got = _run(env, pr, want_codes=True)
-    a, _ = oracle.codes(pr.image, pr.omega, pr.mask, 7, 0.1)
-    assert np.max(np.abs(got["codes"] - a)) < 2e-5
+    got = _run(env, pr, want_codes=True, codes_form=codes_form)
+    a, bits = oracle.codes(pr.image, pr.omega, pr.mask, 7, 0.1)
+    err = np.max(np.abs(got["codes"] - a))
+    assert err < bound, err
+    assert np.array_equal(got["bits"], bits)
+
+
+def test_codes_form_selection(env):
+    """k > 256: the automatic form falls back to FP32 codes; the tensor-core
+    form is refused."""
+    cs, ctx, torch = env
+    pr = synth.make_problem(20, 21, 2, 8, p=5, k=300, seed=12)
+    prm = cs.Params.from_synth(pr.params)
+    img = _dev(torch, pr.image)
+    c = ctx.codes(img, _dev(torch, pr.omega), _dev(torch, pr.mask), prm)
+    ctx.sync()
+    _, bits = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1, want_codes=False)
+    assert np.array_equal(c["bitmask"].cpu().numpy().view(np.uint32), bits)
+    prm.codes_form = cs.CODES_TC
+    with pytest.raises(cs.CsError) as ei:
+        ctx.codes(img, _dev(torch, pr.omega), _dev(torch, pr.mask), prm)
+    assert ei.value.status == cs.CS_ERR_UNSUPPORTED
+    prm.codes_form = 7
+    with pytest.raises(cs.CsError) as ei:
+        ctx.codes(img, _dev(torch, pr.omega), _dev(torch, pr.mask), prm)
+    assert ei.value.status == cs.CS_ERR_INVALID_ARG
 
 
 def test_threshold_ties_exact(env):
@@ -102,9 +131,10 @@ def test_threshold_ties_exact(env):
     a, _ = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1)
     for tau in (abs(a[100, 3]), abs(a[7, 40]), np.nextafter(abs(a[55, 12]), 0)):
         pr.params.tau = float(tau)
-        got = _run(env, pr)
         _, bits = oracle.codes(pr.image, pr.omega, pr.mask, 5, tau, want_codes=False)
-        assert np.array_equal(got["bits"], bits)
+        for cf in (1, 2):
+            got = _run(env, pr, codes_form=cf)
+            assert np.array_equal(got["bits"], bits), cf
 
 
 def test_flat_and_constant_images(env):
@@ -113,9 +143,10 @@ def test_flat_and_constant_images(env):
     for val in (0.0, 0.4):
         pr = synth.make_problem(20, 24, 2, 8, p=7, k=98, seed=10)
         pr.image[:] = val
-        got = _run(env, pr)
         ref = oracle.data_term(pr, want_dist2=True)
-        _check_all(pr, got, ref)
+        for cf in (1, 2):
+            got = _run(env, pr, codes_form=cf)
+            _check_all(pr, got, ref)
         if val == 0.0:
             assert (got["bits"][:, :3] == np.uint32(0xFFFFFFFF)).all()
 

@@ -4,8 +4,9 @@ budget owned by another allocator, or where cudaMalloc's implicit device
 synchronisation is not acceptable).
 
 Called through the C ABI on two calls in a row, it must give exactly the
-bitmask and codes that cs_codes gives (the same tolerance as every other
-co-support test: bit-exact), and reject sizes beyond its fixed scratch.
+bitmask and codes that cs_codes gives in the same (FP32) codes form (the
+same tolerance as every other co-support test: bit-exact), and reject sizes
+beyond its fixed scratch and the tensor-core codes form.
 This file sorts last so that a run stopping at its first failure has run
 every other test; it also passes alone in a fresh process.
 """
@@ -32,7 +33,8 @@ def test_noalloc_matches_cs_codes(cuda_lib, H, W, p, k, seed):
 
     L = cs.lib()
     pr = synth.make_problem(H, W, 2, 10, p=p, k=k, seed=seed)
-    prm = cs.Params.from_synth(pr.params)
+    # the allocation-free entry computes the FP32 CUDA-core form of the codes
+    prm = cs.Params.from_synth(pr.params, codes_form=cs.CODES_FP32)
     img, om, mask = _dev(torch, pr.image), _dev(torch, pr.omega), _dev(torch, pr.mask)
     ctx = cs.Context(0)
     ref = ctx.codes(img, om, mask, prm, want_codes=True, want_lead16=True)
@@ -69,3 +71,7 @@ def test_noalloc_rejects_oversize(cuda_lib):
     rc = L.cs_codes_noalloc(dummy, 10, 10, dummy, 2000, dummy, ctypes.byref(prm), None, None,
                             dummy, dummy, None)
     assert rc == cs.CS_ERR_INVALID_ARG
+    prm.codes_form = cs.CODES_TC
+    rc = L.cs_codes_noalloc(dummy, 10, 10, dummy, 98, dummy, ctypes.byref(prm), None, None,
+                            dummy, dummy, None)
+    assert rc == cs.CS_ERR_UNSUPPORTED
