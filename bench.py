@@ -215,9 +215,10 @@ FORM_NAMES = {"fp32": "plain FP32 (CUDA cores, popc TSM)",
               "bf16": "tensor cores (tcgen05): BF16 exact texture dot, split-BF16 colour, exact location",
               "fp8": "tensor cores (tcgen05): FP8 exact texture dot, split-BF16 colour, exact location"}
 # kernels one step launches (cs_data_term, per-sample form): offsets, seed,
-# row scan, column envelope; row norms, codes, guard; gather; then either the
-# plain sum, or Morton sort, tile build and the tcgen05 sum
-LAUNCHES = {"fp32": 9, "bf16": 11, "fp8": 11}
+# row scan, column envelope; row norms, operator split, tcgen05 codes, guard;
+# gather; then either the plain sum, or Morton sort, tile build, the tcgen05
+# sum and the FP64 recompute of rows below the FP32 floor
+LAUNCHES = {"fp32": 10, "bf16": 13, "fp8": 13}
 
 
 def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=None):
@@ -253,6 +254,7 @@ def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=Non
     ctx.profile(False)
     ctx.sync()
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    refined = ctx.refined_count()  # pixels of the last step recomputed in FP64
     stage = {}
     for name, st in (("codes", cs.STAGE_CODES), ("dist", cs.STAGE_DIST),
                      ("gather", cs.STAGE_GATHER), ("sum", cs.STAGE_SUM)):
@@ -283,6 +285,7 @@ def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=Non
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    stage["refined_pixels"] = refined
     return dev_ms, e2e_ms, stage, h2d, d2h
 
 
@@ -355,6 +358,7 @@ def main():
         sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         forms_out = {}
+        refined = {f: res[f][2].pop("refined_pixels") for f in forms}
         for form in forms:
             d_ms, e_ms, stage, h2d, d2h = res[form]
             peak, pipe = alu_peak_pairs(form, Wk, sm_mhz, n_sm)
@@ -363,7 +367,8 @@ def main():
                 "form": FORM_NAMES[form], "pairs_per_s": pairs_rank * args.steps / (d_ms * 1e-3),
                 "ms_per_step": d_ms / args.steps, "stage_ms": stage,
                 "sum_kernel_pairs_per_s": achieved, "sum_kernel_peak": peak,
-                "sum_kernel_frac": achieved / peak, "binding_pipe": pipe}
+                "sum_kernel_frac": achieved / peak, "binding_pipe": pipe,
+                "fp64_recomputed_pixels": refined[form]}
         d_ms, e_ms, stage, h2d, d2h = res[head]
         peak, pipe = alu_peak_pairs(head, Wk, sm_mhz, n_sm)
         achieved = pairs_rank / (stage["sum"] * 1e-3)

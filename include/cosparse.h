@@ -81,6 +81,10 @@ typedef struct cs_ctx cs_ctx;
  *   alpha      rho_i(x) = alpha * max(|x - x_v|, d_min)  (Sec. 3.1: alpha = 1.3)
  *   d_min      floor on the nearest-scribble distance in pixels (default 1)
  *   kappa_beta beta_i(x) = kappa_beta * rho_i(x): beta proportional to rho (Sec. 3.1)
+ *   l_tol      tensor-core forms: a label row whose a-priori error bound on L
+ *              exceeds l_tol * max(|L|, 1) is recomputed in FP64 on the GPU
+ *              (default 1e-3; 0 recomputes only rows below the FP32 floor;
+ *              smaller values recompute more rows, at FP64 speed)
  */
 typedef struct {
     int32_t p;
@@ -92,6 +96,7 @@ typedef struct {
     double alpha;
     double d_min;
     double kappa_beta;
+    double l_tol;
 } cs_params;
 
 void cs_params_default(cs_params* out);
@@ -218,6 +223,28 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
                         int k, int n_labels, const int32_t* label_off,
                         const int32_t* sample_pix, const cs_params* prm, int32_t* dist2,
                         float* neglog, float* post, void* stream);
+
+/*
+ * Precision control of the tensor-core forms (CS_BF16, CS_FP8). Every pair
+ * exponent e_j (log2 units) is <= 0, so their sum accumulates 2^(e_j + s)
+ * in FP32 with the fixed shift s = 96 - ceil(log2 m_i) and cannot overflow.
+ * A pixel is recomputed on the GPU in double precision (all labels:
+ * exponents, two-pass log-sum-exp and normalisation in FP64) before the
+ * call's work completes when one of its label rows either totals below
+ * m_i 2^-100 after the shift (terms may have underflowed) or has an a-priori
+ * error bound above l_tol * max(|L|, 1). The bound (log2 units)
+ * adds 2^-15 C Q for the two-piece BF16 colour splits (C = log2 e /
+ * (2 sigma_c2), Q = 2 |I| max_j |I_j| + max_j |I_j|^2), 2^-21 (Bt k + C Q)
+ * for the tensor core's FP32 accumulation of the colour MMA onto the integer
+ * texture sum (Bt = log2 e / beta), and 6 u (3 (|log2 S| + log2 m) +
+ * |nA| <K> + 2 |R0| + 1) for the FP32 epilogue, where the pairs' exponents and
+ * squared offsets K from their sample tile's anchor are averaged with the
+ * pairs' shares of the row sum S as weights (R0 = Bt |b_x| + C |I|^2,
+ * nA = -log2 e / (2 rho^2)). cs_refined_count returns how many pixels the last tensor-core
+ * cs_likelihood / cs_data_term call on ctx recomputed (0 after the plain
+ * form). It synchronises `stream`.
+ */
+cs_status cs_refined_count(cs_ctx* ctx, int32_t* count, void* stream);
 
 /*
  * The whole data term in one call: patches, codes and co-support bitmasks of

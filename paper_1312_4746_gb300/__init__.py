@@ -45,6 +45,7 @@ EXPORTS = (
     "cs_cosupport",
     "cs_likelihood",
     "cs_data_term",
+    "cs_refined_count",
     "cs_batch_create",
     "cs_batch_run",
     "cs_batch_config",
@@ -87,6 +88,7 @@ class Params(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("d_min", ctypes.c_double),
         ("kappa_beta", ctypes.c_double),
+        ("l_tol", ctypes.c_double),
     ]
 
     @classmethod
@@ -152,6 +154,7 @@ def lib(path: str | None = None):
     L.cs_last_error.argtypes = [V]
     L.cs_last_error.restype = ctypes.c_char_p
     L.cs_sync_status.argtypes = [V, V]
+    L.cs_refined_count.argtypes = [V, ctypes.POINTER(ctypes.c_int32), V]
     L.cs_codes.argtypes = [V, V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V]
     L.cs_cosupport.argtypes = [V, V, I, I, D, V, V]
     L.cs_codes_noalloc.argtypes = [V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V, V]
@@ -179,7 +182,7 @@ def lib(path: str | None = None):
     L.cs_mlp_grad.argtypes = [V, V, I, V, V, I, V, V, V]
     L.cs_profile_enable.argtypes = [V, I]
     L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
-    for f in ("cs_create", "cs_sync_status", "cs_codes", "cs_cosupport", "cs_likelihood",
+    for f in ("cs_create", "cs_sync_status", "cs_refined_count", "cs_codes", "cs_cosupport", "cs_likelihood",
               "cs_data_term", "cs_profile_enable", "cs_profile_read", "cs_surrogate_fit",
               "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_mlp_forward",
               "cs_mlp_grad", "cs_batch_create", "cs_batch_run", "cs_batch_config",
@@ -326,6 +329,12 @@ class Context:
             _ptr(out.get("bitmask")), _ptr(out.get("dist2")), _ptr(out["neglog"]),
             _ptr(out.get("post")), _stream()))
         return out
+
+    def refined_count(self):
+        """Pixels the last tensor-core sum recomputed in FP64 (cs_refined_count)."""
+        n = ctypes.c_int32()
+        self.check(self._lib.cs_refined_count(self.handle, ctypes.byref(n), _stream()))
+        return n.value
 
     # ------------------------------------------------------------------ batches
 

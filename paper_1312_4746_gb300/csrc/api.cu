@@ -124,6 +124,7 @@ void cs_params_default(cs_params* out) {
     out->alpha = 1.3;
     out->d_min = 1.0;
     out->kappa_beta = 1.0;
+    out->l_tol = 1e-3;
 }
 
 cs_status cs_create(cs_ctx** out, int device) {
@@ -174,6 +175,23 @@ void cs_destroy(cs_ctx* ctx) {
 
 const char* cs_last_error(const cs_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_noctx_err.c_str();
+}
+
+cs_status cs_refined_count(cs_ctx* ctx, int32_t* count, void* stream) {
+    if (!ctx || !count)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_refined_count: null argument");
+    *count = 0;
+    if (!ctx->last_fb_count) return CS_OK;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    int v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->last_fb_count, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cs_set_error(ctx, CS_ERR_CUDA, "cs_refined_count: %s", cudaGetErrorString(e));
+    }
+    *count = v;
+    return CS_OK;
 }
 
 cs_status cs_sync_status(cs_ctx* ctx, void* stream) {
@@ -267,6 +285,8 @@ cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int
     if (!(prm->sigma_c2 > 0) || !(prm->alpha > 0) || !(prm->d_min > 0) || !(prm->kappa_beta > 0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG,
                             "%s: sigma_c2, alpha, d_min and kappa_beta must be > 0", fn);
+    if (!(prm->l_tol >= 0.0))
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: l_tol must be >= 0", fn);
     if (prm->mode != CS_MODE_PERSAMPLE && prm->mode != CS_MODE_FACTORISED)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown mode %d", fn, prm->mode);
     if (prm->precision != CS_FP32 && prm->precision != CS_BF16 && prm->precision != CS_FP8)
@@ -335,6 +355,9 @@ void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2) {
     L.t.tile_c = c.take<int2>(L.tc_form ? (size_t)L.total_tiles : 0);
     L.t.perm = c.take<int32_t>(L.tc_form ? (size_t)S : 0);
     L.desc = c.take<TcImage>(L.tc_form ? 1 : 0);
+    L.imax2 = c.take<float>(L.tc_form ? (size_t)n : 0);
+    L.fb_list = c.take<int2>(L.tc_form ? (size_t)P : 0);
+    L.fb_count = c.take<int>(L.tc_form ? 1 : 0);
 }
 
 static cudaError_t enqueue_codes(cs_ctx* ctx, const CodesArgs& a, cudaStream_t st) {
@@ -406,6 +429,10 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
     T.persample = L.persample;
     T.desc = L.desc;
     T.first_item = 0;
+    T.fb_list = L.fb_list;
+    T.fb_count = L.fb_count;
+    T.imax2 = L.imax2;
+    T.l_tol = (float)prm->l_tol;
     return T;
 }
 
@@ -422,6 +449,7 @@ static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
     if (e != cudaSuccess) return e;
     StageTimer tm(ctx, CS_STAGE_SUM, st);
     if (!L.tc_form) return launch_sum_plain(cs_sum_args(L, img, bitmask, prm, neglog, post), st);
+    ctx->last_fb_count = L.fb_count;
     return launch_sum_tc(cs_tc_launch(ctx, L, img, bitmask, prm, neglog, post), st);
 }
 

@@ -75,6 +75,9 @@ struct cs_batch {
     bool tc = false;
     char* mem = nullptr;
     TcImage* descs = nullptr;
+    int2* fb_list = nullptr;  // FP64 recompute list over all images
+    int* fb_count = nullptr;
+    int total_pixels = 0;
     int n_streams = 4, order_mode = 0;
     std::vector<int> order;       // image index at each processing position
     std::vector<int> first_item;  // first work item at each processing position
@@ -156,7 +159,11 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
                       (float)b->prm.kappa_beta,
                       (float)b->prm.sigma_c2,
                       ctx->d_err,
-                      ctx->n_sm};
+                      ctx->n_sm,
+                      b->fb_list,
+                      b->fb_count,
+                      b->total_pixels,
+                      (float)b->prm.l_tol};
         e = launch_tc_sum(b->descs, (int)b->order.size(), b->n_items, p, st);
     }
     return e;
@@ -291,6 +298,7 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
         if (*c == ' ') *c = '_';
     sig << dp.name << ":k" << k << "p" << prm->p << "m" << prm->mode << "f" << prm->precision
         << ":n" << n_images;
+    long long total_px = 0;
     for (int i = 0; i < n_images; ++i) {
         BatchImage& m = b->im[i];
         m.d = images[i];
@@ -299,8 +307,14 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
         const long long P = (long long)m.d.H * m.d.W;
         m.pairs = (double)P * m.off[m.d.n_labels];
         b->pairs += m.pairs;
+        total_px += P;
         sig << ":" << m.d.W << "x" << m.d.H << "x" << m.d.n_labels << "x" << m.off[m.d.n_labels];
     }
+    if (total_px > (1ll << 31) - 1) {
+        cs_batch_destroy(b);
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: more than 2^31 pixels in one batch", fn);
+    }
+    b->total_pixels = (int)total_px;
     // the signature is hashed so that cache lines stay short
     {
         const std::string full = sig.str();
@@ -324,6 +338,8 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
             cs_lik_carve(c, m.L, m.d.dist2);
         }
         b->descs = c.take<TcImage>(b->tc ? (size_t)n_images : 0);
+        b->fb_list = c.take<int2>(b->tc ? (size_t)b->total_pixels : 0);
+        b->fb_count = c.take<int>(b->tc ? 1 : 0);
     };
     Carve m0(nullptr);
     carve_all(m0);

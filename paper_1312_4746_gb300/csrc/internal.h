@@ -14,6 +14,7 @@
 #define CS_DEVERR_GUARD_FULL 101  // co-support guard list overflowed
 #define CS_DEVERR_TIMEOUT 102     // bounded wait gave up
 #define CS_DEVERR_BAD_SAMPLE 103  // a sample index lies outside the image
+#define CS_DEVERR_REFINE_FULL 104 // the FP64 recompute list overflowed
 
 // Largest supported shapes.
 #define CS_MAX_K 1024
@@ -37,6 +38,7 @@ struct cs_ctx {
     size_t surr_cap = 0;
     int surr_n = 0, surr_train = 0, surr_val = 0;
     bool surr_ready = false;
+    int* last_fb_count = nullptr;  // FP64 recompute count of the last tensor-core sum
     cudaStream_t side = nullptr;  // distance transform overlapping the codes
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool profiling = false;
@@ -198,6 +200,9 @@ struct LikPlan {
     int32_t *colbuf, *vbuf, *fbuf, *d2;
     SampleTables t;
     TcImage* desc;  // tensor-core form: descriptor slot
+    int2* fb_list;  // tensor-core form: FP64 recompute list (P entries) and count
+    int* fb_count;
+    float* imax2;   // tensor-core form: per label max |I_j|^2
 };
 
 typedef LikPlan LikPlanRef;
@@ -237,9 +242,14 @@ struct TcImage {
     const uint32_t* rep;       // majority co-supports (factorised form)
     float* neglog;
     float* post;
+    // per-sample tables (original order), read by the FP64 recompute
+    const float *sx, *sy, *sr, *sg, *sb;
+    const uint32_t* sbits;  // word-major [Wk][n_samples]
+    const float* imax2;     // per label: max_j |I_j|^2 (error bound)
+    int n_samples;
     int H, W, ntx, n_labels;
     int first_item;  // work-item index of this image's first pixel tile
-    int pad[3];
+    int pad[2];
 };
 struct TcSumParams {
     int k;
@@ -247,6 +257,12 @@ struct TcSumParams {
     float alpha, d_min, kappa_beta, sigma_c2;
     int* d_err;
     int n_sm;
+    // pixels with a label row below the FP32 floor: (image, pixel), their
+    // count (cleared by the launch) and the capacity (>= all pixels)
+    int2* fb_list;
+    int* fb_count;
+    int fb_cap;
+    float l_tol;  // relative tolerance on L of the a-priori row bound (0: off)
 };
 struct TcLaunch {
     const float* img;
@@ -271,6 +287,10 @@ struct TcLaunch {
     bool persample;  // per-sample texture kernel (else factorised)
     TcImage* desc;   // device slot receiving this image's descriptor
     int first_item;  // its first work item in the sum launch
+    int2* fb_list;   // FP64 recompute list (H W entries) and its count
+    int* fb_count;
+    float* imax2;    // per label max |I_j|^2 (written by the preparation)
+    float l_tol;
 };
 size_t tc_copy_bytes(int k, bool tex8, bool persample);
 int tc_tiles_per_label(int m);

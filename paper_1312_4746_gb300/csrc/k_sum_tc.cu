@@ -26,11 +26,13 @@
 // the A operand's delta entries per stage. In the factorised form D1 is the
 // colour part alone with Bt = 1.
 //
-// All full exponents are <= 0. The first chunk of 16 samples each warp sees
-// for a label fixes a reference maximum M; later terms can then exceed it by
-// at most -(M + R0), so when -(M + R0) + log2(m_i) <= 120 the sum of
-// 2^(e - M) cannot overflow and no further maximum is tracked; otherwise the
-// warp keeps a running maximum with lazy rescaling.
+// All full exponents are <= 0, so no running maximum is needed: the row sum
+// accumulates 2^(e + shift) with a fixed shift 96 - ceil(log2 m_i) (no term
+// above 2^96 / m_i, no overflow), in packed f32x2 arithmetic, TwoSum-
+// compensated across 16-sample chunks. A pixel goes to the FP64 recompute
+// (refine_fp64_kernel) when one of its label rows totals less than
+// m_i 2^-100 (terms may have underflowed) or when the row's a-priori error
+// bound exceeds l_tol max(|L|, 1) (derivation at the flagging site).
 //
 // One persistent CTA per SM; a pixel tile is 16 x 8 pixels (one TMEM lane
 // each), a sample tile 128 samples (one TMEM column each).
@@ -69,8 +71,11 @@ constexpr uint32_t TMEM_COLS = 512;     // D1[2] at 0, 128; Dl[2] at 256, 384
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr float LN2 = 0.6931471805599453f;
 constexpr uint64_t WAIT_NS = 1000000000ull;  // 1 s per wait
-constexpr float LAZY = 8.f;                  // slow path: rescale once the max grows by 2^8
-constexpr float SAFE = 120.f;                // fixed-reference range limit (log2)
+// The sum runs on 2^(e + SHIFT_i) with SHIFT_i = 96 - ceil(log2 m_i): every
+// term is <= 2^96 / m_i, so the row sum stays below 2^96. A shifted total
+// below m_i 2^-100 may have lost mass to FP32 underflow (each lost term is
+// < 2^-126, at most m_i of them: relative loss < 2^-26) and is recomputed.
+constexpr float FLOOR_PER_SAMPLE = 7.888609052210118e-31f;  // 2^-100
 
 struct TcArgs {
     const TcImage* images;  // n_images descriptors, ordered by first_item
@@ -78,6 +83,10 @@ struct TcArgs {
     int k, Wk;
     float alpha, d_min, kappa_beta, sigma_c2;
     int* d_err;
+    int2* fb_list;  // (image, pixel) of pixels to recompute in FP64
+    int* fb_count;
+    int fb_cap;
+    float l_tol;    // relative tolerance on L of the a-priori row bound (0: off)
 };
 
 // Image of work item g: the last descriptor whose first item is <= g.
@@ -173,57 +182,62 @@ __device__ __forceinline__ void loc_row_a(int px, int py, int dx, int dy, uint4&
                     pack2(one, one));
 }
 
-// Online log-sum-exp over 16 columns (nv of them valid) of one pixel row:
-// exponents e = nA Dl + Bt D1 + nK (log2 units). With a fixed reference
-// maximum M (see the file header) and a full chunk, four independent sums
-// of 2^(e - M); otherwise the general path with the running maximum (lazy
-// rescale) until the reference can be fixed. TwoSum-compensated into (S, C).
-__device__ __forceinline__ void lse16(const uint32_t (&r1)[16], const uint32_t (&rl)[16], int nv,
-                                      float nA, float Bt, float nK, float R0, float lim,
-                                      float& M, float& S, float& Cc, bool& fixed) {
+// Packed FP32 pairs (Blackwell f32x2 instructions: one issue, two lanes of work).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// Sum over 16 columns (nv of them valid) of one pixel row of 2^e, with
+// e = nA Dl + Bt D1 + nKR (log2 units, shifted full exponents), added to (S, Cc) by
+// TwoSum; returns the chunk's sum. A full chunk takes the packed path.
+__device__ __forceinline__ float sum16(const uint32_t (&r1)[16], const uint32_t (&rl)[16], int nv,
+                                       float nA, float Bt, float nKR, float& S, float& Cc) {
     float ts;
-    if (fixed && nv >= 16) {
-        const float nM = nK - M;
-        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    if (nv >= 16) {
+        const float2 bt2 = make_float2(Bt, Bt), na2 = make_float2(nA, nA), k2 = make_float2(nKR, nKR);
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < 16; u += 4) {
-            t0 += ex2f(fmaf(nA, __uint_as_float(rl[u + 0]), fmaf(Bt, __uint_as_float(r1[u + 0]), nM)));
-            t1 += ex2f(fmaf(nA, __uint_as_float(rl[u + 1]), fmaf(Bt, __uint_as_float(r1[u + 1]), nM)));
-            t2 += ex2f(fmaf(nA, __uint_as_float(rl[u + 2]), fmaf(Bt, __uint_as_float(r1[u + 2]), nM)));
-            t3 += ex2f(fmaf(nA, __uint_as_float(rl[u + 3]), fmaf(Bt, __uint_as_float(r1[u + 3]), nM)));
+            float2 v0 = fma2(bt2, make_float2(__uint_as_float(r1[u]), __uint_as_float(r1[u + 1])), k2);
+            float2 v1 = fma2(bt2, make_float2(__uint_as_float(r1[u + 2]), __uint_as_float(r1[u + 3])), k2);
+            v0 = fma2(na2, make_float2(__uint_as_float(rl[u]), __uint_as_float(rl[u + 1])), v0);
+            v1 = fma2(na2, make_float2(__uint_as_float(rl[u + 2]), __uint_as_float(rl[u + 3])), v1);
+            acc0 = add2(acc0, make_float2(ex2f(v0.x), ex2f(v0.y)));
+            acc1 = add2(acc1, make_float2(ex2f(v1.x), ex2f(v1.y)));
         }
-        ts = (t0 + t1) + (t2 + t3);
+        const float2 t = add2(acc0, acc1);
+        ts = t.x + t.y;
     } else {
-        // first pass: maximum over the valid columns; second pass: the sum
-        float m = -INFINITY;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const float v = fmaf(nA, __uint_as_float(rl[u]), fmaf(Bt, __uint_as_float(r1[u]), nK));
-            if (u < nv) m = fmaxf(m, v);
-        }
-        if (!fixed && (m > M + LAZY || M == -INFINITY)) {
-            const float sc = ex2f(M - m);
-            S *= sc;
-            Cc *= sc;
-            M = m;
-        }
-        const float nM = nK - M;
         float t0 = 0.f, t1 = 0.f;
 #pragma unroll
         for (int u = 0; u < 16; u += 2) {
-            const float v0 = fmaf(nA, __uint_as_float(rl[u]), fmaf(Bt, __uint_as_float(r1[u]), nM));
-            const float v1 = fmaf(nA, __uint_as_float(rl[u + 1]), fmaf(Bt, __uint_as_float(r1[u + 1]), nM));
+            const float v0 = fmaf(nA, __uint_as_float(rl[u]), fmaf(Bt, __uint_as_float(r1[u]), nKR));
+            const float v1 = fmaf(nA, __uint_as_float(rl[u + 1]), fmaf(Bt, __uint_as_float(r1[u + 1]), nKR));
             t0 += u < nv ? ex2f(v0) : 0.f;
             t1 += u + 1 < nv ? ex2f(v1) : 0.f;
         }
         ts = t0 + t1;
-        // every later exponent is <= -R0, i.e. at most -(M + R0) above M
-        if (!fixed) fixed = __all_sync(0xffffffffu, -(M + R0) <= lim);
     }
     const float sn = S + ts;
     const float bb = sn - S;
     Cc += (S - (sn - bb)) + (ts - bb);
     S = sn;
+    return ts;
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
@@ -432,6 +446,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(atex_full);
 
+            bool flagged = false;  // a label row of this pixel fell below the floor
             for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
                 const int D = live ? im.dist2[(size_t)i * P + pix] : 0;
                 const float rho = a.alpha * fmaxf(sqrtf((float)D), a.d_min);
@@ -461,10 +476,10 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 if (lane == 0) tc::mbar_arrive(acol_full + cb);
 
                 const int m_i = im.label_off[i + 1] - im.label_off[i];
-                const float lim = SAFE - log2f((float)m_i);
+                const float shift = (float)(96 - (32 - __clz(m_i - 1)));  // 96 - ceil(log2 m)
+                const float R0s = R0 + shift;
                 const int nt = tiles_of(im.tile_off, i), t0 = im.tile_off[i];
-                float M = -INFINITY, S = 0.f, Ccomp = 0.f;
-                bool fixed = false;  // warp-uniform: reference maximum fixed
+                float S = 0.f, Ccomp = 0.f, wK = 0.f;  // wK: sum of tile sums x K
                 int2 c_next = im.tile_c[t0];  // anchors fetched one tile ahead
                 for (int t = 0; t < nt; ++t, ++it) {
                     const int2 c = c_next;
@@ -474,9 +489,10 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     if (!ok) break;
                     tc::fence_after_sync();
                     const int nvalid = min(BN, m_i - t * BN);
-                    // per-tile location constant nA |x' + delta|^2, delta = o - c
+                    // per-tile constant nA |x' + delta|^2 + R0, delta = o - c
                     const float kx = (float)(rx + ox - c.x), ky = (float)(ry + oy - c.y);
-                    const float nK = nA * fmaf(kx, kx, ky * ky);
+                    const float K = fmaf(kx, kx, ky * ky);
+                    const float nKR = fmaf(nA, K, R0s);
                     const int cbase = hf * CPW;
                     const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
                     if (cbase < nvalid) {  // warp-uniform
@@ -487,8 +503,9 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                                 tc::tmem_ld16(lb + 16u * ch, x1);
                                 tc::tmem_ld16(lb + 256u + 16u * ch, xl);
                                 tc::tmem_ld_wait();
-                                lse16(x1, xl, nvalid - cbase - 16 * ch, nA, Bt, nK, R0, lim, M, S,
-                                      Ccomp, fixed);
+                                wK = fmaf(sum16(x1, xl, nvalid - cbase - 16 * ch, nA, Bt, nKR, S,
+                                                Ccomp),
+                                          K, wK);
                             }
                         }
                     }
@@ -505,34 +522,53 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 float4* xb = xchg + (size_t)xbuf * (EPQ - 1) * 4 * 32;
                 uint64_t* xbar = xchg_full + xbuf * 4 + q;
                 if (hf > 0) {
-                    xb[((hf - 1) * 4 + q) * 32 + lane] = make_float4(M, S, Ccomp, 0.f);
+                    xb[((hf - 1) * 4 + q) * 32 + lane] = make_float4(S, Ccomp, wK, 0.f);
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(xbar);
                 } else {
                     ok = wait_warp(xbar, (uint32_t)((li >> 2) & 1), abort_flag, a.d_err, 11);
                     if (!ok) break;
-                    float Mm = M;
-#pragma unroll
-                    for (int h = 0; h < EPQ - 1; ++h) Mm = fmaxf(Mm, xb[(h * 4 + q) * 32 + lane].x);
-                    float Sm = S * ex2f(M - Mm), Cm = Ccomp * ex2f(M - Mm);
+                    float Sm = S, Cm = Ccomp, wKm = wK;
 #pragma unroll
                     for (int h = 0; h < EPQ - 1; ++h) {
                         const float4 v = xb[(h * 4 + q) * 32 + lane];
-                        const float sc = ex2f(v.x - Mm);
-                        Sm += v.y * sc;
-                        Cm += v.z * sc;
+                        Sm += v.x;
+                        Cm += v.y;
+                        wKm += v.z;
                     }
-                    const float lse2 = R0 + Mm + log2f(Sm + Cm);
+                    const float tot = Sm + Cm;  // shifted by 2^shift
+                    const float lse2 = log2f(tot) - shift;
+                    const float Lv = lse2 * LN2 - logf((float)m_i) -
+                                     logf(6.283185307179586f * rho * rho) - log_col_norm;
+                    // below the floor the FP32 terms may have lost mass to
+                    // underflow; above the tolerance the bound on the error of
+                    // L (log2 units) is too loose: recompute in FP64. Bound:
+                    // colour splits 2^-15 C Q; the colour MMA's accumulation
+                    // onto the integer texture sum 2^-21 (Bt k + C Q); the FP32
+                    // epilogue 6u per pair, weighted by the pairs' shares of
+                    // the sum: |e_j| averages at most |log2 S| + log2 m, the
+                    // tile offsets |nA| K average |nA| wK / S, plus |R0|.
+                    const float im2 = im.imax2[i];
+                    const float CQ = Cc * fmaf(2.f * sqrtf(I2), sqrtf(im2), im2);
+                    const float BK = PERSAMPLE ? Bt * (float)a.k : 0.f;
+                    const float E2 =
+                        3.1e-05f * CQ + 4.76837158203125e-07f * (BK + CQ) +
+                        3.5762787e-07f * (3.f * (fabsf(lse2) + log2f((float)m_i)) -
+                                          nA * (wKm / tot) + 2.f * fabsf(R0) + shift + 1.f);
+                    if (!(tot >= FLOOR_PER_SAMPLE * (float)m_i) ||
+                        (a.l_tol > 0.f && E2 * LN2 > a.l_tol * fmaxf(fabsf(Lv), 1.f)))
+                        flagged = true;
                     // -L into the output plane; normalised once all labels are done
-                    if (live)
-                        im.neglog[(size_t)i * P + pix] = -(lse2 * LN2 - logf((float)m_i) -
-                                                          logf(6.283185307179586f * rho * rho) -
-                                                          log_col_norm);
+                    if (live) im.neglog[(size_t)i * P + pix] = -Lv;
                 }
             }
             if (!ok) break;
-            // label normalisation (and the factorised texture posterior) by part 0
-            if (hf == 0 && live) {
+            // label normalisation (and the factorised texture posterior) by part
+            // 0; a flagged pixel is listed for the FP64 recompute instead
+            if (hf == 0 && live && flagged) {
+                const int idx = atomicAdd(a.fb_count, 1);
+                if (idx < a.fb_cap) a.fb_list[idx] = make_int2(image_of(a, g), pix);
+            } else if (hf == 0 && live) {
                 if (!PERSAMPLE) {
                     float tmax = -INFINITY;
                     for (int i = 0; i < im.n_labels; ++i) {
@@ -572,6 +608,94 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
     if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// FP64 recompute of the pixels flagged by the sum (a label row below the FP32
+// floor or above the error tolerance): one warp per listed pixel, every
+// label; per label the exponents
+// e_j = -|x - x_j|^2 / (2 rho^2) - |I - I_j|^2 / (2 sigma_c2) [- TSM / beta]
+// in double, a two-pass log-sum-exp across the lanes, then the label
+// normalisation (and, factorised, the texture posterior) in double.
+__global__ void __launch_bounds__(128) refine_fp64_kernel(
+    const TcImage* __restrict__ images, const int2* __restrict__ list,
+    const int* __restrict__ count, int cap, int Wk, double alpha, double d_min, double kappa_beta,
+    double sigma_c2, bool persample, int* __restrict__ d_err) {
+    __shared__ double sL[4][CS_MAX_LABELS];
+    __shared__ double sT[4][CS_MAX_LABELS];
+    int cnt = *count;
+    if (cnt > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && atomicCAS(d_err, 0, CS_DEVERR_REFINE_FULL) == 0)
+            d_err[1] = cnt;
+        cnt = cap;
+    }
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * 4;
+    const double PI2 = 6.283185307179586;
+    const double col_norm = 1.5 * log(PI2 * sigma_c2), c_col = 0.5 / sigma_c2;
+    for (int e = blockIdx.x * 4 + wib; e < cnt; e += nwarps) {
+        const int2 it = list[e];
+        const TcImage& im = images[it.x];
+        const int pix = it.y, x = pix % im.W, y = pix / im.W;
+        const long long P = (long long)im.H * im.W;
+        const double IR = im.img[(size_t)pix * 3], IG = im.img[(size_t)pix * 3 + 1],
+                     IB = im.img[(size_t)pix * 3 + 2];
+        uint32_t bx[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) bx[w] = w < Wk ? im.bitmask[(size_t)pix * Wk + w] : 0u;
+        for (int i = 0; i < im.n_labels; ++i) {
+            const double rho = alpha * fmax(sqrt((double)im.dist2[(size_t)i * P + pix]), d_min);
+            const double c_loc = 0.5 / (rho * rho);
+            const double c_tex = persample ? 1.0 / (kappa_beta * rho) : 0.0;
+            const int off = im.label_off[i], m = im.label_off[i + 1] - off;
+            auto expo = [&](int j) {
+                const int s = off + j;
+                const double dx = (double)x - (double)im.sx[s], dy = (double)y - (double)im.sy[s];
+                const double dr = IR - (double)im.sr[s], dg = IG - (double)im.sg[s],
+                             db = IB - (double)im.sb[s];
+                int h = 0;
+                if (persample)
+                    for (int w = 0; w < Wk; ++w) h += __popc(bx[w] ^ im.sbits[(size_t)w * im.n_samples + s]);
+                return -(dx * dx + dy * dy) * c_loc - (dr * dr + dg * dg + db * db) * c_col -
+                       (double)h * c_tex;
+            };
+            double mx = -INFINITY;
+            for (int j = lane; j < m; j += 32) mx = fmax(mx, expo(j));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            double sum = 0.0;
+            for (int j = lane; j < m; j += 32) sum += exp(expo(j) - mx);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) {
+                sL[wib][i] = mx + log(sum) - log((double)m) - log(PI2 * rho * rho) - col_norm;
+                if (!persample) {
+                    int h = 0;
+                    for (int w = 0; w < Wk; ++w) h += __popc(bx[w] ^ im.rep[i * Wk + w]);
+                    sT[wib][i] = -(double)h / (kappa_beta * rho);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int n = im.n_labels;
+            if (!persample) {
+                double tm = -INFINITY, ts = 0.0;
+                for (int i = 0; i < n; ++i) tm = fmax(tm, sT[wib][i]);
+                for (int i = 0; i < n; ++i) ts += exp(sT[wib][i] - tm);
+                const double tl = tm + log(ts);
+                for (int i = 0; i < n; ++i) sL[wib][i] += sT[wib][i] - tl;
+            }
+            double lm = -INFINITY, ls = 0.0;
+            for (int i = 0; i < n; ++i) lm = fmax(lm, sL[wib][i]);
+            for (int i = 0; i < n; ++i) ls += exp(sL[wib][i] - lm);
+            const double lse = lm + log(ls);
+            for (int i = 0; i < n; ++i) {
+                im.neglog[(size_t)i * P + pix] = (float)(-sL[wib][i]);
+                if (im.post) im.post[(size_t)i * P + pix] = (float)exp(sL[wib][i] - lse);
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -652,7 +776,8 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
                                    int total_tiles, SampleTables t, int n_samples, int k,
                                    float Cc, const int32_t* __restrict__ perm,
                                    uint8_t* __restrict__ blob, int2* __restrict__ tile_c,
-                                   TcImage desc, TcImage* __restrict__ desc_dst) {
+                                   float* __restrict__ imax2, TcImage desc,
+                                   TcImage* __restrict__ desc_dst) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid == 0) *desc_dst = desc;  // this image's descriptor for the sum launch
@@ -703,7 +828,9 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
     uint32_t lw[8] = {0, 0, 0, 0, 0, 0, pack2(bf16_bits(1073741824.f), 0), 0};
     if (valid) {
         const float R = t.sr[s], G = t.sg[s], B = t.sb[s];
-        const float qv = -Cc * fmaf(R, R, fmaf(G, G, B * B));
+        const float i2 = fmaf(R, R, fmaf(G, G, B * B));
+        atomicMax(reinterpret_cast<int*>(imax2) + i, __float_as_int(i2));  // i2 >= 0
+        const float qv = -Cc * i2;
         uint16_t hr, lr, hg, lg, hb, lb, hq, lq;
         split_bf16(R, hr, lr);
         split_bf16(G, hg, lg);
@@ -749,16 +876,26 @@ cudaError_t prepare(const TcLaunch& L, cudaStream_t st) {
     d.rep = L.t.rep;
     d.neglog = L.neglog;
     d.post = L.post;
+    d.sx = L.t.sx;
+    d.sy = L.t.sy;
+    d.sr = L.t.sr;
+    d.sg = L.t.sg;
+    d.sb = L.t.sb;
+    d.sbits = L.t.sbits;
+    d.imax2 = L.imax2;
+    d.n_samples = L.n_samples;
     d.H = L.H;
     d.W = L.W;
     d.ntx = (L.W + TW - 1) / TW;
     d.n_labels = L.n_labels;
     d.first_item = L.first_item;
+    cudaError_t e = cudaMemsetAsync(L.imax2, 0, sizeof(float) * L.n_labels, st);
+    if (e != cudaSuccess) return e;
     morton_sort_kernel<<<L.n_chunks, 1024, 0, st>>>(L.d_label_off, L.n_labels, L.t, L.t.perm);
     build_tiles_kernel<TEX8, KS, PERSAMPLE>
         <<<(unsigned)(((long long)total_tiles * BN + 127) / 128), 128, 0, st>>>(
             L.d_label_off, L.d_tile_off, L.n_labels, total_tiles, L.t, L.n_samples, L.k, Cc,
-            L.t.perm, L.blob, L.t.tile_c, d, L.desc);
+            L.t.perm, L.blob, L.t.tile_c, L.imax2, d, L.desc);
     return cudaGetLastError();
 }
 
@@ -778,11 +915,19 @@ cudaError_t sum(const TcImage* descs, int n_images, int n_items, const TcSumPara
     a.kappa_beta = p.kappa_beta;
     a.sigma_c2 = p.sigma_c2;
     a.d_err = p.d_err;
+    a.fb_list = p.fb_list;
+    a.fb_count = p.fb_count;
+    a.fb_cap = p.fb_cap;
+    a.l_tol = p.l_tol;
     cudaError_t e = cudaFuncSetAttribute(sum_tc_kernel<TEX8, KS, PERSAMPLE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.fb_count, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const int grid = n_items < p.n_sm ? n_items : p.n_sm;
     sum_tc_kernel<TEX8, KS, PERSAMPLE><<<grid, THREADS, C::smem_bytes, st>>>(a);
+    refine_fp64_kernel<<<2 * p.n_sm, 128, 0, st>>>(
+        descs, p.fb_list, p.fb_count, p.fb_cap, (p.k + 31) / 32, (double)p.alpha, (double)p.d_min,
+        (double)p.kappa_beta, (double)p.sigma_c2, PERSAMPLE, p.d_err);
     return cudaGetLastError();
 }
 
@@ -846,7 +991,8 @@ cudaError_t launch_sum_tc(const TcLaunch& L, cudaStream_t st) {
     one.first_item = 0;
     cudaError_t e = launch_tc_prepare(one, st);
     if (e != cudaSuccess) return e;
-    TcSumParams p{L.k, L.tex8, L.persample, L.alpha, L.d_min, L.kappa_beta, L.sigma_c2, L.d_err,
-                  L.n_sm};
+    TcSumParams p{L.k,       L.tex8,  L.persample, L.alpha,      L.d_min, L.kappa_beta,
+                  L.sigma_c2, L.d_err, L.n_sm,      L.fb_list,    L.fb_count,
+                  L.H * L.W,  L.l_tol};
     return launch_tc_sum(L.desc, 1, tc_pixel_tiles(L.H, L.W), p, st);
 }

@@ -113,3 +113,61 @@ def test_workload2_tc_sampled(env):
     pix = np.unique(rng.integers(0, P, 3000)).astype(np.int32)
     ref = oracle.data_term(pr, pix=pix)
     _check(L[:, pix], post[:, pix], ref)
+
+
+@pytest.mark.parametrize("mode,kw", [
+    (0, {"kappa_beta": 0.02}),  # texture exponents of hundreds: most rows below 2^-80
+    (1, {"sigma_c2": 2e-4}),    # colour exponents of hundreds in the Parzen sum
+])
+def test_fp64_recompute_of_underflowing_rows(env, mode, kw):
+    """Rows whose FP32 sum of 2^e (e <= 0) falls below the floor are recomputed
+    in double precision on the GPU; the result then matches the FP64 oracle
+    to float rounding, and the rest of the image stays within the form's bar."""
+    import dataclasses
+
+    cs, ctx, torch = env
+    pr = synth.make_problem(40, 52, 3, 60, p=5, k=50, seed=21, cap_frac=0.9)
+    pr = dataclasses.replace(pr, params=dataclasses.replace(pr.params, **kw))
+    for precision in (2, 1):
+        L, post = _run(env, pr, precision, mode)
+        n_ref = ctx.refined_count()
+        assert n_ref > 0, "expected rows below the FP32 floor"
+        ref = oracle.data_term(pr, mode=mode)
+        rel = np.abs(L - ref["L"]) / np.maximum(np.abs(ref["L"]), 1.0)
+        assert float(np.max(rel)) <= L_TOL, float(np.max(rel))
+        # pixels with an extreme label row: many of them agree to ~float rounding
+        tight = np.max(rel, axis=0) <= 1e-6
+        assert tight.sum() >= n_ref
+        np.testing.assert_allclose(post.sum(0), 1.0, atol=1e-5)
+
+
+def _run_tol(env, pr, precision, mode, l_tol):
+    cs, ctx, torch = env
+    prm = cs.Params.from_synth(pr.params, precision=precision, mode=mode, l_tol=l_tol)
+    img = _dev(torch, pr.image)
+    c = ctx.codes(img, _dev(torch, pr.omega), _dev(torch, pr.mask), prm)
+    out = ctx.likelihood(img, c["bitmask"], pr.k, pr.label_off, _dev(torch, pr.sample_pix), prm)
+    n = ctx.refined_count()
+    nl = pr.n_labels
+    return -out["neglog"].cpu().numpy().reshape(nl, -1).astype(np.float64), n
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_row_bound_tolerance(env, mode):
+    """The a-priori row bound: with l_tol = 1e-5 every row either meets the
+    plain form's 1e-5 bar or is recomputed in FP64; the bar holds at every
+    tolerance; tighter tolerances recompute more pixels; l_tol = 0 recomputes
+    nothing at the default parameters."""
+    pr = synth.make_workload(1)
+    ref = oracle.data_term(pr, mode=mode)
+    P = pr.H * pr.W
+    counts = {}
+    for tol in (0.0, 1e-3, 1e-4, 1e-5):
+        L, n = _run_tol(env, pr, 2, mode, tol)
+        counts[tol] = n
+        rel = float(np.max(np.abs(L - ref["L"]) / np.maximum(np.abs(ref["L"]), 1.0)))
+        assert rel <= (max(tol, 1e-5) if tol > 0 else L_TOL), (tol, rel)
+    assert counts[0.0] == 0
+    assert counts[1e-3] <= counts[1e-4] <= counts[1e-5]
+    print(f"mode {mode}: pixels recomputed in FP64 at l_tol 1e-3 / 1e-4 / 1e-5: "
+          f"{counts[1e-3]} / {counts[1e-4]} / {counts[1e-5]} of {P}")
