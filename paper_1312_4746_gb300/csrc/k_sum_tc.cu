@@ -156,6 +156,8 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
 // then observes the (already completed) phase itself for memory ordering.
 __device__ __forceinline__ bool wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           int* d_err, int site) {
+    // fast path: the phase has already completed (every lane tests it)
+    if (__all_sync(0xffffffffu, tc::mbar_test_wait(bar, parity))) return true;
     int ok = 1;
     if ((threadIdx.x & 31) == 0) ok = wait_bar(bar, parity, abort_flag, d_err, site);
     ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -509,9 +511,10 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                             }
                         }
                     }
+                    // tcgen05.wait::ld is warp-collective: every lane's loads
+                    // are complete here; one elected lane releases the buffer
                     tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(tmem_empty + b);
+                    tc::mbar_arrive_elect(tmem_empty + b);
                 }
                 if (!ok) break;
                 // merge the EPQ column parts of each pixel. Four exchange
