@@ -184,54 +184,62 @@ __device__ __forceinline__ void loc_row_a(int px, int py, int dx, int dy, uint4&
                     pack2(one, one));
 }
 
-// Packed FP32 pairs (Blackwell f32x2 instructions: one issue, two lanes of work).
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+// Packed FP32 pairs (Blackwell f32x2 instructions: one issue, two lanes of
+// work) on 64-bit registers holding (low, high) = (element 0, element 1).
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
     return d;
 }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// 2^x of both halves.
+__device__ __forceinline__ uint64_t ex2x2(uint64_t v) {
+    uint64_t d;
+    asm("{\n\t.reg .f32 x, y;\n\tmov.b64 {x, y}, %1;\n\t"
+        "ex2.approx.ftz.f32 x, x;\n\tex2.approx.ftz.f32 y, y;\n\t"
+        "mov.b64 %0, {x, y};\n\t}"
+        : "=l"(d)
+        : "l"(v));
+    return d;
+}
+__device__ __forceinline__ float lo32(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi32(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
 // Sum over 16 columns (nv of them valid) of one pixel row of 2^e, with
-// e = nA Dl + Bt D1 + nKR (log2 units, shifted full exponents), added to (S, Cc) by
-// TwoSum; returns the chunk's sum. A full chunk takes the packed path.
-__device__ __forceinline__ float sum16(const uint32_t (&r1)[16], const uint32_t (&rl)[16], int nv,
-                                       float nA, float Bt, float nKR, float& S, float& Cc) {
+// e = nA Dl + Bt D1 + nKR (log2 units, shifted full exponents), added to
+// (S, Cc) by TwoSum; returns the chunk's sum. A full chunk takes the packed
+// path. r1 / rl hold D1 / Dl as packed column pairs.
+__device__ __forceinline__ float sum16(const uint64_t (&r1)[8], const uint64_t (&rl)[8], int nv,
+                                       uint64_t na2, uint64_t bt2, uint64_t k2, float& S,
+                                       float& Cc) {
     float ts;
     if (nv >= 16) {
-        const float2 bt2 = make_float2(Bt, Bt), na2 = make_float2(nA, nA), k2 = make_float2(nKR, nKR);
-        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+        uint64_t acc0 = 0, acc1 = 0;  // (0.f, 0.f)
 #pragma unroll
-        for (int u = 0; u < 16; u += 4) {
-            float2 v0 = fma2(bt2, make_float2(__uint_as_float(r1[u]), __uint_as_float(r1[u + 1])), k2);
-            float2 v1 = fma2(bt2, make_float2(__uint_as_float(r1[u + 2]), __uint_as_float(r1[u + 3])), k2);
-            v0 = fma2(na2, make_float2(__uint_as_float(rl[u]), __uint_as_float(rl[u + 1])), v0);
-            v1 = fma2(na2, make_float2(__uint_as_float(rl[u + 2]), __uint_as_float(rl[u + 3])), v1);
-            acc0 = add2(acc0, make_float2(ex2f(v0.x), ex2f(v0.y)));
-            acc1 = add2(acc1, make_float2(ex2f(v1.x), ex2f(v1.y)));
+        for (int u = 0; u < 8; u += 2) {
+            const uint64_t v0 = fma2(na2, rl[u], fma2(bt2, r1[u], k2));
+            const uint64_t v1 = fma2(na2, rl[u + 1], fma2(bt2, r1[u + 1], k2));
+            acc0 = add2(acc0, ex2x2(v0));
+            acc1 = add2(acc1, ex2x2(v1));
         }
-        const float2 t = add2(acc0, acc1);
-        ts = t.x + t.y;
+        const uint64_t t = add2(acc0, acc1);
+        ts = lo32(t) + hi32(t);
     } else {
         float t0 = 0.f, t1 = 0.f;
 #pragma unroll
-        for (int u = 0; u < 16; u += 2) {
-            const float v0 = fmaf(nA, __uint_as_float(rl[u]), fmaf(Bt, __uint_as_float(r1[u]), nKR));
-            const float v1 = fmaf(nA, __uint_as_float(rl[u + 1]), fmaf(Bt, __uint_as_float(r1[u + 1]), nKR));
-            t0 += u < nv ? ex2f(v0) : 0.f;
-            t1 += u + 1 < nv ? ex2f(v1) : 0.f;
+        for (int u = 0; u < 8; ++u) {
+            const uint64_t v = fma2(na2, rl[u], fma2(bt2, r1[u], k2));
+            t0 += 2 * u < nv ? ex2f(lo32(v)) : 0.f;
+            t1 += 2 * u + 1 < nv ? ex2f(hi32(v)) : 0.f;
         }
         ts = t0 + t1;
     }
@@ -477,6 +485,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(acol_full + cb);
 
+                const uint64_t na2 = pk2(nA, nA), bt2 = pk2(Bt, Bt);
                 const int m_i = im.label_off[i + 1] - im.label_off[i];
                 const float shift = (float)(96 - (32 - __clz(m_i - 1)));  // 96 - ceil(log2 m)
                 const float R0s = R0 + shift;
@@ -498,14 +507,13 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     const int cbase = hf * CPW;
                     const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
                     if (cbase < nvalid) {  // warp-uniform
-                        uint32_t x1[16], xl[16];
+                        const uint64_t k2 = pk2(nKR, nKR);
+                        uint64_t x1[8], xl[8];
 #pragma unroll
                         for (int ch = 0; ch < CPW / 16; ++ch) {
                             if (cbase + 16 * ch < nvalid) {  // warp-uniform
-                                tc::tmem_ld16(lb + 16u * ch, x1);
-                                tc::tmem_ld16(lb + 256u + 16u * ch, xl);
-                                tc::tmem_ld_wait();
-                                wK = fmaf(sum16(x1, xl, nvalid - cbase - 16 * ch, nA, Bt, nKR, S,
+                                tc::tmem_ld16x2_wait(lb + 16u * ch, lb + 256u + 16u * ch, x1, xl);
+                                wK = fmaf(sum16(x1, xl, nvalid - cbase - 16 * ch, na2, bt2, k2, S,
                                                 Ccomp),
                                           K, wK);
                             }
