@@ -401,12 +401,14 @@ SumArgs cs_sum_args(const LikPlan& L, const float* img, const uint32_t* bitmask,
 }
 
 TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uint32_t* bitmask,
-                      const cs_params* prm, float* neglog, float* post) {
+                      const int32_t* sample_pix, const cs_params* prm, float* neglog,
+                      float* post) {
     TcLaunch T{};
     T.img = img;
     T.H = L.H;
     T.W = L.W;
     T.bitmask = bitmask;
+    T.sample_pix = sample_pix;
     T.k = L.k;
     T.n_labels = L.n_labels;
     T.d_label_off = L.d_off;
@@ -436,10 +438,12 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
     return T;
 }
 
+// Gather and sum; with `sorted` the tensor-core sample order was already
+// enqueued (cs_data_term sorts on the side stream).
 static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
                                const uint32_t* bitmask, const int32_t* sample_pix,
                                const cs_params* prm, float* neglog, float* post,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool sorted = false) {
     cudaError_t e;
     {
         StageTimer tm(ctx, CS_STAGE_GATHER, st);
@@ -450,7 +454,8 @@ static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
     StageTimer tm(ctx, CS_STAGE_SUM, st);
     if (!L.tc_form) return launch_sum_plain(cs_sum_args(L, img, bitmask, prm, neglog, post), st);
     ctx->last_fb_count = L.fb_count;
-    return launch_sum_tc(cs_tc_launch(ctx, L, img, bitmask, prm, neglog, post), st);
+    return launch_sum_tc(cs_tc_launch(ctx, L, img, bitmask, sample_pix, prm, neglog, post),
+                         sorted, st);
 }
 
 extern "C" {
@@ -631,10 +636,15 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     if (e == cudaSuccess) e = enqueue_distances(ctx, L, sample_pix, ctx->side);
+    // the tensor-core sample order depends only on the scribbles as well
+    if (e == cudaSuccess && L.tc_form)
+        e = launch_tc_sort(cs_tc_launch(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post),
+                           ctx->side);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
     if (e == cudaSuccess) e = enqueue_codes(ctx, a, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join, 0);
-    if (e == cudaSuccess) e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st);
+    if (e == cudaSuccess)
+        e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st, L.tc_form);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return cs_check_launch(ctx, fn);
 }

@@ -134,8 +134,8 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
                               m.d.sample_pix, L.S, !L.persample, L.t, ss);
         if (e != cudaSuccess) break;
         if (b->tc) {
-            TcLaunch T = cs_tc_launch(ctx, L, m.d.img, m.codes.bitmask, &b->prm, m.d.neglog,
-                                      m.d.post);
+            TcLaunch T = cs_tc_launch(ctx, L, m.d.img, m.codes.bitmask, m.d.sample_pix, &b->prm,
+                                      m.d.neglog, m.d.post);
             T.desc = b->descs + s;
             T.first_item = b->first_item[s];
             e = launch_tc_prepare(T, ss);

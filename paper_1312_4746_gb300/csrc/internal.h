@@ -268,6 +268,7 @@ struct TcLaunch {
     const float* img;
     int H, W;
     const uint32_t* bitmask;
+    const int32_t* sample_pix;
     int k;
     int n_labels;
     const int32_t* d_label_off;
@@ -296,13 +297,18 @@ size_t tc_copy_bytes(int k, bool tex8, bool persample);
 int tc_tiles_per_label(int m);
 int tc_pixel_tiles(int H, int W);
 bool tc_supported(int k, bool tex8);
-// Morton sort and sample tiles of one image; writes *L.desc.
+// Morton order of the samples (needs only the label offsets and sample
+// pixels), then the sample tiles (needs the gathered tables; writes *L.desc),
+// or both.
+cudaError_t launch_tc_sort(const TcLaunch& L, cudaStream_t st);
+cudaError_t launch_tc_tiles(const TcLaunch& L, cudaStream_t st);
 cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st);
 // One persistent launch over the items of n_images prepared images.
 cudaError_t launch_tc_sum(const TcImage* descs, int n_images, int n_items, const TcSumParams& p,
                           cudaStream_t st);
-// Both, for a single image (L.desc must be set).
-cudaError_t launch_sum_tc(const TcLaunch& L, cudaStream_t st);
+// Preparation (the tiles only when `sorted`) and the sum, for a single image
+// (L.desc must be set).
+cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st);
 
 // Validation and planning helpers shared by the entry points.
 cs_status cs_check_image(cs_ctx* ctx, const char* fn, int H, int W, int k);
@@ -318,7 +324,8 @@ void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2);
 SumArgs cs_sum_args(const LikPlan& L, const float* img, const uint32_t* bitmask,
                     const cs_params* prm, float* neglog, float* post);
 TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uint32_t* bitmask,
-                      const cs_params* prm, float* neglog, float* post);
+                      const int32_t* sample_pix, const cs_params* prm, float* neglog,
+                      float* post);
 
 // Learned surrogate (MLP) kernels.
 int mlp_param_count(int n);

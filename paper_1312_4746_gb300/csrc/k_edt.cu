@@ -10,7 +10,10 @@
 //      envelope of the parabolas (y - q)^2 + h(q)^2 over the rows q with
 //      finite h, built in one sweep and read back in a second; intersection
 //      abscissae are compared as exact rationals with 64-bit cross products,
-//      so the result equals the brute-force minimum bit for bit.
+//      so the result equals the brute-force minimum bit for bit. For images
+//      with few columns and rows (labels x width < 16384, height <= 64) an
+//      outward scan per pixel with early exit gives the same minimum with
+//      far more parallelism.
 // The sample gather builds SoA tables of every sample (location, colour,
 // co-support bitmask and its popcount) and, for the factorised form, the
 // majority co-support of each label (Eq. tex-rep: bit set iff 2 * count >= m).
@@ -160,6 +163,39 @@ __global__ void cols_envelope_kernel(int H, int W, int n_labels, const int32_t* 
     }
 }
 
+// Column pass for small images (one thread per label and pixel, x fastest):
+// D(y) = min over rows q of h(q)^2 + (y - q)^2, scanning q outwards from y
+// and stopping once (y - q)^2 alone reaches the best value found, which no
+// farther row can beat. Exact (integer arithmetic); O(min(H, sqrt(D))) per
+// pixel, so it is chosen only for short images whose envelope pass has too
+// few columns to fill the GPU.
+__global__ void cols_scan_kernel(int H, int W, int n_labels, const int32_t* __restrict__ h,
+                                 int32_t* __restrict__ dist2) {
+    const long long P = (long long)H * W;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= P * n_labels) return;
+    const int i = (int)(tid / P);
+    const int rem = (int)(tid % P), y = rem / W, x = rem % W;
+    const int32_t* col = h + (size_t)i * P + x;
+    const int32_t h0 = col[(size_t)y * W];
+    int32_t D = h0 == INF ? INF : h0 * h0;
+    for (int d = 1; d < H; ++d) {
+        const int32_t d2 = d * d;
+        if (d2 >= D) break;
+        const bool up = y >= d, dn = y + d < H;
+        if (!up && !dn) break;
+        if (up) {
+            const int32_t a = col[(size_t)(y - d) * W];
+            if (a != INF) D = min(D, a * a + d2);
+        }
+        if (dn) {
+            const int32_t b = col[(size_t)(y + d) * W];
+            if (b != INF) D = min(D, b * b + d2);
+        }
+    }
+    dist2[(size_t)i * P + rem] = D;
+}
+
 __global__ void gather_kernel(const float* __restrict__ img, int W, long long P,
                               const uint32_t* __restrict__ bitmask, int Wk,
                               const int32_t* __restrict__ sample_pix, int n_samples,
@@ -220,6 +256,13 @@ cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
     rows_binary_kernel<<<(unsigned)((nrow * 32 + 127) / 128), 128, 0, st>>>(
         a.H, a.W, a.n_labels, a.seedbits, a.colbuf);
     const long long ncol = (long long)a.n_labels * a.W;
+    if (ncol < 16384 && a.H <= 64) {
+        // too few columns for the envelope pass to fill the GPU: scan per pixel
+        const long long n = (long long)a.n_labels * a.H * a.W;
+        cols_scan_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.H, a.W, a.n_labels,
+                                                                       a.colbuf, a.dist2);
+        return cudaGetLastError();
+    }
     // shared-memory stacks when at least 16 columns fit in 100 KB
     const size_t per_thread = (size_t)a.H * 2 * sizeof(int32_t);
     int tb = (int)std::min<size_t>(32, (100u * 1024u) / per_thread);

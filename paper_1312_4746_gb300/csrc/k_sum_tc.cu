@@ -723,7 +723,9 @@ __device__ __forceinline__ uint32_t morton16(uint32_t v) {
 }
 
 __global__ void __launch_bounds__(1024) morton_sort_kernel(const int32_t* __restrict__ label_off,
-                                                           int n_labels, SampleTables t,
+                                                           int n_labels,
+                                                           const int32_t* __restrict__ sample_pix,
+                                                           int W, long long P,
                                                            int32_t* __restrict__ perm) {
     __shared__ uint32_t key[4096];
     __shared__ int32_t idx[4096];
@@ -745,7 +747,9 @@ __global__ void __launch_bounds__(1024) morton_sort_kernel(const int32_t* __rest
     for (int e = threadIdx.x; e < n2; e += blockDim.x) {
         if (e < cnt) {
             const int sidx = start + e;
-            key[e] = morton16((uint32_t)t.sx[sidx]) | (morton16((uint32_t)t.sy[sidx]) << 1);
+            int pix = sample_pix[sidx];
+            if (pix < 0 || pix >= P) pix = 0;  // reported by the seed kernel
+            key[e] = morton16((uint32_t)(pix % W)) | (morton16((uint32_t)(pix / W)) << 1);
             idx[e] = sidx;
         } else {
             key[e] = 0xFFFFFFFFu;
@@ -873,7 +877,7 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
-cudaError_t prepare(const TcLaunch& L, cudaStream_t st) {
+cudaError_t tiles(const TcLaunch& L, cudaStream_t st) {
     const int total_tiles = L.total_tiles;
     const float Cc = 1.4426950408889634f / (2.f * L.sigma_c2);
     TcImage d{};
@@ -902,7 +906,6 @@ cudaError_t prepare(const TcLaunch& L, cudaStream_t st) {
     d.first_item = L.first_item;
     cudaError_t e = cudaMemsetAsync(L.imax2, 0, sizeof(float) * L.n_labels, st);
     if (e != cudaSuccess) return e;
-    morton_sort_kernel<<<L.n_chunks, 1024, 0, st>>>(L.d_label_off, L.n_labels, L.t, L.t.perm);
     build_tiles_kernel<TEX8, KS, PERSAMPLE>
         <<<(unsigned)(((long long)total_tiles * BN + 127) / 128), 128, 0, st>>>(
             L.d_label_off, L.d_tile_off, L.n_labels, total_tiles, L.t, L.n_samples, L.k, Cc,
@@ -982,10 +985,21 @@ bool tc_supported(int k, bool tex8) { return tex8 ? k <= 256 : k <= 128; }
 
 int tc_pixel_tiles(int H, int W) { return ((W + TW - 1) / TW) * ((H + TH - 1) / TH); }
 
-cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st) {
+cudaError_t launch_tc_sort(const TcLaunch& L, cudaStream_t st) {
+    morton_sort_kernel<<<L.n_chunks, 1024, 0, st>>>(L.d_label_off, L.n_labels, L.sample_pix, L.W,
+                                                    (long long)L.H * L.W, L.t.perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_tiles(const TcLaunch& L, cudaStream_t st) {
     return dispatch(L.k, L.tex8, L.persample, [&](auto t8, auto ks, auto ps) {
-        return prepare<decltype(t8)::value, decltype(ks)::value, decltype(ps)::value>(L, st);
+        return tiles<decltype(t8)::value, decltype(ks)::value, decltype(ps)::value>(L, st);
     });
+}
+
+cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st) {
+    cudaError_t e = launch_tc_sort(L, st);
+    return e != cudaSuccess ? e : launch_tc_tiles(L, st);
 }
 
 cudaError_t launch_tc_sum(const TcImage* descs, int n_images, int n_items, const TcSumParams& p,
@@ -997,10 +1011,10 @@ cudaError_t launch_tc_sum(const TcImage* descs, int n_images, int n_items, const
     });
 }
 
-cudaError_t launch_sum_tc(const TcLaunch& L, cudaStream_t st) {
+cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st) {
     TcLaunch one = L;
     one.first_item = 0;
-    cudaError_t e = launch_tc_prepare(one, st);
+    cudaError_t e = sorted ? launch_tc_tiles(one, st) : launch_tc_prepare(one, st);
     if (e != cudaSuccess) return e;
     TcSumParams p{L.k,       L.tex8,  L.persample, L.alpha,      L.d_min, L.kappa_beta,
                   L.sigma_c2, L.d_err, L.n_sm,      L.fb_list,    L.fb_count,

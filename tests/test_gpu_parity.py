@@ -232,3 +232,26 @@ def test_data_term_entry(env, precision):
     ref = oracle.data_term(pr, want_dist2=True)
     assert np.array_equal(one["bitmask"].cpu().numpy().view(np.uint32), ref["bits_px"])
     assert np.array_equal(one["dist2"].cpu().numpy().reshape(pr.n_labels, -1), ref["dist2"])
+
+
+@pytest.mark.parametrize("H,W,nl,m,seed", [
+    (12, 5500, 3, [40, 1, 300], 31),   # labels x width >= 16384: envelope column pass
+    (60, 90, 2, [1, 25], 32),          # short image, few columns: outward-scan column pass
+    (1030, 15, 2, [3, 9], 33),         # tall and narrow: envelope pass, global-memory stacks
+])
+def test_distance_transform_paths(env, H, W, nl, m, seed):
+    """Both column passes of the exact distance transform equal brute force."""
+    cs, ctx, torch = env
+    rng = np.random.default_rng(seed)
+    P = H * W
+    pix = [np.sort(rng.choice(P, mi, replace=False)) for mi in m]
+    off = np.concatenate([[0], np.cumsum(m)]).astype(np.int32)
+    smp = np.concatenate(pix).astype(np.int32)
+    img = rng.uniform(0, 1, (H, W, 3)).astype(np.float32)
+    k = 16
+    prm = cs.Params.default(p=3)
+    bits = torch.zeros((P, 1), dtype=torch.int32, device="cuda:0")
+    out = ctx.likelihood(_dev(torch, img), bits, k, off, _dev(torch, smp), prm, want_dist2=True)
+    ctx.sync()
+    ref = oracle.dist2(H, W, off, smp)
+    assert np.array_equal(out["dist2"].cpu().numpy().reshape(nl, -1), ref)
