@@ -214,40 +214,39 @@ __device__ __forceinline__ uint64_t ex2x2(uint64_t v) {
 __device__ __forceinline__ float lo32(uint64_t v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float hi32(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
-// Sum over 16 columns (nv of them valid) of one pixel row of 2^e, with
-// e = nA Dl + Bt D1 + nKR (log2 units, shifted full exponents), added to
-// (S, Cc) by TwoSum; returns the chunk's sum. A full chunk takes the packed
-// path. r1 / rl hold D1 / Dl as packed column pairs.
-__device__ __forceinline__ float sum16(const uint64_t (&r1)[8], const uint64_t (&rl)[8], int nv,
-                                       uint64_t na2, uint64_t bt2, uint64_t k2, float& S,
-                                       float& Cc) {
-    float ts;
-    if (nv >= 16) {
-        uint64_t acc0 = 0, acc1 = 0;  // (0.f, 0.f)
+// Sum over 16 columns of one pixel row of 2^e, e = nA Dl + Bt D1 + nKR
+// (log2 units, shifted full exponents); r1 / rl hold D1 / Dl as packed
+// column pairs. Full chunk: packed arithmetic; partial chunk: the first nv.
+__device__ __forceinline__ float sum16_full(const uint64_t (&r1)[8], const uint64_t (&rl)[8],
+                                            uint64_t na2, uint64_t bt2, uint64_t k2) {
+    uint64_t acc0 = 0, acc1 = 0;  // (0.f, 0.f)
 #pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-            const uint64_t v0 = fma2(na2, rl[u], fma2(bt2, r1[u], k2));
-            const uint64_t v1 = fma2(na2, rl[u + 1], fma2(bt2, r1[u + 1], k2));
-            acc0 = add2(acc0, ex2x2(v0));
-            acc1 = add2(acc1, ex2x2(v1));
-        }
-        const uint64_t t = add2(acc0, acc1);
-        ts = lo32(t) + hi32(t);
-    } else {
-        float t0 = 0.f, t1 = 0.f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const uint64_t v = fma2(na2, rl[u], fma2(bt2, r1[u], k2));
-            t0 += 2 * u < nv ? ex2f(lo32(v)) : 0.f;
-            t1 += 2 * u + 1 < nv ? ex2f(hi32(v)) : 0.f;
-        }
-        ts = t0 + t1;
+    for (int u = 0; u < 8; u += 2) {
+        const uint64_t v0 = fma2(na2, rl[u], fma2(bt2, r1[u], k2));
+        const uint64_t v1 = fma2(na2, rl[u + 1], fma2(bt2, r1[u + 1], k2));
+        acc0 = add2(acc0, ex2x2(v0));
+        acc1 = add2(acc1, ex2x2(v1));
     }
+    const uint64_t t = add2(acc0, acc1);
+    return lo32(t) + hi32(t);
+}
+__device__ __forceinline__ float sum16_part(const uint64_t (&r1)[8], const uint64_t (&rl)[8],
+                                            int nv, uint64_t na2, uint64_t bt2, uint64_t k2) {
+    float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const uint64_t v = fma2(na2, rl[u], fma2(bt2, r1[u], k2));
+        t0 += 2 * u < nv ? ex2f(lo32(v)) : 0.f;
+        t1 += 2 * u + 1 < nv ? ex2f(hi32(v)) : 0.f;
+    }
+    return t0 + t1;
+}
+// (S, Cc) += ts by TwoSum.
+__device__ __forceinline__ void two_sum(float ts, float& S, float& Cc) {
     const float sn = S + ts;
     const float bb = sn - S;
     Cc += (S - (sn - bb)) + (ts - bb);
     S = sn;
-    return ts;
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
@@ -506,16 +505,27 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     const float nKR = fmaf(nA, K, R0s);
                     const int cbase = hf * CPW;
                     const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
-                    if (cbase < nvalid) {  // warp-uniform
-                        const uint64_t k2 = pk2(nKR, nKR);
-                        uint64_t x1[8], xl[8];
+                    const uint64_t k2 = pk2(nKR, nKR);
+                    uint64_t x1[8], xl[8];
+                    if (cbase + CPW <= nvalid) {  // warp-uniform: all columns valid
+                        float ts = 0.f;
 #pragma unroll
                         for (int ch = 0; ch < CPW / 16; ++ch) {
-                            if (cbase + 16 * ch < nvalid) {  // warp-uniform
+                            tc::tmem_ld16x2_wait(lb + 16u * ch, lb + 256u + 16u * ch, x1, xl);
+                            ts += sum16_full(x1, xl, na2, bt2, k2);
+                        }
+                        two_sum(ts, S, Ccomp);
+                        wK = fmaf(ts, K, wK);
+                    } else if (cbase < nvalid) {  // warp-uniform: the label's last tile
+#pragma unroll
+                        for (int ch = 0; ch < CPW / 16; ++ch) {
+                            const int nv = nvalid - cbase - 16 * ch;
+                            if (nv > 0) {  // warp-uniform
                                 tc::tmem_ld16x2_wait(lb + 16u * ch, lb + 256u + 16u * ch, x1, xl);
-                                wK = fmaf(sum16(x1, xl, nvalid - cbase - 16 * ch, na2, bt2, k2, S,
-                                                Ccomp),
-                                          K, wK);
+                                const float ts = nv >= 16 ? sum16_full(x1, xl, na2, bt2, k2)
+                                                          : sum16_part(x1, xl, nv, na2, bt2, k2);
+                                two_sum(ts, S, Ccomp);
+                                wK = fmaf(ts, K, wK);
                             }
                         }
                     }
