@@ -38,6 +38,21 @@ WORKLOAD = 2
 WORKLOAD_NAME = "481x321 RGB, 5 labels x 2000 samples, 7x7 patches, Omega 98x49"
 
 
+def rank_seed(rank: int) -> int:
+    """Weak scaling: every rank draws its own image of the bench workload."""
+    return 1000 + WORKLOAD + 7919 * rank
+
+
+def combine(dev_ms, e2e_ms, pairs_rank, steps, world, reduce_max):
+    """Whole-job numbers from this rank's times: the max over ranks of the
+    device and end-to-end times (reduce_max: list of floats -> list of the
+    maxima over ranks), and the pairs of all ranks divided by them."""
+    dev_ms, e2e_ms = reduce_max([dev_ms, e2e_ms])
+    total = pairs_rank * world * steps
+    return {"value": total / (dev_ms * 1e-3), "e2e_value": total / (e2e_ms * 1e-3),
+            "ms_per_step": dev_ms / steps, "dev_ms": dev_ms, "e2e_ms": e2e_ms}
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -289,6 +304,46 @@ def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=Non
     return dev_ms, e2e_ms, stage, h2d, d2h
 
 
+def measure_batch(ctx, cs, torch, dev, n_images, reduce_max, world, runs=5):
+    """The batch workload (uneven images, one persistent tensor-core sum over
+    all of them) through cs_batch_*: autotuned, captured in a CUDA graph,
+    timed with CUDA events over `runs` replays after the tuning run."""
+    import dataclasses
+
+    from paper_1312_4746_gb300 import synth
+
+    probs = synth.make_batch(n_images)
+    probs = [dataclasses.replace(q, omega=probs[0].omega, mask=probs[0].mask) for q in probs]
+    pairs = float(sum(q.H * q.W * q.n_samples for q in probs))
+    om = torch.from_numpy(probs[0].omega).to(dev)
+    mask = torch.from_numpy(probs[0].mask).to(dev)
+    inp = [{"img": torch.from_numpy(q.image).to(dev),
+            "sample_pix": torch.from_numpy(q.sample_pix).to(dev), "label_off": q.label_off}
+           for q in probs]
+    prm = cs.Params.from_synth(probs[0].params, precision=FORMS["fp8"])
+    b = ctx.batch(inp, om, mask, prm, flags=cs.BATCH_GRAPH | cs.BATCH_AUTOTUNE)
+    b.run()  # tunes, then captures the graph
+    b.run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(runs):
+        b.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    (ms,) = reduce_max([e0.elapsed_time(e1) / runs])
+    cfg = b.config()
+    b.close()
+    return {"workload": f"{n_images} images 240-640 x 160-480, 2-10 labels x 500-5000 "
+                        "samples, 7x7 patches, Omega 98x49 (seeds 100000+b)",
+            "form": FORM_NAMES["fp8"], "pairs_per_run": pairs, "ms_per_run": ms,
+            "pairs_per_s": pairs * world / (ms * 1e-3), "runs": runs,
+            "graph": True, "autotuned": {"n_streams": cfg["n_streams"],
+                                         "order": "by cost" if cfg["order"] == 0 else "given"},
+            "l2": "not flushed: each run reads and writes about 1 GB (images, bitmasks, distances, outputs), far above L2"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,6 +353,8 @@ def main():
     ap.add_argument("--form", default="fp8", choices=list(FORMS))
     ap.add_argument("--ref-pixels", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-images", type=int, default=64,
+                    help="also time a batch of this many uneven images (0: skip)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -322,7 +379,7 @@ def main():
     from paper_1312_4746_gb300 import synth
 
     # weak scaling: every rank gets its own image of the same shape
-    pr = synth.make_workload(WORKLOAD, seed=1000 + WORKLOAD + 7919 * rank)
+    pr = synth.make_workload(WORKLOAD, seed=rank_seed(rank))
     P = pr.H * pr.W
     Wk = (pr.k + 31) // 32
     ctx = cs.Context(local)
@@ -348,10 +405,11 @@ def main():
         return [float(v) for v in t]
 
     head = args.form
-    dev_ms, e2e_ms = reduce_max([res[head][0], res[head][1]])
-    total_pairs = pairs_rank * world * args.steps
-    value = total_pairs / (dev_ms * 1e-3)
-    e2e_value = total_pairs / (e2e_ms * 1e-3)
+    comb = combine(res[head][0], res[head][1], pairs_rank, args.steps, world, reduce_max)
+    dev_ms, value, e2e_value = comb["dev_ms"], comb["value"], comb["e2e_value"]
+    batch = None
+    if args.batch_images > 0:
+        batch = measure_batch(ctx, cs, torch, dev, args.batch_images, reduce_max, world)
     if rank == 0:
         peaks, src = _peaks()
         clocks = clk.summary()
@@ -395,6 +453,8 @@ def main():
             "forms": forms_out,
             "clocks": clocks,
         }
+        if batch is not None:
+            line["batch"] = batch
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pr)
         print(json.dumps(line))
