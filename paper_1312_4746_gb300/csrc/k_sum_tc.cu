@@ -151,6 +151,24 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     return false;
 }
 
+// Single-thread bounded wait by polling (no suspension, so the thread reacts
+// as soon as the phase completes); the timer is read every 256 polls.
+__device__ __forceinline__ bool spin_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                         int* d_err, int site) {
+    if (*abort_flag) return false;
+    uint64_t deadline = 0;
+    for (uint32_t n = 0;; ++n) {
+        if (tc::mbar_test_wait(bar, parity)) return true;
+        if ((n & 255u) == 255u) {
+            const uint64_t now = tc::globaltimer();
+            if (deadline == 0) deadline = now + WAIT_NS;
+            else if (now > deadline) break;
+        }
+    }
+    set_abort(abort_flag, d_err, site);
+    return false;
+}
+
 // Warp-uniform bounded wait: lane 0 waits with the deadline and broadcasts
 // the outcome, so a timeout can never split the warp; on success every lane
 // then observes the (already completed) phase itself for memory ordering.
@@ -353,8 +371,8 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     const int nt = tiles_of(im.tile_off, i);
                     for (int t = 0; ok && t < nt; ++t, ++it) {
                         const int s = (int)(it % STAGES), b = (int)(it & 1);
-                        ok = wait_bar(full + s, (uint32_t)((it / STAGES) & 1), abort_flag, a.d_err, 5) &&
-                             wait_bar(tmem_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag,
+                        ok = spin_bar(full + s, (uint32_t)((it / STAGES) & 1), abort_flag, a.d_err, 5) &&
+                             spin_bar(tmem_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag,
                                       a.d_err, 6);
                         if (!ok) break;
                         tc::fence_after_sync();
