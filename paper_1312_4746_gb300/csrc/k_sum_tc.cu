@@ -169,6 +169,27 @@ __device__ __forceinline__ bool spin_bar(uint64_t* bar, uint32_t parity, volatil
     return false;
 }
 
+// Warp-uniform polling wait (every lane tests the same phase, so the warp
+// stays converged; the timer is read every 256 polls).
+__device__ __forceinline__ bool spin_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* d_err, int site) {
+    uint64_t deadline = 0;
+    for (uint32_t n = 0;; ++n) {
+        if (__all_sync(0xffffffffu, tc::mbar_test_wait(bar, parity))) return true;
+        if ((n & 255u) == 255u) {
+            int late = 0;
+            if ((threadIdx.x & 31) == 0) {
+                const uint64_t now = tc::globaltimer();
+                if (deadline == 0) deadline = now + WAIT_NS;
+                else late = now > deadline || *abort_flag;
+            }
+            if (__shfl_sync(0xffffffffu, late, 0)) break;
+        }
+    }
+    if ((threadIdx.x & 31) == 0) set_abort(abort_flag, d_err, site);
+    return false;
+}
+
 // Warp-uniform bounded wait: lane 0 waits with the deadline and broadcasts
 // the outcome, so a timeout can never split the warp; on success every lane
 // then observes the (already completed) phase itself for memory ordering.
@@ -513,7 +534,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     const int2 c = c_next;
                     if (t + 1 < nt) c_next = im.tile_c[t0 + t + 1];
                     const int b = (int)(it & 1);
-                    ok = wait_warp(tmem_full + b, (uint32_t)((it >> 1) & 1), abort_flag, a.d_err, 10);
+                    ok = spin_warp(tmem_full + b, (uint32_t)((it >> 1) & 1), abort_flag, a.d_err, 10);
                     if (!ok) break;
                     tc::fence_after_sync();
                     const int nvalid = min(BN, m_i - t * BN);
