@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 for (int t = 0; ok && t < nt; ++t, ++it) {
                     const int s = (int)(it % STAGES);
                     const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-                    ok = wait_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1);
+                    ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1);
                     if (!ok) break;
                     uint8_t* st = ring + s * C::stage_bytes;
                     const int2 c = im.tile_c[t0 + t];
