@@ -60,7 +60,6 @@ namespace {
 
 constexpr int BM = 128, BN = 128;
 constexpr int TW = 16, TH = 8;          // pixel tile 16 x 8
-constexpr int STAGES = 3;
 constexpr int EPQ = 4;                  // epilogue warps per TMEM lane quadrant
 constexpr int EPI_WARPS = 4 * EPQ;      // 16
 constexpr int CPW = BN / EPQ;           // columns per epilogue warp per tile (32)
@@ -101,6 +100,7 @@ __device__ __forceinline__ int image_of(const TcArgs& a, int g) {
 
 template <bool TEX8, int KS, bool PERSAMPLE>
 struct Cfg {
+    static constexpr int STAGES = KS <= 5 ? 4 : 3;  // sample-tile ring depth (shared memory)
     static constexpr int tex_bytes = PERSAMPLE ? KS * 4096 : 0;
     static constexpr int col_off = tex_bytes;
     static constexpr int bloc_off = tex_bytes + 4096;         // sample-side location slab
@@ -143,14 +143,6 @@ __device__ __forceinline__ void set_abort(volatile int* abort_flag, int* d_err, 
     if (atomicCAS(d_err, 0, CS_DEVERR_TIMEOUT) == 0) d_err[1] = site;
 }
 
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                         int* d_err, int site) {
-    if (*abort_flag) return false;
-    if (tc::mbar_wait(bar, parity, tc::globaltimer() + WAIT_NS)) return true;
-    set_abort(abort_flag, d_err, site);
-    return false;
-}
-
 // Single-thread bounded wait by polling (no suspension, so the thread reacts
 // as soon as the phase completes); the timer is read every 256 polls.
 __device__ __forceinline__ bool spin_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
@@ -188,20 +180,6 @@ __device__ __forceinline__ bool spin_warp(uint64_t* bar, uint32_t parity, volati
     }
     if ((threadIdx.x & 31) == 0) set_abort(abort_flag, d_err, site);
     return false;
-}
-
-// Warp-uniform bounded wait: lane 0 waits with the deadline and broadcasts
-// the outcome, so a timeout can never split the warp; on success every lane
-// then observes the (already completed) phase itself for memory ordering.
-__device__ __forceinline__ bool wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* d_err, int site) {
-    // fast path: the phase has already completed (every lane tests it)
-    if (__all_sync(0xffffffffu, tc::mbar_test_wait(bar, parity))) return true;
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = wait_bar(bar, parity, abort_flag, d_err, site);
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (ok) tc::mbar_wait(bar, parity, tc::globaltimer() + WAIT_NS);
-    return ok != 0;
 }
 
 __device__ __forceinline__ int tiles_of(const int32_t* tile_off, int i) {
@@ -297,9 +275,9 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
     uint8_t* acol = smem + C::acol_off;
     float4* xchg = reinterpret_cast<float4*>(smem + C::xchg_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::bar_off);
-    uint64_t* full = bars;                    // [STAGES] producer arrival + TMA bytes
-    uint64_t* empty = bars + STAGES;          // [STAGES] MMA commit
-    uint64_t* tmem_full = bars + 2 * STAGES;  // [2] MMA commit
+    uint64_t* full = bars;                    // [C::STAGES] producer arrival + TMA bytes
+    uint64_t* empty = bars + C::STAGES;          // [C::STAGES] MMA commit
+    uint64_t* tmem_full = bars + 2 * C::STAGES;  // [2] MMA commit
     uint64_t* tmem_empty = tmem_full + 2;     // [2] epilogue warps
     uint64_t* acol_full = tmem_full + 4;      // [2] epilogue warps
     uint64_t* acol_empty = tmem_full + 6;     // [2] MMA commit
@@ -312,7 +290,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < C::STAGES; ++s) {
             tc::mbar_init(full + s, 1);
             tc::mbar_init(empty + s, 1);
         }
@@ -348,8 +326,8 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             for (int i = 0; ok && i < im.n_labels; ++i) {
                 const int t0 = im.tile_off[i], nt = tiles_of(im.tile_off, i);
                 for (int t = 0; ok && t < nt; ++t, ++it) {
-                    const int s = (int)(it % STAGES);
-                    const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                    const int s = (int)(it % C::STAGES);
+                    const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
                     ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1);
                     if (!ok) break;
                     uint8_t* st = ring + s * C::stage_bytes;
@@ -374,8 +352,8 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
         }
         // drain: copies still in flight must land before the CTA exits
         if (lane == 0)
-            for (uint32_t d = (it > STAGES ? it - STAGES : 0); d < it; ++d)
-                tc::mbar_wait(full + (int)(d % STAGES), (uint32_t)((d / STAGES) & 1),
+            for (uint32_t d = (it > C::STAGES ? it - C::STAGES : 0); d < it; ++d)
+                tc::mbar_wait(full + (int)(d % C::STAGES), (uint32_t)((d / C::STAGES) & 1),
                               tc::globaltimer() + WAIT_NS);
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
@@ -385,14 +363,14 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             long long last = -1;
             for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x, ++lpt) {
                 const TcImage& im = a.images[image_of(a, g)];
-                ok = wait_bar(atex_full, (uint32_t)(lpt & 1), abort_flag, a.d_err, 3);
+                ok = spin_bar(atex_full, (uint32_t)(lpt & 1), abort_flag, a.d_err, 3);
                 for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
                     const int cb = (int)(li & 1);
-                    ok = wait_bar(acol_full + cb, (uint32_t)((li >> 1) & 1), abort_flag, a.d_err, 4);
+                    ok = spin_bar(acol_full + cb, (uint32_t)((li >> 1) & 1), abort_flag, a.d_err, 4);
                     const int nt = tiles_of(im.tile_off, i);
                     for (int t = 0; ok && t < nt; ++t, ++it) {
-                        const int s = (int)(it % STAGES), b = (int)(it & 1);
-                        ok = spin_bar(full + s, (uint32_t)((it / STAGES) & 1), abort_flag, a.d_err, 5) &&
+                        const int s = (int)(it % C::STAGES), b = (int)(it & 1);
+                        ok = spin_bar(full + s, (uint32_t)((it / C::STAGES) & 1), abort_flag, a.d_err, 5) &&
                              spin_bar(tmem_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag,
                                       a.d_err, 6);
                         if (!ok) break;
@@ -454,7 +432,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 for (int w = 0; w < a.Wk; ++w) popx += __popc(bxp[w]);
             // texture operand rows: this warp writes slabs sl = hf, hf + EPQ, ...
             if (PERSAMPLE) {
-                ok = wait_warp(atex_empty, (uint32_t)((lpt & 1) ^ 1), abort_flag, a.d_err, 7);
+                ok = spin_warp(atex_empty, (uint32_t)((lpt & 1) ^ 1), abort_flag, a.d_err, 7);
                 if (!ok) break;
                 for (int sl = hf; sl < KS; sl += EPQ) {
                     // FP8: slab sl holds codes 32 sl .. 32 sl + 31 (bitmask word sl);
@@ -504,7 +482,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 const float R0 = (PERSAMPLE ? -Bt * (float)popx : 0.f) - Cc * I2;
                 // colour operand row (16 bf16): this warp writes half hf (hf < 2)
                 const int cb = (int)(li & 1);
-                ok = wait_warp(acol_empty + cb, (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag, a.d_err, 8);
+                ok = spin_warp(acol_empty + cb, (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag, a.d_err, 8);
                 if (!ok) break;
                 if (hf < 2) {
                     uint16_t h0, l0, h1, l1;
@@ -586,7 +564,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(xbar);
                 } else {
-                    ok = wait_warp(xbar, (uint32_t)((li >> 2) & 1), abort_flag, a.d_err, 11);
+                    ok = spin_warp(xbar, (uint32_t)((li >> 2) & 1), abort_flag, a.d_err, 11);
                     if (!ok) break;
                     float Sm = S, Cm = Ccomp, wKm = wK;
 #pragma unroll
