@@ -87,67 +87,87 @@ __global__ void rows_binary_kernel(int H, int W, int n_labels, const uint32_t* _
     }
 }
 
-// Pass 2 (one thread per label and column, coalesced across a warp): lower
-// envelope over y of the parabolas (y - q)^2 + h(q)^2. The stack of envelope
-// rows v[k] and their offsets F[k] = h(v_k)^2 + v_k^2 lives either in shared
-// memory (stride = threads per block) or in global scratch (stride = total
-// threads); intersections are compared as exact rationals in 64 bits.
+// Column pass, split: in each block of 32 columns the first warp builds the
+// lower envelope of every column (one thread per column, as above), then
+// all NSEG warps read it back, warp s for the rows [s H / NSEG, (s + 1) H /
+// NSEG); each thread finds the envelope segment of its first row by binary
+// search over the breakpoints (the same exact comparison, monotone in the
+// segment index) and walks on from there.
+constexpr int NSEG = 4;
+
 template <bool SHARED>
-__global__ void cols_envelope_kernel(int H, int W, int n_labels, const int32_t* __restrict__ h,
-                                     int32_t* __restrict__ gv, int32_t* __restrict__ gF,
-                                     int32_t* __restrict__ dist2) {
+__global__ void __launch_bounds__(32 * NSEG) cols_envelope_split_kernel(
+    int H, int W, int n_labels, const int32_t* __restrict__ h, int32_t* __restrict__ gv,
+    int32_t* __restrict__ gF, int32_t* __restrict__ dist2) {
     extern __shared__ int32_t smem[];
-    const long long nthr = (long long)n_labels * W;
-    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= nthr) return;
-    const int i = (int)(tid / W), x = (int)(tid % W);
+    __shared__ int s_kk[32];
+    const long long ncol = (long long)n_labels * W;
+    const int c = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const long long col_id = blockIdx.x * 32ll + c;
+    const bool valid = col_id < ncol;
+    const int i = valid ? (int)(col_id / W) : 0, x = valid ? (int)(col_id % W) : 0;
     int32_t *v, *F;
     long long stride;
     if (SHARED) {
-        v = smem + threadIdx.x;
-        F = smem + (size_t)H * blockDim.x + threadIdx.x;
-        stride = blockDim.x;
+        v = smem + c;
+        F = smem + (size_t)H * 32 + c;
+        stride = 32;
     } else {
-        v = gv + tid;
-        F = gF + tid;
-        stride = nthr;
+        v = gv + col_id;
+        F = gF + col_id;
+        stride = ncol;
     }
     const int32_t* col = h + (size_t)i * H * W + x;
-    int32_t* out = dist2 + (size_t)i * H * W + x;
-    int kk = -1;
-    constexpr int PF = 16;  // rows of h fetched ahead (independent loads)
-    for (int q0 = 0; q0 < H; q0 += PF) {
-        int32_t hv[PF];
+    if (seg == 0 && valid) {
+        int kk = -1;
+        constexpr int PF = 16;  // rows of h fetched ahead (independent loads)
+        for (int q0 = 0; q0 < H; q0 += PF) {
+            int32_t hv[PF];
 #pragma unroll
-        for (int u = 0; u < PF; ++u) hv[u] = q0 + u < H ? col[(size_t)(q0 + u) * W] : INF;
+            for (int u = 0; u < PF; ++u) hv[u] = q0 + u < H ? col[(size_t)(q0 + u) * W] : INF;
 #pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const int q = q0 + u;
-            const int32_t hq = hv[u];
-            if (hq == INF) continue;
-            const int32_t Fq = hq * hq + q * q;
-            while (kk > 0) {
-                const int vk = v[kk * stride], vp = v[(kk - 1) * stride];
-                const int32_t Fv = F[kk * stride], Fp = F[(kk - 1) * stride];
-                // drop v[kk] if s(vk, q) <= z(vp, vk)
-                if ((long long)(Fq - Fv) * (vk - vp) <= (long long)(Fv - Fp) * (q - vk))
-                    --kk;
-                else
-                    break;
+            for (int u = 0; u < PF; ++u) {
+                const int q = q0 + u;
+                const int32_t hq = hv[u];
+                if (hq == INF) continue;
+                const int32_t Fq = hq * hq + q * q;
+                while (kk > 0) {
+                    const int vk = v[kk * stride], vp = v[(kk - 1) * stride];
+                    const int32_t Fv = F[kk * stride], Fp = F[(kk - 1) * stride];
+                    if ((long long)(Fq - Fv) * (vk - vp) <= (long long)(Fv - Fp) * (q - vk))
+                        --kk;
+                    else
+                        break;
+                }
+                ++kk;
+                v[kk * stride] = q;
+                F[kk * stride] = Fq;
             }
-            ++kk;
-            v[kk * stride] = q;
-            F[kk * stride] = Fq;
         }
+        s_kk[c] = kk;
     }
+    __syncthreads();  // envelopes complete (shared or global) for the whole block
+    if (!valid) return;
+    const int kk = s_kk[c];
+    int32_t* out = dist2 + (size_t)i * H * W + x;
+    const int y0 = (int)((long long)H * seg / NSEG), y1 = (int)((long long)H * (seg + 1) / NSEG);
     if (kk < 0) {  // no valid seed of this label (only possible after a bad sample index)
-        for (int y = 0; y < H; ++y) out[(size_t)y * W] = INF;
+        for (int y = y0; y < y1; ++y) out[(size_t)y * W] = INF;
         return;
     }
-    int j = 0;
-    int vj = v[0];
-    int32_t Fj = F[0];
-    for (int y = 0; y < H; ++y) {
+    // first segment j whose right breakpoint is not left of y0
+    int lo = 0, hi = kk;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int vm = v[mid * stride], vn = v[(mid + 1) * stride];
+        const int32_t Fm = F[mid * stride], Fn = F[(mid + 1) * stride];
+        if ((long long)(Fn - Fm) < 2ll * y0 * (vn - vm)) lo = mid + 1;  // z(v_mid, v_mid+1) < y0
+        else hi = mid;
+    }
+    int j = lo;
+    int vj = v[j * stride];
+    int32_t Fj = F[j * stride];
+    for (int y = y0; y < y1; ++y) {
         while (j < kk) {
             const int vn = v[(j + 1) * stride];
             const int32_t Fn = F[(j + 1) * stride];
@@ -263,18 +283,16 @@ cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
                                                                        a.colbuf, a.dist2);
         return cudaGetLastError();
     }
-    // shared-memory stacks when at least 16 columns fit in 100 KB
-    const size_t per_thread = (size_t)a.H * 2 * sizeof(int32_t);
-    int tb = (int)std::min<size_t>(32, (100u * 1024u) / per_thread);
-    if (tb >= 16) {
-        tb = tb / 16 * 16;
-        const size_t smem = per_thread * tb;
-        cudaFuncSetAttribute(cols_envelope_kernel<true>,
+    // envelopes of 32 columns per block in shared memory when they fit
+    const size_t smem = (size_t)a.H * 2 * sizeof(int32_t) * 32;
+    const unsigned nblk = (unsigned)((ncol + 31) / 32);
+    if (smem <= 110u * 1024u) {
+        cudaFuncSetAttribute(cols_envelope_split_kernel<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cols_envelope_kernel<true><<<(unsigned)((ncol + tb - 1) / tb), tb, smem, st>>>(
+        cols_envelope_split_kernel<true><<<nblk, 32 * NSEG, smem, st>>>(
             a.H, a.W, a.n_labels, a.colbuf, nullptr, nullptr, a.dist2);
     } else {
-        cols_envelope_kernel<false><<<(unsigned)((ncol + 63) / 64), 64, 0, st>>>(
+        cols_envelope_split_kernel<false><<<nblk, 32 * NSEG, 0, st>>>(
             a.H, a.W, a.n_labels, a.colbuf, a.vbuf, a.fbuf, a.dist2);
     }
     return cudaGetLastError();
