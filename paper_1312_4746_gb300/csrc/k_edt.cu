@@ -6,9 +6,9 @@
 //   1. seed bitmaps: one bit per pixel and label;
 //   2. row pass (one warp per label and row): horizontal distance h to the
 //      nearest seed in the same row, from bit scans of the bitmap words;
-//   3. column pass (one thread per label and column, coalesced): lower
-//      envelope of the parabolas (y - q)^2 + h(q)^2 over the rows q with
-//      finite h, built in one sweep and read back in a second; intersection
+//   3. column pass (a builder thread per label and column, four readers):
+//      lower envelope of the parabolas (y - q)^2 + h(q)^2 over the rows q
+//      with finite h, built in one sweep and read back by row ranges; intersection
 //      abscissae are compared as exact rationals with 64-bit cross products,
 //      so the result equals the brute-force minimum bit for bit. For images
 //      with few columns and rows (labels x width < 16384, height <= 64) an
@@ -88,7 +88,10 @@ __global__ void rows_binary_kernel(int H, int W, int n_labels, const uint32_t* _
 }
 
 // Column pass, split: in each block of 32 columns the first warp builds the
-// lower envelope of every column (one thread per column, as above), then
+// lower envelope of every column (one thread per column, one sweep over the
+// rows with finite h: a row's parabola (y - q)^2 + h(q)^2 replaces the stack
+// top while it lies below it from the top's breakpoint on, compared exactly
+// with 64-bit cross products), then
 // all NSEG warps read it back, warp s for the rows [s H / NSEG, (s + 1) H /
 // NSEG); each thread finds the envelope segment of its first row by binary
 // search over the breakpoints (the same exact comparison, monotone in the
