@@ -228,11 +228,13 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
  * Precision control of the tensor-core forms (CS_BF16, CS_FP8). Every pair
  * exponent e_j (log2 units) is <= 0, so their sum accumulates 2^(e_j + s)
  * in FP32 with the fixed shift s = 96 - ceil(log2 m_i) and cannot overflow.
- * A pixel is recomputed on the GPU in double precision (all labels:
- * exponents, two-pass log-sum-exp and normalisation in FP64) before the
- * call's work completes when one of its label rows either totals below
- * m_i 2^-100 after the shift (terms may have underflowed) or has an a-priori
- * error bound above l_tol * max(|L|, 1). The bound (log2 units)
+ * A label row is summed again on the GPU
+ * before the call's work completes when it either totals below m_i 2^-100
+ * after the shift (terms may have underflowed) or has an a-priori error
+ * bound above l_tol * max(|L|, 1): exponents formed in double precision,
+ * their offsets from the row maximum exponentiated in FP32 and accumulated
+ * in double (two passes); the pixel's label normalisation is then redone in
+ * double. The bound (log2 units)
  * adds 2^-15 C Q for the two-piece BF16 colour splits (C = log2 e /
  * (2 sigma_c2), Q = 2 |I| max_j |I_j| + max_j |I_j|^2), 2^-21 (Bt k + C Q)
  * for the tensor core's FP32 accumulation of the colour MMA onto the integer

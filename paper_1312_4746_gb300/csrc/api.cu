@@ -356,7 +356,7 @@ void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2) {
     L.t.perm = c.take<int32_t>(L.tc_form ? (size_t)S : 0);
     L.desc = c.take<TcImage>(L.tc_form ? 1 : 0);
     L.imax2 = c.take<float>(L.tc_form ? (size_t)n : 0);
-    L.fb_list = c.take<int2>(L.tc_form ? (size_t)P : 0);
+    L.fb_list = c.take<int4>(L.tc_form ? (size_t)P : 0);
     L.fb_count = c.take<int>(L.tc_form ? 1 : 0);
 }
 

@@ -75,7 +75,7 @@ struct cs_batch {
     bool tc = false;
     char* mem = nullptr;
     TcImage* descs = nullptr;
-    int2* fb_list = nullptr;  // FP64 recompute list over all images
+    int4* fb_list = nullptr;  // FP64 recompute list over all images
     int* fb_count = nullptr;
     int total_pixels = 0;
     int n_streams = 4, order_mode = 0;
@@ -338,7 +338,7 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
             cs_lik_carve(c, m.L, m.d.dist2);
         }
         b->descs = c.take<TcImage>(b->tc ? (size_t)n_images : 0);
-        b->fb_list = c.take<int2>(b->tc ? (size_t)b->total_pixels : 0);
+        b->fb_list = c.take<int4>(b->tc ? (size_t)b->total_pixels : 0);
         b->fb_count = c.take<int>(b->tc ? 1 : 0);
     };
     Carve m0(nullptr);

@@ -200,7 +200,7 @@ struct LikPlan {
     int32_t *colbuf, *vbuf, *fbuf, *d2;
     SampleTables t;
     TcImage* desc;  // tensor-core form: descriptor slot
-    int2* fb_list;  // tensor-core form: FP64 recompute list (P entries) and count
+    int4* fb_list;  // tensor-core form: FP64 recompute list (P entries) and count
     int* fb_count;
     float* imax2;   // tensor-core form: per label max |I_j|^2
 };
@@ -257,9 +257,9 @@ struct TcSumParams {
     float alpha, d_min, kappa_beta, sigma_c2;
     int* d_err;
     int n_sm;
-    // pixels with a label row below the FP32 floor: (image, pixel), their
-    // count (cleared by the launch) and the capacity (>= all pixels)
-    int2* fb_list;
+    // pixels with flagged label rows: (image, pixel, label mask low, high),
+    // their count (cleared by the launch) and the capacity (>= all pixels)
+    int4* fb_list;
     int* fb_count;
     int fb_cap;
     float l_tol;  // relative tolerance on L of the a-priori row bound (0: off)
@@ -288,7 +288,7 @@ struct TcLaunch {
     bool persample;  // per-sample texture kernel (else factorised)
     TcImage* desc;   // device slot receiving this image's descriptor
     int first_item;  // its first work item in the sum launch
-    int2* fb_list;   // FP64 recompute list (H W entries) and its count
+    int4* fb_list;   // FP64 recompute list (H W entries) and its count
     int* fb_count;
     float* imax2;    // per label max |I_j|^2 (written by the preparation)
     float l_tol;

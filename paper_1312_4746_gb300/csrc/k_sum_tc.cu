@@ -82,7 +82,7 @@ struct TcArgs {
     int k, Wk;
     float alpha, d_min, kappa_beta, sigma_c2;
     int* d_err;
-    int2* fb_list;  // (image, pixel) of pixels to recompute in FP64
+    int4* fb_list;  // (image, pixel, flagged-label mask low, high) to recompute
     int* fb_count;
     int fb_cap;
     float l_tol;    // relative tolerance on L of the a-priori row bound (0: off)
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(atex_full);
 
-            bool flagged = false;  // a label row of this pixel fell below the floor
+            uint64_t fmask = 0;  // label rows of this pixel flagged for the FP64 recompute
             for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
                 const int D = live ? im.dist2[(size_t)i * P + pix] : 0;
                 const float rho = a.alpha * fmaxf(sqrtf((float)D), a.d_min);
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                                           nA * (wKm / tot) + 2.f * fabsf(R0) + shift + 1.f);
                     if (!(tot >= FLOOR_PER_SAMPLE * (float)m_i) ||
                         (a.l_tol > 0.f && E2 * LN2 > a.l_tol * fmaxf(fabsf(Lv), 1.f)))
-                        flagged = true;
+                        fmask |= 1ull << i;
                     // -L into the output plane; normalised once all labels are done
                     if (live) im.neglog[(size_t)i * P + pix] = -Lv;
                 }
@@ -603,9 +603,11 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             if (!ok) break;
             // label normalisation (and the factorised texture posterior) by part
             // 0; a flagged pixel is listed for the FP64 recompute instead
-            if (hf == 0 && live && flagged) {
+            if (hf == 0 && live && fmask) {
                 const int idx = atomicAdd(a.fb_count, 1);
-                if (idx < a.fb_cap) a.fb_list[idx] = make_int2(image_of(a, g), pix);
+                if (idx < a.fb_cap)
+                    a.fb_list[idx] = make_int4(image_of(a, g), pix, (int)(uint32_t)fmask,
+                                               (int)(uint32_t)(fmask >> 32));
             } else if (hf == 0 && live) {
                 if (!PERSAMPLE) {
                     float tmax = -INFINITY;
@@ -649,14 +651,18 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
     }
 }
 
-// FP64 recompute of the pixels flagged by the sum (a label row below the FP32
-// floor or above the error tolerance): one warp per listed pixel, every
-// label; per label the exponents
+// Recompute of the pixels flagged by the sum (a label row below the FP32
+// floor or above the error tolerance): one warp per listed pixel. Each
+// flagged label row is summed again with the exponents
 // e_j = -|x - x_j|^2 / (2 rho^2) - |I - I_j|^2 / (2 sigma_c2) [- TSM / beta]
-// in double, a two-pass log-sum-exp across the lanes, then the label
-// normalisation (and, factorised, the texture posterior) in double.
+// formed in double precision (no cancellation between expanded products),
+// their offsets from the row maximum exponentiated in FP32 (relative error
+// ~1e-7 per term) and accumulated in double across the lanes (two passes:
+// maximum, then sum); the other rows keep the sum's value. The label
+// normalisation (and, factorised, the texture posterior) is then redone in
+// double for the pixel.
 __global__ void __launch_bounds__(128) refine_fp64_kernel(
-    const TcImage* __restrict__ images, const int2* __restrict__ list,
+    const TcImage* __restrict__ images, const int4* __restrict__ list,
     const int* __restrict__ count, int cap, int Wk, double alpha, double d_min, double kappa_beta,
     double sigma_c2, bool persample, int* __restrict__ d_err) {
     __shared__ double sL[4][CS_MAX_LABELS];
@@ -672,8 +678,9 @@ __global__ void __launch_bounds__(128) refine_fp64_kernel(
     const double PI2 = 6.283185307179586;
     const double col_norm = 1.5 * log(PI2 * sigma_c2), c_col = 0.5 / sigma_c2;
     for (int e = blockIdx.x * 4 + wib; e < cnt; e += nwarps) {
-        const int2 it = list[e];
+        const int4 it = list[e];
         const TcImage& im = images[it.x];
+        const uint64_t fmask = (uint64_t)(uint32_t)it.z | ((uint64_t)(uint32_t)it.w << 32);
         const int pix = it.y, x = pix % im.W, y = pix / im.W;
         const long long P = (long long)im.H * im.W;
         const double IR = im.img[(size_t)pix * 3], IG = im.img[(size_t)pix * 3 + 1],
@@ -683,6 +690,15 @@ __global__ void __launch_bounds__(128) refine_fp64_kernel(
         for (int w = 0; w < 8; ++w) bx[w] = w < Wk ? im.bitmask[(size_t)pix * Wk + w] : 0u;
         for (int i = 0; i < im.n_labels; ++i) {
             const double rho = alpha * fmax(sqrt((double)im.dist2[(size_t)i * P + pix]), d_min);
+            if (lane == 0 && !persample) {
+                int h = 0;
+                for (int w = 0; w < Wk; ++w) h += __popc(bx[w] ^ im.rep[i * Wk + w]);
+                sT[wib][i] = -(double)h / (kappa_beta * rho);
+            }
+            if (!((fmask >> i) & 1ull)) {  // this row keeps the sum's value
+                if (lane == 0) sL[wib][i] = -(double)im.neglog[(size_t)i * P + pix];
+                continue;
+            }
             const double c_loc = 0.5 / (rho * rho);
             const double c_tex = persample ? 1.0 / (kappa_beta * rho) : 0.0;
             const int off = im.label_off[i], m = im.label_off[i + 1] - off;
@@ -702,17 +718,11 @@ __global__ void __launch_bounds__(128) refine_fp64_kernel(
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             double sum = 0.0;
-            for (int j = lane; j < m; j += 32) sum += exp(expo(j) - mx);
+            for (int j = lane; j < m; j += 32) sum += (double)__expf((float)(expo(j) - mx));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (lane == 0) {
+            if (lane == 0)
                 sL[wib][i] = mx + log(sum) - log((double)m) - log(PI2 * rho * rho) - col_norm;
-                if (!persample) {
-                    int h = 0;
-                    for (int w = 0; w < Wk; ++w) h += __popc(bx[w] ^ im.rep[i * Wk + w]);
-                    sT[wib][i] = -(double)h / (kappa_beta * rho);
-                }
-            }
         }
         __syncwarp();
         if (lane == 0) {
