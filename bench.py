@@ -13,6 +13,10 @@ Metric: pixel x sample likelihood pairs per second, whole job.
   e2e    the same steps through the C ABI starting from pinned host buffers:
          host->device copy of the inputs, the step, device->host copy of the
          data term f_i (neglog), all inside the timed region
+Secondary blocks of the same line (not the headline): "forms" (the plain
+FP32 form beside the FP8 one), "batch" (64 uneven images through
+cs_batch_*, graph-replayed and autotuned) and "large" (the 1024x1024 and
+4096x4096 workloads, both forms).
 Under torchrun (N > 1) every rank runs its own image (weak scaling, no
 collective on the data path); rank 0 prints the max-over-ranks line.
 
@@ -223,7 +227,7 @@ def cpu_baseline(pr, budget_s=15.0):
 # DRAM bytes per launch of the sum kernels on this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
 # kernels as they are now)
-TRAFFIC = {"sum_tc_kernel": 9.47e6, "sum_plain_kernel": 7.83e6}
+TRAFFIC = {"sum_tc_kernel": 9.46e6, "sum_plain_kernel": 7.83e6}
 
 FORMS = {"fp32": 0, "bf16": 1, "fp8": 2}
 FORM_NAMES = {"fp32": "plain FP32 (CUDA cores, popc TSM)",
@@ -344,6 +348,43 @@ def measure_batch(ctx, cs, torch, dev, n_images, reduce_max, world, runs=5):
             "l2": "not flushed: each run reads and writes about 1 GB (images, bitmasks, distances, outputs), far above L2"}
 
 
+def measure_large(ctx, cs, torch, dev, reduce_max, world, steps=3):
+    """The 1024 x 1024 (10 labels x 20000 samples) and 4096 x 4096 (16 x 6250,
+    9x9 patches, Omega 162x81) workloads through cs_data_term, both forms:
+    CUDA events over `steps` steps after one warm-up step (inputs of several
+    hundred MB to GB per step, above L2)."""
+    from paper_1312_4746_gb300 import synth
+
+    out = {}
+    stream = torch.cuda.current_stream()
+    for wl in (4, 5):
+        pr = synth.make_workload(wl)
+        img = torch.from_numpy(pr.image).to(dev)
+        om = torch.from_numpy(pr.omega).to(dev)
+        mask = torch.from_numpy(pr.mask).to(dev)
+        smp = torch.from_numpy(pr.sample_pix).to(dev)
+        pairs = float(pr.H * pr.W * pr.n_samples)
+        entry = {"workload": pr.name or f"{pr.W}x{pr.H}", "pairs_per_step": pairs}
+        for form in ("fp8", "fp32"):
+            prm = cs.Params.from_synth(pr.params, precision=FORMS[form])
+            res = ctx.data_term(img, om, mask, pr.label_off, smp, prm)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.data_term(img, om, mask, pr.label_off, smp, prm, out=res)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            (ms,) = reduce_max([e0.elapsed_time(e1) / steps])
+            entry[form] = {"ms_per_step": ms, "pairs_per_s": pairs * world / (ms * 1e-3),
+                           "fp64_recomputed_pixels": ctx.refined_count() if form != "fp32" else 0}
+            del res
+        out[f"{pr.W}x{pr.H}"] = entry
+        del img, om, mask, smp
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,6 +396,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-images", type=int, default=64,
                     help="also time a batch of this many uneven images (0: skip)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 1024x1024 and 4096x4096 workloads")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -410,6 +453,7 @@ def main():
     batch = None
     if args.batch_images > 0:
         batch = measure_batch(ctx, cs, torch, dev, args.batch_images, reduce_max, world)
+    large = None if args.no_large else measure_large(ctx, cs, torch, dev, reduce_max, world)
     if rank == 0:
         peaks, src = _peaks()
         clocks = clk.summary()
@@ -455,6 +499,8 @@ def main():
         }
         if batch is not None:
             line["batch"] = batch
+        if large is not None:
+            line["large"] = large
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pr)
         print(json.dumps(line))
