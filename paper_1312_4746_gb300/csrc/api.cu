@@ -142,12 +142,16 @@ cs_status cs_create(cs_ctx** out, int device) {
     if (cudaMalloc(&c->d_err, 2 * sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_err, 0, 2 * sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (c->d_err) cudaFree(c->d_err);
         if (c->side) cudaStreamDestroy(c->side);
+        if (c->side2) cudaStreamDestroy(c->side2);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
         delete c;
         return cs_set_error(nullptr, CS_ERR_CUDA, "cs_create: cannot set up the context");
     }
@@ -168,8 +172,10 @@ void cs_destroy(cs_ctx* ctx) {
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->surr_buf) cudaFree(ctx->surr_buf);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->side2) cudaStreamDestroy(ctx->side2);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
     delete ctx;
 }
 
@@ -365,11 +371,14 @@ static cudaError_t enqueue_codes(cs_ctx* ctx, const CodesArgs& a, cudaStream_t s
     return launch_codes(a, st);
 }
 
-// Distance transform (on `side` when given, else on `st`), then gather and sum on `st`.
+// Label offsets to the device, then the distance transform, on `st`
+// (with_offsets false: the offsets were enqueued earlier on an ordered stream).
 static cudaError_t enqueue_distances(cs_ctx* ctx, const LikPlan& L, const int32_t* sample_pix,
-                                     cudaStream_t st) {
-    cudaError_t e = launch_set_offsets(L.offs, 2 * (L.n_labels + 1), L.d_off, st);
-    if (e != cudaSuccess) return e;
+                                     cudaStream_t st, bool with_offsets = true) {
+    if (with_offsets) {
+        cudaError_t e = launch_set_offsets(L.offs, 2 * (L.n_labels + 1), L.d_off, st);
+        if (e != cudaSuccess) return e;
+    }
     EdtArgs ea{L.H, L.W, L.n_labels, L.d_off, sample_pix, L.S, L.seedbits, L.colbuf,
                L.vbuf, L.fbuf, L.d2, ctx->d_err};
     StageTimer tm(ctx, CS_STAGE_DIST, st);
@@ -631,18 +640,24 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     cs_plan_codes(c, a, P, k, !bitmask);
     cs_lik_carve(c, L, dist2);
     a.d_err = ctx->d_err;
-    // fork: the distance transform depends only on the scribbles and runs on
-    // the context's side stream while the codes run on the caller's stream
-    cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
+    // fork: the distance transform and the tensor-core sample order depend
+    // only on the scribbles; they run on the context's two side streams while
+    // the codes run on the caller's stream
+    cudaError_t e = launch_set_offsets(L.offs, 2 * (L.n_labels + 1), L.d_off, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-    if (e == cudaSuccess) e = enqueue_distances(ctx, L, sample_pix, ctx->side);
-    // the tensor-core sample order depends only on the scribbles as well
-    if (e == cudaSuccess && L.tc_form)
-        e = launch_tc_sort(cs_tc_launch(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post),
-                           ctx->side);
+    if (e == cudaSuccess) e = enqueue_distances(ctx, L, sample_pix, ctx->side, false);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+    if (e == cudaSuccess && L.tc_form) {
+        e = cudaStreamWaitEvent(ctx->side2, ctx->ev_fork, 0);
+        if (e == cudaSuccess)
+            e = launch_tc_sort(cs_tc_launch(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post),
+                               ctx->side2);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
+    }
     if (e == cudaSuccess) e = enqueue_codes(ctx, a, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join, 0);
+    if (e == cudaSuccess && L.tc_form) e = cudaStreamWaitEvent(st, ctx->ev_join2, 0);
     if (e == cudaSuccess)
         e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st, L.tc_form);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));

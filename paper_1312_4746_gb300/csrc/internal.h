@@ -39,8 +39,9 @@ struct cs_ctx {
     int surr_n = 0, surr_train = 0, surr_val = 0;
     bool surr_ready = false;
     int* last_fb_count = nullptr;  // FP64 recompute count of the last tensor-core sum
-    cudaStream_t side = nullptr;  // distance transform overlapping the codes
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side = nullptr;   // distance transform overlapping the codes
+    cudaStream_t side2 = nullptr;  // sample order overlapping both
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     bool profiling = false;
     std::vector<StageRecord> records;
     std::vector<cudaEvent_t> event_pool;
