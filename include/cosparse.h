@@ -396,6 +396,17 @@ cs_status cs_surrogate_params(cs_ctx* ctx, float* host_params, int cap, int* n_p
  */
 cs_status cs_surrogate_info(cs_ctx* ctx, float* host_stats, int cap, float* eta, float* loss,
                             int* n_train, int* n_val);
+/*
+ * cs_surrogate_save / cs_surrogate_load: the fitted surrogate (FP32 master
+ * weights, standardisation statistics, calibrated eta, last loss, training
+ * and validation counts) to / from a file (HOST path; a small versioned
+ * binary format, host byte order). Loading replaces the context's surrogate
+ * and resets the optimiser state. Both synchronise the device.
+ * Errors: CS_ERR_INVALID_ARG (no surrogate to save, unreadable or malformed
+ * file), CS_ERR_NOMEM, CS_ERR_CUDA.
+ */
+cs_status cs_surrogate_save(cs_ctx* ctx, const char* path);
+cs_status cs_surrogate_load(cs_ctx* ctx, const char* path);
 int cs_mlp_param_count(int n_out);
 cs_status cs_mlp_forward(cs_ctx* ctx, const float* params, int n_out, const float* X, int rows,
                          float* Z, void* stream);

@@ -55,6 +55,8 @@ EXPORTS = (
     "cs_surrogate_eval",
     "cs_surrogate_params",
     "cs_surrogate_info",
+    "cs_surrogate_save",
+    "cs_surrogate_load",
     "cs_mlp_param_count",
     "cs_mlp_forward",
     "cs_mlp_grad",
@@ -176,6 +178,8 @@ def lib(path: str | None = None):
                                     V, V]
     L.cs_surrogate_params.argtypes = [V, V, I, ctypes.POINTER(I)]
     L.cs_surrogate_info.argtypes = [V, V, I, V, V, ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.cs_surrogate_save.argtypes = [V, ctypes.c_char_p]
+    L.cs_surrogate_load.argtypes = [V, ctypes.c_char_p]
     L.cs_mlp_param_count.argtypes = [I]
     L.cs_mlp_param_count.restype = I
     L.cs_mlp_forward.argtypes = [V, V, I, V, I, V, V]
@@ -184,7 +188,8 @@ def lib(path: str | None = None):
     L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     for f in ("cs_create", "cs_sync_status", "cs_refined_count", "cs_codes", "cs_cosupport", "cs_likelihood",
               "cs_data_term", "cs_profile_enable", "cs_profile_read", "cs_surrogate_fit",
-              "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_mlp_forward",
+              "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_surrogate_save",
+              "cs_surrogate_load", "cs_mlp_forward",
               "cs_mlp_grad", "cs_batch_create", "cs_batch_run", "cs_batch_config",
               "cs_batch_data_term"):
         getattr(L, f).restype = I
@@ -415,6 +420,14 @@ class Context:
         return {"mu_x": st[:21], "sd_x": st[21:42], "mu_t": st[42:42 + n],
                 "sd_t": st[42 + n:42 + 2 * n], "eta": eta.value, "loss": loss.value,
                 "n_train": ntr.value, "n_val": nva.value}
+
+    def surrogate_save(self, path):
+        """cs_surrogate_save (synchronises)."""
+        self.check(self._lib.cs_surrogate_save(self.handle, os.fsencode(path)))
+
+    def surrogate_load(self, path):
+        """cs_surrogate_load (synchronises)."""
+        self.check(self._lib.cs_surrogate_load(self.handle, os.fsencode(path)))
 
     def mlp_forward(self, params_dev, n_out, X):
         import torch

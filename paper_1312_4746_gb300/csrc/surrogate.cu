@@ -276,6 +276,80 @@ cs_status cs_surrogate_params(cs_ctx* ctx, float* host_params, int cap, int* n_p
     return CS_OK;
 }
 
+// File: "CSSURR01", int32 n_labels, n_params, n_train, n_val, then float32
+// params[n_params], stats[42 + 2 n], eta, loss (host byte order).
+static const char SURR_MAGIC[8] = {'C', 'S', 'S', 'U', 'R', 'R', '0', '1'};
+
+cs_status cs_surrogate_save(cs_ctx* ctx, const char* path) {
+    const char* fn = "cs_surrogate_save";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!path) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: path is NULL", fn);
+    if (!ctx->surr_ready) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: no surrogate", fn);
+    DeviceGuard g(ctx->device);
+    const int n = ctx->surr_n, np = mlp_param_count(n), ns = 2 * NIN + 2 * n;
+    std::vector<float> buf((size_t)np + ns + 2);
+    SurrPtrs sp = surr_ptrs(ctx, n);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data(), sp.p, sizeof(float) * np, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(buf.data() + np, sp.stats, sizeof(float) * (ns + 2), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    }
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: cannot open %s", fn, path);
+    const int32_t hdr[4] = {n, np, ctx->surr_train, ctx->surr_val};
+    const bool ok = std::fwrite(SURR_MAGIC, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1 &&
+                    std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: write to %s failed", fn, path);
+    return CS_OK;
+}
+
+cs_status cs_surrogate_load(cs_ctx* ctx, const char* path) {
+    const char* fn = "cs_surrogate_load";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!path) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: path is NULL", fn);
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: cannot open %s", fn, path);
+    char magic[8];
+    int32_t hdr[4];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, SURR_MAGIC, 8) == 0 &&
+              std::fread(hdr, sizeof hdr, 1, f) == 1;
+    const int n = ok ? hdr[0] : 0;
+    ok = ok && n >= 1 && n <= CS_MAX_LABELS && hdr[1] == mlp_param_count(n) && hdr[2] >= 0 &&
+         hdr[3] >= 0;
+    std::vector<float> buf;
+    if (ok) {
+        buf.resize((size_t)hdr[1] + 2 * NIN + 2 * n + 2);
+        ok = std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    }
+    std::fclose(f);
+    if (!ok) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: %s is not a surrogate file", fn, path);
+    DeviceGuard g(ctx->device);
+    cs_status s = ensure_surrogate(ctx, n);
+    if (s) return s;
+    const int np = hdr[1], ns = 2 * NIN + 2 * n;
+    SurrPtrs sp = surr_ptrs(ctx, n);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(sp.p, buf.data(), sizeof(float) * np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(sp.stats, buf.data() + np, sizeof(float) * (ns + 2), cudaMemcpyHostToDevice);
+    // fresh optimiser state: a later fit starts from these weights' values
+    if (e == cudaSuccess) e = cudaMemset(sp.m, 0, sizeof(float) * 3 * (size_t)np);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->surr_ready = false;
+        return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    }
+    ctx->surr_n = n;
+    ctx->surr_train = hdr[2];
+    ctx->surr_val = hdr[3];
+    ctx->surr_ready = true;
+    return CS_OK;
+}
+
 cs_status cs_surrogate_info(cs_ctx* ctx, float* host_stats, int cap, float* eta, float* loss,
                             int* n_train, int* n_val) {
     if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_surrogate_info: ctx is NULL");

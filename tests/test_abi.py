@@ -79,3 +79,9 @@ def test_image_struct_layout():
     # cs_image: pointer, 4 x int32, then six pointers (64-bit ABI)
     assert ctypes.sizeof(cs.Image) == 8 + 16 + 6 * 8
     assert cs.Image.label_off.offset == 24
+
+
+def test_surrogate_file_args_no_gpu(L, tmp_path):
+    assert L.cs_surrogate_save(None, b"x") == cs.CS_ERR_INVALID_ARG
+    assert L.cs_surrogate_load(None, str(tmp_path / "missing").encode()) == cs.CS_ERR_INVALID_ARG
+    assert b"ctx" in L.cs_last_error(None)

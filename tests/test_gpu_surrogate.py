@@ -158,3 +158,31 @@ def test_surrogate_requires_fit(env):
         fresh.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm)
     assert ei.value.status == cs.CS_ERR_INVALID_ARG
     fresh.close()
+
+
+def test_surrogate_save_load_roundtrip(env, tmp_path):
+    """A saved surrogate loaded into a fresh context evaluates identically;
+    a malformed file is refused."""
+    cs, ctx, torch = env
+    pr = synth.make_problem(64, 72, 3, 300, p=7, k=98, n_regions=3, seed=41)
+    prm = cs.Params.from_synth(pr.params)
+    img, c, smp, _ = _exact(env, pr, prm)
+    ctx.surrogate_fit(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
+                      frac=0.1, steps=100, seed=5)
+    path = str(tmp_path / "net.cssurr")
+    ctx.surrogate_save(path)
+    a, _ = ctx.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
+                              margin=-1.0, count=False)
+    other = cs.Context(0)
+    other.surrogate_load(path)
+    b, _ = other.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
+                                margin=-1.0, count=False)
+    torch.cuda.synchronize()
+    assert torch.equal(a["neglog"], b["neglog"]) and torch.equal(a["post"], b["post"])
+    assert np.array_equal(ctx.surrogate_params(), other.surrogate_params())
+    bad = tmp_path / "bad.cssurr"
+    bad.write_bytes(b"not a surrogate")
+    with pytest.raises(cs.CsError) as ei:
+        other.surrogate_load(str(bad))
+    assert ei.value.status == cs.CS_ERR_INVALID_ARG
+    other.close()
