@@ -334,6 +334,15 @@ cs_status cs_batch_config(const cs_batch* b, int32_t* n_streams, int32_t* order,
 /* Frees the batch (waits for its streams first). NULL is a no-op. */
 void cs_batch_destroy(cs_batch* b);
 
+/* The likelihood step alone over a batch (as cs_likelihood per image, with
+ * one persistent tensor-core sum over all images in the tensor-core forms):
+ * each image's `bitmask` is a required DEVICE INPUT (P x ceil(k/32) uint32,
+ * e.g. from cs_codes); the other fields as in cs_batch_create. One-shot:
+ * plans, runs on `stream` and frees its memory after the run (synchronises
+ * the stream). */
+cs_status cs_batch_likelihood(cs_ctx* ctx, const cs_image* images, int n_images, int k,
+                              const cs_params* prm, void* stream);
+
 /* One-shot batch: create (no flags), run on `stream`, destroy. The batch
  * memory is freed only after the run completes (the call synchronises the
  * stream). */

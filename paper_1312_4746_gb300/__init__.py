@@ -51,6 +51,7 @@ EXPORTS = (
     "cs_batch_config",
     "cs_batch_destroy",
     "cs_batch_data_term",
+    "cs_batch_likelihood",
     "cs_surrogate_fit",
     "cs_surrogate_eval",
     "cs_surrogate_params",
@@ -172,6 +173,7 @@ def lib(path: str | None = None):
     L.cs_batch_destroy.restype = None
     L.cs_batch_data_term.argtypes = [V, ctypes.POINTER(Image), I, V, I, V, ctypes.POINTER(Params),
                                      V]
+    L.cs_batch_likelihood.argtypes = [V, ctypes.POINTER(Image), I, I, ctypes.POINTER(Params), V]
     U64 = ctypes.c_uint64
     L.cs_surrogate_fit.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, I, U64, V]
     L.cs_surrogate_eval.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, V, V,
@@ -191,7 +193,7 @@ def lib(path: str | None = None):
               "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_surrogate_save",
               "cs_surrogate_load", "cs_mlp_forward",
               "cs_mlp_grad", "cs_batch_create", "cs_batch_run", "cs_batch_config",
-              "cs_batch_data_term"):
+              "cs_batch_data_term", "cs_batch_likelihood"):
         getattr(L, f).restype = I
     if path is None:
         _lib = L
@@ -350,6 +352,14 @@ class Context:
         allocated here (torch) and returned with the batch."""
         return Batch(self, images, omega, mask, params, flags, want_post, want_bitmask, want_dist2)
 
+    def batch_likelihood(self, images, k, params: Params, want_post=True):
+        """cs_batch_likelihood: every image dict also carries its device
+        'bitmask' (from codes); one-shot, synchronises the current stream."""
+        arr, outs, keep = _batch_descs(images, int(k), want_post, False, False, bitmask_in=True)
+        self.check(self._lib.cs_batch_likelihood(self.handle, arr, len(images), int(k),
+                                                 ctypes.byref(params), _stream()))
+        return outs
+
     def batch_data_term(self, images, omega, mask, params: Params, want_post=True):
         """cs_batch_data_term (one-shot; synchronises the current stream)."""
         arr, outs, keep = _batch_descs(images, int(omega.shape[0]), want_post, False, False)
@@ -447,7 +457,7 @@ class Context:
         return g, loss
 
 
-def _batch_descs(images, k, want_post, want_bitmask, want_dist2):
+def _batch_descs(images, k, want_post, want_bitmask, want_dist2, bitmask_in=False):
     import numpy as np
     import torch
 
@@ -463,7 +473,8 @@ def _batch_descs(images, k, want_post, want_bitmask, want_dist2):
         o = {"neglog": torch.empty((nl, H, W), dtype=torch.float32, device=dev),
              "post": torch.empty((nl, H, W), dtype=torch.float32, device=dev) if want_post else None,
              "dist2": torch.empty((nl, H, W), dtype=torch.int32, device=dev) if want_dist2 else None,
-             "bitmask": (torch.empty((H * W, (k + 31) // 32), dtype=torch.int32, device=dev)
+             "bitmask": (d["bitmask"] if bitmask_in else
+                         torch.empty((H * W, (k + 31) // 32), dtype=torch.int32, device=dev)
                          if want_bitmask else None)}
         arr[i] = Image(img.data_ptr(), H, W, nl, 0, off.ctypes.data, d["sample_pix"].data_ptr(),
                        _ptr(o["bitmask"]), _ptr(o["dist2"]), o["neglog"].data_ptr(), _ptr(o["post"]))

@@ -84,6 +84,7 @@ struct cs_batch {
     int n_items = 0;
     double pairs = 0, tuned_ms = -1;
     bool tuned = false, ran = false;
+    bool codes_given = false;  // likelihood only: the images' bitmasks are inputs
     std::string sig;
     cudaStream_t streams[MAX_STREAMS] = {};
     cudaStream_t cap = nullptr;
@@ -128,7 +129,7 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
                        L.vbuf, L.fbuf, L.d2, ctx->d_err};
             e = launch_edt(ea, ss);
         }
-        if (e == cudaSuccess) e = launch_codes(m.codes, ss);
+        if (e == cudaSuccess && !b->codes_given) e = launch_codes(m.codes, ss);
         if (e == cudaSuccess)
             e = launch_gather(m.d.img, L.H, L.W, m.codes.bitmask, L.k, L.n_labels, L.d_off,
                               m.d.sample_pix, L.S, !L.persample, L.t, ss);
@@ -251,14 +252,17 @@ void cs_batch_destroy(cs_batch* b) {
     delete b;
 }
 
-cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, const float* omega,
-                          int k, const float* mask, const cs_params* prm, int flags,
-                          cs_batch** out) {
-    const char* fn = "cs_batch_create";
+}  // extern "C"
+
+// Both batch entry points: with codes_given the images' bitmasks are inputs
+// and the codes stage is skipped (omega and mask unused).
+static cs_status batch_create(const char* fn, cs_ctx* ctx, const cs_image* images, int n_images,
+                              const float* omega, int k, const float* mask, const cs_params* prm,
+                              int flags, bool codes_given, cs_batch** out) {
     if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
     if (!out) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: out is NULL", fn);
     *out = nullptr;
-    if (!images || !omega || !mask)
+    if (!images || (!codes_given && (!omega || !mask)))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
     if (n_images < 1 || n_images > MAX_IMAGES)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: n_images=%d outside 1..%d", fn,
@@ -272,7 +276,7 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
     for (int i = 0; i < n_images; ++i) {
         const cs_image& d = images[i];
         snprintf(where, sizeof(where), "%s: image %d", fn, i);
-        if (!d.img || !d.sample_pix || !d.neglog)
+        if (!d.img || !d.sample_pix || !d.neglog || (codes_given && !d.bitmask))
             return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", where);
         if (d.reserved != 0)
             return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: reserved field must be 0", where);
@@ -282,6 +286,7 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
     if ((s = cs_check_params(ctx, fn, prm, k))) return s;
 
     cs_batch* b = new cs_batch();
+    b->codes_given = codes_given;
     b->ctx = ctx;
     b->omega = omega;
     b->mask = mask;
@@ -331,7 +336,7 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
             const long long P = (long long)m.d.H * m.d.W;
             m.codes = CodesArgs{m.d.img, m.d.H, m.d.W, omega, k, mask, prm->p, prm->tau,
                                 nullptr, nullptr, m.d.bitmask};
-            m.codes.tc = cs_codes_use_tc(prm, k);
+            m.codes.tc = !codes_given && cs_codes_use_tc(prm, k);
             cs_plan_codes(c, m.codes, P, k, !m.d.bitmask);
             m.codes.d_err = ctx->d_err;
             cs_lik_plan(m.L, m.d.H, m.d.W, k, m.d.n_labels, m.off.data(), prm);
@@ -379,6 +384,15 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
     return CS_OK;
 }
 
+extern "C" {
+
+cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, const float* omega,
+                          int k, const float* mask, const cs_params* prm, int flags,
+                          cs_batch** out) {
+    return batch_create("cs_batch_create", ctx, images, n_images, omega, k, mask, prm, flags,
+                        false, out);
+}
+
 cs_status cs_batch_run(cs_batch* b, void* stream) {
     if (!b) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_batch_run: batch is NULL");
     const char* fn = "cs_batch_run";
@@ -408,6 +422,23 @@ cs_status cs_batch_config(const cs_batch* b, int32_t* n_streams, int32_t* order,
     if (order) *order = b->order_mode;
     if (pairs) *pairs = b->pairs;
     if (tuned_ms) *tuned_ms = b->tuned_ms;
+    return CS_OK;
+}
+
+cs_status cs_batch_likelihood(cs_ctx* ctx, const cs_image* images, int n_images, int k,
+                              const cs_params* prm, void* stream) {
+    cs_batch* b = nullptr;
+    cs_status s = batch_create("cs_batch_likelihood", ctx, images, n_images, nullptr, k, nullptr,
+                               prm, 0, true, &b);
+    if (s) return s;
+    s = cs_batch_run(b, stream);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    cs_batch_destroy(b);
+    if (s) return s;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cs_set_error(ctx, CS_ERR_CUDA, "cs_batch_likelihood: %s", cudaGetErrorString(e));
+    }
     return CS_OK;
 }
 

@@ -152,3 +152,21 @@ def test_batch_invalid(env):
     with pytest.raises(cs.CsError) as ei:
         ctx.batch([], omega, mask, prm)
     assert ei.value.status == cs.CS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", [2, 0])
+def test_batch_likelihood_with_given_bitmasks(env, precision):
+    """cs_batch_likelihood on bitmasks computed beforehand gives what
+    cs_likelihood gives on each image."""
+    cs, ctx, torch = env
+    probs = _problems()
+    prm = cs.Params.from_synth(probs[0].params, precision=precision)
+    omega, mask = _dev(torch, probs[0].omega), _dev(torch, probs[0].mask)
+    inp = _inputs(torch, probs)
+    for x in inp:
+        x["bitmask"] = ctx.codes(x["img"], omega, mask, prm)["bitmask"]
+    outs = ctx.batch_likelihood(inp, probs[0].k, prm)
+    for q, x, o in zip(probs, inp, outs):
+        ref = ctx.likelihood(x["img"], x["bitmask"], q.k, q.label_off, x["sample_pix"], prm)
+        ctx.sync()
+        _same(o, ref)
