@@ -87,33 +87,98 @@ __global__ void rows_binary_kernel(int H, int W, int n_labels, const uint32_t* _
     }
 }
 
-// Column pass, split: in each block of 32 columns the first warp builds the
-// lower envelope of every column (one thread per column, one sweep over the
-// rows with finite h: a row's parabola (y - q)^2 + h(q)^2 replaces the stack
-// top while it lies below it from the top's breakpoint on, compared exactly
-// with 64-bit cross products), then
-// all NSEG warps read it back, warp s for the rows [s H / NSEG, (s + 1) H /
-// NSEG); each thread finds the envelope segment of its first row by binary
-// search over the breakpoints (the same exact comparison, monotone in the
-// segment index) and walks on from there.
+// Column pass, split: in each block of 32 columns two warps build the lower
+// envelopes of every column, warp b over the rows of half b (one thread per
+// column and half; one sweep over the half's rows with finite h: a row's
+// parabola (y - q)^2 + h(q)^2 replaces the stack top while it lies below it
+// from the top's breakpoint on, compared exactly with 64-bit cross
+// products); then all NSEG warps read them back, warp s for the rows
+// [s H / NSEG, (s + 1) H / NSEG): each thread finds the segment of its first
+// row in both half-envelopes by binary search over the breakpoints (the same
+// exact comparison, monotone in the segment index), walks on, and keeps the
+// smaller of the two values, the minimum over all rows.
 constexpr int NSEG = 4;
+
+__device__ __forceinline__ int env_build(const int32_t* __restrict__ col, int W, int q_lo, int q_hi,
+                                         int32_t* v, int32_t* F, long long stride) {
+    int kk = -1;
+    constexpr int PF = 16;  // rows of h fetched ahead (independent loads)
+    for (int q0 = q_lo; q0 < q_hi; q0 += PF) {
+        int32_t hv[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) hv[u] = q0 + u < q_hi ? col[(size_t)(q0 + u) * W] : INF;
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int q = q0 + u;
+            const int32_t hq = hv[u];
+            if (hq == INF) continue;
+            const int32_t Fq = hq * hq + q * q;
+            while (kk > 0) {
+                const int vk = v[kk * stride], vp = v[(kk - 1) * stride];
+                const int32_t Fv = F[kk * stride], Fp = F[(kk - 1) * stride];
+                if ((long long)(Fq - Fv) * (vk - vp) <= (long long)(Fv - Fp) * (q - vk))
+                    --kk;
+                else
+                    break;
+            }
+            ++kk;
+            v[kk * stride] = q;
+            F[kk * stride] = Fq;
+        }
+    }
+    return kk;
+}
+
+// Reader state on one envelope: current segment j (vertex vj, value Fj).
+struct EnvCursor {
+    int j, kk, vj;
+    int32_t Fj;
+};
+__device__ __forceinline__ EnvCursor env_seek(const int32_t* v, const int32_t* F,
+                                              long long stride, int kk, int y0) {
+    int lo = 0, hi = kk;
+    while (lo < hi) {  // first segment whose right breakpoint is not left of y0
+        const int mid = (lo + hi) >> 1;
+        const int vm = v[mid * stride], vn = v[(mid + 1) * stride];
+        const int32_t Fm = F[mid * stride], Fn = F[(mid + 1) * stride];
+        if ((long long)(Fn - Fm) < 2ll * y0 * (vn - vm)) lo = mid + 1;  // z(v_mid, v_mid+1) < y0
+        else hi = mid;
+    }
+    return {lo, kk, v[lo * stride], F[lo * stride]};
+}
+__device__ __forceinline__ int32_t env_value(EnvCursor& c, const int32_t* v, const int32_t* F,
+                                             long long stride, int y) {
+    while (c.j < c.kk) {
+        const int vn = v[(c.j + 1) * stride];
+        const int32_t Fn = F[(c.j + 1) * stride];
+        if ((long long)(Fn - c.Fj) < 2ll * y * (vn - c.vj)) {  // z(vj, vn) < y
+            ++c.j;
+            c.vj = vn;
+            c.Fj = Fn;
+        } else {
+            break;
+        }
+    }
+    return (y - c.vj) * (y - c.vj) + (c.Fj - c.vj * c.vj);
+}
 
 template <bool SHARED>
 __global__ void __launch_bounds__(32 * NSEG) cols_envelope_split_kernel(
     int H, int W, int n_labels, const int32_t* __restrict__ h, int32_t* __restrict__ gv,
     int32_t* __restrict__ gF, int32_t* __restrict__ dist2) {
     extern __shared__ int32_t smem[];
-    __shared__ int s_kk[32];
+    __shared__ int s_kk[2][32];
     const long long ncol = (long long)n_labels * W;
     const int c = threadIdx.x & 31, seg = threadIdx.x >> 5;
     const long long col_id = blockIdx.x * 32ll + c;
     const bool valid = col_id < ncol;
     const int i = valid ? (int)(col_id / W) : 0, x = valid ? (int)(col_id % W) : 0;
+    const int HH = (H + 1) / 2;  // rows (and stack entries) per half
     int32_t *v, *F;
     long long stride;
     if (SHARED) {
         v = smem + c;
-        F = smem + (size_t)H * 32 + c;
+        F = smem + (size_t)2 * HH * 32 + c;
         stride = 32;
     } else {
         v = gv + col_id;
@@ -121,68 +186,26 @@ __global__ void __launch_bounds__(32 * NSEG) cols_envelope_split_kernel(
         stride = ncol;
     }
     const int32_t* col = h + (size_t)i * H * W + x;
-    if (seg == 0 && valid) {
-        int kk = -1;
-        constexpr int PF = 16;  // rows of h fetched ahead (independent loads)
-        for (int q0 = 0; q0 < H; q0 += PF) {
-            int32_t hv[PF];
-#pragma unroll
-            for (int u = 0; u < PF; ++u) hv[u] = q0 + u < H ? col[(size_t)(q0 + u) * W] : INF;
-#pragma unroll
-            for (int u = 0; u < PF; ++u) {
-                const int q = q0 + u;
-                const int32_t hq = hv[u];
-                if (hq == INF) continue;
-                const int32_t Fq = hq * hq + q * q;
-                while (kk > 0) {
-                    const int vk = v[kk * stride], vp = v[(kk - 1) * stride];
-                    const int32_t Fv = F[kk * stride], Fp = F[(kk - 1) * stride];
-                    if ((long long)(Fq - Fv) * (vk - vp) <= (long long)(Fv - Fp) * (q - vk))
-                        --kk;
-                    else
-                        break;
-                }
-                ++kk;
-                v[kk * stride] = q;
-                F[kk * stride] = Fq;
-            }
-        }
-        s_kk[c] = kk;
+    if (seg < 2 && valid) {
+        const int q_lo = seg * HH, q_hi = min(H, q_lo + HH);
+        s_kk[seg][c] = env_build(col, W, q_lo, q_hi, v + (size_t)seg * HH * stride,
+                                 F + (size_t)seg * HH * stride, stride);
     }
     __syncthreads();  // envelopes complete (shared or global) for the whole block
     if (!valid) return;
-    const int kk = s_kk[c];
     int32_t* out = dist2 + (size_t)i * H * W + x;
     const int y0 = (int)((long long)H * seg / NSEG), y1 = (int)((long long)H * (seg + 1) / NSEG);
-    if (kk < 0) {  // no valid seed of this label (only possible after a bad sample index)
-        for (int y = y0; y < y1; ++y) out[(size_t)y * W] = INF;
-        return;
-    }
-    // first segment j whose right breakpoint is not left of y0
-    int lo = 0, hi = kk;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int vm = v[mid * stride], vn = v[(mid + 1) * stride];
-        const int32_t Fm = F[mid * stride], Fn = F[(mid + 1) * stride];
-        if ((long long)(Fn - Fm) < 2ll * y0 * (vn - vm)) lo = mid + 1;  // z(v_mid, v_mid+1) < y0
-        else hi = mid;
-    }
-    int j = lo;
-    int vj = v[j * stride];
-    int32_t Fj = F[j * stride];
+    const int k0 = s_kk[0][c], k1 = s_kk[1][c];
+    const int32_t* v1 = v + (size_t)HH * stride;
+    const int32_t* F1 = F + (size_t)HH * stride;
+    EnvCursor c0{}, c1{};
+    if (k0 >= 0) c0 = env_seek(v, F, stride, k0, y0);
+    if (k1 >= 0) c1 = env_seek(v1, F1, stride, k1, y0);
     for (int y = y0; y < y1; ++y) {
-        while (j < kk) {
-            const int vn = v[(j + 1) * stride];
-            const int32_t Fn = F[(j + 1) * stride];
-            if ((long long)(Fn - Fj) < 2ll * y * (vn - vj)) {  // z(vj, vn) < y
-                ++j;
-                vj = vn;
-                Fj = Fn;
-            } else {
-                break;
-            }
-        }
-        out[(size_t)y * W] = (y - vj) * (y - vj) + (Fj - vj * vj);
+        int32_t d = INF;  // INF when the label has no valid seed (a bad sample index)
+        if (k0 >= 0) d = env_value(c0, v, F, stride, y);
+        if (k1 >= 0) d = min(d, env_value(c1, v1, F1, stride, y));
+        out[(size_t)y * W] = d;
     }
 }
 
@@ -286,8 +309,8 @@ cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
                                                                        a.colbuf, a.dist2);
         return cudaGetLastError();
     }
-    // envelopes of 32 columns per block in shared memory when they fit
-    const size_t smem = (size_t)a.H * 2 * sizeof(int32_t) * 32;
+    // envelopes of 32 columns per block (two halves) in shared memory when they fit
+    const size_t smem = (size_t)((a.H + 1) / 2) * 2 * 2 * sizeof(int32_t) * 32;
     const unsigned nblk = (unsigned)((ncol + 31) / 32);
     if (smem <= 110u * 1024u) {
         cudaFuncSetAttribute(cols_envelope_split_kernel<true>,
