@@ -167,13 +167,16 @@ __global__ void __launch_bounds__(TILE* TILE)
         for (int j = k; j < 16; ++j) lead16[(size_t)pix * 16 + j] = 0.f;
 }
 
-// Canonical double-precision recomputation of guarded entries, one thread
-// per entry: the patch and code follow the exact operation order of the
-// definition (gray, mask product, index-order sums, division by the square
-// root), with every operation correctly rounded and no contraction, so the
-// result is bit-identical to a sequential evaluation. An entry (pixel, j)
-// recomputes code j; (pixel, -1) recomputes every code of a nearly flat
-// patch. Guarded bits were left clear by the codes kernel and are set here.
+// Canonical double-precision recomputation of guarded entries, one warp per
+// entry (entries spread round-robin over the blocks, so over the SMs): the
+// patch and code follow the exact operation order of the definition (gray,
+// mask product, index-order sums, division by the square root), with every
+// operation correctly rounded and no contraction, so the result is
+// bit-identical to a sequential evaluation. The element-wise steps (pixel
+// loads, products, quotients) run across the lanes; only the three
+// index-order sums run on lane 0. An entry (pixel, j) decides code j;
+// (pixel, -1) every code of a nearly flat patch (one lane per code). Guarded
+// bits were left clear by the codes kernel and are set here.
 __device__ __forceinline__ double canon_v(const float* __restrict__ img, int H, int W,
                                           const float* __restrict__ mask, int p, int y, int x,
                                           int t) {
@@ -192,6 +195,8 @@ __global__ void __launch_bounds__(128) codes_guard_kernel(
     const float* __restrict__ mask, double tau, const int2* __restrict__ guard, int guard_cap,
     const int* __restrict__ guard_count, uint32_t* __restrict__ bitmask, int* __restrict__ d_err) {
     constexpr int N = P * P;
+    constexpr int NL = (N + 31) / 32;  // elements per lane
+    __shared__ double s_buf[4][N];      // per warp: values for the lane-0 sums
     int cnt = *guard_count;
     if (cnt > guard_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && atomicCAS(d_err, 0, CS_DEVERR_GUARD_FULL) == 0)
@@ -199,40 +204,80 @@ __global__ void __launch_bounds__(128) codes_guard_kernel(
         cnt = guard_cap;
     }
     const int Wk = (k + 31) >> 5;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double* sb = s_buf[wib];
+    for (int e = blockIdx.x + gridDim.x * wib; e < cnt; e += gridDim.x * 4) {
         const int2 g = guard[e];
         const int y = g.x / W, x = g.x % W;
-        // the element-wise steps are independent across t (unrolled, in
-        // registers); only the index-order sums form dependent chains
-        double s[N];
+        double c[NL];
 #pragma unroll
-        for (int t = 0; t < N; ++t) s[t] = canon_v(img, H, W, mask, P, y, x, t);
-        double mu = 0.0;
-#pragma unroll
-        for (int t = 0; t < N; ++t) mu = __dadd_rn(mu, s[t]);
-        mu = __ddiv_rn(mu, (double)N);
-        double ss = 0.0;
-#pragma unroll
-        for (int t = 0; t < N; ++t) {
-            s[t] = __dadd_rn(s[t], -mu);
-            ss = __dadd_rn(ss, __dmul_rn(s[t], s[t]));
+        for (int u = 0; u < NL; ++u) {
+            const int t = lane + 32 * u;
+            if (t < N) sb[t] = canon_v(img, H, W, mask, P, y, x, t);
         }
+        __syncwarp();
+        double mu = 0.0;
+        if (lane == 0) {
+            for (int t = 0; t < N; ++t) mu = __dadd_rn(mu, sb[t]);
+            mu = __ddiv_rn(mu, (double)N);
+        }
+        mu = __shfl_sync(0xffffffffu, mu, 0);
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+            const int t = lane + 32 * u;
+            c[u] = t < N ? __dadd_rn(sb[t], -mu) : 0.0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+            const int t = lane + 32 * u;
+            if (t < N) sb[t] = __dmul_rn(c[u], c[u]);
+        }
+        __syncwarp();
+        double ss = 0.0;
+        if (lane == 0)
+            for (int t = 0; t < N; ++t) ss = __dadd_rn(ss, sb[t]);
+        ss = __shfl_sync(0xffffffffu, ss, 0);
         if (ss == 0.0) {
 #pragma unroll
-            for (int t = 0; t < N; ++t) s[t] = 0.0;
+            for (int u = 0; u < NL; ++u) c[u] = 0.0;
         } else {
             const double nrm = __dsqrt_rn(ss);
 #pragma unroll
-            for (int t = 0; t < N; ++t) s[t] = __ddiv_rn(s[t], nrm);
+            for (int u = 0; u < NL; ++u) c[u] = __ddiv_rn(c[u], nrm);  // s_t
         }
-        const int jlo = g.y < 0 ? 0 : g.y, jhi = g.y < 0 ? k : g.y + 1;
-        for (int j = jlo; j < jhi; ++j) {
-            const float* oj = omega + (size_t)j * N;
-            double a = 0.0;
+        __syncwarp();
+        if (g.y >= 0) {
+            // one code: products across the lanes, the index-order sum on lane 0
+            const float* oj = omega + (size_t)g.y * N;
 #pragma unroll
-            for (int t = 0; t < N; ++t) a = __dadd_rn(a, __dmul_rn((double)oj[t], s[t]));
-            if (fabs(a) <= tau) atomicOr(bitmask + (size_t)g.x * Wk + (j >> 5), 1u << (j & 31));
+            for (int u = 0; u < NL; ++u) {
+                const int t = lane + 32 * u;
+                if (t < N) sb[t] = __dmul_rn((double)oj[t], c[u]);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                double a = 0.0;
+                for (int t = 0; t < N; ++t) a = __dadd_rn(a, sb[t]);
+                if (fabs(a) <= tau)
+                    atomicOr(bitmask + (size_t)g.x * Wk + (g.y >> 5), 1u << (g.y & 31));
+            }
+        } else {
+            // nearly flat patch: every code, one lane per code
+#pragma unroll
+            for (int u = 0; u < NL; ++u) {
+                const int t = lane + 32 * u;
+                if (t < N) sb[t] = c[u];
+            }
+            __syncwarp();
+            for (int j = lane; j < k; j += 32) {
+                const float* oj = omega + (size_t)j * N;
+                double a = 0.0;
+                for (int t = 0; t < N; ++t) a = __dadd_rn(a, __dmul_rn((double)oj[t], sb[t]));
+                if (fabs(a) <= tau) atomicOr(bitmask + (size_t)g.x * Wk + (j >> 5), 1u << (j & 31));
+            }
         }
+        __syncwarp();
     }
 }
 
