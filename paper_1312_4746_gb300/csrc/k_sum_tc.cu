@@ -60,13 +60,6 @@ namespace {
 
 constexpr int BM = 128, BN = 128;
 constexpr int TW = 16, TH = 8;          // pixel tile 16 x 8
-constexpr int EPQ = 4;                  // epilogue warps per TMEM lane quadrant
-constexpr int EPI_WARPS = 4 * EPQ;      // 16
-constexpr int CPW = BN / EPQ;           // columns per epilogue warp per tile (32)
-constexpr int PRODUCER = EPI_WARPS;     // warp 16
-constexpr int MMA_WARP = EPI_WARPS + 1;
-constexpr int THREADS = (EPI_WARPS + 2) * 32;
-constexpr uint32_t TMEM_COLS = 512;     // D1[2] at 0, 128; Dl[2] at 256, 384
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr float LN2 = 0.6931471805599453f;
 constexpr uint64_t WAIT_NS = 1000000000ull;  // 1 s per wait
@@ -100,13 +93,30 @@ __device__ __forceinline__ int image_of(const TcArgs& a, int g) {
 
 template <bool TEX8, int KS, bool PERSAMPLE>
 struct Cfg {
-    static constexpr int STAGES = KS <= 5 ? 4 : 3;  // sample-tile ring depth (shared memory)
     static constexpr int tex_bytes = PERSAMPLE ? KS * 4096 : 0;
     static constexpr int col_off = tex_bytes;
     static constexpr int bloc_off = tex_bytes + 4096;         // sample-side location slab
     static constexpr int aloc_off = tex_bytes + 2 * 4096;     // pixel-side location slab
     static constexpr int copy_bytes = tex_bytes + 2 * 4096;   // bulk-copied part of a stage
     static constexpr int stage_bytes = tex_bytes + 3 * 4096;
+    // Two CTAs per SM, each with one 256-column accumulator (D1 | Dl), a
+    // two-stage ring and 8 epilogue warps, when that layout fits twice in the
+    // SM's 228 KB: one CTA's epilogue then overlaps the other's MMAs. Else one
+    // CTA per SM with a double-buffered 512-column accumulator and 16
+    // epilogue warps.
+    static constexpr int pair_bytes = 2 * stage_bytes + tex_bytes + 2 * 4096 + 4 * 4 * 32 * 16 +
+                                      (2 * 2 + 26) * 8 + 16;
+    static constexpr bool PAIR = 2 * (pair_bytes + 1024) <= 228 * 1024;
+    static constexpr int MIN_BLOCKS = PAIR ? 2 : 1;
+    static constexpr int NB = PAIR ? 1 : 2;                  // accumulator buffers
+    static constexpr uint32_t TMEM_COLS = 256u * NB;         // D1[b] at b BN, Dl[b] at (NB + b) BN
+    static constexpr int EPQ = PAIR ? 2 : 4;                 // epilogue warps per TMEM lane quadrant
+    static constexpr int EPI_WARPS = 4 * EPQ;
+    static constexpr int CPW = BN / EPQ;                     // columns per epilogue warp per tile
+    static constexpr int PRODUCER = EPI_WARPS;
+    static constexpr int MMA_WARP = EPI_WARPS + 1;
+    static constexpr int THREADS = (EPI_WARPS + 2) * 32;
+    static constexpr int STAGES = PAIR ? 2 : (KS <= 5 ? 4 : 3);  // sample-tile ring depth
     // shared memory map
     static constexpr int ring_off = 0;
     static constexpr int atex_off = ring_off + STAGES * stage_bytes;
@@ -115,8 +125,11 @@ struct Cfg {
     static constexpr int bar_off = xchg_off + 4 * (EPQ - 1) * 4 * 32 * 16;
     static constexpr int n_bars = 2 * STAGES + 2 + 2 + 2 + 2 + 2 + 16;
     static constexpr int misc_off = bar_off + n_bars * 8;
-    // at least 120 KB so that two CTAs never share an SM (each holds all 512 TMEM columns)
-    static constexpr int smem_bytes = misc_off + 16 > 120 * 1024 ? misc_off + 16 : 120 * 1024;
+    // a floor on the shared memory keeps a third CTA (or, with 512 columns,
+    // a second) off the SM, so that tensor memory allocation never waits
+    static constexpr int smem_floor = PAIR ? 80 * 1024 : 120 * 1024;
+    static constexpr int smem_bytes = misc_off + 16 > smem_floor ? misc_off + 16 : smem_floor;
+    static_assert(!PAIR || misc_off + 16 == pair_bytes, "two-CTA layout size");
     static constexpr uint32_t id_tex = TEX8 ? tc::idesc(BM, BN, 0, 0) : tc::idesc(BM, BN, 1, 1);
     static constexpr uint32_t id_bf16 = tc::idesc(BM, BN, 1, 1);
 };
@@ -267,8 +280,11 @@ __device__ __forceinline__ void two_sum(float ts, float& S, float& Cc) {
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
-__global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
+                                  (Cfg<TEX8, KS, PERSAMPLE>::MIN_BLOCKS)) sum_tc_kernel(TcArgs a) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
+    constexpr int EPQ = C::EPQ, EPI_WARPS = C::EPI_WARPS, CPW = C::CPW, NB = C::NB;
+    constexpr int PRODUCER = C::PRODUCER, MMA_WARP = C::MMA_WARP;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ring = smem + C::ring_off;
     uint8_t* atex = smem + C::atex_off;
@@ -307,7 +323,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
         tc::fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(tmem_base_s, TMEM_COLS);
+        tc::tmem_alloc(tmem_base_s, C::TMEM_COLS);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -369,14 +385,14 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                     ok = spin_bar(acol_full + cb, (uint32_t)((li >> 1) & 1), abort_flag, a.d_err, 4);
                     const int nt = tiles_of(im.tile_off, i);
                     for (int t = 0; ok && t < nt; ++t, ++it) {
-                        const int s = (int)(it % C::STAGES), b = (int)(it & 1);
+                        const int s = (int)(it % C::STAGES), b = (int)(it % NB);
                         ok = spin_bar(full + s, (uint32_t)((it / C::STAGES) & 1), abort_flag, a.d_err, 5) &&
-                             spin_bar(tmem_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag,
+                             spin_bar(tmem_empty + b, (uint32_t)(((it / NB) & 1) ^ 1), abort_flag,
                                       a.d_err, 6);
                         if (!ok) break;
                         tc::fence_after_sync();
                         const uint32_t d1 = tmem + (uint32_t)(b * BN);
-                        const uint32_t dl = tmem + 256u + (uint32_t)(b * BN);
+                        const uint32_t dl = tmem + (uint32_t)((NB + b) * BN);
                         const uint8_t* st = ring + s * C::stage_bytes;
                         if (PERSAMPLE) {
 #pragma unroll
@@ -403,7 +419,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
             }
             // drain: the last MMAs must finish before the tensor memory is freed
             if (last >= 0)
-                tc::mbar_wait(tmem_full + (int)(last & 1), (uint32_t)((last >> 1) & 1),
+                tc::mbar_wait(tmem_full + (int)(last % NB), (uint32_t)((last / NB) & 1),
                               tc::globaltimer() + WAIT_NS);
         }
     } else {
@@ -511,8 +527,8 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 for (int t = 0; t < nt; ++t, ++it) {
                     const int2 c = c_next;
                     if (t + 1 < nt) c_next = im.tile_c[t0 + t + 1];
-                    const int b = (int)(it & 1);
-                    ok = spin_warp(tmem_full + b, (uint32_t)((it >> 1) & 1), abort_flag, a.d_err, 10);
+                    const int b = (int)(it % NB);
+                    ok = spin_warp(tmem_full + b, (uint32_t)((it / NB) & 1), abort_flag, a.d_err, 10);
                     if (!ok) break;
                     tc::fence_after_sync();
                     const int nvalid = min(BN, m_i - t * BN);
@@ -528,7 +544,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                         float ts = 0.f;
 #pragma unroll
                         for (int ch = 0; ch < CPW / 16; ++ch) {
-                            tc::tmem_ld16x2_wait(lb + 16u * ch, lb + 256u + 16u * ch, x1, xl);
+                            tc::tmem_ld16x2_wait(lb + 16u * ch, lb + (uint32_t)(NB * BN) + 16u * ch, x1, xl);
                             ts += sum16_full(x1, xl, na2, bt2, k2);
                         }
                         two_sum(ts, S, Ccomp);
@@ -538,7 +554,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                         for (int ch = 0; ch < CPW / 16; ++ch) {
                             const int nv = nvalid - cbase - 16 * ch;
                             if (nv > 0) {  // warp-uniform
-                                tc::tmem_ld16x2_wait(lb + 16u * ch, lb + 256u + 16u * ch, x1, xl);
+                                tc::tmem_ld16x2_wait(lb + 16u * ch, lb + (uint32_t)(NB * BN) + 16u * ch, x1, xl);
                                 const float ts = nv >= 16 ? sum16_full(x1, xl, na2, bt2, k2)
                                                           : sum16_part(x1, xl, nv, na2, bt2, k2);
                                 two_sum(ts, S, Ccomp);
@@ -553,9 +569,10 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
                 }
                 if (!ok) break;
                 // merge the EPQ column parts of each pixel. Four exchange
-                // buffers: a part can run at most two sample tiles ahead of
-                // another (tensor memory is double-buffered and every label has
-                // at least one tile), so buffer li & 3 is free when rewritten.
+                // buffers: a part can run at most NB <= 2 sample tiles ahead
+                // of another (tensor memory holds NB accumulators and every
+                // label has at least one tile), so buffer li & 3 is free when
+                // rewritten.
                 const int xbuf = (int)(li & 3);
                 float4* xb = xchg + (size_t)xbuf * (EPQ - 1) * 4 * 32;
                 uint64_t* xbar = xchg_full + xbuf * 4 + q;
@@ -647,7 +664,7 @@ __global__ void __launch_bounds__(THREADS, 1) sum_tc_kernel(TcArgs a) {
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, TMEM_COLS);
+        tc::tmem_dealloc(tmem, C::TMEM_COLS);
     }
 }
 
@@ -974,8 +991,9 @@ cudaError_t sum(const TcImage* descs, int n_images, int n_items, const TcSumPara
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.fb_count, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    const int grid = n_items < p.n_sm ? n_items : p.n_sm;
-    sum_tc_kernel<TEX8, KS, PERSAMPLE><<<grid, THREADS, C::smem_bytes, st>>>(a);
+    const int slots = C::MIN_BLOCKS * p.n_sm;
+    const int grid = n_items < slots ? n_items : slots;
+    sum_tc_kernel<TEX8, KS, PERSAMPLE><<<grid, C::THREADS, C::smem_bytes, st>>>(a);
     refine_fp64_kernel<<<2 * p.n_sm, 128, 0, st>>>(
         descs, p.fb_list, p.fb_count, p.fb_cap, (p.k + 31) / 32, (double)p.alpha, (double)p.d_min,
         (double)p.kappa_beta, (double)p.sigma_c2, PERSAMPLE, p.d_err);
