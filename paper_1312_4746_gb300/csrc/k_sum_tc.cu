@@ -63,6 +63,7 @@ constexpr int TW = 16, TH = 8;          // pixel tile 16 x 8
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr float LN2 = 0.6931471805599453f;
 constexpr uint64_t WAIT_NS = 1000000000ull;  // 1 s per wait
+constexpr uint32_t SUSPEND_NS = 1000u;       // longest suspension of one barrier test
 // The sum runs on 2^(e + SHIFT_i) with SHIFT_i = 96 - ceil(log2 m_i): every
 // term is <= 2^96 / m_i, so the row sum stays below 2^96. A shifted total
 // below m_i 2^-100 may have lost mass to FP32 underflow (each lost term is
@@ -156,14 +157,16 @@ __device__ __forceinline__ void set_abort(volatile int* abort_flag, int* d_err, 
     if (atomicCAS(d_err, 0, CS_DEVERR_TIMEOUT) == 0) d_err[1] = site;
 }
 
-// Single-thread bounded wait by polling (no suspension, so the thread reacts
-// as soon as the phase completes); the timer is read every 256 polls.
+// Single-thread bounded wait. Each test may suspend the thread for up to
+// 1 us (it resumes when the phase completes), so a waiting warp takes no
+// issue slots from the working warps of the SM's other CTA; the timer is
+// read every 256 tests.
 __device__ __forceinline__ bool spin_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                          int* d_err, int site) {
     if (*abort_flag) return false;
     uint64_t deadline = 0;
     for (uint32_t n = 0;; ++n) {
-        if (tc::mbar_test_wait(bar, parity)) return true;
+        if (tc::mbar_try_wait(bar, parity, SUSPEND_NS)) return true;
         if ((n & 255u) == 255u) {
             const uint64_t now = tc::globaltimer();
             if (deadline == 0) deadline = now + WAIT_NS;
@@ -174,13 +177,13 @@ __device__ __forceinline__ bool spin_bar(uint64_t* bar, uint32_t parity, volatil
     return false;
 }
 
-// Warp-uniform polling wait (every lane tests the same phase, so the warp
-// stays converged; the timer is read every 256 polls).
+// Warp-uniform bounded wait (every lane tests the same phase, so the warp
+// stays converged); suspending tests as in spin_bar.
 __device__ __forceinline__ bool spin_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           int* d_err, int site) {
     uint64_t deadline = 0;
     for (uint32_t n = 0;; ++n) {
-        if (__all_sync(0xffffffffu, tc::mbar_test_wait(bar, parity))) return true;
+        if (__all_sync(0xffffffffu, tc::mbar_try_wait(bar, parity, SUSPEND_NS))) return true;
         if ((n & 255u) == 255u) {
             int late = 0;
             if ((threadIdx.x & 31) == 0) {
