@@ -346,8 +346,8 @@ void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2) {
     L.seedbits = c.take<uint32_t>((size_t)n * L.H * ((L.W + 31) / 32));
     L.colbuf = c.take<int32_t>(P * n);
     // envelope stacks: two halves of (H + 1) / 2 rows per column
-    L.vbuf = c.take<int32_t>((size_t)((L.H + 1) / 2) * 2 * L.W * n);
-    L.fbuf = c.take<int32_t>((size_t)((L.H + 1) / 2) * 2 * L.W * n);
+    L.vbuf = c.take<int32_t>((size_t)(L.H + 7) * L.W * n);  // S ceil(H / S) <= H + 7 rows
+    L.fbuf = c.take<int32_t>((size_t)(L.H + 7) * L.W * n);
     int32_t* d2s = c.take<int32_t>(dist2 ? 0 : P * n);
     L.d2 = dist2 ? dist2 : d2s;
     L.t.sx = c.take<float>(S);

@@ -131,7 +131,7 @@ struct EdtArgs {
     int n_samples;
     uint32_t* seedbits;  // scratch n_labels * H * ceil(W/32)
     int32_t* colbuf;  // scratch n_labels * P (horizontal distances)
-    int32_t* vbuf;    // scratch n_labels * W * 2 ceil(H/2) (envelope rows, when not in shared memory)
+    int32_t* vbuf;    // scratch n_labels * W * (H + 7) (envelope rows, when not in shared memory)
     int32_t* fbuf;    // scratch, same size (envelope values, likewise)
     int32_t* dist2;   // output n_labels * P
     int* d_err;

@@ -6,9 +6,10 @@
 //   1. seed bitmaps: one bit per pixel and label;
 //   2. row pass (one warp per label and row): horizontal distance h to the
 //      nearest seed in the same row, from bit scans of the bitmap words;
-//   3. column pass (a builder thread per label and column, four readers):
-//      lower envelope of the parabolas (y - q)^2 + h(q)^2 over the rows q
-//      with finite h, built in one sweep and read back by row ranges; intersection
+//   3. column pass (2, 4 or 8 builder threads per label and column, one per
+//      row segment, and eight readers): lower envelopes of the parabolas
+//      (y - q)^2 + h(q)^2 over each segment's rows q with finite h, each
+//      built in one sweep and read back by row ranges; intersection
 //      abscissae are compared as exact rationals with 64-bit cross products,
 //      so the result equals the brute-force minimum bit for bit. For images
 //      with few columns and rows (labels x width < 16384, height <= 64) an
@@ -19,6 +20,7 @@
 // majority co-support of each label (Eq. tex-rep: bit set iff 2 * count >= m).
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -87,17 +89,19 @@ __global__ void rows_binary_kernel(int H, int W, int n_labels, const uint32_t* _
     }
 }
 
-// Column pass, split: in each block of 32 columns two warps build the lower
-// envelopes of every column, warp b over the rows of half b (one thread per
-// column and half; one sweep over the half's rows with finite h: a row's
-// parabola (y - q)^2 + h(q)^2 replaces the stack top while it lies below it
-// from the top's breakpoint on, compared exactly with 64-bit cross
+// Column pass, split: in each block of 32 columns S warps build the lower
+// envelopes of every column, warp b over the rows of segment b (one thread
+// per column and segment; one sweep over the segment's rows with finite h: a
+// row's parabola (y - q)^2 + h(q)^2 replaces the stack top while it lies
+// below it from the top's breakpoint on, compared exactly with 64-bit cross
 // products); then all NSEG warps read them back, warp s for the rows
 // [s H / NSEG, (s + 1) H / NSEG): each thread finds the segment of its first
-// row in both half-envelopes by binary search over the breakpoints (the same
-// exact comparison, monotone in the segment index), walks on, and keeps the
-// smaller of the two values, the minimum over all rows.
-constexpr int NSEG = 4;
+// row in each of the S envelopes by binary search over the breakpoints (the
+// same exact comparison, monotone in the segment index), walks on, and keeps
+// the smallest of the S values, the minimum over all rows. More segments
+// shorten the sequential sweeps at the cost of more envelopes per read.
+constexpr int NSEG = 8;  // reader warps per block (and the most segments)
+
 
 __device__ __forceinline__ int env_build(const int32_t* __restrict__ col, int W, int q_lo, int q_hi,
                                          int32_t* v, int32_t* F, long long stride) {
@@ -162,23 +166,24 @@ __device__ __forceinline__ int32_t env_value(EnvCursor& c, const int32_t* v, con
     return (y - c.vj) * (y - c.vj) + (c.Fj - c.vj * c.vj);
 }
 
-template <bool SHARED>
+template <bool SHARED, int S>
 __global__ void __launch_bounds__(32 * NSEG) cols_envelope_split_kernel(
     int H, int W, int n_labels, const int32_t* __restrict__ h, int32_t* __restrict__ gv,
     int32_t* __restrict__ gF, int32_t* __restrict__ dist2) {
+    static_assert(S >= 1 && S <= NSEG, "segments");
     extern __shared__ int32_t smem[];
-    __shared__ int s_kk[2][32];
+    __shared__ int s_kk[S][32];
     const long long ncol = (long long)n_labels * W;
     const int c = threadIdx.x & 31, seg = threadIdx.x >> 5;
     const long long col_id = blockIdx.x * 32ll + c;
     const bool valid = col_id < ncol;
     const int i = valid ? (int)(col_id / W) : 0, x = valid ? (int)(col_id % W) : 0;
-    const int HH = (H + 1) / 2;  // rows (and stack entries) per half
+    const int HS = (H + S - 1) / S;  // rows (and stack entries) per segment
     int32_t *v, *F;
     long long stride;
     if (SHARED) {
         v = smem + c;
-        F = smem + (size_t)2 * HH * 32 + c;
+        F = smem + (size_t)S * HS * 32 + c;
         stride = 32;
     } else {
         v = gv + col_id;
@@ -186,25 +191,32 @@ __global__ void __launch_bounds__(32 * NSEG) cols_envelope_split_kernel(
         stride = ncol;
     }
     const int32_t* col = h + (size_t)i * H * W + x;
-    if (seg < 2 && valid) {
-        const int q_lo = seg * HH, q_hi = min(H, q_lo + HH);
-        s_kk[seg][c] = env_build(col, W, q_lo, q_hi, v + (size_t)seg * HH * stride,
-                                 F + (size_t)seg * HH * stride, stride);
+    if (seg < S && valid) {
+        const int q_lo = seg * HS, q_hi = min(H, q_lo + HS);
+        s_kk[seg][c] = q_lo < q_hi ? env_build(col, W, q_lo, q_hi, v + (size_t)seg * HS * stride,
+                                               F + (size_t)seg * HS * stride, stride)
+                                   : -1;
     }
     __syncthreads();  // envelopes complete (shared or global) for the whole block
     if (!valid) return;
     int32_t* out = dist2 + (size_t)i * H * W + x;
     const int y0 = (int)((long long)H * seg / NSEG), y1 = (int)((long long)H * (seg + 1) / NSEG);
-    const int k0 = s_kk[0][c], k1 = s_kk[1][c];
-    const int32_t* v1 = v + (size_t)HH * stride;
-    const int32_t* F1 = F + (size_t)HH * stride;
-    EnvCursor c0{}, c1{};
-    if (k0 >= 0) c0 = env_seek(v, F, stride, k0, y0);
-    if (k1 >= 0) c1 = env_seek(v1, F1, stride, k1, y0);
+    EnvCursor cur[S];
+    int kk[S];
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        kk[b] = s_kk[b][c];
+        if (kk[b] >= 0)
+            cur[b] = env_seek(v + (size_t)b * HS * stride, F + (size_t)b * HS * stride, stride,
+                              kk[b], y0);
+    }
     for (int y = y0; y < y1; ++y) {
         int32_t d = INF;  // INF when the label has no valid seed (a bad sample index)
-        if (k0 >= 0) d = env_value(c0, v, F, stride, y);
-        if (k1 >= 0) d = min(d, env_value(c1, v1, F1, stride, y));
+#pragma unroll
+        for (int b = 0; b < S; ++b)
+            if (kk[b] >= 0)
+                d = min(d, env_value(cur[b], v + (size_t)b * HS * stride,
+                                     F + (size_t)b * HS * stride, stride, y));
         out[(size_t)y * W] = d;
     }
 }
@@ -309,18 +321,29 @@ cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st) {
                                                                        a.colbuf, a.dist2);
         return cudaGetLastError();
     }
-    // envelopes of 32 columns per block (two halves) in shared memory when they fit
-    const size_t smem = (size_t)((a.H + 1) / 2) * 2 * 2 * sizeof(int32_t) * 32;
+    // envelopes of 32 columns per block (S segments) in shared memory when they fit
     const unsigned nblk = (unsigned)((ncol + 31) / 32);
-    if (smem <= 110u * 1024u) {
-        cudaFuncSetAttribute(cols_envelope_split_kernel<true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cols_envelope_split_kernel<true><<<nblk, 32 * NSEG, smem, st>>>(
-            a.H, a.W, a.n_labels, a.colbuf, nullptr, nullptr, a.dist2);
-    } else {
-        cols_envelope_split_kernel<false><<<nblk, 32 * NSEG, 0, st>>>(
-            a.H, a.W, a.n_labels, a.colbuf, a.vbuf, a.fbuf, a.dist2);
-    }
+    auto run = [&](auto seg_c) -> cudaError_t {
+        constexpr int S = decltype(seg_c)::value;
+        const size_t smem = (size_t)((a.H + S - 1) / S) * S * 2 * sizeof(int32_t) * 32;
+        if (smem <= 110u * 1024u) {
+            cudaError_t e2 = cudaFuncSetAttribute(cols_envelope_split_kernel<true, S>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem);
+            if (e2 != cudaSuccess) return e2;
+            cols_envelope_split_kernel<true, S><<<nblk, 32 * NSEG, smem, st>>>(
+                a.H, a.W, a.n_labels, a.colbuf, nullptr, nullptr, a.dist2);
+        } else {
+            cols_envelope_split_kernel<false, S><<<nblk, 32 * NSEG, 0, st>>>(
+                a.H, a.W, a.n_labels, a.colbuf, a.vbuf, a.fbuf, a.dist2);
+        }
+        return cudaSuccess;
+    };
+    // the fewest segments (2, 4 or 8) whose sweeps are at most 128 rows long
+    e = a.H > 512 ? run(std::integral_constant<int, 8>{})
+      : a.H > 256 ? run(std::integral_constant<int, 4>{})
+                  : run(std::integral_constant<int, 2>{});
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

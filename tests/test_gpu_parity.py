@@ -237,10 +237,13 @@ def test_data_term_entry(env, precision):
 @pytest.mark.parametrize("H,W,nl,m,seed", [
     (12, 5500, 3, [40, 1, 300], 31),   # labels x width >= 16384: envelope column pass
     (60, 90, 2, [1, 25], 32),          # short image, few columns: outward-scan column pass
-    (1030, 15, 2, [3, 9], 33),         # tall and narrow: envelope pass, global-memory stacks
+    (1030, 15, 2, [3, 9], 33),         # tall and narrow: 8 envelope segments, global-memory stacks
+    (200, 70, 2, [5, 30], 34),         # 2 segments, shared-memory stacks
+    (400, 50, 3, [2, 17, 60], 35),     # 4 segments, shared-memory stacks
+    (480, 33, 2, [1, 40], 36),         # 4 segments, global-memory stacks; segments without seeds
 ])
 def test_distance_transform_paths(env, H, W, nl, m, seed):
-    """Both column passes of the exact distance transform equal brute force."""
+    """Every column pass of the exact distance transform equals brute force."""
     cs, ctx, torch = env
     rng = np.random.default_rng(seed)
     P = H * W
