@@ -344,13 +344,15 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
             const int ox = (pt % im.ntx) * TW, oy = (pt / im.ntx) * TH;
             for (int i = 0; ok && i < im.n_labels; ++i) {
                 const int t0 = im.tile_off[i], nt = tiles_of(im.tile_off, i);
+                int2 c_next = im.tile_c[t0];  // anchors fetched one tile ahead
                 for (int t = 0; ok && t < nt; ++t, ++it) {
                     const int s = (int)(it % C::STAGES);
                     const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
+                    const int2 c = c_next;
+                    if (t + 1 < nt) c_next = im.tile_c[t0 + t + 1];
                     ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1);
                     if (!ok) break;
                     uint8_t* st = ring + s * C::stage_bytes;
-                    const int2 c = im.tile_c[t0 + t];
 #pragma unroll
                     for (int u = 0; u < BM / 32; ++u) {
                         const int r = u * 32 + lane;
