@@ -156,7 +156,7 @@ struct SampleTables {
     int32_t* spop;    // popcount of each sample's bitmask
     uint32_t* rep;    // [n_labels][Wk]
     uint8_t* blob;    // tensor-core sample tiles (ring-stage layout)
-    int2* tile_c;     // tensor-core sample tile anchors
+    uint32_t* tile_xy;  // tensor-core tile slots: sample position x | y << 16
     int32_t* perm;    // tensor-core sample order (Morton order in chunks of 4096)
 };
 cudaError_t launch_gather(const float* img, int H, int W, const uint32_t* bitmask, int k,
@@ -239,7 +239,7 @@ struct TcImage {
     const int32_t* label_off;  // n_labels + 1
     const int32_t* tile_off;   // first sample tile of each label, n_labels + 1
     const uint8_t* blob;       // sample tiles in ring-stage layout
-    const int2* tile_c;        // sample tile anchors
+    const uint32_t* tile_xy;   // per tile slot: sample position x | y << 16
     const uint32_t* rep;       // majority co-supports (factorised form)
     float* neglog;
     float* post;
@@ -296,6 +296,7 @@ struct TcLaunch {
 };
 size_t tc_copy_bytes(int k, bool tex8, bool persample);
 int tc_tiles_per_label(int m);
+int tc_tile_samples();  // samples per tensor-core sample tile
 int tc_pixel_tiles(int H, int W);
 bool tc_supported(int k, bool tex8);
 // Morton order of the samples (needs only the label offsets and sample

@@ -2,29 +2,25 @@
 // of Sec. 3.1 Eq. (color) x Eq. (post_text) (per-sample or factorised).
 //
 // Per pixel x and label i (log2 units, C = log2(e) / (2 sigma_c2),
-// Bt = log2(e) / beta_i(x), nA = -log2(e) / (2 rho_i(x)^2)):
+// Bt = log2(e) / beta_i(x), nA = -log2(e) / (2 rho_i(x)^2), f = nA / Bt):
 //   e_j = nA |x - x_j|^2 - C |I - I_j|^2 - Bt TSM(b_x, b_j)
-//       = Bt D1_j + nA (Dl_j + K) + R0,
+//       = Bt D1_j + nA |x'|^2 + R0,
 //   D1_j = sum_t (2 b_x,t - 1) b_j,t  +  (1/Bt) (2 C I.I_j - C |I_j|^2)
-//   Dl_j = -2 x'.s_j - 2 delta.s_j + |s_j|^2,   R0 = -Bt |b_x| - C |I|^2,
-//   K = |x'|^2 + |delta|^2 + 2 x'.delta,
-// where x' = x - o (o the pixel tile's origin), s_j = x_j - c (c the first
-// sample of the sample tile, its anchor) and delta = o - c, so that
-// |x - x_j|^2 = |x' - s_j + delta|^2 = Dl_j + K.
-// The texture sum is an exact integer (2 b_x.b_j - |b_j|, so TSM = |b_x| minus
-// it) from an FP8 (e4m3, values 0 and +-1) or BF16 MMA; the colour part is a
-// 16-wide BF16 MMA over hi/lo splits of both factors (relative error about
-// 2^-17) into the same FP32 accumulator. Dl is a second 16-wide BF16 MMA whose
-// operands are exact small integers: x' < 16 x 8; s = 128 h + l and
-// delta = 128 dh + dl with |h|, |dh| < 256 and 0 <= l, dl < 128 (the cross
-// term delta.s as four products of pieces); |s|^2 in four exact BF16 pieces.
-// The samples of each label are sorted in Morton order in chunks of 4096, so
-// a sample tile spans a small region; then every partial sum of Dl for a
-// sample near the pixel stays below 2^24 and the squared distance is exact
-// (it is exact whenever the tile spans less than ~2300 pixels). The
-// B operand of Dl is precomputed per sample tile; the producer writes only
-// the A operand's delta entries per stage. In the factorised form D1 is the
-// colour part alone with Bt = 1.
+//          + f (-2 x'.u_j + |u_j|^2),                R0 = -Bt |b_x| - C |I|^2,
+// where x' = x - o and u_j = x_j - o relative to the centre o of the pixel
+// tile, so that |x - x_j|^2 = |x'|^2 - 2 x'.u_j + |u_j|^2 with |x'| <= 9:
+// the location terms carry the magnitude of |x - x_j|^2 itself (no
+// cancellation between large offsets). One FP32 accumulator per sample
+// receives all of it from tcgen05 MMAs: the texture sum (an exact integer,
+// 2 b_x.b_j - |b_j|, so TSM = |b_x| minus it) from an FP8 (e4m3, values 0
+// and +-1) or BF16 MMA; the colour part from a 16-wide BF16 MMA over hi/lo
+// splits of both factors (relative error about 2^-17); the location part
+// from two 16-wide BF16 MMAs whose sample side is exact (2u in two bf16
+// pieces per axis, |u|^2 in four) and whose pixel side holds three-piece
+// splits of -f x' and f (relative error below 2^-24). The sample side of
+// the location is formed per (pixel tile, sample tile) by the producer from
+// the sample positions; the pixel side per label by the epilogue. In the
+// factorised form D1 holds the colour and location parts with Bt = 1.
 //
 // All full exponents are <= 0, so no running maximum is needed: the row sum
 // accumulates 2^(e + shift) with a fixed shift 96 - ceil(log2 m_i) (no term
@@ -34,17 +30,20 @@
 // m_i 2^-100 (terms may have underflowed) or when the row's a-priori error
 // bound exceeds l_tol max(|L|, 1) (derivation at the flagging site).
 //
-// One persistent CTA per SM; a pixel tile is 16 x 8 pixels (one TMEM lane
-// each), a sample tile 128 samples (one TMEM column each).
-//   warp 16      producer: per stage, bulk-copies (TMA) the pre-laid-out
-//                texture, colour and location slabs of a sample tile and
-//                writes the pixel-side location slab (x' and delta entries)
-//   warp 17      MMA issuer: D1 <- texture slabs + colour slab,
-//                Dl <- location slab; TMEM double-buffered (4 x 128 columns)
-//   warps 0..15  epilogue: warp w reads lanes 32 (w % 4) .. +31 and columns
-//                32 (w / 4) .. +31 of each tile (two 16-column loads),
-//                merges the four column parts per label and normalises
-//                over labels.
+// Two persistent CTAs per SM (one where the shared-memory layout does not
+// fit twice); a pixel tile is 16 x 8 pixels (one TMEM lane each), a sample
+// tile 128 samples (one TMEM column each).
+//   warp 8       producer: per stage, bulk-copies (TMA) the pre-laid-out
+//                texture and colour slabs of a sample tile and writes its
+//                two location slabs for this pixel tile
+//   warp 9       MMA issuer: D1 <- texture slabs + colour slab + location
+//                slabs; TMEM double-buffered (2 x 128 columns per CTA), so
+//                one tile's MMAs run while the epilogue reads the previous
+//   warps 0..7   epilogue: per label, writes the pixel-side colour and
+//                location rows; warp w reads lanes 32 (w % 4) .. +31 and
+//                columns 64 (w / 4) .. +63 of each tile (16-column loads),
+//                merges the two column parts per label and normalises over
+//                labels (16 warps of 32 columns in the one-CTA layout).
 // Every mbarrier wait is bounded by the global timer; on expiry the CTA sets
 // the device error word, stops issuing, drains its copies and MMAs, frees its
 // tensor memory and exits.
@@ -94,43 +93,53 @@ __device__ __forceinline__ int image_of(const TcArgs& a, int g) {
 
 template <bool TEX8, int KS, bool PERSAMPLE>
 struct Cfg {
+    // ring stage: texture slabs, colour slab (both bulk-copied), then the two
+    // sample-side location slabs the producer writes
     static constexpr int tex_bytes = PERSAMPLE ? KS * 4096 : 0;
     static constexpr int col_off = tex_bytes;
-    static constexpr int bloc_off = tex_bytes + 4096;         // sample-side location slab
-    static constexpr int aloc_off = tex_bytes + 2 * 4096;     // pixel-side location slab
-    static constexpr int copy_bytes = tex_bytes + 2 * 4096;   // bulk-copied part of a stage
+    static constexpr int copy_bytes = tex_bytes + 4096;       // bulk-copied part of a stage
+    static constexpr int bl_off = tex_bytes + 4096;           // location slabs L0, L1
     static constexpr int stage_bytes = tex_bytes + 3 * 4096;
-    // Two CTAs per SM, each with one 256-column accumulator (D1 | Dl), a
-    // two-stage ring and 8 epilogue warps, when that layout fits twice in the
-    // SM's 228 KB: one CTA's epilogue then overlaps the other's MMAs. Else one
-    // CTA per SM with a double-buffered 512-column accumulator and 16
-    // epilogue warps.
-    static constexpr int pair_bytes = 2 * stage_bytes + tex_bytes + 2 * 4096 + 4 * 4 * 32 * 16 +
-                                      (2 * 2 + 26) * 8 + 16;
-    static constexpr bool PAIR = 2 * (pair_bytes + 1024) <= 228 * 1024;
+    static constexpr int NB = 2;                              // D1 accumulators (128 columns each)
+    static constexpr uint32_t TMEM_COLS = 128u * NB;
+    static constexpr int XB = 2 * NB;                         // label-merge exchange buffers
+    static constexpr int AP = 3 * 4096;                       // pixel-side colour + L0 + L1 slabs
+    // Two CTAs per SM (each 256 TMEM columns, a sample ring of two or more
+    // stages, 8 epilogue warps) when that layout fits twice in the SM's
+    // 228 KB (a CTA of the pair may use 228 KB / 2 - 1 KB, the per-CTA
+    // reservation), with two label buffers of pixel-side operands or, if only
+    // that fits, one; else one CTA per SM with 16 epilogue warps.
+    static constexpr int PAIR_LIMIT = 228 * 1024 / 2 - 1024;
+    static constexpr int pair_bytes(int stages, int acb) {
+        return stages * stage_bytes + tex_bytes + acb * AP + XB * 1 * 4 * 32 * 8 +
+               (2 * stages + 26) * 8 + 16;
+    }
+    static constexpr bool PAIR = pair_bytes(2, 1) <= PAIR_LIMIT;
+    static constexpr int ACB = !PAIR || pair_bytes(2, 2) <= PAIR_LIMIT ? 2 : 1;  // label buffers
     static constexpr int MIN_BLOCKS = PAIR ? 2 : 1;
-    static constexpr int NB = PAIR ? 1 : 2;                  // accumulator buffers
-    static constexpr uint32_t TMEM_COLS = 256u * NB;         // D1[b] at b BN, Dl[b] at (NB + b) BN
     static constexpr int EPQ = PAIR ? 2 : 4;                 // epilogue warps per TMEM lane quadrant
     static constexpr int EPI_WARPS = 4 * EPQ;
     static constexpr int CPW = BN / EPQ;                     // columns per epilogue warp per tile
     static constexpr int PRODUCER = EPI_WARPS;
     static constexpr int MMA_WARP = EPI_WARPS + 1;
     static constexpr int THREADS = (EPI_WARPS + 2) * 32;
-    static constexpr int STAGES = PAIR ? 2 : (KS <= 5 ? 4 : 3);  // sample-tile ring depth
+    // sample-tile ring depth: as deep as the shared memory allows (2 to 4)
+    static constexpr int STAGES = !PAIR                          ? (KS <= 5 ? 4 : 3)
+                                  : pair_bytes(4, ACB) <= PAIR_LIMIT ? 4
+                                  : pair_bytes(3, ACB) <= PAIR_LIMIT ? 3 : 2;
     // shared memory map
     static constexpr int ring_off = 0;
     static constexpr int atex_off = ring_off + STAGES * stage_bytes;
     static constexpr int acol_off = atex_off + tex_bytes;
-    static constexpr int xchg_off = acol_off + 2 * 4096;              // [4][EPQ-1][4][32] float4
-    static constexpr int bar_off = xchg_off + 4 * (EPQ - 1) * 4 * 32 * 16;
+    static constexpr int xchg_off = acol_off + ACB * AP;              // [XB][EPQ-1][4][32] float2
+    static constexpr int bar_off = xchg_off + XB * (EPQ - 1) * 4 * 32 * 8;
     static constexpr int n_bars = 2 * STAGES + 2 + 2 + 2 + 2 + 2 + 16;
     static constexpr int misc_off = bar_off + n_bars * 8;
-    // a floor on the shared memory keeps a third CTA (or, with 512 columns,
-    // a second) off the SM, so that tensor memory allocation never waits
+    // a floor on the shared memory keeps a third CTA (or, unpaired, a
+    // second) off the SM, so that tensor memory allocation never waits
     static constexpr int smem_floor = PAIR ? 80 * 1024 : 120 * 1024;
     static constexpr int smem_bytes = misc_off + 16 > smem_floor ? misc_off + 16 : smem_floor;
-    static_assert(!PAIR || misc_off + 16 == pair_bytes, "two-CTA layout size");
+    static_assert(!PAIR || misc_off + 16 == pair_bytes(STAGES, ACB), "two-CTA layout size");
     static constexpr uint32_t id_tex = TEX8 ? tc::idesc(BM, BN, 0, 0) : tc::idesc(BM, BN, 1, 1);
     static constexpr uint32_t id_bf16 = tc::idesc(BM, BN, 1, 1);
 };
@@ -202,19 +211,56 @@ __device__ __forceinline__ int tiles_of(const int32_t* tile_off, int i) {
     return tile_off[i + 1] - tile_off[i];
 }
 
-// Pixel-side location row for tile-relative position (px, py) and offset
-// (dx, dy) = o - c: [-256 px, -2 px, -256 py, -2 py, -32768 dhx, -256 dhx,
-// -256 dlx, -2 dlx, (same for y), 1, 1, 1, 1] with d = 128 dh + dl.
-__device__ __forceinline__ void loc_row_a(int px, int py, int dx, int dy, uint4& lo, uint4& hi) {
-    const int dhx = dx >> 7, dlx = dx & 127, dhy = dy >> 7, dly = dy & 127;
-    const uint16_t one = bf16_bits(1.f);
-    lo = make_uint4(pack2(bf16_bits(-256.f * px), bf16_bits(-2.f * px)),
-                    pack2(bf16_bits(-256.f * py), bf16_bits(-2.f * py)),
-                    pack2(bf16_bits(-32768.f * dhx), bf16_bits(-256.f * dhx)),
-                    pack2(bf16_bits(-256.f * dlx), bf16_bits(-2.f * dlx)));
-    hi = make_uint4(pack2(bf16_bits(-32768.f * dhy), bf16_bits(-256.f * dhy)),
-                    pack2(bf16_bits(-256.f * dly), bf16_bits(-2.f * dly)), pack2(one, one),
-                    pack2(one, one));
+// Sample-side location rows (two 16-wide slabs L0, L1) of a sample at
+// packed position w (x | y << 16) relative to the pixel tile's centre
+// (cx, cy), u = x_j - centre: 2u per axis in two exact bf16 pieces (h, l),
+// |u|^2 (< 2^31) in four exact bf16 pieces q0..q3:
+//   L0 = [hx lx hx lx hx lx  hy ly hy ly hy ly  q0 q1 q2 q3],
+//   L1 = [q0 q1 q2 q0 q1 0 ...];
+// the pixel side holds the matching pieces of -f x' and f (see the
+// epilogue). The pieces are bit fields of the integers (at most 8
+// significant bits each, so exact in bf16): 2u = (2u & ~255) + (2u & 255)
+// and |u|^2 by bytes from its leading bit down. A padded sample has
+// q0 = 2^30 and zeros elsewhere, so that its exponent vanishes.
+__device__ __forceinline__ uint32_t bf16_exact(int v) {  // v has <= 8 significant bits
+    return __float_as_uint((float)v) >> 16;
+}
+__device__ __forceinline__ void loc_row_b(uint32_t w, int cx, int cy, bool valid, uint4& l0a,
+                                          uint4& l0b, uint4& l1a) {
+    if (!valid) {
+        l0a = make_uint4(0, 0, 0, 0);
+        l0b = make_uint4(0, 0, bf16_exact(1 << 30), 0);
+        l1a = make_uint4(0, 0, 0, 0);
+        return;
+    }
+    const int ux = (int)(w & 0xFFFFu) - cx, uy = (int)(w >> 16) - cy;  // |u| < 2^15
+    const int vx = 2 * ux, vy = 2 * uy;
+    const uint32_t px = bf16_exact(vx & ~255) | (bf16_exact(vx & 255) << 16);
+    const uint32_t py = bf16_exact(vy & ~255) | (bf16_exact(vy & 255) << 16);
+    // |u|^2 in bytes below its leading bit: q0 = bits [k, k + 8), q1 = bits
+    // [k - 8, k), ... (k = max(lead - 7, 0)), so that each piece is at most
+    // 2^-8 of the one before and the pixel side may drop the smallest products
+    const uint32_t q = (uint32_t)(ux * ux + uy * uy);
+    const int k0 = max(24 - __clz((int)q), 0), k1 = max(k0 - 8, 0), k2 = max(k0 - 16, 0);
+    const uint32_t q0 = bf16_exact((int)(q & (0xFFu << k0))),
+                   q1 = bf16_exact((int)(q & (0xFFu << k1) & ((1u << k0) - 1u))),
+                   q2 = bf16_exact((int)(q & (0xFFu << k2) & ((1u << k1) - 1u))),
+                   q3 = bf16_exact((int)(q & ((1u << k2) - 1u)));
+    l0a = make_uint4(px, px, px, py);
+    l0b = make_uint4(py, py, q0 | (q1 << 16), q2 | (q3 << 16));
+    l1a = make_uint4(q0 | (q1 << 16), q2 | (q0 << 16), q1, 0);
+}
+
+// Three bf16 pieces of an FP32 value (each the rounding of the exact
+// remainder; v = p1 + p2 + p3 + r with |r| <= 2^-24 |v|).
+__device__ __forceinline__ void split3_bf16(float v, uint16_t& p1, uint16_t& p2, uint16_t& p3) {
+    const __nv_bfloat16 b1 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(b1);
+    const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(b2);
+    p1 = __bfloat16_as_ushort(b1);
+    p2 = __bfloat16_as_ushort(b2);
+    p3 = bf16_bits(r2);
 }
 
 // Packed FP32 pairs (Blackwell f32x2 instructions: one issue, two lanes of
@@ -247,28 +293,25 @@ __device__ __forceinline__ uint64_t ex2x2(uint64_t v) {
 __device__ __forceinline__ float lo32(uint64_t v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float hi32(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
-// Sum over 16 columns of one pixel row of 2^e, e = nA Dl + Bt D1 + nKR
-// (log2 units, shifted full exponents); r1 / rl hold D1 / Dl as packed
-// column pairs. Full chunk: packed arithmetic; partial chunk: the first nv.
-__device__ __forceinline__ float sum16_full(const uint64_t (&r1)[8], const uint64_t (&rl)[8],
-                                            uint64_t na2, uint64_t bt2, uint64_t k2) {
+// Sum over 16 columns of one pixel row of 2^e, e = Bt D1 + k (log2 units,
+// shifted full exponents); r1 holds D1 as packed column pairs. Full chunk:
+// packed arithmetic; partial chunk: the first nv.
+__device__ __forceinline__ float sum16_full(const uint64_t (&r1)[8], uint64_t bt2, uint64_t k2) {
     uint64_t acc0 = 0, acc1 = 0;  // (0.f, 0.f)
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
-        const uint64_t v0 = fma2(na2, rl[u], fma2(bt2, r1[u], k2));
-        const uint64_t v1 = fma2(na2, rl[u + 1], fma2(bt2, r1[u + 1], k2));
-        acc0 = add2(acc0, ex2x2(v0));
-        acc1 = add2(acc1, ex2x2(v1));
+        acc0 = add2(acc0, ex2x2(fma2(bt2, r1[u], k2)));
+        acc1 = add2(acc1, ex2x2(fma2(bt2, r1[u + 1], k2)));
     }
     const uint64_t t = add2(acc0, acc1);
     return lo32(t) + hi32(t);
 }
-__device__ __forceinline__ float sum16_part(const uint64_t (&r1)[8], const uint64_t (&rl)[8],
-                                            int nv, uint64_t na2, uint64_t bt2, uint64_t k2) {
+__device__ __forceinline__ float sum16_part(const uint64_t (&r1)[8], int nv, uint64_t bt2,
+                                            uint64_t k2) {
     float t0 = 0.f, t1 = 0.f;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-        const uint64_t v = fma2(na2, rl[u], fma2(bt2, r1[u], k2));
+        const uint64_t v = fma2(bt2, r1[u], k2);
         t0 += 2 * u < nv ? ex2f(lo32(v)) : 0.f;
         t1 += 2 * u + 1 < nv ? ex2f(hi32(v)) : 0.f;
     }
@@ -292,7 +335,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
     uint8_t* ring = smem + C::ring_off;
     uint8_t* atex = smem + C::atex_off;
     uint8_t* acol = smem + C::acol_off;
-    float4* xchg = reinterpret_cast<float4*>(smem + C::xchg_off);
+    float2* xchg = reinterpret_cast<float2*>(smem + C::xchg_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::bar_off);
     uint64_t* full = bars;                    // [C::STAGES] producer arrival + TMA bytes
     uint64_t* empty = bars + C::STAGES;          // [C::STAGES] MMA commit
@@ -338,36 +381,64 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
         // ------------------------------------------------------------ producer
         uint32_t it = 0;  // tiles issued by this CTA (< 2^32 in any launch)
         bool ok = true;
+        // the upper half of every L1 row stays zero (made visible to the
+        // tensor cores by the proxy fence of each stage's first fill)
+        for (int s = 0; s < C::STAGES; ++s)
+            for (int j = lane; j < BN; j += 32)
+                *reinterpret_cast<uint4*>(ring + s * C::stage_bytes + C::bl_off + 4096 +
+                                          tc::slab_off(j, 16)) = make_uint4(0, 0, 0, 0);
         for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x) {
             const TcImage& im = a.images[image_of(a, g)];
             const int pt = g - im.first_item;
-            const int ox = (pt % im.ntx) * TW, oy = (pt / im.ntx) * TH;
-            for (int i = 0; ok && i < im.n_labels; ++i) {
-                const int t0 = im.tile_off[i], nt = tiles_of(im.tile_off, i);
-                int2 c_next = im.tile_c[t0];  // anchors fetched one tile ahead
-                for (int t = 0; ok && t < nt; ++t, ++it) {
+            // centre of the pixel tile: the origin of the location operands
+            const int cx = (pt % im.ntx) * TW + TW / 2, cy = (pt / im.ntx) * TH + TH / 2;
+            // the image's tiles are contiguous over its labels: walk them in
+            // order, with the next tile's sample positions fetched one tile
+            // ahead
+            const int T1 = im.tile_off[im.n_labels];
+            int i = 0, lab_first = im.tile_off[0], lab_end = im.tile_off[1];
+            int m_i = im.label_off[1] - im.label_off[0];
+            uint32_t w_next[BN / 32];  // positions of samples 32 u + lane of a tile
+#pragma unroll
+            for (int u = 0; u < BN / 32; ++u) w_next[u] = im.tile_xy[(size_t)lab_first * BN + 32 * u + lane];
+            for (int T = lab_first; ok && T < T1; ++T, ++it) {
+                if (T == lab_end) {  // every label has at least one tile
+                    ++i;
+                    lab_first = T;
+                    lab_end = im.tile_off[i + 1];
+                    m_i = im.label_off[i + 1] - im.label_off[i];
+                }
+                uint32_t w[BN / 32];
+#pragma unroll
+                for (int u = 0; u < BN / 32; ++u) {
+                    w[u] = w_next[u];
+                    if (T + 1 < T1) w_next[u] = im.tile_xy[(size_t)(T + 1) * BN + 32 * u + lane];
+                }
+                {
                     const int s = (int)(it % C::STAGES);
                     const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
-                    const int2 c = c_next;
-                    if (t + 1 < nt) c_next = im.tile_c[t0 + t + 1];
                     ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1);
                     if (!ok) break;
                     uint8_t* st = ring + s * C::stage_bytes;
+                    const int nvalid = min(BN, m_i - (T - lab_first) * BN);
+                    // the copy first, so that it lands while the location
+                    // slabs are written; the arrival follows them
+                    if (lane == 0) {
+                        tc::mbar_expect_tx(full + s, C::copy_bytes);
+                        tc::bulk_g2s(st, im.blob + (size_t)T * C::copy_bytes, C::copy_bytes, full + s);
+                    }
 #pragma unroll
-                    for (int u = 0; u < BM / 32; ++u) {
-                        const int r = u * 32 + lane;
-                        uint4 lo, hi;
-                        loc_row_a(r % TW, r / TW, ox - c.x, oy - c.y, lo, hi);
-                        *reinterpret_cast<uint4*>(st + C::aloc_off + tc::slab_off(r, 0)) = lo;
-                        *reinterpret_cast<uint4*>(st + C::aloc_off + tc::slab_off(r, 16)) = hi;
+                    for (int u = 0; u < BN / 32; ++u) {
+                        const int j = 32 * u + lane;
+                        uint4 l0a, l0b, l1a;
+                        loc_row_b(w[u], cx, cy, j < nvalid, l0a, l0b, l1a);
+                        *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 0)) = l0a;
+                        *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 16)) = l0b;
+                        *reinterpret_cast<uint4*>(st + C::bl_off + 4096 + tc::slab_off(j, 0)) = l1a;
                     }
                     tc::fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0) {
-                        tc::mbar_arrive_expect_tx(full + s, C::copy_bytes);
-                        tc::bulk_g2s(st, im.blob + (size_t)(t0 + t) * C::copy_bytes, C::copy_bytes,
-                                     full + s);
-                    }
+                    if (lane == 0) tc::mbar_arrive(full + s);
                 }
             }
         }
@@ -386,9 +457,10 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                 const TcImage& im = a.images[image_of(a, g)];
                 ok = spin_bar(atex_full, (uint32_t)(lpt & 1), abort_flag, a.d_err, 3);
                 for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
-                    const int cb = (int)(li & 1);
-                    ok = spin_bar(acol_full + cb, (uint32_t)((li >> 1) & 1), abort_flag, a.d_err, 4);
+                    const int cb = (int)(li % C::ACB);
+                    ok = spin_bar(acol_full + cb, (uint32_t)((li / C::ACB) & 1), abort_flag, a.d_err, 4);
                     const int nt = tiles_of(im.tile_off, i);
+                    const uint8_t* ap = acol + cb * C::AP;  // colour, L0, L1 slabs of this label
                     for (int t = 0; ok && t < nt; ++t, ++it) {
                         const int s = (int)(it % C::STAGES), b = (int)(it % NB);
                         ok = spin_bar(full + s, (uint32_t)((it / C::STAGES) & 1), abort_flag, a.d_err, 5) &&
@@ -397,7 +469,6 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                         if (!ok) break;
                         tc::fence_after_sync();
                         const uint32_t d1 = tmem + (uint32_t)(b * BN);
-                        const uint32_t dl = tmem + (uint32_t)((NB + b) * BN);
                         const uint8_t* st = ring + s * C::stage_bytes;
                         if (PERSAMPLE) {
 #pragma unroll
@@ -410,10 +481,12 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                                                  tc::smem_desc(st + sl * 4096), C::id_tex, sl > 0);
                             }
                         }
-                        tc::mma_bf16(d1, tc::smem_desc(acol + cb * 4096),
-                                     tc::smem_desc(st + C::col_off), C::id_bf16, PERSAMPLE ? 1 : 0);
-                        tc::mma_bf16(dl, tc::smem_desc(st + C::aloc_off),
-                                     tc::smem_desc(st + C::bloc_off), C::id_bf16, 0);
+                        tc::mma_bf16(d1, tc::smem_desc(ap), tc::smem_desc(st + C::col_off),
+                                     C::id_bf16, PERSAMPLE ? 1 : 0);
+                        tc::mma_bf16(d1, tc::smem_desc(ap + 4096), tc::smem_desc(st + C::bl_off),
+                                     C::id_bf16, 1);
+                        tc::mma_bf16(d1, tc::smem_desc(ap + 8192),
+                                     tc::smem_desc(st + C::bl_off + 4096), C::id_bf16, 1);
                         tc::mma_commit(empty + s);
                         tc::mma_commit(tmem_full + b);
                         last = it;
@@ -446,7 +519,9 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
             const float* Ip = im.img + (size_t)pix * 3;
             const float IR = Ip[0], IG = Ip[1], IB = Ip[2];
             const float I2 = fmaf(IR, IR, fmaf(IG, IG, IB * IB));
-            const int ox = (pt % im.ntx) * TW, oy = (pt / im.ntx) * TH;
+            // x' = position relative to the pixel tile's centre
+            const int xpx = rx - TW / 2, xpy = ry - TH / 2;
+            const float xsq = (float)(xpx * xpx + xpy * xpy);
             const uint32_t* bxp = im.bitmask + (size_t)pix * a.Wk;  // this pixel's co-support words
             int popx = 0;
             if (live)
@@ -501,69 +576,90 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                 const float Bt = PERSAMPLE ? LOG2E / (a.kappa_beta * rho) : 1.f;
                 const float g = PERSAMPLE ? (a.kappa_beta * rho) / LOG2E : 1.f;
                 const float R0 = (PERSAMPLE ? -Bt * (float)popx : 0.f) - Cc * I2;
-                // colour operand row (16 bf16): this warp writes half hf (hf < 2)
-                const int cb = (int)(li & 1);
-                ok = spin_warp(acol_empty + cb, (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag, a.d_err, 8);
+                // pixel-side operand rows of this label: colour (16 bf16, two
+                // halves) and location L0, L1 (pieces of -f x' and f, f =
+                // nA / Bt, matching the sample side's pieces of 2u and |u|^2);
+                // jobs 0..3 = colour half 0, colour half 1, L0, L1, job j on
+                // warp part j % EPQ
+                const int cb = (int)(li % C::ACB);
+                ok = spin_warp(acol_empty + cb, (uint32_t)(((li / C::ACB) & 1) ^ 1), abort_flag,
+                               a.d_err, 8);
                 if (!ok) break;
-                if (hf < 2) {
-                    uint16_t h0, l0, h1, l1;
-                    if (hf == 0) {
-                        split_bf16(2.f * Cc * g * IR, h0, l0);
-                        split_bf16(2.f * Cc * g * IG, h1, l1);
+                uint8_t* ap = acol + cb * C::AP;
+                const float f = nA * g;
+#pragma unroll
+                for (int job = hf; job < 4; job += EPQ) {
+                    uint4 lo = make_uint4(0, 0, 0, 0), hi = make_uint4(0, 0, 0, 0);
+                    if (job < 2) {
+                        uint16_t h0, l0, h1, l1;
+                        if (job == 0) {
+                            split_bf16(2.f * Cc * g * IR, h0, l0);
+                            split_bf16(2.f * Cc * g * IG, h1, l1);
+                        } else {
+                            split_bf16(2.f * Cc * g * IB, h0, l0);
+                            split_bf16(g, h1, l1);
+                        }
+                        lo = make_uint4(pack2(h0, h0), pack2(l0, l0), pack2(h1, h1), pack2(l1, l1));
                     } else {
-                        split_bf16(2.f * Cc * g * IB, h0, l0);
-                        split_bf16(g, h1, l1);
+                        uint16_t f1, f2, f3;
+                        split3_bf16(f, f1, f2, f3);
+                        if (job == 2) {
+                            uint16_t x1, x2, x3, y1, y2, y3;
+                            split3_bf16(-f * (float)xpx, x1, x2, x3);
+                            split3_bf16(-f * (float)xpy, y1, y2, y3);
+                            lo = make_uint4(pack2(x1, x1), pack2(x2, x2), pack2(x3, x3), pack2(y1, y1));
+                            hi = make_uint4(pack2(y2, y2), pack2(y3, y3), pack2(f1, f1), pack2(f1, f1));
+                        } else {
+                            lo = make_uint4(pack2(f2, f2), pack2(f2, f3), pack2(f3, 0), 0);
+                        }
                     }
-                    uint4 pk = make_uint4(pack2(h0, h0), pack2(l0, l0), pack2(h1, h1), pack2(l1, l1));
-                    if (!live) pk = make_uint4(0, 0, 0, 0);
-                    *reinterpret_cast<uint4*>(acol + cb * 4096 + tc::slab_off(r, 16 * hf)) = pk;
-                    tc::fence_proxy_async_smem();
+                    if (!live) lo = hi = make_uint4(0, 0, 0, 0);
+                    if (job < 2) {
+                        *reinterpret_cast<uint4*>(ap + tc::slab_off(r, 16 * job)) = lo;
+                    } else {
+                        uint8_t* sl = ap + 4096 * (job - 1);
+                        *reinterpret_cast<uint4*>(sl + tc::slab_off(r, 0)) = lo;
+                        *reinterpret_cast<uint4*>(sl + tc::slab_off(r, 16)) = hi;
+                    }
                 }
+                tc::fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(acol_full + cb);
 
-                const uint64_t na2 = pk2(nA, nA), bt2 = pk2(Bt, Bt);
+                const uint64_t bt2 = pk2(Bt, Bt);
                 const int m_i = im.label_off[i + 1] - im.label_off[i];
                 const float shift = (float)(96 - (32 - __clz(m_i - 1)));  // 96 - ceil(log2 m)
-                const float R0s = R0 + shift;
-                const int nt = tiles_of(im.tile_off, i), t0 = im.tile_off[i];
-                float S = 0.f, Ccomp = 0.f, wK = 0.f;  // wK: sum of tile sums x K
-                int2 c_next = im.tile_c[t0];  // anchors fetched one tile ahead
+                // e_j = Bt D1_j + nA |x'|^2 + R0 (+ shift)
+                const float R0x = fmaf(nA, xsq, R0);
+                const uint64_t k2 = pk2(R0x + shift, R0x + shift);
+                const int nt = tiles_of(im.tile_off, i);
+                float S = 0.f, Ccomp = 0.f;
                 for (int t = 0; t < nt; ++t, ++it) {
-                    const int2 c = c_next;
-                    if (t + 1 < nt) c_next = im.tile_c[t0 + t + 1];
                     const int b = (int)(it % NB);
                     ok = spin_warp(tmem_full + b, (uint32_t)((it / NB) & 1), abort_flag, a.d_err, 10);
                     if (!ok) break;
                     tc::fence_after_sync();
                     const int nvalid = min(BN, m_i - t * BN);
-                    // per-tile constant nA |x' + delta|^2 + R0, delta = o - c
-                    const float kx = (float)(rx + ox - c.x), ky = (float)(ry + oy - c.y);
-                    const float K = fmaf(kx, kx, ky * ky);
-                    const float nKR = fmaf(nA, K, R0s);
                     const int cbase = hf * CPW;
                     const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
-                    const uint64_t k2 = pk2(nKR, nKR);
-                    uint64_t x1[8], xl[8];
+                    uint64_t x1[8];
                     if (cbase + CPW <= nvalid) {  // warp-uniform: all columns valid
                         float ts = 0.f;
 #pragma unroll
                         for (int ch = 0; ch < CPW / 16; ++ch) {
-                            tc::tmem_ld16x2_wait(lb + 16u * ch, lb + (uint32_t)(NB * BN) + 16u * ch, x1, xl);
-                            ts += sum16_full(x1, xl, na2, bt2, k2);
+                            tc::tmem_ld16_wait_pk(lb + 16u * ch, x1);
+                            ts += sum16_full(x1, bt2, k2);
                         }
                         two_sum(ts, S, Ccomp);
-                        wK = fmaf(ts, K, wK);
                     } else if (cbase < nvalid) {  // warp-uniform: the label's last tile
 #pragma unroll
                         for (int ch = 0; ch < CPW / 16; ++ch) {
                             const int nv = nvalid - cbase - 16 * ch;
                             if (nv > 0) {  // warp-uniform
-                                tc::tmem_ld16x2_wait(lb + 16u * ch, lb + (uint32_t)(NB * BN) + 16u * ch, x1, xl);
-                                const float ts = nv >= 16 ? sum16_full(x1, xl, na2, bt2, k2)
-                                                          : sum16_part(x1, xl, nv, na2, bt2, k2);
+                                tc::tmem_ld16_wait_pk(lb + 16u * ch, x1);
+                                const float ts = nv >= 16 ? sum16_full(x1, bt2, k2)
+                                                          : sum16_part(x1, nv, bt2, k2);
                                 two_sum(ts, S, Ccomp);
-                                wK = fmaf(ts, K, wK);
                             }
                         }
                     }
@@ -573,28 +669,27 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                     tc::mbar_arrive_elect(tmem_empty + b);
                 }
                 if (!ok) break;
-                // merge the EPQ column parts of each pixel. Four exchange
-                // buffers: a part can run at most NB <= 2 sample tiles ahead
-                // of another (tensor memory holds NB accumulators and every
-                // label has at least one tile), so buffer li & 3 is free when
+                // merge the EPQ column parts of each pixel. XB = 2 NB exchange
+                // buffers: a part can run at most NB sample tiles ahead of
+                // another (tensor memory holds NB accumulators and every label
+                // has at least one tile), so buffer li % XB is free when
                 // rewritten.
-                const int xbuf = (int)(li & 3);
-                float4* xb = xchg + (size_t)xbuf * (EPQ - 1) * 4 * 32;
+                const int xbuf = (int)(li % C::XB);
+                float2* xb = xchg + (size_t)xbuf * (EPQ - 1) * 4 * 32;
                 uint64_t* xbar = xchg_full + xbuf * 4 + q;
                 if (hf > 0) {
-                    xb[((hf - 1) * 4 + q) * 32 + lane] = make_float4(S, Ccomp, wK, 0.f);
+                    xb[((hf - 1) * 4 + q) * 32 + lane] = make_float2(S, Ccomp);
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(xbar);
                 } else {
-                    ok = spin_warp(xbar, (uint32_t)((li >> 2) & 1), abort_flag, a.d_err, 11);
+                    ok = spin_warp(xbar, (uint32_t)((li / C::XB) & 1), abort_flag, a.d_err, 11);
                     if (!ok) break;
-                    float Sm = S, Cm = Ccomp, wKm = wK;
+                    float Sm = S, Cm = Ccomp;
 #pragma unroll
                     for (int h = 0; h < EPQ - 1; ++h) {
-                        const float4 v = xb[(h * 4 + q) * 32 + lane];
+                        const float2 v = xb[(h * 4 + q) * 32 + lane];
                         Sm += v.x;
                         Cm += v.y;
-                        wKm += v.z;
                     }
                     const float tot = Sm + Cm;  // shifted by 2^shift
                     const float lse2 = log2f(tot) - shift;
@@ -603,18 +698,25 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                     // below the floor the FP32 terms may have lost mass to
                     // underflow; above the tolerance the bound on the error of
                     // L (log2 units) is too loose: recompute in FP64. Bound:
-                    // colour splits 2^-15 C Q; the colour MMA's accumulation
-                    // onto the integer texture sum 2^-21 (Bt k + C Q); the FP32
-                    // epilogue 6u per pair, weighted by the pairs' shares of
-                    // the sum: |e_j| averages at most |log2 S| + log2 m, the
-                    // tile offsets |nA| K average |nA| wK / S, plus |R0|.
+                    // colour splits 2^-15 C Q. Accumulation of the colour and
+                    // the two location MMAs onto the exact texture sum, 2^-21
+                    // of the magnitudes per instruction, plus the location
+                    // pieces' residuals (<= 2^-24): at most 2^-19 (Bt k + C Q +
+                    // |nA| M_j), where the location products of sample j sum
+                    // in magnitude to M_j <= (|u_j| + |x'|)^2 <= 2 |x - x_j|^2 +
+                    // 8 |x'|^2 and |nA| |x - x_j|^2 <= |e_j| (every part of the
+                    // exponent is <= 0); weighted by the pairs' shares of the
+                    // sum, |e_j| averages at most |log2 S| + log2 m. The FP32
+                    // epilogue: 6u per pair on the same weights plus the
+                    // per-pixel constant.
                     const float im2 = im.imax2[i];
                     const float CQ = Cc * fmaf(2.f * sqrtf(I2), sqrtf(im2), im2);
                     const float BK = PERSAMPLE ? Bt * (float)a.k : 0.f;
+                    const float Ew = fabsf(lse2) + log2f((float)m_i);
                     const float E2 =
-                        3.1e-05f * CQ + 4.76837158203125e-07f * (BK + CQ) +
-                        3.5762787e-07f * (3.f * (fabsf(lse2) + log2f((float)m_i)) -
-                                          nA * (wKm / tot) + 2.f * fabsf(R0) + shift + 1.f);
+                        3.1e-05f * CQ +
+                        1.9073486e-06f * (BK + CQ - 8.f * nA * xsq + 2.f * Ew) +
+                        3.5762787e-07f * (3.f * Ew + 2.f * fabsf(R0x) + shift + 1.f);
                     if (!(tot >= FLOOR_PER_SAMPLE * (float)m_i) ||
                         (a.l_tol > 0.f && E2 * LN2 > a.l_tol * fmaxf(fabsf(Lv), 1.f)))
                         fmask |= 1ull << i;
@@ -839,17 +941,16 @@ __global__ void __launch_bounds__(1024) morton_sort_kernel(const int32_t* __rest
 }
 
 // Sample tiles laid out as the bulk-copied part of a ring stage: texture
-// slabs (b_j in {0, 1}), the colour slab (hi/lo bf16 of I_j and of
-// -C |I_j|^2) and the sample-side location slab ([h, l] of s = x_j - c per
-// axis, repeated as the pixel side's four cross products need, then |s|^2 in
-// four exact bf16 pieces); padded rows are zero except |s|^2 = 2^30, which
-// makes their exponents vanish. tile_c receives each tile's anchor c.
+// slabs (b_j in {0, 1}) and the colour slab (hi/lo bf16 of I_j and of
+// -C |I_j|^2); padded rows are zero. tile_xy receives each tile slot's
+// sample position x | y << 16 (the producer forms the location slabs from
+// it per pixel tile).
 template <bool TEX8, int KS, bool PERSAMPLE>
 __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
                                    const int32_t* __restrict__ tile_off, int n_labels,
                                    int total_tiles, SampleTables t, int n_samples, int k,
                                    float Cc, const int32_t* __restrict__ perm,
-                                   uint8_t* __restrict__ blob, int2* __restrict__ tile_c,
+                                   uint8_t* __restrict__ blob, uint32_t* __restrict__ tile_xy,
                                    float* __restrict__ imax2, TcImage desc,
                                    TcImage* __restrict__ desc_dst) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
@@ -867,9 +968,7 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
     const int pos = first + r;
     const bool valid = pos < label_off[i + 1];
     const int s = valid ? perm[pos] : 0;
-    const int s0 = perm[first];
-    const int cx = (int)t.sx[s0], cy = (int)t.sy[s0];
-    if (r == 0) tile_c[tile] = make_int2(cx, cy);
+    tile_xy[gid] = valid ? (uint32_t)t.sx[s] | ((uint32_t)t.sy[s] << 16) : 0u;
     uint8_t* st = blob + (size_t)tile * C::copy_bytes;
     if (PERSAMPLE) {
         for (int sl = 0; sl < KS; ++sl) {
@@ -899,7 +998,6 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
         }
     }
     uint32_t pw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t lw[8] = {0, 0, 0, 0, 0, 0, pack2(bf16_bits(1073741824.f), 0), 0};
     if (valid) {
         const float R = t.sr[s], G = t.sg[s], B = t.sb[s];
         const float i2 = fmaf(R, R, fmaf(G, G, B * B));
@@ -914,25 +1012,9 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
         pw[2] = pack2(hg, lg); pw[3] = pack2(hg, lg);
         pw[4] = pack2(hb, lb); pw[5] = pack2(hb, lb);
         pw[6] = pack2(hq, lq); pw[7] = pack2(hq, lq);
-        const int dx = (int)t.sx[s] - cx, dy = (int)t.sy[s] - cy;
-        const uint32_t hxl = pack2(bf16_bits((float)(dx >> 7)), bf16_bits((float)(dx & 127)));
-        const uint32_t hyl = pack2(bf16_bits((float)(dy >> 7)), bf16_bits((float)(dy & 127)));
-        // |s|^2 < 2^30 in four integer pieces of at most 8 significant bits
-        int rem = dx * dx + dy * dy;
-        uint16_t qp[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const __nv_bfloat16 bq = __float2bfloat16_rn((float)rem);
-            qp[u] = __bfloat16_as_ushort(bq);
-            rem -= (int)__bfloat162float(bq);
-        }
-        lw[0] = hxl; lw[1] = hyl; lw[2] = hxl; lw[3] = hxl;
-        lw[4] = hyl; lw[5] = hyl; lw[6] = pack2(qp[0], qp[1]); lw[7] = pack2(qp[2], qp[3]);
     }
     *reinterpret_cast<uint4*>(st + C::col_off + tc::slab_off(r, 0)) = make_uint4(pw[0], pw[1], pw[2], pw[3]);
     *reinterpret_cast<uint4*>(st + C::col_off + tc::slab_off(r, 16)) = make_uint4(pw[4], pw[5], pw[6], pw[7]);
-    *reinterpret_cast<uint4*>(st + C::bloc_off + tc::slab_off(r, 0)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-    *reinterpret_cast<uint4*>(st + C::bloc_off + tc::slab_off(r, 16)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
@@ -946,7 +1028,7 @@ cudaError_t tiles(const TcLaunch& L, cudaStream_t st) {
     d.label_off = L.d_label_off;
     d.tile_off = L.d_tile_off;
     d.blob = L.blob;
-    d.tile_c = L.t.tile_c;
+    d.tile_xy = L.t.tile_xy;
     d.rep = L.t.rep;
     d.neglog = L.neglog;
     d.post = L.post;
@@ -968,7 +1050,7 @@ cudaError_t tiles(const TcLaunch& L, cudaStream_t st) {
     build_tiles_kernel<TEX8, KS, PERSAMPLE>
         <<<(unsigned)(((long long)total_tiles * BN + 127) / 128), 128, 0, st>>>(
             L.d_label_off, L.d_tile_off, L.n_labels, total_tiles, L.t, L.n_samples, L.k, Cc,
-            L.t.perm, L.blob, L.t.tile_c, L.imax2, d, L.desc);
+            L.t.perm, L.blob, L.t.tile_xy, L.imax2, d, L.desc);
     return cudaGetLastError();
 }
 
@@ -1036,10 +1118,12 @@ cudaError_t dispatch(int k, bool tex8, bool persample, F&& f) {
 
 size_t tc_copy_bytes(int k, bool tex8, bool persample) {
     const int ks = tex8 ? (k + 31) / 32 : (k + 15) / 16;
-    return (size_t)(persample ? ks * 4096 : 0) + 2 * 4096;
+    return (size_t)(persample ? ks * 4096 : 0) + 4096;
 }
 
 int tc_tiles_per_label(int m) { return (m + BN - 1) / BN; }
+
+int tc_tile_samples() { return BN; }
 
 bool tc_supported(int k, bool tex8) { return tex8 ? k <= 256 : k <= 128; }
 

@@ -41,6 +41,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  "r"(bytes)
                  : "memory");
 }
+// Adds `bytes` to the transaction count the current phase waits for
+// (no arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
 // Tests the phase with the given parity; the thread may be suspended for up
 // to `hint_ns` nanoseconds while the phase is incomplete (it does not spin).
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity,
@@ -160,6 +167,18 @@ __device__ __forceinline__ void tmem_ld16x2_wait(uint32_t ta, uint32_t tb, uint6
         "mov.b64 %0, {a0, a1};\n\t""mov.b64 %1, {a2, a3};\n\t""mov.b64 %2, {a4, a5};\n\t""mov.b64 %3, {a6, a7};\n\t""mov.b64 %4, {a8, a9};\n\t""mov.b64 %5, {a10, a11};\n\t""mov.b64 %6, {a12, a13};\n\t""mov.b64 %7, {a14, a15};\n\t""mov.b64 %8, {b0, b1};\n\t""mov.b64 %9, {b2, b3};\n\t""mov.b64 %10, {b4, b5};\n\t""mov.b64 %11, {b6, b7};\n\t""mov.b64 %12, {b8, b9};\n\t""mov.b64 %13, {b10, b11};\n\t""mov.b64 %14, {b12, b13};\n\t""mov.b64 %15, {b14, b15};\n\t""}"
         : "=l"(ra[0]), "=l"(ra[1]), "=l"(ra[2]), "=l"(ra[3]), "=l"(ra[4]), "=l"(ra[5]), "=l"(ra[6]), "=l"(ra[7]), "=l"(rb[0]), "=l"(rb[1]), "=l"(rb[2]), "=l"(rb[3]), "=l"(rb[4]), "=l"(rb[5]), "=l"(rb[6]), "=l"(rb[7])
         : "r"(ta), "r"(tb)
+        : "memory");
+}
+// One 16-column load (32 lanes x 32 bits), its wait, and the values as 8
+// packed pairs (column 2i in the low half).
+__device__ __forceinline__ void tmem_ld16_wait_pk(uint32_t ta, uint64_t (&ra)[8]) {
+    asm volatile(
+        "{\n\t.reg .b32 a<16>;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n\t"
+        "mov.b64 %0, {a0, a1};\n\t""mov.b64 %1, {a2, a3};\n\t""mov.b64 %2, {a4, a5};\n\t""mov.b64 %3, {a6, a7};\n\t""mov.b64 %4, {a8, a9};\n\t""mov.b64 %5, {a10, a11};\n\t""mov.b64 %6, {a12, a13};\n\t""mov.b64 %7, {a14, a15};\n\t""}"
+        : "=l"(ra[0]), "=l"(ra[1]), "=l"(ra[2]), "=l"(ra[3]), "=l"(ra[4]), "=l"(ra[5]), "=l"(ra[6]), "=l"(ra[7])
+        : "r"(ta)
         : "memory");
 }
 __device__ __forceinline__ void tmem_ld_wait() {
