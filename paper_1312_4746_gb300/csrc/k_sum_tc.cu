@@ -33,10 +33,11 @@
 // Two persistent CTAs per SM (one where the shared-memory layout does not
 // fit twice); a pixel tile is 16 x 8 pixels (one TMEM lane each), a sample
 // tile 128 samples (one TMEM column each).
-//   warp 8       producer: per stage, bulk-copies (TMA) the pre-laid-out
-//                texture and colour slabs of a sample tile and writes its
-//                two location slabs for this pixel tile
-//   warp 9       MMA issuer: D1 <- texture slabs + colour slab + location
+//   warps 8..11  producers: per stage, one bulk-copies (TMA) the
+//                pre-laid-out texture and colour slabs of a sample tile, and
+//                all four write its two location slabs for this pixel tile
+//                (32 samples each)
+//   warp 12      MMA issuer: D1 <- texture slabs + colour slab + location
 //                slabs; TMEM double-buffered (2 x 128 columns per CTA), so
 //                one tile's MMAs run while the epilogue reads the previous
 //   warps 0..7   epilogue: per label, writes the pixel-side colour and
@@ -120,9 +121,10 @@ struct Cfg {
     static constexpr int EPQ = PAIR ? 2 : 4;                 // epilogue warps per TMEM lane quadrant
     static constexpr int EPI_WARPS = 4 * EPQ;
     static constexpr int CPW = BN / EPQ;                     // columns per epilogue warp per tile
+    static constexpr int NPROD = 4;                          // producer warps
     static constexpr int PRODUCER = EPI_WARPS;
-    static constexpr int MMA_WARP = EPI_WARPS + 1;
-    static constexpr int THREADS = (EPI_WARPS + 2) * 32;
+    static constexpr int MMA_WARP = EPI_WARPS + NPROD;
+    static constexpr int THREADS = (EPI_WARPS + NPROD + 1) * 32;
     // sample-tile ring depth: as deep as the shared memory allows (2 to 4)
     static constexpr int STAGES = !PAIR                          ? (KS <= 5 ? 4 : 3)
                                   : pair_bytes(4, ACB) <= PAIR_LIMIT ? 4
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
-            tc::mbar_init(full + s, 1);
+            tc::mbar_init(full + s, C::NPROD);
             tc::mbar_init(empty + s, 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -377,14 +379,15 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_base_s;
 
-    if (warp == PRODUCER) {
+    if (warp >= PRODUCER && warp < PRODUCER + C::NPROD) {
+        const int pw = warp - PRODUCER;  // producer warp: rows 32 u + lane, u = pw mod NPROD
         // ------------------------------------------------------------ producer
         uint32_t it = 0;  // tiles issued by this CTA (< 2^32 in any launch)
         bool ok = true;
         // the upper half of every L1 row stays zero (made visible to the
         // tensor cores by the proxy fence of each stage's first fill)
         for (int s = 0; s < C::STAGES; ++s)
-            for (int j = lane; j < BN; j += 32)
+            for (int j = 32 * pw + lane; j < BN; j += 32 * C::NPROD)
                 *reinterpret_cast<uint4*>(ring + s * C::stage_bytes + C::bl_off + 4096 +
                                           tc::slab_off(j, 16)) = make_uint4(0, 0, 0, 0);
         for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x) {
@@ -398,9 +401,11 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
             const int T1 = im.tile_off[im.n_labels];
             int i = 0, lab_first = im.tile_off[0], lab_end = im.tile_off[1];
             int m_i = im.label_off[1] - im.label_off[0];
-            uint32_t w_next[BN / 32];  // positions of samples 32 u + lane of a tile
+            constexpr int RV = BN / 32 / C::NPROD;  // rows of 32 samples per producer warp
+            uint32_t w_next[RV];  // positions of samples 32 (pw + NPROD v) + lane of a tile
 #pragma unroll
-            for (int u = 0; u < BN / 32; ++u) w_next[u] = im.tile_xy[(size_t)lab_first * BN + 32 * u + lane];
+            for (int v = 0; v < RV; ++v)
+                w_next[v] = im.tile_xy[(size_t)lab_first * BN + 32 * (pw + C::NPROD * v) + lane];
             for (int T = lab_first; ok && T < T1; ++T, ++it) {
                 if (T == lab_end) {  // every label has at least one tile
                     ++i;
@@ -408,11 +413,12 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                     lab_end = im.tile_off[i + 1];
                     m_i = im.label_off[i + 1] - im.label_off[i];
                 }
-                uint32_t w[BN / 32];
+                uint32_t w[RV];
 #pragma unroll
-                for (int u = 0; u < BN / 32; ++u) {
-                    w[u] = w_next[u];
-                    if (T + 1 < T1) w_next[u] = im.tile_xy[(size_t)(T + 1) * BN + 32 * u + lane];
+                for (int v = 0; v < RV; ++v) {
+                    w[v] = w_next[v];
+                    if (T + 1 < T1)
+                        w_next[v] = im.tile_xy[(size_t)(T + 1) * BN + 32 * (pw + C::NPROD * v) + lane];
                 }
                 {
                     const int s = (int)(it % C::STAGES);
@@ -423,15 +429,15 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                     const int nvalid = min(BN, m_i - (T - lab_first) * BN);
                     // the copy first, so that it lands while the location
                     // slabs are written; the arrival follows them
-                    if (lane == 0) {
+                    if (pw == 0 && lane == 0) {
                         tc::mbar_expect_tx(full + s, C::copy_bytes);
                         tc::bulk_g2s(st, im.blob + (size_t)T * C::copy_bytes, C::copy_bytes, full + s);
                     }
 #pragma unroll
-                    for (int u = 0; u < BN / 32; ++u) {
-                        const int j = 32 * u + lane;
+                    for (int v = 0; v < RV; ++v) {
+                        const int j = 32 * (pw + C::NPROD * v) + lane;
                         uint4 l0a, l0b, l1a;
-                        loc_row_b(w[u], cx, cy, j < nvalid, l0a, l0b, l1a);
+                        loc_row_b(w[v], cx, cy, j < nvalid, l0a, l0b, l1a);
                         *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 0)) = l0a;
                         *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 16)) = l0b;
                         *reinterpret_cast<uint4*>(st + C::bl_off + 4096 + tc::slab_off(j, 0)) = l1a;
@@ -443,7 +449,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
             }
         }
         // drain: copies still in flight must land before the CTA exits
-        if (lane == 0)
+        if (pw == 0 && lane == 0)
             for (uint32_t d = (it > C::STAGES ? it - C::STAGES : 0); d < it; ++d)
                 tc::mbar_wait(full + (int)(d % C::STAGES), (uint32_t)((d / C::STAGES) & 1),
                               tc::globaltimer() + WAIT_NS);
