@@ -2,10 +2,11 @@
 
 The texture dot products are exact integers on the tensor cores (FP8 or BF16
 operands with values 0 and +-1); the colour term runs through hi/lo BF16
-splits (relative error about 2^-17 per factor). Bars: max probability error
-<= 1e-2 and argmax agreement >= 99.9% (required of the reduced-precision
-forms), and, because the only approximation is the colour split, max
-relative error on L <= 1e-4 here.
+splits (relative error about 2^-17 per factor); the location term, relative
+to each pixel tile's centre, through exact pieces of the sample offsets and
+three-piece splits of the pixel-side factors (relative error below 2^-24).
+Bars: max probability error <= 1e-2 and argmax agreement >= 99.9% (required
+of the reduced-precision forms), and max relative error on L <= 1e-4 here.
 """
 import numpy as np
 import pytest
@@ -82,6 +83,22 @@ def test_ragged_tc(env, H, W, nl, m, p, k, seed, precision):
         L, post = _run(env, pr, precision, mode)
         ref = oracle.data_term(pr, mode=mode)
         _check(L, post, ref)
+
+
+@pytest.mark.parametrize("H,W,nl,m,seed", [
+    (24, 6000, 2, 150, 41),   # wide: sample offsets from a pixel tile up to ~6000 px
+    (3000, 20, 3, 120, 42),   # tall
+])
+def test_far_samples_tc(env, H, W, nl, m, seed):
+    """Pixels and samples thousands of pixels apart: the location pieces stay
+    exact and L stays within the bar at sampled pixels of both ends."""
+    pr = synth.make_problem(H, W, nl, m, p=5, k=50, seed=seed, cap_frac=0.9)
+    L, post = _run(env, pr, 2, 0)
+    rng = np.random.default_rng(seed)
+    P = H * W
+    pix = np.unique(np.concatenate([rng.integers(0, P, 500), [0, W - 1, P - W, P - 1]])).astype(np.int32)
+    ref = oracle.data_term(pr, pix=pix)
+    _check(L[:, pix], post[:, pix], ref)
 
 
 def test_tc_matches_plain(env):
