@@ -543,6 +543,305 @@ __global__ void __launch_bounds__(128, 4) codes_tc_kernel(
     }
 }
 
+// codes_tcp_kernel: the same product, persistent (one or two CTAs per SM)
+// and pipelined over the 16 x 8 pixel tiles. The operator pieces are copied
+// once per CTA. Four builder warps form the normalised patches of tile t + 1
+// (each warp two pixel rows, from its own gray window) while the MMAs of
+// tile t run, then write its A operand once those MMAs have read the
+// previous one; four epilogue warps threshold tile t - 1 from the other of
+// two TMEM accumulators; one thread issues the MMAs. The arithmetic per
+// pixel and entry is that of codes_tc_kernel.
+constexpr int CP_THREADS = 9 * 32;
+
+struct CpOff {
+    int b, win, w, rn, prm, bars, misc, total;
+};
+template <int P>
+__host__ __device__ constexpr CpOff cp_off(int np) {
+    constexpr int KS = ct_ks(P), N = P * P, WW = CT_W + P - 1, WH = P + 1;
+    CpOff o{};
+    o.b = 3 * KS * 4096;                                   // A: 3 KS slabs of 128 rows
+    o.win = o.b + 3 * KS * np * 32;                        // B: operator pieces
+    o.w = o.win + 4 * 2 * WH * WW * 4;                     // builder windows: gray, |gray|
+    o.rn = o.w + ((N + 3) & ~3) * 4;                       // patch mask
+    o.prm = (o.rn + np * 4 + 15) & ~15;                    // row norms
+    o.bars = o.prm + 2 * 128 * 16;                         // per-pixel parameters [2][128]
+    o.misc = o.bars + 16 * 8;                              // mbarriers
+    o.total = o.misc + 16;                                 // TMEM base, abort flag
+    return o;
+}
+
+// Bounded wait shared by the roles: gives up after CT_WAIT_NS or once
+// another role has aborted.
+__device__ __forceinline__ bool cp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        int* d_err, int site) {
+    const uint64_t deadline = tc::globaltimer() + CT_WAIT_NS;
+    for (uint32_t n = 0;; ++n) {
+        if (tc::mbar_try_wait(bar, parity, 1000u)) return true;
+        if ((n & 63u) == 63u && (*abort_flag || tc::globaltimer() > deadline)) break;
+    }
+    *abort_flag = 1;
+    ct_set_error(d_err, site);
+    return false;
+}
+
+template <int P>
+__global__ void __launch_bounds__(CP_THREADS, P <= 7 ? 2 : 1) codes_tcp_kernel(
+    const float* __restrict__ img, int H, int W, const uint8_t* __restrict__ blob, int k, int np,
+    const float* __restrict__ mask, const float* __restrict__ rownorm, float tau_f,
+    float tau_slack, float* __restrict__ codes, float* __restrict__ lead16,
+    uint32_t* __restrict__ bitmask, int2* __restrict__ guard, int guard_cap,
+    int* __restrict__ guard_count, int* __restrict__ d_err) {
+    constexpr int N = P * P, R = (P - 1) / 2, KS = ct_ks(P);
+    constexpr int WW = CT_W + P - 1, WH = P + 1;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const CpOff o = cp_off<P>(np);
+    uint8_t* sa = smem;
+    uint8_t* sb = smem + o.b;
+    float* win = reinterpret_cast<float*>(smem + o.win);
+    float* s_w = reinterpret_cast<float*>(smem + o.w);
+    float* s_rn = reinterpret_cast<float*>(smem + o.rn);
+    int4* prm = reinterpret_cast<int4*>(smem + o.prm);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + o.bars);
+    uint64_t* b_full = bars + 0;   // operator copy
+    uint64_t* a_full = bars + 1;   // builders -> MMA (4 warps)
+    uint64_t* a_empty = bars + 2;  // MMA commit -> builders
+    uint64_t* t_full = bars + 3;   // [2] MMA commit -> epilogue
+    uint64_t* t_empty = bars + 5;  // [2] epilogue (4 warps) -> MMA
+    uint64_t* p_full = bars + 7;   // [2] builders (4 warps) -> epilogue: pixel parameters
+    uint64_t* p_empty = bars + 9;  // [2] epilogue (4 warps) -> builders
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + o.misc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + o.misc + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t ncols = ct_cols(np);
+    const uint32_t b_bytes = (uint32_t)(3 * KS * np * 32);
+    const int ntx = (W + CT_W - 1) / CT_W, ntiles = ntx * ((H + CT_H - 1) / CT_H);
+    if (tid == 0) {
+        tc::mbar_init(b_full, 1);
+        tc::mbar_init(a_full, 4);
+        tc::mbar_init(a_empty, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(t_full + b, 1);
+            tc::mbar_init(t_empty + b, 4);
+            tc::mbar_init(p_full + b, 4);
+            tc::mbar_init(p_empty + b, 4);
+        }
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+        tc::mbar_arrive_expect_tx(b_full, b_bytes);
+        tc::bulk_g2s(sb, blob, b_bytes, b_full);
+    }
+    if (warp == 8) {
+        tc::tmem_alloc(s_tmem, 2 * ncols);
+        tc::tmem_relinquish();
+    }
+    for (int i = tid; i < N; i += CP_THREADS) s_w[i] = mask[i];
+    for (int i = tid; i < np; i += CP_THREADS) s_rn[i] = i < k ? rownorm[i] : 0.f;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *s_tmem;
+
+    if (warp < 4) {
+        // ---------------------------------------------------------- builders
+        float* wg = win + warp * 2 * WH * WW;  // gray window of pixel rows 2 warp, 2 warp + 1
+        float* wa = wg + WH * WW;              // |gray| bound window
+        const int r = 32 * warp + lane, tx = lane % CT_W, tyl = lane / CT_W;
+        int kk = 0;
+        for (int T = blockIdx.x; T < ntiles; T += gridDim.x, ++kk) {
+            const int x0 = (T % ntx) * CT_W, y0 = (T / ntx) * CT_H;
+            for (int i = lane; i < WH * WW; i += 32) {
+                const int ly = i / WW, lx = i % WW;
+                const int yy = min(max(y0 + 2 * warp + ly - R, 0), H - 1);
+                const int xx = min(max(x0 + lx - R, 0), W - 1);
+                const float* px = img + ((size_t)yy * W + xx) * 3;
+                const float rr = px[0], gg = px[1], bb = px[2];
+                wg[i] = __fadd_rn(__fadd_rn(__fmul_rn(0.299f, rr), __fmul_rn(0.587f, gg)),
+                                  __fmul_rn(0.114f, bb));
+                wa[i] = (0.299f * fabsf(rr) + 0.587f * fabsf(gg) + 0.114f * fabsf(bb)) * (1.f + 4 * U32);
+            }
+            __syncwarp();
+            const int x = x0 + tx, y = y0 + 2 * warp + tyl;
+            const bool live = x < W && y < H;
+            const int pix = live ? y * W + x : 0;
+            float sum = 0.f, kc = 0.f, vabs = 0.f, e2 = 0.f;
+#pragma unroll
+            for (int dy = 0; dy < P; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < P; ++dx) {
+                    const int t = dy * P + dx, li = (tyl + dy) * WW + tx + dx;
+                    const float v = __fmul_rn(s_w[t], wg[li]);
+                    const float yk = __fsub_rn(v, kc);
+                    const float tk = __fadd_rn(sum, yk);
+                    kc = __fsub_rn(__fsub_rn(tk, sum), yk);
+                    sum = tk;
+                    vabs += fabsf(v);
+                    const float ew = fabsf(s_w[t]) * wa[li];
+                    e2 = fmaf(ew, ew, e2);
+                }
+            const float mu = __fdiv_rn(sum, (float)N);
+            float ss = 0.f;
+#pragma unroll
+            for (int dy = 0; dy < P; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < P; ++dx) {
+                    const int t = dy * P + dx, li = (tyl + dy) * WW + tx + dx;
+                    const float c = __fsub_rn(__fmul_rn(s_w[t], wg[li]), mu);
+                    ss = fmaf(c, c, ss);
+                }
+            const float cn = sqrtf(ss);
+            const float dc = (2.f * 5.1f * U32) * sqrtf(e2) * 1.0001f +
+                             3.1f * U32 * vabs * rsqrtf((float)N) * 1.0001f + U32 * cn;
+            const bool whole = !(cn > 4.f * dc);
+            const float inv = whole ? 0.f : __frcp_rn(cn);
+            const float ds = whole ? 0.f : (2.f * dc / cn) * 1.0001f + 0.5f * (N + 7) * U32;
+            constexpr float EPS_TC = 4.1f * 5.9604645e-08f + KS * 4.76837158203125e-07f * 1.016f +
+                                     5 * KS * 4.76837158203125e-07f * 0.0079f;
+            const float ebase = (ds + EPS_TC * (1.f + ds)) * 1.25f;
+            // the A operand is free once the previous tile's MMAs have read it
+            if (!cp_wait(a_empty, (uint32_t)((kk & 1) ^ 1), abort_flag, d_err, 23)) break;
+#pragma unroll
+            for (int sl = 0; sl < KS; ++sl) {
+                uint32_t w1[8], w2[8], w3[8];
+#pragma unroll
+                for (int e2i = 0; e2i < 8; ++e2i) {
+                    uint32_t p1 = 0, p2 = 0, p3 = 0;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int t = 16 * sl + 2 * e2i + h;
+                        float v = 0.f;
+                        if (t < N && live) {
+                            const int li = (tyl + t / P) * WW + tx + t % P;
+                            v = __fmul_rn(__fsub_rn(__fmul_rn(s_w[t], wg[li]), mu), inv);
+                        }
+                        const __nv_bfloat16 b1 = __float2bfloat16_rn(v);
+                        const float r1 = v - __bfloat162float(b1);
+                        const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+                        const float r2 = r1 - __bfloat162float(b2);
+                        const __nv_bfloat16 b3 = __float2bfloat16_rn(r2);
+                        p1 |= (uint32_t)__bfloat16_as_ushort(b1) << (16 * h);
+                        p2 |= (uint32_t)__bfloat16_as_ushort(b2) << (16 * h);
+                        p3 |= (uint32_t)__bfloat16_as_ushort(b3) << (16 * h);
+                    }
+                    w1[e2i] = p1;
+                    w2[e2i] = p2;
+                    w3[e2i] = p3;
+                }
+                uint8_t* a1 = sa + sl * 4096;
+                uint8_t* a2 = sa + (KS + sl) * 4096;
+                uint8_t* a3 = sa + (2 * KS + sl) * 4096;
+                *reinterpret_cast<uint4*>(a1 + tc::slab_off(r, 0)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                *reinterpret_cast<uint4*>(a1 + tc::slab_off(r, 16)) = make_uint4(w1[4], w1[5], w1[6], w1[7]);
+                *reinterpret_cast<uint4*>(a2 + tc::slab_off(r, 0)) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                *reinterpret_cast<uint4*>(a2 + tc::slab_off(r, 16)) = make_uint4(w2[4], w2[5], w2[6], w2[7]);
+                *reinterpret_cast<uint4*>(a3 + tc::slab_off(r, 0)) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+                *reinterpret_cast<uint4*>(a3 + tc::slab_off(r, 16)) = make_uint4(w3[4], w3[5], w3[6], w3[7]);
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(a_full);
+            // this pixel's parameters for the epilogue
+            const int pb = kk & 1;
+            if (!cp_wait(p_empty + pb, (uint32_t)(((kk >> 1) & 1) ^ 1), abort_flag, d_err, 24)) break;
+            prm[pb * 128 + r] = make_int4(live ? pix : -1, whole ? 1 : 0, __float_as_int(ebase), 0);
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(p_full + pb);
+        }
+    } else if (warp < 8) {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;
+        const uint32_t lrow = tmem + ((uint32_t)(32 * q) << 16);
+        const int Wk = (k + 31) >> 5, nch = np / 16;
+        int kk = 0;
+        for (int T = blockIdx.x; T < ntiles; T += gridDim.x, ++kk) {
+            const int b = kk & 1;
+            if (!cp_wait(p_full + b, (uint32_t)((kk >> 1) & 1), abort_flag, d_err, 25)) break;
+            const int4 pp = prm[b * 128 + 32 * q + lane];
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(p_empty + b);
+            if (!cp_wait(t_full + b, (uint32_t)((kk >> 1) & 1), abort_flag, d_err, 26)) break;
+            tc::fence_after_sync();
+            const bool live = pp.x >= 0, whole = pp.y != 0;
+            const int pix = live ? pp.x : 0;
+            const float ebase = __int_as_float(pp.z);
+            uint32_t word = 0;
+            for (int c = 0; c < nch; ++c) {
+                uint32_t v[16];
+                tc::tmem_ld16(lrow + (uint32_t)(b * ncols) + 16u * c, v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int j = 16 * c + e;
+                    if (j < k && live) {
+                        const float a = __uint_as_float(v[e]);
+                        const float aa = fabsf(a);
+                        const float E = s_rn[j] * ebase + tau_slack;
+                        if (!whole) {
+                            if (fabsf(aa - tau_f) <= E)
+                                guard_push(guard, guard_cap, guard_count, pix, j);
+                            else if (aa <= tau_f)
+                                word |= 1u << (j & 31);
+                        }
+                        if (codes) codes[(size_t)pix * k + j] = a;
+                        if (lead16 && j < 16) lead16[(size_t)pix * 16 + j] = a;
+                    }
+                }
+                if ((c & 1) || c == nch - 1) {
+                    if (live && bitmask) bitmask[(size_t)pix * Wk + (c >> 1)] = word;
+                    word = 0;
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(t_empty + b);
+            if (live && whole) guard_push(guard, guard_cap, guard_count, pix, -1);
+            if (live && lead16)
+                for (int j = k; j < 16; ++j) lead16[(size_t)pix * 16 + j] = 0.f;
+        }
+    } else if (lane == 0) {
+        // ---------------------------------------------------------- MMA issuer
+        long long last = -1;
+        if (cp_wait(b_full, 0, abort_flag, d_err, 21)) {
+            const uint32_t id = tc::idesc(128, np, 1, 1);
+            int kk = 0;
+            for (int T = blockIdx.x; T < ntiles; T += gridDim.x, ++kk) {
+                const int b = kk & 1;
+                if (!cp_wait(a_full, (uint32_t)(kk & 1), abort_flag, d_err, 22) ||
+                    !cp_wait(t_empty + b, (uint32_t)(((kk >> 1) & 1) ^ 1), abort_flag, d_err, 27))
+                    break;
+                tc::fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)(b * ncols);
+                // (operator piece, patch piece), smallest products first
+                const int order[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
+#pragma unroll
+                for (int gi = 0; gi < 6; ++gi)
+#pragma unroll
+                    for (int sl = 0; sl < KS; ++sl)
+                        tc::mma_bf16(d, tc::smem_desc(sa + (order[gi][1] * KS + sl) * 4096),
+                                     tc::smem_desc(sb + (order[gi][0] * KS + sl) * np * 32), id,
+                                     gi > 0 || sl > 0);
+                tc::mma_commit(a_empty);
+                tc::mma_commit(t_full + b);
+                last = kk;
+            }
+        } else {
+            // the copy must land before the CTA may exit
+            tc::mbar_wait(b_full, 0, tc::globaltimer() + CT_WAIT_NS);
+        }
+        // drain: the last MMAs must finish before the tensor memory is freed
+        if (last >= 0)
+            tc::mbar_wait(t_full + (int)(last & 1), (uint32_t)((last >> 1) & 1),
+                          tc::globaltimer() + CT_WAIT_NS);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 8) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 2 * ncols);
+    }
+}
+
 template <int P>
 size_t ct_smem(int np) {
     constexpr int N = P * P, KS = ct_ks(P), GW = CT_W + P - 1, GH = CT_H + P - 1;
@@ -569,11 +868,36 @@ cudaError_t launch_tc_p(const CodesArgs& a, cudaStream_t st) {
                                                            a.omega_blob);
     const float tau_f = (float)a.tau;
     const float slack = fabsf(tau_f - (float)a.tau) + 2.f * U32 * tau_f + 1e-12f;
-    dim3 grd((a.W + CT_W - 1) / CT_W, (a.H + CT_H - 1) / CT_H);
-    codes_tc_kernel<P><<<grd, 128, smem, st>>>(a.img, a.H, a.W, a.omega_blob, a.k, np, a.mask,
-                                               a.rownorm, tau_f, slack, a.codes, a.lead16,
-                                               a.bitmask, a.guard, a.guard_cap, a.guard_count,
-                                               a.d_err);
+    // persistent and pipelined where its layout fits (at most two CTAs per
+    // SM: TMEM holds two accumulators each), else one CTA per pixel tile
+    const int ncols2 = 2 * (int)ct_cols(np);
+    size_t psmem = (size_t)cp_off<P>(np).total;
+    int per_sm = 512 / ncols2;
+    const int per_sm_smem = (int)(233472 / (psmem + 1024));
+    if (per_sm > per_sm_smem) per_sm = per_sm_smem;
+    if (per_sm > (P <= 7 ? 2 : 1)) per_sm = P <= 7 ? 2 : 1;  // registers (launch bounds)
+    if (per_sm < 1) {
+        dim3 grd((a.W + CT_W - 1) / CT_W, (a.H + CT_H - 1) / CT_H);
+        codes_tc_kernel<P><<<grd, 128, smem, st>>>(a.img, a.H, a.W, a.omega_blob, a.k, np, a.mask,
+                                                   a.rownorm, tau_f, slack, a.codes, a.lead16,
+                                                   a.bitmask, a.guard, a.guard_cap, a.guard_count,
+                                                   a.d_err);
+        return cudaGetLastError();
+    }
+    const size_t floor_b = 233472 / (per_sm + 1) - 1024 + 16;  // no further CTA fits
+    if (psmem < floor_b) psmem = floor_b;
+    e = cudaFuncSetAttribute(codes_tcp_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)psmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const int ntiles = ((a.W + CT_W - 1) / CT_W) * ((a.H + CT_H - 1) / CT_H);
+    const int grid = ntiles < per_sm * n_sm ? ntiles : per_sm * n_sm;
+    codes_tcp_kernel<P><<<grid, CP_THREADS, psmem, st>>>(
+        a.img, a.H, a.W, a.omega_blob, a.k, np, a.mask, a.rownorm, tau_f, slack, a.codes,
+        a.lead16, a.bitmask, a.guard, a.guard_cap, a.guard_count, a.d_err);
     return cudaGetLastError();
 }
 
