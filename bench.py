@@ -231,8 +231,8 @@ TRAFFIC = {"sum_tc_kernel": 9.32e6, "sum_plain_kernel": 7.83e6}
 
 FORMS = {"fp32": 0, "bf16": 1, "fp8": 2}
 FORM_NAMES = {"fp32": "plain FP32 (CUDA cores, popc TSM)",
-              "bf16": "tensor cores (tcgen05): BF16 exact texture dot, split-BF16 colour, exact location",
-              "fp8": "tensor cores (tcgen05): FP8 exact texture dot, split-BF16 colour, exact location"}
+              "bf16": "tensor cores (tcgen05): BF16 exact texture dot, split-BF16 colour, location from exact offset pieces (one FP32 accumulator)",
+              "fp8": "tensor cores (tcgen05): FP8 exact texture dot, split-BF16 colour, location from exact offset pieces (one FP32 accumulator)"}
 # kernels one step launches (cs_data_term, per-sample form): offsets, seed,
 # row scan, column envelope; row norms, operator split, tcgen05 codes, guard;
 # gather; then either the plain sum, or Morton sort, tile build, the tcgen05

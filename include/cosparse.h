@@ -53,7 +53,7 @@ typedef int cs_status;
 
 /* Arithmetic forms. */
 #define CS_FP32 0 /* CUDA-core FP32 with exact integer distances and popc TSM */
-#define CS_BF16 1 /* tensor-core (tcgen05) TSM and colour dot products, FP32 accumulation */
+#define CS_BF16 1 /* tensor-core (tcgen05) TSM, colour and location dot products, FP32 accumulation */
 #define CS_FP8 2  /* as CS_BF16 with FP8 operands where they are exact */
 
 /* Forms of the operator product (codes). */
