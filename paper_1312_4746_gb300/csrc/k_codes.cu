@@ -313,8 +313,17 @@ __host__ __device__ constexpr uint32_t ct_cols(int np) {
 // Operator pieces in the B-operand layout: 3 KS slabs of np rows x 16 bf16
 // (slab piece * KS + s holds piece `piece` of columns 16 s .. 16 s + 15).
 __global__ void omega_split_kernel(const float* __restrict__ omega, int k, int n, int ks, int np,
-                                   uint8_t* __restrict__ blob) {
+                                   uint8_t* __restrict__ blob, float* __restrict__ rownorm,
+                                   int* __restrict__ guard_count) {
     const int total = 3 * ks * np * 16;
+    // the first k threads also give the row norms (as rownorm_kernel)
+    const int jr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jr == 0) *guard_count = 0;
+    if (jr < k) {
+        float sq = 0.f;
+        for (int t = 0; t < n; ++t) sq = fmaf(omega[(size_t)jr * n + t], omega[(size_t)jr * n + t], sq);
+        rownorm[jr] = sqrtf(sq) * (1.f + (0.5f * n + 2.f) * U32);
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int e = i % 16, j = (i / 16) % np, sl = i / (16 * np);
         const int piece = sl / ks, t = 16 * (sl % ks) + e;
@@ -865,7 +874,7 @@ cudaError_t launch_tc_p(const CodesArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const int total = 3 * ct_ks(P) * np * 16;
     omega_split_kernel<<<(total + 255) / 256, 256, 0, st>>>(a.omega, a.k, P * P, ct_ks(P), np,
-                                                           a.omega_blob);
+                                                           a.omega_blob, a.rownorm, a.guard_count);
     const float tau_f = (float)a.tau;
     const float slack = fabsf(tau_f - (float)a.tau) + 2.f * U32 * tau_f + 1e-12f;
     // persistent and pipelined where its layout fits (at most two CTAs per
@@ -939,7 +948,9 @@ size_t codes_tc_blob_bytes(int k, int p) { return (size_t)3 * ct_ks(p) * ct_np(k
 
 cudaError_t launch_codes(const CodesArgs& a, cudaStream_t st) {
     const int n = a.p * a.p;
-    rownorm_kernel<<<(a.k + 127) / 128, 128, 0, st>>>(a.omega, a.k, n, a.rownorm, a.guard_count);
+    // (the tensor-core form's operator split also gives the row norms)
+    if (!a.tc)
+        rownorm_kernel<<<(a.k + 127) / 128, 128, 0, st>>>(a.omega, a.k, n, a.rownorm, a.guard_count);
     cudaError_t e;
     if (a.tc) {
         if (!a.omega_blob || !codes_tc_supported(a.k, a.p)) return cudaErrorInvalidValue;
