@@ -270,11 +270,27 @@ __global__ void __launch_bounds__(128) codes_guard_kernel(
                 if (t < N) sb[t] = c[u];
             }
             __syncwarp();
-            for (int j = lane; j < k; j += 32) {
-                const float* oj = omega + (size_t)j * N;
-                double a = 0.0;
-                for (int t = 0; t < N; ++t) a = __dadd_rn(a, __dmul_rn((double)oj[t], sb[t]));
-                if (fabs(a) <= tau) atomicOr(bitmask + (size_t)g.x * Wk + (j >> 5), 1u << (j & 31));
+            // up to CG codes per lane at once: independent index-order sums,
+            // interleaved so that their latencies overlap
+            constexpr int CG = 8;
+            for (int j0 = lane; j0 < k; j0 += 32 * CG) {
+                double acc[CG];
+#pragma unroll
+                for (int q = 0; q < CG; ++q) acc[q] = 0.0;
+                for (int t = 0; t < N; ++t) {
+                    const double st = sb[t];
+#pragma unroll
+                    for (int q = 0; q < CG; ++q) {
+                        const int j = j0 + 32 * q;
+                        if (j < k) acc[q] = __dadd_rn(acc[q], __dmul_rn((double)omega[(size_t)j * N + t], st));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < CG; ++q) {
+                    const int j = j0 + 32 * q;
+                    if (j < k && fabs(acc[q]) <= tau)
+                        atomicOr(bitmask + (size_t)g.x * Wk + (j >> 5), 1u << (j & 31));
+                }
             }
         }
         __syncwarp();
