@@ -78,6 +78,7 @@ def test_workload1_full(env, mode):
     (1, 7, 1, 3, 3, 40, 4),        # one-row image, windows clamp everywhere
     (5, 1, 2, 1, 5, 64, 5),        # one-column image, single sample per label
     (130, 129, 5, 300, 7, 256, 6), # k = 256 (8 words), P not a multiple of 128
+    (29, 35, 2, 20, 9, 256, 13),   # 9x9 patches and k = 256: the per-tile codes kernel
 ])
 def test_ragged_shapes(env, H, W, nl, m, p, k, seed):
     pr = synth.make_problem(H, W, nl, m, p=p, k=k, seed=seed, cap_frac=0.9)
