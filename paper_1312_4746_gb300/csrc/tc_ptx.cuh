@@ -62,18 +62,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity,
         : "memory");
     return ok != 0;
 }
-// Non-blocking test of the phase with the given parity.
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
 // One elected lane of the (converged) warp arrives.
 __device__ __forceinline__ void mbar_arrive_elect(uint64_t* bar) {
     asm volatile(
@@ -139,35 +127,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-}
-// 32 lanes x 32 bits, 32 consecutive columns.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-}
-// Two 16-column loads (32 lanes x 32 bits each), the wait for both, and
-// the values as 8 + 8 packed pairs (column 2i in the low half), ready for
-// the f32x2 instructions.
-__device__ __forceinline__ void tmem_ld16x2_wait(uint32_t ta, uint32_t tb, uint64_t (&ra)[8],
-                                                 uint64_t (&rb)[8]) {
-    asm volatile(
-        "{\n\t.reg .b32 a<16>, b<16>;\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, [%16];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {b0,b1,b2,b3,b4,b5,b6,b7,b8,b9,b10,b11,b12,b13,b14,b15}, [%17];\n\t"
-        "tcgen05.wait::ld.sync.aligned;\n\t"
-        "mov.b64 %0, {a0, a1};\n\t""mov.b64 %1, {a2, a3};\n\t""mov.b64 %2, {a4, a5};\n\t""mov.b64 %3, {a6, a7};\n\t""mov.b64 %4, {a8, a9};\n\t""mov.b64 %5, {a10, a11};\n\t""mov.b64 %6, {a12, a13};\n\t""mov.b64 %7, {a14, a15};\n\t""mov.b64 %8, {b0, b1};\n\t""mov.b64 %9, {b2, b3};\n\t""mov.b64 %10, {b4, b5};\n\t""mov.b64 %11, {b6, b7};\n\t""mov.b64 %12, {b8, b9};\n\t""mov.b64 %13, {b10, b11};\n\t""mov.b64 %14, {b12, b13};\n\t""mov.b64 %15, {b14, b15};\n\t""}"
-        : "=l"(ra[0]), "=l"(ra[1]), "=l"(ra[2]), "=l"(ra[3]), "=l"(ra[4]), "=l"(ra[5]), "=l"(ra[6]), "=l"(ra[7]), "=l"(rb[0]), "=l"(rb[1]), "=l"(rb[2]), "=l"(rb[3]), "=l"(rb[4]), "=l"(rb[5]), "=l"(rb[6]), "=l"(rb[7])
-        : "r"(ta), "r"(tb)
-        : "memory");
 }
 // One 16-column load (32 lanes x 32 bits), its wait, and the values as 8
 // packed pairs (column 2i in the low half).
