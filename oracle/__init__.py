@@ -6,7 +6,10 @@ and never imports the product package.
 
 ``oracle.c`` evaluates the paper's definitions literally in double precision
 (Sec. 2, Eq. 1, Eq. tsm_clean, Eq. tex-rep, Sec. 3.1 Eq. color / post_text /
-joined, Eq. energy1); ``mlp.py`` holds the surrogate network's FP64 forward,
+joined, Eq. energy1); the smooth co-support texture (Eq. map_tsm,
+approx_cosupp and post_text on iota, ``iota`` / ``median_rows`` /
+``smooth_reps`` / ``smooth_log_posterior``) is numpy on the C oracle's FP64
+codes and Parzen sum (mode 2); ``mlp.py`` holds the surrogate network's FP64 forward,
 analytic backward and Adam step. This module compiles ``oracle.c`` with gcc
 (no FMA contraction) and wraps it with ctypes.
 
@@ -181,6 +184,44 @@ def likelihood(image, bits_px, bits_smp, k, label_off, sample_pix, sigma_c2=1.3,
     return out
 
 
+def iota(a, sigma):
+    """Eq. (map_tsm): smooth co-support indicator exp(-a_j^2 / sigma), elementwise."""
+    a = np.asarray(a, np.float64)
+    return np.exp(-(a * a) / float(sigma))
+
+
+def median_rows(values):
+    """Elementwise median over the rows of a (m, k) array (Eq. approx_cosupp):
+    the middle value of each column for odd m, the mean of the two middle
+    values for even m. Written out with a sort per column."""
+    v = np.sort(np.asarray(values, np.float64), axis=0)
+    m = v.shape[0]
+    if m < 1:
+        raise ValueError("median of an empty set")
+    if m % 2:
+        return v[m // 2].copy()
+    return 0.5 * (v[m // 2 - 1] + v[m // 2])
+
+
+def smooth_reps(iota_smp, label_off):
+    """Eq. (approx_cosupp) / Sec. 3.1: each label's textural representative
+    c_i, the elementwise median of its samples' smooth co-supports;
+    (n_labels, k) float64."""
+    label_off = np.asarray(label_off)
+    return np.stack([median_rows(iota_smp[label_off[i]:label_off[i + 1]])
+                     for i in range(len(label_off) - 1)])
+
+
+def smooth_log_posterior(iota_px, reps, beta):
+    """Eq. (post_text): log of the texture posterior of each label,
+    log softmax_i(-||c_i - iota(O s_x)||_1 / beta_i(x)); iota_px (cnt, k),
+    reps (n, k), beta (n, cnt) -> (n, cnt) float64."""
+    l1 = np.abs(reps[:, None, :] - iota_px[None, :, :]).sum(axis=2)  # (n, cnt)
+    t = -l1 / beta
+    tmax = t.max(axis=0)
+    return t - (tmax + np.log(np.exp(t - tmax).sum(axis=0)))
+
+
 def data_term(problem, pix=None, mode=None, want_dist2=False):
     """Whole oracle pipeline on a synthetic problem: codes and co-supports at
     the listed pixels and at every scribble sample, then the likelihoods."""
@@ -188,13 +229,27 @@ def data_term(problem, pix=None, mode=None, want_dist2=False):
     p = prm.p
     mode = prm.mode if mode is None else mode
     k = problem.omega.shape[0]
-    _, bits_px = codes(problem.image, problem.omega, problem.mask, p, prm.tau, pix=pix,
-                       want_codes=False)
-    _, bits_smp = codes(problem.image, problem.omega, problem.mask, p, prm.tau,
-                        pix=problem.sample_pix, want_codes=False)
+    smooth = mode == 2
+    a_px, bits_px = codes(problem.image, problem.omega, problem.mask, p, prm.tau, pix=pix,
+                          want_codes=smooth)
+    a_smp, bits_smp = codes(problem.image, problem.omega, problem.mask, p, prm.tau,
+                            pix=problem.sample_pix, want_codes=smooth)
     out = likelihood(problem.image, bits_px, bits_smp, k, problem.label_off, problem.sample_pix,
                      prm.sigma_c2, prm.alpha, prm.d_min, prm.kappa_beta, mode, pix=pix,
-                     want_dist2=want_dist2)
+                     want_dist2=want_dist2 or smooth)
+    if smooth:
+        # Sec. 3.1 with Eq. (map_tsm), (approx_cosupp), (post_text): the Parzen
+        # sum times the softmax texture posterior on smooth co-supports,
+        # beta_i(x) = kappa_beta rho_i(x), rho_i(x) = alpha max(|x - x_v|, d_min)
+        sigma = getattr(prm, "iota_sigma", 0.01)
+        reps = smooth_reps(iota(a_smp, sigma), problem.label_off)
+        rho = prm.alpha * np.maximum(np.sqrt(out["dist2"].astype(np.float64)), prm.d_min)
+        L = out["L"] + smooth_log_posterior(iota(a_px, sigma), reps, prm.kappa_beta * rho)
+        lmax = L.max(axis=0)
+        post = np.exp(L - (lmax + np.log(np.exp(L - lmax).sum(axis=0))))
+        out.update({"L": L, "neglog": -L, "post": post, "reps": reps})
+        if not want_dist2:
+            del out["dist2"]
     out["bits_px"] = bits_px
     out["bits_smp"] = bits_smp
     return out

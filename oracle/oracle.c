@@ -179,6 +179,8 @@ int oracle_dist2(int H, int W, int n_labels, const int32_t* label_off, const int
  * mode 0:   per-sample product of location, colour and texture kernels
  * mode 1:   factorised, Eq. (joined): Parzen colour-location sum times the
  *           texture softmax of Eq. (post_text) on the majority co-supports
+ * mode 2:   the Parzen colour-location sum alone (the smooth texture
+ *           posterior of Eq. (post_text) is added by the Python layer)
  * dist2:    optional output, n_labels x n_pix
  */
 int oracle_likelihood(const float* img, int H, int W, const uint32_t* bits_px,
@@ -189,7 +191,7 @@ int oracle_likelihood(const float* img, int H, int W, const uint32_t* bits_px,
     int Wk = (k + 31) / 32;
     int count = pix_list ? n_pix : H * W;
     if (n_labels < 1 || k < 1 || sigma_c2 <= 0.0 || alpha <= 0.0 || d_min <= 0.0 ||
-        kappa_beta <= 0.0 || (mode != 0 && mode != 1))
+        kappa_beta <= 0.0 || (mode != 0 && mode != 1 && mode != 2))
         return -1;
     for (int i = 0; i < n_labels; ++i)
         if (label_off[i + 1] - label_off[i] < 1) return -1;

@@ -54,7 +54,8 @@ class Params:
     alpha: float = 1.3
     d_min: float = 1.0
     kappa_beta: float = 1.0
-    mode: int = 0  # 0 = per-sample texture kernel, 1 = factorised (Eq. joined)
+    mode: int = 0  # 0 = per-sample texture kernel, 1 = factorised (Eq. joined), 2 = smooth
+    iota_sigma: float = 0.01  # Eq. map_tsm's sigma (the paper's value) for the smooth texture
 
 
 @dataclasses.dataclass

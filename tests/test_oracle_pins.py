@@ -397,3 +397,88 @@ def test_beta_limits():
         win = order[0]
         # parzen part of the winner is unchanged: its texture log-posterior is ~0
         assert abs(small["L"][win, q] - f_big["L"][win, q] - math.log(3)) < 1e-6
+
+
+# ---------------------------------------------------------------- smooth texture (Sec. 2, Sec. 3.1)
+
+def test_iota_closed_form():
+    """Eq. (map_tsm): iota(0) = 1, iota(sqrt(sigma)) = 1/e, even in a, and it
+    tends to the co-support indicator as sigma -> 0."""
+    s = 0.01
+    np.testing.assert_array_equal(oracle.iota([0.0, -0.0], s), [1.0, 1.0])
+    assert abs(oracle.iota([math.sqrt(s)], s)[0] - math.exp(-1.0)) < 1e-15
+    a = np.array([-0.3, -0.05, 0.02, 0.4])
+    np.testing.assert_array_equal(oracle.iota(a, s), oracle.iota(-a, s))
+    assert np.all(oracle.iota(a, 1e-9) < 1e-300)
+
+
+def test_median_rows_hand_values():
+    """Eq. (approx_cosupp): elementwise median; odd m -> the middle value,
+    even m -> the mean of the two middle values, m = 1 -> the row itself;
+    independent of the row order."""
+    v = np.array([[0.9, 0.1], [0.1, 0.4], [0.5, 0.7]])
+    np.testing.assert_array_equal(oracle.median_rows(v), [0.5, 0.4])
+    np.testing.assert_array_equal(oracle.median_rows(v[:2]), [0.5, 0.25])
+    np.testing.assert_array_equal(oracle.median_rows(v[1:2]), v[1])
+    np.testing.assert_array_equal(oracle.median_rows(v[::-1]), [0.5, 0.4])
+    w = np.array([[4.0], [1.0], [3.0], [2.0]])
+    np.testing.assert_array_equal(oracle.median_rows(w), [2.5])
+
+
+def test_smooth_posterior_closed_form():
+    """Eq. (post_text) on a hand example: representatives (1, 0) and (0, 1),
+    a pixel with iota = (1, 0): l1 distances 0 and 2, so with beta = 1 the
+    log posteriors are -log(1 + e^-2) and -2 - log(1 + e^-2); they sum to 1 in
+    probability; equal representatives give the uniform posterior; small beta
+    is winner-take-all, large beta uniform."""
+    reps = np.array([[1.0, 0.0], [0.0, 1.0]])
+    px = np.array([[1.0, 0.0]])
+    lp = oracle.smooth_log_posterior(px, reps, np.ones((2, 1)))
+    z = math.log(1.0 + math.exp(-2.0))
+    np.testing.assert_allclose(lp[:, 0], [-z, -2.0 - z], rtol=0, atol=1e-15)
+    assert abs(np.exp(lp).sum() - 1.0) < 1e-15
+    same = oracle.smooth_log_posterior(px, np.ones((3, 2)), np.ones((3, 1)))
+    np.testing.assert_allclose(same, -math.log(3), atol=1e-15)
+    win = oracle.smooth_log_posterior(px, reps, np.full((2, 1), 1e-3))
+    assert win[0, 0] > -1e-12 and win[1, 0] < -1e3
+    flat = oracle.smooth_log_posterior(px, reps, np.full((2, 1), 1e12))
+    np.testing.assert_allclose(flat, -math.log(2), atol=1e-9)
+
+
+@pytest.mark.parametrize("val", [0.0, 0.7])
+def test_smooth_mode_constant_image(val):
+    """Constant image: every masked patch is the same (the zero image: s = 0,
+    all codes 0, iota = 1), so every pixel and sample has the same smooth
+    co-support, every representative equals it and the texture posterior is
+    uniform: L (mode 2) = Parzen sum - log n."""
+    pr = synth.make_problem(12, 16, 3, 4, p=5, seed=15)
+    pr.image[:] = val
+    pr.params.mode = 2
+    out = oracle.data_term(pr)
+    a0, _ = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1, pix=np.array([0], np.int32))
+    np.testing.assert_array_equal(out["reps"], np.repeat(oracle.iota(a0, 0.01), 3, axis=0))
+    if val == 0.0:
+        np.testing.assert_array_equal(out["reps"], np.ones((3, pr.k)))
+    _, bpx = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1)
+    _, bsm = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1, pix=pr.sample_pix)
+    parzen = oracle.likelihood(pr.image, bpx, bsm, pr.k, pr.label_off, pr.sample_pix, mode=2)
+    np.testing.assert_allclose(out["L"], parzen["L"] - math.log(3), atol=1e-12)
+    np.testing.assert_allclose(out["post"].sum(axis=0), 1.0, atol=1e-12)
+
+
+def test_smooth_mode_single_sample_labels():
+    """One scribble sample per label: each representative is that sample's
+    smooth co-support, so at a sample's own pixel the l1 distance to its
+    label's representative is 0 and that label's texture posterior is the
+    largest; the Parzen part is the mode-2 C oracle's."""
+    pr = synth.make_problem(20, 24, 3, 1, p=5, seed=17)
+    pr.params.mode = 2
+    out = oracle.data_term(pr, pix=pr.sample_pix)
+    a_smp, _ = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1, pix=pr.sample_pix)
+    np.testing.assert_array_equal(out["reps"], oracle.iota(a_smp, 0.01))
+    _, bpx = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1, pix=pr.sample_pix)
+    parzen = oracle.likelihood(pr.image, bpx, bpx, pr.k, pr.label_off, pr.sample_pix,
+                               mode=2, pix=pr.sample_pix)
+    tex = out["L"] - parzen["L"]  # log texture posterior at each sample pixel
+    for q in range(3):
+        assert np.argmax(tex[:, q]) == q or np.isclose(tex[q, q], tex[:, q].max())
