@@ -50,6 +50,10 @@ typedef int cs_status;
 /* Likelihood forms (Sec. 3.1). */
 #define CS_MODE_PERSAMPLE 0  /* each sample carries k_rho * k_sigma * exp(-TSM/beta) */
 #define CS_MODE_FACTORISED 1 /* Eq. (joined): Parzen sum times the Eq. (post_text) softmax */
+#define CS_MODE_SMOOTH 2     /* as CS_MODE_FACTORISED with the smooth co-support of Eq. (map_tsm):
+                                representatives c_i = elementwise median of iota(O s) over each
+                                label's samples (Eq. approx_cosupp), softmax of
+                                -||c_i - iota(O s_x)||_1 / beta_i(x); cs_data_term only */
 
 /* Arithmetic forms. */
 #define CS_FP32 0 /* CUDA-core FP32 with exact integer distances and popc TSM */
@@ -66,7 +70,8 @@ typedef struct cs_ctx cs_ctx;
 /*
  * Scalar parameters. Fill with cs_params_default() and override fields.
  *   p          patch side, odd, 3..9 (n = p*p window elements; Sec. 5 uses 9)
- *   mode       CS_MODE_PERSAMPLE or CS_MODE_FACTORISED
+ *   mode       CS_MODE_PERSAMPLE, CS_MODE_FACTORISED or CS_MODE_SMOOTH (the
+ *              last through cs_data_term only; elsewhere CS_ERR_UNSUPPORTED)
  *   precision  CS_FP32, CS_BF16 or CS_FP8 (the pixel x sample sum)
  *   codes_form the operator product (Sec. 2, a = O s): CS_CODES_AUTO (the
  *              tensor-core form when k <= 256, else FP32), CS_CODES_FP32
@@ -85,6 +90,11 @@ typedef struct cs_ctx cs_ctx;
  *              exceeds l_tol * max(|L|, 1) is recomputed in FP64 on the GPU
  *              (default 1e-3; 0 recomputes only rows below the FP32 floor;
  *              smaller values recompute more rows, at FP64 speed)
+ *   iota_sigma sigma of Eq. (map_tsm), iota(a)_j = exp(-a_j^2 / sigma), for
+ *              CS_MODE_SMOOTH (default 0.01, the paper's value; > 0). Its codes
+ *              are FP32 dot products of the FP32-normalised patch; a patch
+ *              whose centred norm is within the FP32 rounding bound of zero
+ *              is taken as flat (every code 0).
  */
 typedef struct {
     int32_t p;
@@ -97,6 +107,7 @@ typedef struct {
     double d_min;
     double kappa_beta;
     double l_tol;
+    double iota_sigma;
 } cs_params;
 
 void cs_params_default(cs_params* out);

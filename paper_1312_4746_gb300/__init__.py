@@ -25,6 +25,7 @@ CS_ERR_DEVICE = 6
 
 MODE_PERSAMPLE = 0
 MODE_FACTORISED = 1
+MODE_SMOOTH = 2  # smooth co-support texture (Eq. map_tsm, approx_cosupp, post_text); data_term only
 FP32 = 0
 BF16 = 1
 FP8 = 2
@@ -92,6 +93,7 @@ class Params(ctypes.Structure):
         ("d_min", ctypes.c_double),
         ("kappa_beta", ctypes.c_double),
         ("l_tol", ctypes.c_double),
+        ("iota_sigma", ctypes.c_double),
     ]
 
     @classmethod
@@ -106,7 +108,8 @@ class Params(ctypes.Structure):
     def from_synth(cls, sp, **kw):
         """From a ``synth.Params`` dataclass."""
         p = cls.default(p=sp.p, mode=sp.mode, tau=sp.tau, sigma_c2=sp.sigma_c2, alpha=sp.alpha,
-                        d_min=sp.d_min, kappa_beta=sp.kappa_beta)
+                        d_min=sp.d_min, kappa_beta=sp.kappa_beta,
+                        iota_sigma=getattr(sp, "iota_sigma", 0.01))
         for k, v in kw.items():
             setattr(p, k, v)
         return p

@@ -125,6 +125,7 @@ void cs_params_default(cs_params* out) {
     out->d_min = 1.0;
     out->kappa_beta = 1.0;
     out->l_tol = 1e-3;
+    out->iota_sigma = 0.01;
 }
 
 cs_status cs_create(cs_ctx** out, int device) {
@@ -286,15 +287,24 @@ cs_status cs_check_labels(cs_ctx* ctx, const char* fn, int n_labels,
     return CS_OK;
 }
 
-cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k) {
+cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k,
+                          bool allow_smooth) {
     if (!prm) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: params is NULL", fn);
     if (!(prm->sigma_c2 > 0) || !(prm->alpha > 0) || !(prm->d_min > 0) || !(prm->kappa_beta > 0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG,
                             "%s: sigma_c2, alpha, d_min and kappa_beta must be > 0", fn);
     if (!(prm->l_tol >= 0.0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: l_tol must be >= 0", fn);
-    if (prm->mode != CS_MODE_PERSAMPLE && prm->mode != CS_MODE_FACTORISED)
+    if (prm->mode == CS_MODE_SMOOTH) {
+        if (!allow_smooth)
+            return cs_set_error(ctx, CS_ERR_UNSUPPORTED,
+                                "%s: the smooth texture mode is available through cs_data_term",
+                                fn);
+        if (!(prm->iota_sigma > 0))
+            return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: iota_sigma must be > 0", fn);
+    } else if (prm->mode != CS_MODE_PERSAMPLE && prm->mode != CS_MODE_FACTORISED) {
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown mode %d", fn, prm->mode);
+    }
     if (prm->precision != CS_FP32 && prm->precision != CS_BF16 && prm->precision != CS_FP8)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown precision %d", fn,
                             prm->precision);
@@ -426,6 +436,7 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
     T.total_tiles = L.total_tiles;
     T.n_samples = L.S;
     T.t = L.t;
+    if (prm->mode == CS_MODE_SMOOTH) T.t.rep = nullptr;  // no bitmask texture posterior
     T.blob = L.t.blob;
     T.n_chunks = L.n_chunks;
     T.dist2 = L.d2;
@@ -624,8 +635,9 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     if (!s) s = cs_check_patch(ctx, fn, prm);
     if (!s) s = cs_check_codes_form(ctx, fn, prm, k);
     if (!s) s = cs_check_labels(ctx, fn, n_labels, label_off);
-    if (!s) s = cs_check_params(ctx, fn, prm, k);
+    if (!s) s = cs_check_params(ctx, fn, prm, k, true);
     if (s) return s;
+    const bool smooth = prm->mode == CS_MODE_SMOOTH;
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const long long P = (long long)H * W;
@@ -636,10 +648,16 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     Carve m(nullptr);
     cs_plan_codes(m, a, P, k, !bitmask);
     cs_lik_carve(m, L, dist2);
+    if (smooth) {  // smooth texture: sample iota (code-major) and representatives
+        m.take<float>((size_t)k * L.S);
+        m.take<float>((size_t)n_labels * k);
+    }
     if ((s = cs_ensure_scratch(ctx, m.off))) return s;
     Carve c(ctx->scratch);
     cs_plan_codes(c, a, P, k, !bitmask);
     cs_lik_carve(c, L, dist2);
+    float* iota_smp = smooth ? c.take<float>((size_t)k * L.S) : nullptr;
+    float* reps = smooth ? c.take<float>((size_t)n_labels * k) : nullptr;
     a.d_err = ctx->d_err;
     // fork: the distance transform and the tensor-core sample order depend
     // only on the scribbles; they run on the context's two side streams while
@@ -661,6 +679,12 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     if (e == cudaSuccess && L.tc_form) e = cudaStreamWaitEvent(st, ctx->ev_join2, 0);
     if (e == cudaSuccess)
         e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st, L.tc_form);
+    if (e == cudaSuccess && smooth) {
+        SmoothArgs sa{img, H, W, omega, k, prm->p, mask, sample_pix, L.S, (float)prm->iota_sigma,
+                      iota_smp, L.d_off, reps, n_labels, L.d2, (float)prm->alpha,
+                      (float)prm->d_min, (float)prm->kappa_beta, neglog, post};
+        e = launch_smooth(sa, st);
+    }
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return cs_check_launch(ctx, fn);
 }

@@ -138,6 +138,28 @@ struct EdtArgs {
 };
 cudaError_t launch_edt(const EdtArgs& a, cudaStream_t st);
 
+// Smooth co-sparse texture posterior (CS_MODE_SMOOTH), after the Parzen sum.
+struct SmoothArgs {
+    const float* img;
+    int H, W;
+    const float* omega;
+    int k, p;
+    const float* mask;
+    const int32_t* sample_pix;
+    int S;
+    float sigma;
+    float* iota_smp;             // scratch k x S (code-major)
+    const int32_t* d_label_off;  // device, n_labels + 1
+    float* reps;                 // scratch n_labels x k
+    int n_labels;
+    const int32_t* dist2;
+    float alpha, d_min, kappa_beta;
+    float* neglog;  // in: -L of the Parzen sum; out: -L with the texture posterior
+    float* post;    // optional
+};
+cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t st);
+size_t smooth_smem_bytes(int p, int k, int n_labels);
+
 // Small host arrays passed by value (no pageable copy, so calls can be
 // captured in a CUDA graph): label offsets and first sample tile per label.
 struct OffsetsParam {
@@ -316,7 +338,8 @@ cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st);
 cs_status cs_check_image(cs_ctx* ctx, const char* fn, int H, int W, int k);
 cs_status cs_check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm);
 cs_status cs_check_labels(cs_ctx* ctx, const char* fn, int n_labels, const int32_t* label_off);
-cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k);
+cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int k,
+                          bool allow_smooth = false);
 void cs_plan_codes(Carve& c, CodesArgs& a, long long P, int k, bool own_bitmask);
 bool cs_codes_use_tc(const cs_params* prm, int k);
 cs_status cs_check_codes_form(cs_ctx* ctx, const char* fn, const cs_params* prm, int k);

@@ -739,7 +739,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                     a.fb_list[idx] = make_int4(image_of(a, g), pix, (int)(uint32_t)fmask,
                                                (int)(uint32_t)(fmask >> 32));
             } else if (hf == 0 && live) {
-                if (!PERSAMPLE) {
+                if (!PERSAMPLE && im.rep) {  // factorised: the majority-co-support posterior
                     float tmax = -INFINITY;
                     for (int i = 0; i < im.n_labels; ++i) {
                         const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
@@ -820,7 +820,7 @@ __global__ void __launch_bounds__(128) refine_fp64_kernel(
         for (int w = 0; w < 8; ++w) bx[w] = w < Wk ? im.bitmask[(size_t)pix * Wk + w] : 0u;
         for (int i = 0; i < im.n_labels; ++i) {
             const double rho = alpha * fmax(sqrt((double)im.dist2[(size_t)i * P + pix]), d_min);
-            if (lane == 0 && !persample) {
+            if (lane == 0 && !persample && im.rep) {
                 int h = 0;
                 for (int w = 0; w < Wk; ++w) h += __popc(bx[w] ^ im.rep[i * Wk + w]);
                 sT[wib][i] = -(double)h / (kappa_beta * rho);
@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(128) refine_fp64_kernel(
         __syncwarp();
         if (lane == 0) {
             const int n = im.n_labels;
-            if (!persample) {
+            if (!persample && im.rep) {
                 double tm = -INFINITY, ts = 0.0;
                 for (int i = 0; i < n; ++i) tm = fmax(tm, sT[wib][i]);
                 for (int i = 0; i < n; ++i) ts += exp(sT[wib][i] - tm);

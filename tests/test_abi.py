@@ -37,7 +37,8 @@ def test_version_and_defaults(L):
     p = cs.Params.default()
     assert p.p == 7 and p.tau == 0.1 and p.sigma_c2 == 1.3 and p.alpha == 1.3
     assert p.d_min == 1.0 and p.kappa_beta == 1.0 and p.mode == 0 and p.precision == 0
-    assert p.codes_form == cs.CODES_AUTO and p.l_tol == 1e-3
+    assert p.codes_form == cs.CODES_AUTO and p.l_tol == 1e-3 and p.iota_sigma == 0.01
+    assert ctypes.sizeof(cs.Params) == 4 * 4 + 7 * 8
 
 
 def test_null_ctx_rejected(L):
