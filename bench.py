@@ -240,12 +240,14 @@ FORM_NAMES = {"fp32": "plain FP32 (CUDA cores, popc TSM)",
 LAUNCHES = {"fp32": 10, "bf16": 13, "fp8": 13}
 
 
-def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=None):
+def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=None, mode=None):
     """Device time (ms) of `steps` data-term steps with inputs resident, the
     per-stage times, and the end-to-end time from pinned host buffers."""
     P = pr.H * pr.W
     nl = pr.n_labels
     prm = cs.Params.from_synth(pr.params, precision=FORMS[form])
+    if mode is not None:
+        prm.mode = mode
     img = torch.from_numpy(pr.image).to(dev)
     om = torch.from_numpy(pr.omega).to(dev)
     mask = torch.from_numpy(pr.mask).to(dev)
@@ -438,6 +440,9 @@ def main():
         for form in forms:
             res[form] = measure(ctx, cs, torch, pr, form, args.steps, args.warmup, dev, stream,
                                 flush)
+        # the smooth co-sparse texture (mode 2): FP8 Parzen sum + smooth texture posterior
+        res_smooth = measure(ctx, cs, torch, pr, "fp8", args.steps, args.warmup, dev, stream,
+                             flush, mode=cs.MODE_SMOOTH)
     if world > 1:
         torch.distributed.barrier()
 
@@ -495,6 +500,13 @@ def main():
                                        f"{pair_ops(head, Wk)[pipe]} per pair x {n_sm} SMs x "
                                        f"{sm_mhz:.0f} MHz (median SM clock sampled under load)"},
             "forms": forms_out,
+            "smooth": {
+                "form": "mode 2: FP8 tensor-core Parzen colour-location sum, then the smooth "
+                        "co-sparse texture posterior (iota of FP32 codes, sigma "
+                        f"{pr.params.iota_sigma}, median representatives, l1 softmax)",
+                "ms_per_step": res_smooth[0] / args.steps,
+                "pairs_per_s": pairs_rank * args.steps / (res_smooth[0] * 1e-3),
+                "stage_ms": res_smooth[2]},
             "clocks": clocks,
         }
         if batch is not None:
