@@ -9,7 +9,8 @@ and never imports the product package.
 joined, Eq. energy1); the smooth co-support texture (Eq. map_tsm,
 approx_cosupp and post_text on iota, ``iota`` / ``median_rows`` /
 ``smooth_reps`` / ``smooth_log_posterior``) is numpy on the C oracle's FP64
-codes and Parzen sum (mode 2); ``mlp.py`` holds the surrogate network's FP64 forward,
+codes and Parzen sum (mode 2); ``segment.py`` is the FP64 primal-dual
+multilabel segmentation of Sec. 4 on the data term; ``mlp.py`` holds the surrogate network's FP64 forward,
 analytic backward and Adam step. This module compiles ``oracle.c`` with gcc
 (no FMA contraction) and wraps it with ctypes.
 
