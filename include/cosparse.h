@@ -247,17 +247,52 @@ cs_status cs_likelihood(cs_ctx* ctx, const float* img, int H, int W, const uint3
  * in double (two passes); the pixel's label normalisation is then redone in
  * double. The bound (log2 units)
  * adds 2^-15 C Q for the two-piece BF16 colour splits (C = log2 e /
- * (2 sigma_c2), Q = 2 |I| max_j |I_j| + max_j |I_j|^2), 2^-21 (Bt k + C Q)
- * for the tensor core's FP32 accumulation of the colour MMA onto the integer
- * texture sum (Bt = log2 e / beta), and 6 u (3 (|log2 S| + log2 m) +
- * |nA| <K> + 2 |R0| + 1) for the FP32 epilogue, where the pairs' exponents and
- * squared offsets K from their sample tile's anchor are averaged with the
- * pairs' shares of the row sum S as weights (R0 = Bt |b_x| + C |I|^2,
- * nA = -log2 e / (2 rho^2)). cs_refined_count returns how many pixels the last tensor-core
+ * (2 sigma_c2), Q = 2 |I| max_j |I_j| + max_j |I_j|^2),
+ * 2^-19 (Bt k + C Q + 8 |nA| |x'|^2 + 2 (|log2 S| + log2 m)) for the tensor
+ * core's FP32 accumulation of the colour and location MMAs onto the integer
+ * texture sum (Bt = log2 e / beta, nA = -log2 e / (2 rho^2), x' the pixel's
+ * offset from the centre of its 16 x 8 tile; the location enters relative
+ * to that centre), and 6 u (3 (|log2 S| + log2 m) + 2 |R0 + nA |x'|^2| +
+ * shift + 1) for the FP32 epilogue, where the pairs' exponents are averaged
+ * with the pairs' shares of the row sum S as weights (R0 = -Bt |b_x| -
+ * C |I|^2). cs_refined_count returns how many pixels the last tensor-core
  * cs_likelihood / cs_data_term call on ctx recomputed (0 after the plain
  * form). It synchronises `stream`.
  */
 cs_status cs_refined_count(cs_ctx* ctx, int32_t* count, void* stream);
+
+/*
+ * Convex multilabel segmentation on a data term (Sec. 4): the relaxation of
+ * Eq. (energy1) in Eq. (sets), minimised by the primal-dual iteration of
+ * Eq. (algo) -- projected ascent in xi (|xi(x)| <= lambda g(x) / 2) and mu
+ * (<= 0), projected descent in m ([0, 1]) and u (the simplex, by Michelot's
+ * algorithm), over-relaxation of u and m -- and binarised by argmax.
+ * g(x) = exp(-|grad I(x)| / gamma) / (2 gamma) on the 8-bit scale (255 I),
+ * forward differences; step sizes 1/2 (xi, mu), 1/5 (u), 1/|Omega| (m);
+ * start u = 1/n, m = 1.
+ *
+ *   f          DEVICE n_labels x H x W float32: data term f_i(x), e.g. the
+ *              neglog output of cs_data_term
+ *   img        DEVICE H x W x 3 float32 (the edge weight g)
+ *   sp         lambda >= 0 (boundary weight), nu >= 0 (MDL label cost, 0 for
+ *              supervised segmentation), gamma > 0 (paper: 5), iterations >= 0
+ *   u          DEVICE n_labels x H x W float32 out: the relaxed indicators
+ *   labels     DEVICE H x W int32 out or NULL: argmax_i u_i(x)
+ * Uses the context's scratch (4 n P + P floats). Asynchronous on `stream`
+ * (3 launches per iteration). Errors: CS_ERR_INVALID_ARG for null or
+ * out-of-range arguments.
+ */
+typedef struct {
+    double lambda;
+    double nu;
+    double gamma;
+    int32_t iterations;
+    int32_t reserved;
+} cs_seg_params;
+
+void cs_seg_params_default(cs_seg_params* out);
+cs_status cs_segment(cs_ctx* ctx, const float* f, const float* img, int H, int W, int n_labels,
+                     const cs_seg_params* sp, float* u, int32_t* labels, void* stream);
 
 /*
  * The whole data term in one call: patches, codes and co-support bitmasks of

@@ -47,6 +47,8 @@ EXPORTS = (
     "cs_likelihood",
     "cs_data_term",
     "cs_refined_count",
+    "cs_seg_params_default",
+    "cs_segment",
     "cs_batch_create",
     "cs_batch_run",
     "cs_batch_config",
@@ -115,6 +117,26 @@ class Params(ctypes.Structure):
         return p
 
 
+class SegParams(ctypes.Structure):
+    """Mirror of cs_seg_params (include/cosparse.h)."""
+
+    _fields_ = [
+        ("lam", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("iterations", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+    @classmethod
+    def default(cls, **kw):
+        p = cls()
+        lib().cs_seg_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+
 class Image(ctypes.Structure):
     """Mirror of cs_image (include/cosparse.h)."""
 
@@ -161,6 +183,9 @@ def lib(path: str | None = None):
     L.cs_last_error.restype = ctypes.c_char_p
     L.cs_sync_status.argtypes = [V, V]
     L.cs_refined_count.argtypes = [V, ctypes.POINTER(ctypes.c_int32), V]
+    L.cs_seg_params_default.argtypes = [ctypes.POINTER(SegParams)]
+    L.cs_seg_params_default.restype = None
+    L.cs_segment.argtypes = [V, V, V, I, I, I, ctypes.POINTER(SegParams), V, V, V]
     L.cs_codes.argtypes = [V, V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V]
     L.cs_cosupport.argtypes = [V, V, I, I, D, V, V]
     L.cs_codes_noalloc.argtypes = [V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V, V]
@@ -191,7 +216,7 @@ def lib(path: str | None = None):
     L.cs_mlp_grad.argtypes = [V, V, I, V, V, I, V, V, V]
     L.cs_profile_enable.argtypes = [V, I]
     L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
-    for f in ("cs_create", "cs_sync_status", "cs_refined_count", "cs_codes", "cs_cosupport", "cs_likelihood",
+    for f in ("cs_create", "cs_sync_status", "cs_refined_count", "cs_segment", "cs_codes", "cs_cosupport", "cs_likelihood",
               "cs_data_term", "cs_profile_enable", "cs_profile_read", "cs_surrogate_fit",
               "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_surrogate_save",
               "cs_surrogate_load", "cs_mlp_forward",
@@ -338,6 +363,23 @@ class Context:
             ctypes.c_void_p(off.ctypes.data), _ptr(sample_pix), ctypes.byref(params),
             _ptr(out.get("bitmask")), _ptr(out.get("dist2")), _ptr(out["neglog"]),
             _ptr(out.get("post")), _stream()))
+        return out
+
+    def segment(self, f, img, sp: "SegParams", want_labels=True, out=None):
+        """cs_segment: convex multilabel segmentation (Sec. 4) on the data term
+        f (device (n, H, W) float32, e.g. neglog); returns dict 'u' (n, H, W)
+        and 'labels' (H, W) int32."""
+        import torch
+
+        n, H, W = int(f.shape[0]), int(f.shape[1]), int(f.shape[2])
+        dev = f.device
+        if out is None:
+            out = {"u": torch.empty((n, H, W), dtype=torch.float32, device=dev),
+                   "labels": torch.empty((H, W), dtype=torch.int32, device=dev)
+                   if want_labels else None}
+        self.check(self._lib.cs_segment(self.handle, _ptr(f), _ptr(img), H, W, n,
+                                        ctypes.byref(sp), _ptr(out["u"]), _ptr(out.get("labels")),
+                                        _stream()))
         return out
 
     def refined_count(self):

@@ -184,6 +184,41 @@ const char* cs_last_error(const cs_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_noctx_err.c_str();
 }
 
+void cs_seg_params_default(cs_seg_params* out) {
+    if (!out) return;
+    memset(out, 0, sizeof *out);
+    out->lambda = 1.0;
+    out->nu = 0.0;
+    out->gamma = 5.0;
+    out->iterations = 300;
+}
+
+cs_status cs_segment(cs_ctx* ctx, const float* f, const float* img, int H, int W, int n_labels,
+                     const cs_seg_params* sp, float* u, int32_t* labels, void* stream) {
+    const char* fn = "cs_segment";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!f || !img || !sp || !u)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
+    if (H < 1 || W < 1 || (long long)H * W > (1ll << 31) - 1)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: bad image size %d x %d", fn, H, W);
+    if (n_labels < 1 || n_labels > CS_MAX_LABELS)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: n_labels=%d outside 1..%d", fn,
+                            n_labels, CS_MAX_LABELS);
+    if (!(sp->lambda >= 0) || !(sp->nu >= 0) || !(sp->gamma > 0) || sp->iterations < 0)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG,
+                            "%s: need lambda >= 0, nu >= 0, gamma > 0, iterations >= 0", fn);
+    DeviceGuard g(ctx->device);
+    const long long P = (long long)H * W;
+    const int nblk = (int)((P + 255) / 256 < 512 ? (P + 255) / 256 : 512);
+    cs_status s = cs_ensure_scratch(ctx, seg_scratch_bytes(P, n_labels, nblk));
+    if (s) return s;
+    SegArgs a{f, img, H, W, n_labels, (float)sp->lambda, (float)sp->nu, (float)sp->gamma,
+              sp->iterations, u, labels, reinterpret_cast<float*>(ctx->scratch), nblk};
+    cudaError_t e = launch_segment(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return CS_OK;
+}
+
 cs_status cs_refined_count(cs_ctx* ctx, int32_t* count, void* stream) {
     if (!ctx || !count)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_refined_count: null argument");

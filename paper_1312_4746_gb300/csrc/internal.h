@@ -158,6 +158,21 @@ struct SmoothArgs {
     float* post;    // optional
 };
 cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t st);
+
+// Convex multilabel segmentation (Sec. 4) on a data term.
+struct SegArgs {
+    const float* f;    // data term, n_labels x H x W
+    const float* img;  // H x W x 3
+    int H, W, n_labels;
+    float lambda, nu, gamma;
+    int iterations;
+    float* u;          // out: relaxed indicators, n_labels x H x W
+    int32_t* labels;   // out (optional): argmax, H x W
+    float* scratch;    // seg_scratch_bytes()
+    int nblk;          // blocks per label of the dual step
+};
+size_t seg_scratch_bytes(long long P, int n, int nblk);
+cudaError_t launch_segment(const SegArgs& a, cudaStream_t st);
 size_t smooth_smem_bytes(int p, int k, int n_labels);
 
 // Small host arrays passed by value (no pageable copy, so calls can be

@@ -39,6 +39,9 @@ def test_version_and_defaults(L):
     assert p.d_min == 1.0 and p.kappa_beta == 1.0 and p.mode == 0 and p.precision == 0
     assert p.codes_form == cs.CODES_AUTO and p.l_tol == 1e-3 and p.iota_sigma == 0.01
     assert ctypes.sizeof(cs.Params) == 4 * 4 + 7 * 8
+    sp = cs.SegParams.default()
+    assert ctypes.sizeof(cs.SegParams) == 3 * 8 + 2 * 4
+    assert sp.lam == 1.0 and sp.nu == 0.0 and sp.gamma == 5.0 and sp.iterations == 300
 
 
 def test_null_ctx_rejected(L):

@@ -1,0 +1,117 @@
+"""Convex multilabel segmentation (cs_segment, Sec. 4) vs the FP64 reference
+(oracle/segment.py) on the same data term.
+
+The GPU iterates in FP32, the reference in FP64; the primal-dual steps are
+non-expansive, so the iterates stay close: bars max |u - u_ref| <= 2e-3 after
+the iterations, labels equal wherever the reference's top two indicators
+differ by more than 1e-2. The boundary term is checked to shorten the
+boundaries of the pointwise argmin, and the Dice score (Eq. dice) against
+the synthetic Voronoi cells is reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import segment as oseg
+from paper_1312_4746_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(cuda_lib):
+    import torch
+
+    import paper_1312_4746_gb300 as cs
+
+    ctx = cs.Context(0)
+    yield cs, ctx, torch
+    ctx.close()
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _data_term(env, pr):
+    cs, ctx, torch = env
+    prm = cs.Params.from_synth(pr.params, precision=2)
+    out = ctx.data_term(_dev(torch, pr.image), _dev(torch, pr.omega), _dev(torch, pr.mask),
+                        pr.label_off, _dev(torch, pr.sample_pix), prm)
+    return out["neglog"]
+
+
+@pytest.mark.parametrize("lam,nu,iters", [(2.0, 0.0, 200), (8.0, 0.0, 300), (2.0, 50.0, 150)])
+def test_segment_matches_reference(env, lam, nu, iters):
+    cs, ctx, torch = env
+    pr = synth.make_problem(40, 48, 3, 60, p=7, k=98, seed=61)
+    f = _data_term(env, pr)
+    sp = cs.SegParams.default(lam=lam, nu=nu, iterations=iters)
+    out = ctx.segment(f, _dev(torch, pr.image), sp)
+    ctx.sync()
+    u = out["u"].cpu().numpy().astype(np.float64)
+    lab = out["labels"].cpu().numpy()
+    u_ref, lab_ref = oseg.segment(f.cpu().numpy().astype(np.float64), pr.image, lam, nu=nu,
+                                  iterations=iters)
+    err = float(np.max(np.abs(u - u_ref)))
+    srt = np.sort(u_ref, axis=0)
+    clear = (srt[-1] - srt[-2]) > 1e-2
+    assert err <= 2e-3, err
+    assert np.array_equal(lab[clear], lab_ref[clear])
+    np.testing.assert_allclose(u.sum(axis=0), 1.0, atol=1e-5)
+    assert u.min() >= 0.0
+    print(f"segment lambda {lam} nu {nu}, {iters} iterations: max |u - u_ref| {err:.2e}, "
+          f"labels equal on all {int(clear.sum())} pixels whose top two indicators differ "
+          f"by more than 1e-2 ({clear.mean():.3f} of the image)")
+
+
+def test_segment_lambda_zero_argmin(env):
+    cs, ctx, torch = env
+    rng = np.random.default_rng(62)
+    f = rng.uniform(0, 5, (4, 33, 29)).astype(np.float32)
+    img = rng.uniform(0, 1, (33, 29, 3)).astype(np.float32)
+    out = ctx.segment(_dev(torch, f), _dev(torch, img),
+                      cs.SegParams.default(lam=0.0, iterations=100))
+    ctx.sync()
+    np.testing.assert_array_equal(out["labels"].cpu().numpy(), np.argmin(f, axis=0))
+
+
+def test_segment_constant_data_uniform(env):
+    cs, ctx, torch = env
+    f = np.full((3, 17, 21), 1.5, np.float32)
+    img = np.random.default_rng(63).uniform(0, 1, (17, 21, 3)).astype(np.float32)
+    out = ctx.segment(_dev(torch, f), _dev(torch, img),
+                      cs.SegParams.default(lam=4.0, iterations=40))
+    ctx.sync()
+    np.testing.assert_allclose(out["u"].cpu().numpy(), 1.0 / 3.0, atol=1e-6)
+
+
+def _boundary(lab):
+    return int((lab[:, 1:] != lab[:, :-1]).sum() + (lab[1:, :] != lab[:-1, :]).sum())
+
+
+def test_segment_regularises_and_scores(env):
+    """The boundary term shortens the label boundaries of the pointwise
+    argmin of the data term; the Dice score (Eq. dice) against the Voronoi
+    cells the scribbles were drawn in is reported for both."""
+    cs, ctx, torch = env
+    pr = synth.make_problem(160, 200, 4, 400, p=7, k=98, seed=64)  # label i scribbled in cell i
+    f = _data_term(env, pr)
+    img = _dev(torch, pr.image)
+    lab0 = ctx.segment(f, img, cs.SegParams.default(lam=0.0, iterations=1))["labels"].cpu().numpy()
+    np.testing.assert_array_equal(lab0, np.argmin(f.cpu().numpy(), axis=0))
+    lab1 = ctx.segment(f, img, cs.SegParams.default(lam=4.0, iterations=300))["labels"]
+    lab1 = lab1.cpu().numpy()
+    b0, b1 = _boundary(lab0), _boundary(lab1)
+    d0, d1 = oseg.dice(lab0, pr.regions, 4), oseg.dice(lab1, pr.regions, 4)
+    print(f"200x160, 4 labels: boundary pixels {b0} -> {b1}; Dice vs cells {d0:.4f} -> {d1:.4f}")
+    assert b1 < b0
+
+
+def test_segment_invalid(env):
+    cs, ctx, torch = env
+    f = torch.zeros((2, 4, 4), device="cuda:0")
+    img = torch.zeros((4, 4, 3), device="cuda:0")
+    with pytest.raises(cs.CsError) as ei:
+        ctx.segment(f, img, cs.SegParams.default(gamma=0.0))
+    assert ei.value.status == cs.CS_ERR_INVALID_ARG
