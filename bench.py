@@ -310,6 +310,29 @@ def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=Non
     return dev_ms, e2e_ms, stage, h2d, d2h
 
 
+def measure_segment(ctx, cs, torch, pr, dev, stream, iterations=300, runs=3):
+    """Convex multilabel segmentation (cs_segment) of this workload's FP8 data
+    term: device time of `iterations` primal-dual iterations plus argmax."""
+    prm = cs.Params.from_synth(pr.params, precision=FORMS["fp8"])
+    f = ctx.data_term(torch.from_numpy(pr.image).to(dev), torch.from_numpy(pr.omega).to(dev),
+                      torch.from_numpy(pr.mask).to(dev), pr.label_off,
+                      torch.from_numpy(pr.sample_pix).to(dev), prm)["neglog"]
+    img = torch.from_numpy(pr.image).to(dev)
+    sp = cs.SegParams.default(lam=4.0, iterations=iterations)
+    out = ctx.segment(f, img, sp)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(runs):
+        ctx.segment(f, img, sp, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / runs
+    return {"what": f"cs_segment on the FP8 data term: {iterations} primal-dual iterations "
+                    f"(lambda {sp.lam}, nu {sp.nu}, gamma {sp.gamma}) and argmax",
+            "ms": ms, "ms_per_iteration": ms / iterations}
+
+
 def measure_batch(ctx, cs, torch, dev, n_images, reduce_max, world, runs=5):
     """The batch workload (uneven images, one persistent tensor-core sum over
     all of them) through cs_batch_*: autotuned, captured in a CUDA graph,
@@ -443,6 +466,7 @@ def main():
         # the smooth co-sparse texture (mode 2): FP8 Parzen sum + smooth texture posterior
         res_smooth = measure(ctx, cs, torch, pr, "fp8", args.steps, args.warmup, dev, stream,
                              flush, mode=cs.MODE_SMOOTH)
+        seg = measure_segment(ctx, cs, torch, pr, dev, stream)
     if world > 1:
         torch.distributed.barrier()
 
@@ -507,6 +531,7 @@ def main():
                 "ms_per_step": res_smooth[0] / args.steps,
                 "pairs_per_s": pairs_rank * args.steps / (res_smooth[0] * 1e-3),
                 "stage_ms": res_smooth[2]},
+            "segment": seg,
             "clocks": clocks,
         }
         if batch is not None:

@@ -278,9 +278,12 @@ cs_status cs_refined_count(cs_ctx* ctx, int32_t* count, void* stream);
  *              supervised segmentation), gamma > 0 (paper: 5), iterations >= 0
  *   u          DEVICE n_labels x H x W float32 out: the relaxed indicators
  *   labels     DEVICE H x W int32 out or NULL: argmax_i u_i(x)
- * Uses the context's scratch (4 n P + P floats). Asynchronous on `stream`
- * (3 launches per iteration). Errors: CS_ERR_INVALID_ARG for null or
- * out-of-range arguments.
+ * Uses the context's scratch (4 n P + P floats). Asynchronous on `stream`:
+ * one cooperative launch runs every iteration, with grid barriers between
+ * the dual and primal steps. Errors: CS_ERR_INVALID_ARG for null or
+ * out-of-range arguments; CS_ERR_CUDA when the launch fails; a grid barrier
+ * that waits longer than 1 s ends the launch and is reported as
+ * CS_ERR_TIMEOUT by the next cs_sync_status.
  */
 typedef struct {
     double lambda;

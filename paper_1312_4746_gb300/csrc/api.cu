@@ -209,11 +209,14 @@ cs_status cs_segment(cs_ctx* ctx, const float* f, const float* img, int H, int W
                             "%s: need lambda >= 0, nu >= 0, gamma > 0, iterations >= 0", fn);
     DeviceGuard g(ctx->device);
     const long long P = (long long)H * W;
-    const int nblk = (int)((P + 255) / 256 < 512 ? (P + 255) / 256 : 512);
+    const int nblk = seg_blocks(P, n_labels, ctx->n_sm);
+    if (nblk < 1)
+        return cs_set_error(ctx, CS_ERR_CUDA, "%s: the solver kernel cannot be resident", fn);
     cs_status s = cs_ensure_scratch(ctx, seg_scratch_bytes(P, n_labels, nblk));
     if (s) return s;
     SegArgs a{f, img, H, W, n_labels, (float)sp->lambda, (float)sp->nu, (float)sp->gamma,
-              sp->iterations, u, labels, reinterpret_cast<float*>(ctx->scratch), nblk};
+              sp->iterations, u, labels, reinterpret_cast<float*>(ctx->scratch), nblk,
+              ctx->d_err};
     cudaError_t e = launch_segment(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return CS_OK;

@@ -169,9 +169,11 @@ struct SegArgs {
     float* u;          // out: relaxed indicators, n_labels x H x W
     int32_t* labels;   // out (optional): argmax, H x W
     float* scratch;    // seg_scratch_bytes()
-    int nblk;          // blocks per label of the dual step
+    int nblk;          // blocks of the cooperative launch (seg_blocks)
+    int* d_err;        // device error word (timeout of a grid barrier)
 };
 size_t seg_scratch_bytes(long long P, int n, int nblk);
+int seg_blocks(long long P, int n_labels, int n_sm);  // 0 if the kernel cannot be resident
 cudaError_t launch_segment(const SegArgs& a, cudaStream_t st);
 size_t smooth_smem_bytes(int p, int k, int n_labels);
 

@@ -65,6 +65,43 @@ def test_segment_matches_reference(env, lam, nu, iters):
           f"by more than 1e-2 ({clear.mean():.3f} of the image)")
 
 
+@pytest.mark.parametrize("H,W,nl,seed", [(37, 53, 5, 65), (1, 700, 2, 66), (650, 1, 3, 67)])
+def test_segment_ragged(env, H, W, nl, seed):
+    """Pixel ranges of the blocks that do not start on a row; one-row and
+    one-column images (all differences across an edge zero)."""
+    cs, ctx, torch = env
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0, 4, (nl, H, W)).astype(np.float32)
+    img = rng.uniform(0, 1, (H, W, 3)).astype(np.float32)
+    out = ctx.segment(_dev(torch, f), _dev(torch, img),
+                      cs.SegParams.default(lam=3.0, iterations=120))
+    ctx.sync()
+    u_ref, _ = oseg.segment(f.astype(np.float64), img, 3.0, iterations=120)
+    err = float(np.max(np.abs(out["u"].cpu().numpy() - u_ref)))
+    assert err <= 2e-3, err
+
+
+def test_segment_full_size(env):
+    """The 481 x 321, five-label workload on the FP8 data term, in the grid the
+    benchmark runs (every co-resident block): 100 iterations vs the FP64
+    reference on every pixel."""
+    cs, ctx, torch = env
+    pr = synth.make_workload(2)
+    f = _data_term(env, pr)
+    sp = cs.SegParams.default(lam=4.0, iterations=100)
+    out = ctx.segment(f, _dev(torch, pr.image), sp)
+    ctx.sync()
+    u = out["u"].cpu().numpy().astype(np.float64)
+    u_ref, lab_ref = oseg.segment(f.cpu().numpy().astype(np.float64), pr.image, 4.0,
+                                  iterations=100)
+    err = float(np.max(np.abs(u - u_ref)))
+    srt = np.sort(u_ref, axis=0)
+    clear = (srt[-1] - srt[-2]) > 1e-2
+    assert err <= 2e-3, err
+    assert np.array_equal(out["labels"].cpu().numpy()[clear], lab_ref[clear])
+    print(f"segment 481x321, 5 labels, 100 iterations: max |u - u_ref| {err:.2e}")
+
+
 def test_segment_lambda_zero_argmin(env):
     cs, ctx, torch = env
     rng = np.random.default_rng(62)
