@@ -10,13 +10,16 @@ joined, Eq. energy1); the smooth co-support texture (Eq. map_tsm,
 approx_cosupp and post_text on iota, ``iota`` / ``median_rows`` /
 ``smooth_reps`` / ``smooth_log_posterior``) is numpy on the C oracle's FP64
 codes and Parzen sum (mode 2); ``segment.py`` is the FP64 primal-dual
-multilabel segmentation of Sec. 4 on the data term; ``mlp.py`` holds the surrogate network's FP64 forward,
+multilabel segmentation of Sec. 4 on the data term; ``unsup.py`` is the
+unsupervised mode of Sec. 3.2 (k-means on colour, k-medians on iota, the
+two-factor data term); ``mlp.py`` holds the surrogate network's FP64 forward,
 analytic backward and Adam step. This module compiles ``oracle.c`` with gcc
 (no FMA contraction) and wraps it with ctypes.
 
 Parity status of each function is recorded next to it; every function here is
-pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py`` and
-``tests/test_oracle_mlp.py``.
+pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``,
+``tests/test_oracle_mlp.py``, ``tests/test_oracle_segment.py`` and
+``tests/test_oracle_unsup.py``.
 """
 from __future__ import annotations
 
