@@ -298,6 +298,78 @@ cs_status cs_segment(cs_ctx* ctx, const float* f, const float* img, int H, int W
                      const cs_seg_params* sp, float* u, int32_t* labels, void* stream);
 
 /*
+ * Unsupervised mode (Sec. 3.2): segment classes found without scribbles.
+ * k-means on the colour pixels gives colour classes, k-medians on the
+ * smooth co-supports iota(O s_x) (Eq. map_tsm) texture classes; every
+ * (colour class a, texture class b) pair is a segment i = a n_texture + b,
+ * and the MDL label cost nu of cs_segment then removes segments.
+ *
+ * Both clusterings start from caller-given points (the random draw is the
+ * caller's), run `iterations` rounds of assignment then update, and return
+ * the assignment to the final centres. Assignments are decided in FP32 with
+ * the distance summed in a fixed order and the lower class winning ties, so
+ * that results are bit-reproducible; a class that wins no point keeps its
+ * centre. Asynchronous on `stream`; device pointers unless marked HOST.
+ *
+ * cs_kmeans: points X (N x 3 float32, e.g. the image), squared Euclidean
+ *   distance ((d0^2 + d1^2) + d2^2) without contraction; a centroid is
+ *   float32(S / (cnt 2^24)), S the exact integer sum of rint(2^24 v) over
+ *   the members (the exact mean of the values rounded to multiples of
+ *   2^-24).
+ * cs_kmedians: points are the N columns of V (k x N float32, code-major),
+ *   l1 distance summed over j = 0 .. k-1 in turn; a centre is the
+ *   elementwise median of its members (for an even count the mean of the two
+ *   middle values, (lo + hi) * 0.5 in FP32).
+ *   n_classes  1..16;  init HOST n_classes start indices in [0, N)
+ *   centres    out: n_classes x 3 (k-means) or n_classes x k (k-medians)
+ *   assign     out: N int32 or NULL
+ * Errors: CS_ERR_INVALID_ARG (null pointer, N < 1, k outside 1..1024,
+ * n_classes outside 1..16, a start index outside [0, N), iterations < 0).
+ */
+cs_status cs_kmeans(cs_ctx* ctx, const float* X, int N, int n_classes, const int32_t* init,
+                    int iterations, float* centres, int32_t* assign, void* stream);
+cs_status cs_kmedians(cs_ctx* ctx, const float* V, int N, int k, int n_classes,
+                      const int32_t* init, int iterations, float* centres, int32_t* assign,
+                      void* stream);
+
+/*
+ * cs_unsup_data_term: the unsupervised data term of an image. iota of every
+ * pixel from FP32 codes (prm->p, prm->iota_sigma; as CS_MODE_SMOOTH), k-means
+ * on the pixels' colours, k-medians on iota, then per pixel
+ *   f_{a n_t + b}(x) = -log softmax_a(-|I(x) - mu_a|^2 / (2 sigma_c2))
+ *                      -log softmax_b(-||c_b - iota(O s_x)||_1 / beta),
+ * the product of a colour and a texture posterior as in Eq. post_text
+ * (one beta: there are no scribble locations). Uses prm->p, iota_sigma,
+ * sigma_c2; the other cs_params fields are ignored.
+ *   img, omega, mask  as for cs_codes; k = rows of omega
+ *   colour_init       HOST n_colour pixel indices (start centres)
+ *   texture_init      HOST n_texture pixel indices (start centres)
+ *   neglog            out: (n_colour n_texture) x H x W float32
+ *   colour_centres    out or NULL: n_colour x 3
+ *   texture_centres   out or NULL: n_texture x k
+ *   colour_assign, texture_assign  out or NULL: H x W int32
+ * Uses the context's scratch (k H W floats of iota plus small arrays).
+ * Errors: CS_ERR_INVALID_ARG (as cs_kmeans / cs_kmedians; n_colour n_texture
+ * > 64; iota_sigma, sigma_c2 or beta not > 0; image checks of cs_codes),
+ * CS_ERR_UNSUPPORTED (p not in 3..9 odd), CS_ERR_NOMEM, CS_ERR_CUDA.
+ */
+typedef struct {
+    int32_t n_colour;             /* colour classes (k-means), 1..16 */
+    int32_t n_texture;            /* texture classes (k-medians), 1..16 */
+    int32_t kmeans_iterations;    /* >= 0 */
+    int32_t kmedians_iterations;  /* >= 0 */
+    double beta;                  /* texture temperature, > 0 */
+} cs_unsup_params;
+
+void cs_unsup_params_default(cs_unsup_params* out); /* 4, 4, 10, 10, beta 1 */
+cs_status cs_unsup_data_term(cs_ctx* ctx, const float* img, int H, int W, const float* omega,
+                             int k, const float* mask, const cs_params* prm,
+                             const cs_unsup_params* up, const int32_t* colour_init,
+                             const int32_t* texture_init, float* neglog, float* colour_centres,
+                             float* texture_centres, int32_t* colour_assign,
+                             int32_t* texture_assign, void* stream);
+
+/*
  * The whole data term in one call: patches, codes and co-support bitmasks of
  * every pixel (as cs_codes) followed by the likelihoods (as cs_likelihood).
  * The scribble distance transform depends only on the samples; it runs on a

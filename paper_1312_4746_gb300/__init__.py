@@ -49,6 +49,10 @@ EXPORTS = (
     "cs_refined_count",
     "cs_seg_params_default",
     "cs_segment",
+    "cs_kmeans",
+    "cs_kmedians",
+    "cs_unsup_params_default",
+    "cs_unsup_data_term",
     "cs_batch_create",
     "cs_batch_run",
     "cs_batch_config",
@@ -137,6 +141,26 @@ class SegParams(ctypes.Structure):
         return p
 
 
+class UnsupParams(ctypes.Structure):
+    """Mirror of cs_unsup_params (include/cosparse.h)."""
+
+    _fields_ = [
+        ("n_colour", ctypes.c_int32),
+        ("n_texture", ctypes.c_int32),
+        ("kmeans_iterations", ctypes.c_int32),
+        ("kmedians_iterations", ctypes.c_int32),
+        ("beta", ctypes.c_double),
+    ]
+
+    @classmethod
+    def default(cls, **kw):
+        p = cls()
+        lib().cs_unsup_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+
 class Image(ctypes.Structure):
     """Mirror of cs_image (include/cosparse.h)."""
 
@@ -186,6 +210,12 @@ def lib(path: str | None = None):
     L.cs_seg_params_default.argtypes = [ctypes.POINTER(SegParams)]
     L.cs_seg_params_default.restype = None
     L.cs_segment.argtypes = [V, V, V, I, I, I, ctypes.POINTER(SegParams), V, V, V]
+    L.cs_kmeans.argtypes = [V, V, I, I, V, I, V, V, V]
+    L.cs_kmedians.argtypes = [V, V, I, I, I, V, I, V, V, V]
+    L.cs_unsup_params_default.argtypes = [ctypes.POINTER(UnsupParams)]
+    L.cs_unsup_params_default.restype = None
+    L.cs_unsup_data_term.argtypes = [V, V, I, I, V, I, V, ctypes.POINTER(Params),
+                                     ctypes.POINTER(UnsupParams), V, V, V, V, V, V, V, V]
     L.cs_codes.argtypes = [V, V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V]
     L.cs_cosupport.argtypes = [V, V, I, I, D, V, V]
     L.cs_codes_noalloc.argtypes = [V, I, I, V, I, V, ctypes.POINTER(Params), V, V, V, V, V]
@@ -380,6 +410,71 @@ class Context:
         self.check(self._lib.cs_segment(self.handle, _ptr(f), _ptr(img), H, W, n,
                                         ctypes.byref(sp), _ptr(out["u"]), _ptr(out.get("labels")),
                                         _stream()))
+        return out
+
+    # ------------------------------------------------------------ unsupervised
+
+    @staticmethod
+    def _host_idx(idx):
+        import numpy as np
+
+        a = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+        return a, a.ctypes.data_as(ctypes.c_void_p)
+
+    def kmeans(self, X, init, iterations, want_assign=True):
+        """cs_kmeans on device points X (N, 3) float32 from the start indices
+        ``init`` (host); returns dict 'centres' (n, 3) and 'assign' (N,)."""
+        import torch
+
+        keep, ip = self._host_idx(init)
+        N, n = int(X.shape[0]), len(keep)
+        out = {"centres": torch.empty((n, 3), dtype=torch.float32, device=X.device),
+               "assign": torch.empty(N, dtype=torch.int32, device=X.device) if want_assign
+               else None}
+        self.check(self._lib.cs_kmeans(self.handle, _ptr(X), N, n, ip, int(iterations),
+                                       _ptr(out["centres"]), _ptr(out["assign"]), _stream()))
+        return out
+
+    def kmedians(self, V, init, iterations, want_assign=True):
+        """cs_kmedians on the columns of device V (k, N) float32."""
+        import torch
+
+        keep, ip = self._host_idx(init)
+        k, N, n = int(V.shape[0]), int(V.shape[1]), len(keep)
+        out = {"centres": torch.empty((n, k), dtype=torch.float32, device=V.device),
+               "assign": torch.empty(N, dtype=torch.int32, device=V.device) if want_assign
+               else None}
+        self.check(self._lib.cs_kmedians(self.handle, _ptr(V), N, k, n, ip, int(iterations),
+                                         _ptr(out["centres"]), _ptr(out["assign"]), _stream()))
+        return out
+
+    def unsup_data_term(self, img, omega, mask, params: Params, up: "UnsupParams", colour_init,
+                        texture_init, out=None):
+        """cs_unsup_data_term (Sec. 3.2): returns dict 'neglog'
+        (n_colour n_texture, H, W), 'colour_centres', 'texture_centres',
+        'colour_assign', 'texture_assign'."""
+        import torch
+
+        H, W = int(img.shape[0]), int(img.shape[1])
+        k = int(omega.shape[0])
+        dev = img.device
+        ck, cp = self._host_idx(colour_init)
+        tk, tp = self._host_idx(texture_init)
+        if len(ck) != up.n_colour or len(tk) != up.n_texture:
+            raise ValueError("start index counts must equal n_colour and n_texture")
+        if out is None:
+            out = {"neglog": torch.empty((up.n_colour * up.n_texture, H, W), dtype=torch.float32,
+                                         device=dev),
+                   "colour_centres": torch.empty((up.n_colour, 3), dtype=torch.float32, device=dev),
+                   "texture_centres": torch.empty((up.n_texture, k), dtype=torch.float32,
+                                                  device=dev),
+                   "colour_assign": torch.empty((H, W), dtype=torch.int32, device=dev),
+                   "texture_assign": torch.empty((H, W), dtype=torch.int32, device=dev)}
+        self.check(self._lib.cs_unsup_data_term(
+            self.handle, _ptr(img), H, W, _ptr(omega), k, _ptr(mask), ctypes.byref(params),
+            ctypes.byref(up), cp, tp, _ptr(out["neglog"]), _ptr(out.get("colour_centres")),
+            _ptr(out.get("texture_centres")), _ptr(out.get("colour_assign")),
+            _ptr(out.get("texture_assign")), _stream()))
         return out
 
     def refined_count(self):

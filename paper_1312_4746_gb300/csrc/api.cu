@@ -222,6 +222,150 @@ cs_status cs_segment(cs_ctx* ctx, const float* f, const float* img, int H, int W
     return CS_OK;
 }
 
+// ---------------------------------------------------------------- unsupervised mode
+
+static cs_status unsup_init(cs_ctx* ctx, const char* fn, const int32_t* init, int n, long long N,
+                            UnsupInit* out) {
+    if (!init) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: start indices are NULL", fn);
+    memset(out, 0, sizeof *out);
+    for (int i = 0; i < n; ++i) {
+        if (init[i] < 0 || init[i] >= N)
+            return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: start index %d = %d outside [0, %lld)",
+                                fn, i, init[i], N);
+        out->v[i] = init[i];
+    }
+    return CS_OK;
+}
+
+static cs_status unsup_classes(cs_ctx* ctx, const char* fn, int n, int iterations) {
+    if (n < 1 || n > CS_MAX_CLASSES)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: %d classes outside 1..%d", fn, n,
+                            CS_MAX_CLASSES);
+    if (iterations < 0) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: iterations < 0", fn);
+    return CS_OK;
+}
+
+cs_status cs_kmeans(cs_ctx* ctx, const float* X, int N, int n_classes, const int32_t* init,
+                    int iterations, float* centres, int32_t* assign, void* stream) {
+    const char* fn = "cs_kmeans";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!X || !centres) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null pointer", fn);
+    if (N < 1) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: N = %d < 1", fn, N);
+    cs_status s = unsup_classes(ctx, fn, n_classes, iterations);
+    UnsupInit in;
+    if (!s) s = unsup_init(ctx, fn, init, n_classes, N, &in);
+    if (s) return s;
+    DeviceGuard g(ctx->device);
+    if ((s = cs_ensure_scratch(ctx, kmeans_scratch_bytes(n_classes)))) return s;
+    KmeansArgs a{X, N, n_classes, in, iterations, centres, assign, ctx->scratch, ctx->n_sm};
+    cudaError_t e = launch_kmeans(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return CS_OK;
+}
+
+cs_status cs_kmedians(cs_ctx* ctx, const float* V, int N, int k, int n_classes,
+                      const int32_t* init, int iterations, float* centres, int32_t* assign,
+                      void* stream) {
+    const char* fn = "cs_kmedians";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!V || !centres) return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null pointer", fn);
+    if (N < 1 || k < 1 || k > CS_MAX_K)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: bad shape N=%d k=%d", fn, N, k);
+    cs_status s = unsup_classes(ctx, fn, n_classes, iterations);
+    UnsupInit in;
+    if (!s) s = unsup_init(ctx, fn, init, n_classes, N, &in);
+    if (s) return s;
+    DeviceGuard g(ctx->device);
+    Carve m(nullptr);
+    m.take<char>(kmedians_scratch_bytes(N, n_classes));
+    m.take<int32_t>(N);
+    if ((s = cs_ensure_scratch(ctx, m.off))) return s;
+    Carve c(ctx->scratch);
+    void* ks = c.take<char>(kmedians_scratch_bytes(N, n_classes));
+    int32_t* work = assign ? assign : c.take<int32_t>(N);
+    KmediansArgs a{V, N, k, n_classes, in, iterations, centres, assign, work, ks, ctx->n_sm};
+    cudaError_t e = launch_kmedians(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return CS_OK;
+}
+
+void cs_unsup_params_default(cs_unsup_params* out) {
+    if (!out) return;
+    memset(out, 0, sizeof *out);
+    out->n_colour = 4;
+    out->n_texture = 4;
+    out->kmeans_iterations = 10;
+    out->kmedians_iterations = 10;
+    out->beta = 1.0;
+}
+
+cs_status cs_unsup_data_term(cs_ctx* ctx, const float* img, int H, int W, const float* omega,
+                             int k, const float* mask, const cs_params* prm,
+                             const cs_unsup_params* up, const int32_t* colour_init,
+                             const int32_t* texture_init, float* neglog, float* colour_centres,
+                             float* texture_centres, int32_t* colour_assign,
+                             int32_t* texture_assign, void* stream) {
+    const char* fn = "cs_unsup_data_term";
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+    if (!img || !omega || !mask || !up || !neglog)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: null required pointer", fn);
+    cs_status s = cs_check_image(ctx, fn, H, W, k);
+    if (!s) s = cs_check_patch(ctx, fn, prm);
+    if (s) return s;
+    if (!(prm->iota_sigma > 0) || !(prm->sigma_c2 > 0) || !(up->beta > 0))
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: iota_sigma, sigma_c2 and beta must be > 0",
+                            fn);
+    const long long P = (long long)H * W;
+    UnsupInit ci, ti;
+    if (!s) s = unsup_classes(ctx, fn, up->n_colour, up->kmeans_iterations);
+    if (!s) s = unsup_classes(ctx, fn, up->n_texture, up->kmedians_iterations);
+    if (!s) s = unsup_init(ctx, fn, colour_init, up->n_colour, P, &ci);
+    if (!s) s = unsup_init(ctx, fn, texture_init, up->n_texture, P, &ti);
+    if (s) return s;
+    if (up->n_colour * up->n_texture > CS_MAX_LABELS)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: %d x %d segments exceed %d", fn,
+                            up->n_colour, up->n_texture, CS_MAX_LABELS);
+    DeviceGuard g(ctx->device);
+    const int nc = up->n_colour, nt = up->n_texture;
+    auto carve = [&](Carve& c, float** iota, float** cc, float** tc, void** km, void** kd,
+                     int32_t** work) {
+        *iota = c.take<float>((size_t)k * P);
+        *cc = colour_centres ? colour_centres : c.take<float>(3 * (size_t)nc);
+        *tc = texture_centres ? texture_centres : c.take<float>((size_t)nt * k);
+        *km = c.take<char>(kmeans_scratch_bytes(nc));
+        *kd = c.take<char>(kmedians_scratch_bytes(P, nt));
+        *work = texture_assign ? texture_assign : c.take<int32_t>(P);
+    };
+    float *iota, *cc, *tc;
+    void *km, *kd;
+    int32_t* work;
+    Carve m(nullptr);
+    carve(m, &iota, &cc, &tc, &km, &kd, &work);
+    if ((s = cs_ensure_scratch(ctx, m.off))) return s;
+    Carve c(ctx->scratch);
+    carve(c, &iota, &cc, &tc, &km, &kd, &work);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_iota_pixels(img, H, W, omega, k, prm->p, mask, (float)prm->iota_sigma,
+                                       iota, st);
+    if (e == cudaSuccess) {
+        KmeansArgs a{img, (int)P, nc, ci, up->kmeans_iterations, cc, nullptr, km, ctx->n_sm};
+        e = launch_kmeans(a, st);
+    }
+    if (e == cudaSuccess) {
+        KmediansArgs a{iota, (int)P, k, nt, ti, up->kmedians_iterations, tc, nullptr, work, kd,
+                       ctx->n_sm};
+        e = launch_kmedians(a, st);
+    }
+    if (e == cudaSuccess) {
+        UnsupFinalArgs a{img, (int)P, iota, k, cc, nc, tc, nt, (float)(0.5 / prm->sigma_c2),
+                         (float)(1.0 / up->beta), neglog, colour_assign, texture_assign,
+                         ctx->n_sm};
+        e = launch_unsup_final(a, st);
+    }
+    if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return CS_OK;
+}
+
 cs_status cs_refined_count(cs_ctx* ctx, int32_t* count, void* stream) {
     if (!ctx || !count)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_refined_count: null argument");

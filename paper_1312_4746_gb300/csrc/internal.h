@@ -19,6 +19,7 @@
 // Largest supported shapes.
 #define CS_MAX_K 1024
 #define CS_MAX_LABELS 64
+#define CS_MAX_CLASSES 16  // colour or texture classes of the unsupervised mode
 #define CS_MAX_SIDE 23170  // keeps W^2 + H^2 < 2^31 for the exact distances
 
 struct StageRecord {
@@ -176,6 +177,59 @@ size_t seg_scratch_bytes(long long P, int n, int nblk);
 int seg_blocks(long long P, int n_labels, int n_sm);  // 0 if the kernel cannot be resident
 cudaError_t launch_segment(const SegArgs& a, cudaStream_t st);
 size_t smooth_smem_bytes(int p, int k, int n_labels);
+
+// Unsupervised mode (Sec. 3.2): iota of every pixel, clusterings, data term.
+cudaError_t launch_iota_pixels(const float* img, int H, int W, const float* omega, int k, int p,
+                               const float* mask, float sigma, float* iota /* k x H W */,
+                               cudaStream_t st);
+// out[i * k + j] = median over group i of V[j * S + e] (e in off[i] .. off[i+1]-1,
+// through members[] when given); empty groups keep their row.
+cudaError_t launch_group_medians(const float* V, int S, int k, int n_groups, const int32_t* off,
+                                 const int32_t* members, float* out, cudaStream_t st);
+struct UnsupInit {
+    int32_t v[CS_MAX_CLASSES];  // start pixels (validated on the host)
+};
+struct KmeansArgs {
+    const float* X;  // N x 3
+    int N, n;
+    UnsupInit init;
+    int iterations;
+    float* C;          // out: n x 3
+    int32_t* assign;   // out (optional): N
+    void* scratch;     // kmeans_scratch_bytes(n)
+    int n_sm;
+};
+struct KmediansArgs {
+    const float* V;  // k x N, code-major
+    int N, k, n;
+    UnsupInit init;
+    int iterations;
+    float* C;              // out: n x k
+    int32_t* assign;       // out (optional): N
+    int32_t* work_assign;  // N (may equal assign)
+    void* scratch;         // kmedians_scratch_bytes(N, n)
+    int n_sm;
+};
+struct UnsupFinalArgs {
+    const float* img;  // P x 3
+    int P;
+    const float* V;  // k x P iota
+    int k;
+    const float* Ccol;
+    int nc;
+    const float* Ctex;
+    int nt;
+    float inv2s2, inv_beta;
+    float* neglog;     // (nc nt) x P
+    int32_t* cassign;  // optional
+    int32_t* tassign;  // optional
+    int n_sm;
+};
+size_t kmeans_scratch_bytes(int n);
+size_t kmedians_scratch_bytes(long long N, int n);
+cudaError_t launch_kmeans(const KmeansArgs& a, cudaStream_t st);
+cudaError_t launch_kmedians(const KmediansArgs& a, cudaStream_t st);
+cudaError_t launch_unsup_final(const UnsupFinalArgs& a, cudaStream_t st);
 
 // Small host arrays passed by value (no pageable copy, so calls can be
 // captured in a CUDA graph): label offsets and first sample tile per label.

@@ -9,7 +9,7 @@
 // whose centred norm is within the FP32 bound of zero is taken as flat
 // (s = 0, every code 0, iota = 1). Three launches after the sum:
 //   smooth_iota_samples_kernel  iota of every scribble sample (code-major)
-//   smooth_median_kernel        c_i by exact radix selection (one block per
+//   group_median_kernel         c_i by exact radix selection (one block per
 //                               label and code; the mean of the two middle
 //                               values for an even count)
 //   smooth_texture_kernel       per pixel: iota, l1 to each c_i, the texture
@@ -93,7 +93,8 @@ __device__ __forceinline__ float dot_row(const float* row, const float* s, int n
     return a0 + a1;
 }
 
-// iota of every scribble sample, code-major: iota_smp[j * S + s].
+// iota of every scribble sample (every pixel when sample_pix is null),
+// code-major: iota_smp[j * S + s].
 template <int P>
 __global__ void __launch_bounds__(SL) smooth_iota_samples_kernel(
     const float* __restrict__ img, int H, int W, const float* __restrict__ omega, int k,
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(SL) smooth_iota_samples_kernel(
     __syncthreads();
     const int s_idx = blockIdx.x * SL + threadIdx.x;
     const bool live = s_idx < S;
-    int pix = live ? sample_pix[s_idx] : 0;
+    int pix = live ? (sample_pix ? sample_pix[s_idx] : s_idx) : 0;  // no list: every pixel
     if (pix < 0 || pix >= H * W) pix = 0;  // reported by the distance transform's seed pass
     const int y = pix / W, x = pix % W;
     auto px_at = [&](int t) {
@@ -129,17 +130,26 @@ __global__ void __launch_bounds__(SL) smooth_iota_samples_kernel(
     }
 }
 
-// r-th smallest (0-based) of the m non-negative floats v[0..m) by four 8-bit
-// radix passes over their bit patterns (order-preserving for values >= 0).
-__device__ float radix_select(const float* __restrict__ v, int m, int r, unsigned* hist,
-                              unsigned* s_state) {
+// Order-preserving map of a float's bits to an unsigned key, and back.
+__device__ __forceinline__ unsigned f2key(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// r-th smallest (0-based) of the m floats get(0 .. m-1) by four 8-bit radix
+// passes over their order-preserving keys.
+template <class Get>
+__device__ float radix_select(Get get, int m, int r, unsigned* hist, unsigned* s_state) {
     unsigned prefix = 0, pmask = 0;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
         __syncthreads();
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const unsigned u = __float_as_uint(v[i]);
+            const unsigned u = f2key(get(i));
             if ((u & pmask) == prefix) atomicAdd(hist + ((u >> shift) & 255u), 1u);
         }
         __syncthreads();
@@ -159,21 +169,32 @@ __device__ float radix_select(const float* __restrict__ v, int m, int r, unsigne
         r = (int)s_state[1];
         __syncthreads();
     }
-    return __uint_as_float(prefix);
+    return key2f(prefix);
 }
 
-// c[i * k + j] = median over label i's samples of iota_smp[j][s].
-__global__ void __launch_bounds__(256) smooth_median_kernel(
-    const float* __restrict__ iota_smp, int S, int k, const int32_t* __restrict__ label_off,
-    float* __restrict__ reps) {
+// out[i * k + j] = median over group i of V[j * S + e], e running over the
+// group's entries: off[i] .. off[i + 1] - 1 directly, or members[...] of that
+// range when a member list is given. An empty group leaves its row as it is.
+__global__ void __launch_bounds__(256) group_median_kernel(
+    const float* __restrict__ V, int S, int k, const int32_t* __restrict__ off,
+    const int32_t* __restrict__ members, float* __restrict__ out) {
     __shared__ unsigned hist[256];
     __shared__ unsigned s_state[2];
     const int i = blockIdx.y, j = blockIdx.x;
-    const int off = label_off[i], m = label_off[i + 1] - off;
-    const float* v = iota_smp + (size_t)j * S + off;
-    const float lo = radix_select(v, m, (m - 1) / 2, hist, s_state);
-    const float hi = (m % 2) ? lo : radix_select(v, m, m / 2, hist, s_state);
-    if (threadIdx.x == 0) reps[(size_t)i * k + j] = (m % 2) ? lo : 0.5f * (lo + hi);
+    const int o = off[i], m = off[i + 1] - o;
+    if (m <= 0) return;
+    const float* v = V + (size_t)j * S;
+    float lo, hi;
+    if (members) {
+        auto get = [&](int e) { return v[members[o + e]]; };
+        lo = radix_select(get, m, (m - 1) / 2, hist, s_state);
+        hi = (m % 2) ? lo : radix_select(get, m, m / 2, hist, s_state);
+    } else {
+        auto get = [&](int e) { return v[o + e]; };
+        lo = radix_select(get, m, (m - 1) / 2, hist, s_state);
+        hi = (m % 2) ? lo : radix_select(get, m, m / 2, hist, s_state);
+    }
+    if (threadIdx.x == 0) out[(size_t)i * k + j] = (m % 2) ? lo : __fmul_rn(0.5f, __fadd_rn(lo, hi));
 }
 
 // Per pixel: iota of its codes, l1 to each representative, the texture
@@ -261,8 +282,8 @@ cudaError_t smooth_p(const SmoothArgs& a, cudaStream_t st) {
     constexpr int N = P * P, NP = (N + 3) & ~3, TW = ST + P - 1;
     smooth_iota_samples_kernel<P><<<(a.S + SL - 1) / SL, SL, 0, st>>>(
         a.img, a.H, a.W, a.omega, a.k, a.mask, a.sample_pix, a.S, a.sigma, a.iota_smp);
-    smooth_median_kernel<<<dim3(a.k, a.n_labels), 256, 0, st>>>(a.iota_smp, a.S, a.k,
-                                                                 a.d_label_off, a.reps);
+    group_median_kernel<<<dim3(a.k, a.n_labels), 256, 0, st>>>(a.iota_smp, a.S, a.k,
+                                                                a.d_label_off, nullptr, a.reps);
     const size_t smem = sizeof(float) * ((size_t)32 * NP + 2 * TW * TW + ((N + 3) & ~3) +
                                          (size_t)a.n_labels * a.k + (size_t)a.n_labels * ST * ST);
     cudaError_t e = cudaFuncSetAttribute(smooth_texture_kernel<P>,
@@ -275,12 +296,38 @@ cudaError_t smooth_p(const SmoothArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t iota_pixels_p(const float* img, int H, int W, const float* omega, int k,
+                          const float* mask, float sigma, float* iota, cudaStream_t st) {
+    const int S = H * W;
+    smooth_iota_samples_kernel<P><<<(S + SL - 1) / SL, SL, 0, st>>>(img, H, W, omega, k, mask,
+                                                                   nullptr, S, sigma, iota);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t smooth_smem_bytes(int p, int k, int n_labels) {
     const int N = p * p, NP = (N + 3) & ~3, TW = ST + p - 1;
     return sizeof(float) * ((size_t)32 * NP + 2 * TW * TW + NP + (size_t)n_labels * k +
                             (size_t)n_labels * ST * ST);
+}
+
+cudaError_t launch_iota_pixels(const float* img, int H, int W, const float* omega, int k, int p,
+                               const float* mask, float sigma, float* iota, cudaStream_t st) {
+    switch (p) {
+        case 3: return iota_pixels_p<3>(img, H, W, omega, k, mask, sigma, iota, st);
+        case 5: return iota_pixels_p<5>(img, H, W, omega, k, mask, sigma, iota, st);
+        case 7: return iota_pixels_p<7>(img, H, W, omega, k, mask, sigma, iota, st);
+        case 9: return iota_pixels_p<9>(img, H, W, omega, k, mask, sigma, iota, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_group_medians(const float* V, int S, int k, int n_groups, const int32_t* off,
+                                 const int32_t* members, float* out, cudaStream_t st) {
+    group_median_kernel<<<dim3(k, n_groups), 256, 0, st>>>(V, S, k, off, members, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t st) {

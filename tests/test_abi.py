@@ -42,6 +42,10 @@ def test_version_and_defaults(L):
     sp = cs.SegParams.default()
     assert ctypes.sizeof(cs.SegParams) == 3 * 8 + 2 * 4
     assert sp.lam == 1.0 and sp.nu == 0.0 and sp.gamma == 5.0 and sp.iterations == 300
+    up = cs.UnsupParams.default()
+    assert ctypes.sizeof(cs.UnsupParams) == 4 * 4 + 8
+    assert (up.n_colour, up.n_texture, up.kmeans_iterations, up.kmedians_iterations,
+            up.beta) == (4, 4, 10, 10, 1.0)
 
 
 def test_null_ctx_rejected(L):
@@ -54,6 +58,13 @@ def test_null_ctx_rejected(L):
                            None, None) == cs.CS_ERR_INVALID_ARG
     assert L.cs_cosupport(None, None, 4, 8, 0.1, None, None) == cs.CS_ERR_INVALID_ARG
     assert L.cs_sync_status(None, None) == cs.CS_ERR_INVALID_ARG
+    init = (ctypes.c_int32 * 2)(0, 1)
+    assert L.cs_kmeans(None, None, 4, 2, init, 1, None, None, None) == cs.CS_ERR_INVALID_ARG
+    assert L.cs_kmedians(None, None, 4, 3, 2, init, 1, None, None, None) == cs.CS_ERR_INVALID_ARG
+    up = cs.UnsupParams.default()
+    assert L.cs_unsup_data_term(None, None, 4, 4, None, 8, None, ctypes.byref(p), ctypes.byref(up),
+                                init, init, None, None, None, None, None,
+                                None) == cs.CS_ERR_INVALID_ARG
     h = ctypes.c_void_p()
     assert L.cs_create(None, 0) == cs.CS_ERR_INVALID_ARG
     L.cs_destroy(None)  # no-op
