@@ -333,6 +333,45 @@ def measure_segment(ctx, cs, torch, pr, dev, stream, iterations=300, runs=3):
             "ms": ms, "ms_per_iteration": ms / iterations}
 
 
+def measure_unsup(ctx, cs, torch, pr, dev, stream, runs=3):
+    """Unsupervised segmentation of this workload's image (Sec. 3.2 with the
+    Berkeley settings: 16 initial segments = 4 colour x 4 texture classes,
+    lambda 6, nu 1100): cs_unsup_data_term, then cs_segment; device time of
+    each part, and how many labels the label cost leaves."""
+    import numpy as np
+
+    P = pr.H * pr.W
+    prm = cs.Params.from_synth(pr.params)
+    prm.sigma_c2 = 0.02
+    up = cs.UnsupParams.default(beta=0.5)
+    ci = np.random.default_rng(2).choice(P, up.n_colour, replace=False).astype(np.int32)
+    ti = np.random.default_rng(3).choice(P, up.n_texture, replace=False).astype(np.int32)
+    img = torch.from_numpy(pr.image).to(dev)
+    om = torch.from_numpy(pr.omega).to(dev)
+    mk = torch.from_numpy(pr.mask).to(dev)
+    sp = cs.SegParams.default(lam=6.0, nu=1100.0, iterations=300)
+    out = ctx.unsup_data_term(img, om, mk, prm, up, ci, ti)  # warm-up
+    seg = ctx.segment(out["neglog"], img, sp)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_dt = t_seg = 0.0
+    for _ in range(runs):
+        ev[0].record(stream)
+        ctx.unsup_data_term(img, om, mk, prm, up, ci, ti, out=out)
+        ev[1].record(stream)
+        ctx.segment(out["neglog"], img, sp, out=seg)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        t_dt += ev[0].elapsed_time(ev[1]) / runs
+        t_seg += ev[1].elapsed_time(ev[2]) / runs
+    used = int(torch.unique(seg["labels"]).numel())
+    return {"what": "unsupervised segmentation: iota of every pixel, k-means (4 colour classes, "
+                    "10 rounds), k-medians (4 texture classes, 10 rounds), 16-segment data term "
+                    "(sigma_c2 0.02, beta 0.5), then 300 solver iterations with lambda 6, nu 1100",
+            "data_term_ms": t_dt, "segment_ms": t_seg, "total_ms": t_dt + t_seg,
+            "labels_left": used}
+
+
 def measure_batch(ctx, cs, torch, dev, n_images, reduce_max, world, runs=5):
     """The batch workload (uneven images, one persistent tensor-core sum over
     all of them) through cs_batch_*: autotuned, captured in a CUDA graph,
@@ -467,6 +506,7 @@ def main():
         res_smooth = measure(ctx, cs, torch, pr, "fp8", args.steps, args.warmup, dev, stream,
                              flush, mode=cs.MODE_SMOOTH)
         seg = measure_segment(ctx, cs, torch, pr, dev, stream)
+        uns = measure_unsup(ctx, cs, torch, pr, dev, stream)
     if world > 1:
         torch.distributed.barrier()
 
@@ -532,6 +572,7 @@ def main():
                 "pairs_per_s": pairs_rank * args.steps / (res_smooth[0] * 1e-3),
                 "stage_ms": res_smooth[2]},
             "segment": seg,
+            "unsupervised": uns,
             "clocks": clocks,
         }
         if batch is not None:

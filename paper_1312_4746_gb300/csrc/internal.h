@@ -182,10 +182,6 @@ size_t smooth_smem_bytes(int p, int k, int n_labels);
 cudaError_t launch_iota_pixels(const float* img, int H, int W, const float* omega, int k, int p,
                                const float* mask, float sigma, float* iota /* k x H W */,
                                cudaStream_t st);
-// out[i * k + j] = median over group i of V[j * S + e] (e in off[i] .. off[i+1]-1,
-// through members[] when given); empty groups keep their row.
-cudaError_t launch_group_medians(const float* V, int S, int k, int n_groups, const int32_t* off,
-                                 const int32_t* members, float* out, cudaStream_t st);
 struct UnsupInit {
     int32_t v[CS_MAX_CLASSES];  // start pixels (validated on the host)
 };
@@ -207,7 +203,7 @@ struct KmediansArgs {
     float* C;              // out: n x k
     int32_t* assign;       // out (optional): N
     int32_t* work_assign;  // N (may equal assign)
-    void* scratch;         // kmedians_scratch_bytes(N, n)
+    void* scratch;         // kmedians_scratch_bytes(N, n) (unused at present)
     int n_sm;
 };
 struct UnsupFinalArgs {

@@ -9,7 +9,7 @@
 // whose centred norm is within the FP32 bound of zero is taken as flat
 // (s = 0, every code 0, iota = 1). Three launches after the sum:
 //   smooth_iota_samples_kernel  iota of every scribble sample (code-major)
-//   group_median_kernel         c_i by exact radix selection (one block per
+//   smooth_median_kernel        c_i by exact radix selection (one block per
 //                               label and code; the mean of the two middle
 //                               values for an even count)
 //   smooth_texture_kernel       per pixel: iota, l1 to each c_i, the texture
@@ -172,29 +172,19 @@ __device__ float radix_select(Get get, int m, int r, unsigned* hist, unsigned* s
     return key2f(prefix);
 }
 
-// out[i * k + j] = median over group i of V[j * S + e], e running over the
-// group's entries: off[i] .. off[i + 1] - 1 directly, or members[...] of that
-// range when a member list is given. An empty group leaves its row as it is.
-__global__ void __launch_bounds__(256) group_median_kernel(
-    const float* __restrict__ V, int S, int k, const int32_t* __restrict__ off,
-    const int32_t* __restrict__ members, float* __restrict__ out) {
+// c[i * k + j] = median over label i's samples of iota_smp[j][s].
+__global__ void __launch_bounds__(256) smooth_median_kernel(
+    const float* __restrict__ iota_smp, int S, int k, const int32_t* __restrict__ label_off,
+    float* __restrict__ reps) {
     __shared__ unsigned hist[256];
     __shared__ unsigned s_state[2];
     const int i = blockIdx.y, j = blockIdx.x;
-    const int o = off[i], m = off[i + 1] - o;
-    if (m <= 0) return;
-    const float* v = V + (size_t)j * S;
-    float lo, hi;
-    if (members) {
-        auto get = [&](int e) { return v[members[o + e]]; };
-        lo = radix_select(get, m, (m - 1) / 2, hist, s_state);
-        hi = (m % 2) ? lo : radix_select(get, m, m / 2, hist, s_state);
-    } else {
-        auto get = [&](int e) { return v[o + e]; };
-        lo = radix_select(get, m, (m - 1) / 2, hist, s_state);
-        hi = (m % 2) ? lo : radix_select(get, m, m / 2, hist, s_state);
-    }
-    if (threadIdx.x == 0) out[(size_t)i * k + j] = (m % 2) ? lo : __fmul_rn(0.5f, __fadd_rn(lo, hi));
+    const int off = label_off[i], m = label_off[i + 1] - off;
+    const float* v = iota_smp + (size_t)j * S + off;
+    auto get = [&](int e) { return v[e]; };
+    const float lo = radix_select(get, m, (m - 1) / 2, hist, s_state);
+    const float hi = (m % 2) ? lo : radix_select(get, m, m / 2, hist, s_state);
+    if (threadIdx.x == 0) reps[(size_t)i * k + j] = (m % 2) ? lo : __fmul_rn(0.5f, __fadd_rn(lo, hi));
 }
 
 // Per pixel: iota of its codes, l1 to each representative, the texture
@@ -282,8 +272,8 @@ cudaError_t smooth_p(const SmoothArgs& a, cudaStream_t st) {
     constexpr int N = P * P, NP = (N + 3) & ~3, TW = ST + P - 1;
     smooth_iota_samples_kernel<P><<<(a.S + SL - 1) / SL, SL, 0, st>>>(
         a.img, a.H, a.W, a.omega, a.k, a.mask, a.sample_pix, a.S, a.sigma, a.iota_smp);
-    group_median_kernel<<<dim3(a.k, a.n_labels), 256, 0, st>>>(a.iota_smp, a.S, a.k,
-                                                                a.d_label_off, nullptr, a.reps);
+    smooth_median_kernel<<<dim3(a.k, a.n_labels), 256, 0, st>>>(a.iota_smp, a.S, a.k,
+                                                                 a.d_label_off, a.reps);
     const size_t smem = sizeof(float) * ((size_t)32 * NP + 2 * TW * TW + ((N + 3) & ~3) +
                                          (size_t)a.n_labels * a.k + (size_t)a.n_labels * ST * ST);
     cudaError_t e = cudaFuncSetAttribute(smooth_texture_kernel<P>,
@@ -322,12 +312,6 @@ cudaError_t launch_iota_pixels(const float* img, int H, int W, const float* omeg
         case 9: return iota_pixels_p<9>(img, H, W, omega, k, mask, sigma, iota, st);
         default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_group_medians(const float* V, int S, int k, int n_groups, const int32_t* off,
-                                 const int32_t* members, float* out, cudaStream_t st) {
-    group_median_kernel<<<dim3(k, n_groups), 256, 0, st>>>(V, S, k, off, members, out);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t st) {

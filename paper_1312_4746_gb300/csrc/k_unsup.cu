@@ -11,8 +11,8 @@
 // bit. A k-means centroid is the exact mean of the members' values rounded
 // to multiples of 2^-24: integer sums (order-free atomics), one double
 // division, one rounding to FP32. A k-medians centre is the elementwise
-// median by radix selection over the class's member list. A class without
-// members keeps its centre.
+// median by radix selection, all classes of a code in one pass over the
+// points. A class without members keeps its centre.
 #include <cstdint>
 
 #include "internal.h"
@@ -20,6 +20,7 @@
 namespace {
 
 constexpr int UB = 256;             // threads per block
+constexpr int MB = 512;             // threads per block of the median kernel
 constexpr float QSCALE = 16777216.f;  // 2^24
 
 __global__ void kmeans_init_kernel(const float* __restrict__ X, UnsupInit init, int n,
@@ -104,6 +105,7 @@ __device__ __forceinline__ void l1_all(const float* __restrict__ V, int N, int k
                                        const float* C, int n, float (&d)[CS_MAX_CLASSES]) {
 #pragma unroll
     for (int b = 0; b < CS_MAX_CLASSES; ++b) d[b] = 0.f;
+#pragma unroll 4
     for (int j = 0; j < k; ++j) {
         const float v = V[(size_t)j * N + q];
 #pragma unroll
@@ -136,36 +138,100 @@ __global__ void __launch_bounds__(UB) kmedians_assign_kernel(
         if (s_cnt[t]) atomicAdd(counts + t, s_cnt[t]);
 }
 
-// Class offsets (exclusive scan of the counts), fill cursors cleared.
-__global__ void class_offsets_kernel(unsigned* __restrict__ counts, int n,
-                                     int32_t* __restrict__ off, unsigned* __restrict__ cursor) {
-    if (threadIdx.x != 0) return;
-    int acc = 0;
-    for (int b = 0; b < n; ++b) {
-        off[b] = acc;
-        acc += (int)counts[b];
-        counts[b] = 0u;
-        cursor[b] = 0u;
-    }
-    off[n] = acc;
+// Order-preserving map of a float's bits to an unsigned key, and back.
+__device__ __forceinline__ unsigned key_of(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_of(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Member lists by class (order within a class is free: medians do not see it).
-__global__ void class_scatter_kernel(const int32_t* __restrict__ assign, int N,
-                                     const int32_t* __restrict__ off, unsigned* __restrict__ cursor,
-                                     int32_t* __restrict__ members) {
+// One block per code j: the elementwise median of every class over the
+// points assigned to it, by radix selection (four 8-bit passes) on all
+// classes at once. Each pass reads row j of V and the assignment once,
+// coalesced; histogram updates are aggregated per (class, digit) within a
+// warp. For an even count the upper middle value is the lower one when that
+// key occurs at least twice more from its rank on, else the least key above
+// it (one more pass). Classes without points keep their centre.
+__global__ void __launch_bounds__(MB) class_median_kernel(const float* __restrict__ V, int N,
+                                                          int k, const int32_t* __restrict__ assign,
+                                                          int n, float* __restrict__ C) {
+    __shared__ unsigned hist[CS_MAX_CLASSES][256];
+    __shared__ unsigned s_pre[CS_MAX_CLASSES], s_msk[CS_MAX_CLASSES], s_rank[CS_MAX_CLASSES];
+    __shared__ unsigned s_cnt[CS_MAX_CLASSES], s_eq[CS_MAX_CLASSES], s_min[CS_MAX_CLASSES];
+    __shared__ int s_need;
+    const int j = blockIdx.x;
     const unsigned lane = threadIdx.x & 31u;
-    for (int q = blockIdx.x * UB + threadIdx.x; q < N; q += gridDim.x * UB) {
-        const int b = assign[q];
-        // one atomic per class and warp: the lowest lane of each class group
-        // reserves the group's slots
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, b);
-        const int leader = __ffs(peers) - 1;
-        unsigned base = 0;
-        if ((int)lane == leader) base = atomicAdd(cursor + b, (unsigned)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        members[off[b] + (int)(base + __popc(peers & ((1u << lane) - 1u)))] = q;
+    const float* v = V + (size_t)j * N;
+    if (threadIdx.x < CS_MAX_CLASSES) {
+        s_pre[threadIdx.x] = s_msk[threadIdx.x] = s_cnt[threadIdx.x] = s_eq[threadIdx.x] = 0u;
+        s_rank[threadIdx.x] = 0u;
+        s_min[threadIdx.x] = 0xffffffffu;
+    }
+    if (threadIdx.x == 0) s_need = 0;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        for (int t = threadIdx.x; t < n * 256; t += MB) hist[t >> 8][t & 255] = 0u;
+        __syncthreads();
+        for (int q = threadIdx.x; q < N; q += MB) {
+            const int b = assign[q];
+            const unsigned key = key_of(v[q]);
+            const bool take = (key & s_msk[b]) == s_pre[b];
+            const unsigned dig = (key >> shift) & 255u;
+            const unsigned grp =
+                __match_any_sync(__activemask(), take ? ((unsigned)b << 8 | dig) : 0xffffffffu);
+            if (take && (int)lane == __ffs(grp) - 1) atomicAdd(&hist[b][dig], (unsigned)__popc(grp));
+        }
+        __syncthreads();
+        if (threadIdx.x < n) {
+            const int b = threadIdx.x;
+            if (pass == 0) {
+                unsigned m = 0;
+                for (int d = 0; d < 256; ++d) m += hist[b][d];
+                s_cnt[b] = m;
+                s_rank[b] = m ? (m - 1) / 2 : 0u;
+            }
+            if (s_cnt[b]) {
+                const unsigned r = s_rank[b];
+                unsigned acc = 0;
+                int d = 0;
+                for (; d < 255; ++d) {
+                    if (acc + hist[b][d] > r) break;
+                    acc += hist[b][d];
+                }
+                s_pre[b] |= (unsigned)d << shift;
+                s_msk[b] |= 255u << shift;
+                s_rank[b] = r - acc;
+                if (pass == 3) {
+                    s_eq[b] = hist[b][d];
+                    if (!(s_cnt[b] & 1u) && s_eq[b] - s_rank[b] < 2u) atomicOr(&s_need, 1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (s_need) {  // least key above the lower middle value, for the classes that need it
+        for (int q = threadIdx.x; q < N; q += MB) {
+            const int b = assign[q];
+            const unsigned key = key_of(v[q]);
+            const bool take = !(s_cnt[b] & 1u) && s_eq[b] - s_rank[b] < 2u && key > s_pre[b];
+            const unsigned act = __activemask();
+            const unsigned grp = __match_any_sync(act, take ? (unsigned)b : 0xffffffffu);
+            const unsigned mn = __reduce_min_sync(grp, take ? key : 0xffffffffu);
+            if (take && (int)lane == __ffs(grp) - 1) atomicMin(&s_min[b], mn);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < n && s_cnt[threadIdx.x]) {
+        const int b = threadIdx.x;
+        const float lo = float_of(s_pre[b]);
+        float out = lo;
+        if (!(s_cnt[b] & 1u)) {
+            const float hi = s_eq[b] - s_rank[b] >= 2u ? lo : float_of(s_min[b]);
+            out = __fmul_rn(0.5f, __fadd_rn(lo, hi));
+        }
+        C[(size_t)b * k + j] = out;
     }
 }
 
@@ -245,7 +311,9 @@ size_t kmeans_scratch_bytes(int n) {
 }
 
 size_t kmedians_scratch_bytes(long long N, int n) {
-    return sizeof(int32_t) * ((size_t)N + (size_t)n + 1) + 2 * sizeof(unsigned) * (size_t)n + 256;
+    (void)N;
+    (void)n;
+    return 256;  // the assignment buffer is the caller's work_assign
 }
 
 cudaError_t launch_kmeans(const KmeansArgs& a, cudaStream_t st) {
@@ -265,24 +333,16 @@ cudaError_t launch_kmeans(const KmeansArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_kmedians(const KmediansArgs& a, cudaStream_t st) {
-    int32_t* members = reinterpret_cast<int32_t*>(a.scratch);
-    int32_t* off = members + a.N;
-    unsigned* counts = reinterpret_cast<unsigned*>(off + a.n + 1);
-    unsigned* cursor = counts + a.n;
     const size_t smem = sizeof(float) * (size_t)a.n * a.k;
     cudaError_t e = set_smem((const void*)kmedians_assign_kernel, smem);
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned) * a.n, st)) != cudaSuccess) return e;
     kmedians_init_kernel<<<(a.n * a.k + UB - 1) / UB, UB, 0, st>>>(a.V, a.N, a.k, a.init, a.n,
                                                                    a.C);
     const int g = grid_for(a.N, a.n_sm);
     for (int it = 0; it < a.iterations; ++it) {
         kmedians_assign_kernel<<<g, UB, smem, st>>>(a.V, a.N, a.k, a.C, a.n, a.work_assign,
-                                                    counts);
-        class_offsets_kernel<<<1, 32, 0, st>>>(counts, a.n, off, cursor);
-        class_scatter_kernel<<<g, UB, 0, st>>>(a.work_assign, a.N, off, cursor, members);
-        if ((e = launch_group_medians(a.V, a.N, a.k, a.n, off, members, a.C, st)) != cudaSuccess)
-            return e;
+                                                    nullptr);
+        class_median_kernel<<<a.k, MB, 0, st>>>(a.V, a.N, a.k, a.work_assign, a.n, a.C);
     }
     if (a.assign)
         kmedians_assign_kernel<<<g, UB, smem, st>>>(a.V, a.N, a.k, a.C, a.n, a.assign, nullptr);
