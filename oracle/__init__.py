@@ -66,7 +66,7 @@ def _load():
             lib.oracle_tsm.argtypes = [P, P, i]
             lib.oracle_majority.argtypes = [P, i, i, P, P]
             lib.oracle_dist2.argtypes = [i, i, i, P, P, P, i, P]
-            lib.oracle_likelihood.argtypes = [P, i, i, P, P, i, i, P, P, d, d, d, d, i, P, i,
+            lib.oracle_likelihood.argtypes = [P, i, i, P, P, i, i, P, P, d, d, d, d, i, i, P, i,
                                               P, P, P, P]
             for f in ("oracle_codes", "oracle_patches", "oracle_tsm", "oracle_majority",
                       "oracle_dist2", "oracle_likelihood"):
@@ -156,8 +156,10 @@ def dist2(H, W, label_off, sample_pix, pix=None):
 
 
 def likelihood(image, bits_px, bits_smp, k, label_off, sample_pix, sigma_c2=1.3, alpha=1.3,
-               d_min=1.0, kappa_beta=1.0, mode=0, pix=None, want_dist2=False):
+               d_min=1.0, kappa_beta=1.0, mode=0, pix=None, want_dist2=False, rho_variance=0):
     """Log-likelihoods L (n_labels, cnt), data term -L and label posteriors.
+    rho_variance = 1 reads rho as the location kernel's variance (Sec. 3.1),
+    0 as its standard deviation.
 
     Returns dict with 'L', 'neglog', 'post' (float64) and optionally 'dist2'.
     """
@@ -178,7 +180,8 @@ def likelihood(image, bits_px, bits_smp, k, label_off, sample_pix, sigma_c2=1.3,
     d2 = np.zeros((nl, cnt), np.int64) if want_dist2 else None
     rc = _load().oracle_likelihood(_p(image), H, W, _p(bits_px), _p(bits_smp), k, nl,
                                    _p(label_off), _p(sample_pix), float(sigma_c2), float(alpha),
-                                   float(d_min), float(kappa_beta), int(mode), _p(pix), cnt,
+                                   float(d_min), float(kappa_beta), int(mode),
+                                   int(rho_variance), _p(pix), cnt,
                                    _p(L), _p(neg), _p(post), _p(d2))
     if rc:
         raise ValueError("oracle_likelihood: invalid arguments")
@@ -240,7 +243,8 @@ def data_term(problem, pix=None, mode=None, want_dist2=False):
                             pix=problem.sample_pix, want_codes=smooth)
     out = likelihood(problem.image, bits_px, bits_smp, k, problem.label_off, problem.sample_pix,
                      prm.sigma_c2, prm.alpha, prm.d_min, prm.kappa_beta, mode, pix=pix,
-                     want_dist2=want_dist2 or smooth)
+                     want_dist2=want_dist2 or smooth,
+                     rho_variance=int(getattr(prm, "rho_variance", 0)))
     if smooth:
         # Sec. 3.1 with Eq. (map_tsm), (approx_cosupp), (post_text): the Parzen
         # sum times the softmax texture posterior on smooth co-supports,

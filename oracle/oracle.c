@@ -25,7 +25,9 @@
  *   v = w . g, mu = sum(v)/n, c = v - mu, s = c / sqrt(sum c^2), s = 0 when
  *   sum c^2 == 0; all sums run in index order; the co-support test is
  *   |a_j| <= tau (inclusive); rho = alpha * max(sqrt(D), d_min) is a standard
- *   deviation, k_rho(u) = exp(-|u|^2 / (2 rho^2)) / (2 pi rho^2); the colour
+ *   deviation, k_rho(u) = exp(-|u|^2 / (2 rho^2)) / (2 pi rho^2), or, with
+ *   rho_variance = 1, the variance, k_rho(u) = exp(-|u|^2 / (2 rho)) / (2 pi rho)
+ *   (Sec. 3.1 calls rho the variance but defines it as a length); the colour
  *   kernel has variance sigma_c2 per channel over d = 3 channels; beta =
  *   kappa_beta * rho; in the per-sample form each sample also carries the
  *   factor exp(-TSM(b_x, b_j) / beta); in the factorised form the texture
@@ -186,12 +188,14 @@ int oracle_dist2(int H, int W, int n_labels, const int32_t* label_off, const int
 int oracle_likelihood(const float* img, int H, int W, const uint32_t* bits_px,
                       const uint32_t* bits_smp, int k, int n_labels, const int32_t* label_off,
                       const int32_t* sample_pix, double sigma_c2, double alpha, double d_min,
-                      double kappa_beta, int mode, const int32_t* pix_list, int n_pix, double* L,
+                      double kappa_beta, int mode, int rho_variance, const int32_t* pix_list,
+                      int n_pix, double* L,
                       double* neglog, double* post, int64_t* dist2_out) {
     int Wk = (k + 31) / 32;
     int count = pix_list ? n_pix : H * W;
     if (n_labels < 1 || k < 1 || sigma_c2 <= 0.0 || alpha <= 0.0 || d_min <= 0.0 ||
-        kappa_beta <= 0.0 || (mode != 0 && mode != 1 && mode != 2))
+        kappa_beta <= 0.0 || (mode != 0 && mode != 1 && mode != 2) ||
+        (rho_variance != 0 && rho_variance != 1))
         return -1;
     for (int i = 0; i < n_labels; ++i)
         if (label_off[i + 1] - label_off[i] < 1) return -1;
@@ -224,6 +228,7 @@ int oracle_likelihood(const float* img, int H, int W, const uint32_t* bits_px,
             double dist = sqrt((double)D);
             double rho = alpha * (dist > d_min ? dist : d_min);
             double beta = kappa_beta * rho;
+            double s2 = rho_variance ? rho : rho * rho; /* variance of the location kernel */
             /* first pass: exponents and their maximum */
             double emax = -INFINITY;
             for (int s = mstart; s < mend; ++s) {
@@ -235,7 +240,7 @@ int oracle_likelihood(const float* img, int H, int W, const uint32_t* bits_px,
                     double d = (double)Ix[c] - (double)Is[c];
                     dc += d * d;
                 }
-                double e = -dloc / (2.0 * rho * rho) - dc / (2.0 * sigma_c2);
+                double e = -dloc / (2.0 * s2) - dc / (2.0 * sigma_c2);
                 if (mode == 0) e -= (double)tsm_hard(bx, bits_smp + (size_t)s * Wk, k) / beta;
                 if (e > emax) emax = e;
             }
@@ -250,12 +255,12 @@ int oracle_likelihood(const float* img, int H, int W, const uint32_t* bits_px,
                     double d = (double)Ix[c] - (double)Is[c];
                     dc += d * d;
                 }
-                double e = -dloc / (2.0 * rho * rho) - dc / (2.0 * sigma_c2);
+                double e = -dloc / (2.0 * s2) - dc / (2.0 * sigma_c2);
                 if (mode == 0) e -= (double)tsm_hard(bx, bits_smp + (size_t)s * Wk, k) / beta;
                 sum += exp(e - emax);
             }
             double m = (double)(mend - mstart);
-            Lq[i] = emax + log(sum) - log(m) - log(2.0 * M_PI * rho * rho) - log_col_norm;
+            Lq[i] = emax + log(sum) - log(m) - log(2.0 * M_PI * s2) - log_col_norm;
             if (mode == 1) Tq[i] = -(double)tsm_hard(bx, rep + (size_t)i * Wk, k) / beta;
         }
         if (mode == 1) {

@@ -230,13 +230,15 @@ def _setup(H=14, W=18, nl=2, m=6, p=5, seed=10):
     return pr, bpx, bsm
 
 
-def _kernel_terms(pr, bpx, bsm, q, s, rho, beta, texture=True):
-    """log of one summand via scipy's Gaussian log-densities."""
+def _kernel_terms(pr, bpx, bsm, q, s, rho, beta, texture=True, rho_variance=False):
+    """log of one summand via scipy's Gaussian log-densities (location
+    covariance rho^2 I, or rho I when rho is read as the variance)."""
     W = pr.W
     y, x = divmod(q, W)
     sp = pr.sample_pix[s]
     sy, sx = divmod(int(sp), W)
-    loc = stats.multivariate_normal(mean=[0, 0], cov=rho * rho * np.eye(2)).logpdf([x - sx, y - sy])
+    cov = (rho if rho_variance else rho * rho) * np.eye(2)
+    loc = stats.multivariate_normal(mean=[0, 0], cov=cov).logpdf([x - sx, y - sy])
     Ix = pr.image.reshape(-1, 3)[q].astype(np.float64)
     Is = pr.image.reshape(-1, 3)[sp].astype(np.float64)
     col = stats.multivariate_normal(mean=[0, 0, 0], cov=1.3 * np.eye(3)).logpdf(Ix - Is)
@@ -285,6 +287,39 @@ def test_parzen_sum_scipy():
                      for s in range(pr.label_off[i], pr.label_off[i + 1])]
             expect = special.logsumexp(terms) - math.log(len(terms))
             assert abs(out["L"][i, q] - expect) < 1e-10
+
+
+def test_rho_variance_reading_scipy():
+    """rho read as the location kernel's variance (Sec. 3.1 names it so):
+    the Parzen sum against scipy with covariance rho I; beta = kappa_beta rho
+    unchanged. A dropped switch (rho^2 kept in the exponent or in the
+    normaliser) fails here."""
+    pr, bpx, bsm = _setup(m=4, seed=17)
+    out = oracle.likelihood(pr.image, bpx, bsm, pr.k, pr.label_off, pr.sample_pix,
+                            rho_variance=1)
+    for q in (2, 61, 140, 251):
+        for i in range(pr.n_labels):
+            rho, beta = _rho_beta(pr, q, i)
+            terms = [_kernel_terms(pr, bpx, bsm, q, s, rho, beta, rho_variance=True)
+                     for s in range(pr.label_off[i], pr.label_off[i + 1])]
+            expect = special.logsumexp(terms) - math.log(len(terms))
+            assert abs(out["L"][i, q] - expect) < 1e-10
+
+
+def test_rho_readings_agree_at_unit_rho():
+    """With rho = 1 at every pixel (alpha = 1 / d_min and every distance
+    below d_min) the two readings are the same kernel, in every mode."""
+    pr, bpx, bsm = _setup(m=3, seed=18)
+    kw = dict(alpha=1e-3, d_min=1e3)
+    for mode in (0, 1):
+        a = oracle.likelihood(pr.image, bpx, bsm, pr.k, pr.label_off, pr.sample_pix, mode=mode,
+                              **kw)
+        b = oracle.likelihood(pr.image, bpx, bsm, pr.k, pr.label_off, pr.sample_pix, mode=mode,
+                              rho_variance=1, **kw)
+        np.testing.assert_allclose(a["L"], b["L"], rtol=0, atol=1e-12)
+    c = oracle.likelihood(pr.image, bpx, bsm, pr.k, pr.label_off, pr.sample_pix, rho_variance=1)
+    d = oracle.likelihood(pr.image, bpx, bsm, pr.k, pr.label_off, pr.sample_pix)
+    assert np.abs(c["L"] - d["L"]).max() > 1e-3  # and differ elsewhere
 
 
 def test_constant_image_is_plain_kde():
