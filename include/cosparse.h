@@ -95,6 +95,16 @@ typedef struct cs_ctx cs_ctx;
  *              are FP32 dot products of the FP32-normalised patch; a patch
  *              whose centred norm is within the FP32 rounding bound of zero
  *              is taken as flat (every code 0).
+ *   rho_variance how rho_i(x) enters the location kernel k_rho (Sec. 3.1
+ *              calls rho the kernel's variance but defines it as a length):
+ *              0 (default) rho is the standard deviation,
+ *              k_rho(u) = exp(-|u|^2 / (2 rho^2)) / (2 pi rho^2);
+ *              1 rho is the variance, k_rho(u) = exp(-|u|^2 / (2 rho)) / (2 pi rho).
+ *              beta = kappa_beta rho either way. Every likelihood form.
+ *   patch_order order of the patch steps (Sec. 3.1 masks "prior to
+ *              normalization"): 0 (default) mask, centre, normalise;
+ *              1 centre, mask, centre again, normalise (not built:
+ *              CS_ERR_UNSUPPORTED).
  */
 typedef struct {
     int32_t p;
@@ -108,6 +118,8 @@ typedef struct {
     double kappa_beta;
     double l_tol;
     double iota_sigma;
+    int32_t rho_variance;
+    int32_t patch_order;
 } cs_params;
 
 void cs_params_default(cs_params* out);

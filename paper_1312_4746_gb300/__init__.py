@@ -100,6 +100,8 @@ class Params(ctypes.Structure):
         ("kappa_beta", ctypes.c_double),
         ("l_tol", ctypes.c_double),
         ("iota_sigma", ctypes.c_double),
+        ("rho_variance", ctypes.c_int32),
+        ("patch_order", ctypes.c_int32),
     ]
 
     @classmethod
@@ -115,7 +117,8 @@ class Params(ctypes.Structure):
         """From a ``synth.Params`` dataclass."""
         p = cls.default(p=sp.p, mode=sp.mode, tau=sp.tau, sigma_c2=sp.sigma_c2, alpha=sp.alpha,
                         d_min=sp.d_min, kappa_beta=sp.kappa_beta,
-                        iota_sigma=getattr(sp, "iota_sigma", 0.01))
+                        iota_sigma=getattr(sp, "iota_sigma", 0.01),
+                        rho_variance=int(getattr(sp, "rho_variance", 0)))
         for k, v in kw.items():
             setattr(p, k, v)
         return p

@@ -126,6 +126,8 @@ void cs_params_default(cs_params* out) {
     out->kappa_beta = 1.0;
     out->l_tol = 1e-3;
     out->iota_sigma = 0.01;
+    out->rho_variance = 0;
+    out->patch_order = 0;
 }
 
 cs_status cs_create(cs_ctx** out, int device) {
@@ -435,6 +437,10 @@ cs_status cs_check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm) {
         return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "%s: patch side %d not in 3..9", fn, prm->p);
     if (!(prm->tau >= 0.0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: tau must be >= 0", fn);
+    if (prm->patch_order != 0)
+        return cs_set_error(ctx, prm->patch_order == 1 ? CS_ERR_UNSUPPORTED : CS_ERR_INVALID_ARG,
+                            "%s: patch_order %d (only 0, mask before centring, is built)", fn,
+                            prm->patch_order);
     if (prm->codes_form != CS_CODES_AUTO && prm->codes_form != CS_CODES_FP32 &&
         prm->codes_form != CS_CODES_TC)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown codes_form %d", fn,
@@ -477,6 +483,8 @@ cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int
                             "%s: sigma_c2, alpha, d_min and kappa_beta must be > 0", fn);
     if (!(prm->l_tol >= 0.0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: l_tol must be >= 0", fn);
+    if (prm->rho_variance != 0 && prm->rho_variance != 1)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: rho_variance must be 0 or 1", fn);
     if (prm->mode == CS_MODE_SMOOTH) {
         if (!allow_smooth)
             return cs_set_error(ctx, CS_ERR_UNSUPPORTED,
@@ -597,6 +605,7 @@ SumArgs cs_sum_args(const LikPlan& L, const float* img, const uint32_t* bitmask,
     a.kappa_beta = (float)prm->kappa_beta;
     a.sigma_c2 = (float)prm->sigma_c2;
     a.mode = prm->mode;
+    a.rho_var = prm->rho_variance != 0;
     a.neglog = neglog;
     a.post = post;
     return a;
@@ -626,6 +635,7 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
     T.d_min = (float)prm->d_min;
     T.kappa_beta = (float)prm->kappa_beta;
     T.sigma_c2 = (float)prm->sigma_c2;
+    T.rho_var = prm->rho_variance != 0;
     T.neglog = neglog;
     T.post = post;
     T.d_err = ctx->d_err;

@@ -164,7 +164,8 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
                       b->fb_list,
                       b->fb_count,
                       b->total_pixels,
-                      (float)b->prm.l_tol};
+                      (float)b->prm.l_tol,
+                      b->prm.rho_variance != 0};
         e = launch_tc_sum(b->descs, (int)b->order.size(), b->n_items, p, st);
     }
     return e;

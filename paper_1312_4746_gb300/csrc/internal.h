@@ -266,6 +266,7 @@ struct SumArgs {
     float alpha, d_min, kappa_beta;
     float sigma_c2;
     int mode;
+    bool rho_var;  // rho is the location kernel's variance (else its standard deviation)
     float* neglog;
     float* post;
     // optional pixel list (device), its length (device) and capacity; with
@@ -353,6 +354,7 @@ struct TcSumParams {
     int* fb_count;
     int fb_cap;
     float l_tol;  // relative tolerance on L of the a-priori row bound (0: off)
+    bool rho_var;  // rho is the location kernel's variance (else its standard deviation)
 };
 struct TcLaunch {
     const float* img;
@@ -370,6 +372,7 @@ struct TcLaunch {
     int n_chunks;  // Morton-sort chunks (4096 samples) over all labels
     const int32_t* dist2;
     float alpha, d_min, kappa_beta, sigma_c2;
+    bool rho_var;
     float* neglog;
     float* post;
     int* d_err;
@@ -453,6 +456,7 @@ struct SurrogateEvalArgs {
     const uint32_t* rep;
     int Wk, mode;
     float alpha, d_min, kappa_beta, sigma_c2, margin, eps;
+    bool rho_var;
     float* neglog;
     float* post;
     int32_t* fb_list;

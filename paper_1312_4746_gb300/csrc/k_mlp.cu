@@ -16,7 +16,8 @@
 //   gradient vector with atomics (loss = mean (z - t)^2 / 2 over batch and labels).
 // adam_kernel: bias-corrected Adam on the fp32 masters, clears the gradient.
 // mlp_eval_kernel: forward pass per pixel from raw features, then
-//   L_i = sd_t,i z_i + mu_t,i - log m_i - log(2 pi rho_i^2) - 1.5 log(2 pi sigma_c2)
+//   L_i = sd_t,i z_i + mu_t,i - log m_i - log(2 pi s2_i) - 1.5 log(2 pi sigma_c2)
+//   (s2_i = rho_i^2, or rho_i when rho is read as the location variance)
 //   (+ the factorised texture log-posterior), posteriors, and the fallback
 //   decision (top-2 posterior margin below `margin`, or top-2 log-likelihood
 //   gap below the calibrated `gap_min`): such pixels are appended to a list
@@ -387,8 +388,8 @@ __global__ void __launch_bounds__(BS) surrogate_eval_kernel(
     const float* __restrict__ eta, const float* __restrict__ img, const float* __restrict__ lead16,
     int H, int W, const int32_t* __restrict__ dist2, const int32_t* __restrict__ label_off,
     const uint32_t* __restrict__ bitmask, const uint32_t* __restrict__ rep, int Wk, int mode,
-    float alpha, float d_min, float kappa_beta, float sigma_c2, float margin, float eps,
-    float* __restrict__ neglog, float* __restrict__ post, int32_t* __restrict__ fb_list,
+    float alpha, float d_min, float kappa_beta, float sigma_c2, bool rho_var, float margin,
+    float eps, float* __restrict__ neglog, float* __restrict__ post, int32_t* __restrict__ fb_list,
     int* __restrict__ fb_count) {
     extern __shared__ float smem[];
     const int np = off_b4(n) + n;
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(BS) surrogate_eval_kernel(
         const float rho = alpha * fmaxf(sqrtf((float)dist2[(size_t)j * P + q]), d_min);
         const float T = z[j] * stats[2 * NIN + n + j] + stats[2 * NIN + j];
         z[j] = T - logf((float)(label_off[j + 1] - label_off[j])) -
-               logf(6.283185307179586f * rho * rho) - log_col_norm;
+               logf(6.283185307179586f * (rho_var ? rho : rho * rho)) - log_col_norm;
         if (mode == CS_MODE_FACTORISED) {
             int h = 0;
             for (int w = 0; w < Wk; ++w) h += __popc(bx[w & 7] ^ rep[j * Wk + w]);
@@ -511,7 +512,7 @@ cudaError_t launch_surrogate_eval(const SurrogateEvalArgs& a, cudaStream_t st) {
     const long long P = (long long)a.H * a.W;
     surrogate_eval_kernel<<<(unsigned)((P + BS - 1) / BS), BS, smem, st>>>(
         a.params, a.n, a.stats, a.eta, a.img, a.lead16, a.H, a.W, a.dist2, a.label_off,
-        a.bitmask, a.rep, a.Wk, a.mode, a.alpha, a.d_min, a.kappa_beta, a.sigma_c2, a.margin,
-        a.eps, a.neglog, a.post, a.fb_list, a.fb_count);
+        a.bitmask, a.rep, a.Wk, a.mode, a.alpha, a.d_min, a.kappa_beta, a.sigma_c2, a.rho_var,
+        a.margin, a.eps, a.neglog, a.post, a.fb_list, a.fb_count);
     return cudaGetLastError();
 }

@@ -36,12 +36,13 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
-// rho, -log2(e)/(2 rho^2), -w log2(e)/beta, and the normalising constant
+// rho, -log2(e)/(2 s2), -w log2(e)/beta and the location variance s2
+// (rho^2, or rho itself when rho is read as the variance)
 __device__ __forceinline__ void label_consts(int D, float alpha, float d_min, float kappa_beta,
-                                             float& rho, float& nA, float& nB) {
+                                             bool rho_var, float& rho, float& nA, float& nB) {
     float d = sqrtf((float)D);
     rho = alpha * fmaxf(d, d_min);
-    nA = -LOG2E / (2.f * rho * rho);
+    nA = -LOG2E / (2.f * (rho_var ? rho : rho * rho));
     nB = -LOG2E / (kappa_beta * rho);
 }
 
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
 #pragma unroll
         for (int u = 0; u < NPIX; ++u) {
             long long q = qpix[u];
-            label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, rho[u],
+            label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, a.rho_var, rho[u],
                          nA[u], nB[u]);
             nB[u] *= wtex;
             M[u] = -INFINITY;
@@ -163,7 +164,8 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
                 a.T_out[(size_t)i * a.list_cap + item[u]] = lse;
                 continue;
             }
-            const float L = lse - logm - logf(6.283185307179586f * rho[u] * rho[u]) - log_col_norm;
+            const float s2 = a.rho_var ? rho[u] : rho[u] * rho[u];
+            const float L = lse - logm - logf(6.283185307179586f * s2) - log_col_norm;
             a.neglog[(size_t)i * P + q] = -L;
         }
     }
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
             float tmax = -INFINITY;
             for (int i = 0; i < a.n_labels; ++i) {
                 float rho, nA, nB;
-                label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, rho, nA, nB);
+                label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, a.rho_var, rho, nA, nB);
                 int h = 0;
 #pragma unroll
                 for (int w = 0; w < WK; ++w) h += __popc(pbits[u][w] ^ a.t.rep[i * WK + w]);
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
             float ts = 0.f;
             for (int i = 0; i < a.n_labels; ++i) {
                 float rho, nA, nB;
-                label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, rho, nA, nB);
+                label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, a.rho_var, rho, nA, nB);
                 int h = 0;
 #pragma unroll
                 for (int w = 0; w < WK; ++w) h += __popc(pbits[u][w] ^ a.t.rep[i * WK + w]);
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(THREADS) sum_plain_kernel(SumArgs a) {
             const float tlse2 = tmax + log2f(ts);
             for (int i = 0; i < a.n_labels; ++i) {
                 float rho, nA, nB;
-                label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, rho, nA, nB);
+                label_consts(a.dist2[(size_t)i * P + q], a.alpha, a.d_min, a.kappa_beta, a.rho_var, rho, nA, nB);
                 int h = 0;
 #pragma unroll
                 for (int w = 0; w < WK; ++w) h += __popc(pbits[u][w] ^ a.t.rep[i * WK + w]);

@@ -75,6 +75,7 @@ struct TcArgs {
     int n_images, n_items;  // work items: (image, pixel tile) pairs
     int k, Wk;
     float alpha, d_min, kappa_beta, sigma_c2;
+    bool rho_var;   // rho is the location kernel's variance (else its standard deviation)
     int* d_err;
     int4* fb_list;  // (image, pixel, flagged-label mask low, high) to recompute
     int* fb_count;
@@ -578,7 +579,8 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
             for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
                 const int D = live ? im.dist2[(size_t)i * P + pix] : 0;
                 const float rho = a.alpha * fmaxf(sqrtf((float)D), a.d_min);
-                const float nA = -LOG2E / (2.f * rho * rho);
+                const float s2 = a.rho_var ? rho : rho * rho;  // location variance
+                const float nA = -LOG2E / (2.f * s2);
                 const float Bt = PERSAMPLE ? LOG2E / (a.kappa_beta * rho) : 1.f;
                 const float g = PERSAMPLE ? (a.kappa_beta * rho) / LOG2E : 1.f;
                 const float R0 = (PERSAMPLE ? -Bt * (float)popx : 0.f) - Cc * I2;
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                     const float tot = Sm + Cm;  // shifted by 2^shift
                     const float lse2 = log2f(tot) - shift;
                     const float Lv = lse2 * LN2 - logf((float)m_i) -
-                                     logf(6.283185307179586f * rho * rho) - log_col_norm;
+                                     logf(6.283185307179586f * s2) - log_col_norm;
                     // below the floor the FP32 terms may have lost mass to
                     // underflow; above the tolerance the bound on the error of
                     // L (log2 units) is too loose: recompute in FP64. Bound:
@@ -794,7 +796,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
 __global__ void __launch_bounds__(128) refine_fp64_kernel(
     const TcImage* __restrict__ images, const int4* __restrict__ list,
     const int* __restrict__ count, int cap, int Wk, double alpha, double d_min, double kappa_beta,
-    double sigma_c2, bool persample, int* __restrict__ d_err) {
+    double sigma_c2, bool persample, bool rho_var, int* __restrict__ d_err) {
     __shared__ double sL[4][CS_MAX_LABELS];
     __shared__ double sT[4][CS_MAX_LABELS];
     int cnt = *count;
@@ -829,7 +831,8 @@ __global__ void __launch_bounds__(128) refine_fp64_kernel(
                 if (lane == 0) sL[wib][i] = -(double)im.neglog[(size_t)i * P + pix];
                 continue;
             }
-            const double c_loc = 0.5 / (rho * rho);
+            const double s2 = rho_var ? rho : rho * rho;  // location variance
+            const double c_loc = 0.5 / s2;
             const double c_tex = persample ? 1.0 / (kappa_beta * rho) : 0.0;
             const int off = im.label_off[i], m = im.label_off[i + 1] - off;
             auto expo = [&](int j) {
@@ -852,7 +855,7 @@ __global__ void __launch_bounds__(128) refine_fp64_kernel(
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             if (lane == 0)
-                sL[wib][i] = mx + log(sum) - log((double)m) - log(PI2 * rho * rho) - col_norm;
+                sL[wib][i] = mx + log(sum) - log((double)m) - log(PI2 * s2) - col_norm;
         }
         __syncwarp();
         if (lane == 0) {
@@ -1075,6 +1078,7 @@ cudaError_t sum(const TcImage* descs, int n_images, int n_items, const TcSumPara
     a.d_min = p.d_min;
     a.kappa_beta = p.kappa_beta;
     a.sigma_c2 = p.sigma_c2;
+    a.rho_var = p.rho_var;
     a.d_err = p.d_err;
     a.fb_list = p.fb_list;
     a.fb_count = p.fb_count;
@@ -1089,7 +1093,7 @@ cudaError_t sum(const TcImage* descs, int n_images, int n_items, const TcSumPara
     sum_tc_kernel<TEX8, KS, PERSAMPLE><<<grid, C::THREADS, C::smem_bytes, st>>>(a);
     refine_fp64_kernel<<<2 * p.n_sm, 128, 0, st>>>(
         descs, p.fb_list, p.fb_count, p.fb_cap, (p.k + 31) / 32, (double)p.alpha, (double)p.d_min,
-        (double)p.kappa_beta, (double)p.sigma_c2, PERSAMPLE, p.d_err);
+        (double)p.kappa_beta, (double)p.sigma_c2, PERSAMPLE, p.rho_var, p.d_err);
     return cudaGetLastError();
 }
 
@@ -1168,6 +1172,6 @@ cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     TcSumParams p{L.k,       L.tex8,  L.persample, L.alpha,      L.d_min, L.kappa_beta,
                   L.sigma_c2, L.d_err, L.n_sm,      L.fb_list,    L.fb_count,
-                  L.H * L.W,  L.l_tol};
+                  L.H * L.W,  L.l_tol, L.rho_var};
     return launch_tc_sum(L.desc, 1, tc_pixel_tiles(L.H, L.W), p, st);
 }

@@ -242,6 +242,7 @@ cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const u
         a.d_min = (float)prm->d_min;
         a.kappa_beta = (float)prm->kappa_beta;
         a.sigma_c2 = (float)prm->sigma_c2;
+        a.rho_var = prm->rho_variance != 0;
         a.margin = (float)margin;
         a.eps = 0.005f;
         a.neglog = neglog;

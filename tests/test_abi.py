@@ -38,7 +38,8 @@ def test_version_and_defaults(L):
     assert p.p == 7 and p.tau == 0.1 and p.sigma_c2 == 1.3 and p.alpha == 1.3
     assert p.d_min == 1.0 and p.kappa_beta == 1.0 and p.mode == 0 and p.precision == 0
     assert p.codes_form == cs.CODES_AUTO and p.l_tol == 1e-3 and p.iota_sigma == 0.01
-    assert ctypes.sizeof(cs.Params) == 4 * 4 + 7 * 8
+    assert p.rho_variance == 0 and p.patch_order == 0
+    assert ctypes.sizeof(cs.Params) == 4 * 4 + 7 * 8 + 2 * 4
     sp = cs.SegParams.default()
     assert ctypes.sizeof(cs.SegParams) == 3 * 8 + 2 * 4
     assert sp.lam == 1.0 and sp.nu == 0.0 and sp.gamma == 5.0 and sp.iterations == 300
