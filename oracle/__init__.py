@@ -61,8 +61,8 @@ def _load():
             lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             i, d = ctypes.c_int, ctypes.c_double
-            lib.oracle_codes.argtypes = [P, i, i, P, i, P, i, d, P, i, P, P]
-            lib.oracle_patches.argtypes = [P, i, i, P, i, P, i, P]
+            lib.oracle_codes.argtypes = [P, i, i, P, i, P, i, d, P, i, P, P, i]
+            lib.oracle_patches.argtypes = [P, i, i, P, i, P, i, P, i]
             lib.oracle_tsm.argtypes = [P, P, i]
             lib.oracle_majority.argtypes = [P, i, i, P, P]
             lib.oracle_dist2.argtypes = [i, i, i, P, P, P, i, P]
@@ -87,22 +87,25 @@ def n_words(k: int) -> int:
     return (k + 31) // 32
 
 
-def patches(image, mask, p, pix=None):
-    """Normalised masked gray patches s_x (Sec. 2, Sec. 3.1), FP64, one row per pixel."""
+def patches(image, mask, p, pix=None, order=0):
+    """Normalised masked gray patches s_x (Sec. 2, Sec. 3.1), FP64, one row per
+    pixel. order 0: mask, centre, normalise; order 1: centre, mask, centre
+    again, normalise."""
     image = _c(image, np.float32)
     mask = _c(mask, np.float32)
     H, W = image.shape[:2]
     pix = None if pix is None else _c(pix, np.int32)
     cnt = H * W if pix is None else len(pix)
     out = np.zeros((cnt, p * p), np.float64)
-    rc = _load().oracle_patches(_p(image), H, W, _p(mask), p, _p(pix), cnt, _p(out))
+    rc = _load().oracle_patches(_p(image), H, W, _p(mask), p, _p(pix), cnt, _p(out), int(order))
     if rc:
         raise ValueError("oracle_patches: invalid arguments")
     return out
 
 
-def codes(image, omega, mask, p, tau, pix=None, want_codes=True):
-    """Codes a = O s (Sec. 2) and co-support bitmasks (Eq. 1 with |a_j| <= tau).
+def codes(image, omega, mask, p, tau, pix=None, want_codes=True, order=0):
+    """Codes a = O s (Sec. 2) and co-support bitmasks (Eq. 1 with |a_j| <= tau)
+    of the patches of ``patches(..., order)``.
 
     Returns (codes (cnt, k) float64 or None, bitmask (cnt, ceil(k/32)) uint32).
     """
@@ -117,7 +120,7 @@ def codes(image, omega, mask, p, tau, pix=None, want_codes=True):
     cod = np.zeros((cnt, k), np.float64) if want_codes else None
     bm = np.zeros((cnt, n_words(k)), np.uint32)
     rc = _load().oracle_codes(_p(image), H, W, _p(omega), k, _p(mask), p, float(tau), _p(pix),
-                              cnt, _p(cod), _p(bm))
+                              cnt, _p(cod), _p(bm), int(order))
     if rc:
         raise ValueError("oracle_codes: invalid arguments")
     return cod, bm
@@ -237,10 +240,11 @@ def data_term(problem, pix=None, mode=None, want_dist2=False):
     mode = prm.mode if mode is None else mode
     k = problem.omega.shape[0]
     smooth = mode == 2
+    order = int(getattr(prm, "patch_order", 0))
     a_px, bits_px = codes(problem.image, problem.omega, problem.mask, p, prm.tau, pix=pix,
-                          want_codes=smooth)
+                          want_codes=smooth, order=order)
     a_smp, bits_smp = codes(problem.image, problem.omega, problem.mask, p, prm.tau,
-                            pix=problem.sample_pix, want_codes=smooth)
+                            pix=problem.sample_pix, want_codes=smooth, order=order)
     out = likelihood(problem.image, bits_px, bits_smp, k, problem.label_off, problem.sample_pix,
                      prm.sigma_c2, prm.alpha, prm.d_min, prm.kappa_beta, mode, pix=pix,
                      want_dist2=want_dist2 or smooth,

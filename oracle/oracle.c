@@ -54,16 +54,25 @@ static double gray_at(const float* img, int W, int y, int x) {
 }
 
 /* Sec. 2 / Sec. 3.1: masked, zero-mean, unit-norm gray patch at (y, x). */
+/* order 0: v = w . g, then centre and normalise (the mask "prior to
+ * normalization" of Sec. 3.1 read literally); order 1: centre g first,
+ * v = w . (g - mean g), then centre again and normalise. */
 static void patch_at(const float* img, int H, int W, int y, int x, const float* mask, int p,
-                     double* s) {
+                     int order, double* s) {
     int r = (p - 1) / 2, n = p * p, t;
-    double mu = 0.0, ss = 0.0, nrm;
+    double mu = 0.0, ss = 0.0, nrm, mg = 0.0;
     for (int dy = 0; dy < p; ++dy)
         for (int dx = 0; dx < p; ++dx) {
             t = dy * p + dx;
-            s[t] = (double)mask[t] *
-                   gray_at(img, W, clampi(y + dy - r, 0, H - 1), clampi(x + dx - r, 0, W - 1));
+            s[t] = gray_at(img, W, clampi(y + dy - r, 0, H - 1), clampi(x + dx - r, 0, W - 1));
         }
+    if (order == 1) {
+        for (t = 0; t < n; ++t) mg += s[t];
+        mg = mg / (double)n;
+        for (t = 0; t < n; ++t) s[t] = (double)mask[t] * (s[t] - mg);
+    } else {
+        for (t = 0; t < n; ++t) s[t] = (double)mask[t] * s[t];
+    }
     for (t = 0; t < n; ++t) mu += s[t];
     mu = mu / (double)n;
     for (t = 0; t < n; ++t) s[t] = s[t] - mu;
@@ -83,8 +92,8 @@ static void patch_at(const float* img, int H, int W, int y, int x, const float* 
  */
 int oracle_codes(const float* img, int H, int W, const float* omega, int k, const float* mask,
                  int p, double tau, const int32_t* pix_list, int n_pix, double* codes,
-                 uint32_t* bitmask) {
-    if (H < 1 || W < 1 || p < 1 || (p & 1) == 0 || k < 1) return -1;
+                 uint32_t* bitmask, int order) {
+    if (H < 1 || W < 1 || p < 1 || (p & 1) == 0 || k < 1 || (order != 0 && order != 1)) return -1;
     int n = p * p, Wk = (k + 31) / 32;
     int count = pix_list ? n_pix : H * W;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -92,7 +101,7 @@ int oracle_codes(const float* img, int H, int W, const float* omega, int k, cons
         int pix = pix_list ? pix_list[q] : q;
         int y = pix / W, x = pix % W;
         double* s = (double*)malloc(sizeof(double) * (size_t)n);
-        patch_at(img, H, W, y, x, mask, p, s);
+        patch_at(img, H, W, y, x, mask, p, order, s);
         if (bitmask) memset(bitmask + (size_t)q * Wk, 0, sizeof(uint32_t) * (size_t)Wk);
         for (int j = 0; j < k; ++j) {
             double a = 0.0;
@@ -107,12 +116,12 @@ int oracle_codes(const float* img, int H, int W, const float* omega, int k, cons
 
 /* Normalised patches themselves (for the pins on Sec. 2's normalisation). */
 int oracle_patches(const float* img, int H, int W, const float* mask, int p,
-                   const int32_t* pix_list, int n_pix, double* out) {
-    if (H < 1 || W < 1 || p < 1 || (p & 1) == 0) return -1;
+                   const int32_t* pix_list, int n_pix, double* out, int order) {
+    if (H < 1 || W < 1 || p < 1 || (p & 1) == 0 || (order != 0 && order != 1)) return -1;
     int n = p * p, count = pix_list ? n_pix : H * W;
     for (int q = 0; q < count; ++q) {
         int pix = pix_list ? pix_list[q] : q;
-        patch_at(img, H, W, pix / W, pix % W, mask, p, out + (size_t)q * n);
+        patch_at(img, H, W, pix / W, pix % W, mask, p, order, out + (size_t)q * n);
     }
     return 0;
 }

@@ -57,6 +57,7 @@ class Params:
     mode: int = 0  # 0 = per-sample texture kernel, 1 = factorised (Eq. joined), 2 = smooth
     iota_sigma: float = 0.01  # Eq. map_tsm's sigma (the paper's value) for the smooth texture
     rho_variance: int = 0  # 1: rho is the location kernel's variance (else its standard deviation)
+    patch_order: int = 0  # 1: centre, mask, centre again, normalise (else mask, centre, normalise)
 
 
 @dataclasses.dataclass

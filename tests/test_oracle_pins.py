@@ -106,6 +106,56 @@ def test_gain_invariance_exact():
     assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
 
 
+def test_centre_first_constant_image_is_flat():
+    """patch_order 1 centres the gray values before the mask: a constant
+    image gives g - mean g = 0 exactly, so s = 0 (where order 0 gives the
+    centred mask), and every code is in the co-support."""
+    p = 7
+    w = synth.make_mask(p)
+    img = np.full((15, 15, 3), 0.5, np.float32)
+    pix = np.array([7 * 15 + 7], np.int32)
+    assert np.all(oracle.patches(img, w, p, pix=pix, order=1) == 0.0)
+    assert np.abs(oracle.patches(img, w, p, pix=pix, order=0)).max() > 0.1
+
+
+def test_centre_first_ramp_closed_form():
+    """Horizontal gray ramp g = c dx + b, symmetric mask w(dy, dx): order 1
+    gives v = w (c (dx - r)), whose mean is zero by the mask's symmetry, so
+    s = w (dx - r) / ||w (dx - r)||, independent of the bias b."""
+    p, r = 5, 2
+    w = synth.make_mask(p).astype(np.float64).reshape(p, p)
+    H, W = 9, 11
+    xs = np.arange(W, dtype=np.float64)
+    img = np.repeat((0.05 * xs + 0.3)[None, :, None], H, axis=0).repeat(3, axis=2)
+    img = img.astype(np.float32)
+    q = 4 * W + 5
+    s = oracle.patches(img, w.reshape(-1).astype(np.float32), p, pix=np.array([q], np.int32),
+                       order=1)[0].reshape(p, p)
+    # the gray value of channel-equal pixels is the value itself (weights sum to 1)
+    dx = np.arange(p, dtype=np.float64)[None, :] - r
+    e = w * dx
+    np.testing.assert_allclose(s, e / np.linalg.norm(e), atol=2e-7)
+    s2 = oracle.patches(img + np.float32(0.25), w.reshape(-1).astype(np.float32), p,
+                        pix=np.array([q], np.int32), order=1)[0].reshape(p, p)
+    np.testing.assert_allclose(s2, s, atol=2e-7)
+    s0 = oracle.patches(img, w.reshape(-1).astype(np.float32), p, pix=np.array([q], np.int32),
+                        order=0)[0].reshape(p, p)
+    assert np.abs(s0 - s).max() > 1e-2  # the literal order differs here
+
+
+def test_orders_agree_for_a_uniform_mask():
+    """With a constant mask, w (g - mean g) already has zero mean and equals
+    w g - mean(w g): both orders give the same patch and codes."""
+    pr = synth.make_problem(16, 18, 2, 8, p=5, seed=19)
+    w = np.full(25, 0.7, np.float32)
+    a0, b0 = oracle.codes(pr.image, pr.omega, w, 5, 0.1, order=0)
+    a1, b1 = oracle.codes(pr.image, pr.omega, w, 5, 0.1, order=1)
+    np.testing.assert_allclose(a1, a0, rtol=0, atol=1e-12)
+    s1 = oracle.patches(pr.image, pr.mask, 5, order=1)
+    np.testing.assert_allclose(s1.sum(1), 0.0, atol=1e-12)
+    np.testing.assert_allclose(np.linalg.norm(s1, axis=1), 1.0, atol=1e-12)
+
+
 def test_flat_window_all_cosupport():
     """An all-zero window has sum c^2 == 0, so s = 0, a = 0 and every j is in
     the co-support (Eq. 1)."""
