@@ -103,8 +103,12 @@ typedef struct cs_ctx cs_ctx;
  *              beta = kappa_beta rho either way. Every likelihood form.
  *   patch_order order of the patch steps (Sec. 3.1 masks "prior to
  *              normalization"): 0 (default) mask, centre, normalise;
- *              1 centre, mask, centre again, normalise (not built:
- *              CS_ERR_UNSUPPORTED).
+ *              1 centre the gray values, mask, centre again, normalise
+ *              (bias-invariant). Order 1 computes every code in double
+ *              precision in the canonical index order (codes_form is
+ *              ignored; the bitmasks are exact, the codes the double values
+ *              rounded to FP32); CS_ERR_UNSUPPORTED in CS_MODE_SMOOTH and
+ *              cs_unsup_data_term, whose patches are mask-first.
  */
 typedef struct {
     int32_t p;

@@ -317,6 +317,8 @@ cs_status cs_unsup_data_term(cs_ctx* ctx, const float* img, int H, int W, const 
     if (!(prm->iota_sigma > 0) || !(prm->sigma_c2 > 0) || !(up->beta > 0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: iota_sigma, sigma_c2 and beta must be > 0",
                             fn);
+    if (prm->patch_order != 0)
+        return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "%s: mask-first patches only", fn);
     const long long P = (long long)H * W;
     UnsupInit ci, ti;
     if (!s) s = unsup_classes(ctx, fn, up->n_colour, up->kmeans_iterations);
@@ -437,10 +439,8 @@ cs_status cs_check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm) {
         return cs_set_error(ctx, CS_ERR_UNSUPPORTED, "%s: patch side %d not in 3..9", fn, prm->p);
     if (!(prm->tau >= 0.0))
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: tau must be >= 0", fn);
-    if (prm->patch_order != 0)
-        return cs_set_error(ctx, prm->patch_order == 1 ? CS_ERR_UNSUPPORTED : CS_ERR_INVALID_ARG,
-                            "%s: patch_order %d (only 0, mask before centring, is built)", fn,
-                            prm->patch_order);
+    if (prm->patch_order != 0 && prm->patch_order != 1)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: patch_order must be 0 or 1", fn);
     if (prm->codes_form != CS_CODES_AUTO && prm->codes_form != CS_CODES_FP32 &&
         prm->codes_form != CS_CODES_TC)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown codes_form %d", fn,
@@ -449,7 +449,7 @@ cs_status cs_check_patch(cs_ctx* ctx, const char* fn, const cs_params* prm) {
 }
 
 bool cs_codes_use_tc(const cs_params* prm, int k) {
-    if (prm->codes_form == CS_CODES_FP32) return false;
+    if (prm->codes_form == CS_CODES_FP32 || prm->patch_order == 1) return false;
     return codes_tc_supported(k, prm->p);
 }
 
@@ -492,6 +492,9 @@ cs_status cs_check_params(cs_ctx* ctx, const char* fn, const cs_params* prm, int
                                 fn);
         if (!(prm->iota_sigma > 0))
             return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: iota_sigma must be > 0", fn);
+        if (prm->patch_order != 0)
+            return cs_set_error(ctx, CS_ERR_UNSUPPORTED,
+                                "%s: the smooth texture mode builds mask-first patches only", fn);
     } else if (prm->mode != CS_MODE_PERSAMPLE && prm->mode != CS_MODE_FACTORISED) {
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown mode %d", fn, prm->mode);
     }
@@ -692,6 +695,7 @@ cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* ome
     const long long P = (long long)H * W;
     CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, codes, lead16, bitmask};
     a.tc = cs_codes_use_tc(prm, k);
+    a.order = prm->patch_order;
     Carve m(nullptr);
     cs_plan_codes(m, a, P, k, !bitmask);
     if ((s = cs_ensure_scratch(ctx, m.off))) return s;
@@ -835,6 +839,7 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     const long long P = (long long)H * W;
     CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, nullptr, nullptr, bitmask};
     a.tc = cs_codes_use_tc(prm, k);
+    a.order = prm->patch_order;
     LikPlan L{};
     cs_lik_plan(L, H, W, k, n_labels, label_off, prm);
     Carve m(nullptr);

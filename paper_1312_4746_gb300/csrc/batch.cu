@@ -338,6 +338,7 @@ static cs_status batch_create(const char* fn, cs_ctx* ctx, const cs_image* image
             m.codes = CodesArgs{m.d.img, m.d.H, m.d.W, omega, k, mask, prm->p, prm->tau,
                                 nullptr, nullptr, m.d.bitmask};
             m.codes.tc = !codes_given && cs_codes_use_tc(prm, k);
+            m.codes.order = prm->patch_order;
             cs_plan_codes(c, m.codes, P, k, !m.d.bitmask);
             m.codes.d_err = ctx->d_err;
             cs_lik_plan(m.L, m.d.H, m.d.W, k, m.d.n_labels, m.off.data(), prm);

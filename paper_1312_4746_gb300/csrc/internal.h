@@ -115,6 +115,9 @@ struct CodesArgs {
     // tensor-core form: operator hi/lo parts in the B-operand layout
     bool tc = false;
     uint8_t* omega_blob = nullptr;
+    // patch order 1 (centre, mask, centre again, normalise): every code in
+    // double precision in the canonical order (no guard list)
+    int order = 0;
 };
 // FP32 CUDA-core codes, or (a.tc) the tcgen05 split-BF16 GEMM; both followed
 // by the canonical FP64 recompute of guarded entries.

@@ -297,6 +297,114 @@ __global__ void __launch_bounds__(128) codes_guard_kernel(
     }
 }
 
+// Patch order 1 (centre the gray values, mask, centre again, normalise):
+// every code of every pixel in double precision, in the canonical index
+// order of the reference, one warp per pixel; the co-support test on the
+// double value is therefore the reference's decision. Codes and lead16 are
+// the double values rounded to FP32.
+template <int P>
+__global__ void __launch_bounds__(128) codes_fp64_kernel(
+    const float* __restrict__ img, int H, int W, const float* __restrict__ omega, int k,
+    const float* __restrict__ mask, double tau, float* __restrict__ codes,
+    float* __restrict__ lead16, uint32_t* __restrict__ bitmask) {
+    constexpr int N = P * P;
+    constexpr int NL = (N + 31) / 32;
+    constexpr int CG = 4;  // codes per lane in flight
+    constexpr int R = (P - 1) / 2;
+    __shared__ double s_buf[4][N];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int Wk = (k + 31) >> 5;
+    double* sb = s_buf[wib];
+    const long long PT = (long long)H * W;
+    for (long long q = (long long)blockIdx.x * 4 + wib; q < PT; q += (long long)gridDim.x * 4) {
+        const int y = (int)(q / W), x = (int)(q % W);
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+            const int t = lane + 32 * u;
+            if (t < N) {
+                const int yy = min(max(y + t / P - R, 0), H - 1);
+                const int xx = min(max(x + t % P - R, 0), W - 1);
+                const float* px = img + ((size_t)yy * W + xx) * 3;
+                sb[t] = __dadd_rn(__dadd_rn(__dmul_rn(0.299, (double)px[0]),
+                                            __dmul_rn(0.587, (double)px[1])),
+                                  __dmul_rn(0.114, (double)px[2]));
+            }
+        }
+        __syncwarp();
+        double mg = 0.0;
+        if (lane == 0) {
+            for (int t = 0; t < N; ++t) mg = __dadd_rn(mg, sb[t]);
+            mg = __ddiv_rn(mg, (double)N);
+        }
+        mg = __shfl_sync(0xffffffffu, mg, 0);
+        double c[NL];
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+            const int t = lane + 32 * u;
+            c[u] = t < N ? __dmul_rn((double)mask[t], __dadd_rn(sb[t], -mg)) : 0.0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+            const int t = lane + 32 * u;
+            if (t < N) sb[t] = c[u];
+        }
+        __syncwarp();
+        double mu = 0.0;
+        if (lane == 0) {
+            for (int t = 0; t < N; ++t) mu = __dadd_rn(mu, sb[t]);
+            mu = __ddiv_rn(mu, (double)N);
+        }
+        mu = __shfl_sync(0xffffffffu, mu, 0);
+#pragma unroll
+        for (int u = 0; u < NL; ++u) c[u] = __dadd_rn(c[u], -mu);
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+            const int t = lane + 32 * u;
+            if (t < N) sb[t] = __dmul_rn(c[u], c[u]);
+        }
+        __syncwarp();
+        double ss = 0.0;
+        if (lane == 0)
+            for (int t = 0; t < N; ++t) ss = __dadd_rn(ss, sb[t]);
+        ss = __shfl_sync(0xffffffffu, ss, 0);
+        const double nrm = ss == 0.0 ? 0.0 : __dsqrt_rn(ss);
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+            const int t = lane + 32 * u;
+            if (t < N) sb[t] = ss == 0.0 ? 0.0 : __ddiv_rn(c[u], nrm);  // s_t
+        }
+        __syncwarp();
+        // codes j = jb + 32 g + lane, index-order sums; one ballot per word
+        for (int jb = 0; jb < k; jb += 32 * CG) {
+            double acc[CG];
+#pragma unroll
+            for (int g = 0; g < CG; ++g) acc[g] = 0.0;
+            for (int t = 0; t < N; ++t) {
+                const double st = sb[t];
+#pragma unroll
+                for (int g = 0; g < CG; ++g) {
+                    const int j = jb + 32 * g + lane;
+                    if (j < k) acc[g] = __dadd_rn(acc[g], __dmul_rn((double)omega[(size_t)j * N + t], st));
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < CG; ++g) {
+                const int j = jb + 32 * g + lane;
+                const bool in = j < k;
+                if (in && codes) codes[q * k + j] = (float)acc[g];
+                if (lead16 && j < 16) lead16[q * 16 + j] = in ? (float)acc[g] : 0.f;
+                const unsigned word = __ballot_sync(0xffffffffu, in && fabs(acc[g]) <= tau);
+                const int w = (jb >> 5) + g;
+                if (bitmask && lane == 0 && w < Wk) bitmask[q * Wk + w] = word;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------- tensor-core codes
 //
 // codes_tc_kernel: the operator product as a tcgen05 GEMM. One CTA per
@@ -964,6 +1072,18 @@ size_t codes_tc_blob_bytes(int k, int p) { return (size_t)3 * ct_ks(p) * ct_np(k
 
 cudaError_t launch_codes(const CodesArgs& a, cudaStream_t st) {
     const int n = a.p * a.p;
+    if (a.order == 1) {
+        const long long PT = (long long)a.H * a.W;
+        const int grid = (int)((PT + 3) / 4 < 152 * 16 ? (PT + 3) / 4 : 152 * 16);
+        switch (a.p) {
+            case 3: codes_fp64_kernel<3><<<grid, 128, 0, st>>>(a.img, a.H, a.W, a.omega, a.k, a.mask, a.tau, a.codes, a.lead16, a.bitmask); break;
+            case 5: codes_fp64_kernel<5><<<grid, 128, 0, st>>>(a.img, a.H, a.W, a.omega, a.k, a.mask, a.tau, a.codes, a.lead16, a.bitmask); break;
+            case 7: codes_fp64_kernel<7><<<grid, 128, 0, st>>>(a.img, a.H, a.W, a.omega, a.k, a.mask, a.tau, a.codes, a.lead16, a.bitmask); break;
+            case 9: codes_fp64_kernel<9><<<grid, 128, 0, st>>>(a.img, a.H, a.W, a.omega, a.k, a.mask, a.tau, a.codes, a.lead16, a.bitmask); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     // (the tensor-core form's operator split also gives the row norms)
     if (!a.tc)
         rownorm_kernel<<<(a.k + 127) / 128, 128, 0, st>>>(a.omega, a.k, n, a.rownorm, a.guard_count);

@@ -98,6 +98,7 @@ extern "C" cs_status cs_codes_noalloc(const float* img, int H, int W, const floa
     cudaError_t e = cudaMemsetAsync(dev_status, 0, 2 * sizeof(int32_t), st);
     if (e == cudaSuccess) {
         CodesArgs a{img, H, W, omega, k, mask, prm->p, prm->tau, codes, lead16, bitmask};
+        a.order = prm->patch_order;
         a.rownorm = reinterpret_cast<float*>(scratch + OFF_ROWNORM);
         a.guard_count = reinterpret_cast<int*>(scratch + OFF_COUNT);
         a.guard = reinterpret_cast<int2*>(scratch + OFF_GUARD);

@@ -113,5 +113,8 @@ def test_switch_validation(env):
         ctx.data_term(*args, cs.Params.from_synth(pr.params, rho_variance=2))
     assert ei.value.status == cs.CS_ERR_INVALID_ARG
     with pytest.raises(cs.CsError) as ei:
-        ctx.data_term(*args, cs.Params.from_synth(pr.params, patch_order=1))
+        ctx.data_term(*args, cs.Params.from_synth(pr.params, patch_order=2))
+    assert ei.value.status == cs.CS_ERR_INVALID_ARG
+    with pytest.raises(cs.CsError) as ei:  # the smooth mode builds mask-first patches only
+        ctx.data_term(*args, cs.Params.from_synth(pr.params, patch_order=1, mode=2))
     assert ei.value.status == cs.CS_ERR_UNSUPPORTED
