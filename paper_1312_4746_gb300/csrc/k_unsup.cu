@@ -13,6 +13,8 @@
 // division, one rounding to FP32. A k-medians centre is the elementwise
 // median by radix selection, all classes of a code in one pass over the
 // points. A class without members keeps its centre.
+#include <cooperative_groups.h>
+
 #include <cstdint>
 
 #include "internal.h"
@@ -147,92 +149,136 @@ __device__ __forceinline__ float float_of(unsigned k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// One block per code j: the elementwise median of every class over the
-// points assigned to it, by radix selection (four 8-bit passes) on all
-// classes at once. Each pass reads row j of V and the assignment once,
-// coalesced; histogram updates are aggregated per (class, digit) within a
-// warp. For an even count the upper middle value is the lower one when that
-// key occurs at least twice more from its rank on, else the least key above
-// it (one more pass). Classes without points keep their centre.
-__global__ void __launch_bounds__(MB) class_median_kernel(const float* __restrict__ V, int N,
-                                                          int k, const int32_t* __restrict__ assign,
-                                                          int n, float* __restrict__ C) {
+// One cluster of MC blocks per code j: the elementwise median of every class
+// over the points assigned to it, by radix selection (four 8-bit passes) on
+// all classes at once. Each block histograms its slice of the points (row j
+// of V and the assignment, coalesced; updates aggregated per (class, digit)
+// within a warp); block 0 of the cluster merges the slices' histograms
+// through distributed shared memory, chooses each class's digit and the
+// other blocks copy its choice. For an even count the upper middle value is
+// the lower one when that key occurs at least twice more from its rank on,
+// else the least key above it (one more pass, merged the same way). Classes
+// without points keep their centre. The cluster barriers are the hardware's.
+constexpr int MC = 4;  // blocks per code
+
+struct MedState {
+    unsigned pre[CS_MAX_CLASSES], msk[CS_MAX_CLASSES], rank[CS_MAX_CLASSES];
+    unsigned cnt[CS_MAX_CLASSES], eq[CS_MAX_CLASSES], need;
+};
+
+__global__ void __cluster_dims__(MC, 1, 1) __launch_bounds__(MB)
+    class_median_kernel(const float* __restrict__ V, int N, int k,
+                        const int32_t* __restrict__ assign, int n, float* __restrict__ C) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
     __shared__ unsigned hist[CS_MAX_CLASSES][256];
-    __shared__ unsigned s_pre[CS_MAX_CLASSES], s_msk[CS_MAX_CLASSES], s_rank[CS_MAX_CLASSES];
-    __shared__ unsigned s_cnt[CS_MAX_CLASSES], s_eq[CS_MAX_CLASSES], s_min[CS_MAX_CLASSES];
-    __shared__ int s_need;
-    const int j = blockIdx.x;
+    __shared__ unsigned merged[CS_MAX_CLASSES][256];
+    __shared__ unsigned s_min[CS_MAX_CLASSES];
+    __shared__ MedState st;
+    const int rank = (int)cluster.block_rank();
+    const int j = blockIdx.x / MC;
     const unsigned lane = threadIdx.x & 31u;
     const float* v = V + (size_t)j * N;
+    const int chunk = (N + MC - 1) / MC;
+    const int q0 = min(rank * chunk, N), q1 = min(q0 + chunk, N);
     if (threadIdx.x < CS_MAX_CLASSES) {
-        s_pre[threadIdx.x] = s_msk[threadIdx.x] = s_cnt[threadIdx.x] = s_eq[threadIdx.x] = 0u;
-        s_rank[threadIdx.x] = 0u;
+        st.pre[threadIdx.x] = st.msk[threadIdx.x] = st.rank[threadIdx.x] = 0u;
+        st.cnt[threadIdx.x] = st.eq[threadIdx.x] = 0u;
         s_min[threadIdx.x] = 0xffffffffu;
     }
-    if (threadIdx.x == 0) s_need = 0;
+    if (threadIdx.x == 0) st.need = 0u;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         for (int t = threadIdx.x; t < n * 256; t += MB) hist[t >> 8][t & 255] = 0u;
         __syncthreads();
-        for (int q = threadIdx.x; q < N; q += MB) {
+        for (int q = q0 + threadIdx.x; q < q1; q += MB) {
             const int b = assign[q];
             const unsigned key = key_of(v[q]);
-            const bool take = (key & s_msk[b]) == s_pre[b];
+            const bool take = (key & st.msk[b]) == st.pre[b];
             const unsigned dig = (key >> shift) & 255u;
             const unsigned grp =
                 __match_any_sync(__activemask(), take ? ((unsigned)b << 8 | dig) : 0xffffffffu);
             if (take && (int)lane == __ffs(grp) - 1) atomicAdd(&hist[b][dig], (unsigned)__popc(grp));
         }
-        __syncthreads();
-        if (threadIdx.x < n) {
-            const int b = threadIdx.x;
-            if (pass == 0) {
+        cluster.sync();  // every slice's histogram is complete
+        if (rank == 0) {
+            for (int t = threadIdx.x; t < n * 256; t += MB) {
                 unsigned m = 0;
-                for (int d = 0; d < 256; ++d) m += hist[b][d];
-                s_cnt[b] = m;
-                s_rank[b] = m ? (m - 1) / 2 : 0u;
+                for (int r = 0; r < MC; ++r) m += cluster.map_shared_rank(&hist[0][0], r)[t];
+                merged[t >> 8][t & 255] = m;
             }
-            if (s_cnt[b]) {
-                const unsigned r = s_rank[b];
-                unsigned acc = 0;
-                int d = 0;
-                for (; d < 255; ++d) {
-                    if (acc + hist[b][d] > r) break;
-                    acc += hist[b][d];
+            __syncthreads();
+            if (threadIdx.x < n) {
+                const int b = threadIdx.x;
+                if (pass == 0) {
+                    unsigned m = 0;
+                    for (int d = 0; d < 256; ++d) m += merged[b][d];
+                    st.cnt[b] = m;
+                    st.rank[b] = m ? (m - 1) / 2 : 0u;
                 }
-                s_pre[b] |= (unsigned)d << shift;
-                s_msk[b] |= 255u << shift;
-                s_rank[b] = r - acc;
-                if (pass == 3) {
-                    s_eq[b] = hist[b][d];
-                    if (!(s_cnt[b] & 1u) && s_eq[b] - s_rank[b] < 2u) atomicOr(&s_need, 1);
+                if (st.cnt[b]) {
+                    const unsigned r = st.rank[b];
+                    unsigned acc = 0;
+                    int d = 0;
+                    for (; d < 255; ++d) {
+                        if (acc + merged[b][d] > r) break;
+                        acc += merged[b][d];
+                    }
+                    st.pre[b] |= (unsigned)d << shift;
+                    st.msk[b] |= 255u << shift;
+                    st.rank[b] = r - acc;
+                    if (pass == 3) {
+                        st.eq[b] = merged[b][d];
+                        if (!(st.cnt[b] & 1u) && st.eq[b] - st.rank[b] < 2u) atomicOr(&st.need, 1u);
+                    }
                 }
             }
         }
+        cluster.sync();  // block 0's choice is made
+        if (rank != 0) {
+            const MedState* s0 = cluster.map_shared_rank(&st, 0);
+            if (threadIdx.x < CS_MAX_CLASSES) {
+                const int b = threadIdx.x;
+                st.pre[b] = s0->pre[b];
+                st.msk[b] = s0->msk[b];
+                st.rank[b] = s0->rank[b];
+                st.cnt[b] = s0->cnt[b];
+                st.eq[b] = s0->eq[b];
+            }
+            if (threadIdx.x == 0) st.need = s0->need;
+        }
         __syncthreads();
     }
-    if (s_need) {  // least key above the lower middle value, for the classes that need it
-        for (int q = threadIdx.x; q < N; q += MB) {
+    // block 0 reads the other blocks' minima below: all blocks take part in
+    // the same cluster barriers whether or not a class needs the pass
+    if (st.need) {  // least key above the lower middle value, for the classes that need it
+        for (int q = q0 + threadIdx.x; q < q1; q += MB) {
             const int b = assign[q];
             const unsigned key = key_of(v[q]);
-            const bool take = !(s_cnt[b] & 1u) && s_eq[b] - s_rank[b] < 2u && key > s_pre[b];
+            const bool take = !(st.cnt[b] & 1u) && st.eq[b] - st.rank[b] < 2u && key > st.pre[b];
             const unsigned act = __activemask();
             const unsigned grp = __match_any_sync(act, take ? (unsigned)b : 0xffffffffu);
             const unsigned mn = __reduce_min_sync(grp, take ? key : 0xffffffffu);
             if (take && (int)lane == __ffs(grp) - 1) atomicMin(&s_min[b], mn);
         }
-        __syncthreads();
     }
-    if (threadIdx.x < n && s_cnt[threadIdx.x]) {
+    cluster.sync();  // every slice's minima are in place
+    if (rank == 0 && threadIdx.x < n && st.cnt[threadIdx.x]) {
         const int b = threadIdx.x;
-        const float lo = float_of(s_pre[b]);
+        const float lo = float_of(st.pre[b]);
         float out = lo;
-        if (!(s_cnt[b] & 1u)) {
-            const float hi = s_eq[b] - s_rank[b] >= 2u ? lo : float_of(s_min[b]);
+        if (!(st.cnt[b] & 1u)) {
+            float hi = lo;
+            if (st.eq[b] - st.rank[b] < 2u) {
+                unsigned m = 0xffffffffu;
+                for (int r = 0; r < MC; ++r) m = min(m, cluster.map_shared_rank(&s_min[0], r)[b]);
+                hi = float_of(m);
+            }
             out = __fmul_rn(0.5f, __fadd_rn(lo, hi));
         }
         C[(size_t)b * k + j] = out;
     }
+    cluster.sync();  // no block exits while block 0 may still read its shared memory
 }
 
 // Last step: colour and texture assignments to the final centres and the
@@ -342,7 +388,7 @@ cudaError_t launch_kmedians(const KmediansArgs& a, cudaStream_t st) {
     for (int it = 0; it < a.iterations; ++it) {
         kmedians_assign_kernel<<<g, UB, smem, st>>>(a.V, a.N, a.k, a.C, a.n, a.work_assign,
                                                     nullptr);
-        class_median_kernel<<<a.k, MB, 0, st>>>(a.V, a.N, a.k, a.work_assign, a.n, a.C);
+        class_median_kernel<<<a.k * MC, MB, 0, st>>>(a.V, a.N, a.k, a.work_assign, a.n, a.C);
     }
     if (a.assign)
         kmedians_assign_kernel<<<g, UB, smem, st>>>(a.V, a.N, a.k, a.C, a.n, a.assign, nullptr);
