@@ -278,14 +278,9 @@ cs_status cs_kmedians(cs_ctx* ctx, const float* V, int N, int k, int n_classes,
     if (!s) s = unsup_init(ctx, fn, init, n_classes, N, &in);
     if (s) return s;
     DeviceGuard g(ctx->device);
-    Carve m(nullptr);
-    m.take<char>(kmedians_scratch_bytes(N, n_classes));
-    m.take<int32_t>(N);
-    if ((s = cs_ensure_scratch(ctx, m.off))) return s;
-    Carve c(ctx->scratch);
-    void* ks = c.take<char>(kmedians_scratch_bytes(N, n_classes));
-    int32_t* work = assign ? assign : c.take<int32_t>(N);
-    KmediansArgs a{V, N, k, n_classes, in, iterations, centres, assign, work, ks, ctx->n_sm};
+    if (!assign && (s = cs_ensure_scratch(ctx, sizeof(int32_t) * (size_t)N))) return s;
+    int32_t* work = assign ? assign : reinterpret_cast<int32_t*>(ctx->scratch);
+    KmediansArgs a{V, N, k, n_classes, in, iterations, centres, assign, work, ctx->n_sm};
     cudaError_t e = launch_kmedians(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return CS_OK;
@@ -331,23 +326,21 @@ cs_status cs_unsup_data_term(cs_ctx* ctx, const float* img, int H, int W, const 
                             up->n_colour, up->n_texture, CS_MAX_LABELS);
     DeviceGuard g(ctx->device);
     const int nc = up->n_colour, nt = up->n_texture;
-    auto carve = [&](Carve& c, float** iota, float** cc, float** tc, void** km, void** kd,
-                     int32_t** work) {
+    auto carve = [&](Carve& c, float** iota, float** cc, float** tc, void** km, int32_t** work) {
         *iota = c.take<float>((size_t)k * P);
         *cc = colour_centres ? colour_centres : c.take<float>(3 * (size_t)nc);
         *tc = texture_centres ? texture_centres : c.take<float>((size_t)nt * k);
         *km = c.take<char>(kmeans_scratch_bytes(nc));
-        *kd = c.take<char>(kmedians_scratch_bytes(P, nt));
         *work = texture_assign ? texture_assign : c.take<int32_t>(P);
     };
     float *iota, *cc, *tc;
-    void *km, *kd;
+    void* km;
     int32_t* work;
     Carve m(nullptr);
-    carve(m, &iota, &cc, &tc, &km, &kd, &work);
+    carve(m, &iota, &cc, &tc, &km, &work);
     if ((s = cs_ensure_scratch(ctx, m.off))) return s;
     Carve c(ctx->scratch);
-    carve(c, &iota, &cc, &tc, &km, &kd, &work);
+    carve(c, &iota, &cc, &tc, &km, &work);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = launch_iota_pixels(img, H, W, omega, k, prm->p, mask, (float)prm->iota_sigma,
                                        iota, st);
@@ -356,7 +349,7 @@ cs_status cs_unsup_data_term(cs_ctx* ctx, const float* img, int H, int W, const 
         e = launch_kmeans(a, st);
     }
     if (e == cudaSuccess) {
-        KmediansArgs a{iota, (int)P, k, nt, ti, up->kmedians_iterations, tc, nullptr, work, kd,
+        KmediansArgs a{iota, (int)P, k, nt, ti, up->kmedians_iterations, tc, nullptr, work,
                        ctx->n_sm};
         e = launch_kmedians(a, st);
     }

@@ -206,7 +206,6 @@ struct KmediansArgs {
     float* C;              // out: n x k
     int32_t* assign;       // out (optional): N
     int32_t* work_assign;  // N (may equal assign)
-    void* scratch;         // kmedians_scratch_bytes(N, n) (unused at present)
     int n_sm;
 };
 struct UnsupFinalArgs {
@@ -225,7 +224,6 @@ struct UnsupFinalArgs {
     int n_sm;
 };
 size_t kmeans_scratch_bytes(int n);
-size_t kmedians_scratch_bytes(long long N, int n);
 cudaError_t launch_kmeans(const KmeansArgs& a, cudaStream_t st);
 cudaError_t launch_kmedians(const KmediansArgs& a, cudaStream_t st);
 cudaError_t launch_unsup_final(const UnsupFinalArgs& a, cudaStream_t st);

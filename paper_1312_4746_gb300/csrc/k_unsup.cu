@@ -118,11 +118,9 @@ __device__ __forceinline__ void l1_all(const float* __restrict__ V, int N, int k
 
 __global__ void __launch_bounds__(UB) kmedians_assign_kernel(
     const float* __restrict__ V, int N, int k, const float* __restrict__ Cg, int n,
-    int32_t* __restrict__ assign, unsigned* __restrict__ counts) {
+    int32_t* __restrict__ assign) {
     extern __shared__ float C[];  // n x k
-    __shared__ unsigned s_cnt[CS_MAX_CLASSES];
     for (int t = threadIdx.x; t < n * k; t += UB) C[t] = Cg[t];
-    for (int t = threadIdx.x; t < n; t += UB) s_cnt[t] = 0u;
     __syncthreads();
     for (int q = blockIdx.x * UB + threadIdx.x; q < N; q += gridDim.x * UB) {
         float d[CS_MAX_CLASSES];
@@ -132,12 +130,7 @@ __global__ void __launch_bounds__(UB) kmedians_assign_kernel(
         for (int b = 1; b < CS_MAX_CLASSES; ++b)
             if (b < n && d[b] < d[best]) best = b;
         assign[q] = best;
-        if (counts) atomicAdd(s_cnt + best, 1u);
     }
-    if (!counts) return;
-    __syncthreads();
-    for (int t = threadIdx.x; t < n; t += UB)
-        if (s_cnt[t]) atomicAdd(counts + t, s_cnt[t]);
 }
 
 // Order-preserving map of a float's bits to an unsigned key, and back.
@@ -356,12 +349,6 @@ size_t kmeans_scratch_bytes(int n) {
     return sizeof(unsigned long long) * 3 * (size_t)n + sizeof(unsigned) * (size_t)n + 256;
 }
 
-size_t kmedians_scratch_bytes(long long N, int n) {
-    (void)N;
-    (void)n;
-    return 256;  // the assignment buffer is the caller's work_assign
-}
-
 cudaError_t launch_kmeans(const KmeansArgs& a, cudaStream_t st) {
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(a.scratch);
     unsigned* counts = reinterpret_cast<unsigned*>(sums + 3 * a.n);
@@ -386,12 +373,11 @@ cudaError_t launch_kmedians(const KmediansArgs& a, cudaStream_t st) {
                                                                    a.C);
     const int g = grid_for(a.N, a.n_sm);
     for (int it = 0; it < a.iterations; ++it) {
-        kmedians_assign_kernel<<<g, UB, smem, st>>>(a.V, a.N, a.k, a.C, a.n, a.work_assign,
-                                                    nullptr);
+        kmedians_assign_kernel<<<g, UB, smem, st>>>(a.V, a.N, a.k, a.C, a.n, a.work_assign);
         class_median_kernel<<<a.k * MC, MB, 0, st>>>(a.V, a.N, a.k, a.work_assign, a.n, a.C);
     }
     if (a.assign)
-        kmedians_assign_kernel<<<g, UB, smem, st>>>(a.V, a.N, a.k, a.C, a.n, a.assign, nullptr);
+        kmedians_assign_kernel<<<g, UB, smem, st>>>(a.V, a.N, a.k, a.C, a.n, a.assign);
     return cudaGetLastError();
 }
 
