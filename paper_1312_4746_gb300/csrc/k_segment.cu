@@ -18,7 +18,9 @@
 // barrier. The working set (about 6 n |Omega| floats) stays in L2. The grid
 // barriers are bounded waits: on timeout the kernel records the site in the
 // error word, raises an abort flag that every other block sees, and returns.
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 
 #include "internal.h"
 
@@ -301,19 +303,25 @@ SegKernel seg_kernel(long long P, int n) {
 }
 
 int seg_grid(long long P, int n, int n_sm) {
-    // co-resident blocks per SM, per variant (labels 1..8, 16, 64; narrow / wide index)
-    static int per_sm[2][10] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
-                                {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
+    // co-resident blocks per SM, per variant (labels 1..8, 16, 64; narrow /
+    // wide index); -1 until queried (calls from several threads store the
+    // same value)
+    static std::atomic<int> per_sm[2][10];
+    static std::once_flag init;
+    std::call_once(init, [] {
+        for (auto& row : per_sm)
+            for (auto& v : row) v.store(-1);
+    });
     const int v = n <= 8 ? n - 1 : n <= 16 ? 8 : 9;
-    int& slot = per_sm[seg_narrow(P, n) ? 0 : 1][v];
-    if (slot < 0) {
-        int nb = 0;
+    std::atomic<int>& slot = per_sm[seg_narrow(P, n) ? 0 : 1][v];
+    int nb = slot.load();
+    if (nb < 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, seg_kernel(P, n), SB, 0) !=
             cudaSuccess)
             nb = 0;
-        slot = nb;
+        slot.store(nb);
     }
-    const int k = slot < 2 ? slot : 2;
+    const int k = nb < 2 ? nb : 2;
     return k * n_sm;
 }
 
