@@ -372,6 +372,38 @@ def test_rho_readings_agree_at_unit_rho():
     assert np.abs(c["L"] - d["L"]).max() > 1e-3  # and differ elsewhere
 
 
+def test_duplicate_samples_weight_the_parzen_sum():
+    """A scribble pixel listed twice counts twice: L is the log of the
+    list's mean, so doubling every sample of a label changes nothing, and
+    doubling one sample weights its term by 2 (scipy logsumexp with
+    weights); the per-sample texture kernel and the distances see the list
+    as given."""
+    pr, bpx, bsm = _setup(m=4, seed=20)
+    off = pr.label_off
+    base = oracle.likelihood(pr.image, bpx, bsm, pr.k, off, pr.sample_pix)
+    # every sample of every label twice
+    rep = np.concatenate([np.repeat(pr.sample_pix[off[i]:off[i + 1]], 2)
+                          for i in range(pr.n_labels)]).astype(np.int32)
+    off2 = (2 * off).astype(np.int32)
+    _, bsm2 = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1, pix=rep)
+    two = oracle.likelihood(pr.image, bpx, bsm2, pr.k, off2, rep)
+    np.testing.assert_allclose(two["L"], base["L"], rtol=0, atol=1e-12)
+    # the first sample of label 0 twice
+    s0 = int(off[0])
+    one = np.insert(pr.sample_pix, s0, pr.sample_pix[s0]).astype(np.int32)
+    off1 = off.copy().astype(np.int32)
+    off1[1:] += 1
+    _, bsm1 = oracle.codes(pr.image, pr.omega, pr.mask, 5, 0.1, pix=one)
+    out = oracle.likelihood(pr.image, bpx, bsm1, pr.k, off1, one)
+    for q in (5, 90):
+        rho, beta = _rho_beta(pr, q, 0)
+        terms = [_kernel_terms(pr, bpx, bsm, q, s, rho, beta) for s in range(off[0], off[1])]
+        w = np.ones(len(terms))
+        w[0] = 2.0
+        expect = special.logsumexp(terms, b=w) - math.log(w.sum())
+        assert abs(out["L"][0, q] - expect) < 1e-10
+
+
 def test_constant_image_is_plain_kde():
     """A constant image makes every patch identical (TSM = 0) and every
     colour difference zero, so L_i is a plain 2-D Gaussian KDE of the scribble
