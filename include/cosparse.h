@@ -293,7 +293,10 @@ cs_status cs_refined_count(cs_ctx* ctx, int32_t* count, void* stream);
  *   sp         lambda >= 0 (boundary weight), nu >= 0 (MDL label cost, 0 for
  *              supervised segmentation), gamma > 0 (paper: 5), iterations >= 0
  *   u          DEVICE n_labels x H x W float32 out: the relaxed indicators
- *   labels     DEVICE H x W int32 out or NULL: argmax_i u_i(x)
+ *   labels     DEVICE H x W int32 out or NULL: argmax_i u_i(x), the lowest
+ *              label on ties
+ *   n_labels   1..64;  H W < 2^31
+ * Defaults (cs_seg_params_default): lambda 1, nu 0, gamma 5, 300 iterations.
  * Uses the context's scratch (4 n P + P floats). Asynchronous on `stream`:
  * one cooperative launch runs every iteration, with grid barriers between
  * the dual and primal steps. Errors: CS_ERR_INVALID_ARG for null or
