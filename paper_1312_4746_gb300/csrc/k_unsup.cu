@@ -11,8 +11,8 @@
 // bit. A k-means centroid is the exact mean of the members' values rounded
 // to multiples of 2^-24: integer sums (order-free atomics), one double
 // division, one rounding to FP32. A k-medians centre is the elementwise
-// median by radix selection, all classes of a code in one pass over the
-// points. A class without members keeps its centre.
+// median by radix selection, all classes of a code at once on a cluster of
+// blocks that split the points. A class without members keeps its centre.
 #include <cooperative_groups.h>
 
 #include <cstdint>
