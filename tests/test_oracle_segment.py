@@ -104,6 +104,33 @@ def test_smoothing_removes_isolated_pixel():
     assert lab0[4, 4] == 1 and np.all(lab == 0)
 
 
+def test_large_lambda_gives_the_cheapest_constant_labelling():
+    """With a boundary weight far above the data costs (g = 1/10 on a
+    constant image) every boundary costs more than any data gain: the
+    minimiser is the constant labelling by the label of least total cost."""
+    for seed in range(3):
+        rng = np.random.default_rng(100 + seed)
+        f = rng.uniform(0, 2, (3, 6, 7))
+        u, lab = seg.segment(f, np.zeros((6, 7, 3), np.float32), lam=200.0, iterations=600)
+        best = int(np.argmin(f.reshape(3, -1).sum(axis=1)))
+        assert np.all(lab == best)
+        np.testing.assert_allclose(u[best], 1.0, atol=1e-9)
+
+
+def test_large_label_cost_keeps_one_label():
+    """Eq. mdl: with nu far above the data costs (and no boundary term) a
+    second label never pays for itself; the solution uses the single label
+    of least total cost, where nu = 0 keeps the pointwise argmin."""
+    for seed in range(3):
+        rng = np.random.default_rng(200 + seed)
+        f = rng.uniform(0, 2, (3, 6, 7))
+        img = np.zeros((6, 7, 3), np.float32)
+        _, lab0 = seg.segment(f, img, lam=0.0, nu=0.0, iterations=1500)
+        _, lab = seg.segment(f, img, lam=0.0, nu=1e3, iterations=1500)
+        np.testing.assert_array_equal(lab0, np.argmin(f, axis=0))
+        assert np.all(lab == int(np.argmin(f.reshape(3, -1).sum(axis=1))))
+
+
 def test_dice_hand_example():
     a = np.array([[0, 0, 1], [1, 1, 1]])
     b = np.array([[0, 1, 1], [1, 1, 0]])
