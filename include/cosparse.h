@@ -151,6 +151,34 @@ const char* cs_last_error(const cs_ctx* ctx);
 cs_status cs_sync_status(cs_ctx* ctx, void* stream);
 
 /*
+ * Test hook for the timeout path of the bounded device waits (the paper has
+ * no counterpart: every barrier wait in the library's kernels gives up after
+ * a time limit, records a timeout in the device error word and lets the
+ * launch end, and this hook lets a test make one such wait run out).
+ *   limit_ns  time limit of every bounded wait of the context's later
+ *             launches (0 restores the default, 1 s)
+ *   stall     one-shot stall of the next launch of one kernel:
+ *             CS_STALL_NONE     none (disarms a pending stall)
+ *             CS_STALL_SEGMENT  cs_segment: the last block of the cooperative
+ *                               launch skips its arrival at the first grid
+ *                               barrier of the iterations (needs iterations > 0)
+ *             CS_STALL_SUM      the tensor-core sum (cs_likelihood or
+ *                               cs_data_term with CS_BF16 / CS_FP8): the
+ *                               MMA-issuing thread of the last CTA waits,
+ *                               before it issues anything, on a barrier that
+ *                               nothing completes
+ * The other waits of that launch then run out after limit_ns (or see the
+ * abort flag the first one raised); the launch ends, cs_sync_status returns
+ * CS_ERR_TIMEOUT, the stalled launch's outputs are undefined, and the
+ * context stays usable: the next launch runs normally.
+ * Errors: CS_ERR_INVALID_ARG (ctx NULL, limit_ns < 0, unknown stall).
+ */
+#define CS_STALL_NONE 0
+#define CS_STALL_SEGMENT 1
+#define CS_STALL_SUM 2
+cs_status cs_test_wait(cs_ctx* ctx, int64_t limit_ns, int stall);
+
+/*
  * Patches, codes and co-support bitmasks for every pixel
  * (Sec. 2: a = O s with s a zero-mean, unit-norm patch; Sec. 3.1: gray
  * patch centred at x, multiplied element-wise by a Gaussian mask before the
@@ -190,10 +218,12 @@ cs_status cs_codes(cs_ctx* ctx, const float* img, int H, int W, const float* ome
  * ~8 MB array in device memory that every GPU which loads the library holds
  * until the process exits. The caller passes inputs and outputs as for
  * cs_codes (bitmask required), plus dev_status: DEVICE 2 x int32, cleared by
- * the call and set to a nonzero code (and a count) if more entries needed the
- * exact double-precision recheck than the scratch holds (the bitmask is then
- * not guaranteed exact). Limits: H * W <= 2^20 pixels, k <= 1024; larger
- * requests return CS_ERR_INVALID_ARG before anything is launched. It always
+ * the call and set to {101, n} if n entries needed the exact double-precision
+ * recheck and n exceeds the 2^20 the scratch holds (only the first 2^20 are
+ * rechecked: the bitmask is then not guaranteed exact). Limits: H * W <= 2^20
+ * pixels, k <= 1024; larger requests, and the parameter values cs_codes
+ * rejects (patch side, tau, patch_order, codes_form), return
+ * CS_ERR_INVALID_ARG or CS_ERR_UNSUPPORTED before anything is launched. It always
  * computes the FP32 CUDA-core form of the codes (the codes cs_codes returns
  * with codes_form = CS_CODES_FP32); codes_form = CS_CODES_TC returns
  * CS_ERR_UNSUPPORTED.

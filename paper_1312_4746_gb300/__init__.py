@@ -33,6 +33,10 @@ CODES_AUTO = 0
 CODES_FP32 = 1
 CODES_TC = 2
 
+STALL_NONE = 0
+STALL_SEGMENT = 1
+STALL_SUM = 2
+
 # every symbol include/cosparse.h declares
 EXPORTS = (
     "cs_params_default",
@@ -41,6 +45,7 @@ EXPORTS = (
     "cs_destroy",
     "cs_last_error",
     "cs_sync_status",
+    "cs_test_wait",
     "cs_codes",
     "cs_codes_noalloc",
     "cs_cosupport",
@@ -209,6 +214,7 @@ def lib(path: str | None = None):
     L.cs_last_error.argtypes = [V]
     L.cs_last_error.restype = ctypes.c_char_p
     L.cs_sync_status.argtypes = [V, V]
+    L.cs_test_wait.argtypes = [V, ctypes.c_int64, I]
     L.cs_refined_count.argtypes = [V, ctypes.POINTER(ctypes.c_int32), V]
     L.cs_seg_params_default.argtypes = [ctypes.POINTER(SegParams)]
     L.cs_seg_params_default.restype = None
@@ -249,7 +255,7 @@ def lib(path: str | None = None):
     L.cs_mlp_grad.argtypes = [V, V, I, V, V, I, V, V, V]
     L.cs_profile_enable.argtypes = [V, I]
     L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
-    for f in ("cs_create", "cs_sync_status", "cs_refined_count", "cs_segment", "cs_codes", "cs_cosupport", "cs_likelihood",
+    for f in ("cs_create", "cs_sync_status", "cs_test_wait", "cs_refined_count", "cs_segment", "cs_codes", "cs_cosupport", "cs_likelihood",
               "cs_data_term", "cs_profile_enable", "cs_profile_read", "cs_surrogate_fit",
               "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_surrogate_save",
               "cs_surrogate_load", "cs_mlp_forward",
@@ -290,6 +296,11 @@ class Context:
     def sync(self):
         """Wait for the current stream and raise on a device-side error."""
         self.check(self._lib.cs_sync_status(self.handle, _stream()))
+
+    def test_wait(self, limit_ns: int = 0, stall: int = 0):
+        """Timeout-path test hook (cs_test_wait): the limit of the bounded
+        device waits (0: the default 1 s) and a one-shot stall (STALL_*)."""
+        self.check(self._lib.cs_test_wait(self.handle, int(limit_ns), int(stall)))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -219,6 +219,9 @@ cs_status cs_segment(cs_ctx* ctx, const float* f, const float* img, int H, int W
     SegArgs a{f, img, H, W, n_labels, (float)sp->lambda, (float)sp->nu, (float)sp->gamma,
               sp->iterations, u, labels, reinterpret_cast<float*>(ctx->scratch), nblk,
               ctx->d_err};
+    a.wait_ns = ctx->wait_ns;
+    a.stall = ctx->stall == CS_STALL_SEGMENT;
+    if (a.stall) ctx->stall = CS_STALL_NONE;  // one-shot
     cudaError_t e = launch_segment(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return CS_OK;
@@ -377,6 +380,17 @@ cs_status cs_refined_count(cs_ctx* ctx, int32_t* count, void* stream) {
         return cs_set_error(ctx, CS_ERR_CUDA, "cs_refined_count: %s", cudaGetErrorString(e));
     }
     *count = v;
+    return CS_OK;
+}
+
+cs_status cs_test_wait(cs_ctx* ctx, int64_t limit_ns, int stall) {
+    if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_test_wait: ctx is NULL");
+    if (limit_ns < 0 || (stall != CS_STALL_NONE && stall != CS_STALL_SEGMENT &&
+                         stall != CS_STALL_SUM))
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "cs_test_wait: limit %lld ns, stall %d",
+                            (long long)limit_ns, stall);
+    ctx->wait_ns = (unsigned long long)limit_ns;
+    ctx->stall = stall;
     return CS_OK;
 }
 
@@ -644,6 +658,9 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
     T.fb_count = L.fb_count;
     T.imax2 = L.imax2;
     T.l_tol = (float)prm->l_tol;
+    T.wait_ns = ctx->wait_ns;
+    T.stall = ctx->stall == CS_STALL_SUM;
+    if (T.stall) ctx->stall = CS_STALL_NONE;  // one-shot
     return T;
 }
 

@@ -166,6 +166,7 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
                       b->total_pixels,
                       (float)b->prm.l_tol,
                       b->prm.rho_variance != 0};
+        p.wait_ns = ctx->wait_ns;
         e = launch_tc_sum(b->descs, (int)b->order.size(), b->n_items, p, st);
     }
     return e;

@@ -44,6 +44,11 @@ struct cs_ctx {
     cudaStream_t side2 = nullptr;  // sample order overlapping both
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     bool profiling = false;
+    // timeout-path test hook (cs_test_wait): wait limit of the bounded device
+    // waits (0: the kernels' own 1 s) and a one-shot stall of the next
+    // solver or tensor-core sum launch
+    unsigned long long wait_ns = 0;
+    int stall = 0;
     std::vector<StageRecord> records;
     std::vector<cudaEvent_t> event_pool;
 };
@@ -175,6 +180,9 @@ struct SegArgs {
     float* scratch;    // seg_scratch_bytes()
     int nblk;          // blocks of the cooperative launch (seg_blocks)
     int* d_err;        // device error word (timeout of a grid barrier)
+    unsigned long long wait_ns = 0;  // limit of each grid-barrier wait (0: 1 s)
+    bool stall = false;  // timeout-path test: the last block skips its first arrival of
+                         // the iterations
 };
 size_t seg_scratch_bytes(long long P, int n, int nblk);
 int seg_blocks(long long P, int n_labels, int n_sm);  // 0 if the kernel cannot be resident
@@ -356,6 +364,8 @@ struct TcSumParams {
     int fb_cap;
     float l_tol;  // relative tolerance on L of the a-priori row bound (0: off)
     bool rho_var;  // rho is the location kernel's variance (else its standard deviation)
+    unsigned long long wait_ns = 0;  // limit of each bounded wait (0: the kernel's 1 s)
+    bool stall = false;  // timeout-path test: one CTA waits on a barrier nobody completes
 };
 struct TcLaunch {
     const float* img;
@@ -386,6 +396,8 @@ struct TcLaunch {
     int* fb_count;
     float* imax2;    // per label max |I_j|^2 (written by the preparation)
     float l_tol;
+    unsigned long long wait_ns;  // as TcSumParams
+    bool stall;
 };
 size_t tc_copy_bytes(int k, bool tex8, bool persample);
 int tc_tiles_per_label(int m);

@@ -45,14 +45,17 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // Grid barrier on a monotonic arrival counter: barrier number `k` (from 1)
 // completes when the counter reaches k * gridDim.x. bar[0] = counter,
 // bar[1] = abort flag. Returns false (for the whole block) when this block
-// gave up or another block raised the abort flag.
-__device__ bool grid_barrier(unsigned* bar, unsigned k, int* d_err, int site, int* s_ok) {
+// gave up or another block raised the abort flag. `arrive` false (the
+// timeout-path test) skips this block's arrival, so that no block's wait
+// completes: every block gives up after `wait_ns` or on the abort flag.
+__device__ bool grid_barrier(unsigned* bar, unsigned k, int* d_err, int site, int* s_ok,
+                             uint64_t wait_ns, bool arrive = true) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(bar, 1u);
+        if (arrive) atomicAdd(bar, 1u);
         const unsigned target = k * gridDim.x;
-        const uint64_t deadline = seg_clock() + SEG_WAIT_NS;
+        const uint64_t deadline = seg_clock() + wait_ns;
         int ok = 1;
         for (unsigned n = 0;; ++n) {
             if ((int)(ld_acquire(bar) - target) >= 0) break;
@@ -93,6 +96,8 @@ struct SegState {
     int* d_err;
     int H, W, n, iterations;
     float lambda, nu, gamma;
+    uint64_t wait_ns;  // limit of each grid-barrier wait
+    bool stall;        // the last block skips its arrival at the first barrier of the iterations
 };
 
 // N: the label count when it is at most 8 (every label loop unrolled
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(SB, 2) seg_solve_kernel(SegState S) {
     }
     for (int i = threadIdx.x; i < n; i += SB) s_m[i] = s_mb[i] = 1.f;
     unsigned nbar = 0;
-    if (!grid_barrier(S.bar, ++nbar, S.d_err, 40, &s_ok)) return;
+    if (!grid_barrier(S.bar, ++nbar, S.d_err, 40, &s_ok, S.wait_ns)) return;
 
     const float inv_area = 1.f / (float)P;
     for (int it = 0; it < S.iterations; ++it) {
@@ -194,7 +199,9 @@ __global__ void __launch_bounds__(SB, 2) seg_solve_kernel(SegState S) {
             for (int w = 0; w < NW; ++w) s += red[i][w];
             S.parts[(size_t)i * G + b] = s;
         }
-        if (!grid_barrier(S.bar, ++nbar, S.d_err, 41, &s_ok)) return;
+        if (!grid_barrier(S.bar, ++nbar, S.d_err, 41, &s_ok, S.wait_ns,
+                          !(S.stall && it == 0 && b == G - 1)))
+            return;
 
         // m step: m <- clamp(m - (nu + sum mu) / |Omega|, 0, 1), mb = 2 m_new - m;
         // one warp per label, the same summation order in every block
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(SB, 2) seg_solve_kernel(SegState S) {
                     S.u[e] = un;
                 }
         }
-        if (!grid_barrier(S.bar, ++nbar, S.d_err, 42, &s_ok)) return;
+        if (!grid_barrier(S.bar, ++nbar, S.d_err, 42, &s_ok, S.wait_ns)) return;
     }
 
     if (S.labels)
@@ -363,6 +370,8 @@ cudaError_t launch_segment(const SegArgs& a, cudaStream_t st) {
     S.lambda = a.lambda;
     S.nu = a.nu;
     S.gamma = a.gamma;
+    S.wait_ns = a.wait_ns ? a.wait_ns : SEG_WAIT_NS;
+    S.stall = a.stall && a.iterations > 0;
     cudaError_t e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     void* args[] = {&S};

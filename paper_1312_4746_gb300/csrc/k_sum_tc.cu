@@ -81,6 +81,8 @@ struct TcArgs {
     int* fb_count;
     int fb_cap;
     float l_tol;    // relative tolerance on L of the a-priori row bound (0: off)
+    uint64_t wait_ns;  // time limit of each barrier wait (0: WAIT_NS)
+    bool stall;        // the MMA issuer of the last CTA waits on a barrier nobody completes
 };
 
 // Image of work item g: the last descriptor whose first item is <= g.
@@ -114,7 +116,7 @@ struct Cfg {
     static constexpr int PAIR_LIMIT = 228 * 1024 / 2 - 1024;
     static constexpr int pair_bytes(int stages, int acb) {
         return stages * stage_bytes + tex_bytes + acb * AP + XB * 1 * 4 * 32 * 8 +
-               (2 * stages + 26) * 8 + 16;
+               (2 * stages + 27) * 8 + 16;
     }
     static constexpr bool PAIR = pair_bytes(2, 1) <= PAIR_LIMIT;
     static constexpr int ACB = !PAIR || pair_bytes(2, 2) <= PAIR_LIMIT ? 2 : 1;  // label buffers
@@ -136,7 +138,7 @@ struct Cfg {
     static constexpr int acol_off = atex_off + tex_bytes;
     static constexpr int xchg_off = acol_off + ACB * AP;              // [XB][EPQ-1][4][32] float2
     static constexpr int bar_off = xchg_off + XB * (EPQ - 1) * 4 * 32 * 8;
-    static constexpr int n_bars = 2 * STAGES + 2 + 2 + 2 + 2 + 2 + 16;
+    static constexpr int n_bars = 2 * STAGES + 2 + 2 + 2 + 2 + 2 + 16 + 1;
     static constexpr int misc_off = bar_off + n_bars * 8;
     // a floor on the shared memory keeps a third CTA (or, unpaired, a
     // second) off the SM, so that tensor memory allocation never waits
@@ -174,14 +176,14 @@ __device__ __forceinline__ void set_abort(volatile int* abort_flag, int* d_err, 
 // issue slots from the working warps of the SM's other CTA; the timer is
 // read every 256 tests.
 __device__ __forceinline__ bool spin_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                         int* d_err, int site) {
+                                         int* d_err, int site, uint64_t wait_ns) {
     if (*abort_flag) return false;
     uint64_t deadline = 0;
     for (uint32_t n = 0;; ++n) {
         if (tc::mbar_try_wait(bar, parity, SUSPEND_NS)) return true;
         if ((n & 255u) == 255u) {
             const uint64_t now = tc::globaltimer();
-            if (deadline == 0) deadline = now + WAIT_NS;
+            if (deadline == 0) deadline = now + wait_ns;
             else if (now > deadline) break;
         }
     }
@@ -192,7 +194,7 @@ __device__ __forceinline__ bool spin_bar(uint64_t* bar, uint32_t parity, volatil
 // Warp-uniform bounded wait (every lane tests the same phase, so the warp
 // stays converged); suspending tests as in spin_bar.
 __device__ __forceinline__ bool spin_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* d_err, int site) {
+                                          int* d_err, int site, uint64_t wait_ns) {
     uint64_t deadline = 0;
     for (uint32_t n = 0;; ++n) {
         if (__all_sync(0xffffffffu, tc::mbar_try_wait(bar, parity, SUSPEND_NS))) return true;
@@ -200,7 +202,7 @@ __device__ __forceinline__ bool spin_warp(uint64_t* bar, uint32_t parity, volati
             int late = 0;
             if ((threadIdx.x & 31) == 0) {
                 const uint64_t now = tc::globaltimer();
-                if (deadline == 0) deadline = now + WAIT_NS;
+                if (deadline == 0) deadline = now + wait_ns;
                 else late = now > deadline || *abort_flag;
             }
             if (__shfl_sync(0xffffffffu, late, 0)) break;
@@ -349,10 +351,12 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
     uint64_t* atex_full = tmem_full + 8;      // [1] epilogue warps
     uint64_t* atex_empty = tmem_full + 9;     // [1] MMA commit
     uint64_t* xchg_full = tmem_full + 10;     // [4 buffers][4 quadrants]
+    uint64_t* stall_bar = tmem_full + 26;     // [1] nobody arrives (timeout-path tests)
     uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + C::misc_off);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::misc_off + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t wait_ns = a.wait_ns ? a.wait_ns : WAIT_NS;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -368,6 +372,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
         tc::mbar_init(atex_full, EPI_WARPS);
         tc::mbar_init(atex_empty, 1);
         for (int x = 0; x < 16; ++x) tc::mbar_init(xchg_full + x, EPQ - 1);
+        tc::mbar_init(stall_bar, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                 {
                     const int s = (int)(it % C::STAGES);
                     const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
-                    ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1);
+                    ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1, wait_ns);
                     if (!ok) break;
                     uint8_t* st = ring + s * C::stage_bytes;
                     const int nvalid = min(BN, m_i - (T - lab_first) * BN);
@@ -453,26 +458,30 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
         if (pw == 0 && lane == 0)
             for (uint32_t d = (it > C::STAGES ? it - C::STAGES : 0); d < it; ++d)
                 tc::mbar_wait(full + (int)(d % C::STAGES), (uint32_t)((d / C::STAGES) & 1),
-                              tc::globaltimer() + WAIT_NS);
+                              tc::globaltimer() + wait_ns);
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t it = 0, li = 0, lpt = 0;
             bool ok = true;
             long long last = -1;
+            // test hook: nothing has been issued yet, so every other role
+            // drains cleanly once this wait gives up and raises the abort flag
+            if (a.stall && blockIdx.x == gridDim.x - 1)
+                ok = spin_bar(stall_bar, 0, abort_flag, a.d_err, 2, wait_ns);
             for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x, ++lpt) {
                 const TcImage& im = a.images[image_of(a, g)];
-                ok = spin_bar(atex_full, (uint32_t)(lpt & 1), abort_flag, a.d_err, 3);
+                ok = spin_bar(atex_full, (uint32_t)(lpt & 1), abort_flag, a.d_err, 3, wait_ns);
                 for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
                     const int cb = (int)(li % C::ACB);
-                    ok = spin_bar(acol_full + cb, (uint32_t)((li / C::ACB) & 1), abort_flag, a.d_err, 4);
+                    ok = spin_bar(acol_full + cb, (uint32_t)((li / C::ACB) & 1), abort_flag, a.d_err, 4, wait_ns);
                     const int nt = tiles_of(im.tile_off, i);
                     const uint8_t* ap = acol + cb * C::AP;  // colour, L0, L1 slabs of this label
                     for (int t = 0; ok && t < nt; ++t, ++it) {
                         const int s = (int)(it % C::STAGES), b = (int)(it % NB);
-                        ok = spin_bar(full + s, (uint32_t)((it / C::STAGES) & 1), abort_flag, a.d_err, 5) &&
+                        ok = spin_bar(full + s, (uint32_t)((it / C::STAGES) & 1), abort_flag, a.d_err, 5, wait_ns) &&
                              spin_bar(tmem_empty + b, (uint32_t)(((it / NB) & 1) ^ 1), abort_flag,
-                                      a.d_err, 6);
+                                      a.d_err, 6, wait_ns);
                         if (!ok) break;
                         tc::fence_after_sync();
                         const uint32_t d1 = tmem + (uint32_t)(b * BN);
@@ -505,7 +514,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
             // drain: the last MMAs must finish before the tensor memory is freed
             if (last >= 0)
                 tc::mbar_wait(tmem_full + (int)(last % NB), (uint32_t)((last / NB) & 1),
-                              tc::globaltimer() + WAIT_NS);
+                              tc::globaltimer() + wait_ns);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -535,7 +544,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                 for (int w = 0; w < a.Wk; ++w) popx += __popc(bxp[w]);
             // texture operand rows: this warp writes slabs sl = hf, hf + EPQ, ...
             if (PERSAMPLE) {
-                ok = spin_warp(atex_empty, (uint32_t)((lpt & 1) ^ 1), abort_flag, a.d_err, 7);
+                ok = spin_warp(atex_empty, (uint32_t)((lpt & 1) ^ 1), abort_flag, a.d_err, 7, wait_ns);
                 if (!ok) break;
                 for (int sl = hf; sl < KS; sl += EPQ) {
                     // FP8: slab sl holds codes 32 sl .. 32 sl + 31 (bitmask word sl);
@@ -591,7 +600,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                 // warp part j % EPQ
                 const int cb = (int)(li % C::ACB);
                 ok = spin_warp(acol_empty + cb, (uint32_t)(((li / C::ACB) & 1) ^ 1), abort_flag,
-                               a.d_err, 8);
+                               a.d_err, 8, wait_ns);
                 if (!ok) break;
                 uint8_t* ap = acol + cb * C::AP;
                 const float f = nA * g;
@@ -644,7 +653,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                 float S = 0.f, Ccomp = 0.f;
                 for (int t = 0; t < nt; ++t, ++it) {
                     const int b = (int)(it % NB);
-                    ok = spin_warp(tmem_full + b, (uint32_t)((it / NB) & 1), abort_flag, a.d_err, 10);
+                    ok = spin_warp(tmem_full + b, (uint32_t)((it / NB) & 1), abort_flag, a.d_err, 10, wait_ns);
                     if (!ok) break;
                     tc::fence_after_sync();
                     const int nvalid = min(BN, m_i - t * BN);
@@ -690,7 +699,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(xbar);
                 } else {
-                    ok = spin_warp(xbar, (uint32_t)((li / C::XB) & 1), abort_flag, a.d_err, 11);
+                    ok = spin_warp(xbar, (uint32_t)((li / C::XB) & 1), abort_flag, a.d_err, 11, wait_ns);
                     if (!ok) break;
                     float Sm = S, Cm = Ccomp;
 #pragma unroll
@@ -1084,6 +1093,8 @@ cudaError_t sum(const TcImage* descs, int n_images, int n_items, const TcSumPara
     a.fb_count = p.fb_count;
     a.fb_cap = p.fb_cap;
     a.l_tol = p.l_tol;
+    a.wait_ns = p.wait_ns;
+    a.stall = p.stall;
     cudaError_t e = cudaFuncSetAttribute(sum_tc_kernel<TEX8, KS, PERSAMPLE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.fb_count, 0, sizeof(int), st);
@@ -1172,6 +1183,6 @@ cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     TcSumParams p{L.k,       L.tex8,  L.persample, L.alpha,      L.d_min, L.kappa_beta,
                   L.sigma_c2, L.d_err, L.n_sm,      L.fb_list,    L.fb_count,
-                  L.H * L.W,  L.l_tol, L.rho_var};
+                  L.H * L.W,  L.l_tol, L.rho_var,   L.wait_ns,    L.stall};
     return launch_tc_sum(L.desc, 1, tc_pixel_tiles(L.H, L.W), p, st);
 }

@@ -73,12 +73,9 @@ extern "C" cs_status cs_codes_noalloc(const float* img, int H, int W, const floa
     if (k < 1 || k > NOALLOC_MAX_K)
         return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: k=%d outside 1..%d", fn, k,
                             NOALLOC_MAX_K);
-    if (prm->p < 1 || (prm->p & 1) == 0)
-        return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: patch side %d is not odd", fn, prm->p);
-    if (prm->p < 3 || prm->p > 9)
-        return cs_set_error(nullptr, CS_ERR_UNSUPPORTED, "%s: patch side %d not in 3..9", fn, prm->p);
-    if (!(prm->tau >= 0.0))
-        return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: tau must be >= 0", fn);
+    // patch side, tau, patch order and codes form: the checks cs_codes makes
+    cs_status s = cs_check_patch(nullptr, fn, prm);
+    if (s) return s;
     // the fixed scratch holds no operator operand tiles: FP32 CUDA-core codes only
     if (prm->codes_form == CS_CODES_TC)
         return cs_set_error(nullptr, CS_ERR_UNSUPPORTED, "%s: computes the FP32 codes form only",
@@ -89,7 +86,7 @@ extern "C" cs_status cs_codes_noalloc(const float* img, int H, int W, const floa
         return cs_set_error(nullptr, CS_ERR_CUDA, "%s: no current CUDA device", fn);
     }
     void* base = nullptr;
-    cs_status s = noalloc_scratch(device, &base);
+    s = noalloc_scratch(device, &base);
     if (s) return s;
     unsigned char* scratch = static_cast<unsigned char*>(base);
     cudaStream_t st = (cudaStream_t)stream;

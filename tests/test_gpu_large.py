@@ -7,6 +7,10 @@ oracle at sampled pixels (the oracle cannot afford every pair):
   (1.7e12 pairs; distance transform with global-memory envelopes, six FP8
   texture slabs, 49 sample tiles per label).
 
+The 4096 x 4096 workload is also checked on a contiguous 256 x 256 crop
+(every pixel of it) against the oracle with the full image's samples,
+distances and patches.
+
 Bars: bitmasks and distances bit-exact at the sampled pixels; plain FP32 L
 within 1e-5 relative; the tensor-core form within its guarantee l_tol
 (default 1e-3; and 1e-4 when asked for, through the FP64 recompute of rows
@@ -36,7 +40,7 @@ def env(cuda_lib):
 @pytest.mark.parametrize("wl,n_pix", [(4, 800), (5, 600)])
 def test_large_workload_sampled(env, wl, n_pix):
     cs, ctx, torch = env
-    pr = synth.make_workload(wl)
+    pr = _wl5() if wl == 5 else synth.make_workload(wl)
     dev = "cuda:0"
     img = torch.from_numpy(pr.image).to(dev)
     om = torch.from_numpy(pr.omega).to(dev)
@@ -77,3 +81,69 @@ def test_large_workload_sampled(env, wl, n_pix):
               f"max rel err on L {rel:.2e}, pixels recomputed in FP64 {n_fp64}")
         del out
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("precision,l_tol,bar", [(2, 1e-3, 1e-3), (2, 1e-4, 1e-4), (0, None, 1e-5)])
+def test_workload5_crop(env, precision, l_tol, bar):
+    """A contiguous 256 x 256 crop of the 4096 x 4096 workload (16 labels x
+    6250 samples, 9x9 patches, Omega 162x81; 6.6e9 pairs for the oracle):
+    whole 16 x 8 pixel tiles next to each other, every Morton-ordered sample
+    tile of every label and any label row the tensor-core form recomputes in
+    FP64, all within one region of the image. The GPU runs the full image; the
+    oracle evaluates the crop's pixels with the full image's samples,
+    distances and patches. The crop is placed on a scribble of label 0, so it
+    holds samples, short and long scribble distances and region borders."""
+    cs, ctx, torch = env
+    pr = _wl5()
+    H, W, nl = pr.H, pr.W, pr.n_labels
+    s = int(pr.sample_pix[0])
+    x0 = min(max(s % W - 128, 0), W - 256)
+    y0 = min(max(s // W - 128, 0), H - 256)
+    yy, xx = np.mgrid[y0:y0 + 256, x0:x0 + 256]
+    pix = (yy * W + xx).ravel().astype(np.int32)
+    assert len(np.unique(pr.regions.ravel()[pix])) > 1
+    ref = _wl5_crop_ref(pr, pix)
+    dev = "cuda:0"
+    prm = cs.Params.from_synth(pr.params, precision=precision)
+    if l_tol is not None:
+        prm.l_tol = l_tol
+    out = ctx.data_term(torch.from_numpy(pr.image).to(dev), torch.from_numpy(pr.omega).to(dev),
+                        torch.from_numpy(pr.mask).to(dev), pr.label_off,
+                        torch.from_numpy(pr.sample_pix).to(dev), prm, want_bitmask=True,
+                        want_dist2=True)
+    ctx.sync()
+    idx = torch.from_numpy(pix.astype(np.int64)).to(dev)
+    bits = out["bitmask"].index_select(0, idx).cpu().numpy().view(np.uint32)
+    d2 = out["dist2"].reshape(nl, -1).index_select(1, idx).cpu().numpy()
+    L = -out["neglog"].reshape(nl, -1).index_select(1, idx).cpu().numpy().astype(np.float64)
+    post = out["post"].reshape(nl, -1).index_select(1, idx).cpu().numpy()
+    n_fp64 = ctx.refined_count() if precision else 0
+    del out
+    torch.cuda.empty_cache()
+    assert np.array_equal(bits, ref["bits_px"])
+    assert np.array_equal(d2, ref["dist2"])
+    rel = float(np.max(np.abs(L - ref["L"]) / np.maximum(np.abs(ref["L"]), 1.0)))
+    perr = float(np.max(np.abs(post - ref["post"])))
+    srt = np.sort(ref["post"], axis=0)
+    tie = (srt[-1] - srt[-2]) < 1e-12
+    agree = float(np.mean((np.argmax(post, 0) == np.argmax(ref["post"], 0)) | tie))
+    print(f"4096x4096, crop 256x256 at ({x0}, {y0}), precision {precision} l_tol {l_tol}: "
+          f"max rel err on L {rel:.2e}, max prob err {perr:.2e}, argmax agreement {agree:.5f}, "
+          f"pixels recomputed in FP64 {n_fp64}")
+    assert rel <= bar and perr <= 1e-2 and agree >= 0.999, (rel, perr, agree)
+
+
+_WL5 = {}
+
+
+def _wl5():
+    if "pr" not in _WL5:
+        _WL5["pr"] = synth.make_workload(5)
+    return _WL5["pr"]
+
+
+def _wl5_crop_ref(pr, pix):
+    key = ("ref", int(pix[0]))
+    if key not in _WL5:
+        _WL5[key] = oracle.data_term(pr, pix=pix, want_dist2=True)
+    return _WL5[key]

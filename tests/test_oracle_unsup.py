@@ -13,18 +13,18 @@ def _blobs(rng, n, centres, spread):
 
 def test_kmeans_matches_scipy_kmeans2():
     """Same start and round count as scipy's Lloyd iteration (float64 means):
-    the centres agree to the 2^-24 rounding of the values, and the final
-    assignment is scipy's nearest-centroid routine on those centres."""
+    the centres agree to float64 rounding, and the final assignment is
+    scipy's nearest-centroid routine on those centres."""
     vq = pytest.importorskip("scipy.cluster.vq")
     rng = np.random.default_rng(10)
     X, _ = _blobs(rng, 3000, [[0.2, 0.3, 0.7], [0.8, 0.1, 0.2], [0.5, 0.9, 0.4],
                               [0.1, 0.1, 0.1]], 0.08)
     init = [5, 17, 400, 1234]
     for T in (1, 4, 12):
-        C, lab = unsup.kmeans_fp32(X, init, T)
+        C, lab = unsup.kmeans(X, init, T)
         ref, _ = vq.kmeans2(X.astype(np.float64), X[init].astype(np.float64), iter=T,
                             minit="matrix", missing="warn")
-        np.testing.assert_allclose(C, ref, rtol=0, atol=2e-7)
+        np.testing.assert_allclose(C, ref, rtol=0, atol=1e-13)
         lab_ref, _ = vq.vq(X.astype(np.float64), C.astype(np.float64))
         np.testing.assert_array_equal(lab, lab_ref)
 
@@ -36,39 +36,48 @@ def test_kmeans_objective_non_increasing_and_blob_means():
     init = [int(np.nonzero(truth == a)[0][0]) for a in range(3)]
     prev = np.inf
     for T in range(6):
-        C, lab = unsup.kmeans_fp32(X, init, T)
-        obj = float(((X.astype(np.float64) - C[lab].astype(np.float64)) ** 2).sum())
+        C, lab = unsup.kmeans(X, init, T)
+        obj = float(((X.astype(np.float64) - C[lab]) ** 2).sum())
         assert obj <= prev * (1 + 1e-12)
         prev = obj
     np.testing.assert_array_equal(lab, truth)
     for a in range(3):
         np.testing.assert_allclose(C[a], X[truth == a].astype(np.float64).mean(axis=0),
-                                   atol=1e-7)
+                                   rtol=0, atol=1e-14)
 
 
 def test_kmeans_empty_class_keeps_centre_and_ties_go_low():
     X = np.array([[0, 0, 0], [1, 1, 1], [1, 1, 0.9]], np.float32)
-    C, lab = unsup.kmeans_fp32(X, [0, 0, 1], 3)  # classes 0 and 1 start equal
+    C, lab = unsup.kmeans(X, [0, 0, 1], 3)  # classes 0 and 1 start equal
     np.testing.assert_array_equal(lab, [0, 2, 2])  # the tie goes to class 0
     np.testing.assert_array_equal(C[1], X[0])  # class 1 never wins a pixel
-    assert abs(float(C[2, 2]) - 0.95) < 1e-7
+    assert float(C[2, 2]) == (1.0 + float(np.float32(0.9))) / 2
 
 
-def test_fixed_point_mean_rounding():
-    """Centroid = float32(sum rint(2^24 v) / (cnt 2^24)): a hand case."""
-    X = np.array([[2.0 ** -25, 0.5, 1.0], [0.0, 0.25, 1.0]], np.float32)
-    C = unsup.colour_means(X, np.array([0, 0]), np.zeros((1, 3), np.float32))
-    # rint(0.5) = 0 (half to even): the tiny value vanishes
-    np.testing.assert_array_equal(C[0], np.array([0.0, 0.375, 1.0], np.float32))
+def test_mean_is_the_true_mean():
+    """A centroid is the plain mean of its members (no rounding of the
+    values): a hand case with a value far below the others' spacing, and
+    the update of one class leaves the others alone."""
+    X = np.array([[2.0 ** -25, 0.5, 1.0], [0.0, 0.25, 1.0], [0.7, 0.7, 0.7]], np.float32)
+    C0 = np.array([[0.0, 0.0, 0.0], [9.0, 9.0, 9.0], [0.6, 0.6, 0.6]])
+    C = unsup.colour_means(X, np.array([0, 0, 2]), C0)
+    np.testing.assert_array_equal(C[0], [2.0 ** -26, 0.375, 1.0])
+    np.testing.assert_array_equal(C[1], C0[1])
+    np.testing.assert_array_equal(C[2], X[2].astype(np.float64))
 
 
-def test_median_fp32_matches_numpy_median():
+def test_texture_medians_match_numpy_median():
+    """The k-medians update against numpy's median per class (odd, even and
+    single-member classes); an empty class keeps its centre."""
     rng = np.random.default_rng(12)
-    for m in (1, 2, 3, 10, 11):
-        v = rng.uniform(0, 1, (m, 7)).astype(np.float32)
-        got = unsup.median_fp32(v).astype(np.float64)
-        ref = np.median(v.astype(np.float64), axis=0)
-        np.testing.assert_allclose(got, ref, rtol=1.2e-7, atol=0)
+    k, N = 7, 31
+    V = rng.uniform(0, 1, (k, N)).astype(np.float32)
+    lab = np.array([0] * 10 + [1] * 11 + [3] * 1 + [0] * 9, np.int32)[:N]
+    C0 = rng.uniform(0, 1, (4, k))
+    C = unsup.texture_medians(V, lab, C0)
+    for b in (0, 1, 3):
+        np.testing.assert_array_equal(C[b], np.median(V[:, lab == b].astype(np.float64), axis=1))
+    np.testing.assert_array_equal(C[2], C0[2])
 
 
 def test_kmedians_assignment_and_centres():
@@ -84,26 +93,25 @@ def test_kmedians_assignment_and_centres():
     init = [int(np.nonzero(truth == b)[0][0]) for b in range(4)]
     prev = np.inf
     for T in (0, 1, 2, 5):
-        C, lab = unsup.kmedians_fp32(V, init, T)
-        D = dist.cdist(V.T.astype(np.float64), C.astype(np.float64), "cityblock")
+        C, lab = unsup.kmedians(V, init, T)
+        D = dist.cdist(V.T.astype(np.float64), C, "cityblock")
         srt = np.sort(D, axis=1)
-        clear = (srt[:, 1] - srt[:, 0]) > 1e-4
+        clear = (srt[:, 1] - srt[:, 0]) > 1e-12
         np.testing.assert_array_equal(lab[clear], np.argmin(D, axis=1)[clear])
         obj = float(D[np.arange(N), lab].sum())
         assert obj <= prev * (1 + 1e-6)
         prev = obj
     # centres after T rounds are the medians of the members of round T's assignment
-    C4, _ = unsup.kmedians_fp32(V, init, 4)
-    lab4 = unsup.assign_texture(V, unsup.kmedians_fp32(V, init, 3)[0])
+    C4, _ = unsup.kmedians(V, init, 4)
+    lab4 = unsup.assign_texture(V, unsup.kmedians(V, init, 3)[0])
     for b in range(4):
-        np.testing.assert_allclose(C4[b], np.median(V[:, lab4 == b].astype(np.float64), axis=1),
-                                   rtol=1.2e-7, atol=0)
+        np.testing.assert_array_equal(C4[b], np.median(V[:, lab4 == b].astype(np.float64), axis=1))
 
 
 def test_median_is_l1_optimal():
     rng = np.random.default_rng(14)
     v = rng.uniform(0, 1, (15, 5)).astype(np.float32)
-    c = unsup.median_fp32(v).astype(np.float64)
+    c = unsup.texture_medians(v.T, np.zeros(15, np.int32), np.zeros((1, 5)))[0]
     cost = np.abs(v - c).sum()
     for _ in range(50):
         d = c + rng.normal(0, 0.05, 5)

@@ -75,3 +75,61 @@ def test_noalloc_rejects_oversize(cuda_lib):
     rc = L.cs_codes_noalloc(dummy, 10, 10, dummy, 98, dummy, ctypes.byref(prm), None, None,
                             dummy, dummy, None)
     assert rc == cs.CS_ERR_UNSUPPORTED
+
+
+def test_noalloc_rejects_bad_params(cuda_lib):
+    """The same parameter checks as cs_codes: patch order and codes form."""
+    import paper_1312_4746_gb300 as cs
+
+    L = cs.lib()
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the call must fail before launching
+    for field, value in (("patch_order", 2), ("patch_order", -1), ("codes_form", 7)):
+        prm = cs.Params.default(p=7)
+        setattr(prm, field, value)
+        rc = L.cs_codes_noalloc(dummy, 10, 10, dummy, 98, dummy, ctypes.byref(prm), None, None,
+                                dummy, dummy, None)
+        assert rc == cs.CS_ERR_INVALID_ARG, (field, value)
+
+
+def test_noalloc_guard_overflow_reported(cuda_lib):
+    """More entries needing the exact double-precision recheck than the fixed
+    list holds (2^20): a one-pixel checkerboard makes every interior window
+    one of two patterns, every operator row is the same unit vector, and tau
+    is set to the exact code of one pattern, so about half of all P x k
+    entries lie within their FP32 error bound of tau. The call reports the
+    overflow in dev_status (code 101, then the number of entries), and a
+    normal call afterwards starts from a clean status."""
+    import torch
+
+    import oracle
+    import paper_1312_4746_gb300 as cs
+
+    L = cs.lib()
+    H, W, p, k = 192, 192, 7, 128
+    yy, xx = np.mgrid[0:H, 0:W]
+    g = np.where((yy + xx) % 2 == 0, 0.8, 0.2).astype(np.float32)
+    img = np.repeat(g[:, :, None], 3, axis=2).copy()
+    row = np.random.default_rng(5).normal(size=p * p)
+    om = np.tile((row / np.linalg.norm(row)).astype(np.float32), (k, 1))
+    mask = synth.make_mask(p)
+    a, _ = oracle.codes(img, om, mask, p, 0.0, pix=np.array([(H // 2) * W + W // 2], np.int32))
+    prm = cs.Params.default(p=p, codes_form=cs.CODES_FP32)
+    prm.tau = float(abs(a[0, 0]))
+    P, Wk = H * W, (k + 31) // 32
+    d_img, d_om, d_mask = _dev(torch, img), _dev(torch, om), _dev(torch, mask)
+    bits = torch.empty((P, Wk), dtype=torch.int32, device="cuda:0")
+    status = torch.zeros(2, dtype=torch.int32, device="cuda:0")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.cs_codes_noalloc(cs._ptr(d_img), H, W, cs._ptr(d_om), k, cs._ptr(d_mask),
+                            ctypes.byref(prm), None, None, cs._ptr(bits), cs._ptr(status), stream)
+    assert rc == cs.CS_OK, L.cs_last_error(None)
+    torch.cuda.synchronize()
+    st = status.tolist()
+    assert st[0] == 101 and st[1] > (1 << 20), st
+    print(f"guard overflow reported: status {st[0]}, {st[1]} entries for a list of {1 << 20}")
+    prm.tau = 0.1  # a normal call on the same scratch: clean status again
+    rc = L.cs_codes_noalloc(cs._ptr(d_img), H, W, cs._ptr(d_om), k, cs._ptr(d_mask),
+                            ctypes.byref(prm), None, None, cs._ptr(bits), cs._ptr(status), stream)
+    assert rc == cs.CS_OK
+    torch.cuda.synchronize()
+    assert status.tolist() == [0, 0]
