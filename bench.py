@@ -13,10 +13,13 @@ Metric: pixel x sample likelihood pairs per second, whole job.
   e2e    the same steps through the C ABI starting from pinned host buffers:
          host->device copy of the inputs, the step, device->host copy of the
          data term f_i (neglog), all inside the timed region
-Secondary blocks of the same line (not the headline): "forms" (the plain
-FP32 form beside the FP8 one), "batch" (64 uneven images through
-cs_batch_*, graph-replayed and autotuned) and "large" (the 1024x1024 and
-4096x4096 workloads, both forms).
+Secondary blocks of the same line (not the headline): "forms" (the BF16
+tensor-core and the plain FP32 forms beside the FP8 one, each with its error
+against the FP64 oracle at sampled pixels, computed outside the timed
+region), "batch" (64 uneven images through cs_batch_*, graph-replayed and
+autotuned) and "large" (the 1024x1024 and 4096x4096 workloads, both forms,
+with their errors). The ALU roofline's denominators come from
+cs_unit_rates, a microbenchmark of the pipes run at the start ("unit_rates").
 Under torchrun (N > 1) every rank runs its own image (weak scaling, no
 collective on the data path); rank 0 prints the max-over-ranks line.
 
@@ -132,9 +135,18 @@ def _peaks():
 
 # Nominal per-SM, per-clock rates of the pipes the pair loops use on GB300
 # (152 SMs): 128 FP32 lanes, 64 INT32, 16 popc and 32 ex2 (special-function)
-# results per clock. A probe of chained FFMA / popc / ex2 on the box measured
-# 117, 15.2 and 30.3 per clock, consistent with these.
+# results per clock. The roofline uses the rates cs_unit_rates measures on
+# the device where it has them (FP32, popc, ex2) and these nominal figures
+# for the rest (INT32), and reports both.
 PIPE_LANES = {"fp32": 128, "int32": 64, "mufu": 32, "popc": 16}
+
+
+def measured_lanes(rates):
+    """Per-SM per-clock rates for the roofline: measured where probed."""
+    lanes = dict(PIPE_LANES)
+    if rates:
+        lanes.update({"fp32": rates["ffma"], "popc": rates["popc"], "mufu": rates["ex2"]})
+    return lanes
 
 
 def pair_ops(form: str, Wk: int) -> dict:
@@ -152,11 +164,38 @@ def pair_ops(form: str, Wk: int) -> dict:
     return {"fp32": 3, "mufu": 1}
 
 
-def alu_peak_pairs(form: str, Wk: int, sm_mhz: float, n_sm: int = 152) -> tuple[float, str]:
+def alu_peak_pairs(form: str, Wk: int, sm_mhz: float, n_sm: int = 152,
+                   lanes: dict | None = None) -> tuple[float, str]:
+    lanes = lanes or PIPE_LANES
     ops = pair_ops(form, Wk)
-    rates = {k: PIPE_LANES[k] / v for k, v in ops.items()}
+    rates = {k: lanes[k] / v for k, v in ops.items()}
     pipe = min(rates, key=rates.get)
     return rates[pipe] * n_sm * sm_mhz * 1e6, pipe
+
+
+def errors(L, post, ref):
+    """A form's error against the oracle at the sampled pixels: max relative
+    error on L (max |L - L_o| / max(|L_o|, 1)), max probability error and
+    argmax agreement (oracle ties within 1e-12 count as agreement)."""
+    L = np.asarray(L, np.float64)
+    post = np.asarray(post, np.float64)
+    rel = float(np.max(np.abs(L - ref["L"]) / np.maximum(np.abs(ref["L"]), 1.0)))
+    perr = float(np.max(np.abs(post - ref["post"])))
+    srt = np.sort(ref["post"], axis=0)
+    tie = (srt[-1] - srt[-2]) < 1e-12 if srt.shape[0] > 1 else np.ones(srt.shape[1], bool)
+    agree = float(np.mean((np.argmax(post, 0) == np.argmax(ref["post"], 0)) | tie))
+    return {"max_rel_err_L": rel, "max_prob_err": perr, "argmax_agreement": agree}
+
+
+def sample_pixels(pr, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(rng.integers(0, pr.H * pr.W, n)).astype(np.int32)
+
+
+def gather_px(torch, t, nl, pix):
+    """(nl, len(pix)) host copy of the sampled pixels of a (nl, H, W) tensor."""
+    idx = torch.from_numpy(pix.astype(np.int64)).to(t.device)
+    return t.reshape(nl, -1).index_select(1, idx).cpu().numpy()
 
 
 def run_reference(args):
@@ -307,7 +346,7 @@ def measure(ctx, cs, torch, pr, form, steps, warmup, dev, stream, flush, clk=Non
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
     stage["refined_pixels"] = refined
-    return dev_ms, e2e_ms, stage, h2d, d2h
+    return dev_ms, e2e_ms, stage, h2d, d2h, out
 
 
 def measure_segment(ctx, cs, torch, pr, dev, stream, iterations=300, runs=3):
@@ -419,10 +458,13 @@ def measure_large(ctx, cs, torch, dev, reduce_max, world, steps=3):
     hundred MB to GB per step, above L2)."""
     from paper_1312_4746_gb300 import synth
 
+    import oracle
+
     out = {}
     stream = torch.cuda.current_stream()
     for wl in (4, 5):
         pr = synth.make_workload(wl)
+        pix = sample_pixels(pr, 256, 40 + wl)
         img = torch.from_numpy(pr.image).to(dev)
         om = torch.from_numpy(pr.omega).to(dev)
         mask = torch.from_numpy(pr.mask).to(dev)
@@ -441,8 +483,14 @@ def measure_large(ctx, cs, torch, dev, reduce_max, world, steps=3):
             torch.cuda.synchronize()
             (ms,) = reduce_max([e0.elapsed_time(e1) / steps])
             entry[form] = {"ms_per_step": ms, "pairs_per_s": pairs * world / (ms * 1e-3),
-                           "fp64_recomputed_pixels": ctx.refined_count() if form != "fp32" else 0}
+                           "fp64_recomputed_pixels": ctx.refined_count() if form != "fp32" else 0,
+                           "_got": (-gather_px(torch, res["neglog"], pr.n_labels, pix),
+                                    gather_px(torch, res["post"], pr.n_labels, pix))}
             del res
+        ref = oracle.data_term(pr, pix=pix)
+        for form in ("fp8", "fp32"):
+            entry[form]["error_vs_oracle"] = errors(*entry[form].pop("_got"), ref)
+        entry["error_sample"] = f"{len(pix)} random pixels x all samples (FP64 oracle)"
         out[f"{pr.W}x{pr.H}"] = entry
         del img, om, mask, smp
         torch.cuda.empty_cache()
@@ -494,8 +542,9 @@ def main():
     stream = torch.cuda.current_stream()
     pairs_rank = P * pr.n_samples
 
-    forms = [args.form] + [f for f in ("fp32",) if f != args.form]
+    forms = [args.form] + [f for f in ("bf16", "fp32") if f != args.form]
     res = {}
+    rates = ctx.unit_rates() if rank == 0 else None  # pipe rates for the roofline
     if world > 1:
         torch.distributed.barrier()
     with ClockSampler(local) as clk:
@@ -528,20 +577,35 @@ def main():
         clocks = clk.summary()
         sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        import oracle
+
+        lanes = measured_lanes(rates)
+        # errors against the FP64 oracle at sampled pixels (outside the timed region)
+        pix = sample_pixels(pr, 2000, 17)
+        ref = oracle.data_term(pr, pix=pix)
+        nl = pr.n_labels
         forms_out = {}
         refined = {f: res[f][2].pop("refined_pixels") for f in forms}
         for form in forms:
-            d_ms, e_ms, stage, h2d, d2h = res[form]
-            peak, pipe = alu_peak_pairs(form, Wk, sm_mhz, n_sm)
+            d_ms, e_ms, stage, h2d, d2h, o = res[form]
+            peak, pipe = alu_peak_pairs(form, Wk, sm_mhz, n_sm, lanes)
             achieved = pairs_rank / (stage["sum"] * 1e-3)
             forms_out[form] = {
                 "form": FORM_NAMES[form], "pairs_per_s": pairs_rank * args.steps / (d_ms * 1e-3),
                 "ms_per_step": d_ms / args.steps, "stage_ms": stage,
                 "sum_kernel_pairs_per_s": achieved, "sum_kernel_peak": peak,
                 "sum_kernel_frac": achieved / peak, "binding_pipe": pipe,
-                "fp64_recomputed_pixels": refined[form]}
-        d_ms, e_ms, stage, h2d, d2h = res[head]
-        peak, pipe = alu_peak_pairs(head, Wk, sm_mhz, n_sm)
+                "fp64_recomputed_pixels": refined[form],
+                "error_vs_oracle": errors(-gather_px(torch, o["neglog"], nl, pix),
+                                          gather_px(torch, o["post"], nl, pix), ref)}
+        pr_s = synth.make_workload(WORKLOAD, seed=rank_seed(rank))
+        pr_s.params.mode = 2
+        ref_s = oracle.data_term(pr_s, pix=pix)
+        o = res_smooth[5]
+        smooth_err = errors(-gather_px(torch, o["neglog"], nl, pix),
+                            gather_px(torch, o["post"], nl, pix), ref_s)
+        d_ms, e_ms, stage, h2d, d2h, _ = res[head]
+        peak, pipe = alu_peak_pairs(head, Wk, sm_mhz, n_sm, lanes)
         achieved = pairs_rank / (stage["sum"] * 1e-3)
         kernel = "sum_plain_kernel" if head == "fp32" else "sum_tc_kernel"
         line = {
@@ -560,9 +624,16 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
                          "frac": achieved / peak, "traffic": TRAFFIC.get(kernel), "kernel": kernel,
                          "binding_pipe": pipe,
-                         "peak_basis": f"{PIPE_LANES[pipe]} {pipe} results/SM/clk / "
+                         "peak_basis": f"{lanes[pipe]:.1f} {pipe} results/SM/clk "
+                                       f"({'measured by cs_unit_rates' if rates and pipe != 'int32' else 'nominal'}; "
+                                       f"nominal {PIPE_LANES[pipe]}) / "
                                        f"{pair_ops(head, Wk)[pipe]} per pair x {n_sm} SMs x "
-                                       f"{sm_mhz:.0f} MHz (median SM clock sampled under load)"},
+                                       f"{sm_mhz:.0f} MHz (median SM clock sampled under load)",
+                         "peak_nominal": alu_peak_pairs(head, Wk, sm_mhz, n_sm)[0]},
+            "error_vs_oracle": forms_out[head]["error_vs_oracle"],
+            "error_sample": f"{len(pix)} random pixels x all {pr.n_samples} samples (FP64 oracle, "
+                            "outside the timed region)",
+            "unit_rates": rates,
             "forms": forms_out,
             "smooth": {
                 "form": "mode 2: FP8 tensor-core Parzen colour-location sum, then the smooth "
@@ -570,7 +641,7 @@ def main():
                         f"{pr.params.iota_sigma}, median representatives, l1 softmax)",
                 "ms_per_step": res_smooth[0] / args.steps,
                 "pairs_per_s": pairs_rank * args.steps / (res_smooth[0] * 1e-3),
-                "stage_ms": res_smooth[2]},
+                "stage_ms": res_smooth[2], "error_vs_oracle": smooth_err},
             "segment": seg,
             "unsupervised": uns,
             "clocks": clocks,

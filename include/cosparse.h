@@ -593,6 +593,24 @@ cs_status cs_mlp_grad(cs_ctx* ctx, const float* params, int n_out, const float* 
                       const float* T, int rows, float* grads, float* loss, void* stream);
 
 /*
+ * Measured issue rates of the arithmetic pipes the pixel x sample sums use
+ * (a measurement aid for their rooflines; the paper has no counterpart):
+ * sustained results per SM per clock of ex2.approx (the special-function
+ * unit's exponential), popc, FFMA and the packed FFMA2 (fma.rn.f32x2, two
+ * results per instruction), from 8 independent chains per thread in one
+ * 1024-thread block per SM, each block timed by its SM's cycle counter (so
+ * the figures are per clock, whatever the clock frequency was).
+ *   out        HOST 4 doubles: ex2, popc, FFMA, FFMA2 results / SM / clock
+ *              (median over the SMs)
+ *   clock_mhz  HOST double or NULL: the SM clock implied by the slowest
+ *              block's cycles over the FFMA launch's event time
+ * Allocates a few KB, launches 8 short kernels (about a millisecond each) on
+ * the legacy default stream and synchronises the device.
+ * Errors: CS_ERR_INVALID_ARG (null ctx or out), CS_ERR_CUDA.
+ */
+cs_status cs_unit_rates(cs_ctx* ctx, double* out, double* clock_mhz);
+
+/*
  * Stage timing. While enabled, every call records a pair of CUDA events on
  * its stream around each stage it launches:
  *   CS_STAGE_CODES   patches, codes, bitmasks and the FP64 guard pass

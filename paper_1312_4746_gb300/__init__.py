@@ -73,6 +73,7 @@ EXPORTS = (
     "cs_mlp_param_count",
     "cs_mlp_forward",
     "cs_mlp_grad",
+    "cs_unit_rates",
     "cs_profile_enable",
     "cs_profile_read",
 )
@@ -253,6 +254,8 @@ def lib(path: str | None = None):
     L.cs_mlp_param_count.restype = I
     L.cs_mlp_forward.argtypes = [V, V, I, V, I, V, V]
     L.cs_mlp_grad.argtypes = [V, V, I, V, V, I, V, V, V]
+    L.cs_unit_rates.argtypes = [V, V, V]
+    L.cs_unit_rates.restype = I
     L.cs_profile_enable.argtypes = [V, I]
     L.cs_profile_read.argtypes = [V, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     for f in ("cs_create", "cs_sync_status", "cs_test_wait", "cs_refined_count", "cs_segment", "cs_codes", "cs_cosupport", "cs_likelihood",
@@ -296,6 +299,15 @@ class Context:
     def sync(self):
         """Wait for the current stream and raise on a device-side error."""
         self.check(self._lib.cs_sync_status(self.handle, _stream()))
+
+    def unit_rates(self):
+        """cs_unit_rates: measured results per SM per clock of ex2, popc, FFMA
+        and FFMA2, and the implied SM clock (MHz)."""
+        out = (ctypes.c_double * 4)()
+        clk = ctypes.c_double()
+        self.check(self._lib.cs_unit_rates(self.handle, out, ctypes.byref(clk)))
+        return {"ex2": out[0], "popc": out[1], "ffma": out[2], "ffma2": out[3],
+                "clock_mhz": clk.value}
 
     def test_wait(self, limit_ns: int = 0, stall: int = 0):
         """Timeout-path test hook (cs_test_wait): the limit of the bounded
