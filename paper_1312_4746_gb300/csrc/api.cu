@@ -659,8 +659,7 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
     T.imax2 = L.imax2;
     T.l_tol = (float)prm->l_tol;
     T.wait_ns = ctx->wait_ns;
-    T.stall = ctx->stall == CS_STALL_SUM;
-    if (T.stall) ctx->stall = CS_STALL_NONE;  // one-shot
+    T.stall = false;
     return T;
 }
 
@@ -680,8 +679,10 @@ static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
     StageTimer tm(ctx, CS_STAGE_SUM, st);
     if (!L.tc_form) return launch_sum_plain(cs_sum_args(L, img, bitmask, prm, neglog, post), st);
     ctx->last_fb_count = L.fb_count;
-    return launch_sum_tc(cs_tc_launch(ctx, L, img, bitmask, sample_pix, prm, neglog, post),
-                         sorted, st);
+    TcLaunch T = cs_tc_launch(ctx, L, img, bitmask, sample_pix, prm, neglog, post);
+    T.stall = ctx->stall == CS_STALL_SUM;  // the timeout-path test hook, one-shot
+    if (T.stall) ctx->stall = CS_STALL_NONE;
+    return launch_sum_tc(T, sorted, st);
 }
 
 extern "C" {
