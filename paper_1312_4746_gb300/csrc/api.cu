@@ -570,11 +570,14 @@ void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2) {
     L.t.rep = c.take<uint32_t>((size_t)n * Wk);
     L.t.blob = c.take<uint8_t>(L.tc_form ? (size_t)L.total_tiles * L.stage_bytes : 0, 1024);
     L.t.tile_xy = c.take<uint32_t>(L.tc_form ? (size_t)L.total_tiles * tc_tile_samples() : 0);
+    L.t.tile_xb = c.take<uint32_t>(L.tc_form ? (size_t)L.total_tiles * tc_tile_samples() : 0);
     L.t.perm = c.take<int32_t>(L.tc_form ? (size_t)S : 0);
     L.desc = c.take<TcImage>(L.tc_form ? 1 : 0);
     L.imax2 = c.take<float>(L.tc_form ? (size_t)n : 0);
     L.fb_list = c.take<int4>(L.tc_form ? (size_t)P : 0);
     L.fb_count = c.take<int>(L.tc_form ? 1 : 0);
+    L.queue = c.take<unsigned>(L.tc_form ? 2 : 0);
+    L.flags = c.take<unsigned long long>(L.tc_form ? (size_t)P : 0);
 }
 
 static cudaError_t enqueue_codes(cs_ctx* ctx, const CodesArgs& a, cudaStream_t st) {
@@ -654,8 +657,12 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
     T.persample = L.persample;
     T.desc = L.desc;
     T.first_item = 0;
+    T.pix_off = 0;
+    T.first_ptile = 0;
     T.fb_list = L.fb_list;
     T.fb_count = L.fb_count;
+    T.queue = L.queue;
+    T.flags = L.flags;
     T.imax2 = L.imax2;
     T.l_tol = (float)prm->l_tol;
     T.wait_ns = ctx->wait_ns;

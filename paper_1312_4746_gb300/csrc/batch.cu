@@ -77,11 +77,17 @@ struct cs_batch {
     TcImage* descs = nullptr;
     int4* fb_list = nullptr;  // FP64 recompute list over all images
     int* fb_count = nullptr;
+    unsigned* queue = nullptr;             // item counter of the sum launch
+    unsigned long long* flag_words = nullptr;   // per-pixel flag words over all images
     int total_pixels = 0;
     int n_streams = 4, order_mode = 0;
     std::vector<int> order;       // image index at each processing position
-    std::vector<int> first_item;  // first work item at each processing position
-    int n_items = 0;
+    // at each processing position: the number of its first item, its first
+    // pixel and first pixel tile in the launch, its (pixel tiles, labels)
+    std::vector<long long> first_item, pix_off;
+    std::vector<int> first_ptile;
+    std::vector<int2> shapes;
+    long long n_items = 0;
     double pairs = 0, tuned_ms = -1;
     bool tuned = false, ran = false;
     bool codes_given = false;  // likelihood only: the images' bitmasks are inputs
@@ -103,11 +109,21 @@ static void set_order(cs_batch* b, int n_streams, int order_mode) {
         std::stable_sort(b->order.begin(), b->order.end(),
                          [&](int x, int y) { return b->im[x].pairs > b->im[y].pairs; });
     b->first_item.resize(n);
-    int items = 0;
+    b->pix_off.resize(n);
+    b->first_ptile.resize(n);
+    b->shapes.resize(n);
+    long long items = 0, pix = 0;
+    int ptiles = 0;
     for (int s = 0; s < n; ++s) {
         b->first_item[s] = items;
+        b->pix_off[s] = pix;
+        b->first_ptile[s] = ptiles;
         const BatchImage& m = b->im[b->order[s]];
-        items += tc_pixel_tiles(m.L.H, m.L.W);
+        const int npt = tc_pixel_tiles(m.L.H, m.L.W);
+        b->shapes[s] = make_int2(npt, m.L.n_labels);
+        items += (long long)npt * m.L.n_labels;
+        pix += (long long)m.L.H * m.L.W;
+        ptiles += npt;
     }
     b->n_items = items;
 }
@@ -139,6 +155,8 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
                                       m.d.neglog, m.d.post);
             T.desc = b->descs + s;
             T.first_item = b->first_item[s];
+            T.pix_off = b->pix_off[s];
+            T.first_ptile = b->first_ptile[s];
             e = launch_tc_prepare(T, ss);
         } else {
             e = launch_sum_plain(cs_sum_args(L, m.d.img, m.codes.bitmask, &b->prm, m.d.neglog,
@@ -167,7 +185,12 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
                       (float)b->prm.l_tol,
                       b->prm.rho_variance != 0};
         p.wait_ns = ctx->wait_ns;
-        e = launch_tc_sum(b->descs, (int)b->order.size(), b->n_items, p, st);
+        p.n_items = b->n_items;
+        p.total_pixels = b->total_pixels;
+        p.shapes = b->shapes.data();
+        p.queue = b->queue;
+        p.flags = b->flag_words;
+        e = launch_tc_sum(b->descs, (int)b->order.size(), p, st);
     }
     return e;
 }
@@ -348,6 +371,8 @@ static cs_status batch_create(const char* fn, cs_ctx* ctx, const cs_image* image
         b->descs = c.take<TcImage>(b->tc ? (size_t)n_images : 0);
         b->fb_list = c.take<int4>(b->tc ? (size_t)b->total_pixels : 0);
         b->fb_count = c.take<int>(b->tc ? 1 : 0);
+        b->queue = c.take<unsigned>(b->tc ? 2 : 0);
+        b->flag_words = c.take<unsigned long long>(b->tc ? (size_t)b->total_pixels : 0);
     };
     Carve m0(nullptr);
     carve_all(m0);

@@ -255,6 +255,7 @@ struct SampleTables {
     uint32_t* rep;    // [n_labels][Wk]
     uint8_t* blob;    // tensor-core sample tiles (ring-stage layout)
     uint32_t* tile_xy;  // tensor-core tile slots: sample position x | y << 16
+    uint32_t* tile_xb;  // tensor-core tile slots: texture codes beyond the MMA slabs
     int32_t* perm;    // tensor-core sample order (Morton order in chunks of 4096)
 };
 cudaError_t launch_gather(const float* img, int H, int W, const uint32_t* bitmask, int k,
@@ -303,6 +304,8 @@ struct LikPlan {
     int4* fb_list;  // tensor-core form: FP64 recompute list (P entries) and count
     int* fb_count;
     float* imax2;   // tensor-core form: per label max |I_j|^2
+    unsigned* queue;             // tensor-core form: the sum launch's two claim counters
+    unsigned long long* flags;   // tensor-core form: per-pixel flag words
 };
 
 typedef LikPlan LikPlanRef;
@@ -330,7 +333,9 @@ cudaError_t cs_enqueue_exact_list(cs_ctx* ctx, const LikPlan& L, const float* im
 
 // Tensor-core (tcgen05) pixel x sample sum.
 // One image of a sum launch; the launch reads an array of these from device
-// memory, ordered by first_item, and processes items (image, pixel tile).
+// memory, in launch order (first_item ascending), and processes items
+// (image, pixel tile, label), numbered image by image, pixel tile by pixel
+// tile, label by label.
 struct TcImage {
     const float* img;
     const uint32_t* bitmask;
@@ -346,10 +351,13 @@ struct TcImage {
     const float *sx, *sy, *sr, *sg, *sb;
     const uint32_t* sbits;  // word-major [Wk][n_samples]
     const float* imax2;     // per label: max_j |I_j|^2 (error bound)
+    const uint32_t* tile_xb;  // per tile slot: texture codes beyond the MMA slabs
     int n_samples;
     int H, W, ntx, n_labels;
-    int first_item;  // work-item index of this image's first pixel tile
-    int pad[2];
+    int n_ptiles;          // pixel tiles of the image
+    int first_ptile;       // number of its first pixel tile in the launch
+    long long first_item;  // number of the image's first item in the launch
+    long long pix_off;     // its first pixel in the launch's flag words
 };
 struct TcSumParams {
     int k;
@@ -366,6 +374,14 @@ struct TcSumParams {
     bool rho_var;  // rho is the location kernel's variance (else its standard deviation)
     unsigned long long wait_ns = 0;  // limit of each bounded wait (0: the kernel's 1 s)
     bool stall = false;  // timeout-path test: one CTA waits on a barrier nobody completes
+    // the launch: items (image, pixel tile, label) and pixels over all
+    // images; per image in launch order (HOST) its pixel tiles and labels;
+    // the two claim counters (whole pixel tiles, then single items) and the
+    // per-pixel flag words (all cleared by the launch)
+    long long n_items = 0, total_pixels = 0;
+    const int2* shapes = nullptr;  // n_images x (pixel tiles, labels)
+    unsigned* queue = nullptr;
+    unsigned long long* flags = nullptr;
 };
 struct TcLaunch {
     const float* img;
@@ -391,9 +407,14 @@ struct TcLaunch {
     bool tex8;       // texture operands in FP8 (else BF16)
     bool persample;  // per-sample texture kernel (else factorised)
     TcImage* desc;   // device slot receiving this image's descriptor
-    int first_item;  // its first work item in the sum launch
+    // its place in the sum launch: number of its first item and of its first
+    // pixel tile, first pixel in the launch's flag words
+    long long first_item, pix_off;
+    int first_ptile;
     int4* fb_list;   // FP64 recompute list (H W entries) and its count
     int* fb_count;
+    unsigned* queue;             // the launch's two claim counters
+    unsigned long long* flags;   // flag words (one per pixel)
     float* imax2;    // per label max |I_j|^2 (written by the preparation)
     float l_tol;
     unsigned long long wait_ns;  // as TcSumParams
@@ -410,8 +431,9 @@ bool tc_supported(int k, bool tex8);
 cudaError_t launch_tc_sort(const TcLaunch& L, cudaStream_t st);
 cudaError_t launch_tc_tiles(const TcLaunch& L, cudaStream_t st);
 cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st);
-// One persistent launch over the items of n_images prepared images.
-cudaError_t launch_tc_sum(const TcImage* descs, int n_images, int n_items, const TcSumParams& p,
+// One persistent launch over the items of n_images prepared images (sizes,
+// counters and flag words in p).
+cudaError_t launch_tc_sum(const TcImage* descs, int n_images, const TcSumParams& p,
                           cudaStream_t st);
 // Preparation (the tiles only when `sorted`) and the sum, for a single image
 // (L.desc must be set).

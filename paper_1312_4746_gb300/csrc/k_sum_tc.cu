@@ -12,27 +12,41 @@
 // the location terms carry the magnitude of |x - x_j|^2 itself (no
 // cancellation between large offsets). One FP32 accumulator per sample
 // receives all of it from tcgen05 MMAs: the texture sum (an exact integer,
-// 2 b_x.b_j - |b_j|, so TSM = |b_x| minus it) from an FP8 (e4m3, values 0
-// and +-1) or BF16 MMA; the colour part from a 16-wide BF16 MMA over hi/lo
-// splits of both factors (relative error about 2^-17); the location part
-// from two 16-wide BF16 MMAs whose sample side is exact (2u in two bf16
-// pieces per axis, |u|^2 in four) and whose pixel side holds three-piece
-// splits of -f x' and f (relative error below 2^-24). The sample side of
-// the location is formed per (pixel tile, sample tile) by the producer from
-// the sample positions; the pixel side per label by the epilogue. In the
-// factorised form D1 holds the colour and location parts with Bt = 1.
+// 2 b_x.b_j - |b_j|, so TSM = |b_x| minus it) from FP8 (e4m3, values 0 and
+// +-1) or BF16 MMAs over whole 32-code (16-code) slabs, the last few codes
+// (k mod 32 or k mod 16, when at most EXT_MAX) riding in spare columns of
+// the second location slab as BF16 +-1 / 0; the colour part from a 16-wide
+// BF16 MMA over hi/lo splits of both factors (relative error about 2^-17);
+// the location part from two 16-wide BF16 MMAs whose sample side is exact
+// (2u in two bf16 pieces per axis, |u|^2 in four) and whose pixel side
+// holds three-piece splits of -f x' and f (relative error below 2^-24). The
+// sample side of the location is formed per (pixel tile, sample tile) by the
+// producer from the sample positions; the pixel side per label by the
+// epilogue. In the factorised form D1 holds the colour and location parts
+// with Bt = 1.
 //
 // All full exponents are <= 0, so no running maximum is needed: the row sum
 // accumulates 2^(e + shift) with a fixed shift 96 - ceil(log2 m_i) (no term
 // above 2^96 / m_i, no overflow), in packed f32x2 arithmetic, TwoSum-
-// compensated across 16-sample chunks. A pixel goes to the FP64 recompute
-// (refine_fp64_kernel) when one of its label rows totals less than
-// m_i 2^-100 (terms may have underflowed) or when the row's a-priori error
-// bound exceeds l_tol max(|L|, 1) (derivation at the flagging site).
+// compensated across 16-sample chunks. A label row goes to the FP64
+// recompute (refine_fp64_kernel) when it totals less than m_i 2^-100 (terms
+// may have underflowed) or when its a-priori error bound exceeds
+// l_tol max(|L|, 1) (derivation at the flagging site).
+//
+// Work items are (image, 16 x 8 pixel tile, label): all sample tiles of one
+// label for one pixel tile (one TMEM lane per pixel, one TMEM column per
+// sample of a 128-sample tile), numbered image by image, pixel tile by pixel
+// tile, label by label. The persistent CTAs claim work from global counters:
+// whole pixel tiles (all their labels, consecutive items) until about one
+// pixel tile per CTA is left, then single items, each CTA one claim ahead of
+// its producers, so that the two CTAs sharing an SM, which do not run at the
+// same speed, and all SMs finish within about one item of each other. A CTA
+// passes its claims (runs of consecutive items) to its roles through a small
+// ring in shared memory. The label normalisation runs in a separate pass
+// once every label row is written.
 //
 // Two persistent CTAs per SM (one where the shared-memory layout does not
-// fit twice); a pixel tile is 16 x 8 pixels (one TMEM lane each), a sample
-// tile 128 samples (one TMEM column each).
+// fit twice).
 //   warps 8..11  producers: per stage, one bulk-copies (TMA) the
 //                pre-laid-out texture and colour slabs of a sample tile, and
 //                all four write its two location slabs for this pixel tile
@@ -40,11 +54,13 @@
 //   warp 12      MMA issuer: D1 <- texture slabs + colour slab + location
 //                slabs; TMEM double-buffered (2 x 128 columns per CTA), so
 //                one tile's MMAs run while the epilogue reads the previous
-//   warps 0..7   epilogue: per label, writes the pixel-side colour and
-//                location rows; warp w reads lanes 32 (w % 4) .. +31 and
-//                columns 64 (w / 4) .. +63 of each tile (16-column loads),
-//                merges the two column parts per label and normalises over
-//                labels (16 warps of 32 columns in the one-CTA layout).
+//   warps 0..7   epilogue: writes the pixel-side colour and location rows
+//                of the NEXT item while it sums the current one (two label
+//                buffers), so that the MMAs run on across label boundaries;
+//                warp w reads lanes 32 (w % 4) .. +31 and columns
+//                64 (w / 4) .. +63 of each tile (16-column loads), merges the
+//                two column parts per item (16 warps of 32 columns in the
+//                one-CTA layout).
 // Every mbarrier wait is bounded by the global timer; on expiry the CTA sets
 // the device error word, stops issuing, drains its copies and MMAs, frees its
 // tensor memory and exits.
@@ -71,28 +87,85 @@ constexpr uint32_t SUSPEND_NS = 1000u;       // longest suspension of one barrie
 constexpr float FLOOR_PER_SAMPLE = 7.888609052210118e-31f;  // 2^-100
 
 struct TcArgs {
-    const TcImage* images;  // n_images descriptors, ordered by first_item
-    int n_images, n_items;  // work items: (image, pixel tile) pairs
+    const TcImage* images;  // n_images descriptors, in launch (first_item) order
+    int n_images;
+    long long n_items;      // items over all images
+    long long total_pixels; // pixels over all images
+    int pt1;                // pixel tiles claimed whole, with all their labels
+    long long i1;           // first item claimed on its own (the rest, after them)
     int k, Wk;
+    int ext;                // texture codes carried in the second location slab
     float alpha, d_min, kappa_beta, sigma_c2;
     bool rho_var;   // rho is the location kernel's variance (else its standard deviation)
     int* d_err;
-    int4* fb_list;  // (image, pixel, flagged-label mask low, high) to recompute
+    int4* fb_list;  // (image, pixel) of pixels with flagged label rows
     int* fb_count;
     int fb_cap;
+    unsigned* queue;           // claim counters: whole pixel tiles, single items
+    unsigned long long* flags; // per pixel: label rows flagged for the FP64 recompute
     float l_tol;    // relative tolerance on L of the a-priori row bound (0: off)
     uint64_t wait_ns;  // time limit of each barrier wait (0: WAIT_NS)
     bool stall;        // the MMA issuer of the last CTA waits on a barrier nobody completes
 };
 
-// Image of work item g: the last descriptor whose first item is <= g.
-__device__ __forceinline__ int image_of(const TcArgs& a, int g) {
+// A work item: image, pixel tile, label (img == -1: no more items).
+struct Item {
+    int img, pt, lab;
+};
+
+// Item number n (0 <= n < n_items), or none.
+__device__ Item item_of(const TcArgs& a, long long n) {
+    Item it{-1, 0, 0};
+    if (n < 0 || n >= a.n_items) return it;
+    int lo = 0, hi = a.n_images - 1;  // the last image whose first item is <= n
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.images[mid].first_item <= n) lo = mid; else hi = mid - 1;
+    }
+    const TcImage& m = a.images[lo];
+    const long long local = n - m.first_item;
+    it.img = lo;
+    it.pt = (int)(local / m.n_labels);
+    it.lab = (int)(local - (long long)it.pt * m.n_labels);
+    return it;
+}
+
+// Image of pixel tile number t of the launch (the last image whose first
+// pixel tile is <= t).
+__device__ __forceinline__ int ptile_image(const TcArgs& a, int t) {
     int lo = 0, hi = a.n_images - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (a.images[mid].first_item <= g) lo = mid; else hi = mid - 1;
+        if (a.images[mid].first_ptile <= t) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Ring of claims in shared memory: entry e (a run of consecutive item
+// numbers: first, count; count 0 marks the end) sits in slot e % QD;
+// q_full[slot] completes when it is written, q_empty[slot] when every reader
+// has taken it. Depth QD covers the claimer's lead over the slowest reader
+// (one claim of look-ahead, the producers' sample tiles in flight and the
+// epilogue's one item of look-ahead, each item at least one tile).
+constexpr int QD = 16;
+
+// A reader's place in the ring: the entry it holds and the item within it.
+struct RingPos {
+    int e = -1, first = 0, count = 0, k = 0;
+};
+
+// Texture codes in the MMA slabs and in the second location slab: whole
+// slabs of 32 (FP8) or 16 (BF16) codes, and the remaining k mod 32 (16)
+// codes in the location slab's EXT_MAX spare columns when they fit there,
+// else one more slab.
+constexpr int EXT_MAX = 11;
+__host__ __device__ constexpr int tex_slabs(int k, bool tex8) {
+    return tex8 ? (k % 32 <= EXT_MAX ? k / 32 : k / 32 + 1)
+                : (k % 16 <= EXT_MAX ? k / 16 : k / 16 + 1);
+}
+__host__ __device__ constexpr int tex_ext(int k, bool tex8) {
+    return k - tex_slabs(k, tex8) * (tex8 ? 32 : 16) > 0 ? k - tex_slabs(k, tex8) * (tex8 ? 32 : 16)
+                                                           : 0;
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
@@ -106,20 +179,22 @@ struct Cfg {
     static constexpr int stage_bytes = tex_bytes + 3 * 4096;
     static constexpr int NB = 2;                              // D1 accumulators (128 columns each)
     static constexpr uint32_t TMEM_COLS = 128u * NB;
-    static constexpr int XB = 2 * NB;                         // label-merge exchange buffers
+    static constexpr int XB = 2 * NB;                         // item-merge exchange buffers
     static constexpr int AP = 3 * 4096;                       // pixel-side colour + L0 + L1 slabs
     // Two CTAs per SM (each 256 TMEM columns, a sample ring of two or more
     // stages, 8 epilogue warps) when that layout fits twice in the SM's
     // 228 KB (a CTA of the pair may use 228 KB / 2 - 1 KB, the per-CTA
-    // reservation), with two label buffers of pixel-side operands or, if only
-    // that fits, one; else one CTA per SM with 16 epilogue warps.
+    // reservation), else one CTA per SM with 16 epilogue warps. Two label
+    // buffers of pixel-side operands always (the next item's are written
+    // while the current one is summed); the sample ring as deep as fits (2 to
+    // 4 stages) and, if room is left, two pixel-tile texture buffers.
     static constexpr int PAIR_LIMIT = 228 * 1024 / 2 - 1024;
-    static constexpr int pair_bytes(int stages, int acb) {
-        return stages * stage_bytes + tex_bytes + acb * AP + XB * 1 * 4 * 32 * 8 +
-               (2 * stages + 27) * 8 + 16;
+    static constexpr int MISC = 16 + 8 * QD;  // TMEM base, abort flag, claim ring
+    static constexpr int bytes(int stages, int atb, int epq) {
+        return stages * stage_bytes + atb * tex_bytes + 2 * AP + XB * (epq - 1) * 4 * 32 * 8 +
+               (2 * stages + 2 * NB + 4 + 2 * atb + 4 * XB + 1 + 2 * QD) * 8 + MISC;
     }
-    static constexpr bool PAIR = pair_bytes(2, 1) <= PAIR_LIMIT;
-    static constexpr int ACB = !PAIR || pair_bytes(2, 2) <= PAIR_LIMIT ? 2 : 1;  // label buffers
+    static constexpr bool PAIR = bytes(2, 1, 2) <= PAIR_LIMIT;
     static constexpr int MIN_BLOCKS = PAIR ? 2 : 1;
     static constexpr int EPQ = PAIR ? 2 : 4;                 // epilogue warps per TMEM lane quadrant
     static constexpr int EPI_WARPS = 4 * EPQ;
@@ -128,23 +203,25 @@ struct Cfg {
     static constexpr int PRODUCER = EPI_WARPS;
     static constexpr int MMA_WARP = EPI_WARPS + NPROD;
     static constexpr int THREADS = (EPI_WARPS + NPROD + 1) * 32;
-    // sample-tile ring depth: as deep as the shared memory allows (2 to 4)
-    static constexpr int STAGES = !PAIR                          ? (KS <= 5 ? 4 : 3)
-                                  : pair_bytes(4, ACB) <= PAIR_LIMIT ? 4
-                                  : pair_bytes(3, ACB) <= PAIR_LIMIT ? 3 : 2;
+    static constexpr int LIMIT = PAIR ? PAIR_LIMIT : 227 * 1024;
+    // two pixel-tile texture buffers whenever they fit with a two-stage ring
+    // (claimed items seldom share a pixel tile), then the ring as deep as fits
+    static constexpr int ATB = bytes(2, 2, EPQ) <= LIMIT ? 2 : 1;
+    static constexpr int STAGES = bytes(4, ATB, EPQ) <= LIMIT ? 4 : bytes(3, ATB, EPQ) <= LIMIT ? 3 : 2;
     // shared memory map
     static constexpr int ring_off = 0;
     static constexpr int atex_off = ring_off + STAGES * stage_bytes;
-    static constexpr int acol_off = atex_off + tex_bytes;
-    static constexpr int xchg_off = acol_off + ACB * AP;              // [XB][EPQ-1][4][32] float2
+    static constexpr int acol_off = atex_off + ATB * tex_bytes;
+    static constexpr int xchg_off = acol_off + 2 * AP;               // [XB][EPQ-1][4][32] float2
     static constexpr int bar_off = xchg_off + XB * (EPQ - 1) * 4 * 32 * 8;
-    static constexpr int n_bars = 2 * STAGES + 2 + 2 + 2 + 2 + 2 + 16 + 1;
+    static constexpr int n_bars = 2 * STAGES + 2 * NB + 4 + 2 * ATB + 4 * XB + 1 + 2 * QD;
     static constexpr int misc_off = bar_off + n_bars * 8;
     // a floor on the shared memory keeps a third CTA (or, unpaired, a
     // second) off the SM, so that tensor memory allocation never waits
     static constexpr int smem_floor = PAIR ? 80 * 1024 : 120 * 1024;
-    static constexpr int smem_bytes = misc_off + 16 > smem_floor ? misc_off + 16 : smem_floor;
-    static_assert(!PAIR || misc_off + 16 == pair_bytes(STAGES, ACB), "two-CTA layout size");
+    static constexpr int smem_bytes = misc_off + MISC > smem_floor ? misc_off + MISC : smem_floor;
+    static_assert(misc_off + MISC == bytes(STAGES, ATB, EPQ), "layout size");
+    static_assert(bytes(STAGES, ATB, EPQ) <= LIMIT, "shared-memory layout");
     static constexpr uint32_t id_tex = TEX8 ? tc::idesc(BM, BN, 0, 0) : tc::idesc(BM, BN, 1, 1);
     static constexpr uint32_t id_bf16 = tc::idesc(BM, BN, 1, 1);
 };
@@ -219,23 +296,26 @@ __device__ __forceinline__ int tiles_of(const int32_t* tile_off, int i) {
 // Sample-side location rows (two 16-wide slabs L0, L1) of a sample at
 // packed position w (x | y << 16) relative to the pixel tile's centre
 // (cx, cy), u = x_j - centre: 2u per axis in two exact bf16 pieces (h, l),
-// |u|^2 (< 2^31) in four exact bf16 pieces q0..q3:
+// |u|^2 (< 2^31) in four exact bf16 pieces q0..q3, then the sample's
+// remaining texture codes xb (bit e: code 32 KS + e, or 16 KS + e) as bf16
+// 1 / 0:
 //   L0 = [hx lx hx lx hx lx  hy ly hy ly hy ly  q0 q1 q2 q3],
-//   L1 = [q0 q1 q2 q0 q1 0 ...];
+//   L1 = [q0 q1 q2 q0 q1  b0 .. b10];
 // the pixel side holds the matching pieces of -f x' and f (see the
-// epilogue). The pieces are bit fields of the integers (at most 8
-// significant bits each, so exact in bf16): 2u = (2u & ~255) + (2u & 255)
-// and |u|^2 by bytes from its leading bit down. A padded sample has
-// q0 = 2^30 and zeros elsewhere, so that its exponent vanishes.
+// epilogue) and +-1 for the texture codes. The pieces are bit fields of the
+// integers (at most 8 significant bits each, so exact in bf16):
+// 2u = (2u & ~255) + (2u & 255) and |u|^2 by bytes from its leading bit
+// down. A padded sample has q0 = 2^30 and zeros elsewhere, so that its
+// exponent vanishes.
 __device__ __forceinline__ uint32_t bf16_exact(int v) {  // v has <= 8 significant bits
     return __float_as_uint((float)v) >> 16;
 }
-__device__ __forceinline__ void loc_row_b(uint32_t w, int cx, int cy, bool valid, uint4& l0a,
-                                          uint4& l0b, uint4& l1a) {
+__device__ __forceinline__ void loc_row_b(uint32_t w, uint32_t xb, int cx, int cy, bool valid,
+                                          uint4& l0a, uint4& l0b, uint4& l1a, uint4& l1b) {
     if (!valid) {
         l0a = make_uint4(0, 0, 0, 0);
         l0b = make_uint4(0, 0, bf16_exact(1 << 30), 0);
-        l1a = make_uint4(0, 0, 0, 0);
+        l1a = l1b = make_uint4(0, 0, 0, 0);
         return;
     }
     const int ux = (int)(w & 0xFFFFu) - cx, uy = (int)(w >> 16) - cy;  // |u| < 2^15
@@ -253,7 +333,10 @@ __device__ __forceinline__ void loc_row_b(uint32_t w, int cx, int cy, bool valid
                    q3 = bf16_exact((int)(q & ((1u << k2) - 1u)));
     l0a = make_uint4(px, px, px, py);
     l0b = make_uint4(py, py, q0 | (q1 << 16), q2 | (q3 << 16));
-    l1a = make_uint4(q0 | (q1 << 16), q2 | (q0 << 16), q1, 0);
+    auto b = [xb](int e) -> uint32_t { return ((xb >> e) & 1u) ? 0x3F80u : 0u; };
+    l1a = make_uint4(q0 | (q1 << 16), q2 | (q0 << 16), q1 | (b(0) << 16), b(1) | (b(2) << 16));
+    l1b = make_uint4(b(3) | (b(4) << 16), b(5) | (b(6) << 16), b(7) | (b(8) << 16),
+                     b(9) | (b(10) << 16));
 }
 
 // Three bf16 pieces of an FP32 value (each the rounding of the exact
@@ -330,11 +413,71 @@ __device__ __forceinline__ void two_sum(float ts, float& S, float& Cc) {
     S = sn;
 }
 
+// Label normalisation of one pixel once every label row is in the output
+// plane: the factorised form's majority-co-support texture posterior is added
+// first, then the posteriors softmax_i L_i.
+template <bool PERSAMPLE>
+__device__ void normalise_pixel(const TcArgs& a, const TcImage& im, int pix, const uint32_t* bxp) {
+    const long long P = (long long)im.H * im.W;
+    float* nl = im.neglog + pix;
+    if (!PERSAMPLE && im.rep) {  // factorised: the majority-co-support posterior
+        float tmax = -INFINITY;
+        for (int i = 0; i < im.n_labels; ++i) {
+            const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
+            int h = 0;
+            for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
+            tmax = fmaxf(tmax, -LOG2E * (float)h / (a.kappa_beta * rho));
+        }
+        float ts = 0.f;
+        for (int i = 0; i < im.n_labels; ++i) {
+            const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
+            int h = 0;
+            for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
+            ts += ex2f(-LOG2E * (float)h / (a.kappa_beta * rho) - tmax);
+        }
+        const float tl = tmax + log2f(ts);
+        for (int i = 0; i < im.n_labels; ++i) {
+            const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
+            int h = 0;
+            for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
+            nl[(size_t)i * P] = nl[(size_t)i * P] -
+                                (-LOG2E * (float)h / (a.kappa_beta * rho) - tl) * LN2;
+        }
+    }
+    float lmax = -INFINITY;
+    for (int i = 0; i < im.n_labels; ++i) lmax = fmaxf(lmax, -nl[(size_t)i * P]);
+    float ls = 0.f;
+    for (int i = 0; i < im.n_labels; ++i) ls += expf(-nl[(size_t)i * P] - lmax);
+    const float lse = lmax + logf(ls);
+    if (im.post)
+        for (int i = 0; i < im.n_labels; ++i)
+            im.post[(size_t)i * P + pix] = expf(-nl[(size_t)i * P] - lse);
+}
+
+// The normalisation pass after the sum: one thread per pixel of every image
+// of the launch; pixels with a flagged label row are left to the FP64
+// recompute, which normalises them in double.
+template <bool PERSAMPLE>
+__global__ void __launch_bounds__(256) normalise_kernel(TcArgs a) {
+    for (long long gp = blockIdx.x * 256ll + threadIdx.x; gp < a.total_pixels;
+         gp += (long long)gridDim.x * 256) {
+        int lo = 0, hi = a.n_images - 1;  // the last image whose first pixel is <= gp
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.images[mid].pix_off <= gp) lo = mid; else hi = mid - 1;
+        }
+        const TcImage& im = a.images[lo];
+        const int pix = (int)(gp - im.pix_off);
+        if (a.flags[gp] != 0ull) continue;
+        normalise_pixel<PERSAMPLE>(a, im, pix, im.bitmask + (size_t)pix * a.Wk);
+    }
+}
+
 template <bool TEX8, int KS, bool PERSAMPLE>
 __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
                                   (Cfg<TEX8, KS, PERSAMPLE>::MIN_BLOCKS)) sum_tc_kernel(TcArgs a) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
-    constexpr int EPQ = C::EPQ, EPI_WARPS = C::EPI_WARPS, CPW = C::CPW, NB = C::NB;
+    constexpr int EPQ = C::EPQ, EPI_WARPS = C::EPI_WARPS, CPW = C::CPW, NB = C::NB, ATB = C::ATB;
     constexpr int PRODUCER = C::PRODUCER, MMA_WARP = C::MMA_WARP;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ring = smem + C::ring_off;
@@ -342,18 +485,22 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
     uint8_t* acol = smem + C::acol_off;
     float2* xchg = reinterpret_cast<float2*>(smem + C::xchg_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::bar_off);
-    uint64_t* full = bars;                    // [C::STAGES] producer arrival + TMA bytes
-    uint64_t* empty = bars + C::STAGES;          // [C::STAGES] MMA commit
-    uint64_t* tmem_full = bars + 2 * C::STAGES;  // [2] MMA commit
-    uint64_t* tmem_empty = tmem_full + 2;     // [2] epilogue warps
-    uint64_t* acol_full = tmem_full + 4;      // [2] epilogue warps
-    uint64_t* acol_empty = tmem_full + 6;     // [2] MMA commit
-    uint64_t* atex_full = tmem_full + 8;      // [1] epilogue warps
-    uint64_t* atex_empty = tmem_full + 9;     // [1] MMA commit
-    uint64_t* xchg_full = tmem_full + 10;     // [4 buffers][4 quadrants]
-    uint64_t* stall_bar = tmem_full + 26;     // [1] nobody arrives (timeout-path tests)
+    uint64_t* full = bars;                        // [STAGES] producer arrivals + TMA bytes
+    uint64_t* empty = full + C::STAGES;           // [STAGES] MMA commit
+    uint64_t* tmem_full = empty + C::STAGES;      // [NB] MMA commit
+    uint64_t* tmem_empty = tmem_full + NB;        // [NB] epilogue warps
+    uint64_t* acol_full = tmem_empty + NB;        // [2] epilogue warps
+    uint64_t* acol_empty = acol_full + 2;         // [2] MMA commit
+    uint64_t* atex_full = acol_empty + 2;         // [ATB] epilogue warps
+    uint64_t* atex_empty = atex_full + ATB;       // [ATB] MMA commit
+    uint64_t* xchg_full = atex_empty + ATB;       // [XB buffers][4 quadrants]
+    uint64_t* stall_bar = xchg_full + 4 * C::XB;  // [1] nobody arrives (timeout-path tests)
+    uint64_t* q_full = stall_bar + 1;             // [QD] item ring: entry written
+    uint64_t* q_empty = q_full + QD;              // [QD] item ring: entry read by every reader
     uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + C::misc_off);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::misc_off + 4);
+    int* qfirst = reinterpret_cast<int*>(smem + C::misc_off + 16);  // [QD] first item of a claim
+    int* qcount = qfirst + QD;                                      // [QD] its items, 0: end
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t wait_ns = a.wait_ns ? a.wait_ns : WAIT_NS;
@@ -363,16 +510,25 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
             tc::mbar_init(full + s, C::NPROD);
             tc::mbar_init(empty + s, 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NB; ++b) {
             tc::mbar_init(tmem_full + b, 1);
             tc::mbar_init(tmem_empty + b, EPI_WARPS);
+        }
+        for (int b = 0; b < 2; ++b) {
             tc::mbar_init(acol_full + b, EPI_WARPS);
             tc::mbar_init(acol_empty + b, 1);
         }
-        tc::mbar_init(atex_full, EPI_WARPS);
-        tc::mbar_init(atex_empty, 1);
-        for (int x = 0; x < 16; ++x) tc::mbar_init(xchg_full + x, EPQ - 1);
+        for (int b = 0; b < ATB; ++b) {
+            tc::mbar_init(atex_full + b, EPI_WARPS);
+            tc::mbar_init(atex_empty + b, 1);
+        }
+        for (int x = 0; x < 4 * C::XB; ++x) tc::mbar_init(xchg_full + x, EPQ - 1);
         tc::mbar_init(stall_bar, 1);
+        for (int x = 0; x < QD; ++x) {
+            tc::mbar_init(q_full + x, 1);
+            // readers: the producer warps, the MMA issuer, the epilogue warps
+            tc::mbar_init(q_empty + x, C::NPROD + 1 + EPI_WARPS);
+        }
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -384,74 +540,133 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_base_s;
+    // the next item number of a reader (-1: no more items), from its current
+    // claim or the next ring entry; `single`: one thread reads (the MMA
+    // issuer), else a whole warp (lane 0 releases the slot)
+    auto next_num = [&](RingPos& r, int& num, bool single) {
+        if (r.e >= 0 && r.k + 1 < r.count) {
+            num = r.first + ++r.k;
+            return true;
+        }
+        ++r.e;
+        const int slot = r.e % QD;
+        const uint32_t par = (uint32_t)((r.e / QD) & 1);
+        if (!(single ? spin_bar(q_full + slot, par, abort_flag, a.d_err, 14, wait_ns)
+                     : spin_warp(q_full + slot, par, abort_flag, a.d_err, 13, wait_ns)))
+            return false;
+        r.first = qfirst[slot];
+        r.count = qcount[slot];
+        r.k = 0;
+        if (!single) __syncwarp();
+        if (single || (threadIdx.x & 31) == 0) tc::mbar_arrive(q_empty + slot);
+        num = r.count > 0 ? r.first : -1;
+        return true;
+    };
 
     if (warp >= PRODUCER && warp < PRODUCER + C::NPROD) {
         const int pw = warp - PRODUCER;  // producer warp: rows 32 u + lane, u = pw mod NPROD
         // ------------------------------------------------------------ producer
         uint32_t it = 0;  // tiles issued by this CTA (< 2^32 in any launch)
         bool ok = true;
-        // the upper half of every L1 row stays zero (made visible to the
-        // tensor cores by the proxy fence of each stage's first fill)
-        for (int s = 0; s < C::STAGES; ++s)
-            for (int j = 32 * pw + lane; j < BN; j += 32 * C::NPROD)
-                *reinterpret_cast<uint4*>(ring + s * C::stage_bytes + C::bl_off + 4096 +
-                                          tc::slab_off(j, 16)) = make_uint4(0, 0, 0, 0);
-        for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x) {
-            const TcImage& im = a.images[image_of(a, g)];
-            const int pt = g - im.first_item;
-            // centre of the pixel tile: the origin of the location operands
-            const int cx = (pt % im.ntx) * TW + TW / 2, cy = (pt / im.ntx) * TH + TH / 2;
-            // the image's tiles are contiguous over its labels: walk them in
-            // order, with the next tile's sample positions fetched one tile
-            // ahead
-            const int T1 = im.tile_off[im.n_labels];
-            int i = 0, lab_first = im.tile_off[0], lab_end = im.tile_off[1];
-            int m_i = im.label_off[1] - im.label_off[0];
-            constexpr int RV = BN / 32 / C::NPROD;  // rows of 32 samples per producer warp
-            uint32_t w_next[RV];  // positions of samples 32 (pw + NPROD v) + lane of a tile
-#pragma unroll
-            for (int v = 0; v < RV; ++v)
-                w_next[v] = im.tile_xy[(size_t)lab_first * BN + 32 * (pw + C::NPROD * v) + lane];
-            for (int T = lab_first; ok && T < T1; ++T, ++it) {
-                if (T == lab_end) {  // every label has at least one tile
-                    ++i;
-                    lab_first = T;
-                    lab_end = im.tile_off[i + 1];
-                    m_i = im.label_off[i + 1] - im.label_off[i];
+        constexpr int RV = BN / 32 / C::NPROD;  // rows of 32 samples per producer warp
+        int nclaimed = 0;           // warp 0: ring entries written
+        bool claims_ended = false;  // warp 0: the end marker is written
+        bool single = false;        // warp 0: the whole pixel tiles are gone
+        RingPos rp;
+        while (ok) {
+            // warp 0 keeps the ring one claim ahead of its own reads: the
+            // claim after the one it is about to start (the epilogue prepares
+            // each next item's operands while it sums the current one)
+            if (pw == 0) {
+                while (!claims_ended && nclaimed <= rp.e + 2) {
+                    const int slot = nclaimed % QD;
+                    ok = spin_warp(q_empty + slot, (uint32_t)(((nclaimed / QD) & 1) ^ 1), abort_flag,
+                                   a.d_err, 12, wait_ns);
+                    if (!ok) break;
+                    int cnt = 0;
+                    if (lane == 0) {
+                        int first = 0;
+                        if (!single) {
+                            const unsigned t = atomicAdd(a.queue, 1u);
+                            if ((long long)t < a.pt1) {
+                                const int g = ptile_image(a, (int)t);
+                                const TcImage& m = a.images[g];
+                                first = (int)(m.first_item + (long long)(t - m.first_ptile) * m.n_labels);
+                                cnt = m.n_labels;
+                            } else {
+                                single = true;
+                            }
+                        }
+                        if (single) {
+                            const long long i = a.i1 + atomicAdd(a.queue + 1, 1u);
+                            first = (int)i;
+                            cnt = i < a.n_items ? 1 : 0;
+                        }
+                        qfirst[slot] = first;
+                        qcount[slot] = cnt;
+                        tc::mbar_arrive(q_full + slot);  // releases the entry to the readers
+                    }
+                    cnt = __shfl_sync(0xffffffffu, cnt, 0);
+                    single = __shfl_sync(0xffffffffu, (int)single, 0) != 0;
+                    claims_ended = cnt == 0;
+                    ++nclaimed;
                 }
-                uint32_t w[RV];
+                if (!ok) break;
+            }
+            int num = -1;
+            ok = next_num(rp, num, false);
+            if (!ok || num < 0) break;
+            const Item itm = item_of(a, num);
+            const TcImage& im = a.images[itm.img];
+            // centre of the pixel tile: the origin of the location operands
+            const int cx = (itm.pt % im.ntx) * TW + TW / 2, cy = (itm.pt / im.ntx) * TH + TH / 2;
+            const int T0 = im.tile_off[itm.lab], T1 = im.tile_off[itm.lab + 1];
+            const int m_i = im.label_off[itm.lab + 1] - im.label_off[itm.lab];
+            // sample positions (and extra texture bits) one tile ahead
+            uint32_t w_next[RV], x_next[RV];
+#pragma unroll
+            for (int v = 0; v < RV; ++v) {
+                const size_t slot = (size_t)T0 * BN + 32 * (pw + C::NPROD * v) + lane;
+                w_next[v] = im.tile_xy[slot];
+                x_next[v] = a.ext ? im.tile_xb[slot] : 0u;
+            }
+            for (int T = T0; ok && T < T1; ++T, ++it) {
+                uint32_t w[RV], xb[RV];
 #pragma unroll
                 for (int v = 0; v < RV; ++v) {
                     w[v] = w_next[v];
-                    if (T + 1 < T1)
-                        w_next[v] = im.tile_xy[(size_t)(T + 1) * BN + 32 * (pw + C::NPROD * v) + lane];
-                }
-                {
-                    const int s = (int)(it % C::STAGES);
-                    const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
-                    ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1, wait_ns);
-                    if (!ok) break;
-                    uint8_t* st = ring + s * C::stage_bytes;
-                    const int nvalid = min(BN, m_i - (T - lab_first) * BN);
-                    // the copy first, so that it lands while the location
-                    // slabs are written; the arrival follows them
-                    if (pw == 0 && lane == 0) {
-                        tc::mbar_expect_tx(full + s, C::copy_bytes);
-                        tc::bulk_g2s(st, im.blob + (size_t)T * C::copy_bytes, C::copy_bytes, full + s);
+                    xb[v] = x_next[v];
+                    if (T + 1 < T1) {
+                        const size_t slot = (size_t)(T + 1) * BN + 32 * (pw + C::NPROD * v) + lane;
+                        w_next[v] = im.tile_xy[slot];
+                        if (a.ext) x_next[v] = im.tile_xb[slot];
                     }
+                }
+                const int s = (int)(it % C::STAGES);
+                const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
+                ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1, wait_ns);
+                if (!ok) break;
+                uint8_t* st = ring + s * C::stage_bytes;
+                const int nvalid = min(BN, m_i - (T - T0) * BN);
+                // the copy first, so that it lands while the location slabs
+                // are written; the arrival follows them
+                if (pw == 0 && lane == 0) {
+                    tc::mbar_expect_tx(full + s, C::copy_bytes);
+                    tc::bulk_g2s(st, im.blob + (size_t)T * C::copy_bytes, C::copy_bytes, full + s);
+                }
 #pragma unroll
-                    for (int v = 0; v < RV; ++v) {
-                        const int j = 32 * (pw + C::NPROD * v) + lane;
-                        uint4 l0a, l0b, l1a;
-                        loc_row_b(w[v], cx, cy, j < nvalid, l0a, l0b, l1a);
-                        *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 0)) = l0a;
-                        *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 16)) = l0b;
-                        *reinterpret_cast<uint4*>(st + C::bl_off + 4096 + tc::slab_off(j, 0)) = l1a;
-                    }
-                    tc::fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(full + s);
+                for (int v = 0; v < RV; ++v) {
+                    const int j = 32 * (pw + C::NPROD * v) + lane;
+                    uint4 l0a, l0b, l1a, l1b;
+                    loc_row_b(w[v], xb[v], cx, cy, j < nvalid, l0a, l0b, l1a, l1b);
+                    *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 0)) = l0a;
+                    *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 16)) = l0b;
+                    *reinterpret_cast<uint4*>(st + C::bl_off + 4096 + tc::slab_off(j, 0)) = l1a;
+                    *reinterpret_cast<uint4*>(st + C::bl_off + 4096 + tc::slab_off(j, 16)) = l1b;
                 }
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(full + s);
             }
         }
         // drain: copies still in flight must land before the CTA exits
@@ -462,54 +677,73 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t it = 0, li = 0, lpt = 0;
+            uint32_t it = 0, li = 0, ptc = 0;  // tiles, items, pixel tiles started
             bool ok = true;
             long long last = -1;
             // test hook: nothing has been issued yet, so every other role
             // drains cleanly once this wait gives up and raises the abort flag
             if (a.stall && blockIdx.x == gridDim.x - 1)
                 ok = spin_bar(stall_bar, 0, abort_flag, a.d_err, 2, wait_ns);
-            for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x, ++lpt) {
-                const TcImage& im = a.images[image_of(a, g)];
-                ok = spin_bar(atex_full, (uint32_t)(lpt & 1), abort_flag, a.d_err, 3, wait_ns);
-                for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
-                    const int cb = (int)(li % C::ACB);
-                    ok = spin_bar(acol_full + cb, (uint32_t)((li / C::ACB) & 1), abort_flag, a.d_err, 4, wait_ns);
-                    const int nt = tiles_of(im.tile_off, i);
-                    const uint8_t* ap = acol + cb * C::AP;  // colour, L0, L1 slabs of this label
-                    for (int t = 0; ok && t < nt; ++t, ++it) {
-                        const int s = (int)(it % C::STAGES), b = (int)(it % NB);
-                        ok = spin_bar(full + s, (uint32_t)((it / C::STAGES) & 1), abort_flag, a.d_err, 5, wait_ns) &&
-                             spin_bar(tmem_empty + b, (uint32_t)(((it / NB) & 1) ^ 1), abort_flag,
-                                      a.d_err, 6, wait_ns);
-                        if (!ok) break;
-                        tc::fence_after_sync();
-                        const uint32_t d1 = tmem + (uint32_t)(b * BN);
-                        const uint8_t* st = ring + s * C::stage_bytes;
-                        if (PERSAMPLE) {
-#pragma unroll
-                            for (int sl = 0; sl < KS; ++sl) {
-                                if (TEX8)
-                                    tc::mma_fp8(d1, tc::smem_desc(atex + sl * 4096),
-                                                tc::smem_desc(st + sl * 4096), C::id_tex, sl > 0);
-                                else
-                                    tc::mma_bf16(d1, tc::smem_desc(atex + sl * 4096),
-                                                 tc::smem_desc(st + sl * 4096), C::id_tex, sl > 0);
-                            }
-                        }
-                        tc::mma_bf16(d1, tc::smem_desc(ap), tc::smem_desc(st + C::col_off),
-                                     C::id_bf16, PERSAMPLE ? 1 : 0);
-                        tc::mma_bf16(d1, tc::smem_desc(ap + 4096), tc::smem_desc(st + C::bl_off),
-                                     C::id_bf16, 1);
-                        tc::mma_bf16(d1, tc::smem_desc(ap + 8192),
-                                     tc::smem_desc(st + C::bl_off + 4096), C::id_bf16, 1);
-                        tc::mma_commit(empty + s);
-                        tc::mma_commit(tmem_full + b);
-                        last = it;
-                    }
-                    if (ok) tc::mma_commit(acol_empty + cb);
+            RingPos rp;  // the MMA issuer is lane 0 alone: it reads the ring itself
+            int num = -1;
+            ok = ok && next_num(rp, num, true);
+            Item itm = item_of(a, num);
+            int cur_img = -1, cur_pt = -1;
+            while (ok && itm.img >= 0) {
+                const TcImage& im = a.images[itm.img];
+                if (itm.img != cur_img || itm.pt != cur_pt) {  // a new pixel tile
+                    ok = spin_bar(atex_full + (int)(ptc % ATB), (uint32_t)((ptc / ATB) & 1),
+                                  abort_flag, a.d_err, 3, wait_ns);
+                    cur_img = itm.img;
+                    cur_pt = itm.pt;
+                    ++ptc;
                 }
-                if (ok) tc::mma_commit(atex_empty);
+                const int cb = (int)(li & 1);
+                ok = ok && spin_bar(acol_full + cb, (uint32_t)((li >> 1) & 1), abort_flag, a.d_err,
+                                    4, wait_ns);
+                const uint8_t* ap = acol + cb * C::AP;  // colour, L0, L1 slabs of this item
+                const uint8_t* ax = atex + (int)((ptc - 1) % ATB) * C::tex_bytes;
+                const int nt = tiles_of(im.tile_off, itm.lab);
+                for (int t = 0; ok && t < nt; ++t, ++it) {
+                    const int s = (int)(it % C::STAGES), b = (int)(it % NB);
+                    ok = spin_bar(full + s, (uint32_t)((it / C::STAGES) & 1), abort_flag, a.d_err, 5,
+                                  wait_ns) &&
+                         spin_bar(tmem_empty + b, (uint32_t)(((it / NB) & 1) ^ 1), abort_flag,
+                                  a.d_err, 6, wait_ns);
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    const uint32_t d1 = tmem + (uint32_t)(b * BN);
+                    const uint8_t* st = ring + s * C::stage_bytes;
+                    if (PERSAMPLE) {
+#pragma unroll
+                        for (int sl = 0; sl < KS; ++sl) {
+                            if (TEX8)
+                                tc::mma_fp8(d1, tc::smem_desc(ax + sl * 4096),
+                                            tc::smem_desc(st + sl * 4096), C::id_tex, sl > 0);
+                            else
+                                tc::mma_bf16(d1, tc::smem_desc(ax + sl * 4096),
+                                             tc::smem_desc(st + sl * 4096), C::id_tex, sl > 0);
+                        }
+                    }
+                    tc::mma_bf16(d1, tc::smem_desc(ap), tc::smem_desc(st + C::col_off), C::id_bf16,
+                                 (PERSAMPLE && KS > 0) ? 1 : 0);
+                    tc::mma_bf16(d1, tc::smem_desc(ap + 4096), tc::smem_desc(st + C::bl_off),
+                                 C::id_bf16, 1);
+                    tc::mma_bf16(d1, tc::smem_desc(ap + 8192), tc::smem_desc(st + C::bl_off + 4096),
+                                 C::id_bf16, 1);
+                    tc::mma_commit(empty + s);
+                    tc::mma_commit(tmem_full + b);
+                    last = it;
+                }
+                if (!ok) break;
+                tc::mma_commit(acol_empty + cb);
+                ok = next_num(rp, num, true);
+                if (!ok) break;
+                const Item nxt = item_of(a, num);
+                if (nxt.img < 0 || nxt.img != itm.img || nxt.pt != itm.pt)
+                    tc::mma_commit(atex_empty + (int)((ptc - 1) % ATB));
+                itm = nxt;
+                ++li;
             }
             // drain: the last MMAs must finish before the tensor memory is freed
             if (last >= 0)
@@ -518,270 +752,327 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q = warp & 3, hf = warp >> 2;  // lane quadrant, column quarter
+        const int q = warp & 3, hf = warp >> 2;  // lane quadrant, column part
         const int r = 32 * q + lane;             // pixel row of the tile
         const int rx = r % TW, ry = r / TW;
+        // x' = position relative to the pixel tile's centre
+        const int xpx = rx - TW / 2, xpy = ry - TH / 2;
+        const float xsq = (float)(xpx * xpx + xpy * xpy);
         const float Cc = LOG2E / (2.f * a.sigma_c2);
         const float log_col_norm = 1.5f * logf(6.283185307179586f * a.sigma_c2);
-        uint32_t it = 0, li = 0, lpt = 0;
+        uint32_t it = 0, li = 0, pwr = 0;  // tiles, items, pixel-tile operands written
         bool ok = true;
-        for (int g = blockIdx.x; ok && g < a.n_items; g += gridDim.x, ++lpt) {
-            const TcImage& im = a.images[image_of(a, g)];
-            const int pt = g - im.first_item;
-            const long long P = (long long)im.H * im.W;
+
+        // co-support words a pixel row holds in registers (Wk <= WKM)
+        constexpr int WKM = !PERSAMPLE ? 1 : TEX8 ? KS + 1 : KS / 2 + 1;
+        struct Px {
+            bool live;
+            int pix;
+            float IR, IG, IB, I2;
+            int popx;
+            int D;             // squared scribble distance of the item's label
+            uint32_t bw[WKM];  // this pixel's co-support words
+        };
+        // an item's pixel row: the loads are issued here and used only after
+        // the current item's first tile (px_finish), so that their latency
+        // hides behind it
+        auto px_issue = [&](const TcImage& im, int pt, int lab) {
+            Px p;
             const int x = (pt % im.ntx) * TW + rx, y = (pt / im.ntx) * TH + ry;
-            const bool live = x < im.W && y < im.H;
-            const int pix = live ? y * im.W + x : 0;  // < 2^31 (side <= 23170)
-            const float* Ip = im.img + (size_t)pix * 3;
-            const float IR = Ip[0], IG = Ip[1], IB = Ip[2];
-            const float I2 = fmaf(IR, IR, fmaf(IG, IG, IB * IB));
-            // x' = position relative to the pixel tile's centre
-            const int xpx = rx - TW / 2, xpy = ry - TH / 2;
-            const float xsq = (float)(xpx * xpx + xpy * xpy);
-            const uint32_t* bxp = im.bitmask + (size_t)pix * a.Wk;  // this pixel's co-support words
-            int popx = 0;
-            if (live)
-                for (int w = 0; w < a.Wk; ++w) popx += __popc(bxp[w]);
-            // texture operand rows: this warp writes slabs sl = hf, hf + EPQ, ...
+            p.live = x < im.W && y < im.H;
+            p.pix = p.live ? y * im.W + x : 0;  // < 2^31 (side <= 23170)
+            const float* Ip = im.img + (size_t)p.pix * 3;
+            p.IR = Ip[0];
+            p.IG = Ip[1];
+            p.IB = Ip[2];
+            const uint32_t* bxp = im.bitmask + (size_t)p.pix * a.Wk;
+#pragma unroll
+            for (int w = 0; w < WKM; ++w) p.bw[w] = PERSAMPLE && w < a.Wk ? bxp[w] : 0u;
+            p.D = p.live ? im.dist2[(size_t)lab * ((long long)im.H * im.W) + p.pix] : 0;
+            return p;
+        };
+        auto px_finish = [&](Px& p) {
+            p.I2 = fmaf(p.IR, p.IR, fmaf(p.IG, p.IG, p.IB * p.IB));
+            p.popx = 0;
+#pragma unroll
+            for (int w = 0; w < WKM; ++w) p.popx += p.live ? __popc(p.bw[w]) : 0;
+        };
+        // texture operand rows of a pixel tile (the codes of the MMA slabs):
+        // this warp writes slabs sl = hf, hf + EPQ, ... of buffer pwr % ATB
+        auto write_atex = [&](const Px& p) {
+            // the factorised form has no texture operand: only the arrival,
+            // which orders the pixel tiles for the MMA issuer
             if (PERSAMPLE) {
-                ok = spin_warp(atex_empty, (uint32_t)((lpt & 1) ^ 1), abort_flag, a.d_err, 7, wait_ns);
-                if (!ok) break;
-                for (int sl = hf; sl < KS; sl += EPQ) {
-                    // FP8: slab sl holds codes 32 sl .. 32 sl + 31 (bitmask word sl);
-                    // BF16: codes 16 sl .. 16 sl + 15 (half of word sl / 2)
-                    const int wi = TEX8 ? sl : sl >> 1;
-                    const uint32_t word = live && wi < a.Wk ? bxp[wi] : 0u;
-                    const int j0 = TEX8 ? 32 * sl : 16 * sl;
-                    const int valid = live ? min(max(a.k - j0, 0), TEX8 ? 32 : 16) : 0;
-                    const uint32_t bits = TEX8 ? word : (word >> (16 * (sl & 1))) & 0xFFFFu;
-                    uint32_t wv[8];
+            const bool wok = spin_warp(atex_empty + (int)(pwr % ATB),
+                                       (uint32_t)(((pwr / ATB) & 1) ^ 1), abort_flag, a.d_err, 7,
+                                       wait_ns);
+            if (!wok) return false;
+            uint8_t* ax = atex + (int)(pwr % ATB) * C::tex_bytes;
+            for (int sl = hf; sl < KS; sl += EPQ) {
+                // FP8: slab sl holds codes 32 sl .. 32 sl + 31 (bitmask word sl);
+                // BF16: codes 16 sl .. 16 sl + 15 (half of word sl / 2)
+                const int wi = TEX8 ? sl : sl >> 1;
+                uint32_t word = 0u;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        uint32_t packed = 0;
-                        if (TEX8) {
+                for (int w = 0; w < WKM; ++w) word = w == wi ? p.bw[w] : word;
+                if (!p.live) word = 0u;
+                const int j0 = TEX8 ? 32 * sl : 16 * sl;
+                const int valid = p.live ? min(max(a.k - j0, 0), TEX8 ? 32 : 16) : 0;
+                const uint32_t bits = TEX8 ? word : (word >> (16 * (sl & 1))) & 0xFFFFu;
+                uint32_t wv[8];
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int jj = 4 * c + e;
-                                const uint32_t v = jj < valid ? (((bits >> jj) & 1u) ? 0x38u : 0xB8u) : 0u;
-                                packed |= v << (8 * e);
-                            }
-                        } else {
+                for (int c = 0; c < 8; ++c) {
+                    uint32_t packed = 0;
+                    if (TEX8) {
 #pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const int jj = 2 * c + e;
-                                const uint32_t v = jj < valid ? (((bits >> jj) & 1u) ? 0x3F80u : 0xBF80u) : 0u;
-                                packed |= v << (16 * e);
-                            }
+                        for (int e = 0; e < 4; ++e) {
+                            const int jj = 4 * c + e;
+                            const uint32_t v = jj < valid ? (((bits >> jj) & 1u) ? 0x38u : 0xB8u) : 0u;
+                            packed |= v << (8 * e);
                         }
-                        wv[c] = packed;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int jj = 2 * c + e;
+                            const uint32_t v = jj < valid ? (((bits >> jj) & 1u) ? 0x3F80u : 0xBF80u) : 0u;
+                            packed |= v << (16 * e);
+                        }
                     }
-                    uint8_t* base = atex + sl * 4096;
-                    *reinterpret_cast<uint4*>(base + tc::slab_off(r, 0)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-                    *reinterpret_cast<uint4*>(base + tc::slab_off(r, 16)) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+                    wv[c] = packed;
                 }
-                tc::fence_proxy_async_smem();
+                uint8_t* base = ax + sl * 4096;
+                *reinterpret_cast<uint4*>(base + tc::slab_off(r, 0)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                *reinterpret_cast<uint4*>(base + tc::slab_off(r, 16)) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+            }
+            tc::fence_proxy_async_smem();
             }
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(atex_full);
-
-            uint64_t fmask = 0;  // label rows of this pixel flagged for the FP64 recompute
-            for (int i = 0; ok && i < im.n_labels; ++i, ++li) {
-                const int D = live ? im.dist2[(size_t)i * P + pix] : 0;
-                const float rho = a.alpha * fmaxf(sqrtf((float)D), a.d_min);
-                const float s2 = a.rho_var ? rho : rho * rho;  // location variance
-                const float nA = -LOG2E / (2.f * s2);
-                const float Bt = PERSAMPLE ? LOG2E / (a.kappa_beta * rho) : 1.f;
-                const float g = PERSAMPLE ? (a.kappa_beta * rho) / LOG2E : 1.f;
-                const float R0 = (PERSAMPLE ? -Bt * (float)popx : 0.f) - Cc * I2;
-                // pixel-side operand rows of this label: colour (16 bf16, two
-                // halves) and location L0, L1 (pieces of -f x' and f, f =
-                // nA / Bt, matching the sample side's pieces of 2u and |u|^2);
-                // jobs 0..3 = colour half 0, colour half 1, L0, L1, job j on
-                // warp part j % EPQ
-                const int cb = (int)(li % C::ACB);
-                ok = spin_warp(acol_empty + cb, (uint32_t)(((li / C::ACB) & 1) ^ 1), abort_flag,
-                               a.d_err, 8, wait_ns);
-                if (!ok) break;
-                uint8_t* ap = acol + cb * C::AP;
-                const float f = nA * g;
+            if (lane == 0) tc::mbar_arrive(atex_full + (int)(pwr % ATB));
+            ++pwr;
+            return true;
+        };
+        // pixel-side operand rows of item number n (label lab at the pixel
+        // tile of p): colour (16 bf16, two halves) and location L0, L1
+        // (pieces of -f x' and f, f = nA / Bt, matching the sample side's
+        // pieces of 2u and |u|^2, then +-1 for the texture codes that ride in
+        // L1); jobs 0..3 = colour half 0, colour half 1, L0, L1, job j on
+        // warp part j % EPQ
+        auto write_acol = [&](const Px& p, uint32_t n) {
+            const int cb = (int)(n & 1);
+            const bool wok = spin_warp(acol_empty + cb, (uint32_t)(((n >> 1) & 1) ^ 1), abort_flag,
+                                       a.d_err, 8, wait_ns);
+            if (!wok) return false;
+            const int D = p.D;
+            const float rho = a.alpha * fmaxf(sqrtf((float)D), a.d_min);
+            const float s2 = a.rho_var ? rho : rho * rho;  // location variance
+            const float nA = -LOG2E / (2.f * s2);
+            const float g = PERSAMPLE ? (a.kappa_beta * rho) / LOG2E : 1.f;
+            const float f = nA * g;
+            uint8_t* ap = acol + cb * C::AP;
 #pragma unroll
-                for (int job = hf; job < 4; job += EPQ) {
-                    uint4 lo = make_uint4(0, 0, 0, 0), hi = make_uint4(0, 0, 0, 0);
-                    if (job < 2) {
-                        uint16_t h0, l0, h1, l1;
-                        if (job == 0) {
-                            split_bf16(2.f * Cc * g * IR, h0, l0);
-                            split_bf16(2.f * Cc * g * IG, h1, l1);
-                        } else {
-                            split_bf16(2.f * Cc * g * IB, h0, l0);
-                            split_bf16(g, h1, l1);
-                        }
-                        lo = make_uint4(pack2(h0, h0), pack2(l0, l0), pack2(h1, h1), pack2(l1, l1));
+            for (int job = hf; job < 4; job += EPQ) {
+                uint4 lo = make_uint4(0, 0, 0, 0), hi = make_uint4(0, 0, 0, 0);
+                if (job < 2) {
+                    uint16_t h0, l0, h1, l1;
+                    if (job == 0) {
+                        split_bf16(2.f * Cc * g * p.IR, h0, l0);
+                        split_bf16(2.f * Cc * g * p.IG, h1, l1);
                     } else {
-                        uint16_t f1, f2, f3;
-                        split3_bf16(f, f1, f2, f3);
-                        if (job == 2) {
-                            uint16_t x1, x2, x3, y1, y2, y3;
-                            split3_bf16(-f * (float)xpx, x1, x2, x3);
-                            split3_bf16(-f * (float)xpy, y1, y2, y3);
-                            lo = make_uint4(pack2(x1, x1), pack2(x2, x2), pack2(x3, x3), pack2(y1, y1));
-                            hi = make_uint4(pack2(y2, y2), pack2(y3, y3), pack2(f1, f1), pack2(f1, f1));
-                        } else {
-                            lo = make_uint4(pack2(f2, f2), pack2(f2, f3), pack2(f3, 0), 0);
-                        }
+                        split_bf16(2.f * Cc * g * p.IB, h0, l0);
+                        split_bf16(g, h1, l1);
                     }
-                    if (!live) lo = hi = make_uint4(0, 0, 0, 0);
-                    if (job < 2) {
-                        *reinterpret_cast<uint4*>(ap + tc::slab_off(r, 16 * job)) = lo;
-                    } else {
-                        uint8_t* sl = ap + 4096 * (job - 1);
-                        *reinterpret_cast<uint4*>(sl + tc::slab_off(r, 0)) = lo;
-                        *reinterpret_cast<uint4*>(sl + tc::slab_off(r, 16)) = hi;
-                    }
-                }
-                tc::fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(acol_full + cb);
-
-                const uint64_t bt2 = pk2(Bt, Bt);
-                const int m_i = im.label_off[i + 1] - im.label_off[i];
-                const float shift = (float)(96 - (32 - __clz(m_i - 1)));  // 96 - ceil(log2 m)
-                // e_j = Bt D1_j + nA |x'|^2 + R0 (+ shift)
-                const float R0x = fmaf(nA, xsq, R0);
-                const uint64_t k2 = pk2(R0x + shift, R0x + shift);
-                const int nt = tiles_of(im.tile_off, i);
-                float S = 0.f, Ccomp = 0.f;
-                for (int t = 0; t < nt; ++t, ++it) {
-                    const int b = (int)(it % NB);
-                    ok = spin_warp(tmem_full + b, (uint32_t)((it / NB) & 1), abort_flag, a.d_err, 10, wait_ns);
-                    if (!ok) break;
-                    tc::fence_after_sync();
-                    const int nvalid = min(BN, m_i - t * BN);
-                    const int cbase = hf * CPW;
-                    const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
-                    uint64_t x1[8];
-                    if (cbase + CPW <= nvalid) {  // warp-uniform: all columns valid
-                        float ts = 0.f;
-#pragma unroll
-                        for (int ch = 0; ch < CPW / 16; ++ch) {
-                            tc::tmem_ld16_wait_pk(lb + 16u * ch, x1);
-                            ts += sum16_full(x1, bt2, k2);
-                        }
-                        two_sum(ts, S, Ccomp);
-                    } else if (cbase < nvalid) {  // warp-uniform: the label's last tile
-#pragma unroll
-                        for (int ch = 0; ch < CPW / 16; ++ch) {
-                            const int nv = nvalid - cbase - 16 * ch;
-                            if (nv > 0) {  // warp-uniform
-                                tc::tmem_ld16_wait_pk(lb + 16u * ch, x1);
-                                const float ts = nv >= 16 ? sum16_full(x1, bt2, k2)
-                                                          : sum16_part(x1, nv, bt2, k2);
-                                two_sum(ts, S, Ccomp);
-                            }
-                        }
-                    }
-                    // tcgen05.wait::ld is warp-collective: every lane's loads
-                    // are complete here; one elected lane releases the buffer
-                    tc::fence_before_sync();
-                    tc::mbar_arrive_elect(tmem_empty + b);
-                }
-                if (!ok) break;
-                // merge the EPQ column parts of each pixel. XB = 2 NB exchange
-                // buffers: a part can run at most NB sample tiles ahead of
-                // another (tensor memory holds NB accumulators and every label
-                // has at least one tile), so buffer li % XB is free when
-                // rewritten.
-                const int xbuf = (int)(li % C::XB);
-                float2* xb = xchg + (size_t)xbuf * (EPQ - 1) * 4 * 32;
-                uint64_t* xbar = xchg_full + xbuf * 4 + q;
-                if (hf > 0) {
-                    xb[((hf - 1) * 4 + q) * 32 + lane] = make_float2(S, Ccomp);
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(xbar);
+                    lo = make_uint4(pack2(h0, h0), pack2(l0, l0), pack2(h1, h1), pack2(l1, l1));
                 } else {
-                    ok = spin_warp(xbar, (uint32_t)((li / C::XB) & 1), abort_flag, a.d_err, 11, wait_ns);
-                    if (!ok) break;
-                    float Sm = S, Cm = Ccomp;
+                    uint16_t f1, f2, f3;
+                    split3_bf16(f, f1, f2, f3);
+                    if (job == 2) {
+                        uint16_t x1, x2, x3, y1, y2, y3;
+                        split3_bf16(-f * (float)xpx, x1, x2, x3);
+                        split3_bf16(-f * (float)xpy, y1, y2, y3);
+                        lo = make_uint4(pack2(x1, x1), pack2(x2, x2), pack2(x3, x3), pack2(y1, y1));
+                        hi = make_uint4(pack2(y2, y2), pack2(y3, y3), pack2(f1, f1), pack2(f1, f1));
+                    } else {
+                        // texture codes 32 KS + e (16 KS + e): +-1 for e < ext
+                        uint32_t sg[EXT_MAX];
 #pragma unroll
-                    for (int h = 0; h < EPQ - 1; ++h) {
-                        const float2 v = xb[(h * 4 + q) * 32 + lane];
-                        Sm += v.x;
-                        Cm += v.y;
+                        for (int e = 0; e < EXT_MAX; ++e) {
+                            const int code = (TEX8 ? 32 : 16) * KS + e;
+                            uint32_t word = 0u;
+#pragma unroll
+                            for (int w = 0; w < WKM; ++w) word = w == (code >> 5) ? p.bw[w] : word;
+                            sg[e] = (PERSAMPLE && e < a.ext)
+                                        ? (((word >> (code & 31)) & 1u) ? 0x3F80u : 0xBF80u)
+                                        : 0u;
+                        }
+                        lo = make_uint4(pack2(f2, f2), pack2(f2, f3), f3 | (sg[0] << 16),
+                                        sg[1] | (sg[2] << 16));
+                        hi = make_uint4(sg[3] | (sg[4] << 16), sg[5] | (sg[6] << 16),
+                                        sg[7] | (sg[8] << 16), sg[9] | (sg[10] << 16));
                     }
-                    const float tot = Sm + Cm;  // shifted by 2^shift
-                    const float lse2 = log2f(tot) - shift;
-                    const float Lv = lse2 * LN2 - logf((float)m_i) -
-                                     logf(6.283185307179586f * s2) - log_col_norm;
-                    // below the floor the FP32 terms may have lost mass to
-                    // underflow; above the tolerance the bound on the error of
-                    // L (log2 units) is too loose: recompute in FP64. Bound:
-                    // colour splits 2^-15 C Q. Accumulation of the colour and
-                    // the two location MMAs onto the exact texture sum, 2^-21
-                    // of the magnitudes per instruction, plus the location
-                    // pieces' residuals (<= 2^-24): at most 2^-19 (Bt k + C Q +
-                    // |nA| M_j), where the location products of sample j sum
-                    // in magnitude to M_j <= (|u_j| + |x'|)^2 <= 2 |x - x_j|^2 +
-                    // 8 |x'|^2 and |nA| |x - x_j|^2 <= |e_j| (every part of the
-                    // exponent is <= 0); weighted by the pairs' shares of the
-                    // sum, |e_j| averages at most |log2 S| + log2 m. The FP32
-                    // epilogue: 6u per pair on the same weights plus the
-                    // per-pixel constant.
-                    const float im2 = im.imax2[i];
-                    const float CQ = Cc * fmaf(2.f * sqrtf(I2), sqrtf(im2), im2);
-                    const float BK = PERSAMPLE ? Bt * (float)a.k : 0.f;
-                    const float Ew = fabsf(lse2) + log2f((float)m_i);
-                    const float E2 =
-                        3.1e-05f * CQ +
-                        1.9073486e-06f * (BK + CQ - 8.f * nA * xsq + 2.f * Ew) +
-                        3.5762787e-07f * (3.f * Ew + 2.f * fabsf(R0x) + shift + 1.f);
-                    if (!(tot >= FLOOR_PER_SAMPLE * (float)m_i) ||
-                        (a.l_tol > 0.f && E2 * LN2 > a.l_tol * fmaxf(fabsf(Lv), 1.f)))
-                        fmask |= 1ull << i;
-                    // -L into the output plane; normalised once all labels are done
-                    if (live) im.neglog[(size_t)i * P + pix] = -Lv;
+                }
+                if (!p.live) lo = hi = make_uint4(0, 0, 0, 0);
+                if (job < 2) {
+                    *reinterpret_cast<uint4*>(ap + tc::slab_off(r, 16 * job)) = lo;
+                } else {
+                    uint8_t* sl = ap + 4096 * (job - 1);
+                    *reinterpret_cast<uint4*>(sl + tc::slab_off(r, 0)) = lo;
+                    *reinterpret_cast<uint4*>(sl + tc::slab_off(r, 16)) = hi;
+                }
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(acol_full + cb);
+            return true;
+        };
+
+        RingPos rp;
+        int num = -1;
+        ok = next_num(rp, num, false);
+        Item itm = item_of(a, num);
+        Px cpx{};
+        if (ok && itm.img >= 0) {
+            cpx = px_issue(a.images[itm.img], itm.pt, itm.lab);
+            px_finish(cpx);
+            ok = write_atex(cpx) && write_acol(cpx, 0);
+        }
+        while (ok && itm.img >= 0) {
+            const TcImage& im = a.images[itm.img];
+            const long long P = (long long)im.H * im.W;
+            const int i = itm.lab;
+            const float rho = a.alpha * fmaxf(sqrtf((float)cpx.D), a.d_min);
+            const float s2 = a.rho_var ? rho : rho * rho;  // location variance
+            const float nA = -LOG2E / (2.f * s2);
+            const float Bt = PERSAMPLE ? LOG2E / (a.kappa_beta * rho) : 1.f;
+            const float R0 = (PERSAMPLE ? -Bt * (float)cpx.popx : 0.f) - Cc * cpx.I2;
+            const uint64_t bt2 = pk2(Bt, Bt);
+            const int m_i = im.label_off[i + 1] - im.label_off[i];
+            const float shift = (float)(96 - (32 - __clz(m_i - 1)));  // 96 - ceil(log2 m)
+            // e_j = Bt D1_j + nA |x'|^2 + R0 (+ shift)
+            const float R0x = fmaf(nA, xsq, R0);
+            const uint64_t k2 = pk2(R0x + shift, R0x + shift);
+            const int nt = tiles_of(im.tile_off, i);
+            // the next item, and its pixel row's loads in flight during tile 0
+            ok = next_num(rp, num, false);
+            if (!ok) break;
+            const Item nxt = item_of(a, num);
+            const bool n_newpt = nxt.img >= 0 && (nxt.img != itm.img || nxt.pt != itm.pt);
+            Px npx = cpx;
+            if (n_newpt) {
+                npx = px_issue(a.images[nxt.img], nxt.pt, nxt.lab);
+            } else if (nxt.img >= 0) {
+                npx.D = cpx.live ? im.dist2[(size_t)nxt.lab * P + cpx.pix] : 0;
+            }
+            float S = 0.f, Ccomp = 0.f;
+            for (int t = 0; t < nt; ++t, ++it) {
+                const int b = (int)(it % NB);
+                ok = spin_warp(tmem_full + b, (uint32_t)((it / NB) & 1), abort_flag, a.d_err, 10,
+                               wait_ns);
+                if (!ok) break;
+                tc::fence_after_sync();
+                const int nvalid = min(BN, m_i - t * BN);
+                const int cbase = hf * CPW;
+                const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
+                uint64_t x1[8];
+                if (cbase + CPW <= nvalid) {  // warp-uniform: all columns valid
+                    float ts = 0.f;
+#pragma unroll
+                    for (int ch = 0; ch < CPW / 16; ++ch) {
+                        tc::tmem_ld16_wait_pk(lb + 16u * ch, x1);
+                        ts += sum16_full(x1, bt2, k2);
+                    }
+                    two_sum(ts, S, Ccomp);
+                } else if (cbase < nvalid) {  // warp-uniform: the label's last tile
+#pragma unroll
+                    for (int ch = 0; ch < CPW / 16; ++ch) {
+                        const int nv = nvalid - cbase - 16 * ch;
+                        if (nv > 0) {  // warp-uniform
+                            tc::tmem_ld16_wait_pk(lb + 16u * ch, x1);
+                            const float ts = nv >= 16 ? sum16_full(x1, bt2, k2)
+                                                      : sum16_part(x1, nv, bt2, k2);
+                            two_sum(ts, S, Ccomp);
+                        }
+                    }
+                }
+                // tcgen05.wait::ld is warp-collective: every lane's loads are
+                // complete here; one elected lane releases the buffer
+                tc::fence_before_sync();
+                tc::mbar_arrive_elect(tmem_empty + b);
+                if (t == 0 && nxt.img >= 0) {
+                    // the next item's operands, while this item's MMAs run on
+                    if (n_newpt) px_finish(npx);
+                    if (n_newpt && ATB == 2) ok = write_atex(npx);
+                    ok = ok && write_acol(npx, li + 1);
+                    if (!ok) break;
                 }
             }
             if (!ok) break;
-            // label normalisation (and the factorised texture posterior) by part
-            // 0; a flagged pixel is listed for the FP64 recompute instead
-            if (hf == 0 && live && fmask) {
-                const int idx = atomicAdd(a.fb_count, 1);
-                if (idx < a.fb_cap)
-                    a.fb_list[idx] = make_int4(image_of(a, g), pix, (int)(uint32_t)fmask,
-                                               (int)(uint32_t)(fmask >> 32));
-            } else if (hf == 0 && live) {
-                if (!PERSAMPLE && im.rep) {  // factorised: the majority-co-support posterior
-                    float tmax = -INFINITY;
-                    for (int i = 0; i < im.n_labels; ++i) {
-                        const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
-                        int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
-                        tmax = fmaxf(tmax, -LOG2E * (float)h / (a.kappa_beta * rho));
-                    }
-                    float ts = 0.f;
-                    for (int i = 0; i < im.n_labels; ++i) {
-                        const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
-                        int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
-                        ts += ex2f(-LOG2E * (float)h / (a.kappa_beta * rho) - tmax);
-                    }
-                    const float tl = tmax + log2f(ts);
-                    for (int i = 0; i < im.n_labels; ++i) {
-                        const float rho = a.alpha * fmaxf(sqrtf((float)im.dist2[(size_t)i * P + pix]), a.d_min);
-                        int h = 0;
-                        for (int w = 0; w < a.Wk; ++w) h += __popc(bxp[w] ^ im.rep[i * a.Wk + w]);
-                        im.neglog[(size_t)i * P + pix] -= (-LOG2E * (float)h / (a.kappa_beta * rho) - tl) * LN2;
+            // merge the EPQ column parts of each pixel. XB = 2 NB exchange
+            // buffers: a part can run at most NB sample tiles ahead of another
+            // (tensor memory holds NB accumulators and every item has at least
+            // one tile), so buffer li % XB is free when rewritten.
+            const int xbuf = (int)(li % C::XB);
+            float2* xb = xchg + (size_t)xbuf * (EPQ - 1) * 4 * 32;
+            uint64_t* xbar = xchg_full + xbuf * 4 + q;
+            if (hf > 0) {
+                xb[((hf - 1) * 4 + q) * 32 + lane] = make_float2(S, Ccomp);
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(xbar);
+            } else {
+                ok = spin_warp(xbar, (uint32_t)((li / C::XB) & 1), abort_flag, a.d_err, 11, wait_ns);
+                if (!ok) break;
+                float Sm = S, Cm = Ccomp;
+#pragma unroll
+                for (int h = 0; h < EPQ - 1; ++h) {
+                    const float2 v = xb[(h * 4 + q) * 32 + lane];
+                    Sm += v.x;
+                    Cm += v.y;
+                }
+                const float tot = Sm + Cm;  // shifted by 2^shift
+                const float lse2 = log2f(tot) - shift;
+                const float Lv = lse2 * LN2 - logf((float)m_i) - logf(6.283185307179586f * s2) -
+                                 log_col_norm;
+                // below the floor the FP32 terms may have lost mass to
+                // underflow; above the tolerance the bound on the error of L
+                // (log2 units) is too loose: recompute in FP64. Bound: colour
+                // splits 2^-15 C Q. Accumulation of the colour and the two
+                // location MMAs onto the exact texture sum, 2^-21 of the
+                // magnitudes per instruction, plus the location pieces'
+                // residuals (<= 2^-24): at most 2^-19 (Bt k + C Q + |nA| M_j),
+                // where the location products of sample j sum in magnitude to
+                // M_j <= (|u_j| + |x'|)^2 <= 2 |x - x_j|^2 + 8 |x'|^2 and
+                // |nA| |x - x_j|^2 <= |e_j| (every part of the exponent is
+                // <= 0); weighted by the pairs' shares of the sum, |e_j|
+                // averages at most |log2 S| + log2 m. The FP32 epilogue: 6u
+                // per pair on the same weights plus the per-pixel constant.
+                const float im2 = im.imax2[i];
+                const float CQ = Cc * fmaf(2.f * sqrtf(cpx.I2), sqrtf(im2), im2);
+                const float BK = PERSAMPLE ? Bt * (float)a.k : 0.f;
+                const float Ew = fabsf(lse2) + log2f((float)m_i);
+                const float E2 = 3.1e-05f * CQ +
+                                 1.9073486e-06f * (BK + CQ - 8.f * nA * xsq + 2.f * Ew) +
+                                 3.5762787e-07f * (3.f * Ew + 2.f * fabsf(R0x) + shift + 1.f);
+                const bool flag = !(tot >= FLOOR_PER_SAMPLE * (float)m_i) ||
+                                  (a.l_tol > 0.f && E2 * LN2 > a.l_tol * fmaxf(fabsf(Lv), 1.f));
+                if (cpx.live) {
+                    // -L into the output plane; the label normalisation follows
+                    // in its own pass once every row is written
+                    im.neglog[(size_t)i * P + cpx.pix] = -Lv;
+                    if (flag) {
+                        // the FP64 recompute lists a pixel once, with all its flagged rows
+                        const unsigned long long old =
+                            atomicOr(a.flags + im.pix_off + cpx.pix, 1ull << i);
+                        if (old == 0ull) {
+                            const int idx = atomicAdd(a.fb_count, 1);
+                            if (idx < a.fb_cap) a.fb_list[idx] = make_int4(itm.img, cpx.pix, 0, 0);
+                        }
                     }
                 }
-                float lmax = -INFINITY;
-                for (int i = 0; i < im.n_labels; ++i) lmax = fmaxf(lmax, -im.neglog[(size_t)i * P + pix]);
-                float ls = 0.f;
-                for (int i = 0; i < im.n_labels; ++i) ls += expf(-im.neglog[(size_t)i * P + pix] - lmax);
-                const float lse = lmax + logf(ls);
-                if (im.post)
-                    for (int i = 0; i < im.n_labels; ++i)
-                        im.post[(size_t)i * P + pix] = expf(-im.neglog[(size_t)i * P + pix] - lse);
             }
+            // a new pixel tile's texture operand once this one is consumed
+            if (n_newpt && ATB == 1) ok = write_atex(npx);
+            itm = nxt;
+            cpx = npx;
+            ++li;
         }
     }
     tc::fence_before_sync();
@@ -793,7 +1084,8 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
 }
 
 // Recompute of the pixels flagged by the sum (a label row below the FP32
-// floor or above the error tolerance): one warp per listed pixel. Each
+// floor or above the error tolerance): one warp per listed pixel, its
+// flagged rows read from the per-pixel flag words. Each
 // flagged label row is summed again with the exponents
 // e_j = -|x - x_j|^2 / (2 rho^2) - |I - I_j|^2 / (2 sigma_c2) [- TSM / beta]
 // formed in double precision (no cancellation between expanded products),
@@ -804,8 +1096,9 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
 // double for the pixel.
 __global__ void __launch_bounds__(128) refine_fp64_kernel(
     const TcImage* __restrict__ images, const int4* __restrict__ list,
-    const int* __restrict__ count, int cap, int Wk, double alpha, double d_min, double kappa_beta,
-    double sigma_c2, bool persample, bool rho_var, int* __restrict__ d_err) {
+    const int* __restrict__ count, int cap, const unsigned long long* __restrict__ flags, int Wk,
+    double alpha, double d_min, double kappa_beta, double sigma_c2, bool persample, bool rho_var,
+    int* __restrict__ d_err) {
     __shared__ double sL[4][CS_MAX_LABELS];
     __shared__ double sT[4][CS_MAX_LABELS];
     int cnt = *count;
@@ -821,8 +1114,8 @@ __global__ void __launch_bounds__(128) refine_fp64_kernel(
     for (int e = blockIdx.x * 4 + wib; e < cnt; e += nwarps) {
         const int4 it = list[e];
         const TcImage& im = images[it.x];
-        const uint64_t fmask = (uint64_t)(uint32_t)it.z | ((uint64_t)(uint32_t)it.w << 32);
         const int pix = it.y, x = pix % im.W, y = pix / im.W;
+        const uint64_t fmask = flags[im.pix_off + pix];  // the pixel's flagged label rows
         const long long P = (long long)im.H * im.W;
         const double IR = im.img[(size_t)pix * 3], IG = im.img[(size_t)pix * 3 + 1],
                      IB = im.img[(size_t)pix * 3 + 2];
@@ -962,15 +1255,17 @@ __global__ void __launch_bounds__(1024) morton_sort_kernel(const int32_t* __rest
 // slabs (b_j in {0, 1}) and the colour slab (hi/lo bf16 of I_j and of
 // -C |I_j|^2); padded rows are zero. tile_xy receives each tile slot's
 // sample position x | y << 16 (the producer forms the location slabs from
-// it per pixel tile).
+// it per pixel tile) and tile_xb the sample's texture codes beyond the MMA
+// slabs (bit e: code 32 KS + e, or 16 KS + e), which the producer places in
+// the second location slab.
 template <bool TEX8, int KS, bool PERSAMPLE>
 __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
                                    const int32_t* __restrict__ tile_off, int n_labels,
                                    int total_tiles, SampleTables t, int n_samples, int k,
                                    float Cc, const int32_t* __restrict__ perm,
                                    uint8_t* __restrict__ blob, uint32_t* __restrict__ tile_xy,
-                                   float* __restrict__ imax2, TcImage desc,
-                                   TcImage* __restrict__ desc_dst) {
+                                   uint32_t* __restrict__ tile_xb, float* __restrict__ imax2,
+                                   TcImage desc, TcImage* __restrict__ desc_dst) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid == 0) *desc_dst = desc;  // this image's descriptor for the sum launch
@@ -987,6 +1282,11 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
     const bool valid = pos < label_off[i + 1];
     const int s = valid ? perm[pos] : 0;
     tile_xy[gid] = valid ? (uint32_t)t.sx[s] | ((uint32_t)t.sy[s] << 16) : 0u;
+    uint32_t xb = 0;
+    if (PERSAMPLE && valid)
+        for (int e = 0, j = (TEX8 ? 32 : 16) * KS; j < k && e < EXT_MAX; ++e, ++j)
+            xb |= ((t.sbits[(size_t)(j >> 5) * n_samples + s] >> (j & 31)) & 1u) << e;
+    tile_xb[gid] = xb;
     uint8_t* st = blob + (size_t)tile * C::copy_bytes;
     if (PERSAMPLE) {
         for (int sl = 0; sl < KS; ++sl) {
@@ -1062,27 +1362,32 @@ cudaError_t tiles(const TcLaunch& L, cudaStream_t st) {
     d.W = L.W;
     d.ntx = (L.W + TW - 1) / TW;
     d.n_labels = L.n_labels;
+    d.tile_xb = L.t.tile_xb;
+    d.n_ptiles = tc_pixel_tiles(L.H, L.W);
     d.first_item = L.first_item;
+    d.pix_off = L.pix_off;
+    d.first_ptile = L.first_ptile;
     cudaError_t e = cudaMemsetAsync(L.imax2, 0, sizeof(float) * L.n_labels, st);
     if (e != cudaSuccess) return e;
     build_tiles_kernel<TEX8, KS, PERSAMPLE>
         <<<(unsigned)(((long long)total_tiles * BN + 127) / 128), 128, 0, st>>>(
             L.d_label_off, L.d_tile_off, L.n_labels, total_tiles, L.t, L.n_samples, L.k, Cc,
-            L.t.perm, L.blob, L.t.tile_xy, L.imax2, d, L.desc);
+            L.t.perm, L.blob, L.t.tile_xy, L.t.tile_xb, L.imax2, d, L.desc);
     return cudaGetLastError();
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
-cudaError_t sum(const TcImage* descs, int n_images, int n_items, const TcSumParams& p,
-                cudaStream_t st) {
+cudaError_t sum(const TcImage* descs, int n_images, const TcSumParams& p, cudaStream_t st) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
     static_assert(C::smem_bytes <= 227 * 1024, "shared memory budget");
     TcArgs a{};
     a.images = descs;
     a.n_images = n_images;
-    a.n_items = n_items;
+    a.n_items = p.n_items;
+    a.total_pixels = p.total_pixels;
     a.k = p.k;
     a.Wk = (p.k + 31) / 32;
+    a.ext = PERSAMPLE ? tex_ext(p.k, TEX8) : 0;
     a.alpha = p.alpha;
     a.d_min = p.d_min;
     a.kappa_beta = p.kappa_beta;
@@ -1092,19 +1397,39 @@ cudaError_t sum(const TcImage* descs, int n_images, int n_items, const TcSumPara
     a.fb_list = p.fb_list;
     a.fb_count = p.fb_count;
     a.fb_cap = p.fb_cap;
+    a.queue = p.queue;
+    a.flags = p.flags;
     a.l_tol = p.l_tol;
     a.wait_ns = p.wait_ns;
     a.stall = p.stall;
     cudaError_t e = cudaFuncSetAttribute(sum_tc_kernel<TEX8, KS, PERSAMPLE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.fb_count, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.queue, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(p.flags, 0, sizeof(unsigned long long) * (size_t)p.total_pixels, st);
     if (e != cudaSuccess) return e;
-    const int slots = C::MIN_BLOCKS * p.n_sm;
-    const int grid = n_items < slots ? n_items : slots;
+    const long long slots = (long long)C::MIN_BLOCKS * p.n_sm;
+    const int grid = (int)(p.n_items < slots ? p.n_items : slots);
+    // whole pixel tiles while more than about one per CTA is left, then
+    // single items
+    long long total_pt = 0;
+    for (int g = 0; g < n_images; ++g) total_pt += p.shapes[g].x;
+    const long long pt1 = total_pt > grid ? total_pt - grid : 0;
+    long long i1 = 0, seen = 0;
+    for (int g = 0; g < n_images && seen < pt1; ++g) {
+        const long long take = p.shapes[g].x < pt1 - seen ? p.shapes[g].x : pt1 - seen;
+        i1 += take * p.shapes[g].y;
+        seen += take;
+    }
+    a.pt1 = (int)pt1;
+    a.i1 = i1;
     sum_tc_kernel<TEX8, KS, PERSAMPLE><<<grid, C::THREADS, C::smem_bytes, st>>>(a);
     refine_fp64_kernel<<<2 * p.n_sm, 128, 0, st>>>(
-        descs, p.fb_list, p.fb_count, p.fb_cap, (p.k + 31) / 32, (double)p.alpha, (double)p.d_min,
-        (double)p.kappa_beta, (double)p.sigma_c2, PERSAMPLE, p.rho_var, p.d_err);
+        descs, p.fb_list, p.fb_count, p.fb_cap, p.flags, (p.k + 31) / 32, (double)p.alpha,
+        (double)p.d_min, (double)p.kappa_beta, (double)p.sigma_c2, PERSAMPLE, p.rho_var, p.d_err);
+    const long long nblk = (p.total_pixels + 255) / 256, cap = 8ll * p.n_sm;
+    normalise_kernel<PERSAMPLE><<<(unsigned)(nblk < cap ? nblk : cap), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1114,7 +1439,7 @@ cudaError_t dispatch(int k, bool tex8, bool persample, F&& f) {
     if (!tc_supported(k, tex8)) return cudaErrorInvalidValue;
     if (!persample) return f(std::integral_constant<bool, true>{}, std::integral_constant<int, 1>{},
                              std::integral_constant<bool, false>{});
-    const int ks = tex8 ? (k + 31) / 32 : (k + 15) / 16;
+    const int ks = tex_slabs(k, tex8);
 #define CS_TC_CASE(N)                                                                        \
     case N:                                                                                  \
         return tex8 ? f(std::integral_constant<bool, true>{}, std::integral_constant<int, N>{}, \
@@ -1122,6 +1447,7 @@ cudaError_t dispatch(int k, bool tex8, bool persample, F&& f) {
                     : f(std::integral_constant<bool, false>{}, std::integral_constant<int, N>{}, \
                         std::integral_constant<bool, true>{});
     switch (ks) {
+        CS_TC_CASE(0)
         CS_TC_CASE(1)
         CS_TC_CASE(2)
         CS_TC_CASE(3)
@@ -1138,7 +1464,7 @@ cudaError_t dispatch(int k, bool tex8, bool persample, F&& f) {
 }  // namespace
 
 size_t tc_copy_bytes(int k, bool tex8, bool persample) {
-    const int ks = tex8 ? (k + 31) / 32 : (k + 15) / 16;
+    const int ks = tex_slabs(k, tex8);
     return (size_t)(persample ? ks * 4096 : 0) + 4096;
 }
 
@@ -1167,22 +1493,31 @@ cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st) {
     return e != cudaSuccess ? e : launch_tc_tiles(L, st);
 }
 
-cudaError_t launch_tc_sum(const TcImage* descs, int n_images, int n_items, const TcSumParams& p,
+cudaError_t launch_tc_sum(const TcImage* descs, int n_images, const TcSumParams& p,
                           cudaStream_t st) {
-    if (n_images < 1 || n_items < 1) return cudaErrorInvalidValue;
+    if (n_images < 1 || p.n_items < 1 || p.n_items >= (1ll << 31)) return cudaErrorInvalidValue;
     return dispatch(p.k, p.tex8, p.persample, [&](auto t8, auto ks, auto ps) {
-        return sum<decltype(t8)::value, decltype(ks)::value, decltype(ps)::value>(
-            descs, n_images, n_items, p, st);
+        return sum<decltype(t8)::value, decltype(ks)::value, decltype(ps)::value>(descs, n_images,
+                                                                                 p, st);
     });
 }
 
 cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st) {
     TcLaunch one = L;
     one.first_item = 0;
+    one.pix_off = 0;
+    one.first_ptile = 0;
     cudaError_t e = sorted ? launch_tc_tiles(one, st) : launch_tc_prepare(one, st);
     if (e != cudaSuccess) return e;
     TcSumParams p{L.k,       L.tex8,  L.persample, L.alpha,      L.d_min, L.kappa_beta,
                   L.sigma_c2, L.d_err, L.n_sm,      L.fb_list,    L.fb_count,
                   L.H * L.W,  L.l_tol, L.rho_var,   L.wait_ns,    L.stall};
-    return launch_tc_sum(L.desc, 1, tc_pixel_tiles(L.H, L.W), p, st);
+    const int npt = tc_pixel_tiles(L.H, L.W);
+    p.n_items = (long long)npt * L.n_labels;
+    p.total_pixels = (long long)L.H * L.W;
+    const int2 shape = make_int2(npt, L.n_labels);
+    p.shapes = &shape;
+    p.queue = L.queue;
+    p.flags = L.flags;
+    return launch_tc_sum(L.desc, 1, p, st);
 }
