@@ -524,21 +524,30 @@ cs_status cs_batch_data_term(cs_ctx* ctx, const cs_image* images, int n_images,
  * Learned surrogate of the data term (not in the paper: an approximation of
  * the Sec. 3.1 likelihood that the exact sum judges and backs up).
  *
- * A 21 -> 64 -> 64 -> 64 -> n_labels MLP with SiLU activations, bf16 weights
- * (fp32 masters) and fp32 arithmetic maps per-pixel features
- * [R, G, B, x/W, y/H, a_1..a_16] (a = the leading codes, cs_codes' lead16) to
- * the log kernel sums T_i(x) = log sum_j k_rho k_sigma [exp(-TSM/beta)] of
- * every label; L_i(x) = T_i - log m_i - log(2 pi rho_i^2) - 1.5 log(2 pi
- * sigma_c2) then uses the exact scribble distance transform.
+ * An n_in -> 64 -> 64 -> 64 -> n_labels MLP with SiLU activations maps
+ * per-pixel features to the log kernel sums
+ * T_i(x) = log sum_j k_rho k_sigma [exp(-TSM/beta)] of every label;
+ * L_i(x) = T_i - log m_i - log(2 pi rho_i^2) - 1.5 log(2 pi sigma_c2) then
+ * uses the exact scribble distance transform (and, in the factorised mode,
+ * adds the exact texture log-posterior of Eq. post_text). Every contraction
+ * runs on the tensor cores (tcgen05, bf16 weights rounded from fp32 masters,
+ * activations as two bf16 pieces, fp32 accumulation). Feature sets:
+ *   CS_SURR_BASIC     n_in = 21: [R, G, B, x/W, y/H, a_1..a_16] (a = the
+ *                     leading codes, cs_codes' lead16)
+ *   CS_SURR_EXTENDED  n_in = 45 + n_labels (n_labels <= 19): the basic
+ *                     features, log max(d_i, d_min) for every label i (d_i =
+ *                     the exact distance to label i's nearest scribble) and
+ *                     sin, cos of 2^f pi x/W and of 2^f pi y/H, f = 0..5
  *
  * cs_surrogate_fit: selects training pixels q with u(q) < frac and
  *   validation pixels with frac <= u(q) < frac + min(0.01, 20000/P), where
  *   u(q) = splitmix64(seed ^ q) / 2^64; computes their exact T (FP32 form);
  *   standardises features and targets; trains `steps` Adam steps (minibatch
- *   64 x SM count, learning rate 2e-3 with cosine decay to 1e-4) with the
- *   library's own forward/backward kernels; records the largest validation
- *   error eta of L. The network lives in the context. Inputs as in
- *   cs_likelihood plus lead16 (DEVICE P x 16 float32). Asynchronous, but the
+ *   128 x min(SM count, training rows / 128), learning rate 4e-3 with cosine
+ *   decay to 1e-4) with the library's own forward/backward kernels; records
+ *   the largest validation error eta of L. The network lives in the
+ *   context. Inputs as in cs_likelihood plus lead16 (DEVICE P x 16 float32)
+ *   and `features` (CS_SURR_BASIC or CS_SURR_EXTENDED). Asynchronous, but the
  *   pixel selection runs on the host before the call returns.
  * cs_surrogate_eval: evaluates the network at every pixel and writes
  *   neglog/post there, except at pixels whose top-2 posterior margin is below
@@ -549,19 +558,26 @@ cs_status cs_batch_data_term(cs_ctx* ctx, const cs_image* images, int n_images,
  *   n_fallback (HOST int32, may be NULL) receives their count; when given,
  *   the call synchronises.
  * cs_surrogate_params: copies the fp32 master weights to HOST memory
- *   (layout W1[64][21] b1 W2[64][64] b2 W3[64][64] b3 W4[n][64] b4);
+ *   (layout W1[64][n_in] b1 W2[64][64] b2 W3[64][64] b3 W4[n][64] b4);
  *   *n_params receives their count; host_params may be NULL. Synchronises.
  * cs_mlp_forward / cs_mlp_grad: the network kernels on given DEVICE
- *   parameters (same layout, used rounded to bf16) and standardised feature
- *   rows X (rows x 21): outputs Z (rows x n_out), or the gradient of
- *   loss = mean over rows and outputs of (Z - T)^2 / 2 into grads (DEVICE,
- *   cs_mlp_param_count(n_out) floats) and the loss into *loss (DEVICE);
- *   rows must be a positive multiple of 64 for cs_mlp_grad.
+ *   parameters (same layout, used rounded to bf16; 1 <= n_in <= 64) and
+ *   standardised feature rows X (rows x n_in): outputs Z (rows x n_out), or
+ *   the gradient of loss = mean over rows and outputs of (Z - T)^2 / 2 into
+ *   grads (DEVICE, cs_mlp_param_count(n_in, n_out) floats) and the loss into
+ *   *loss (DEVICE). Weight gradients take the bf16 piece of the activations
+ *   (relative error at most 2^-8 of sum |delta| |h| per entry).
+ * Errors: CS_ERR_INVALID_ARG (bad sizes, unknown feature set, too many
+ *   labels for CS_SURR_EXTENDED, no fitted surrogate), CS_ERR_NOMEM,
+ *   CS_ERR_CUDA; a device wait that gives up reports CS_ERR_TIMEOUT through
+ *   cs_sync_status.
  */
+#define CS_SURR_BASIC 0
+#define CS_SURR_EXTENDED 1
 cs_status cs_surrogate_fit(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
                            const float* lead16, int k, int n_labels, const int32_t* label_off,
                            const int32_t* sample_pix, const cs_params* prm, double frac,
-                           int steps, uint64_t seed, void* stream);
+                           int steps, int features, uint64_t seed, void* stream);
 cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
                             const float* lead16, int k, int n_labels, const int32_t* label_off,
                             const int32_t* sample_pix, const cs_params* prm, double margin,
@@ -569,27 +585,27 @@ cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const u
 cs_status cs_surrogate_params(cs_ctx* ctx, float* host_params, int cap, int* n_params);
 /*
  * cs_surrogate_info: HOST copies of the standardisation statistics
- * (mu_x[21], sd_x[21], mu_t[n], sd_t[n]; cap >= 42 + 2n floats, may be NULL),
- * the calibrated validation error eta (nats), the last training step's loss
- * and the training / validation pixel counts. Synchronises.
+ * (mu_x[n_in], sd_x[n_in], mu_t[n], sd_t[n]; cap >= 2 n_in + 2n floats, may
+ * be NULL), the calibrated validation error eta (nats), the last training
+ * step's loss, the training / validation pixel counts and n_in. Synchronises.
  */
 cs_status cs_surrogate_info(cs_ctx* ctx, float* host_stats, int cap, float* eta, float* loss,
-                            int* n_train, int* n_val);
+                            int* n_train, int* n_val, int* n_in);
 /*
  * cs_surrogate_save / cs_surrogate_load: the fitted surrogate (FP32 master
- * weights, standardisation statistics, calibrated eta, last loss, training
- * and validation counts) to / from a file (HOST path; a small versioned
- * binary format, host byte order). Loading replaces the context's surrogate
- * and resets the optimiser state. Both synchronise the device.
+ * weights, feature set, standardisation statistics, calibrated eta, last
+ * loss, training and validation counts) to / from a file (HOST path; a small
+ * versioned binary format, host byte order). Loading replaces the context's
+ * surrogate and resets the optimiser state. Both synchronise the device.
  * Errors: CS_ERR_INVALID_ARG (no surrogate to save, unreadable or malformed
  * file), CS_ERR_NOMEM, CS_ERR_CUDA.
  */
 cs_status cs_surrogate_save(cs_ctx* ctx, const char* path);
 cs_status cs_surrogate_load(cs_ctx* ctx, const char* path);
-int cs_mlp_param_count(int n_out);
-cs_status cs_mlp_forward(cs_ctx* ctx, const float* params, int n_out, const float* X, int rows,
-                         float* Z, void* stream);
-cs_status cs_mlp_grad(cs_ctx* ctx, const float* params, int n_out, const float* X,
+int cs_mlp_param_count(int n_in, int n_out);
+cs_status cs_mlp_forward(cs_ctx* ctx, const float* params, int n_in, int n_out, const float* X,
+                         int rows, float* Z, void* stream);
+cs_status cs_mlp_grad(cs_ctx* ctx, const float* params, int n_in, int n_out, const float* X,
                       const float* T, int rows, float* grads, float* loss, void* stream);
 
 /*
@@ -618,6 +634,8 @@ cs_status cs_unit_rates(cs_ctx* ctx, double* out, double* clock_mhz);
  *   CS_STAGE_GATHER  sample tables and majority co-supports
  *   CS_STAGE_SUM     the pixel x sample likelihood sum and label normalisation
  *   CS_STAGE_SURROGATE  the surrogate network over all pixels
+ *   CS_STAGE_TRAIN   the surrogate network's training steps (forward,
+ *                    backward, gradient sums and Adam)
  * cs_profile_read waits for the recorded events of `stage`, returns their
  * summed duration in milliseconds and the number of recorded launches, and
  * forgets them. Synchronises on those events only.
@@ -627,7 +645,8 @@ cs_status cs_unit_rates(cs_ctx* ctx, double* out, double* clock_mhz);
 #define CS_STAGE_GATHER 2
 #define CS_STAGE_SUM 3
 #define CS_STAGE_SURROGATE 4 /* network evaluation and fallback selection */
-#define CS_N_STAGES 5
+#define CS_STAGE_TRAIN 5
+#define CS_N_STAGES 6
 cs_status cs_profile_enable(cs_ctx* ctx, int on);
 cs_status cs_profile_read(cs_ctx* ctx, int stage, double* ms, int* launches);
 

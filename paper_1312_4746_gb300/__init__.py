@@ -83,6 +83,9 @@ STAGE_DIST = 1
 STAGE_GATHER = 2
 STAGE_SUM = 3
 STAGE_SURROGATE = 4
+STAGE_TRAIN = 5
+SURR_BASIC = 0
+SURR_EXTENDED = 1
 
 
 class CsError(RuntimeError):
@@ -243,17 +246,19 @@ def lib(path: str | None = None):
                                      V]
     L.cs_batch_likelihood.argtypes = [V, ctypes.POINTER(Image), I, I, ctypes.POINTER(Params), V]
     U64 = ctypes.c_uint64
-    L.cs_surrogate_fit.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, I, U64, V]
+    L.cs_surrogate_fit.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, I, I,
+                                   U64, V]
     L.cs_surrogate_eval.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, V, V,
                                     V, V]
     L.cs_surrogate_params.argtypes = [V, V, I, ctypes.POINTER(I)]
-    L.cs_surrogate_info.argtypes = [V, V, I, V, V, ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.cs_surrogate_info.argtypes = [V, V, I, V, V, ctypes.POINTER(I), ctypes.POINTER(I),
+                                    ctypes.POINTER(I)]
     L.cs_surrogate_save.argtypes = [V, ctypes.c_char_p]
     L.cs_surrogate_load.argtypes = [V, ctypes.c_char_p]
-    L.cs_mlp_param_count.argtypes = [I]
+    L.cs_mlp_param_count.argtypes = [I, I]
     L.cs_mlp_param_count.restype = I
-    L.cs_mlp_forward.argtypes = [V, V, I, V, I, V, V]
-    L.cs_mlp_grad.argtypes = [V, V, I, V, V, I, V, V, V]
+    L.cs_mlp_forward.argtypes = [V, V, I, I, V, I, V, V]
+    L.cs_mlp_grad.argtypes = [V, V, I, I, V, V, I, V, V, V]
     L.cs_unit_rates.argtypes = [V, V, V]
     L.cs_unit_rates.restype = I
     L.cs_profile_enable.argtypes = [V, I]
@@ -538,8 +543,9 @@ class Context:
     # ------------------------------------------------------------------ surrogate
 
     def surrogate_fit(self, img, bitmask, lead16, k, label_off, sample_pix, params: Params,
-                      frac=0.05, steps=400, seed=1):
-        """cs_surrogate_fit (network kept in the context)."""
+                      frac=0.05, steps=1000, features=0, seed=1):
+        """cs_surrogate_fit (network kept in the context); features: SURR_BASIC
+        or SURR_EXTENDED."""
         import numpy as np
 
         H, W = int(img.shape[0]), int(img.shape[1])
@@ -547,7 +553,7 @@ class Context:
         self.check(self._lib.cs_surrogate_fit(
             self.handle, _ptr(img), H, W, _ptr(bitmask), _ptr(lead16), int(k), len(off) - 1,
             ctypes.c_void_p(off.ctypes.data), _ptr(sample_pix), ctypes.byref(params),
-            float(frac), int(steps), ctypes.c_uint64(seed), _stream()))
+            float(frac), int(steps), int(features), ctypes.c_uint64(seed), _stream()))
 
     def surrogate_eval(self, img, bitmask, lead16, k, label_off, sample_pix, params: Params,
                        margin=0.1, out=None, want_post=True, count=True):
@@ -581,21 +587,25 @@ class Context:
         return buf
 
     def surrogate_info(self, n_labels):
-        """(stats mu_x, sd_x, mu_t, sd_t; eta; last loss; n_train; n_val)."""
+        """(stats mu_x, sd_x, mu_t, sd_t; eta; last loss; n_train; n_val; n_in)."""
         import numpy as np
 
-        st = np.zeros(42 + 2 * n_labels, np.float32)
         eta = ctypes.c_float()
         loss = ctypes.c_float()
         ntr = ctypes.c_int()
         nva = ctypes.c_int()
+        nin = ctypes.c_int()
+        self.check(self._lib.cs_surrogate_info(self.handle, None, 0, None, None, None, None,
+                                               ctypes.byref(nin)))
+        m = nin.value
+        st = np.zeros(2 * m + 2 * n_labels, np.float32)
         self.check(self._lib.cs_surrogate_info(self.handle, ctypes.c_void_p(st.ctypes.data), st.size,
                                                ctypes.byref(eta), ctypes.byref(loss),
-                                               ctypes.byref(ntr), ctypes.byref(nva)))
+                                               ctypes.byref(ntr), ctypes.byref(nva), None))
         n = n_labels
-        return {"mu_x": st[:21], "sd_x": st[21:42], "mu_t": st[42:42 + n],
-                "sd_t": st[42 + n:42 + 2 * n], "eta": eta.value, "loss": loss.value,
-                "n_train": ntr.value, "n_val": nva.value}
+        return {"mu_x": st[:m], "sd_x": st[m:2 * m], "mu_t": st[2 * m:2 * m + n],
+                "sd_t": st[2 * m + n:2 * m + 2 * n], "eta": eta.value, "loss": loss.value,
+                "n_train": ntr.value, "n_val": nva.value, "n_in": m}
 
     def surrogate_save(self, path):
         """cs_surrogate_save (synchronises)."""
@@ -606,20 +616,24 @@ class Context:
         self.check(self._lib.cs_surrogate_load(self.handle, os.fsencode(path)))
 
     def mlp_forward(self, params_dev, n_out, X):
+        """cs_mlp_forward on standardised rows X (rows x n_in)."""
         import torch
 
         Z = torch.empty((X.shape[0], n_out), dtype=torch.float32, device=X.device)
-        self.check(self._lib.cs_mlp_forward(self.handle, _ptr(params_dev), n_out, _ptr(X),
-                                            int(X.shape[0]), _ptr(Z), _stream()))
+        self.check(self._lib.cs_mlp_forward(self.handle, _ptr(params_dev), int(X.shape[1]), n_out,
+                                            _ptr(X), int(X.shape[0]), _ptr(Z), _stream()))
         return Z
 
     def mlp_grad(self, params_dev, n_out, X, T):
+        """cs_mlp_grad: (gradient, loss) on standardised rows X and targets T."""
         import torch
 
-        g = torch.empty(self._lib.cs_mlp_param_count(n_out), dtype=torch.float32, device=X.device)
+        n_in = int(X.shape[1])
+        g = torch.empty(self._lib.cs_mlp_param_count(n_in, n_out), dtype=torch.float32,
+                        device=X.device)
         loss = torch.empty(1, dtype=torch.float32, device=X.device)
-        self.check(self._lib.cs_mlp_grad(self.handle, _ptr(params_dev), n_out, _ptr(X), _ptr(T),
-                                         int(X.shape[0]), _ptr(g), _ptr(loss), _stream()))
+        self.check(self._lib.cs_mlp_grad(self.handle, _ptr(params_dev), n_in, n_out, _ptr(X),
+                                         _ptr(T), int(X.shape[0]), _ptr(g), _ptr(loss), _stream()))
         return g, loss
 
 

@@ -174,6 +174,7 @@ void cs_destroy(cs_ctx* ctx) {
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->surr_buf) cudaFree(ctx->surr_buf);
+    if (ctx->mlp_part) cudaFree(ctx->mlp_part);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->side2) cudaStreamDestroy(ctx->side2);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);

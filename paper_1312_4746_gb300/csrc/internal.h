@@ -37,8 +37,11 @@ struct cs_ctx {
     // learned surrogate (allocated by the first fit)
     float* surr_buf = nullptr;
     size_t surr_cap = 0;
-    int surr_n = 0, surr_train = 0, surr_val = 0;
+    int surr_n = 0, surr_nin = 0, surr_set = 0, surr_train = 0, surr_val = 0;
     bool surr_ready = false;
+    // per-CTA gradient sums of the network's training kernel
+    float* mlp_part = nullptr;
+    size_t mlp_part_cap = 0;
     int* last_fb_count = nullptr;  // FP64 recompute count of the last tensor-core sum
     cudaStream_t side = nullptr;   // distance transform overlapping the codes
     cudaStream_t side2 = nullptr;  // sample order overlapping both
@@ -457,29 +460,33 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
                       const int32_t* sample_pix, const cs_params* prm, float* neglog,
                       float* post);
 
-// Learned surrogate (MLP) kernels.
-int mlp_param_count(int n);
-size_t mlp_train_smem(int n);
-cudaError_t launch_mlp_train(const float* params, int n, const float* X, const float* T,
-                             int n_rows, long long start, int batch, float* grads,
-                             float* loss_acc, cudaStream_t st);
-cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr, int t,
-                        cudaStream_t st);
-cudaError_t launch_mlp_forward(const float* params, int n, const float* X, int rows, float* Z,
-                               cudaStream_t st);
-cudaError_t launch_features(const float* img, const float* lead16, int H, int W,
+// Learned surrogate (MLP) kernels (k_mlp.cu).
+int mlp_param_count(int nin, int n);
+int mlp_train_ctas(int batch, int n_sm);   // CTAs of one training step
+int mlp_part_stride(int nin, int n);       // floats per CTA in the partials buffer
+cudaError_t launch_mlp_train(const float* params, int nin, int n, const float* X, const float* T,
+                             int n_rows, long long start, int batch, float* part, int G,
+                             int* d_err, uint64_t wait_ns, cudaStream_t st);
+// sums G CTAs' partials into g_out (may be NULL) and *loss (may be NULL); with
+// m non-NULL also an Adam step (step number t >= 1) on p
+cudaError_t launch_reduce_adam(const float* part, int G, int nin, int n, float* p, float* g_out,
+                               float* m, float* v, float lr, int t, float* loss, cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* params, int nin, int n, const float* X, int rows,
+                               float* Z, int n_sm, int* d_err, uint64_t wait_ns, cudaStream_t st);
+cudaError_t launch_features(const float* img, const float* lead16, const int32_t* dist2, int H,
+                            int W, int n, int feature_set, float d_min, int nin,
                             const int32_t* list, int rows, float* X, cudaStream_t st);
-cudaError_t launch_stats(const float* X, const float* T, int n, int cap, int n_rows,
+cudaError_t launch_stats(const float* X, int nin, const float* T, int n, int cap, int n_rows,
                          float* stats, cudaStream_t st);
-cudaError_t launch_standardize(float* X, const float* T, int n, int cap, int rows,
+cudaError_t launch_standardize(float* X, int nin, const float* T, int n, int cap, int rows,
                                const float* stats, float* Ts, cudaStream_t st);
-cudaError_t launch_init_params(float* p, float* m, float* v, float* g, int n, uint64_t seed,
+cudaError_t launch_init_params(float* p, float* m, float* v, int nin, int n, uint64_t seed,
                                cudaStream_t st);
-cudaError_t launch_calib(const float* Z, const float* Ts, int n, int rows, const float* stats,
-                         float* eta, cudaStream_t st);
+cudaError_t launch_calib(const float* Z, const float* Ts, int nin, int n, int rows,
+                         const float* stats, float* eta, cudaStream_t st);
 struct SurrogateEvalArgs {
     const float* params;
-    int n;
+    int nin, n, feature_set;
     const float* stats;
     const float* eta;
     const float* img;
@@ -496,5 +503,8 @@ struct SurrogateEvalArgs {
     float* post;
     int32_t* fb_list;
     int* fb_count;
+    int n_sm;
+    int* d_err;
+    uint64_t wait_ns;
 };
 cudaError_t launch_surrogate_eval(const SurrogateEvalArgs& a, cudaStream_t st);

@@ -1,305 +1,781 @@
-// Learned surrogate of the data term: a 21 -> 64 -> 64 -> 64 -> n MLP (SiLU)
-// that predicts, per pixel and label, the log kernel sum
+// Learned surrogate of the data term on the tensor cores: an
+// nin -> 64 -> 64 -> 64 -> n MLP (SiLU) that predicts, per pixel and label,
+// the log kernel sum
 //   T_i(x) = log sum_j k_rho(x - x_ij) k_sigma(I - I_ij) [exp(-TSM / beta)]
 // of Sec. 3.1 (Eq. color, Eq. post_text); L_i then follows exactly from the
-// scribble distance transform. Weights are used in bf16 (rounded from fp32
-// masters); all arithmetic is fp32.
+// scribble distance transform (and, in the factorised mode, the exact
+// texture posterior of Eq. post_text).
 //
-// Parameter vector (fp32), n = number of labels:
-//   W1 [64][21] | b1 [64] | W2 [64][64] | b2 [64] | W3 [64][64] | b3 [64] | W4 [n][64] | b4 [n]
+// Parameter vector (fp32 masters), nin inputs, n labels:
+//   W1 [64][nin] | b1 [64] | W2 [64][64] | b2 [64] | W3 [64][64] | b3 [64] | W4 [n][64] | b4 [n]
+// The kernels use the weights rounded to bf16.
 //
-// mlp_train_kernel: one block of 64 threads = 64 samples of a minibatch; the
-//   bf16-rounded weights and per-sample activations (h_l) and SiLU derivatives
-//   (g_l) sit in shared memory; after the forward pass each thread forms its
-//   output error, back-propagates it, and the block forms the weight
-//   gradients as small GEMMs over its 64 samples, accumulated into a global
-//   gradient vector with atomics (loss = mean (z - t)^2 / 2 over batch and labels).
-// adam_kernel: bias-corrected Adam on the fp32 masters, clears the gradient.
-// mlp_eval_kernel: forward pass per pixel from raw features, then
-//   L_i = sd_t,i z_i + mu_t,i - log m_i - log(2 pi s2_i) - 1.5 log(2 pi sigma_c2)
-//   (s2_i = rho_i^2, or rho_i when rho is read as the location variance)
-//   (+ the factorised texture log-posterior), posteriors, and the fallback
-//   decision (top-2 posterior margin below `margin`, or top-2 log-likelihood
-//   gap below the calibrated `gap_min`): such pixels are appended to a list
-//   that the exact sum then overwrites.
+// Every contraction runs on tcgen05 (kind::f16, bf16 operands, fp32
+// accumulation in tensor memory), 128 rows (pixels or training rows) per
+// tile, one thread per row for the element-wise work:
+//   forward   Z_l = H_{l-1} W_l^T with H = hi + lo, two bf16 pieces of the
+//             fp32 activation (hi = bf16(h), lo = bf16(h - hi)), so the
+//             activations keep about 16 bits;
+//   backward  P_{l-1} = D_l W_l with D = dLoss/dZ_l split the same way, and
+//             the weight gradient dW_l = D_l^T H_{l-1} from the hi pieces of
+//             H (D in both pieces), summed over the rows of the tile.
+// Operands live in shared memory in one "row layout": element (r, c) of a
+// tile with R rows at byte (c / 8) * 16 R + 16 r + 2 (c % 8). Read K-major
+// (K = columns) it feeds the forward and the propagation's A operand; read
+// MN-major (K = rows) the same bytes feed the weight gradient's operands and
+// the propagation's B operand (W itself, not a transposed copy).
+//
+// Kernels
+//   mlp_train_kernel  forward and backward over the CTA's tiles of a
+//                     minibatch; per-CTA gradient sums (and loss) to a
+//                     partials buffer, in a fixed order.
+//   reduce_adam_kernel sums the partials over the CTAs (fixed order), then
+//                     optionally takes a bias-corrected Adam step.
+//   mlp_fwd_kernel<ROWS>  forward pass on given standardised rows.
+//   mlp_fwd_kernel<EVAL>  features from the pixel, forward pass, then
+//                     L_i = sd_t,i z_i + mu_t,i - log m_i - log(2 pi s2_i)
+//                           - 1.5 log(2 pi sigma_c2) (+ the factorised
+//                     texture log-posterior), the posteriors, and the fallback
+//                     decision (top-2 posterior margin below `margin`, or the
+//                     top-2 gap below the calibrated gap_min): such pixels are
+//                     listed for the exact sum to overwrite.
 #include <cuda_bf16.h>
 
 #include <cstdint>
 
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
-constexpr int NIN = 21, HID = 64, BS = 64, SP = BS + 1;  // SP: padded sample stride
+constexpr int HID = 64;
+constexpr int TR = 128;   // rows per tile (the MMA's M)
+constexpr int NTH = 128;  // threads per CTA, one row each
+constexpr uint64_t MLP_WAIT_NS = 1000000000ull;
 
-__host__ __device__ constexpr int off_W1() { return 0; }
-__host__ __device__ constexpr int off_b1() { return HID * NIN; }
-__host__ __device__ constexpr int off_W2() { return off_b1() + HID; }
-__host__ __device__ constexpr int off_b2() { return off_W2() + HID * HID; }
-__host__ __device__ constexpr int off_W3() { return off_b2() + HID; }
-__host__ __device__ constexpr int off_b3() { return off_W3() + HID * HID; }
-__host__ __device__ constexpr int off_W4() { return off_b3() + HID; }
-__host__ __device__ inline int off_b4(int n) { return off_W4() + n * HID; }
-
-__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-__device__ __forceinline__ float sigm(float u) { return 1.f / (1.f + __expf(-u)); }
-
-// weights (bf16-rounded) into shared memory
-__device__ __forceinline__ void load_weights(const float* __restrict__ params, int np, float* sw) {
-    for (int i = threadIdx.x; i < np; i += blockDim.x) sw[i] = bf16r(params[i]);
+struct Dims {
+    int nin, K0, n, NOp;
+};
+__host__ __device__ inline Dims dims_of(int nin, int n) {
+    return Dims{nin, nin <= 32 ? 32 : 64, n, (n + 15) & ~15};
 }
 
-// z = W4 silu(W3 silu(W2 silu(W1 x + b1) + b2) + b3) + b4 for one sample in
-// registers; optional per-sample shared buffers receive h_l and silu'(u_l).
-template <bool STORE>
-__device__ __forceinline__ void forward_one(const float* sw, const float (&x)[NIN], int n,
-                                            float* H1, float* H2, float* H3, float* G1, float* G2,
-                                            float* G3, int s, float* z) {
-    float h[HID], a[HID];
-    const float* W1 = sw + off_W1();
+struct Off {
+    int W1, b1, W2, b2, W3, b3, W4, b4, np;
+};
+__host__ __device__ inline Off off_of(int nin, int n) {
+    Off o;
+    o.W1 = 0;
+    o.b1 = HID * nin;
+    o.W2 = o.b1 + HID;
+    o.b2 = o.W2 + HID * HID;
+    o.W3 = o.b2 + HID;
+    o.b3 = o.W3 + HID * HID;
+    o.W4 = o.b3 + HID;
+    o.b4 = o.W4 + n * HID;
+    o.np = o.b4 + n;
+    return o;
+}
+
+// ------------------------------------------------------------------ operand helpers
+// Shared-memory descriptor with explicit leading / stride byte offsets (no swizzle).
+__device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = tc::smem_u32(p);
+    uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(lbo >> 4) << 16;
+    d |= (uint64_t)(sbo >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// Row-layout tile of R rows read K-major (K = columns): the next 8 columns
+// are 16 R bytes on, the next 8 rows 128 bytes on.
+__device__ __forceinline__ uint64_t desc_k(const void* p, uint32_t R) { return sdesc(p, 16u * R, 128u); }
+// The same tile read MN-major (MN = columns, K = rows): the next 8 rows (K)
+// are 128 bytes on, the next 8 columns (MN) 16 R bytes on.
+__device__ __forceinline__ uint64_t desc_mn(const void* p, uint32_t R) { return sdesc(p, 128u, 16u * R); }
+constexpr uint32_t A_MN = 1u << 15;  // instruction descriptor: A read MN-major
+constexpr uint32_t B_MN = 1u << 16;  // instruction descriptor: B read MN-major
+
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float bf_hi(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Row r of a 128-row tile: columns [0, C) of v as hi and (optionally) lo
+// bf16 pieces, 16-byte stores (C a multiple of 8).
+template <int C>
+__device__ __forceinline__ void put_row(const float (&v)[64], unsigned char* hi, unsigned char* lo,
+                                        int r) {
 #pragma unroll
-    for (int j = 0; j < HID; ++j) {
-        float acc = sw[off_b1() + j];
+    for (int c8 = 0; c8 < C / 8; ++c8) {
+        uint4 h, l;
+        float e[8];
 #pragma unroll
-        for (int kk = 0; kk < NIN; ++kk) acc = fmaf(W1[j * NIN + kk], x[kk], acc);
-        const float sg = sigm(acc);
-        h[j] = acc * sg;
-        if (STORE) {
-            H1[j * SP + s] = h[j];
-            G1[j * SP + s] = sg * (1.f + acc * (1.f - sg));
+        for (int j = 0; j < 8; ++j) e[j] = v[8 * c8 + j];
+        h.x = pack_bf2(e[0], e[1]);
+        h.y = pack_bf2(e[2], e[3]);
+        h.z = pack_bf2(e[4], e[5]);
+        h.w = pack_bf2(e[6], e[7]);
+        *reinterpret_cast<uint4*>(hi + c8 * (16 * TR) + 16 * r) = h;
+        if (lo) {
+            l.x = pack_bf2(e[0] - bf_hi(e[0]), e[1] - bf_hi(e[1]));
+            l.y = pack_bf2(e[2] - bf_hi(e[2]), e[3] - bf_hi(e[3]));
+            l.z = pack_bf2(e[4] - bf_hi(e[4]), e[5] - bf_hi(e[5]));
+            l.w = pack_bf2(e[6] - bf_hi(e[6]), e[7] - bf_hi(e[7]));
+            *reinterpret_cast<uint4*>(lo + c8 * (16 * TR) + 16 * r) = l;
         }
     }
-    for (int layer = 0; layer < 2; ++layer) {
-        const float* Wl = sw + (layer == 0 ? off_W2() : off_W3());
-        const float* bl = sw + (layer == 0 ? off_b2() : off_b3());
+}
+__device__ __forceinline__ void put_row_k0(const float (&v)[64], int K0, unsigned char* hi,
+                                           unsigned char* lo, int r) {
+    if (K0 == 32) put_row<32>(v, hi, lo, r);
+    else put_row<64>(v, hi, lo, r);
+}
+
+// fp32 weights [rows][cols] -> bf16 row-layout tile of R rows and Cp columns
+// (zero outside rows x cols)
+__device__ void load_w(const float* __restrict__ w, int rows, int cols, int R, int Cp,
+                       unsigned char* dst) {
+    for (int i = threadIdx.x; i < R * Cp; i += blockDim.x) {
+        const int r = i / Cp, c = i % Cp;
+        const float v = (r < rows && c < cols) ? w[r * cols + c] : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(dst + (c >> 3) * (16 * R) + 16 * r + 2 * (c & 7)) =
+            __float2bfloat16_rn(v);
+    }
+}
+
+// columns [col, col + 16 * NC) of this warp's 32 lanes
+template <int NC>
+__device__ __forceinline__ void tm_load(uint32_t taddr, float (&v)[64]) {
 #pragma unroll
-        for (int j = 0; j < HID; ++j) a[j] = bl[j];
-        for (int kk = 0; kk < HID; ++kk) {
-            const float hk = h[kk];
+    for (int q = 0; q < NC; ++q) {
+        uint32_t r[16];
+        tc::tmem_ld16(taddr + 16 * q, r);
+        tc::tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < HID; ++j) a[j] = fmaf(Wl[j * HID + kk], hk, a[j]);
+        for (int j = 0; j < 16; ++j) v[16 * q + j] = __uint_as_float(r[j]);
+    }
+}
+__device__ __forceinline__ void tm_load_n(uint32_t taddr, int ncols, float (&v)[64]) {
+    switch (ncols / 16) {
+        case 1: tm_load<1>(taddr, v); break;
+        case 2: tm_load<2>(taddr, v); break;
+        case 3: tm_load<3>(taddr, v); break;
+        default: tm_load<4>(taddr, v); break;
+    }
+}
+
+__device__ __forceinline__ float sigm(float u) { return 1.f / (1.f + __expf(-u)); }
+
+// Sum of v[0..63] over the warp's lanes by recursive halving: afterwards
+// v[0] and v[1] hold the sums of columns bcol(lane) and bcol(lane) + 1.
+__device__ __forceinline__ void warp_colsum(float (&v)[64], int lane) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int h = 16 >> s, half = 32 >> s;
+        const bool up = lane & h;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const float send = up ? v[j] : v[j + half];
+            const float keep = up ? v[j + half] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
         }
-        float* Hs = layer == 0 ? H2 : H3;
-        float* Gs = layer == 0 ? G2 : G3;
-#pragma unroll
-        for (int j = 0; j < HID; ++j) {
-            const float sg = sigm(a[j]);
-            h[j] = a[j] * sg;
-            if (STORE) {
-                Hs[j * SP + s] = h[j];
-                Gs[j * SP + s] = sg * (1.f + a[j] * (1.f - sg));
+    }
+}
+__device__ __forceinline__ int bcol(int lane) {
+    return ((lane & 16) ? 32 : 0) + ((lane & 8) ? 16 : 0) + ((lane & 4) ? 8 : 0) +
+           ((lane & 2) ? 4 : 0) + ((lane & 1) ? 2 : 0);
+}
+
+// All threads: bounded wait for the commit with the given parity; the result
+// is uniform over the block.
+__device__ bool wait_all(uint64_t* bar, uint32_t parity, uint64_t wait_ns, int* d_err, int site) {
+    bool ok = true;
+    uint64_t deadline = 0;
+    for (uint32_t n = 0;; ++n) {
+        if (tc::mbar_try_wait(bar, parity, 1000u)) break;
+        if ((n & 63u) == 63u) {
+            const uint64_t now = tc::globaltimer();
+            if (deadline == 0) deadline = now + wait_ns;
+            else if (now > deadline) {
+                ok = false;
+                break;
             }
         }
     }
-    const float* W4 = sw + off_W4();
-    for (int j = 0; j < n; ++j) {
-        float acc = sw[off_b4(n) + j];
+    tc::fence_after_sync();
+    ok = __syncthreads_and(ok);
+    if (!ok && threadIdx.x == 0 && atomicCAS(d_err, 0, CS_DEVERR_TIMEOUT) == 0) d_err[1] = site;
+    return ok;
+}
+// After a wait that gave up: one more bounded wait for the MMAs in flight,
+// so that the tensor memory is not freed under them.
+__device__ void drain(uint64_t* bar, uint32_t parity, uint64_t wait_ns) {
+    const uint64_t deadline = tc::globaltimer() + wait_ns;
+    while (!tc::mbar_try_wait(bar, parity, 1000u))
+        if (tc::globaltimer() > deadline) break;
+}
+
+// Generic-proxy shared-memory writes and tensor-memory reads of every thread
+// are done before thread 0 issues MMAs.
+__device__ __forceinline__ void to_issue() {
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+}
+
+// thread 0: D(128 x N) (+)= [Ah | Al](128 x 2K) [W | W]^T, W a row-layout tile
+// of N rows (K-major).
+__device__ __forceinline__ void mma_fwd(uint32_t d, const unsigned char* Ah, const unsigned char* Al,
+                                        int K, const unsigned char* W, int N) {
+    const uint32_t id = tc::idesc(TR, N, 1, 1);
+    for (int part = 0; part < 2; ++part) {
+        const unsigned char* A = part ? Al : Ah;
+        for (int kk = 0; kk < K / 16; ++kk)
+            tc::mma_bf16(d, desc_k(A + kk * (32 * TR), TR), desc_k(W + kk * 32 * N, N), id,
+                         (part | kk) ? 1u : 0u);
+    }
+}
+// thread 0: P(128 x 64) = D(128 x [hi | lo] of K) W(K x 64), W a row-layout
+// tile of K rows read MN-major; D holds hi in columns [0, 64), lo in [64, 128).
+__device__ __forceinline__ void mma_prop(uint32_t d, const unsigned char* D, int K,
+                                         const unsigned char* W) {
+    const uint32_t id = tc::idesc(TR, HID, 1, 1) | B_MN;
+    for (int part = 0; part < 2; ++part)
+        for (int kk = 0; kk < K / 16; ++kk)
+            tc::mma_bf16(d, desc_k(D + (part * 8 + 2 * kk) * (16 * TR), TR),
+                         desc_mn(W + kk * 256, K), id, (part | kk) ? 1u : 0u);
+}
+// thread 0: G(128 x N) (+)= D^T H over the tile's 128 rows: row o' of G is
+// output o' of D's hi piece (o' < 64) or of its lo piece (o' - 64).
+__device__ __forceinline__ void mma_wgrad(uint32_t g, const unsigned char* D, const unsigned char* H,
+                                          int N, bool accumulate) {
+    const uint32_t id = tc::idesc(TR, N, 1, 1) | A_MN | B_MN;
+    for (int kk = 0; kk < TR / 16; ++kk)
+        tc::mma_bf16(g, desc_mn(D + kk * 256, TR), desc_mn(H + kk * 256, TR), id,
+                     (accumulate || kk) ? 1u : 0u);
+}
+
+// ------------------------------------------------------------------ training
+struct TrainLayout {
+    uint32_t W1, W2, W3, W4, X, H1, H2, H3, HL, D, F32, BAR, total;
+};
+__host__ __device__ inline TrainLayout train_layout(int K0, int NOp) {
+    TrainLayout L;
+    uint32_t o = 0;
+    L.W1 = o; o += 2 * HID * K0;
+    L.W2 = o; o += 2 * HID * HID;
+    L.W3 = o; o += 2 * HID * HID;
+    L.W4 = o; o += 2 * NOp * HID;
+    L.X = o; o += 2 * TR * K0;
+    L.H1 = o; o += 2 * TR * HID;
+    L.H2 = o; o += 2 * TR * HID;
+    L.H3 = o; o += 2 * TR * HID;
+    L.HL = o; o += 2 * TR * HID;
+    L.D = o; o += 2 * TR * 2 * HID;
+    L.F32 = o; o += 4 * (4 * HID + 2 * 4 * HID + 4);  // biases, column-sum exchange (x2), loss
+    L.BAR = o; o += 16;
+    L.total = o;
+    return L;
+}
+
+struct TrainArgs {
+    const float* params;
+    int nin, n;
+    const float* X;  // [n_rows][nin] standardised features
+    const float* T;  // [n_rows][n] standardised targets
+    int n_rows;
+    long long start;
+    int batch;       // rows of this step: (start + b) mod n_rows, b < batch
+    float* part;     // [gridDim.x][PS]: gradient sums, then the loss sum
+    int PS;
+    int* d_err;
+    uint64_t wait_ns;
+};
+
+// This thread's delta (row tid, 64 columns) into D as hi / lo pieces, and its
+// column sums (the bias gradient) into ex[buf][warp][64].
+__device__ __forceinline__ void put_delta(float (&dl)[64], unsigned char* D, float* ex, int tid) {
+    put_row<64>(dl, D, D + 8 * 16 * TR, tid);
+    warp_colsum(dl, tid & 31);
+    const int c = bcol(tid & 31);
+    ex[(tid >> 5) * HID + c] = dl[0];
+    ex[(tid >> 5) * HID + c + 1] = dl[1];
+}
+
+__global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const Dims dm = dims_of(a.nin, a.n);
+    const Off of = off_of(a.nin, a.n);
+    const TrainLayout L = train_layout(dm.K0, dm.NOp);
+    unsigned char *W1 = sm + L.W1, *W2 = sm + L.W2, *W3 = sm + L.W3, *W4 = sm + L.W4;
+    unsigned char *Xh = sm + L.X, *H1 = sm + L.H1, *H2 = sm + L.H2, *H3 = sm + L.H3;
+    unsigned char *HL = sm + L.HL, *D = sm + L.D;
+    float* bias = reinterpret_cast<float*>(sm + L.F32);  // b1 b2 b3 b4, 64 each
+    float* ex = bias + 4 * HID;                          // [2][4][64]
+    float* lred = ex + 2 * 4 * HID;                      // [4]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.BAR + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    load_w(a.params + of.W1, HID, a.nin, HID, dm.K0, W1);
+    load_w(a.params + of.W2, HID, HID, HID, HID, W2);
+    load_w(a.params + of.W3, HID, HID, HID, HID, W3);
+    load_w(a.params + of.W4, a.n, HID, dm.NOp, HID, W4);
+    for (int i = tid; i < 4 * HID; i += NTH) {
+        const int l = i / HID, c = i % HID;
+        const int boff = l == 0 ? of.b1 : l == 1 ? of.b2 : l == 2 ? of.b3 : of.b4;
+        bias[i] = (l < 3 || c < a.n) ? __bfloat162float(__float2bfloat16_rn(a.params[boff + c])) : 0.f;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = *tslot;
+    const uint32_t tl = tm + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+    // tensor-memory columns: Z1 0, Z2 64, Z3 128, Z4 192 (then P3 192, P2 128,
+    // P1 64); gradients G1 256, G2 320, G3 384, G4 448
+    const float inv = 1.f / ((float)a.batch * (float)a.n);
+    const int tiles = (a.batch + TR - 1) / TR;
+    uint32_t ph = 0;
+    bool ok = true;
+    float dbias[4] = {0.f, 0.f, 0.f, 0.f};  // thread c < 64: bias gradient column c
+    float lsum = 0.f;
+    int xb = 0;                             // column-sum exchange buffer
+    auto colsum_take = [&](int l) {         // after a block barrier
+        if (tid < HID) {
+            const float* e = ex + xb * 4 * HID;
+            dbias[l] += (e[tid] + e[HID + tid]) + (e[2 * HID + tid] + e[3 * HID + tid]);
+        }
+        xb ^= 1;
+    };
+    float v[64], w[64];
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const bool first = tile == (int)blockIdx.x;
+        const int b = tile * TR + tid;
+        const bool valid = b < a.batch;
+        const long long row = valid ? (a.start + b) % a.n_rows : 0;
+        // ---- forward
 #pragma unroll
-        for (int kk = 0; kk < HID; ++kk) acc = fmaf(W4[j * HID + kk], h[kk], acc);
-        z[j] = acc;
+        for (int c = 0; c < 64; ++c) v[c] = (valid && c < a.nin) ? a.X[row * a.nin + c] : 0.f;
+        put_row_k0(v, dm.K0, Xh, HL, tid);
+        to_issue();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            mma_fwd(tm + 0, Xh, HL, dm.K0, W1, HID);
+            tc::mma_commit(bar);
+        }
+        if (!(ok = wait_all(bar, ph, a.wait_ns, a.d_err, 61))) break;
+        ph ^= 1;
+        unsigned char* Hs[3] = {H1, H2, H3};
+        const unsigned char* Ws[3] = {W2, W3, W4};
+        for (int l = 0; l < 3 && ok; ++l) {
+            tm_load<4>(tl + 64 * l, v);
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+                const float u = v[c] + bias[l * HID + c];
+                v[c] = u * sigm(u);
+            }
+            put_row<64>(v, Hs[l], HL, tid);
+            to_issue();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                mma_fwd(tm + 64 * (l + 1), Hs[l], HL, HID, Ws[l], l < 2 ? HID : dm.NOp);
+                tc::mma_commit(bar);
+            }
+            ok = wait_all(bar, ph, a.wait_ns, a.d_err, 62 + l);
+            ph ^= 1;
+        }
+        if (!ok) break;
+        // ---- loss and output delta
+        tm_load_n(tl + 192, dm.NOp, v);
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+            float dl = 0.f;
+            if (valid && c < a.n) {
+                dl = v[c] + bias[3 * HID + c] - a.T[row * a.n + c];
+                lsum = fmaf(dl, dl, lsum);
+            }
+            w[c] = dl * inv;
+        }
+        put_delta(w, D, ex + xb * 4 * HID, tid);
+        to_issue();
+        colsum_take(3);
+        if (tid == 0) {
+            tc::fence_after_sync();
+            mma_prop(tm + 192, D, dm.NOp, W4);
+            mma_wgrad(tm + 448, D, H3, HID, !first);
+            tc::mma_commit(bar);
+        }
+        if (!(ok = wait_all(bar, ph, a.wait_ns, a.d_err, 65))) break;
+        ph ^= 1;
+        // ---- hidden deltas: D_l = P_l * silu'(Z_l + b_l)
+        const unsigned char* Hin[3] = {Xh, H1, H2};
+        for (int l = 2; l >= 0 && ok; --l) {
+            const int pcol = l == 2 ? 192 : 64 * (l + 1);
+            tm_load<4>(tl + pcol, v);
+            tm_load<4>(tl + 64 * l, w);
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+                const float u = w[c] + bias[l * HID + c];
+                const float s = sigm(u);
+                w[c] = v[c] * (s * (1.f + u * (1.f - s)));
+            }
+            put_delta(w, D, ex + xb * 4 * HID, tid);
+            to_issue();
+            colsum_take(l);
+            if (tid == 0) {
+                tc::fence_after_sync();
+                if (l > 0) mma_prop(tm + 64 * l, D, HID, l == 2 ? W3 : W2);
+                mma_wgrad(tm + 256 + 64 * l, D, Hin[l], l == 0 ? dm.K0 : HID, !first);
+                tc::mma_commit(bar);
+            }
+            ok = wait_all(bar, ph, a.wait_ns, a.d_err, 66 + l);
+            ph ^= 1;
+        }
+    }
+    if (ok) {
+        // ---- per-CTA sums to the partials buffer: G rows o' and o' + 64 add up
+        float* P = a.part + (size_t)blockIdx.x * a.PS;
+        float* S = reinterpret_cast<float*>(D);  // 64 x 65 floats
+        for (int l = 0; l < 4; ++l) {
+            const int cols = l == 0 ? dm.K0 : HID;
+            const int cv = l == 0 ? a.nin : HID, rv = l == 3 ? a.n : HID;
+            const int woff = l == 0 ? of.W1 : l == 1 ? of.W2 : l == 2 ? of.W3 : of.W4;
+            const int boff = l == 0 ? of.b1 : l == 1 ? of.b2 : l == 2 ? of.b3 : of.b4;
+            tm_load_n(tl + 256 + 64 * l, cols, v);
+            __syncthreads();
+            if (tid >= HID) {
+#pragma unroll
+                for (int c = 0; c < 64; ++c)
+                    if (c < cols) S[(tid - HID) * 65 + c] = v[c];
+            }
+            __syncthreads();
+            if (tid < HID) {
+#pragma unroll
+                for (int c = 0; c < 64; ++c)
+                    if (c < cols) S[tid * 65 + c] += v[c];
+            }
+            __syncthreads();
+            for (int i = tid; i < rv * cv; i += NTH) P[woff + i] = S[(i / cv) * 65 + i % cv];
+            if (tid < rv) P[boff + tid] = dbias[l];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if ((tid & 31) == 0) lred[warp] = lsum;
+        __syncthreads();
+        if (tid == 0) P[of.np] = 0.5f * inv * ((lred[0] + lred[1]) + (lred[2] + lred[3]));
+    } else {
+        drain(bar, ph, a.wait_ns);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tm, 512);
     }
 }
 
-// Block-local weight gradient: grad[j][c] += sum_s D[j][s] * A[c][s] for
-// j < rows, c < cols (thread c owns column c).
-__device__ __forceinline__ void wgrad(const float* D, const float* A, int rows, int cols,
-                                      float* __restrict__ gW, float* __restrict__ gb) {
-    const int c = threadIdx.x;
-    if (c < cols) {
-        float av[BS];
-#pragma unroll
-        for (int s = 0; s < BS; ++s) av[s] = A[c * SP + s];
-        for (int j = 0; j < rows; ++j) {
-            float acc = 0.f;
-#pragma unroll
-            for (int s = 0; s < BS; ++s) acc = fmaf(D[j * SP + s], av[s], acc);
-            atomicAdd(gW + j * cols + c, acc);
-        }
-    }
-    for (int j = threadIdx.x; j < rows; j += blockDim.x) {
-        float acc = 0.f;
-        for (int s = 0; s < BS; ++s) acc += D[j * SP + s];
-        atomicAdd(gb + j, acc);
-    }
-}
-
-// X: rows of standardised features; T: standardised targets [row][n];
-// rows taken as (start + b) mod n_rows for b < batch (batch a multiple of 64).
-__global__ void __launch_bounds__(BS) mlp_train_kernel(const float* __restrict__ params, int n,
-                                                     const float* __restrict__ X,
-                                                     const float* __restrict__ T, int n_rows,
-                                                     long long start, int batch,
-                                                     float* __restrict__ grads,
-                                                     float* __restrict__ loss_acc) {
-    extern __shared__ float smem[];
-    const int np = off_b4(n) + n;
-    float* sw = smem;
-    float* H1 = sw + ((np + 3) & ~3);
-    float* H2 = H1 + HID * SP;
-    float* H3 = H2 + HID * SP;
-    float* G1 = H3 + HID * SP;
-    float* G2 = G1 + HID * SP;
-    float* G3 = G2 + HID * SP;
-    float* DZ = G3 + HID * SP;   // [n][SP]
-    float* XS = DZ + 64 * SP;    // [21][SP]
-    load_weights(params, np, sw);
-    __syncthreads();
-    const int s = threadIdx.x;
-    const long long row = (start + (long long)blockIdx.x * BS + s) % n_rows;
-    float x[NIN];
-#pragma unroll
-    for (int kk = 0; kk < NIN; ++kk) {
-        x[kk] = X[row * NIN + kk];
-        XS[kk * SP + s] = x[kk];
-    }
-    float z[64];
-    forward_one<true>(sw, x, n, H1, H2, H3, G1, G2, G3, s, z);
-    const float inv = 1.f / ((float)batch * (float)n);
-    float l = 0.f;
-    for (int j = 0; j < n; ++j) {
-        const float d = z[j] - T[row * n + j];
-        l += d * d;
-        DZ[j * SP + s] = d * inv;
-    }
-    atomicAdd(loss_acc, 0.5f * l * inv);
-    __syncthreads();
-    // output layer gradients
-    wgrad(DZ, H3, n, HID, grads + off_W4(), grads + off_b4(n));
-    // delta of layer 3 (in place over G3): g3 * W4^T dz
-    {
-        const float* W4 = sw + off_W4();
-        for (int kk = 0; kk < HID; ++kk) {
-            float acc = 0.f;
-            for (int j = 0; j < n; ++j) acc = fmaf(DZ[j * SP + s], W4[j * HID + kk], acc);
-            G3[kk * SP + s] *= acc;
-        }
-    }
-    __syncthreads();
-    wgrad(G3, H2, HID, HID, grads + off_W3(), grads + off_b3());
-    {
-        const float* W3 = sw + off_W3();
-        for (int kk = 0; kk < HID; ++kk) {
-            float acc = 0.f;
-            for (int j = 0; j < HID; ++j) acc = fmaf(G3[j * SP + s], W3[j * HID + kk], acc);
-            G2[kk * SP + s] *= acc;
-        }
-    }
-    __syncthreads();
-    wgrad(G2, H1, HID, HID, grads + off_W2(), grads + off_b2());
-    {
-        const float* W2 = sw + off_W2();
-        for (int kk = 0; kk < HID; ++kk) {
-            float acc = 0.f;
-            for (int j = 0; j < HID; ++j) acc = fmaf(G2[j * SP + s], W2[j * HID + kk], acc);
-            G1[kk * SP + s] *= acc;
-        }
-    }
-    __syncthreads();
-    wgrad(G1, XS, HID, NIN, grads + off_W1(), grads + off_b1());
-}
-
-__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int np, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
+// g_i = sum over the CTAs of the partials (fixed order); then, when m is
+// given, bias-corrected Adam on the fp32 masters. Index np: the loss.
+__global__ void reduce_adam_kernel(const float* __restrict__ part, int G, int PS, int np,
+                                   float* __restrict__ p, float* __restrict__ g_out,
+                                   float* __restrict__ m, float* __restrict__ v, float lr, float b1,
+                                   float b2, float eps, float c1, float c2, float* __restrict__ loss) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    g[i] = 0.f;
+    if (i > np) return;
+    float g = 0.f;
+    for (int c = 0; c < G; ++c) g += part[(size_t)c * PS + i];
+    if (i == np) {
+        if (loss) *loss = g;
+        return;
+    }
+    if (g_out) g_out[i] = g;
+    if (m) {
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
 }
 
-// forward pass only, for rows of standardised features (test hook and calibration)
-__global__ void __launch_bounds__(BS) mlp_forward_kernel(const float* __restrict__ params, int n,
-                                                       const float* __restrict__ X, int rows,
-                                                       float* __restrict__ Z) {
-    extern __shared__ float smem[];
-    const int np = off_b4(n) + n;
-    load_weights(params, np, smem);
-    __syncthreads();
-    const long long r = (long long)blockIdx.x * BS + threadIdx.x;
-    if (r >= rows) return;
-    float x[NIN];
+// ------------------------------------------------------------------ features
+struct FeatSrc {
+    const float* img;
+    const float* lead16;
+    const int32_t* dist2;  // [n][P] squared scribble distances (feature set 1)
+    int H, W, n, set;
+    float d_min;
+};
+
+// Raw feature c of pixel q: [R, G, B, x/W, y/H, a_1..a_16], then for feature
+// set 1 log max(d_i, d_min) for every label i and sin, cos of 2^f pi x/W and
+// of 2^f pi y/H for f = 0..5 (the argument reduced exactly: 2^f x mod 2W).
+__device__ __forceinline__ float pixel_feature(const FeatSrc& s, long long q, int c) {
+    const long long P = (long long)s.H * s.W;
+    const int x = (int)(q % s.W), y = (int)(q / s.W);
+    if (c < 3) return s.img[q * 3 + c];
+    if (c == 3) return (float)x / (float)s.W;
+    if (c == 4) return (float)y / (float)s.H;
+    if (c < 21) return s.lead16[q * 16 + (c - 5)];
+    if (s.set == 0) return 0.f;
+    c -= 21;
+    if (c < s.n) return logf(fmaxf(sqrtf((float)s.dist2[(size_t)c * P + q]), s.d_min));
+    c -= s.n;
+    if (c >= 24) return 0.f;
+    const int f = c >> 2, kind = c & 3;
+    const int w = kind < 2 ? s.W : s.H;
+    const long long m = ((long long)(kind < 2 ? x : y) << f) % (2LL * w);
+    const float t = (float)m / (float)w;
+    return (kind & 1) ? cospif(t) : sinpif(t);
+}
+
+// ------------------------------------------------------------------ forward
+enum { SRC_ROWS = 0, SRC_EVAL = 1 };
+
+struct FwdArgs {
+    const float* params;
+    int nin, n;
+    const float* X;  // SRC_ROWS: [rows][nin] standardised
+    int rows;
+    float* Z;        // SRC_ROWS: [rows][n]
+    // SRC_EVAL
+    FeatSrc fs;
+    const float* stats;  // mu_x[nin] sd_x[nin] mu_t[n] sd_t[n]
+    const float* eta;
+    const int32_t* label_off;
+    const uint32_t* bitmask;
+    const uint32_t* rep;
+    int Wk, mode;
+    float alpha, kappa_beta, sigma_c2, margin, eps;
+    bool rho_var;
+    float* neglog;
+    float* post;
+    int32_t* fb_list;
+    int* fb_count;
+    int* d_err;
+    uint64_t wait_ns;
+};
+
+struct FwdLayout {
+    uint32_t W1, W2, W3, W4, HH, HL, F32, BAR, total;
+};
+__host__ __device__ inline FwdLayout fwd_layout(int K0, int NOp) {
+    FwdLayout L;
+    uint32_t o = 0;
+    L.W1 = o; o += 2 * HID * K0;
+    L.W2 = o; o += 2 * HID * HID;
+    L.W3 = o; o += 2 * HID * HID;
+    L.W4 = o; o += 2 * NOp * HID;
+    L.HH = o; o += 2 * TR * HID;
+    L.HL = o; o += 2 * TR * HID;
+    L.F32 = o; o += 4 * (4 * HID + 4 * 64);  // biases; mu_x sd_x mu_t sd_t
+    L.BAR = o; o += 16;
+    L.total = o;
+    return L;
+}
+
+// Surrogate post-processing of one pixel (see the file header).
+__device__ void eval_pixel(const FwdArgs& a, long long q, const float (&zin)[64], const float* mu_t,
+                           const float* sd_t, float gap_min) {
+    const int n = a.n;
+    float z[64];  // indexed by label below: a local copy keeps zin in registers
 #pragma unroll
-    for (int kk = 0; kk < NIN; ++kk) x[kk] = X[r * NIN + kk];
-    float z[64];
-    forward_one<false>(smem, x, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, z);
-    for (int j = 0; j < n; ++j) Z[r * n + j] = z[j];
+    for (int j = 0; j < 64; ++j) z[j] = zin[j];
+    const long long P = (long long)a.fs.H * a.fs.W;
+    const float log_col_norm = 1.5f * logf(6.283185307179586f * a.sigma_c2);
+    uint32_t bx[8];
+    for (int w = 0; w < 8; ++w)
+        bx[w] = (a.mode == CS_MODE_FACTORISED && w < a.Wk) ? a.bitmask[q * a.Wk + w] : 0u;
+    float tmax = -INFINITY;
+    for (int j = 0; j < n; ++j) {
+        const float rho = a.alpha * fmaxf(sqrtf((float)a.fs.dist2[(size_t)j * P + q]), a.fs.d_min);
+        const float T = z[j] * sd_t[j] + mu_t[j];
+        z[j] = T - logf((float)(a.label_off[j + 1] - a.label_off[j])) -
+               logf(6.283185307179586f * (a.rho_var ? rho : rho * rho)) - log_col_norm;
+        if (a.mode == CS_MODE_FACTORISED) {
+            int h = 0;
+            for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[j * a.Wk + w]);
+            tmax = fmaxf(tmax, -(float)h / (a.kappa_beta * rho));
+        }
+    }
+    if (a.mode == CS_MODE_FACTORISED) {
+        float ts = 0.f;
+        for (int j = 0; j < n; ++j) {
+            const float rho = a.alpha * fmaxf(sqrtf((float)a.fs.dist2[(size_t)j * P + q]), a.fs.d_min);
+            int h = 0;
+            for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[j * a.Wk + w]);
+            ts += expf(-(float)h / (a.kappa_beta * rho) - tmax);
+        }
+        const float tl = tmax + logf(ts);
+        for (int j = 0; j < n; ++j) {
+            const float rho = a.alpha * fmaxf(sqrtf((float)a.fs.dist2[(size_t)j * P + q]), a.fs.d_min);
+            int h = 0;
+            for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[j * a.Wk + w]);
+            z[j] += -(float)h / (a.kappa_beta * rho) - tl;
+        }
+    }
+    float m1 = -INFINITY, m2 = -INFINITY;
+    for (int j = 0; j < n; ++j) {
+        if (z[j] > m1) {
+            m2 = m1;
+            m1 = z[j];
+        } else if (z[j] > m2) {
+            m2 = z[j];
+        }
+    }
+    float ls = 0.f;
+    for (int j = 0; j < n; ++j) ls += expf(z[j] - m1);
+    const float lse = m1 + logf(ls);
+    const float p1 = expf(m1 - lse), p2 = n > 1 ? expf(m2 - lse) : 0.f;
+    // a negative margin: the network answers every pixel (no exact fallback)
+    const bool fb = a.margin >= 0.f && ((p1 - p2 < a.margin) || (n > 1 && m1 - m2 < gap_min));
+    if (fb) {
+        const int idx = atomicAdd(a.fb_count, 1);
+        if (idx < P) a.fb_list[idx] = (int32_t)q;
+        return;
+    }
+    for (int j = 0; j < n; ++j) {
+        a.neglog[(size_t)j * P + q] = -z[j];
+        if (a.post) a.post[(size_t)j * P + q] = expf(z[j] - lse);
+    }
 }
 
-}  // namespace
+template <int SRC>
+__global__ void __launch_bounds__(NTH) mlp_fwd_kernel(FwdArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const Dims dm = dims_of(a.nin, a.n);
+    const Off of = off_of(a.nin, a.n);
+    const FwdLayout L = fwd_layout(dm.K0, dm.NOp);
+    unsigned char *W1 = sm + L.W1, *W2 = sm + L.W2, *W3 = sm + L.W3, *W4 = sm + L.W4;
+    unsigned char *HH = sm + L.HH, *HL = sm + L.HL;
+    float* bias = reinterpret_cast<float*>(sm + L.F32);
+    float* mu_x = bias + 4 * HID;
+    float* sd_x = mu_x + 64;
+    float* mu_t = sd_x + 64;
+    float* sd_t = mu_t + 64;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.BAR + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
 
-int mlp_param_count(int n) { return off_b4(n) + n; }
-
-size_t mlp_train_smem(int n) {
-    const int np = off_b4(n) + n;
-    return sizeof(float) * ((size_t)((np + 3) & ~3) + 6 * HID * SP + 64 * SP + NIN * SP);
-}
-
-cudaError_t launch_mlp_train(const float* params, int n, const float* X, const float* T,
-                             int n_rows, long long start, int batch, float* grads,
-                             float* loss_acc, cudaStream_t st) {
-    const size_t smem = mlp_train_smem(n);
-    cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    mlp_train_kernel<<<batch / BS, BS, smem, st>>>(params, n, X, T, n_rows, start, batch, grads,
-                                                   loss_acc);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr, int t,
-                        cudaStream_t st) {
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
-    adam_kernel<<<(np + 255) / 256, 256, 0, st>>>(p, g, m, v, np, lr, b1, b2, 1e-8f, c1, c2);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mlp_forward(const float* params, int n, const float* X, int rows, float* Z,
-                               cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)mlp_param_count(n);
-    cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    mlp_forward_kernel<<<(rows + BS - 1) / BS, BS, smem, st>>>(params, n, X, rows, Z);
-    return cudaGetLastError();
+    load_w(a.params + of.W1, HID, a.nin, HID, dm.K0, W1);
+    load_w(a.params + of.W2, HID, HID, HID, HID, W2);
+    load_w(a.params + of.W3, HID, HID, HID, HID, W3);
+    load_w(a.params + of.W4, a.n, HID, dm.NOp, HID, W4);
+    for (int i = tid; i < 4 * HID; i += NTH) {
+        const int l = i / HID, c = i % HID;
+        const int boff = l == 0 ? of.b1 : l == 1 ? of.b2 : l == 2 ? of.b3 : of.b4;
+        bias[i] = (l < 3 || c < a.n) ? __bfloat162float(__float2bfloat16_rn(a.params[boff + c])) : 0.f;
+    }
+    if (SRC == SRC_EVAL)
+        for (int i = tid; i < 64; i += NTH) {
+            mu_x[i] = i < a.nin ? a.stats[i] : 0.f;
+            sd_x[i] = i < a.nin ? a.stats[a.nin + i] : 1.f;
+            mu_t[i] = i < a.n ? a.stats[2 * a.nin + i] : 0.f;
+            sd_t[i] = i < a.n ? a.stats[2 * a.nin + a.n + i] : 1.f;
+        }
+    if (warp == 0) tc::tmem_alloc(tslot, 64);
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = *tslot;
+    const uint32_t tl = tm + ((uint32_t)(warp * 32) << 16);
+    const long long total = SRC == SRC_ROWS ? (long long)a.rows : (long long)a.fs.H * a.fs.W;
+    const long long tiles = (total + TR - 1) / TR;
+    float gap_min = 0.f;
+    if (SRC == SRC_EVAL)  // a gap g keeps the max probability error <= eps when
+                          // every logit is within eta of the truth:
+                          // (n - 1) exp(-(g - 2 eta)) <= eps
+        gap_min = 2.2f * (*a.eta) + logf(fmaxf((float)(a.n - 1), 1.f) / a.eps);
+    uint32_t ph = 0;
+    bool ok = true;
+    float v[64];
+    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const long long r = tile * TR + tid;
+        const bool valid = r < total;
+        if (SRC == SRC_ROWS) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) v[c] = (valid && c < a.nin) ? a.X[r * a.nin + c] : 0.f;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c)
+                v[c] = (valid && c < a.nin) ? (pixel_feature(a.fs, r, c) - mu_x[c]) / sd_x[c] : 0.f;
+        }
+        put_row_k0(v, dm.K0, HH, HL, tid);
+        for (int l = 0; l < 4; ++l) {
+            to_issue();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                mma_fwd(tm, HH, HL, l == 0 ? dm.K0 : HID, l == 0 ? W1 : l == 1 ? W2 : l == 2 ? W3 : W4,
+                        l < 3 ? HID : dm.NOp);
+                tc::mma_commit(bar);
+            }
+            if (!(ok = wait_all(bar, ph, a.wait_ns, a.d_err, 71 + l))) break;
+            ph ^= 1;
+            if (l < 3) {
+                tm_load<4>(tl, v);
+#pragma unroll
+                for (int c = 0; c < 64; ++c) {
+                    const float u = v[c] + bias[l * HID + c];
+                    v[c] = u * sigm(u);
+                }
+                put_row<64>(v, HH, HL, tid);
+            } else {
+                tm_load_n(tl, dm.NOp, v);
+            }
+        }
+        if (!ok) break;
+        tc::fence_before_sync();  // the next tile's MMAs overwrite these columns
+        if (valid) {
+            if (SRC == SRC_ROWS) {
+#pragma unroll
+                for (int j = 0; j < 64; ++j)
+                    if (j < a.n) a.Z[r * a.n + j] = v[j] + bias[3 * HID + j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) v[j] += bias[3 * HID + j];
+                eval_pixel(a, r, v, mu_t, sd_t, gap_min);
+            }
+        }
+    }
+    if (!ok) drain(bar, ph, a.wait_ns);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tm, 64);
+    }
 }
 
 // ------------------------------------------------------------------ data preparation
-
-namespace {
-
-// raw features of listed pixels: [R, G, B, x / W, y / H, a_1 .. a_16]
-__global__ void features_kernel(const float* __restrict__ img, const float* __restrict__ lead16,
-                                int H, int W, const int32_t* __restrict__ list, int rows,
+__global__ void features_kernel(FeatSrc s, int nin, const int32_t* __restrict__ list, int rows,
                                 float* __restrict__ X) {
-    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    const long long q = list[r];
-    float* x = X + r * NIN;
-    x[0] = img[q * 3 + 0];
-    x[1] = img[q * 3 + 1];
-    x[2] = img[q * 3 + 2];
-    x[3] = (float)(q % W) / (float)W;
-    x[4] = (float)(q / W) / (float)H;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) x[5 + j] = lead16[q * 16 + j];
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)rows * nin) return;
+    const long long r = i / nin;
+    X[i] = pixel_feature(s, list[r], (int)(i % nin));
 }
 
 // one block per column: mean and standard deviation over the first n_rows
-// rows, in double, deterministic tree reduction. Columns 0..20 come from X
-// (row-major, stride 21); columns 21..21+n-1 from T (label-major, stride cap).
-__global__ void stats_kernel(const float* __restrict__ X, const float* __restrict__ T, int n,
-                             int cap, int n_rows, float* __restrict__ stats) {
+// rows, in double, deterministic tree reduction. Columns 0..nin-1 come from
+// X (row-major, stride nin); nin..nin+n-1 from T (label-major, stride cap).
+__global__ void stats_kernel(const float* __restrict__ X, int nin, const float* __restrict__ T,
+                             int n, int cap, int n_rows, float* __restrict__ stats) {
     __shared__ double red[2][256];
     const int c = blockIdx.x;
     double s = 0.0, s2 = 0.0;
     for (int r = threadIdx.x; r < n_rows; r += blockDim.x) {
-        const double v = c < NIN ? (double)X[(size_t)r * NIN + c] : (double)T[(size_t)(c - NIN) * cap + r];
+        const double v = c < nin ? (double)X[(size_t)r * nin + c] : (double)T[(size_t)(c - nin) * cap + r];
         s += v;
         s2 += v * v;
     }
@@ -317,26 +793,26 @@ __global__ void stats_kernel(const float* __restrict__ X, const float* __restric
         const double mu = red[0][0] / n_rows;
         const double var = red[1][0] / n_rows - mu * mu;
         const double sd = var > 1e-12 ? sqrt(var) : 1.0;
-        // layout: mu_x[21] sd_x[21] mu_t[n] sd_t[n]
-        if (c < NIN) {
+        // layout: mu_x[nin] sd_x[nin] mu_t[n] sd_t[n]
+        if (c < nin) {
             stats[c] = (float)mu;
-            stats[NIN + c] = (float)sd;
+            stats[nin + c] = (float)sd;
         } else {
-            stats[2 * NIN + (c - NIN)] = (float)mu;
-            stats[2 * NIN + n + (c - NIN)] = (float)sd;
+            stats[2 * nin + (c - nin)] = (float)mu;
+            stats[2 * nin + n + (c - nin)] = (float)sd;
         }
     }
 }
 
 // X <- (X - mu_x) / sd_x in place; Ts[r][j] = (T[j][r] - mu_t,j) / sd_t,j
-__global__ void standardize_kernel(float* __restrict__ X, const float* __restrict__ T, int n,
-                                   int cap, int rows, const float* __restrict__ stats,
+__global__ void standardize_kernel(float* __restrict__ X, int nin, const float* __restrict__ T,
+                                   int n, int cap, int rows, const float* __restrict__ stats,
                                    float* __restrict__ Ts) {
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    for (int c = 0; c < NIN; ++c) X[r * NIN + c] = (X[r * NIN + c] - stats[c]) / stats[NIN + c];
+    for (int c = 0; c < nin; ++c) X[r * nin + c] = (X[r * nin + c] - stats[c]) / stats[nin + c];
     for (int j = 0; j < n; ++j)
-        Ts[r * n + j] = (T[(size_t)j * cap + r] - stats[2 * NIN + j]) / stats[2 * NIN + n + j];
+        Ts[r * n + j] = (T[(size_t)j * cap + r] - stats[2 * nin + j]) / stats[2 * nin + n + j];
 }
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -347,19 +823,18 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 // Glorot-uniform weights from a counter-based generator, zero biases, zero
-// optimiser state and gradients.
+// optimiser state.
 __global__ void init_params_kernel(float* __restrict__ p, float* __restrict__ m,
-                                   float* __restrict__ v, float* __restrict__ g, int n,
-                                   uint64_t seed) {
-    const int np = off_b4(n) + n;
+                                   float* __restrict__ v, int nin, int n, uint64_t seed) {
+    const Off o = off_of(nin, n);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
+    if (i >= o.np) return;
     float w = 0.f;
     int fan_in = 0, fan_out = 0;
-    if (i < off_b1()) { fan_in = NIN; fan_out = HID; }
-    else if (i >= off_W2() && i < off_b2()) { fan_in = HID; fan_out = HID; }
-    else if (i >= off_W3() && i < off_b3()) { fan_in = HID; fan_out = HID; }
-    else if (i >= off_W4() && i < off_b4(n)) { fan_in = HID; fan_out = n; }
+    if (i < o.b1) { fan_in = nin; fan_out = HID; }
+    else if (i >= o.W2 && i < o.b2) { fan_in = HID; fan_out = HID; }
+    else if (i >= o.W3 && i < o.b3) { fan_in = HID; fan_out = HID; }
+    else if (i >= o.W4 && i < o.b4) { fan_in = HID; fan_out = n; }
     if (fan_in) {
         const double u = (double)(splitmix64(seed ^ (0xA5A5A5A5ull + (uint64_t)i)) >> 11) * 0x1.0p-53;
         const double lim = sqrt(6.0 / (fan_in + fan_out));
@@ -368,151 +843,146 @@ __global__ void init_params_kernel(float* __restrict__ p, float* __restrict__ m,
     p[i] = w;
     m[i] = 0.f;
     v[i] = 0.f;
-    g[i] = 0.f;
 }
 
 // largest |z - t| * sd_t over rows and labels (a positive float: max via int bits)
-__global__ void calib_kernel(const float* __restrict__ Z, const float* __restrict__ Ts, int n,
-                             int rows, const float* __restrict__ stats, float* __restrict__ eta) {
+__global__ void calib_kernel(const float* __restrict__ Z, const float* __restrict__ Ts, int nin,
+                             int n, int rows, const float* __restrict__ stats,
+                             float* __restrict__ eta) {
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r >= rows) return;
     float mx = 0.f;
     for (int j = 0; j < n; ++j)
-        mx = fmaxf(mx, fabsf(Z[r * n + j] - Ts[r * n + j]) * stats[2 * NIN + n + j]);
+        mx = fmaxf(mx, fabsf(Z[r * n + j] - Ts[r * n + j]) * stats[2 * nin + n + j]);
     atomicMax(reinterpret_cast<int*>(eta), __float_as_int(mx));
 }
 
-// surrogate evaluation over all pixels (see the file header)
-__global__ void __launch_bounds__(BS) surrogate_eval_kernel(
-    const float* __restrict__ params, int n, const float* __restrict__ stats,
-    const float* __restrict__ eta, const float* __restrict__ img, const float* __restrict__ lead16,
-    int H, int W, const int32_t* __restrict__ dist2, const int32_t* __restrict__ label_off,
-    const uint32_t* __restrict__ bitmask, const uint32_t* __restrict__ rep, int Wk, int mode,
-    float alpha, float d_min, float kappa_beta, float sigma_c2, bool rho_var, float margin,
-    float eps, float* __restrict__ neglog, float* __restrict__ post, int32_t* __restrict__ fb_list,
-    int* __restrict__ fb_count) {
-    extern __shared__ float smem[];
-    const int np = off_b4(n) + n;
-    load_weights(params, np, smem);
-    __syncthreads();
-    const long long P = (long long)H * W;
-    const long long q = (long long)blockIdx.x * BS + threadIdx.x;
-    if (q >= P) return;
-    float x[NIN];
-    x[0] = img[q * 3 + 0];
-    x[1] = img[q * 3 + 1];
-    x[2] = img[q * 3 + 2];
-    x[3] = (float)(q % W) / (float)W;
-    x[4] = (float)(q / W) / (float)H;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) x[5 + j] = lead16[q * 16 + j];
-#pragma unroll
-    for (int c = 0; c < NIN; ++c) x[c] = (x[c] - stats[c]) / stats[NIN + c];
-    float z[64];
-    forward_one<false>(smem, x, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, z);
-    const float log_col_norm = 1.5f * logf(6.283185307179586f * sigma_c2);
-    uint32_t bx[8];
-    for (int w = 0; w < 8; ++w) bx[w] = (mode == CS_MODE_FACTORISED && w < Wk) ? bitmask[q * Wk + w] : 0u;
-    // log-likelihoods, and the factorised texture posterior
-    float tmax = -INFINITY;
-    for (int j = 0; j < n; ++j) {
-        const float rho = alpha * fmaxf(sqrtf((float)dist2[(size_t)j * P + q]), d_min);
-        const float T = z[j] * stats[2 * NIN + n + j] + stats[2 * NIN + j];
-        z[j] = T - logf((float)(label_off[j + 1] - label_off[j])) -
-               logf(6.283185307179586f * (rho_var ? rho : rho * rho)) - log_col_norm;
-        if (mode == CS_MODE_FACTORISED) {
-            int h = 0;
-            for (int w = 0; w < Wk; ++w) h += __popc(bx[w & 7] ^ rep[j * Wk + w]);
-            tmax = fmaxf(tmax, -(float)h / (kappa_beta * rho));
-        }
-    }
-    if (mode == CS_MODE_FACTORISED) {
-        float ts = 0.f;
-        for (int j = 0; j < n; ++j) {
-            const float rho = alpha * fmaxf(sqrtf((float)dist2[(size_t)j * P + q]), d_min);
-            int h = 0;
-            for (int w = 0; w < Wk; ++w) h += __popc(bx[w & 7] ^ rep[j * Wk + w]);
-            ts += expf(-(float)h / (kappa_beta * rho) - tmax);
-        }
-        const float tl = tmax + logf(ts);
-        for (int j = 0; j < n; ++j) {
-            const float rho = alpha * fmaxf(sqrtf((float)dist2[(size_t)j * P + q]), d_min);
-            int h = 0;
-            for (int w = 0; w < Wk; ++w) h += __popc(bx[w & 7] ^ rep[j * Wk + w]);
-            z[j] += -(float)h / (kappa_beta * rho) - tl;
-        }
-    }
-    float m1 = -INFINITY, m2 = -INFINITY;
-    for (int j = 0; j < n; ++j) {
-        if (z[j] > m1) {
-            m2 = m1;
-            m1 = z[j];
-        } else if (z[j] > m2) {
-            m2 = z[j];
-        }
-    }
-    float ls = 0.f;
-    for (int j = 0; j < n; ++j) ls += expf(z[j] - m1);
-    const float lse = m1 + logf(ls);
-    const float p1 = expf(m1 - lse), p2 = n > 1 ? expf(m2 - lse) : 0.f;
-    // a gap g guarantees a max probability error <= eps when every logit is
-    // within eta of the truth: (n - 1) exp(-(g - 2 eta)) <= eps
-    const float gap_min = 2.2f * (*eta) + logf(fmaxf((float)(n - 1), 1.f) / eps);
-    // margin < 0: the network answers every pixel (no exact fallback)
-    const bool fb = margin >= 0.f && ((p1 - p2 < margin) || (n > 1 && m1 - m2 < gap_min));
-    if (fb) {
-        const int idx = atomicAdd(fb_count, 1);
-        if (idx < P) fb_list[idx] = (int32_t)q;
-        return;
-    }
-    for (int j = 0; j < n; ++j) {
-        neglog[(size_t)j * P + q] = -z[j];
-        if (post) post[(size_t)j * P + q] = expf(z[j] - lse);
-    }
+cudaError_t set_smem(const void* fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
 
-cudaError_t launch_features(const float* img, const float* lead16, int H, int W,
-                            const int32_t* list, int rows, float* X, cudaStream_t st) {
-    features_kernel<<<(rows + 127) / 128, 128, 0, st>>>(img, lead16, H, W, list, rows, X);
-    return cudaGetLastError();
-}
+int mlp_param_count(int nin, int n) { return off_of(nin, n).np; }
 
-cudaError_t launch_stats(const float* X, const float* T, int n, int cap, int n_rows,
-                         float* stats, cudaStream_t st) {
-    stats_kernel<<<NIN + n, 256, 0, st>>>(X, T, n, cap, n_rows, stats);
-    return cudaGetLastError();
+int mlp_train_ctas(int batch, int n_sm) {
+    const int tiles = (batch + TR - 1) / TR;
+    return tiles < n_sm ? tiles : n_sm;
 }
+int mlp_part_stride(int nin, int n) { return (off_of(nin, n).np + 1 + 3) & ~3; }
 
-cudaError_t launch_standardize(float* X, const float* T, int n, int cap, int rows,
-                               const float* stats, float* Ts, cudaStream_t st) {
-    standardize_kernel<<<(rows + 127) / 128, 128, 0, st>>>(X, T, n, cap, rows, stats, Ts);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_init_params(float* p, float* m, float* v, float* g, int n, uint64_t seed,
-                               cudaStream_t st) {
-    const int np = mlp_param_count(n);
-    init_params_kernel<<<(np + 255) / 256, 256, 0, st>>>(p, m, v, g, n, seed);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_calib(const float* Z, const float* Ts, int n, int rows, const float* stats,
-                         float* eta, cudaStream_t st) {
-    calib_kernel<<<(rows + 127) / 128, 128, 0, st>>>(Z, Ts, n, rows, stats, eta);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_surrogate_eval(const SurrogateEvalArgs& a, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)mlp_param_count(a.n);
-    cudaError_t e = cudaFuncSetAttribute(surrogate_eval_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_mlp_train(const float* params, int nin, int n, const float* X, const float* T,
+                             int n_rows, long long start, int batch, float* part, int G,
+                             int* d_err, uint64_t wait_ns, cudaStream_t st) {
+    const Dims dm = dims_of(nin, n);
+    const size_t smem = train_layout(dm.K0, dm.NOp).total;
+    cudaError_t e = set_smem((const void*)mlp_train_kernel, smem);
     if (e != cudaSuccess) return e;
-    const long long P = (long long)a.H * a.W;
-    surrogate_eval_kernel<<<(unsigned)((P + BS - 1) / BS), BS, smem, st>>>(
-        a.params, a.n, a.stats, a.eta, a.img, a.lead16, a.H, a.W, a.dist2, a.label_off,
-        a.bitmask, a.rep, a.Wk, a.mode, a.alpha, a.d_min, a.kappa_beta, a.sigma_c2, a.rho_var,
-        a.margin, a.eps, a.neglog, a.post, a.fb_list, a.fb_count);
+    TrainArgs a{params, nin, n, X, T, n_rows, start, batch, part, mlp_part_stride(nin, n), d_err,
+                wait_ns ? wait_ns : MLP_WAIT_NS};
+    mlp_train_kernel<<<G, NTH, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_adam(const float* part, int G, int nin, int n, float* p, float* g_out,
+                               float* m, float* v, float lr, int t, float* loss, cudaStream_t st) {
+    const int np = mlp_param_count(nin, n);
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    reduce_adam_kernel<<<(np + 1 + 255) / 256, 256, 0, st>>>(part, G, mlp_part_stride(nin, n), np, p,
+                                                             g_out, m, v, lr, b1, b2, 1e-8f, c1, c2,
+                                                             loss);
+    return cudaGetLastError();
+}
+
+static int fwd_grid(long long total, int n_sm) {
+    const long long tiles = (total + TR - 1) / TR;
+    const long long cap = 3LL * n_sm;  // three CTAs per SM (shared memory)
+    return (int)(tiles < cap ? tiles : cap);
+}
+
+cudaError_t launch_mlp_forward(const float* params, int nin, int n, const float* X, int rows,
+                               float* Z, int n_sm, int* d_err, uint64_t wait_ns, cudaStream_t st) {
+    const Dims dm = dims_of(nin, n);
+    const size_t smem = fwd_layout(dm.K0, dm.NOp).total;
+    cudaError_t e = set_smem((const void*)mlp_fwd_kernel<SRC_ROWS>, smem);
+    if (e != cudaSuccess) return e;
+    FwdArgs a{};
+    a.params = params;
+    a.nin = nin;
+    a.n = n;
+    a.X = X;
+    a.rows = rows;
+    a.Z = Z;
+    a.d_err = d_err;
+    a.wait_ns = wait_ns ? wait_ns : MLP_WAIT_NS;
+    mlp_fwd_kernel<SRC_ROWS><<<fwd_grid(rows, n_sm), NTH, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_eval(const SurrogateEvalArgs& s, cudaStream_t st) {
+    const Dims dm = dims_of(s.nin, s.n);
+    const size_t smem = fwd_layout(dm.K0, dm.NOp).total;
+    cudaError_t e = set_smem((const void*)mlp_fwd_kernel<SRC_EVAL>, smem);
+    if (e != cudaSuccess) return e;
+    FwdArgs a{};
+    a.params = s.params;
+    a.nin = s.nin;
+    a.n = s.n;
+    a.fs = FeatSrc{s.img, s.lead16, s.dist2, s.H, s.W, s.n, s.feature_set, s.d_min};
+    a.stats = s.stats;
+    a.eta = s.eta;
+    a.label_off = s.label_off;
+    a.bitmask = s.bitmask;
+    a.rep = s.rep;
+    a.Wk = s.Wk;
+    a.mode = s.mode;
+    a.alpha = s.alpha;
+    a.kappa_beta = s.kappa_beta;
+    a.sigma_c2 = s.sigma_c2;
+    a.margin = s.margin;
+    a.eps = s.eps;
+    a.rho_var = s.rho_var;
+    a.neglog = s.neglog;
+    a.post = s.post;
+    a.fb_list = s.fb_list;
+    a.fb_count = s.fb_count;
+    a.d_err = s.d_err;
+    a.wait_ns = s.wait_ns ? s.wait_ns : MLP_WAIT_NS;
+    mlp_fwd_kernel<SRC_EVAL><<<fwd_grid((long long)s.H * s.W, s.n_sm), NTH, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(const float* img, const float* lead16, const int32_t* dist2, int H,
+                            int W, int n, int feature_set, float d_min, int nin,
+                            const int32_t* list, int rows, float* X, cudaStream_t st) {
+    const long long total = (long long)rows * nin;
+    FeatSrc s{img, lead16, dist2, H, W, n, feature_set, d_min};
+    features_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, nin, list, rows, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const float* X, int nin, const float* T, int n, int cap, int n_rows,
+                         float* stats, cudaStream_t st) {
+    stats_kernel<<<nin + n, 256, 0, st>>>(X, nin, T, n, cap, n_rows, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_standardize(float* X, int nin, const float* T, int n, int cap, int rows,
+                               const float* stats, float* Ts, cudaStream_t st) {
+    standardize_kernel<<<(rows + 127) / 128, 128, 0, st>>>(X, nin, T, n, cap, rows, stats, Ts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_params(float* p, float* m, float* v, int nin, int n, uint64_t seed,
+                               cudaStream_t st) {
+    const int np = mlp_param_count(nin, n);
+    init_params_kernel<<<(np + 255) / 256, 256, 0, st>>>(p, m, v, nin, n, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_calib(const float* Z, const float* Ts, int nin, int n, int rows,
+                         const float* stats, float* eta, cudaStream_t st) {
+    calib_kernel<<<(rows + 127) / 128, 128, 0, st>>>(Z, Ts, nin, n, rows, stats, eta);
     return cudaGetLastError();
 }
