@@ -17,8 +17,10 @@ Secondary blocks of the same line (not the headline): "forms" (the BF16
 tensor-core and the plain FP32 forms beside the FP8 one, each with its error
 against the FP64 oracle at sampled pixels, computed outside the timed
 region), "batch" (64 uneven images through cs_batch_*, graph-replayed and
-autotuned) and "large" (the 1024x1024 and 4096x4096 workloads, both forms,
-with their errors). The ALU roofline's denominators come from
+autotuned), "large" (the 1024x1024 and 4096x4096 workloads, both forms,
+with their errors) and "surrogate" (the learned surrogate on the 1024x1024
+workload: fit and evaluation times, fallback shares and errors against the
+exact sums, per fallback rule). The ALU roofline's denominators come from
 cs_unit_rates, a microbenchmark of the pipes run at the start ("unit_rates").
 Under torchrun (N > 1) every rank runs its own image (weak scaling, no
 collective on the data path); rank 0 prints the max-over-ranks line.
@@ -497,6 +499,94 @@ def measure_large(ctx, cs, torch, dev, reduce_max, world, steps=3):
     return out
 
 
+def measure_surrogate(ctx, cs, torch, dev, reduce_max, world, steps=1000, runs=2):
+    """The learned surrogate on the 1024 x 1024 workload (10 labels x 20000
+    samples): fit on exact FP32 likelihoods at 5% of the pixels (tensor-core
+    training, `steps` Adam steps), then evaluation under each fallback rule,
+    against the exact sums of the same call (cs_likelihood, plain FP32 and
+    FP8 tensor-core forms) as the judge: fallback share, max posterior
+    error and argmax agreement over all pixels and over the pixels the
+    network answers, and the time of fit + eval as pairs/s-equivalent.
+    Per mode (per-sample and factorised texture) and feature set. CUDA
+    events around each call, `runs` timed runs after one warm-up."""
+    from paper_1312_4746_gb300 import synth
+
+    pr = synth.make_workload(4)
+    P, nl = pr.H * pr.W, pr.n_labels
+    pairs = float(P * pr.n_samples)
+    img = torch.from_numpy(pr.image).to(dev)
+    om = torch.from_numpy(pr.omega).to(dev)
+    mask = torch.from_numpy(pr.mask).to(dev)
+    smp = torch.from_numpy(pr.sample_pix).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(runs):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        (ms,) = reduce_max([e0.elapsed_time(e1) / runs])
+        return ms, r
+
+    def err(post, ex_post, sel=None):
+        d = (post - ex_post).abs().amax(0)
+        agree = post.argmax(0) == ex_post.argmax(0)
+        if sel is not None:
+            if not bool(sel.any()):
+                return {"max_prob_err": None, "argmax_agreement": None}
+            d, agree = d[sel], agree[sel]
+        return {"max_prob_err": float(d.max()), "argmax_agreement": float(agree.float().mean())}
+
+    out = {"workload": pr.name, "pairs_per_image": pairs, "training_fraction": 0.05,
+           "steps": steps, "judge": "exact FP32 sums of the whole image (cs_likelihood)"}
+    for mode in (0, 1):
+        prm = cs.Params.from_synth(pr.params, mode=mode)
+        c = ctx.codes(img, om, mask, prm, want_lead16=True)
+        ms32, ex = timed(lambda: ctx.likelihood(img, c["bitmask"], pr.k, pr.label_off, smp, prm))
+        prm8 = cs.Params.from_synth(pr.params, mode=mode, precision=FORMS["fp8"])
+        ms8, _ = timed(lambda: ctx.likelihood(img, c["bitmask"], pr.k, pr.label_off, smp, prm8))
+        ex_post = ex["post"].reshape(nl, P)
+        entry = {"exact_fp32_ms": ms32, "exact_fp8_ms": ms8}
+        for feat, fname in ((cs.SURR_BASIC, "basic"), (cs.SURR_EXTENDED, "extended")):
+            def fit():
+                ctx.surrogate_fit(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
+                                  frac=0.05, steps=steps, features=feat, seed=11)
+            ctx.profile(True)
+            fit_ms, _ = timed(fit)
+            train_ms, _ = ctx.profile_read(cs.STAGE_TRAIN)
+            for st in range(cs.STAGE_TRAIN):  # forget the other stages' records
+                ctx.profile_read(st)
+            ctx.profile(False)
+            info = ctx.surrogate_info(nl)
+            e = {"features": info["n_in"], "fit_ms": fit_ms, "train_ms": train_ms / (runs + 1),
+                 "train_ms_per_step": train_ms / (runs + 1) / steps, "eta_nats": info["eta"],
+                 "final_loss": info["loss"], "rules": {}}
+            for rule, rname in ((cs.FALLBACK_NONE, "none"), (cs.FALLBACK_MARGIN, "margin 0.1"),
+                                (cs.FALLBACK_GUARANTEED, "guaranteed")):
+                def ev():
+                    return ctx.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off,
+                                              smp, prm, rule=rule, margin=0.1, count=False)
+                ev_ms, (o, _) = timed(ev)
+                post = o["post"].reshape(nl, P)
+                # the pixels the network answered: not bit-identical to the exact sum
+                answered = (o["neglog"].reshape(nl, P) != ex["neglog"].reshape(nl, P)).any(0)
+                e["rules"][rname] = {
+                    "eval_ms": ev_ms, "fallback_share": 1.0 - float(answered.float().mean()),
+                    "all_pixels": err(post, ex_post), "answered_pixels": err(post, ex_post, answered),
+                    "pairs_per_s_equiv_fit_plus_eval": pairs * world / ((fit_ms + ev_ms) * 1e-3),
+                    "pairs_per_s_equiv_eval_only": pairs * world / (ev_ms * 1e-3)}
+                del o, post
+            entry[fname] = e
+        out["per-sample" if mode == 0 else "factorised"] = entry
+        del c, ex, ex_post
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -509,7 +599,7 @@ def main():
     ap.add_argument("--batch-images", type=int, default=64,
                     help="also time a batch of this many uneven images (0: skip)")
     ap.add_argument("--no-large", action="store_true",
-                    help="skip the 1024x1024 and 4096x4096 workloads")
+                    help="skip the 1024x1024 and 4096x4096 workloads and the surrogate")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -572,6 +662,7 @@ def main():
     if args.batch_images > 0:
         batch = measure_batch(ctx, cs, torch, dev, args.batch_images, reduce_max, world)
     large = None if args.no_large else measure_large(ctx, cs, torch, dev, reduce_max, world)
+    surr = None if args.no_large else measure_surrogate(ctx, cs, torch, dev, reduce_max, world)
     if rank == 0:
         peaks, src = _peaks()
         clocks = clk.summary()
@@ -650,6 +741,8 @@ def main():
             line["batch"] = batch
         if large is not None:
             line["large"] = large
+        if surr is not None:
+            line["surrogate"] = surr
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pr)
         print(json.dumps(line))

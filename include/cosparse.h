@@ -550,11 +550,17 @@ cs_status cs_batch_data_term(cs_ctx* ctx, const cs_image* images, int n_images,
  *   and `features` (CS_SURR_BASIC or CS_SURR_EXTENDED). Asynchronous, but the
  *   pixel selection runs on the host before the call returns.
  * cs_surrogate_eval: evaluates the network at every pixel and writes
- *   neglog/post there, except at pixels whose top-2 posterior margin is below
- *   `margin` or whose top-2 log-likelihood gap is below
- *   2.2 eta + log((n_labels - 1) / 0.005); those get the exact FP32 sum.
- *   A negative margin disables the fallback: the network answers every pixel
- *   (an approximation with no error guarantee, for speed/accuracy studies).
+ *   neglog/post there, except at the pixels that `rule` sends to the exact
+ *   FP32 sum (margin in [0, 1]):
+ *     CS_FALLBACK_GUARANTEED  the network's top-2 posterior margin is below
+ *                             `margin`, or its top-2 log-likelihood gap is
+ *                             below 2.2 eta + log((n_labels - 1) / 0.005)
+ *                             (every answered pixel then has max posterior
+ *                             error <= 0.005 if all its logits are within
+ *                             eta of the exact ones)
+ *     CS_FALLBACK_MARGIN      the network's top-2 posterior margin is below
+ *                             `margin` (no error guarantee)
+ *     CS_FALLBACK_NONE        none: the network answers every pixel
  *   n_fallback (HOST int32, may be NULL) receives their count; when given,
  *   the call synchronises.
  * cs_surrogate_params: copies the fp32 master weights to HOST memory
@@ -567,21 +573,26 @@ cs_status cs_batch_data_term(cs_ctx* ctx, const cs_image* images, int n_images,
  *   grads (DEVICE, cs_mlp_param_count(n_in, n_out) floats) and the loss into
  *   *loss (DEVICE). Weight gradients take the bf16 piece of the activations
  *   (relative error at most 2^-8 of sum |delta| |h| per entry).
- * Errors: CS_ERR_INVALID_ARG (bad sizes, unknown feature set, too many
- *   labels for CS_SURR_EXTENDED, no fitted surrogate), CS_ERR_NOMEM,
+ * Errors: CS_ERR_INVALID_ARG (bad sizes, unknown feature set or rule, too
+ *   many labels for CS_SURR_EXTENDED, margin outside [0, 1], no fitted
+ *   surrogate), CS_ERR_NOMEM,
  *   CS_ERR_CUDA; a device wait that gives up reports CS_ERR_TIMEOUT through
  *   cs_sync_status.
  */
 #define CS_SURR_BASIC 0
 #define CS_SURR_EXTENDED 1
+#define CS_FALLBACK_GUARANTEED 0
+#define CS_FALLBACK_MARGIN 1
+#define CS_FALLBACK_NONE 2
 cs_status cs_surrogate_fit(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
                            const float* lead16, int k, int n_labels, const int32_t* label_off,
                            const int32_t* sample_pix, const cs_params* prm, double frac,
                            int steps, int features, uint64_t seed, void* stream);
 cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
                             const float* lead16, int k, int n_labels, const int32_t* label_off,
-                            const int32_t* sample_pix, const cs_params* prm, double margin,
-                            float* neglog, float* post, int32_t* n_fallback, void* stream);
+                            const int32_t* sample_pix, const cs_params* prm, int rule,
+                            double margin, float* neglog, float* post, int32_t* n_fallback,
+                            void* stream);
 cs_status cs_surrogate_params(cs_ctx* ctx, float* host_params, int cap, int* n_params);
 /*
  * cs_surrogate_info: HOST copies of the standardisation statistics

@@ -86,6 +86,9 @@ STAGE_SURROGATE = 4
 STAGE_TRAIN = 5
 SURR_BASIC = 0
 SURR_EXTENDED = 1
+FALLBACK_GUARANTEED = 0
+FALLBACK_MARGIN = 1
+FALLBACK_NONE = 2
 
 
 class CsError(RuntimeError):
@@ -248,7 +251,7 @@ def lib(path: str | None = None):
     U64 = ctypes.c_uint64
     L.cs_surrogate_fit.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, I, I,
                                    U64, V]
-    L.cs_surrogate_eval.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), D, V, V,
+    L.cs_surrogate_eval.argtypes = [V, V, I, I, V, V, I, I, V, V, ctypes.POINTER(Params), I, D, V, V,
                                     V, V]
     L.cs_surrogate_params.argtypes = [V, V, I, ctypes.POINTER(I)]
     L.cs_surrogate_info.argtypes = [V, V, I, V, V, ctypes.POINTER(I), ctypes.POINTER(I),
@@ -556,8 +559,9 @@ class Context:
             float(frac), int(steps), int(features), ctypes.c_uint64(seed), _stream()))
 
     def surrogate_eval(self, img, bitmask, lead16, k, label_off, sample_pix, params: Params,
-                       margin=0.1, out=None, want_post=True, count=True):
-        """cs_surrogate_eval: returns (dict with 'neglog'/'post', n_fallback or None)."""
+                       margin=0.1, rule=0, out=None, want_post=True, count=True):
+        """cs_surrogate_eval: returns (dict with 'neglog'/'post', n_fallback or None);
+        rule: FALLBACK_GUARANTEED, FALLBACK_MARGIN or FALLBACK_NONE."""
         import numpy as np
         import torch
 
@@ -572,7 +576,7 @@ class Context:
         self.check(self._lib.cs_surrogate_eval(
             self.handle, _ptr(img), H, W, _ptr(bitmask), _ptr(lead16), int(k), nl,
             ctypes.c_void_p(off.ctypes.data), _ptr(sample_pix), ctypes.byref(params),
-            float(margin), _ptr(out["neglog"]), _ptr(out.get("post")),
+            int(rule), float(margin), _ptr(out["neglog"]), _ptr(out.get("post")),
             ctypes.byref(nfb) if count else None, _stream()))
         return out, (nfb.value if count else None)
 

@@ -464,15 +464,22 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
 int mlp_param_count(int nin, int n);
 int mlp_train_ctas(int batch, int n_sm);   // CTAs of one training step
 int mlp_part_stride(int nin, int n);       // floats per CTA in the partials buffer
-cudaError_t launch_mlp_train(const float* params, int nin, int n, const float* X, const float* T,
-                             int n_rows, long long start, int batch, float* part, int G,
-                             int* d_err, uint64_t wait_ns, cudaStream_t st);
+size_t mlp_image_bytes(int nin, int n);    // the kernels' weight image (16-byte multiple)
+// the weight image of fp32 parameters (bf16 tiles in the kernels' layout + biases)
+cudaError_t launch_mlp_pack(const float* params, int nin, int n, unsigned char* image,
+                            cudaStream_t st);
+cudaError_t launch_mlp_train(const unsigned char* image, int nin, int n, const float* X,
+                             const float* T, int n_rows, long long start, int batch, float* part,
+                             int G, int* d_err, uint64_t wait_ns, cudaStream_t st);
 // sums G CTAs' partials into g_out (may be NULL) and *loss (may be NULL); with
-// m non-NULL also an Adam step (step number t >= 1) on p
+// m non-NULL also an Adam step (step number t >= 1) on p, rewriting the image
+// (when non-NULL) from the updated parameters
 cudaError_t launch_reduce_adam(const float* part, int G, int nin, int n, float* p, float* g_out,
-                               float* m, float* v, float lr, int t, float* loss, cudaStream_t st);
-cudaError_t launch_mlp_forward(const float* params, int nin, int n, const float* X, int rows,
-                               float* Z, int n_sm, int* d_err, uint64_t wait_ns, cudaStream_t st);
+                               float* m, float* v, float lr, int t, float* loss,
+                               unsigned char* image, cudaStream_t st);
+cudaError_t launch_mlp_forward(const unsigned char* image, int nin, int n, const float* X,
+                               int rows, float* Z, int n_sm, int* d_err, uint64_t wait_ns,
+                               cudaStream_t st);
 cudaError_t launch_features(const float* img, const float* lead16, const int32_t* dist2, int H,
                             int W, int n, int feature_set, float d_min, int nin,
                             const int32_t* list, int rows, float* X, cudaStream_t st);
@@ -485,7 +492,7 @@ cudaError_t launch_init_params(float* p, float* m, float* v, int nin, int n, uin
 cudaError_t launch_calib(const float* Z, const float* Ts, int nin, int n, int rows,
                          const float* stats, float* eta, cudaStream_t st);
 struct SurrogateEvalArgs {
-    const float* params;
+    const unsigned char* image;  // weight image (launch_mlp_pack)
     int nin, n, feature_set;
     const float* stats;
     const float* eta;
@@ -496,7 +503,7 @@ struct SurrogateEvalArgs {
     const int32_t* label_off;
     const uint32_t* bitmask;
     const uint32_t* rep;
-    int Wk, mode;
+    int Wk, mode, rule;
     float alpha, d_min, kappa_beta, sigma_c2, margin, eps;
     bool rho_var;
     float* neglog;

@@ -36,8 +36,9 @@
 //                     L_i = sd_t,i z_i + mu_t,i - log m_i - log(2 pi s2_i)
 //                           - 1.5 log(2 pi sigma_c2) (+ the factorised
 //                     texture log-posterior), the posteriors, and the fallback
-//                     decision (top-2 posterior margin below `margin`, or the
-//                     top-2 gap below the calibrated gap_min): such pixels are
+//                     decision of the fallback rule (top-2 posterior margin
+//                     below `margin`; under the guaranteed rule also a top-2
+//                     gap below the calibrated gap_min): such pixels are
 //                     listed for the exact sum to overwrite.
 #include <cuda_bf16.h>
 
@@ -50,7 +51,7 @@ namespace {
 
 constexpr int HID = 64;
 constexpr int TR = 128;   // rows per tile (the MMA's M)
-constexpr int NTH = 128;  // threads per CTA, one row each
+constexpr int NTH = 256;  // threads per CTA, two per row
 constexpr uint64_t MLP_WAIT_NS = 1000000000ull;
 
 struct Dims {
@@ -102,90 +103,128 @@ __device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
 }
 __device__ __forceinline__ float bf_hi(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-// Row r of a 128-row tile: columns [0, C) of v as hi and (optionally) lo
-// bf16 pieces, 16-byte stores (C a multiple of 8).
-template <int C>
-__device__ __forceinline__ void put_row(const float (&v)[64], unsigned char* hi, unsigned char* lo,
-                                        int r) {
+// The weights as the kernels read them (the "image"): the bf16 row-layout
+// tiles W1 (64 x K0), W2, W3 (64 x 64), W4 (NOp x 64), zero outside the
+// parameters, then the biases b1 b2 b3 b4 (64 fp32 each, bf16-rounded, b4
+// zero beyond n). Built by pack_kernel, rewritten by every Adam step, and
+// copied into shared memory in two bulk copies.
+__host__ __device__ inline uint32_t img_wbytes(int K0, int NOp) {
+    return 2u * HID * K0 + 4u * HID * HID + 2u * NOp * HID;
+}
+__host__ __device__ inline uint32_t img_bytes(int K0, int NOp) { return img_wbytes(K0, NOp) + 4u * 4 * HID; }
+
+// Image element (bf16 index) of weight (r, c) of layer l, for a tile of R rows.
+__host__ __device__ inline uint32_t img_elem(uint32_t tile0, uint32_t R, int r, int c) {
+    return tile0 + (uint32_t)(c >> 3) * 8u * R + 8u * r + (c & 7);
+}
+
+// Bulk copy of the image into shared memory (thread 0 issues; every thread
+// waits, bounded).
+__device__ bool load_image(const unsigned char* img, uint32_t wbytes, unsigned char* w_dst,
+                           float* bias_dst, uint64_t* bar, uint64_t wait_ns, int* d_err, int site) {
+    if (threadIdx.x == 0) {
+        tc::mbar_arrive_expect_tx(bar, wbytes + 4u * 4 * HID);
+        tc::bulk_g2s(w_dst, img, wbytes, bar);
+        tc::bulk_g2s(bias_dst, img + wbytes, 4u * 4 * HID, bar);
+    }
+    bool ok = true;
+    uint64_t deadline = 0;
+    for (uint32_t n = 0;; ++n) {
+        if (tc::mbar_try_wait(bar, 0, 1000u)) break;
+        if ((n & 63u) == 63u) {
+            const uint64_t now = tc::globaltimer();
+            if (deadline == 0) deadline = now + wait_ns;
+            else if (now > deadline) {
+                ok = false;
+                break;
+            }
+        }
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok && threadIdx.x == 0 && atomicCAS(d_err, 0, CS_DEVERR_TIMEOUT) == 0) d_err[1] = site;
+    return ok;
+}
+
+// Parameter i (value v) into its place in the image.
+__device__ void img_store(unsigned char* img, const Off& of, const Dims& dm, int i, float v) {
+    __nv_bfloat16* w = reinterpret_cast<__nv_bfloat16*>(img);
+    float* bias = reinterpret_cast<float*>(img + img_wbytes(dm.K0, dm.NOp));
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const uint32_t t2 = HID * dm.K0, t3 = t2 + HID * HID, t4 = t3 + HID * HID;
+    if (i < of.b1) w[img_elem(0, HID, i / dm.nin, i % dm.nin)] = h;
+    else if (i < of.W2) bias[i - of.b1] = __bfloat162float(h);
+    else if (i < of.b2) w[img_elem(t2, HID, (i - of.W2) / HID, (i - of.W2) % HID)] = h;
+    else if (i < of.W3) bias[HID + i - of.b2] = __bfloat162float(h);
+    else if (i < of.b3) w[img_elem(t3, HID, (i - of.W3) / HID, (i - of.W3) % HID)] = h;
+    else if (i < of.W4) bias[2 * HID + i - of.b3] = __bfloat162float(h);
+    else if (i < of.b4) w[img_elem(t4, dm.NOp, (i - of.W4) / HID, (i - of.W4) % HID)] = h;
+    else bias[3 * HID + i - of.b4] = __bfloat162float(h);
+}
+
+// Thread layout of a CTA (256 threads): warp w reads the tensor-memory lanes
+// 32 (w % 4) .. 32 (w % 4) + 31, i.e. those rows of the tile, and owns
+// columns 32 (w / 4) .. 32 (w / 4) + 31 of its row: two threads per row.
+
+// Columns [c0, c0 + 32) of row r, clipped to C (a multiple of 8), into a
+// 128-row tile as the hi and (optionally) lo bf16 pieces, 16-byte stores.
+__device__ __forceinline__ void put_half(const float (&v)[32], int c0, int C, unsigned char* hi,
+                                         unsigned char* lo, int r) {
 #pragma unroll
-    for (int c8 = 0; c8 < C / 8; ++c8) {
-        uint4 h, l;
-        float e[8];
+    for (int k = 0; k < 4; ++k) {
+        const int c8 = (c0 >> 3) + k;
+        if (8 * c8 < C) {
+            float e[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) e[j] = v[8 * c8 + j];
-        h.x = pack_bf2(e[0], e[1]);
-        h.y = pack_bf2(e[2], e[3]);
-        h.z = pack_bf2(e[4], e[5]);
-        h.w = pack_bf2(e[6], e[7]);
-        *reinterpret_cast<uint4*>(hi + c8 * (16 * TR) + 16 * r) = h;
-        if (lo) {
-            l.x = pack_bf2(e[0] - bf_hi(e[0]), e[1] - bf_hi(e[1]));
-            l.y = pack_bf2(e[2] - bf_hi(e[2]), e[3] - bf_hi(e[3]));
-            l.z = pack_bf2(e[4] - bf_hi(e[4]), e[5] - bf_hi(e[5]));
-            l.w = pack_bf2(e[6] - bf_hi(e[6]), e[7] - bf_hi(e[7]));
-            *reinterpret_cast<uint4*>(lo + c8 * (16 * TR) + 16 * r) = l;
+            for (int j = 0; j < 8; ++j) e[j] = v[8 * k + j];
+            uint4 h;
+            h.x = pack_bf2(e[0], e[1]);
+            h.y = pack_bf2(e[2], e[3]);
+            h.z = pack_bf2(e[4], e[5]);
+            h.w = pack_bf2(e[6], e[7]);
+            *reinterpret_cast<uint4*>(hi + c8 * (16 * TR) + 16 * r) = h;
+            if (lo) {
+                uint4 l;
+                l.x = pack_bf2(e[0] - bf_hi(e[0]), e[1] - bf_hi(e[1]));
+                l.y = pack_bf2(e[2] - bf_hi(e[2]), e[3] - bf_hi(e[3]));
+                l.z = pack_bf2(e[4] - bf_hi(e[4]), e[5] - bf_hi(e[5]));
+                l.w = pack_bf2(e[6] - bf_hi(e[6]), e[7] - bf_hi(e[7]));
+                *reinterpret_cast<uint4*>(lo + c8 * (16 * TR) + 16 * r) = l;
+            }
         }
     }
 }
-__device__ __forceinline__ void put_row_k0(const float (&v)[64], int K0, unsigned char* hi,
-                                           unsigned char* lo, int r) {
-    if (K0 == 32) put_row<32>(v, hi, lo, r);
-    else put_row<64>(v, hi, lo, r);
-}
 
-// fp32 weights [rows][cols] -> bf16 row-layout tile of R rows and Cp columns
-// (zero outside rows x cols)
-__device__ void load_w(const float* __restrict__ w, int rows, int cols, int R, int Cp,
-                       unsigned char* dst) {
-    for (int i = threadIdx.x; i < R * Cp; i += blockDim.x) {
-        const int r = i / Cp, c = i % Cp;
-        const float v = (r < rows && c < cols) ? w[r * cols + c] : 0.f;
-        *reinterpret_cast<__nv_bfloat16*>(dst + (c >> 3) * (16 * R) + 16 * r + 2 * (c & 7)) =
-            __float2bfloat16_rn(v);
-    }
-}
-
-// columns [col, col + 16 * NC) of this warp's 32 lanes
-template <int NC>
-__device__ __forceinline__ void tm_load(uint32_t taddr, float (&v)[64]) {
+// 32 consecutive tensor-memory columns of this warp's lanes
+__device__ __forceinline__ void tm_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r0[16], r1[16];
+    tc::tmem_ld16(taddr, r0);
+    tc::tmem_ld16(taddr + 16, r1);
+    tc::tmem_ld_wait();
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-        uint32_t r[16];
-        tc::tmem_ld16(taddr + 16 * q, r);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[16 * q + j] = __uint_as_float(r[j]);
-    }
-}
-__device__ __forceinline__ void tm_load_n(uint32_t taddr, int ncols, float (&v)[64]) {
-    switch (ncols / 16) {
-        case 1: tm_load<1>(taddr, v); break;
-        case 2: tm_load<2>(taddr, v); break;
-        case 3: tm_load<3>(taddr, v); break;
-        default: tm_load<4>(taddr, v); break;
+    for (int j = 0; j < 16; ++j) {
+        v[j] = __uint_as_float(r0[j]);
+        v[16 + j] = __uint_as_float(r1[j]);
     }
 }
 
-__device__ __forceinline__ float sigm(float u) { return 1.f / (1.f + __expf(-u)); }
+// logistic sigmoid (the exponential and the reciprocal on the
+// special-function unit)
+__device__ __forceinline__ float sigm(float u) { return __fdividef(1.f, 1.f + __expf(-u)); }
 
-// Sum of v[0..63] over the warp's lanes by recursive halving: afterwards
-// v[0] and v[1] hold the sums of columns bcol(lane) and bcol(lane) + 1.
-__device__ __forceinline__ void warp_colsum(float (&v)[64], int lane) {
+// Sum of v[0..31] over the warp's lanes by recursive halving: afterwards
+// v[0] holds the sum of column `lane`.
+__device__ __forceinline__ void warp_colsum32(float (&v)[32], int lane) {
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
-        const int h = 16 >> s, half = 32 >> s;
+        const int h = 16 >> s;
         const bool up = lane & h;
 #pragma unroll
-        for (int j = 0; j < half; ++j) {
-            const float send = up ? v[j] : v[j + half];
-            const float keep = up ? v[j + half] : v[j];
+        for (int j = 0; j < h; ++j) {
+            const float send = up ? v[j] : v[j + h];
+            const float keep = up ? v[j + h] : v[j];
             v[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
         }
     }
-}
-__device__ __forceinline__ int bcol(int lane) {
-    return ((lane & 16) ? 32 : 0) + ((lane & 8) ? 16 : 0) + ((lane & 4) ? 8 : 0) +
-           ((lane & 2) ? 4 : 0) + ((lane & 1) ? 2 : 0);
 }
 
 // All threads: bounded wait for the commit with the given parity; the result
@@ -274,14 +313,14 @@ __host__ __device__ inline TrainLayout train_layout(int K0, int NOp) {
     L.H3 = o; o += 2 * TR * HID;
     L.HL = o; o += 2 * TR * HID;
     L.D = o; o += 2 * TR * 2 * HID;
-    L.F32 = o; o += 4 * (4 * HID + 2 * 4 * HID + 4);  // biases, column-sum exchange (x2), loss
-    L.BAR = o; o += 16;
+    L.F32 = o; o += 4 * (4 * HID + 2 * 8 * 32 + 8);  // biases, column-sum exchange (x2), loss
+    L.BAR = o; o += 32;
     L.total = o;
     return L;
 }
 
 struct TrainArgs {
-    const float* params;
+    const unsigned char* image;  // the weight image (bf16 tiles + biases)
     int nin, n;
     const float* X;  // [n_rows][nin] standardised features
     const float* T;  // [n_rows][n] standardised targets
@@ -294,14 +333,13 @@ struct TrainArgs {
     uint64_t wait_ns;
 };
 
-// This thread's delta (row tid, 64 columns) into D as hi / lo pieces, and its
-// column sums (the bias gradient) into ex[buf][warp][64].
-__device__ __forceinline__ void put_delta(float (&dl)[64], unsigned char* D, float* ex, int tid) {
-    put_row<64>(dl, D, D + 8 * 16 * TR, tid);
-    warp_colsum(dl, tid & 31);
-    const int c = bcol(tid & 31);
-    ex[(tid >> 5) * HID + c] = dl[0];
-    ex[(tid >> 5) * HID + c + 1] = dl[1];
+// This thread's half row of the delta into D as hi / lo pieces, and the
+// warp's column sums (bias gradient) into ex[warp][lane].
+__device__ __forceinline__ void put_delta(float (&dl)[32], int c0, unsigned char* D, float* ex,
+                                          int row, int warp, int lane) {
+    put_half(dl, c0, HID, D, D + 8 * 16 * TR, row);
+    warp_colsum32(dl, lane);
+    ex[warp * 32 + lane] = dl[0];
 }
 
 __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
@@ -313,57 +351,54 @@ __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
     unsigned char *Xh = sm + L.X, *H1 = sm + L.H1, *H2 = sm + L.H2, *H3 = sm + L.H3;
     unsigned char *HL = sm + L.HL, *D = sm + L.D;
     float* bias = reinterpret_cast<float*>(sm + L.F32);  // b1 b2 b3 b4, 64 each
-    float* ex = bias + 4 * HID;                          // [2][4][64]
-    float* lred = ex + 2 * 4 * HID;                      // [4]
+    float* ex = bias + 4 * HID;                          // [2][8 warps][32]
+    float* lred = ex + 2 * 8 * 32;                       // [8]
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.BAR + 8);
-    const int tid = threadIdx.x, warp = tid >> 5;
-
-    load_w(a.params + of.W1, HID, a.nin, HID, dm.K0, W1);
-    load_w(a.params + of.W2, HID, HID, HID, HID, W2);
-    load_w(a.params + of.W3, HID, HID, HID, HID, W3);
-    load_w(a.params + of.W4, a.n, HID, dm.NOp, HID, W4);
-    for (int i = tid; i < 4 * HID; i += NTH) {
-        const int l = i / HID, c = i % HID;
-        const int boff = l == 0 ? of.b1 : l == 1 ? of.b2 : l == 2 ? of.b3 : of.b4;
-        bias[i] = (l < 3 || c < a.n) ? __bfloat162float(__float2bfloat16_rn(a.params[boff + c])) : 0.f;
-    }
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.BAR + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, c0 = 32 * (warp >> 2);
+    const int row = 32 * quarter + lane;  // tile row (tensor-memory lane) of this thread
+    uint64_t* lbar = bar + 1;             // weight image arrival
     if (warp == 0) tc::tmem_alloc(tslot, 512);
     if (tid == 0) {
         tc::mbar_init(bar, 1);
+        tc::mbar_init(lbar, 1);
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    const bool loaded =
+        load_image(a.image, img_wbytes(dm.K0, dm.NOp), W1, bias, lbar, a.wait_ns, a.d_err, 60);
+    bool ok = loaded;
     const uint32_t tm = *tslot;
-    const uint32_t tl = tm + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+    const uint32_t tl = tm + ((uint32_t)(32 * quarter) << 16) + c0;  // this thread's lanes, columns
     // tensor-memory columns: Z1 0, Z2 64, Z3 128, Z4 192 (then P3 192, P2 128,
     // P1 64); gradients G1 256, G2 320, G3 384, G4 448
     const float inv = 1.f / ((float)a.batch * (float)a.n);
     const int tiles = (a.batch + TR - 1) / TR;
     uint32_t ph = 0;
-    bool ok = true;
     float dbias[4] = {0.f, 0.f, 0.f, 0.f};  // thread c < 64: bias gradient column c
     float lsum = 0.f;
     int xb = 0;                             // column-sum exchange buffer
     auto colsum_take = [&](int l) {         // after a block barrier
         if (tid < HID) {
-            const float* e = ex + xb * 4 * HID;
-            dbias[l] += (e[tid] + e[HID + tid]) + (e[2 * HID + tid] + e[3 * HID + tid]);
+            const float* e = ex + xb * 8 * 32 + (tid >> 5) * 4 * 32 + (tid & 31);
+            dbias[l] += (e[0] + e[32]) + (e[64] + e[96]);
         }
         xb ^= 1;
     };
-    float v[64], w[64];
+    float v[32], w[32];
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
         const bool first = tile == (int)blockIdx.x;
-        const int b = tile * TR + tid;
+        const int b = tile * TR + row;
         const bool valid = b < a.batch;
-        const long long row = valid ? (a.start + b) % a.n_rows : 0;
+        const long long srow = valid ? (a.start + b) % a.n_rows : 0;
         // ---- forward
 #pragma unroll
-        for (int c = 0; c < 64; ++c) v[c] = (valid && c < a.nin) ? a.X[row * a.nin + c] : 0.f;
-        put_row_k0(v, dm.K0, Xh, HL, tid);
+        for (int j = 0; j < 32; ++j)
+            v[j] = (valid && c0 + j < a.nin) ? a.X[srow * a.nin + c0 + j] : 0.f;
+        put_half(v, c0, dm.K0, Xh, HL, row);
         to_issue();
         if (tid == 0) {
             tc::fence_after_sync();
@@ -375,13 +410,13 @@ __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
         unsigned char* Hs[3] = {H1, H2, H3};
         const unsigned char* Ws[3] = {W2, W3, W4};
         for (int l = 0; l < 3 && ok; ++l) {
-            tm_load<4>(tl + 64 * l, v);
+            tm_ld32(tl + 64 * l, v);
 #pragma unroll
-            for (int c = 0; c < 64; ++c) {
-                const float u = v[c] + bias[l * HID + c];
-                v[c] = u * sigm(u);
+            for (int j = 0; j < 32; ++j) {
+                const float u = v[j] + bias[l * HID + c0 + j];
+                v[j] = u * sigm(u);
             }
-            put_row<64>(v, Hs[l], HL, tid);
+            put_half(v, c0, HID, Hs[l], HL, row);
             to_issue();
             if (tid == 0) {
                 tc::fence_after_sync();
@@ -389,21 +424,22 @@ __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
                 tc::mma_commit(bar);
             }
             ok = wait_all(bar, ph, a.wait_ns, a.d_err, 62 + l);
-            ph ^= 1;
+            if (ok) ph ^= 1;
         }
         if (!ok) break;
-        // ---- loss and output delta
-        tm_load_n(tl + 192, dm.NOp, v);
+        // ---- loss and output delta (columns past NOp are read but not used)
+        tm_ld32(tl + 192, v);
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
+        for (int j = 0; j < 32; ++j) {
+            const int c = c0 + j;
             float dl = 0.f;
             if (valid && c < a.n) {
-                dl = v[c] + bias[3 * HID + c] - a.T[row * a.n + c];
+                dl = v[j] + bias[3 * HID + c] - a.T[srow * a.n + c];
                 lsum = fmaf(dl, dl, lsum);
             }
-            w[c] = dl * inv;
+            w[j] = dl * inv;
         }
-        put_delta(w, D, ex + xb * 4 * HID, tid);
+        put_delta(w, c0, D, ex + xb * 8 * 32, row, warp, lane);
         to_issue();
         colsum_take(3);
         if (tid == 0) {
@@ -418,15 +454,15 @@ __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
         const unsigned char* Hin[3] = {Xh, H1, H2};
         for (int l = 2; l >= 0 && ok; --l) {
             const int pcol = l == 2 ? 192 : 64 * (l + 1);
-            tm_load<4>(tl + pcol, v);
-            tm_load<4>(tl + 64 * l, w);
+            tm_ld32(tl + pcol, v);
+            tm_ld32(tl + 64 * l, w);
 #pragma unroll
-            for (int c = 0; c < 64; ++c) {
-                const float u = w[c] + bias[l * HID + c];
-                const float s = sigm(u);
-                w[c] = v[c] * (s * (1.f + u * (1.f - s)));
+            for (int j = 0; j < 32; ++j) {
+                const float u = w[j] + bias[l * HID + c0 + j];
+                const float sg = sigm(u);
+                w[j] = v[j] * (sg * (1.f + u * (1.f - sg)));
             }
-            put_delta(w, D, ex + xb * 4 * HID, tid);
+            put_delta(w, c0, D, ex + xb * 8 * 32, row, warp, lane);
             to_issue();
             colsum_take(l);
             if (tid == 0) {
@@ -436,7 +472,7 @@ __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
                 tc::mma_commit(bar);
             }
             ok = wait_all(bar, ph, a.wait_ns, a.d_err, 66 + l);
-            ph ^= 1;
+            if (ok) ph ^= 1;
         }
     }
     if (ok) {
@@ -448,18 +484,16 @@ __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
             const int cv = l == 0 ? a.nin : HID, rv = l == 3 ? a.n : HID;
             const int woff = l == 0 ? of.W1 : l == 1 ? of.W2 : l == 2 ? of.W3 : of.W4;
             const int boff = l == 0 ? of.b1 : l == 1 ? of.b2 : l == 2 ? of.b3 : of.b4;
-            tm_load_n(tl + 256 + 64 * l, cols, v);
+            if (c0 < cols) tm_ld32(tl + 256 + 64 * l, v);
             __syncthreads();
-            if (tid >= HID) {
+            if (row >= HID && c0 < cols) {
 #pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (c < cols) S[(tid - HID) * 65 + c] = v[c];
+                for (int j = 0; j < 32; ++j) S[(row - HID) * 65 + c0 + j] = v[j];
             }
             __syncthreads();
-            if (tid < HID) {
+            if (row < HID && c0 < cols) {
 #pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (c < cols) S[tid * 65 + c] += v[c];
+                for (int j = 0; j < 32; ++j) S[row * 65 + c0 + j] += v[j];
             }
             __syncthreads();
             for (int i = tid; i < rv * cv; i += NTH) P[woff + i] = S[(i / cv) * 65 + i % cv];
@@ -467,11 +501,15 @@ __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-        if ((tid & 31) == 0) lred[warp] = lsum;
+        if (lane == 0) lred[warp] = lsum;
         __syncthreads();
-        if (tid == 0) P[of.np] = 0.5f * inv * ((lred[0] + lred[1]) + (lred[2] + lred[3]));
+        if (tid == 0) {
+            float t = 0.f;
+            for (int k = 0; k < NTH / 32; ++k) t += lred[k];
+            P[of.np] = 0.5f * inv * t;
+        }
     } else {
-        drain(bar, ph, a.wait_ns);
+        drain(loaded ? bar : lbar, loaded ? ph : 0u, a.wait_ns);  // copies or MMAs in flight
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -483,14 +521,29 @@ __global__ void __launch_bounds__(NTH, 1) mlp_train_kernel(TrainArgs a) {
 
 // g_i = sum over the CTAs of the partials (fixed order); then, when m is
 // given, bias-corrected Adam on the fp32 masters. Index np: the loss.
-__global__ void reduce_adam_kernel(const float* __restrict__ part, int G, int PS, int np,
-                                   float* __restrict__ p, float* __restrict__ g_out,
-                                   float* __restrict__ m, float* __restrict__ v, float lr, float b1,
-                                   float b2, float eps, float c1, float c2, float* __restrict__ loss) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > np) return;
+// A block covers 32 consecutive indices (one per lane, coalesced) with its 8
+// warps taking every 8th CTA, so each thread's loads are independent; the
+// warps' sums are added in warp order.
+constexpr int RED_W = 8;
+__global__ void __launch_bounds__(32 * RED_W) reduce_adam_kernel(
+    const float* __restrict__ part, int G, int PS, int np, float* __restrict__ p,
+    float* __restrict__ g_out, float* __restrict__ m, float* __restrict__ v, float lr, float b1,
+    float b2, float eps, float c1, float c2, float* __restrict__ loss, unsigned char* image,
+    int nin, int n) {
+    __shared__ float acc[RED_W][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    float s = 0.f;
+    if (i <= np) {
+#pragma unroll 4
+        for (int c = w; c < G; c += RED_W) s += part[(size_t)c * PS + i];
+    }
+    acc[w][lane] = s;
+    __syncthreads();
+    if (w != 0 || i > np) return;
     float g = 0.f;
-    for (int c = 0; c < G; ++c) g += part[(size_t)c * PS + i];
+#pragma unroll
+    for (int k = 0; k < RED_W; ++k) g += acc[k][lane];
     if (i == np) {
         if (loss) *loss = g;
         return;
@@ -501,8 +554,17 @@ __global__ void reduce_adam_kernel(const float* __restrict__ part, int G, int PS
         const float vi = b2 * v[i] + (1.f - b2) * g * g;
         m[i] = mi;
         v[i] = vi;
-        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        if (image) img_store(image, off_of(nin, n), dims_of(nin, n), i, pi);
     }
+}
+
+// the image of the given parameters (zero-filled beforehand)
+__global__ void pack_kernel(const float* __restrict__ p, int nin, int n, unsigned char* image) {
+    const Off of = off_of(nin, n);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < of.np) img_store(image, of, dims_of(nin, n), i, p[i]);
 }
 
 // ------------------------------------------------------------------ features
@@ -540,7 +602,7 @@ __device__ __forceinline__ float pixel_feature(const FeatSrc& s, long long q, in
 enum { SRC_ROWS = 0, SRC_EVAL = 1 };
 
 struct FwdArgs {
-    const float* params;
+    const unsigned char* image;  // the weight image (bf16 tiles + biases)
     int nin, n;
     const float* X;  // SRC_ROWS: [rows][nin] standardised
     int rows;
@@ -552,7 +614,7 @@ struct FwdArgs {
     const int32_t* label_off;
     const uint32_t* bitmask;
     const uint32_t* rep;
-    int Wk, mode;
+    int Wk, mode, rule;
     float alpha, kappa_beta, sigma_c2, margin, eps;
     bool rho_var;
     float* neglog;
@@ -576,18 +638,15 @@ __host__ __device__ inline FwdLayout fwd_layout(int K0, int NOp) {
     L.HH = o; o += 2 * TR * HID;
     L.HL = o; o += 2 * TR * HID;
     L.F32 = o; o += 4 * (4 * HID + 4 * 64);  // biases; mu_x sd_x mu_t sd_t
-    L.BAR = o; o += 16;
+    L.BAR = o; o += 32;
     L.total = o;
     return L;
 }
 
 // Surrogate post-processing of one pixel (see the file header).
-__device__ void eval_pixel(const FwdArgs& a, long long q, const float (&zin)[64], const float* mu_t,
+__device__ void eval_pixel(const FwdArgs& a, long long q, float (&z)[64], const float* mu_t,
                            const float* sd_t, float gap_min) {
     const int n = a.n;
-    float z[64];  // indexed by label below: a local copy keeps zin in registers
-#pragma unroll
-    for (int j = 0; j < 64; ++j) z[j] = zin[j];
     const long long P = (long long)a.fs.H * a.fs.W;
     const float log_col_norm = 1.5f * logf(6.283185307179586f * a.sigma_c2);
     uint32_t bx[8];
@@ -634,8 +693,9 @@ __device__ void eval_pixel(const FwdArgs& a, long long q, const float (&zin)[64]
     for (int j = 0; j < n; ++j) ls += expf(z[j] - m1);
     const float lse = m1 + logf(ls);
     const float p1 = expf(m1 - lse), p2 = n > 1 ? expf(m2 - lse) : 0.f;
-    // a negative margin: the network answers every pixel (no exact fallback)
-    const bool fb = a.margin >= 0.f && ((p1 - p2 < a.margin) || (n > 1 && m1 - m2 < gap_min));
+    const bool fb = a.rule != CS_FALLBACK_NONE &&
+                    ((p1 - p2 < a.margin) ||
+                     (a.rule == CS_FALLBACK_GUARANTEED && n > 1 && m1 - m2 < gap_min));
     if (fb) {
         const int idx = atomicAdd(a.fb_count, 1);
         if (idx < P) a.fb_list[idx] = (int32_t)q;
@@ -648,31 +708,23 @@ __device__ void eval_pixel(const FwdArgs& a, long long q, const float (&zin)[64]
 }
 
 template <int SRC>
-__global__ void __launch_bounds__(NTH) mlp_fwd_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(NTH, 2) mlp_fwd_kernel(FwdArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const Dims dm = dims_of(a.nin, a.n);
-    const Off of = off_of(a.nin, a.n);
     const FwdLayout L = fwd_layout(dm.K0, dm.NOp);
     unsigned char *W1 = sm + L.W1, *W2 = sm + L.W2, *W3 = sm + L.W3, *W4 = sm + L.W4;
     unsigned char *HH = sm + L.HH, *HL = sm + L.HL;
+    float* ZS = reinterpret_cast<float*>(HH);  // [128][33]: upper output half (HH and HL)
     float* bias = reinterpret_cast<float*>(sm + L.F32);
     float* mu_x = bias + 4 * HID;
     float* sd_x = mu_x + 64;
     float* mu_t = sd_x + 64;
     float* sd_t = mu_t + 64;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.BAR + 8);
-    const int tid = threadIdx.x, warp = tid >> 5;
-
-    load_w(a.params + of.W1, HID, a.nin, HID, dm.K0, W1);
-    load_w(a.params + of.W2, HID, HID, HID, HID, W2);
-    load_w(a.params + of.W3, HID, HID, HID, HID, W3);
-    load_w(a.params + of.W4, a.n, HID, dm.NOp, HID, W4);
-    for (int i = tid; i < 4 * HID; i += NTH) {
-        const int l = i / HID, c = i % HID;
-        const int boff = l == 0 ? of.b1 : l == 1 ? of.b2 : l == 2 ? of.b3 : of.b4;
-        bias[i] = (l < 3 || c < a.n) ? __bfloat162float(__float2bfloat16_rn(a.params[boff + c])) : 0.f;
-    }
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.BAR + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, c0 = 32 * (warp >> 2);
+    const int row = 32 * quarter + lane;
     if (SRC == SRC_EVAL)
         for (int i = tid; i < 64; i += NTH) {
             mu_x[i] = i < a.nin ? a.stats[i] : 0.f;
@@ -680,16 +732,21 @@ __global__ void __launch_bounds__(NTH) mlp_fwd_kernel(FwdArgs a) {
             mu_t[i] = i < a.n ? a.stats[2 * a.nin + i] : 0.f;
             sd_t[i] = i < a.n ? a.stats[2 * a.nin + a.n + i] : 1.f;
         }
+    uint64_t* lbar = bar + 1;  // weight image arrival
     if (warp == 0) tc::tmem_alloc(tslot, 64);
     if (tid == 0) {
         tc::mbar_init(bar, 1);
+        tc::mbar_init(lbar, 1);
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    const bool loaded =
+        load_image(a.image, img_wbytes(dm.K0, dm.NOp), W1, bias, lbar, a.wait_ns, a.d_err, 70);
+    bool ok = loaded;
     const uint32_t tm = *tslot;
-    const uint32_t tl = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tl = tm + ((uint32_t)(32 * quarter) << 16) + c0;
     const long long total = SRC == SRC_ROWS ? (long long)a.rows : (long long)a.fs.H * a.fs.W;
     const long long tiles = (total + TR - 1) / TR;
     float gap_min = 0.f;
@@ -698,20 +755,22 @@ __global__ void __launch_bounds__(NTH) mlp_fwd_kernel(FwdArgs a) {
                           // (n - 1) exp(-(g - 2 eta)) <= eps
         gap_min = 2.2f * (*a.eta) + logf(fmaxf((float)(a.n - 1), 1.f) / a.eps);
     uint32_t ph = 0;
-    bool ok = true;
-    float v[64];
+    float v[32];
     for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const long long r = tile * TR + tid;
+        const long long r = tile * TR + row;
         const bool valid = r < total;
         if (SRC == SRC_ROWS) {
 #pragma unroll
-            for (int c = 0; c < 64; ++c) v[c] = (valid && c < a.nin) ? a.X[r * a.nin + c] : 0.f;
+            for (int j = 0; j < 32; ++j)
+                v[j] = (valid && c0 + j < a.nin) ? a.X[r * a.nin + c0 + j] : 0.f;
         } else {
 #pragma unroll
-            for (int c = 0; c < 64; ++c)
-                v[c] = (valid && c < a.nin) ? (pixel_feature(a.fs, r, c) - mu_x[c]) / sd_x[c] : 0.f;
+            for (int j = 0; j < 32; ++j) {
+                const int c = c0 + j;
+                v[j] = (valid && c < a.nin) ? (pixel_feature(a.fs, r, c) - mu_x[c]) / sd_x[c] : 0.f;
+            }
         }
-        put_row_k0(v, dm.K0, HH, HL, tid);
+        put_half(v, c0, dm.K0, HH, HL, row);
         for (int l = 0; l < 4; ++l) {
             to_issue();
             if (tid == 0) {
@@ -722,33 +781,48 @@ __global__ void __launch_bounds__(NTH) mlp_fwd_kernel(FwdArgs a) {
             }
             if (!(ok = wait_all(bar, ph, a.wait_ns, a.d_err, 71 + l))) break;
             ph ^= 1;
+            tm_ld32(tl, v);  // the last layer: columns past NOp are read but not used
             if (l < 3) {
-                tm_load<4>(tl, v);
 #pragma unroll
-                for (int c = 0; c < 64; ++c) {
-                    const float u = v[c] + bias[l * HID + c];
-                    v[c] = u * sigm(u);
+                for (int j = 0; j < 32; ++j) {
+                    const float u = v[j] + bias[l * HID + c0 + j];
+                    v[j] = u * sigm(u);
                 }
-                put_row<64>(v, HH, HL, tid);
-            } else {
-                tm_load_n(tl, dm.NOp, v);
+                put_half(v, c0, HID, HH, HL, row);
             }
         }
         if (!ok) break;
         tc::fence_before_sync();  // the next tile's MMAs overwrite these columns
-        if (valid) {
-            if (SRC == SRC_ROWS) {
 #pragma unroll
-                for (int j = 0; j < 64; ++j)
-                    if (j < a.n) a.Z[r * a.n + j] = v[j] + bias[3 * HID + j];
-            } else {
+        for (int j = 0; j < 32; ++j) v[j] += bias[3 * HID + c0 + j];
+        if (SRC == SRC_ROWS) {
+            if (valid) {
 #pragma unroll
-                for (int j = 0; j < 64; ++j) v[j] += bias[3 * HID + j];
-                eval_pixel(a, r, v, mu_t, sd_t, gap_min);
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < a.n) a.Z[r * a.n + c0 + j] = v[j];
             }
+        } else {
+            // one thread per pixel takes the labels' post-processing; for more
+            // than 32 labels the upper half comes through shared memory
+            float z[64];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) z[j] = v[j];
+            if (a.n > 32) {
+                if (c0) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) ZS[row * 33 + j] = v[j];
+                }
+                __syncthreads();
+                if (!c0) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) z[32 + j] = ZS[row * 33 + j];
+                }
+                __syncthreads();  // ZS is the next tile's operand space
+            }
+            if (!c0 && valid) eval_pixel(a, r, z, mu_t, sd_t, gap_min);
         }
     }
-    if (!ok) drain(bar, ph, a.wait_ns);
+    if (!ok) drain(loaded ? bar : lbar, loaded ? ph : 0u, a.wait_ns);  // copies or MMAs in flight
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -865,50 +939,65 @@ cudaError_t set_smem(const void* fn, size_t bytes) {
 
 int mlp_param_count(int nin, int n) { return off_of(nin, n).np; }
 
+size_t mlp_image_bytes(int nin, int n) {
+    const Dims dm = dims_of(nin, n);
+    return img_bytes(dm.K0, dm.NOp);
+}
+
+cudaError_t launch_mlp_pack(const float* params, int nin, int n, unsigned char* image,
+                            cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(image, 0, mlp_image_bytes(nin, n), st);
+    if (e != cudaSuccess) return e;
+    const int np = mlp_param_count(nin, n);
+    pack_kernel<<<(np + 255) / 256, 256, 0, st>>>(params, nin, n, image);
+    return cudaGetLastError();
+}
+
 int mlp_train_ctas(int batch, int n_sm) {
     const int tiles = (batch + TR - 1) / TR;
     return tiles < n_sm ? tiles : n_sm;
 }
 int mlp_part_stride(int nin, int n) { return (off_of(nin, n).np + 1 + 3) & ~3; }
 
-cudaError_t launch_mlp_train(const float* params, int nin, int n, const float* X, const float* T,
+cudaError_t launch_mlp_train(const unsigned char* image, int nin, int n, const float* X, const float* T,
                              int n_rows, long long start, int batch, float* part, int G,
                              int* d_err, uint64_t wait_ns, cudaStream_t st) {
     const Dims dm = dims_of(nin, n);
     const size_t smem = train_layout(dm.K0, dm.NOp).total;
     cudaError_t e = set_smem((const void*)mlp_train_kernel, smem);
     if (e != cudaSuccess) return e;
-    TrainArgs a{params, nin, n, X, T, n_rows, start, batch, part, mlp_part_stride(nin, n), d_err,
+    TrainArgs a{image, nin, n, X, T, n_rows, start, batch, part, mlp_part_stride(nin, n), d_err,
                 wait_ns ? wait_ns : MLP_WAIT_NS};
     mlp_train_kernel<<<G, NTH, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_adam(const float* part, int G, int nin, int n, float* p, float* g_out,
-                               float* m, float* v, float lr, int t, float* loss, cudaStream_t st) {
+                               float* m, float* v, float lr, int t, float* loss,
+                               unsigned char* image, cudaStream_t st) {
     const int np = mlp_param_count(nin, n);
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
-    reduce_adam_kernel<<<(np + 1 + 255) / 256, 256, 0, st>>>(part, G, mlp_part_stride(nin, n), np, p,
-                                                             g_out, m, v, lr, b1, b2, 1e-8f, c1, c2,
-                                                             loss);
+    reduce_adam_kernel<<<(np + 1 + 31) / 32, 32 * RED_W, 0, st>>>(part, G, mlp_part_stride(nin, n), np,
+                                                                  p, g_out, m, v, lr, b1, b2, 1e-8f,
+                                                                  c1, c2, loss, image, nin, n);
     return cudaGetLastError();
 }
 
 static int fwd_grid(long long total, int n_sm) {
     const long long tiles = (total + TR - 1) / TR;
-    const long long cap = 3LL * n_sm;  // three CTAs per SM (shared memory)
+    const long long cap = 2LL * n_sm;  // two CTAs per SM (registers)
     return (int)(tiles < cap ? tiles : cap);
 }
 
-cudaError_t launch_mlp_forward(const float* params, int nin, int n, const float* X, int rows,
+cudaError_t launch_mlp_forward(const unsigned char* image, int nin, int n, const float* X, int rows,
                                float* Z, int n_sm, int* d_err, uint64_t wait_ns, cudaStream_t st) {
     const Dims dm = dims_of(nin, n);
     const size_t smem = fwd_layout(dm.K0, dm.NOp).total;
     cudaError_t e = set_smem((const void*)mlp_fwd_kernel<SRC_ROWS>, smem);
     if (e != cudaSuccess) return e;
     FwdArgs a{};
-    a.params = params;
+    a.image = image;
     a.nin = nin;
     a.n = n;
     a.X = X;
@@ -926,7 +1015,7 @@ cudaError_t launch_surrogate_eval(const SurrogateEvalArgs& s, cudaStream_t st) {
     cudaError_t e = set_smem((const void*)mlp_fwd_kernel<SRC_EVAL>, smem);
     if (e != cudaSuccess) return e;
     FwdArgs a{};
-    a.params = s.params;
+    a.image = s.image;
     a.nin = s.nin;
     a.n = s.n;
     a.fs = FeatSrc{s.img, s.lead16, s.dist2, s.H, s.W, s.n, s.feature_set, s.d_min};
@@ -937,6 +1026,7 @@ cudaError_t launch_surrogate_eval(const SurrogateEvalArgs& s, cudaStream_t st) {
     a.rep = s.rep;
     a.Wk = s.Wk;
     a.mode = s.mode;
+    a.rule = s.rule;
     a.alpha = s.alpha;
     a.kappa_beta = s.kappa_beta;
     a.sigma_c2 = s.sigma_c2;

@@ -78,17 +78,27 @@ static cs_status ensure_surrogate(cs_ctx* ctx, int nin, int n) {
     return CS_OK;
 }
 
-// per-CTA gradient sums of one training step
-static cs_status ensure_partials(cs_ctx* ctx, size_t floats) {
-    if (ctx->mlp_part && ctx->mlp_part_cap >= floats) return CS_OK;
-    if (ctx->mlp_part) cudaFree(ctx->mlp_part);
-    ctx->mlp_part = nullptr;
-    ctx->mlp_part_cap = 0;
-    if (cudaMalloc(&ctx->mlp_part, floats * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        return cs_set_error(ctx, CS_ERR_NOMEM, "network gradient buffer allocation failed");
+// Network scratch in the context: the kernels' weight image, then the
+// per-CTA gradient sums of one training step (G CTAs).
+struct MlpScratch {
+    unsigned char* image;
+    float* part;
+};
+static cs_status mlp_scratch(cs_ctx* ctx, int nin, int n, int G, MlpScratch& out) {
+    const size_t img = (mlp_image_bytes(nin, n) + 255) & ~(size_t)255;
+    const size_t floats = img / sizeof(float) + (size_t)G * mlp_part_stride(nin, n);
+    if (!ctx->mlp_part || ctx->mlp_part_cap < floats) {
+        if (ctx->mlp_part) cudaFree(ctx->mlp_part);
+        ctx->mlp_part = nullptr;
+        ctx->mlp_part_cap = 0;
+        if (cudaMalloc(&ctx->mlp_part, floats * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return cs_set_error(ctx, CS_ERR_NOMEM, "network scratch allocation failed");
+        }
+        ctx->mlp_part_cap = floats;
     }
-    ctx->mlp_part_cap = floats;
+    out.image = reinterpret_cast<unsigned char*>(ctx->mlp_part);
+    out.part = ctx->mlp_part + img / sizeof(float);
     return CS_OK;
 }
 
@@ -118,8 +128,14 @@ cs_status cs_mlp_forward(cs_ctx* ctx, const float* params, int n_in, int n_out, 
         n_out > CS_MAX_LABELS)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: bad arguments", fn);
     DeviceGuard g(ctx->device);
-    cudaError_t e = launch_mlp_forward(params, n_in, n_out, X, rows, Z, ctx->n_sm, ctx->d_err,
-                                       ctx->wait_ns, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    MlpScratch ms;
+    cs_status s = mlp_scratch(ctx, n_in, n_out, 0, ms);
+    if (s) return s;
+    cudaError_t e = launch_mlp_pack(params, n_in, n_out, ms.image, st);
+    if (e == cudaSuccess)
+        e = launch_mlp_forward(ms.image, n_in, n_out, X, rows, Z, ctx->n_sm, ctx->d_err,
+                               ctx->wait_ns, st);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return cs_check_launch(ctx, fn);
 }
@@ -134,13 +150,16 @@ cs_status cs_mlp_grad(cs_ctx* ctx, const float* params, int n_in, int n_out, con
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int G = mlp_train_ctas(rows, ctx->n_sm);
-    cs_status s = ensure_partials(ctx, (size_t)G * mlp_part_stride(n_in, n_out));
+    MlpScratch ms;
+    cs_status s = mlp_scratch(ctx, n_in, n_out, G, ms);
     if (s) return s;
-    cudaError_t e = launch_mlp_train(params, n_in, n_out, X, T, rows, 0, rows, ctx->mlp_part, G,
-                                     ctx->d_err, ctx->wait_ns, st);
+    cudaError_t e = launch_mlp_pack(params, n_in, n_out, ms.image, st);
     if (e == cudaSuccess)
-        e = launch_reduce_adam(ctx->mlp_part, G, n_in, n_out, nullptr, grads, nullptr, nullptr, 0.f,
-                               1, loss, st);
+        e = launch_mlp_train(ms.image, n_in, n_out, X, T, rows, 0, rows, ms.part, G, ctx->d_err,
+                             ctx->wait_ns, st);
+    if (e == cudaSuccess)
+        e = launch_reduce_adam(ms.part, G, n_in, n_out, nullptr, grads, nullptr, nullptr, 0.f, 1,
+                               loss, nullptr, st);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return cs_check_launch(ctx, fn);
 }
@@ -176,7 +195,8 @@ cs_status cs_surrogate_fit(cs_ctx* ctx, const float* img, int H, int W, const ui
     if ((s = ensure_surrogate(ctx, nin, n))) return s;
     const int batch = 128 * std::max(1, std::min(ctx->n_sm, (ntr + 127) / 128));
     const int G = mlp_train_ctas(batch, ctx->n_sm);
-    if ((s = ensure_partials(ctx, (size_t)G * mlp_part_stride(nin, n)))) return s;
+    MlpScratch ms;
+    if ((s = mlp_scratch(ctx, nin, n, G, ms))) return s;
 
     // scratch: likelihood plan (distances, sample tables), list, targets, features
     LikPlanRef plan;
@@ -213,23 +233,24 @@ cs_status cs_surrogate_fit(cs_ctx* ctx, const float* img, int H, int W, const ui
     if (e == cudaSuccess) e = launch_stats(X, nin, T, n, N, ntr, sp.stats, st);
     if (e == cudaSuccess) e = launch_standardize(X, nin, T, n, N, N, sp.stats, Ts, st);
     if (e == cudaSuccess) e = launch_init_params(sp.p, sp.m, sp.v, nin, n, seed, st);
+    if (e == cudaSuccess) e = launch_mlp_pack(sp.p, nin, n, ms.image, st);
     {
         StageTimer tm(ctx, CS_STAGE_TRAIN, st);
         for (int t = 0; e == cudaSuccess && t < steps; ++t) {
-            e = launch_mlp_train(sp.p, nin, n, X, Ts, ntr, (long long)t * batch, batch, ctx->mlp_part,
+            e = launch_mlp_train(ms.image, nin, n, X, Ts, ntr, (long long)t * batch, batch, ms.part,
                                  G, ctx->d_err, ctx->wait_ns, st);
             // learning rate 4e-3, cosine decay to 1e-4
             const float lr = 1e-4f + 0.5f * (4e-3f - 1e-4f) * (1.f + cosf(3.14159265f * t / steps));
             if (e == cudaSuccess)
-                e = launch_reduce_adam(ctx->mlp_part, G, nin, n, sp.p, nullptr, sp.m, sp.v, lr, t + 1,
-                                       sp.loss, st);
+                e = launch_reduce_adam(ms.part, G, nin, n, sp.p, nullptr, sp.m, sp.v, lr, t + 1,
+                                       sp.loss, ms.image, st);
         }
     }
     // calibration on the validation rows: largest log-likelihood error
     if (e == cudaSuccess) e = cudaMemsetAsync(sp.eta, 0, sizeof(float), st);
     if (e == cudaSuccess)
-        e = launch_mlp_forward(sp.p, nin, n, X + (size_t)ntr * nin, nva, Z, ctx->n_sm, ctx->d_err,
-                               ctx->wait_ns, st);
+        e = launch_mlp_forward(ms.image, nin, n, X + (size_t)ntr * nin, nva, Z, ctx->n_sm,
+                               ctx->d_err, ctx->wait_ns, st);
     if (e == cudaSuccess) e = launch_calib(Z, Ts + (size_t)ntr * n, nin, n, nva, sp.stats, sp.eta, st);
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     ctx->surr_n = n;
@@ -243,8 +264,9 @@ cs_status cs_surrogate_fit(cs_ctx* ctx, const float* img, int H, int W, const ui
 
 cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const uint32_t* bitmask,
                             const float* lead16, int k, int n_labels, const int32_t* label_off,
-                            const int32_t* sample_pix, const cs_params* prm, double margin,
-                            float* neglog, float* post, int32_t* n_fallback, void* stream) {
+                            const int32_t* sample_pix, const cs_params* prm, int rule,
+                            double margin, float* neglog, float* post, int32_t* n_fallback,
+                            void* stream) {
     const char* fn = "cs_surrogate_eval";
     if (!ctx) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
     if (!img || !bitmask || !lead16 || !sample_pix || !neglog)
@@ -252,8 +274,10 @@ cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const u
     if (!ctx->surr_ready || ctx->surr_n != n_labels)
         return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: no surrogate fitted for %d labels", fn,
                             n_labels);
-    if (!(margin <= 1.0))
-        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: margin must be <= 1", fn);
+    if (!(margin >= 0.0 && margin <= 1.0))
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: margin must lie in [0, 1]", fn);
+    if (rule < CS_FALLBACK_GUARANTEED || rule > CS_FALLBACK_NONE)
+        return cs_set_error(ctx, CS_ERR_INVALID_ARG, "%s: unknown fallback rule %d", fn, rule);
     cs_status s = cs_check_likelihood_args(ctx, fn, H, W, k, n_labels, label_off, prm);
     if (s) return s;
     DeviceGuard g(ctx->device);
@@ -272,11 +296,14 @@ cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const u
     int* fb_count = c.take<int>(1);
     const int nin = ctx->surr_nin;
     SurrPtrs sp = surr_ptrs(ctx, nin, n_labels);
+    MlpScratch ms;
+    if ((s = mlp_scratch(ctx, nin, n_labels, 0, ms))) return s;
     cudaError_t e = cudaMemsetAsync(fb_count, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_mlp_pack(sp.p, nin, n_labels, ms.image, st);
     if (e == cudaSuccess) e = cs_enqueue_prepare(ctx, plan, img, bitmask, sample_pix, &exact, st);
     if (e == cudaSuccess) {
         SurrogateEvalArgs a{};
-        a.params = sp.p;
+        a.image = ms.image;
         a.nin = nin;
         a.n = n_labels;
         a.feature_set = ctx->surr_set;
@@ -297,6 +324,7 @@ cs_status cs_surrogate_eval(cs_ctx* ctx, const float* img, int H, int W, const u
         a.kappa_beta = (float)prm->kappa_beta;
         a.sigma_c2 = (float)prm->sigma_c2;
         a.rho_var = prm->rho_variance != 0;
+        a.rule = rule;
         a.margin = (float)margin;
         a.eps = 0.005f;
         a.neglog = neglog;

@@ -131,7 +131,7 @@ def test_surrogate_fit_eval(env, mode, features):
                 ctx.likelihood(img, c["bitmask"], pr.k, pr.label_off, smp, prm)
             else:
                 raw, _ = ctx.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off,
-                                            smp, prm, margin=-1.0, count=False)
+                                            smp, prm, rule=cs.FALLBACK_NONE, count=False)
         torch.cuda.synchronize()
         ts.append((time.perf_counter() - t0) / 3)
     praw = raw["post"].cpu().numpy().reshape(nl, P)
@@ -142,6 +142,23 @@ def test_surrogate_fit_eval(env, mode, features):
           f"max prob err {raw_err:.3f}, argmax agreement {raw_agree:.3f}")
     assert ts[1] < ts[0]
     assert raw_agree > 1.0 / nl  # better than chance
+    # the margin-only rule: exactly the pixels whose network margin is below
+    # 0.1 (decided on the same FP32 posteriors) take the exact sum, bit for bit
+    mg, nfb_m = ctx.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
+                                   rule=cs.FALLBACK_MARGIN, margin=0.1)
+    ctx.sync()
+    top = np.sort(praw, axis=0)
+    fb = (top[-1] - top[-2]) < np.float32(0.1)
+    assert nfb_m == int(fb.sum())
+    neg_m = mg["neglog"].cpu().numpy().reshape(nl, P)
+    neg_raw = raw["neglog"].cpu().numpy().reshape(nl, P)
+    assert np.array_equal(neg_m[:, fb], neg_ex[:, fb])
+    assert np.array_equal(neg_m[:, ~fb], neg_raw[:, ~fb])
+    pm = mg["post"].cpu().numpy().reshape(nl, P)
+    ans = ~fb
+    print(f"  margin rule: fallback share {fb.mean():.3f}; answered pixels: max prob err "
+          f"{np.max(np.abs(pm - post_ex)[:, ans]) if ans.any() else 0:.3f}, argmax agreement "
+          f"{np.mean(np.argmax(pm, 0)[ans] == np.argmax(post_ex, 0)[ans]) if ans.any() else 1:.4f}")
 
 
 def test_surrogate_against_oracle_sampled(env):
@@ -179,7 +196,7 @@ def test_eval_matches_oracle_network(env, mode, features):
     ctx.surrogate_fit(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
                       frac=0.1, steps=200, features=features, seed=9)
     out, _ = ctx.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
-                                margin=-1.0, count=False)
+                                rule=cs.FALLBACK_NONE, count=False)
     ctx.sync()
     n, P = pr.n_labels, pr.H * pr.W
     info = ctx.surrogate_info(n)
@@ -232,11 +249,11 @@ def test_surrogate_save_load_roundtrip(env, tmp_path):
     path = str(tmp_path / "net.cssurr")
     ctx.surrogate_save(path)
     a, _ = ctx.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
-                              margin=-1.0, count=False)
+                              rule=cs.FALLBACK_NONE, count=False)
     other = cs.Context(0)
     other.surrogate_load(path)
     b, _ = other.surrogate_eval(img, c["bitmask"], c["lead16"], pr.k, pr.label_off, smp, prm,
-                                margin=-1.0, count=False)
+                                rule=cs.FALLBACK_NONE, count=False)
     torch.cuda.synchronize()
     assert torch.equal(a["neglog"], b["neglog"]) and torch.equal(a["post"], b["post"])
     assert np.array_equal(ctx.surrogate_params(), other.surrogate_params())
