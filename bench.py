@@ -449,7 +449,15 @@ def measure_batch(ctx, cs, torch, dev, n_images, reduce_max, world, runs=5):
             "form": FORM_NAMES["fp8"], "pairs_per_run": pairs, "ms_per_run": ms,
             "pairs_per_s": pairs * world / (ms * 1e-3), "runs": runs,
             "graph": True, "autotuned": {"n_streams": cfg["n_streams"],
-                                         "order": "by cost" if cfg["order"] == 0 else "given"},
+                                         "order": "by cost" if cfg["order"] == 0 else "given",
+                                         "sum_kernel": (
+                                             f"variant {cfg['sum_variant']}: "
+                                             f"{cfg['sum_shape']['ctas_per_sm']} CTA(s) per SM, "
+                                             f"{cfg['sum_shape']['epilogue_warps']} epilogue warps, "
+                                             f"{cfg['sum_shape']['ring_stages']}-stage sample ring, "
+                                             f"{cfg['sum_shape']['texture_buffers']} pixel-tile "
+                                             "texture buffer(s)"),
+                                         "tuning_ms": cfg["tuned_ms"]},
             "l2": "not flushed: each run reads and writes about 1 GB (images, bitmasks, distances, outputs), far above L2"}
 
 

@@ -448,12 +448,16 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
  *    bitmasks, sample tables and, for the tensor-core forms, the image's
  *    sample tiles and descriptor;
  *  - tensor-core forms: ONE persistent tcgen05 launch over the work items
- *    (image, 16 x 8 pixel tile) of all images, in processing order; CTA c
- *    takes items c, c + 152, ... (plain FP32 form: one sum launch per image
- *    on its stream).
+ *    (image, 16 x 8 pixel tile, label) of all images, in processing order,
+ *    claimed by the CTAs from two device counters (whole pixel tiles while
+ *    more than about one per CTA is left, then single items); then the FP64
+ *    recompute of flagged rows and the label normalisation (plain FP32
+ *    form: one sum launch per image on its stream).
  * Processing order: by decreasing pixel x sample pairs (order 0), so that
  * the persistent launch ends with the cheapest items, or as given (order 1).
- * Results are bit-identical to cs_data_term on each image alone.
+ * Results are bit-identical to cs_data_term on each image alone with the
+ * sum kernel shape that cs_data_term uses (variant 0, the default); the
+ * other shape (variant 1, see cs_batch_config) agrees to rounding.
  */
 typedef struct {
     const float* img;          /* DEVICE H x W x 3 float32 */
@@ -469,7 +473,8 @@ typedef struct {
 } cs_image;
 
 #define CS_BATCH_GRAPH 1    /* capture the run into a CUDA graph after the first run; replay it */
-#define CS_BATCH_AUTOTUNE 2 /* first run times each (n_streams, order) candidate (synchronises) */
+#define CS_BATCH_AUTOTUNE 2 /* first run times each (sum kernel shape, n_streams, order)
+                               candidate (synchronises) */
 
 typedef struct cs_batch cs_batch;
 
@@ -496,10 +501,21 @@ cs_status cs_batch_create(cs_ctx* ctx, const cs_image* images, int n_images, con
 cs_status cs_batch_run(cs_batch* b, void* stream);
 
 /* The configuration in use: streams, order (0 = by decreasing cost,
- * 1 = given), total pixel x sample pairs per run, and the tuned run time in
- * milliseconds (-1 when not tuned). Any output pointer may be NULL. */
+ * 1 = given), total pixel x sample pairs per run, the tuned run time in
+ * milliseconds (-1 when not tuned), the tensor-core sum kernel's shape
+ * variant (0: two CTAs per SM where the layout fits, as cs_likelihood and
+ * cs_data_term use; 1: one CTA per SM with 16 epilogue warps and a deeper
+ * sample ring; the two associate the compensated sums differently and agree
+ * to rounding, each within the l_tol bound) and that shape as 4 ints (CTAs per SM, sample-ring stages,
+ * pixel-tile texture buffers, epilogue warps; zeros in the plain FP32 form).
+ * Any output pointer may be NULL. */
 cs_status cs_batch_config(const cs_batch* b, int32_t* n_streams, int32_t* order, double* pairs,
-                          double* tuned_ms);
+                          double* tuned_ms, int32_t* sum_variant, int32_t* sum_shape);
+
+/* Sets the configuration (1 <= n_streams <= 8, order 0 or 1, sum_variant 0
+ * or 1) instead of tuning it; the next run uses it (and recaptures the graph).
+ * Errors: CS_ERR_INVALID_ARG. */
+cs_status cs_batch_set_config(cs_batch* b, int n_streams, int order, int sum_variant);
 
 /* Frees the batch (waits for its streams first). NULL is a no-op. */
 void cs_batch_destroy(cs_batch* b);

@@ -61,6 +61,7 @@ EXPORTS = (
     "cs_batch_create",
     "cs_batch_run",
     "cs_batch_config",
+    "cs_batch_set_config",
     "cs_batch_destroy",
     "cs_batch_data_term",
     "cs_batch_likelihood",
@@ -242,7 +243,9 @@ def lib(path: str | None = None):
                                   ctypes.POINTER(V)]
     L.cs_batch_run.argtypes = [V, V]
     L.cs_batch_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                                  ctypes.POINTER(D), ctypes.POINTER(D)]
+                                  ctypes.POINTER(D), ctypes.POINTER(D),
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.cs_batch_set_config.argtypes = [V, I, I, I]
     L.cs_batch_destroy.argtypes = [V]
     L.cs_batch_destroy.restype = None
     L.cs_batch_data_term.argtypes = [V, ctypes.POINTER(Image), I, V, I, V, ctypes.POINTER(Params),
@@ -271,7 +274,7 @@ def lib(path: str | None = None):
               "cs_surrogate_eval", "cs_surrogate_params", "cs_surrogate_info", "cs_surrogate_save",
               "cs_surrogate_load", "cs_mlp_forward",
               "cs_mlp_grad", "cs_batch_create", "cs_batch_run", "cs_batch_config",
-              "cs_batch_data_term", "cs_batch_likelihood"):
+              "cs_batch_set_config", "cs_batch_data_term", "cs_batch_likelihood"):
         getattr(L, f).restype = I
     if path is None:
         _lib = L
@@ -688,12 +691,21 @@ class Batch:
         return self.outputs
 
     def config(self):
-        ns, om = ctypes.c_int32(), ctypes.c_int32()
+        ns, om, var = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         pairs, tms = ctypes.c_double(), ctypes.c_double()
+        shape = (ctypes.c_int32 * 4)()
         self.ctx.check(self.ctx._lib.cs_batch_config(self.handle, ctypes.byref(ns), ctypes.byref(om),
-                                                     ctypes.byref(pairs), ctypes.byref(tms)))
+                                                     ctypes.byref(pairs), ctypes.byref(tms),
+                                                     ctypes.byref(var), shape))
         return {"n_streams": ns.value, "order": om.value, "pairs": pairs.value,
-                "tuned_ms": tms.value}
+                "tuned_ms": tms.value, "sum_variant": var.value,
+                "sum_shape": {"ctas_per_sm": shape[0], "ring_stages": shape[1],
+                              "texture_buffers": shape[2], "epilogue_warps": shape[3]}}
+
+    def set_config(self, n_streams, order, sum_variant):
+        """cs_batch_set_config: an explicit configuration instead of tuning."""
+        self.ctx.check(self.ctx._lib.cs_batch_set_config(self.handle, int(n_streams), int(order),
+                                                         int(sum_variant)))
 
     def close(self):
         if self.handle:

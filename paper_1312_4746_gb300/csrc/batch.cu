@@ -1,7 +1,9 @@
 // Batches of images: per-image preparation on several streams, one
 // persistent tensor-core sum launch over all images' pixel tiles, optional
 // CUDA-graph capture of the whole run and a small autotuner over the launch
-// configuration (number of streams, processing order).
+// configuration (number of streams, processing order, and the sum kernel's
+// shape: two CTAs per SM with a shallow sample ring, or one CTA per SM with
+// 16 epilogue warps and a deeper ring; the two agree to rounding).
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -30,7 +32,10 @@ struct BatchImage {
 // Tuned configurations, shared by all contexts of the process and keyed by
 // the batch's shape signature (device name included).
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tuned;
+struct TuneCfg {
+    int streams, order, variant;
+};
+std::map<std::string, TuneCfg> g_tuned;
 bool g_tune_file_loaded = false;
 
 const char* tune_file() {
@@ -48,18 +53,25 @@ void load_tune_file() {
     while (std::getline(in, line)) {
         std::istringstream ls(line);
         std::string sig;
-        int s = 0, o = 0;
-        if (ls >> sig >> s >> o && s >= 1 && s <= MAX_STREAMS && (o == 0 || o == 1))
-            g_tuned[sig] = {s, o};
+        int s = 0, o = 0, v = 0;
+        double ms = 0;
+        // "sig streams order variant ms" (a line without the variant: variant 0)
+        if (!(ls >> sig >> s >> o)) continue;
+        std::string rest;
+        std::getline(ls, rest);
+        std::istringstream rs(rest);
+        if (!(rs >> v >> ms)) v = 0;
+        if (s >= 1 && s <= MAX_STREAMS && (o == 0 || o == 1) && (v == 0 || v == 1))
+            g_tuned[sig] = {s, o, v};
     }
 }
 
-void store_tune(const std::string& sig, int s, int o, double ms) {
-    g_tuned[sig] = {s, o};
+void store_tune(const std::string& sig, int s, int o, int v, double ms) {
+    g_tuned[sig] = {s, o, v};
     const char* f = tune_file();
     if (!f) return;
     std::ofstream out(f, std::ios::app);
-    out << sig << " " << s << " " << o << " " << ms << "\n";
+    out << sig << " " << s << " " << o << " " << v << " " << ms << "\n";
 }
 
 }  // namespace
@@ -81,6 +93,7 @@ struct cs_batch {
     unsigned long long* flag_words = nullptr;   // per-pixel flag words over all images
     int total_pixels = 0;
     int n_streams = 4, order_mode = 0;
+    int variant = 0;              // sum kernel shape (TcSumParams::variant)
     std::vector<int> order;       // image index at each processing position
     // at each processing position: the number of its first item, its first
     // pixel and first pixel tile in the launch, its (pixel tiles, labels)
@@ -190,6 +203,7 @@ static cudaError_t enqueue_run(cs_batch* b, cudaStream_t st) {
         p.shapes = b->shapes.data();
         p.queue = b->queue;
         p.flags = b->flag_words;
+        p.variant = b->variant;
         e = launch_tc_sum(b->descs, (int)b->order.size(), p, st);
     }
     return e;
@@ -220,38 +234,53 @@ static cudaError_t capture(cs_batch* b) {
     return e;
 }
 
-// Times every (streams, order) candidate on `st` and keeps the fastest.
+// The sum kernel shapes worth timing: variant 1 only where it differs from 0.
+static int n_variants(const cs_batch* b) {
+    if (!b->tc) return 1;
+    int s0[4], s1[4];
+    const bool tex8 = b->prm.precision == CS_FP8, ps = b->prm.mode == CS_MODE_PERSAMPLE;
+    if (!tc_sum_shape(b->k, tex8, ps, 0, s0) || !tc_sum_shape(b->k, tex8, ps, 1, s1)) return 1;
+    return std::memcmp(s0, s1, sizeof s0) ? 2 : 1;
+}
+
+// Times every (sum kernel shape, streams, order) candidate on `st` and keeps
+// the fastest.
 static cudaError_t autotune(cs_batch* b, cudaStream_t st) {
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     const int cand_s[] = {1, 2, 4, 8};
-    int best_s = b->n_streams, best_o = b->order_mode;
+    int best_s = b->n_streams, best_o = b->order_mode, best_v = b->variant;
     float best = -1.f;
-    for (int o = 0; e == cudaSuccess && o < 2; ++o)
-        for (int si = 0; e == cudaSuccess && si < 4; ++si) {
-            set_order(b, cand_s[si], o);
-            e = enqueue_run(b, st);  // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(t0, st);
-            for (int r = 0; e == cudaSuccess && r < 2; ++r) e = enqueue_run(b, st);
-            if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-            if (e == cudaSuccess && (best < 0.f || ms < best)) {
-                best = ms;
-                best_s = cand_s[si];
-                best_o = o;
+    const int nv = n_variants(b);
+    for (int v = 0; e == cudaSuccess && v < nv; ++v)
+        for (int o = 0; e == cudaSuccess && o < 2; ++o)
+            for (int si = 0; e == cudaSuccess && si < 4; ++si) {
+                set_order(b, cand_s[si], o);
+                b->variant = v;
+                e = enqueue_run(b, st);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+                for (int r = 0; e == cudaSuccess && r < 2; ++r) e = enqueue_run(b, st);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e == cudaSuccess && (best < 0.f || ms < best)) {
+                    best = ms;
+                    best_s = cand_s[si];
+                    best_o = o;
+                    best_v = v;
+                }
             }
-        }
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     set_order(b, best_s, best_o);
+    b->variant = best_v;
     if (e == cudaSuccess) {
         b->tuned = true;
         b->tuned_ms = best / 2.0;
         std::lock_guard<std::mutex> lk(g_tune_mutex);
-        store_tune(b->sig, best_s, best_o, b->tuned_ms);
+        store_tune(b->sig, best_s, best_o, best_v, b->tuned_ms);
     }
     return e;
 }
@@ -402,8 +431,9 @@ static cs_status batch_create(const char* fn, cs_ctx* ctx, const cs_image* image
         load_tune_file();
         auto it = g_tuned.find(b->sig);
         if (it != g_tuned.end()) {
-            ns = it->second.first;
-            om = it->second.second;
+            ns = it->second.streams;
+            om = it->second.order;
+            b->variant = it->second.variant < n_variants(b) ? it->second.variant : 0;
             b->tuned = true;  // configuration known: no tuning at the first run
         }
     }
@@ -444,12 +474,37 @@ cs_status cs_batch_run(cs_batch* b, void* stream) {
 }
 
 cs_status cs_batch_config(const cs_batch* b, int32_t* n_streams, int32_t* order, double* pairs,
-                          double* tuned_ms) {
+                          double* tuned_ms, int32_t* sum_variant, int32_t* sum_shape) {
     if (!b) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "cs_batch_config: batch is NULL");
     if (n_streams) *n_streams = b->n_streams;
     if (order) *order = b->order_mode;
     if (pairs) *pairs = b->pairs;
     if (tuned_ms) *tuned_ms = b->tuned_ms;
+    if (sum_variant) *sum_variant = b->variant;
+    if (sum_shape) {
+        int sh[4] = {0, 0, 0, 0};
+        if (b->tc)
+            tc_sum_shape(b->k, b->prm.precision == CS_FP8, b->prm.mode == CS_MODE_PERSAMPLE,
+                         b->variant, sh);
+        for (int i = 0; i < 4; ++i) sum_shape[i] = sh[i];
+    }
+    return CS_OK;
+}
+
+cs_status cs_batch_set_config(cs_batch* b, int n_streams, int order, int sum_variant) {
+    const char* fn = "cs_batch_set_config";
+    if (!b) return cs_set_error(nullptr, CS_ERR_INVALID_ARG, "%s: batch is NULL", fn);
+    if (n_streams < 1 || n_streams > MAX_STREAMS || (order != 0 && order != 1) ||
+        (sum_variant != 0 && sum_variant != 1))
+        return cs_set_error(b->ctx, CS_ERR_INVALID_ARG,
+                            "%s: need 1 <= n_streams <= %d, order 0 or 1, variant 0 or 1", fn,
+                            MAX_STREAMS);
+    DeviceGuard g(b->ctx->device);
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    drop_graph(b);  // the next run captures the new configuration
+    set_order(b, n_streams, order);
+    b->variant = sum_variant;
+    b->tuned = true;  // no autotuning over an explicit choice
     return CS_OK;
 }
 

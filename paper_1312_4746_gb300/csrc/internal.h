@@ -385,6 +385,9 @@ struct TcSumParams {
     const int2* shapes = nullptr;  // n_images x (pixel tiles, labels)
     unsigned* queue = nullptr;
     unsigned long long* flags = nullptr;
+    // kernel shape: 0 two CTAs per SM where the layout fits, 1 one CTA per SM
+    // (16 epilogue warps, deeper sample ring); equal to rounding
+    int variant = 0;
 };
 struct TcLaunch {
     const float* img;
@@ -436,6 +439,9 @@ cudaError_t launch_tc_tiles(const TcLaunch& L, cudaStream_t st);
 cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st);
 // One persistent launch over the items of n_images prepared images (sizes,
 // counters and flag words in p).
+// CTAs per SM, sample-ring stages, pixel-tile texture buffers and epilogue
+// warps of the sum kernel for (k, form, variant); false if unsupported
+bool tc_sum_shape(int k, bool tex8, bool persample, int variant, int* shape);
 cudaError_t launch_tc_sum(const TcImage* descs, int n_images, const TcSumParams& p,
                           cudaStream_t st);
 // Preparation (the tiles only when `sorted`) and the sum, for a single image

@@ -168,7 +168,7 @@ __host__ __device__ constexpr int tex_ext(int k, bool tex8) {
                                                            : 0;
 }
 
-template <bool TEX8, int KS, bool PERSAMPLE>
+template <bool TEX8, int KS, bool PERSAMPLE, bool SOLO = false>
 struct Cfg {
     // ring stage: texture slabs, colour slab (both bulk-copied), then the two
     // sample-side location slabs the producer writes
@@ -184,7 +184,11 @@ struct Cfg {
     // Two CTAs per SM (each 256 TMEM columns, a sample ring of two or more
     // stages, 8 epilogue warps) when that layout fits twice in the SM's
     // 228 KB (a CTA of the pair may use 228 KB / 2 - 1 KB, the per-CTA
-    // reservation), else one CTA per SM with 16 epilogue warps. Two label
+    // reservation) and SOLO is not asked for, else one CTA per SM with 16
+    // epilogue warps and the deeper ring that the whole SM's shared memory
+    // allows. The shapes split a sample tile's columns differently among the
+    // epilogue warps, so their compensated sums associate differently: the
+    // results agree to rounding, within the same a-priori bound. Two label
     // buffers of pixel-side operands always (the next item's are written
     // while the current one is summed); the sample ring as deep as fits (2 to
     // 4 stages) and, if room is left, two pixel-tile texture buffers.
@@ -194,7 +198,7 @@ struct Cfg {
         return stages * stage_bytes + atb * tex_bytes + 2 * AP + XB * (epq - 1) * 4 * 32 * 8 +
                (2 * stages + 2 * NB + 4 + 2 * atb + 4 * XB + 1 + 2 * QD) * 8 + MISC;
     }
-    static constexpr bool PAIR = bytes(2, 1, 2) <= PAIR_LIMIT;
+    static constexpr bool PAIR = !SOLO && bytes(2, 1, 2) <= PAIR_LIMIT;
     static constexpr int MIN_BLOCKS = PAIR ? 2 : 1;
     static constexpr int EPQ = PAIR ? 2 : 4;                 // epilogue warps per TMEM lane quadrant
     static constexpr int EPI_WARPS = 4 * EPQ;
@@ -473,10 +477,10 @@ __global__ void __launch_bounds__(256) normalise_kernel(TcArgs a) {
     }
 }
 
-template <bool TEX8, int KS, bool PERSAMPLE>
-__global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE>::THREADS),
-                                  (Cfg<TEX8, KS, PERSAMPLE>::MIN_BLOCKS)) sum_tc_kernel(TcArgs a) {
-    using C = Cfg<TEX8, KS, PERSAMPLE>;
+template <bool TEX8, int KS, bool PERSAMPLE, bool SOLO>
+__global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
+                                  (Cfg<TEX8, KS, PERSAMPLE, SOLO>::MIN_BLOCKS)) sum_tc_kernel(TcArgs a) {
+    using C = Cfg<TEX8, KS, PERSAMPLE, SOLO>;
     constexpr int EPQ = C::EPQ, EPI_WARPS = C::EPI_WARPS, CPW = C::CPW, NB = C::NB, ATB = C::ATB;
     constexpr int PRODUCER = C::PRODUCER, MMA_WARP = C::MMA_WARP;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -1376,9 +1380,9 @@ cudaError_t tiles(const TcLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <bool TEX8, int KS, bool PERSAMPLE>
+template <bool TEX8, int KS, bool PERSAMPLE, bool SOLO>
 cudaError_t sum(const TcImage* descs, int n_images, const TcSumParams& p, cudaStream_t st) {
-    using C = Cfg<TEX8, KS, PERSAMPLE>;
+    using C = Cfg<TEX8, KS, PERSAMPLE, SOLO>;
     static_assert(C::smem_bytes <= 227 * 1024, "shared memory budget");
     TcArgs a{};
     a.images = descs;
@@ -1402,7 +1406,7 @@ cudaError_t sum(const TcImage* descs, int n_images, const TcSumParams& p, cudaSt
     a.l_tol = p.l_tol;
     a.wait_ns = p.wait_ns;
     a.stall = p.stall;
-    cudaError_t e = cudaFuncSetAttribute(sum_tc_kernel<TEX8, KS, PERSAMPLE>,
+    cudaError_t e = cudaFuncSetAttribute(sum_tc_kernel<TEX8, KS, PERSAMPLE, SOLO>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.fb_count, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.queue, 0, 2 * sizeof(unsigned), st);
@@ -1424,7 +1428,7 @@ cudaError_t sum(const TcImage* descs, int n_images, const TcSumParams& p, cudaSt
     }
     a.pt1 = (int)pt1;
     a.i1 = i1;
-    sum_tc_kernel<TEX8, KS, PERSAMPLE><<<grid, C::THREADS, C::smem_bytes, st>>>(a);
+    sum_tc_kernel<TEX8, KS, PERSAMPLE, SOLO><<<grid, C::THREADS, C::smem_bytes, st>>>(a);
     refine_fp64_kernel<<<2 * p.n_sm, 128, 0, st>>>(
         descs, p.fb_list, p.fb_count, p.fb_cap, p.flags, (p.k + 31) / 32, (double)p.alpha,
         (double)p.d_min, (double)p.kappa_beta, (double)p.sigma_c2, PERSAMPLE, p.rho_var, p.d_err);
@@ -1497,9 +1501,26 @@ cudaError_t launch_tc_sum(const TcImage* descs, int n_images, const TcSumParams&
                           cudaStream_t st) {
     if (n_images < 1 || p.n_items < 1 || p.n_items >= (1ll << 31)) return cudaErrorInvalidValue;
     return dispatch(p.k, p.tex8, p.persample, [&](auto t8, auto ks, auto ps) {
-        return sum<decltype(t8)::value, decltype(ks)::value, decltype(ps)::value>(descs, n_images,
-                                                                                 p, st);
+        constexpr bool T8 = decltype(t8)::value, PS = decltype(ps)::value;
+        constexpr int K = decltype(ks)::value;
+        return p.variant == 1 ? sum<T8, K, PS, true>(descs, n_images, p, st)
+                              : sum<T8, K, PS, false>(descs, n_images, p, st);
     });
+}
+
+bool tc_sum_shape(int k, bool tex8, bool persample, int variant, int* shape) {
+    return dispatch(k, tex8, persample, [&](auto t8, auto ks, auto ps) {
+               constexpr bool T8 = decltype(t8)::value, PS = decltype(ps)::value;
+               constexpr int K = decltype(ks)::value;
+               using C0 = Cfg<T8, K, PS, false>;
+               using C1 = Cfg<T8, K, PS, true>;
+               const bool solo = variant == 1;
+               shape[0] = solo ? C1::MIN_BLOCKS : C0::MIN_BLOCKS;
+               shape[1] = solo ? C1::STAGES : C0::STAGES;
+               shape[2] = solo ? C1::ATB : C0::ATB;
+               shape[3] = solo ? C1::EPI_WARPS : C0::EPI_WARPS;
+               return cudaSuccess;
+           }) == cudaSuccess;
 }
 
 cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st) {

@@ -85,7 +85,8 @@ def test_batch_null_args_no_gpu(L):
                              ctypes.byref(b)) == cs.CS_ERR_INVALID_ARG
     assert b"ctx" in L.cs_last_error(None)
     assert L.cs_batch_run(None, None) == cs.CS_ERR_INVALID_ARG
-    assert L.cs_batch_config(None, None, None, None, None) == cs.CS_ERR_INVALID_ARG
+    assert L.cs_batch_config(None, None, None, None, None, None, None) == cs.CS_ERR_INVALID_ARG
+    assert L.cs_batch_set_config(None, 1, 0, 0) == cs.CS_ERR_INVALID_ARG
     assert L.cs_batch_data_term(None, imgs, 1, None, 8, None, ctypes.byref(p),
                                 None) == cs.CS_ERR_INVALID_ARG
     L.cs_batch_destroy(None)  # no-op

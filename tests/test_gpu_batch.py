@@ -2,8 +2,10 @@
 
 Every image of a batch must come out bit-identical to cs_data_term on that
 image alone (same kernels, same per-pixel arithmetic and sample order), in
-every form, with and without CUDA-graph replay and autotuning; one image is
-also checked against the FP64 oracle at sampled pixels.
+every form, with and without CUDA-graph replay and autotuning, when the sum
+kernel has the single-image shape; the other shape agrees within the
+a-priori bound. One image is also checked against the FP64 oracle at
+sampled pixels.
 """
 import dataclasses
 
@@ -109,14 +111,59 @@ def test_batch_autotune(env):
     ctx.sync()
     cfg = b.config()
     assert cfg["n_streams"] in (1, 2, 4, 8) and cfg["order"] in (0, 1)
+    assert cfg["sum_variant"] in (0, 1)
     assert cfg["tuned_ms"] > 0
     for q, x, o in zip(probs, inp, outs):
-        _same(o, _single(ctx, cs, torch, q, x, prm, omega, mask))
+        ref = _single(ctx, cs, torch, q, x, prm, omega, mask)
+        if cfg["sum_variant"] == 0:
+            _same(o, ref)
+        else:
+            _close(o, ref, prm.l_tol)
     b.close()
     # a second batch with the same shapes reuses the tuned configuration
     b2 = ctx.batch(inp, omega, mask, prm, flags=cs.BATCH_AUTOTUNE)
     assert b2.config()["n_streams"] == cfg["n_streams"]
+    assert b2.config()["sum_variant"] == cfg["sum_variant"]
     b2.close()
+
+
+def _close(a, b, l_tol):
+    """Two tensor-core results, each within l_tol max(|L|, 1) of the exact L
+    (rows above the a-priori bound are recomputed in FP64), differ by at most
+    twice that."""
+    x = -a["neglog"].cpu().numpy().astype(np.float64)
+    y = -b["neglog"].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(x - y) <= 2 * l_tol * np.maximum(np.abs(y), 1)), float(np.max(np.abs(x - y)))
+
+
+@pytest.mark.parametrize("precision,mode", [(2, 0), (1, 0), (2, 1)])
+def test_batch_sum_shapes(env, precision, mode):
+    """Both shapes of the tensor-core sum kernel (two CTAs per SM with 8
+    epilogue warps; one CTA per SM with 16 epilogue warps and a deeper sample
+    ring): shape 0 bit-identical to the single-image calls, shape 1 within
+    the a-priori bound of it; an invalid configuration is refused."""
+    cs, ctx, torch = env
+    probs = _problems()
+    prm = cs.Params.from_synth(probs[0].params, precision=precision, mode=mode)
+    omega, mask = _dev(torch, probs[0].omega), _dev(torch, probs[0].mask)
+    inp = _inputs(torch, probs)
+    b = ctx.batch(inp, omega, mask, prm, flags=cs.BATCH_GRAPH)
+    got, shapes = [], []
+    for variant in (0, 1):
+        b.set_config(2, 0, variant)
+        outs = b.run()
+        ctx.sync()
+        cfg = b.config()
+        assert cfg["sum_variant"] == variant
+        shapes.append(cfg["sum_shape"])
+        got.append([{k: o[k].clone() for k in ("neglog", "post")} for o in outs])
+    assert shapes[1]["ctas_per_sm"] == 1 and shapes[1]["epilogue_warps"] == 16
+    for q, x, o0, o1 in zip(probs, inp, got[0], got[1]):
+        _same(o0, _single(ctx, cs, torch, q, x, prm, omega, mask))
+        _close(o1, o0, prm.l_tol)
+    with pytest.raises(cs.CsError):
+        b.set_config(3, 0, 2)
+    b.close()
 
 
 def test_batch_one_shot_and_oracle(env):
