@@ -268,7 +268,7 @@ def cpu_baseline(pr, budget_s=15.0):
 # DRAM bytes per launch of the sum kernels on this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
 # kernels as they are now)
-TRAFFIC = {"sum_tc_kernel": 9.32e6, "sum_plain_kernel": 7.83e6}
+TRAFFIC = {"sum_tc_kernel": 8.89e6, "sum_plain_kernel": 7.83e6}
 
 FORMS = {"fp32": 0, "bf16": 1, "fp8": 2}
 FORM_NAMES = {"fp32": "plain FP32 (CUDA cores, popc TSM)",
@@ -595,6 +595,58 @@ def measure_surrogate(ctx, cs, torch, dev, reduce_max, world, steps=1000, runs=2
     return out
 
 
+def profile_kernels():
+    """A small, fixed case for ncu captures of the hot kernels: after
+    untimed warm-ups (the FP8 data term on the 481x321 workload three times,
+    a 200-step surrogate fit on the 1024x1024 workload), one FP8 data term,
+    one network gradient over 19456 rows and one surrogate evaluation of the
+    1024x1024 image run inside the NVTX range "kernels". Prints nothing
+    measured: the numbers come from the profiler."""
+    import numpy as np
+    import torch
+
+    from paper_1312_4746_gb300 import build as csbuild
+
+    csbuild.build()
+    import paper_1312_4746_gb300 as cs
+    from paper_1312_4746_gb300 import synth
+
+    dev = torch.device("cuda:0")
+    ctx = cs.Context(0)
+    pr = synth.make_workload(WORKLOAD)
+    img = torch.from_numpy(pr.image).to(dev)
+    om = torch.from_numpy(pr.omega).to(dev)
+    mask = torch.from_numpy(pr.mask).to(dev)
+    smp = torch.from_numpy(pr.sample_pix).to(dev)
+    prm = cs.Params.from_synth(pr.params, precision=FORMS["fp8"])
+    out = None
+    for _ in range(3):
+        out = ctx.data_term(img, om, mask, pr.label_off, smp, prm, out=out)
+    p4 = synth.make_workload(4)
+    img4 = torch.from_numpy(p4.image).to(dev)
+    smp4 = torch.from_numpy(p4.sample_pix).to(dev)
+    prm4 = cs.Params.from_synth(p4.params, mode=1)
+    c4 = ctx.codes(img4, torch.from_numpy(p4.omega).to(dev), torch.from_numpy(p4.mask).to(dev),
+                   prm4, want_lead16=True)
+    ctx.surrogate_fit(img4, c4["bitmask"], c4["lead16"], p4.k, p4.label_off, smp4, prm4,
+                      frac=0.05, steps=200, features=cs.SURR_EXTENDED, seed=11)
+    n_in = ctx.surrogate_info(p4.n_labels)["n_in"]
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy(rng.normal(0, 1, (19456, n_in)).astype(np.float32)).to(dev)
+    T = torch.from_numpy(rng.normal(0, 1, (19456, p4.n_labels)).astype(np.float32)).to(dev)
+    params = torch.from_numpy(ctx.surrogate_params()).to(dev)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("kernels")
+    ctx.data_term(img, om, mask, pr.label_off, smp, prm, out=out)
+    ctx.mlp_grad(params, p4.n_labels, X, T)
+    ctx.surrogate_eval(img4, c4["bitmask"], c4["lead16"], p4.k, p4.label_off, smp4, prm4,
+                       rule=cs.FALLBACK_NONE, count=False)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ctx.close()
+    print("profile-kernels: done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,6 +658,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-images", type=int, default=64,
                     help="also time a batch of this many uneven images (0: skip)")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="run only the small fixed case for ncu captures (see profile_kernels)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 1024x1024 and 4096x4096 workloads and the surrogate")
     args = ap.parse_args()
@@ -613,6 +667,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_kernels:
+        profile_kernels()
         return
 
     import torch

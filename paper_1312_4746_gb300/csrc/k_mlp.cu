@@ -576,24 +576,24 @@ struct FeatSrc {
     float d_min;
 };
 
-// Raw feature c of pixel q: [R, G, B, x/W, y/H, a_1..a_16], then for feature
-// set 1 log max(d_i, d_min) for every label i and sin, cos of 2^f pi x/W and
-// of 2^f pi y/H for f = 0..5 (the argument reduced exactly: 2^f x mod 2W).
-__device__ __forceinline__ float pixel_feature(const FeatSrc& s, long long q, int c) {
-    const long long P = (long long)s.H * s.W;
-    const int x = (int)(q % s.W), y = (int)(q / s.W);
-    if (c < 3) return s.img[q * 3 + c];
+// Raw feature c of pixel q = y W + x: [R, G, B, x/W, y/H, a_1..a_16], then
+// for feature set 1 log max(d_i, d_min) for every label i and sin, cos of
+// 2^f pi x/W and of 2^f pi y/H for f = 0..5 (the argument reduced exactly:
+// 2^f x mod 2W). Images hold fewer than 2^31 pixels.
+__device__ __forceinline__ float pixel_feature(const FeatSrc& s, int q, int x, int y, int c) {
+    if (c < 3) return s.img[(size_t)q * 3 + c];
     if (c == 3) return (float)x / (float)s.W;
     if (c == 4) return (float)y / (float)s.H;
-    if (c < 21) return s.lead16[q * 16 + (c - 5)];
+    if (c < 21) return s.lead16[(size_t)q * 16 + (c - 5)];
     if (s.set == 0) return 0.f;
     c -= 21;
-    if (c < s.n) return logf(fmaxf(sqrtf((float)s.dist2[(size_t)c * P + q]), s.d_min));
+    if (c < s.n)
+        return logf(fmaxf(sqrtf((float)s.dist2[(size_t)c * s.H * s.W + q]), s.d_min));
     c -= s.n;
     if (c >= 24) return 0.f;
     const int f = c >> 2, kind = c & 3;
     const int w = kind < 2 ? s.W : s.H;
-    const long long m = ((long long)(kind < 2 ? x : y) << f) % (2LL * w);
+    const int m = (int)(((long long)(kind < 2 ? x : y) << f) % (2LL * w));
     const float t = (float)m / (float)w;
     return (kind & 1) ? cospif(t) : sinpif(t);
 }
@@ -653,6 +653,7 @@ __device__ void eval_pixel(const FwdArgs& a, long long q, float (&z)[64], const 
     for (int w = 0; w < 8; ++w)
         bx[w] = (a.mode == CS_MODE_FACTORISED && w < a.Wk) ? a.bitmask[q * a.Wk + w] : 0u;
     float tmax = -INFINITY;
+    float tex[64];  // factorised mode: the texture exponents -h_j / beta_j
     for (int j = 0; j < n; ++j) {
         const float rho = a.alpha * fmaxf(sqrtf((float)a.fs.dist2[(size_t)j * P + q]), a.fs.d_min);
         const float T = z[j] * sd_t[j] + mu_t[j];
@@ -661,24 +662,15 @@ __device__ void eval_pixel(const FwdArgs& a, long long q, float (&z)[64], const 
         if (a.mode == CS_MODE_FACTORISED) {
             int h = 0;
             for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[j * a.Wk + w]);
-            tmax = fmaxf(tmax, -(float)h / (a.kappa_beta * rho));
+            tex[j] = -(float)h / (a.kappa_beta * rho);
+            tmax = fmaxf(tmax, tex[j]);
         }
     }
     if (a.mode == CS_MODE_FACTORISED) {
         float ts = 0.f;
-        for (int j = 0; j < n; ++j) {
-            const float rho = a.alpha * fmaxf(sqrtf((float)a.fs.dist2[(size_t)j * P + q]), a.fs.d_min);
-            int h = 0;
-            for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[j * a.Wk + w]);
-            ts += expf(-(float)h / (a.kappa_beta * rho) - tmax);
-        }
+        for (int j = 0; j < n; ++j) ts += expf(tex[j] - tmax);
         const float tl = tmax + logf(ts);
-        for (int j = 0; j < n; ++j) {
-            const float rho = a.alpha * fmaxf(sqrtf((float)a.fs.dist2[(size_t)j * P + q]), a.fs.d_min);
-            int h = 0;
-            for (int w = 0; w < a.Wk; ++w) h += __popc(bx[w & 7] ^ a.rep[j * a.Wk + w]);
-            z[j] += -(float)h / (a.kappa_beta * rho) - tl;
-        }
+        for (int j = 0; j < n; ++j) z[j] += tex[j] - tl;
     }
     float m1 = -INFINITY, m2 = -INFINITY;
     for (int j = 0; j < n; ++j) {
@@ -764,10 +756,12 @@ __global__ void __launch_bounds__(NTH, 2) mlp_fwd_kernel(FwdArgs a) {
             for (int j = 0; j < 32; ++j)
                 v[j] = (valid && c0 + j < a.nin) ? a.X[r * a.nin + c0 + j] : 0.f;
         } else {
+            const int q = valid ? (int)r : 0, y = q / a.fs.W, x = q - y * a.fs.W;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int c = c0 + j;
-                v[j] = (valid && c < a.nin) ? (pixel_feature(a.fs, r, c) - mu_x[c]) / sd_x[c] : 0.f;
+                v[j] = (valid && c < a.nin) ? (pixel_feature(a.fs, q, x, y, c) - mu_x[c]) / sd_x[c]
+                                            : 0.f;
             }
         }
         put_half(v, c0, dm.K0, HH, HL, row);
@@ -837,7 +831,8 @@ __global__ void features_kernel(FeatSrc s, int nin, const int32_t* __restrict__ 
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)rows * nin) return;
     const long long r = i / nin;
-    X[i] = pixel_feature(s, list[r], (int)(i % nin));
+    const int q = list[r], y = q / s.W, x = q - y * s.W;
+    X[i] = pixel_feature(s, q, x, y, (int)(i % nin));
 }
 
 // one block per column: mean and standard deviation over the first n_rows
