@@ -49,6 +49,33 @@ __device__ __forceinline__ void guard_push(int2* guard, int cap, int* count, int
     if (idx < cap) guard[idx] = make_int2(pix, j);
 }
 
+// Thresholds codes j0 .. j0 + 15 of one pixel (from a tensor-memory load):
+// entry j (< k) goes to the co-support word when |a_j| <= tau and it is not
+// within its error bound E_j = rn_j ebase + slack of tau; entries within
+// the bound are marked in gword for the exact recheck. No branch per entry;
+// rn is zero-padded beyond k.
+__device__ __forceinline__ void threshold16(const uint32_t (&v)[16], int j0, int k, const float* rn,
+                                            float ebase, float tau_f, float tau_slack,
+                                            uint32_t& word, uint32_t& gword) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int j = j0 + e;
+        const float aa = fabsf(__uint_as_float(v[e]));
+        const float E = rn[j] * ebase + tau_slack;
+        const bool g = fabsf(aa - tau_f) <= E;
+        const uint32_t m = j < k ? 1u << (j & 31) : 0u;
+        word |= (!g && aa <= tau_f) ? m : 0u;
+        gword |= g ? m : 0u;
+    }
+}
+
+// the guard entries of one 32-code word
+__device__ __forceinline__ void guard_word(int2* guard, int cap, int* count, int pix, int w,
+                                           uint32_t gword) {
+    for (uint32_t gm = gword; gm; gm &= gm - 1)
+        guard_push(guard, cap, count, pix, 32 * w + __ffs(gm) - 1);
+}
+
 template <int P>
 __global__ void __launch_bounds__(TILE* TILE)
     codes_f32_kernel(const float* __restrict__ img, int H, int W, const float* __restrict__ omega,
@@ -634,31 +661,24 @@ __global__ void __launch_bounds__(128, 4) codes_tc_kernel(
     if (ok) {
         const int Wk = (k + 31) >> 5;
         const uint32_t lrow = tmem + ((uint32_t)(32 * warp) << 16);
-        uint32_t word = 0;
+        uint32_t word = 0, gword = 0;
         for (int c = 0; c < np / 16; ++c) {
             uint32_t v[16];
             tc::tmem_ld16(lrow + 16u * c, v);
             tc::tmem_ld_wait();
+            threshold16(v, 16 * c, k, s_rn, ebase, tau_f, tau_slack, word, gword);
+            if (live && (codes || lead16)) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int j = 16 * c + e;
-                if (j < k && live) {
-                    const float a = __uint_as_float(v[e]);
-                    const float aa = fabsf(a);
-                    const float E = s_rn[j] * ebase + tau_slack;
-                    if (!whole) {
-                        if (fabsf(aa - tau_f) <= E)
-                            guard_push(guard, guard_cap, guard_count, pix, j);
-                        else if (aa <= tau_f)
-                            word |= 1u << (j & 31);
-                    }
-                    if (codes) codes[(size_t)pix * k + j] = a;
-                    if (lead16 && j < 16) lead16[(size_t)pix * 16 + j] = a;
+                for (int e = 0; e < 16; ++e) {
+                    const int j = 16 * c + e;
+                    if (j < k && codes) codes[(size_t)pix * k + j] = __uint_as_float(v[e]);
+                    if (j < 16 && j < k && lead16) lead16[(size_t)pix * 16 + j] = __uint_as_float(v[e]);
                 }
             }
             if ((c & 1) || c == np / 16 - 1) {
-                if (live && bitmask) bitmask[(size_t)pix * Wk + (c >> 1)] = word;
-                word = 0;
+                if (live && !whole) guard_word(guard, guard_cap, guard_count, pix, c >> 1, gword);
+                if (live && bitmask) bitmask[(size_t)pix * Wk + (c >> 1)] = whole ? 0u : word;
+                word = gword = 0;
             }
         }
         if (live && whole) guard_push(guard, guard_cap, guard_count, pix, -1);
@@ -898,31 +918,25 @@ __global__ void __launch_bounds__(CP_THREADS, P <= 7 ? 2 : 1) codes_tcp_kernel(
             const bool live = pp.x >= 0, whole = pp.y != 0;
             const int pix = live ? pp.x : 0;
             const float ebase = __int_as_float(pp.z);
-            uint32_t word = 0;
+            uint32_t word = 0, gword = 0;
             for (int c = 0; c < nch; ++c) {
                 uint32_t v[16];
                 tc::tmem_ld16(lrow + (uint32_t)(b * ncols) + 16u * c, v);
                 tc::tmem_ld_wait();
+                threshold16(v, 16 * c, k, s_rn, ebase, tau_f, tau_slack, word, gword);
+                if (live && (codes || lead16)) {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int j = 16 * c + e;
-                    if (j < k && live) {
-                        const float a = __uint_as_float(v[e]);
-                        const float aa = fabsf(a);
-                        const float E = s_rn[j] * ebase + tau_slack;
-                        if (!whole) {
-                            if (fabsf(aa - tau_f) <= E)
-                                guard_push(guard, guard_cap, guard_count, pix, j);
-                            else if (aa <= tau_f)
-                                word |= 1u << (j & 31);
-                        }
-                        if (codes) codes[(size_t)pix * k + j] = a;
-                        if (lead16 && j < 16) lead16[(size_t)pix * 16 + j] = a;
+                    for (int e = 0; e < 16; ++e) {
+                        const int j = 16 * c + e;
+                        if (j < k && codes) codes[(size_t)pix * k + j] = __uint_as_float(v[e]);
+                        if (j < 16 && j < k && lead16)
+                            lead16[(size_t)pix * 16 + j] = __uint_as_float(v[e]);
                     }
                 }
                 if ((c & 1) || c == nch - 1) {
-                    if (live && bitmask) bitmask[(size_t)pix * Wk + (c >> 1)] = word;
-                    word = 0;
+                    if (live && !whole) guard_word(guard, guard_cap, guard_count, pix, c >> 1, gword);
+                    if (live && bitmask) bitmask[(size_t)pix * Wk + (c >> 1)] = whole ? 0u : word;
+                    word = gword = 0;
                 }
             }
             tc::fence_before_sync();
