@@ -804,7 +804,8 @@ __global__ void __launch_bounds__(CP_THREADS, P <= 7 ? 2 : 1) codes_tcp_kernel(
         int kk = 0;
         for (int T = blockIdx.x; T < ntiles; T += gridDim.x, ++kk) {
             const int x0 = (T % ntx) * CT_W, y0 = (T / ntx) * CT_H;
-            for (int i = lane; i < WH * WW; i += 32) {
+#pragma unroll
+            for (int i = lane; i < WH * WW; i += 32) {  // every load in flight at once
                 const int ly = i / WW, lx = i % WW;
                 const int yy = min(max(y0 + 2 * warp + ly - R, 0), H - 1);
                 const int xx = min(max(x0 + lx - R, 0), W - 1);
@@ -859,27 +860,27 @@ __global__ void __launch_bounds__(CP_THREADS, P <= 7 ? 2 : 1) codes_tcp_kernel(
                 uint32_t w1[8], w2[8], w3[8];
 #pragma unroll
                 for (int e2i = 0; e2i < 8; ++e2i) {
-                    uint32_t p1 = 0, p2 = 0, p3 = 0;
+                    // two codes' inputs at a time, each split into three bf16
+                    // pieces (v = b1 + b2 + b3 to 24 bits) by paired conversions
+                    float v[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int t = 16 * sl + 2 * e2i + h;
-                        float v = 0.f;
+                        v[h] = 0.f;
                         if (t < N && live) {
                             const int li = (tyl + t / P) * WW + tx + t % P;
-                            v = __fmul_rn(__fsub_rn(__fmul_rn(s_w[t], wg[li]), mu), inv);
+                            v[h] = __fmul_rn(__fsub_rn(__fmul_rn(s_w[t], wg[li]), mu), inv);
                         }
-                        const __nv_bfloat16 b1 = __float2bfloat16_rn(v);
-                        const float r1 = v - __bfloat162float(b1);
-                        const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
-                        const float r2 = r1 - __bfloat162float(b2);
-                        const __nv_bfloat16 b3 = __float2bfloat16_rn(r2);
-                        p1 |= (uint32_t)__bfloat16_as_ushort(b1) << (16 * h);
-                        p2 |= (uint32_t)__bfloat16_as_ushort(b2) << (16 * h);
-                        p3 |= (uint32_t)__bfloat16_as_ushort(b3) << (16 * h);
                     }
-                    w1[e2i] = p1;
-                    w2[e2i] = p2;
-                    w3[e2i] = p3;
+                    const __nv_bfloat162 b1 = __floats2bfloat162_rn(v[0], v[1]);
+                    const float2 f1 = __bfloat1622float2(b1);
+                    const float r0 = v[0] - f1.x, r1 = v[1] - f1.y;
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(r0, r1);
+                    const float2 f2 = __bfloat1622float2(b2);
+                    const __nv_bfloat162 b3 = __floats2bfloat162_rn(r0 - f2.x, r1 - f2.y);
+                    w1[e2i] = *reinterpret_cast<const uint32_t*>(&b1);
+                    w2[e2i] = *reinterpret_cast<const uint32_t*>(&b2);
+                    w3[e2i] = *reinterpret_cast<const uint32_t*>(&b3);
                 }
                 uint8_t* a1 = sa + sl * 4096;
                 uint8_t* a2 = sa + (KS + sl) * 4096;
