@@ -483,6 +483,10 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
     using C = Cfg<TEX8, KS, PERSAMPLE, SOLO>;
     constexpr int EPQ = C::EPQ, EPI_WARPS = C::EPI_WARPS, CPW = C::CPW, NB = C::NB, ATB = C::ATB;
     constexpr int PRODUCER = C::PRODUCER, MMA_WARP = C::MMA_WARP;
+    // With as many ring stages as accumulators, stage it % STAGES and
+    // accumulator it % NB free up with the same MMAs: the producers then wait
+    // on the accumulator's commit and the MMA issuer commits once per tile.
+    constexpr bool ONE_COMMIT = C::STAGES == NB;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ring = smem + C::ring_off;
     uint8_t* atex = smem + C::atex_off;
@@ -648,7 +652,8 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                 }
                 const int s = (int)(it % C::STAGES);
                 const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
-                ok = spin_warp(empty + s, ph ^ 1, abort_flag, a.d_err, 1, wait_ns);
+                ok = spin_warp((ONE_COMMIT ? tmem_full : empty) + s, ph ^ 1, abort_flag, a.d_err, 1,
+                               wait_ns);
                 if (!ok) break;
                 uint8_t* st = ring + s * C::stage_bytes;
                 const int nvalid = min(BN, m_i - (T - T0) * BN);
@@ -735,7 +740,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                                  C::id_bf16, 1);
                     tc::mma_bf16(d1, tc::smem_desc(ap + 8192), tc::smem_desc(st + C::bl_off + 4096),
                                  C::id_bf16, 1);
-                    tc::mma_commit(empty + s);
+                    if (!ONE_COMMIT) tc::mma_commit(empty + s);
                     tc::mma_commit(tmem_full + b);
                     last = it;
                 }
