@@ -156,9 +156,16 @@ def test_surrogate_fit_eval(env, mode, features):
     assert np.array_equal(neg_m[:, ~fb], neg_raw[:, ~fb])
     pm = mg["post"].cpu().numpy().reshape(nl, P)
     ans = ~fb
+    ans_agree = np.mean(np.argmax(pm, 0)[ans] == np.argmax(post_ex, 0)[ans]) if ans.any() else 1.0
     print(f"  margin rule: fallback share {fb.mean():.3f}; answered pixels: max prob err "
           f"{np.max(np.abs(pm - post_ex)[:, ans]) if ans.any() else 0:.3f}, argmax agreement "
-          f"{np.mean(np.argmax(pm, 0)[ans] == np.argmax(post_ex, 0)[ans]) if ans.any() else 1:.4f}")
+          f"{ans_agree:.4f}")
+    if mode == 1 and features == 1:
+        # what the trained network gains where it is useful (the factorised
+        # texture added exactly, the extended features): measured 0.93 alone,
+        # 35% fallback, 99.5% agreement on the answered pixels
+        assert raw_agree >= 0.85
+        assert fb.mean() <= 0.6 and ans_agree >= 0.98
 
 
 def test_surrogate_against_oracle_sampled(env):
