@@ -982,11 +982,19 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                 const int cbase = hf * CPW;
                 const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cbase);
                 uint64_t x1[8];
+                bool released = false;
                 if (cbase + CPW <= nvalid) {  // warp-uniform: all columns valid
                     float ts = 0.f;
 #pragma unroll
                     for (int ch = 0; ch < CPW / 16; ++ch) {
                         tc::tmem_ld16_wait_pk(lb + 16u * ch, x1);
+                        if (ch == CPW / 16 - 1) {
+                            // the last chunk is in registers: release the
+                            // accumulator before its arithmetic
+                            tc::fence_before_sync();
+                            tc::mbar_arrive_elect(tmem_empty + b);
+                            released = true;
+                        }
                         ts += sum16_full(x1, bt2, k2);
                     }
                     two_sum(ts, S, Ccomp);
@@ -1004,8 +1012,10 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                 }
                 // tcgen05.wait::ld is warp-collective: every lane's loads are
                 // complete here; one elected lane releases the buffer
-                tc::fence_before_sync();
-                tc::mbar_arrive_elect(tmem_empty + b);
+                if (!released) {
+                    tc::fence_before_sync();
+                    tc::mbar_arrive_elect(tmem_empty + b);
+                }
                 if (t == 0 && nxt.img >= 0) {
                     // the next item's operands, while this item's MMAs run on
                     if (n_newpt) px_finish(npx);
