@@ -204,6 +204,17 @@ __global__ void __launch_bounds__(TILE* TILE)
 // index-order sums run on lane 0. An entry (pixel, j) decides code j;
 // (pixel, -1) every code of a nearly flat patch (one lane per code). Guarded
 // bits were left clear by the codes kernel and are set here.
+//
+// A code entry is first decided from the same element values with warp-tree
+// sums, when that value is clear of tau by a bound that covers both it and
+// the index-order evaluation: from the values v_t (identical in both), with
+// u = 2^-53, A = sum |v_t|, ss = sum c_t^2, every mean, centring, square,
+// root, quotient, product and N-term sum is within
+//   |a - a_exact| <= |O_j| (e_s + N u (1 + e_s)),
+//   e_s = 2 u sqrt(N) A / sqrt(ss) + (N / 2 + 5) u   (bound on |s - s_exact|)
+// of the exact value in either summation order, so the two differ by at most
+// twice that; the filter asks for four times (an entry closer to tau, or a
+// flat patch, takes the index-order path).
 __device__ __forceinline__ double canon_v(const float* __restrict__ img, int H, int W,
                                           const float* __restrict__ mask, int p, int y, int x,
                                           int t) {
@@ -233,14 +244,62 @@ __global__ void __launch_bounds__(128) codes_guard_kernel(
     const int Wk = (k + 31) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     double* sb = s_buf[wib];
+    auto wsum = [](double v) {  // warp-tree sum, the same value on every lane
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    };
     for (int e = blockIdx.x + gridDim.x * wib; e < cnt; e += gridDim.x * 4) {
         const int2 g = guard[e];
         const int y = g.x / W, x = g.x % W;
         double c[NL];
+        double vv[NL];
 #pragma unroll
         for (int u = 0; u < NL; ++u) {
             const int t = lane + 32 * u;
-            if (t < N) sb[t] = canon_v(img, H, W, mask, P, y, x, t);
+            vv[u] = t < N ? canon_v(img, H, W, mask, P, y, x, t) : 0.0;
+            if (t < N) sb[t] = vv[u];
+        }
+        if (g.y >= 0) {
+            // tree-sum filter (see above); warp-uniform decision
+            double sv = 0.0, av = 0.0;
+#pragma unroll
+            for (int u = 0; u < NL; ++u) {
+                sv = __dadd_rn(sv, vv[u]);
+                av = __dadd_rn(av, fabs(vv[u]));
+            }
+            const double mu_f = __ddiv_rn(wsum(sv), (double)N), A = wsum(av);
+            double sc = 0.0;
+#pragma unroll
+            for (int u = 0; u < NL; ++u) {
+                const int t = lane + 32 * u;
+                c[u] = t < N ? __dadd_rn(vv[u], -mu_f) : 0.0;
+                sc = __dadd_rn(sc, __dmul_rn(c[u], c[u]));
+            }
+            const double ss_f = wsum(sc);
+            if (ss_f > 0.0) {
+                const double nrm_f = __dsqrt_rn(ss_f);
+                const float* oj = omega + (size_t)g.y * N;
+                double sa = 0.0, so = 0.0;
+#pragma unroll
+                for (int u = 0; u < NL; ++u) {
+                    const int t = lane + 32 * u;
+                    const double o = t < N ? (double)oj[t] : 0.0;
+                    sa = __dadd_rn(sa, __dmul_rn(o, __ddiv_rn(c[u], nrm_f)));
+                    so = __dadd_rn(so, __dmul_rn(o, o));
+                }
+                const double a_f = wsum(sa), on = __dsqrt_rn(wsum(so));
+                const double uu = 1.1102230246251565e-16;  // 2^-53
+                const double es = 2.0 * uu * sqrt((double)N) * A / nrm_f + (0.5 * N + 5.0) * uu;
+                const double eps = 4.0 * on * (es + N * uu * (1.0 + es)) * 1.01;
+                const double aa = fabs(a_f);
+                if (aa <= tau - eps || aa > tau + eps) {
+                    if (lane == 0 && aa <= tau - eps)
+                        atomicOr(bitmask + (size_t)g.x * Wk + (g.y >> 5), 1u << (g.y & 31));
+                    __syncwarp();
+                    continue;
+                }
+            }
         }
         __syncwarp();
         double mu = 0.0;
