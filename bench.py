@@ -512,7 +512,7 @@ def measure_surrogate(ctx, cs, torch, dev, reduce_max, world, steps=1000, runs=2
     samples): fit on exact FP32 likelihoods at 5% of the pixels (tensor-core
     training, `steps` Adam steps), then evaluation under each fallback rule,
     against the exact sums of the same call (cs_likelihood, plain FP32 and
-    FP8 tensor-core forms) as the judge: fallback share, max posterior
+    FP8 tensor-core forms) as the reference: fallback share, max posterior
     error and argmax agreement over all pixels and over the pixels the
     network answers, and the time of fit + eval as pairs/s-equivalent.
     Per mode (per-sample and factorised texture) and feature set. CUDA
@@ -550,7 +550,7 @@ def measure_surrogate(ctx, cs, torch, dev, reduce_max, world, steps=1000, runs=2
         return {"max_prob_err": float(d.max()), "argmax_agreement": float(agree.float().mean())}
 
     out = {"workload": pr.name, "pairs_per_image": pairs, "training_fraction": 0.05,
-           "steps": steps, "judge": "exact FP32 sums of the whole image (cs_likelihood)"}
+           "steps": steps, "errors_against": "exact FP32 sums of the whole image (cs_likelihood)"}
     for mode in (0, 1):
         prm = cs.Params.from_synth(pr.params, mode=mode)
         c = ctx.codes(img, om, mask, prm, want_lead16=True)
