@@ -29,9 +29,18 @@ cs_status cs_check_launch(cs_ctx* ctx, const char* what) {
     return CS_OK;
 }
 
+// Drops every cached data-term graph (they name scratch addresses).
+static void drop_dt_graphs(cs_ctx* ctx) {
+    for (auto& g : ctx->dt_graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    ctx->dt_graphs.clear();
+}
+
 cs_status cs_ensure_scratch(cs_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->scratch_cap) return CS_OK;
     size_t want = bytes + bytes / 4 + (1u << 20);
+    drop_dt_graphs(ctx);
+    ++ctx->scratch_gen;
     if (ctx->scratch) {
         cudaFree(ctx->scratch);  // waits for outstanding work on the device
         ctx->scratch = nullptr;
@@ -146,6 +155,7 @@ cs_status cs_create(cs_ctx** out, int device) {
         cudaMemset(c->d_err, 0, 2 * sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
@@ -153,6 +163,7 @@ cs_status cs_create(cs_ctx** out, int device) {
         if (c->d_err) cudaFree(c->d_err);
         if (c->side) cudaStreamDestroy(c->side);
         if (c->side2) cudaStreamDestroy(c->side2);
+        if (c->cap) cudaStreamDestroy(c->cap);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
         if (c->ev_join) cudaEventDestroy(c->ev_join);
         delete c;
@@ -177,6 +188,8 @@ void cs_destroy(cs_ctx* ctx) {
     if (ctx->mlp_part) cudaFree(ctx->mlp_part);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->side2) cudaStreamDestroy(ctx->side2);
+    drop_dt_graphs(ctx);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
@@ -875,31 +888,96 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
     float* iota_smp = smooth ? c.take<float>((size_t)k * L.S) : nullptr;
     float* reps = smooth ? c.take<float>((size_t)n_labels * k) : nullptr;
     a.d_err = ctx->d_err;
-    // fork: the distance transform and the tensor-core sample order depend
-    // only on the scribbles; they run on the context's two side streams while
-    // the codes run on the caller's stream
-    cudaError_t e = launch_set_offsets(L.offs, 2 * (L.n_labels + 1), L.d_off, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-    if (e == cudaSuccess) e = enqueue_distances(ctx, L, sample_pix, ctx->side, false);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
-    if (e == cudaSuccess && L.tc_form) {
-        e = cudaStreamWaitEvent(ctx->side2, ctx->ev_fork, 0);
+    // every launch of the call on stream st (the caller's, or the capture stream)
+    auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+        // fork: the distance transform and the tensor-core sample order depend
+        // only on the scribbles; they run on the context's two side streams while
+        // the codes run on the caller's stream
+        cudaError_t e = launch_set_offsets(L.offs, 2 * (L.n_labels + 1), L.d_off, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+        if (e == cudaSuccess) e = enqueue_distances(ctx, L, sample_pix, ctx->side, false);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+        if (e == cudaSuccess && L.tc_form) {
+            e = cudaStreamWaitEvent(ctx->side2, ctx->ev_fork, 0);
+            if (e == cudaSuccess)
+                e = launch_tc_sort(cs_tc_launch(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post),
+                                   ctx->side2);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
+        }
+        if (e == cudaSuccess) e = enqueue_codes(ctx, a, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join, 0);
+        if (e == cudaSuccess && L.tc_form) e = cudaStreamWaitEvent(st, ctx->ev_join2, 0);
         if (e == cudaSuccess)
-            e = launch_tc_sort(cs_tc_launch(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post),
-                               ctx->side2);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
-    }
-    if (e == cudaSuccess) e = enqueue_codes(ctx, a, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join, 0);
-    if (e == cudaSuccess && L.tc_form) e = cudaStreamWaitEvent(st, ctx->ev_join2, 0);
-    if (e == cudaSuccess)
-        e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st, L.tc_form);
-    if (e == cudaSuccess && smooth) {
-        SmoothArgs sa{img, H, W, omega, k, prm->p, mask, sample_pix, L.S, (float)prm->iota_sigma,
-                      iota_smp, L.d_off, reps, n_labels, L.d2, (float)prm->alpha,
-                      (float)prm->d_min, (float)prm->kappa_beta, neglog, post};
-        e = launch_smooth(sa, st);
+            e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st, L.tc_form);
+        if (e == cudaSuccess && smooth) {
+            SmoothArgs sa{img, H, W, omega, k, prm->p, mask, sample_pix, L.S, (float)prm->iota_sigma,
+                          iota_smp, L.d_off, reps, n_labels, L.d2, (float)prm->alpha,
+                          (float)prm->d_min, (float)prm->kappa_beta, neglog, post};
+            e = launch_smooth(sa, st);
+        }
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    // a plain repeated call replays a graph of its launches (one launch call
+    // instead of about thirty); not under profiling, the timeout hook, or a
+    // capture the caller has open on the stream
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    const bool graphable = !ctx->profiling && ctx->wait_ns == 0 && ctx->stall == 0 &&
+                           cudaStreamIsCapturing(st, &cst) == cudaSuccess &&
+                           cst == cudaStreamCaptureStatusNone;
+    if (!graphable) {
+        cudaGetLastError();
+        e = enqueue(st);
+    } else {
+        std::vector<unsigned char> key;
+        auto put = [&](const void* v, size_t n) {
+            const unsigned char* b = static_cast<const unsigned char*>(v);
+            key.insert(key.end(), b, b + n);
+        };
+        const void* ptrs[] = {img, omega, mask, sample_pix, bitmask, dist2, neglog, post};
+        const int ints[] = {H, W, k, n_labels, ctx->device, (int)ctx->scratch_gen};
+        put(ptrs, sizeof ptrs);
+        put(ints, sizeof ints);
+        put(prm, sizeof *prm);
+        put(label_off, sizeof(int32_t) * (size_t)(n_labels + 1));
+        cs_ctx::DtGraph* hit = nullptr;
+        for (auto& gr : ctx->dt_graphs)
+            if (gr.key == key) hit = &gr;
+        if (!hit) {  // first sight: run directly, remember the key
+            if (ctx->dt_graphs.size() >= 8) {  // evict the least recently used
+                auto lru = ctx->dt_graphs.begin();
+                for (auto it = ctx->dt_graphs.begin(); it != ctx->dt_graphs.end(); ++it)
+                    if (it->used < lru->used) lru = it;
+                if (lru->exec) cudaGraphExecDestroy(lru->exec);
+                ctx->dt_graphs.erase(lru);
+            }
+            ctx->dt_graphs.push_back(cs_ctx::DtGraph{key, nullptr, nullptr, ++ctx->dt_clock});
+            e = enqueue(st);
+        } else {
+            hit->used = ++ctx->dt_clock;
+            if (!hit->exec) {  // second sight: capture on the private stream
+                cudaGraph_t graph = nullptr;
+                e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    const cudaError_t er = enqueue(ctx->cap);
+                    e = cudaStreamEndCapture(ctx->cap, &graph);
+                    if (er != cudaSuccess) e = er;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&hit->exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                hit->last_fb_count = ctx->last_fb_count;
+                if (e != cudaSuccess) {  // not capturable here: run directly
+                    cudaGetLastError();
+                    hit->exec = nullptr;
+                    e = enqueue(st);
+                }
+            }
+            if (hit->exec) {
+                e = cudaGraphLaunch(hit->exec, st);
+                ctx->last_fb_count = hit->last_fb_count;
+            }
+        }
     }
     if (e != cudaSuccess) return cs_set_error(ctx, CS_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return cs_check_launch(ctx, fn);

@@ -54,6 +54,20 @@ struct cs_ctx {
     int stall = 0;
     std::vector<StageRecord> records;
     std::vector<cudaEvent_t> event_pool;
+    // cs_data_term launch graphs: a call repeated with the same arguments
+    // (pointers, sizes, parameters, label offsets) replays the kernels it
+    // captured the second time; scratch_gen invalidates them when the scratch
+    // moves
+    struct DtGraph {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec = nullptr;  // null: seen once, not captured yet
+        int* last_fb_count = nullptr;
+        unsigned long long used = 0;
+    };
+    std::vector<DtGraph> dt_graphs;
+    unsigned long long dt_clock = 0;
+    unsigned scratch_gen = 0;
+    cudaStream_t cap = nullptr;  // capture stream of those graphs
 };
 
 // Records events around one stage when profiling is on (RAII on the stream).
