@@ -584,7 +584,6 @@ void cs_lik_carve(Carve& c, LikPlan& L, int32_t* dist2) {
     L.t.rep = c.take<uint32_t>((size_t)n * Wk);
     L.t.blob = c.take<uint8_t>(L.tc_form ? (size_t)L.total_tiles * L.stage_bytes : 0, 1024);
     L.t.tile_xy = c.take<uint32_t>(L.tc_form ? (size_t)L.total_tiles * tc_tile_samples() : 0);
-    L.t.tile_xb = c.take<uint32_t>(L.tc_form ? (size_t)L.total_tiles * tc_tile_samples() : 0);
     L.t.perm = c.take<int32_t>(L.tc_form ? (size_t)S : 0);
     L.desc = c.take<TcImage>(L.tc_form ? 1 : 0);
     L.imax2 = c.take<float>(L.tc_form ? (size_t)n : 0);

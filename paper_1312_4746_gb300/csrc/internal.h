@@ -272,7 +272,6 @@ struct SampleTables {
     uint32_t* rep;    // [n_labels][Wk]
     uint8_t* blob;    // tensor-core sample tiles (ring-stage layout)
     uint32_t* tile_xy;  // tensor-core tile slots: sample position x | y << 16
-    uint32_t* tile_xb;  // tensor-core tile slots: texture codes beyond the MMA slabs
     int32_t* perm;    // tensor-core sample order (Morton order in chunks of 4096)
 };
 cudaError_t launch_gather(const float* img, int H, int W, const uint32_t* bitmask, int k,
@@ -368,7 +367,6 @@ struct TcImage {
     const float *sx, *sy, *sr, *sg, *sb;
     const uint32_t* sbits;  // word-major [Wk][n_samples]
     const float* imax2;     // per label: max_j |I_j|^2 (error bound)
-    const uint32_t* tile_xb;  // per tile slot: texture codes beyond the MMA slabs
     int n_samples;
     int H, W, ntx, n_labels;
     int n_ptiles;          // pixel tiles of the image

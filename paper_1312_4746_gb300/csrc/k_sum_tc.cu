@@ -48,9 +48,10 @@
 // Two persistent CTAs per SM (one where the shared-memory layout does not
 // fit twice).
 //   warps 8..11  producers: per stage, one bulk-copies (TMA) the
-//                pre-laid-out texture and colour slabs of a sample tile, and
-//                all four write its two location slabs for this pixel tile
-//                (32 samples each)
+//                pre-laid-out part of a sample tile (texture slabs, colour
+//                slab, the texture codes beyond the texture slabs), and all
+//                four write its location rows for this pixel tile (32
+//                samples each)
 //   warp 12      MMA issuer: D1 <- texture slabs + colour slab + location
 //                slabs; TMEM double-buffered (2 x 128 columns per CTA), so
 //                one tile's MMAs run while the epilogue reads the previous
@@ -156,9 +157,9 @@ struct RingPos {
 
 // Texture codes in the MMA slabs and in the second location slab: whole
 // slabs of 32 (FP8) or 16 (BF16) codes, and the remaining k mod 32 (16)
-// codes in the location slab's EXT_MAX spare columns when they fit there,
-// else one more slab.
-constexpr int EXT_MAX = 11;
+// codes in the second half of the second location slab (EXT_MAX columns)
+// when they fit there, else one more slab.
+constexpr int EXT_MAX = 8;
 __host__ __device__ constexpr int tex_slabs(int k, bool tex8) {
     return tex8 ? (k % 32 <= EXT_MAX ? k / 32 : k / 32 + 1)
                 : (k % 16 <= EXT_MAX ? k / 16 : k / 16 + 1);
@@ -170,12 +171,18 @@ __host__ __device__ constexpr int tex_ext(int k, bool tex8) {
 
 template <bool TEX8, int KS, bool PERSAMPLE, bool SOLO = false>
 struct Cfg {
-    // ring stage: texture slabs, colour slab (both bulk-copied), then the two
-    // sample-side location slabs the producer writes
+    // ring stage: the second location slab L1 in halves (tc::halves_off;
+    // the first half, location pieces, written by the producer; the second,
+    // the texture codes beyond the texture slabs, bulk-copied), the texture
+    // slabs and the colour slab (bulk-copied with L1's second half), then
+    // the first location slab L0 (producer)
     static constexpr int tex_bytes = PERSAMPLE ? KS * 4096 : 0;
-    static constexpr int col_off = tex_bytes;
-    static constexpr int copy_bytes = tex_bytes + 4096;       // bulk-copied part of a stage
-    static constexpr int bl_off = tex_bytes + 4096;           // location slabs L0, L1
+    static constexpr int l1_off = 0;
+    static constexpr int copy_off = 2048;                     // bulk-copied part of a stage
+    static constexpr int tex_off = 4096;
+    static constexpr int col_off = 4096 + tex_bytes;
+    static constexpr int copy_bytes = 2048 + tex_bytes + 4096;
+    static constexpr int l0_off = 8192 + tex_bytes;
     static constexpr int stage_bytes = tex_bytes + 3 * 4096;
     static constexpr int NB = 2;                              // D1 accumulators (128 columns each)
     static constexpr uint32_t TMEM_COLS = 128u * NB;
@@ -297,14 +304,15 @@ __device__ __forceinline__ int tiles_of(const int32_t* tile_off, int i) {
     return tile_off[i + 1] - tile_off[i];
 }
 
-// Sample-side location rows (two 16-wide slabs L0, L1) of a sample at
-// packed position w (x | y << 16) relative to the pixel tile's centre
-// (cx, cy), u = x_j - centre: 2u per axis in two exact bf16 pieces (h, l),
-// |u|^2 (< 2^31) in four exact bf16 pieces q0..q3, then the sample's
-// remaining texture codes xb (bit e: code 32 KS + e, or 16 KS + e) as bf16
-// 1 / 0:
+// Sample-side location rows (a 16-wide slab L0 and the first half of L1)
+// of a sample at packed position w (x | y << 16) relative to the pixel
+// tile's centre (cx, cy), u = x_j - centre: 2u per axis in two exact bf16
+// pieces (h, l), |u|^2 (< 2^31) in four exact bf16 pieces q0..q3:
 //   L0 = [hx lx hx lx hx lx  hy ly hy ly hy ly  q0 q1 q2 q3],
-//   L1 = [q0 q1 q2 q0 q1  b0 .. b10];
+//   L1 = [q0 q1 q2 q0 q1  0 0 0 | b0 .. b7],
+// where the second half of L1, the sample's texture codes beyond the
+// texture slabs (code 32 KS + e, or 16 KS + e) as bf16 1 / 0, does not depend
+// on the pixel tile and is laid out with the sample tile (build_tiles_kernel);
 // the pixel side holds the matching pieces of -f x' and f (see the
 // epilogue) and +-1 for the texture codes. The pieces are bit fields of the
 // integers (at most 8 significant bits each, so exact in bf16):
@@ -314,12 +322,12 @@ __device__ __forceinline__ int tiles_of(const int32_t* tile_off, int i) {
 __device__ __forceinline__ uint32_t bf16_exact(int v) {  // v has <= 8 significant bits
     return __float_as_uint((float)v) >> 16;
 }
-__device__ __forceinline__ void loc_row_b(uint32_t w, uint32_t xb, int cx, int cy, bool valid,
-                                          uint4& l0a, uint4& l0b, uint4& l1a, uint4& l1b) {
+__device__ __forceinline__ void loc_row_b(uint32_t w, int cx, int cy, bool valid, uint4& l0a,
+                                          uint4& l0b, uint4& l1a) {
     if (!valid) {
         l0a = make_uint4(0, 0, 0, 0);
         l0b = make_uint4(0, 0, bf16_exact(1 << 30), 0);
-        l1a = l1b = make_uint4(0, 0, 0, 0);
+        l1a = make_uint4(0, 0, 0, 0);
         return;
     }
     const int ux = (int)(w & 0xFFFFu) - cx, uy = (int)(w >> 16) - cy;  // |u| < 2^15
@@ -337,10 +345,7 @@ __device__ __forceinline__ void loc_row_b(uint32_t w, uint32_t xb, int cx, int c
                    q3 = bf16_exact((int)(q & ((1u << k2) - 1u)));
     l0a = make_uint4(px, px, px, py);
     l0b = make_uint4(py, py, q0 | (q1 << 16), q2 | (q3 << 16));
-    auto b = [xb](int e) -> uint32_t { return ((xb >> e) & 1u) ? 0x3F80u : 0u; };
-    l1a = make_uint4(q0 | (q1 << 16), q2 | (q0 << 16), q1 | (b(0) << 16), b(1) | (b(2) << 16));
-    l1b = make_uint4(b(3) | (b(4) << 16), b(5) | (b(6) << 16), b(7) | (b(8) << 16),
-                     b(9) | (b(10) << 16));
+    l1a = make_uint4(q0 | (q1 << 16), q2 | (q0 << 16), q1, 0u);
 }
 
 // Three bf16 pieces of an FP32 value (each the rounding of the exact
@@ -630,25 +635,18 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
             const int cx = (itm.pt % im.ntx) * TW + TW / 2, cy = (itm.pt / im.ntx) * TH + TH / 2;
             const int T0 = im.tile_off[itm.lab], T1 = im.tile_off[itm.lab + 1];
             const int m_i = im.label_off[itm.lab + 1] - im.label_off[itm.lab];
-            // sample positions (and extra texture bits) one tile ahead
-            uint32_t w_next[RV], x_next[RV];
+            // sample positions one tile ahead
+            uint32_t w_next[RV];
 #pragma unroll
-            for (int v = 0; v < RV; ++v) {
-                const size_t slot = (size_t)T0 * BN + 32 * (pw + C::NPROD * v) + lane;
-                w_next[v] = im.tile_xy[slot];
-                x_next[v] = a.ext ? im.tile_xb[slot] : 0u;
-            }
+            for (int v = 0; v < RV; ++v)
+                w_next[v] = im.tile_xy[(size_t)T0 * BN + 32 * (pw + C::NPROD * v) + lane];
             for (int T = T0; ok && T < T1; ++T, ++it) {
-                uint32_t w[RV], xb[RV];
+                uint32_t w[RV];
 #pragma unroll
                 for (int v = 0; v < RV; ++v) {
                     w[v] = w_next[v];
-                    xb[v] = x_next[v];
-                    if (T + 1 < T1) {
-                        const size_t slot = (size_t)(T + 1) * BN + 32 * (pw + C::NPROD * v) + lane;
-                        w_next[v] = im.tile_xy[slot];
-                        if (a.ext) x_next[v] = im.tile_xb[slot];
-                    }
+                    if (T + 1 < T1)
+                        w_next[v] = im.tile_xy[(size_t)(T + 1) * BN + 32 * (pw + C::NPROD * v) + lane];
                 }
                 const int s = (int)(it % C::STAGES);
                 const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
@@ -661,17 +659,17 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                 // are written; the arrival follows them
                 if (pw == 0 && lane == 0) {
                     tc::mbar_expect_tx(full + s, C::copy_bytes);
-                    tc::bulk_g2s(st, im.blob + (size_t)T * C::copy_bytes, C::copy_bytes, full + s);
+                    tc::bulk_g2s(st + C::copy_off, im.blob + (size_t)T * C::copy_bytes, C::copy_bytes,
+                                 full + s);
                 }
 #pragma unroll
                 for (int v = 0; v < RV; ++v) {
                     const int j = 32 * (pw + C::NPROD * v) + lane;
-                    uint4 l0a, l0b, l1a, l1b;
-                    loc_row_b(w[v], xb[v], cx, cy, j < nvalid, l0a, l0b, l1a, l1b);
-                    *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 0)) = l0a;
-                    *reinterpret_cast<uint4*>(st + C::bl_off + tc::slab_off(j, 16)) = l0b;
-                    *reinterpret_cast<uint4*>(st + C::bl_off + 4096 + tc::slab_off(j, 0)) = l1a;
-                    *reinterpret_cast<uint4*>(st + C::bl_off + 4096 + tc::slab_off(j, 16)) = l1b;
+                    uint4 l0a, l0b, l1a;
+                    loc_row_b(w[v], cx, cy, j < nvalid, l0a, l0b, l1a);
+                    *reinterpret_cast<uint4*>(st + C::l0_off + tc::slab_off(j, 0)) = l0a;
+                    *reinterpret_cast<uint4*>(st + C::l0_off + tc::slab_off(j, 16)) = l0b;
+                    *reinterpret_cast<uint4*>(st + C::l1_off + tc::halves_off(j, 0)) = l1a;
                 }
                 tc::fence_proxy_async_smem();
                 __syncwarp();
@@ -728,17 +726,19 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                         for (int sl = 0; sl < KS; ++sl) {
                             if (TEX8)
                                 tc::mma_fp8(d1, tc::smem_desc(ax + sl * 4096),
-                                            tc::smem_desc(st + sl * 4096), C::id_tex, sl > 0);
+                                            tc::smem_desc(st + C::tex_off + sl * 4096), C::id_tex,
+                                            sl > 0);
                             else
                                 tc::mma_bf16(d1, tc::smem_desc(ax + sl * 4096),
-                                             tc::smem_desc(st + sl * 4096), C::id_tex, sl > 0);
+                                             tc::smem_desc(st + C::tex_off + sl * 4096), C::id_tex,
+                                             sl > 0);
                         }
                     }
                     tc::mma_bf16(d1, tc::smem_desc(ap), tc::smem_desc(st + C::col_off), C::id_bf16,
                                  (PERSAMPLE && KS > 0) ? 1 : 0);
-                    tc::mma_bf16(d1, tc::smem_desc(ap + 4096), tc::smem_desc(st + C::bl_off),
+                    tc::mma_bf16(d1, tc::smem_desc(ap + 4096), tc::smem_desc(st + C::l0_off),
                                  C::id_bf16, 1);
-                    tc::mma_bf16(d1, tc::smem_desc(ap + 8192), tc::smem_desc(st + C::bl_off + 4096),
+                    tc::mma_bf16(d1, tc::smem_desc(ap + 8192), tc::smem_desc_halves(st + C::l1_off),
                                  C::id_bf16, 1);
                     if (!ONE_COMMIT) tc::mma_commit(empty + s);
                     tc::mma_commit(tmem_full + b);
@@ -913,10 +913,11 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                                         ? (((word >> (code & 31)) & 1u) ? 0x3F80u : 0xBF80u)
                                         : 0u;
                         }
-                        lo = make_uint4(pack2(f2, f2), pack2(f2, f3), f3 | (sg[0] << 16),
-                                        sg[1] | (sg[2] << 16));
-                        hi = make_uint4(sg[3] | (sg[4] << 16), sg[5] | (sg[6] << 16),
-                                        sg[7] | (sg[8] << 16), sg[9] | (sg[10] << 16));
+                        // L1 = [f2 f2 f2 f3 f3 0 0 0 | codes], against the sample
+                        // side's [q0 q1 q2 q0 q1 0 0 0 | b0 .. b7]
+                        lo = make_uint4(pack2(f2, f2), pack2(f2, f3), f3, 0u);
+                        hi = make_uint4(sg[0] | (sg[1] << 16), sg[2] | (sg[3] << 16),
+                                        sg[4] | (sg[5] << 16), sg[6] | (sg[7] << 16));
                     }
                 }
                 if (!p.live) lo = hi = make_uint4(0, 0, 0, 0);
@@ -1270,20 +1271,20 @@ __global__ void __launch_bounds__(1024) morton_sort_kernel(const int32_t* __rest
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) perm[start + e] = idx[e];
 }
 
-// Sample tiles laid out as the bulk-copied part of a ring stage: texture
-// slabs (b_j in {0, 1}) and the colour slab (hi/lo bf16 of I_j and of
-// -C |I_j|^2); padded rows are zero. tile_xy receives each tile slot's
-// sample position x | y << 16 (the producer forms the location slabs from
-// it per pixel tile) and tile_xb the sample's texture codes beyond the MMA
-// slabs (bit e: code 32 KS + e, or 16 KS + e), which the producer places in
-// the second location slab.
+// Sample tiles laid out as the bulk-copied part of a ring stage: the
+// second half of the location slab L1 (the sample's texture codes beyond
+// the texture slabs, code 32 KS + e or 16 KS + e as bf16 1 / 0 in column
+// 8 + e), the texture slabs (b_j in {0, 1}) and the colour slab (hi/lo bf16
+// of I_j and of -C |I_j|^2); padded rows are zero. tile_xy receives each
+// tile slot's sample position x | y << 16, from which the producer forms
+// the location rows per pixel tile.
 template <bool TEX8, int KS, bool PERSAMPLE>
 __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
                                    const int32_t* __restrict__ tile_off, int n_labels,
                                    int total_tiles, SampleTables t, int n_samples, int k,
                                    float Cc, const int32_t* __restrict__ perm,
                                    uint8_t* __restrict__ blob, uint32_t* __restrict__ tile_xy,
-                                   uint32_t* __restrict__ tile_xb, float* __restrict__ imax2,
+                                   float* __restrict__ imax2,
                                    TcImage desc, TcImage* __restrict__ desc_dst) {
     using C = Cfg<TEX8, KS, PERSAMPLE>;
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1301,12 +1302,15 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
     const bool valid = pos < label_off[i + 1];
     const int s = valid ? perm[pos] : 0;
     tile_xy[gid] = valid ? (uint32_t)t.sx[s] | ((uint32_t)t.sy[s] << 16) : 0u;
-    uint32_t xb = 0;
+    // the bulk-copied part starts with L1's second half
+    uint8_t* cp = blob + (size_t)tile * C::copy_bytes;
+    uint32_t xw[4] = {0u, 0u, 0u, 0u};
     if (PERSAMPLE && valid)
         for (int e = 0, j = (TEX8 ? 32 : 16) * KS; j < k && e < EXT_MAX; ++e, ++j)
-            xb |= ((t.sbits[(size_t)(j >> 5) * n_samples + s] >> (j & 31)) & 1u) << e;
-    tile_xb[gid] = xb;
-    uint8_t* st = blob + (size_t)tile * C::copy_bytes;
+            if ((t.sbits[(size_t)(j >> 5) * n_samples + s] >> (j & 31)) & 1u)
+                xw[e >> 1] |= 0x3F80u << (16 * (e & 1));
+    *reinterpret_cast<uint4*>(cp + tc::halves_off(r, 0)) = make_uint4(xw[0], xw[1], xw[2], xw[3]);
+    uint8_t* st = cp + (C::tex_off - C::copy_off);
     if (PERSAMPLE) {
         for (int sl = 0; sl < KS; ++sl) {
             uint32_t wv[8];
@@ -1350,8 +1354,9 @@ __global__ void build_tiles_kernel(const int32_t* __restrict__ label_off,
         pw[4] = pack2(hb, lb); pw[5] = pack2(hb, lb);
         pw[6] = pack2(hq, lq); pw[7] = pack2(hq, lq);
     }
-    *reinterpret_cast<uint4*>(st + C::col_off + tc::slab_off(r, 0)) = make_uint4(pw[0], pw[1], pw[2], pw[3]);
-    *reinterpret_cast<uint4*>(st + C::col_off + tc::slab_off(r, 16)) = make_uint4(pw[4], pw[5], pw[6], pw[7]);
+    uint8_t* sc = cp + (C::col_off - C::copy_off);
+    *reinterpret_cast<uint4*>(sc + tc::slab_off(r, 0)) = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+    *reinterpret_cast<uint4*>(sc + tc::slab_off(r, 16)) = make_uint4(pw[4], pw[5], pw[6], pw[7]);
 }
 
 template <bool TEX8, int KS, bool PERSAMPLE>
@@ -1381,7 +1386,6 @@ cudaError_t tiles(const TcLaunch& L, cudaStream_t st) {
     d.W = L.W;
     d.ntx = (L.W + TW - 1) / TW;
     d.n_labels = L.n_labels;
-    d.tile_xb = L.t.tile_xb;
     d.n_ptiles = tc_pixel_tiles(L.H, L.W);
     d.first_item = L.first_item;
     d.pix_off = L.pix_off;
@@ -1391,7 +1395,7 @@ cudaError_t tiles(const TcLaunch& L, cudaStream_t st) {
     build_tiles_kernel<TEX8, KS, PERSAMPLE>
         <<<(unsigned)(((long long)total_tiles * BN + 127) / 128), 128, 0, st>>>(
             L.d_label_off, L.d_tile_off, L.n_labels, total_tiles, L.t, L.n_samples, L.k, Cc,
-            L.t.perm, L.blob, L.t.tile_xy, L.t.tile_xb, L.imax2, d, L.desc);
+            L.t.perm, L.blob, L.t.tile_xy, L.imax2, d, L.desc);
     return cudaGetLastError();
 }
 
@@ -1484,7 +1488,7 @@ cudaError_t dispatch(int k, bool tex8, bool persample, F&& f) {
 
 size_t tc_copy_bytes(int k, bool tex8, bool persample) {
     const int ks = tex_slabs(k, tex8);
-    return (size_t)(persample ? ks * 4096 : 0) + 4096;
+    return 2048 + (size_t)(persample ? ks * 4096 : 0) + 4096;
 }
 
 int tc_tiles_per_label(int m) { return (m + BN - 1) / BN; }
