@@ -708,8 +708,11 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                 const int cb = (int)(li & 1);
                 ok = ok && spin_bar(acol_full + cb, (uint32_t)((li >> 1) & 1), abort_flag, a.d_err,
                                     4, wait_ns);
-                const uint8_t* ap = acol + cb * C::AP;  // colour, L0, L1 slabs of this item
-                const uint8_t* ax = atex + (int)((ptc - 1) % ATB) * C::tex_bytes;
+                // descriptor low words: colour, L0, L1 slabs of this item and
+                // this pixel tile's texture slabs (tc::desc_lo)
+                const uint32_t ap = tc::desc_lo(acol + cb * C::AP);
+                const uint32_t ax = tc::desc_lo(atex + (int)((ptc - 1) % ATB) * C::tex_bytes);
+                const uint32_t ring_lo = tc::desc_lo(ring);
                 const int nt = tiles_of(im.tile_off, itm.lab);
                 for (int t = 0; ok && t < nt; ++t, ++it) {
                     const int s = (int)(it % C::STAGES), b = (int)(it % NB);
@@ -720,25 +723,26 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                     if (!ok) break;
                     tc::fence_after_sync();
                     const uint32_t d1 = tmem + (uint32_t)(b * BN);
-                    const uint8_t* st = ring + s * C::stage_bytes;
+                    const uint32_t st = ring_lo + (uint32_t)(s * (C::stage_bytes >> 4));
+                    constexpr uint32_t H = tc::DESC_HI;
                     if (PERSAMPLE) {
 #pragma unroll
                         for (int sl = 0; sl < KS; ++sl) {
+                            const uint64_t da = tc::desc_of(ax + sl * 256, H);
+                            const uint64_t db = tc::desc_of(st + ((C::tex_off + sl * 4096) >> 4), H);
                             if (TEX8)
-                                tc::mma_fp8(d1, tc::smem_desc(ax + sl * 4096),
-                                            tc::smem_desc(st + C::tex_off + sl * 4096), C::id_tex,
-                                            sl > 0);
+                                tc::mma_fp8(d1, da, db, C::id_tex, sl > 0);
                             else
-                                tc::mma_bf16(d1, tc::smem_desc(ax + sl * 4096),
-                                             tc::smem_desc(st + C::tex_off + sl * 4096), C::id_tex,
-                                             sl > 0);
+                                tc::mma_bf16(d1, da, db, C::id_tex, sl > 0);
                         }
                     }
-                    tc::mma_bf16(d1, tc::smem_desc(ap), tc::smem_desc(st + C::col_off), C::id_bf16,
-                                 (PERSAMPLE && KS > 0) ? 1 : 0);
-                    tc::mma_bf16(d1, tc::smem_desc(ap + 4096), tc::smem_desc(st + C::l0_off),
+                    tc::mma_bf16(d1, tc::desc_of(ap, H), tc::desc_of(st + (C::col_off >> 4), H),
+                                 C::id_bf16, (PERSAMPLE && KS > 0) ? 1 : 0);
+                    tc::mma_bf16(d1, tc::desc_of(ap + 256, H), tc::desc_of(st + (C::l0_off >> 4), H),
                                  C::id_bf16, 1);
-                    tc::mma_bf16(d1, tc::smem_desc(ap + 8192), tc::smem_desc_halves(st + C::l1_off),
+                    tc::mma_bf16(d1, tc::desc_of(ap + 512, H),
+                                 tc::desc_of(st + (C::l1_off >> 4) + tc::DESC_HALVES_LBO,
+                                             tc::DESC_HALVES_HI),
                                  C::id_bf16, 1);
                     if (!ONE_COMMIT) tc::mma_commit(empty + s);
                     tc::mma_commit(tmem_full + b);

@@ -192,19 +192,25 @@ __host__ __device__ __forceinline__ uint32_t slab_off(uint32_t r, uint32_t b) {
     return (r >> 3) * 256u + (b >> 4) * 128u + (r & 7u) * 16u + (b & 15u);
 }
 
+// Descriptors from the low word of a base descriptor: a slab at byte
+// offset `off` from the base has the low word lo + off / 16 (the address
+// field holds bits 4..17 of a shared-memory address below 2^18, so the sum
+// never carries out of it); the high words are constants.
+constexpr uint32_t DESC_HI = (256u >> 4) | (1u << 14);  // SBO 256 B, version 1
+__device__ __forceinline__ uint32_t desc_lo(const void* p) {  // LBO 128 B
+    return (smem_u32(p) >> 4) | ((128u >> 4) << 16);
+}
+__device__ __forceinline__ uint64_t desc_of(uint32_t lo, uint32_t hi) {
+    return ((uint64_t)hi << 32) | lo;
+}
 // The other no-swizzle arrangement of a 128-row, 16-wide bf16 K-slab: the
 // rows' first 16-byte K-chunks (elements 0..7) fill the first 2 KB and their
 // second chunks (elements 8..15) the next 2 KB, each as 16 groups of 8 rows
 // 128 B apart: LBO 2048 B (K-chunk to K-chunk), SBO 128 B (8-row group to
-// 8-row group). Each half is then one contiguous block.
-__device__ __forceinline__ uint64_t smem_desc_halves(const void* p) {
-    const uint32_t a = smem_u32(p);
-    uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(2048u >> 4) << 16;  // leading-dimension byte offset
-    d |= (uint64_t)(128u >> 4) << 32;   // stride-dimension byte offset
-    d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
-    return d;
-}
+// 8-row group), so that each half is one contiguous block. Its descriptor:
+// low word desc_lo(p) + DESC_HALVES_LBO, high word DESC_HALVES_HI.
+constexpr uint32_t DESC_HALVES_LBO = ((2048u >> 4) - (128u >> 4)) << 16;
+constexpr uint32_t DESC_HALVES_HI = (128u >> 4) | (1u << 14);
 // Byte offset of (row r, K-chunk c) in that arrangement.
 __host__ __device__ __forceinline__ uint32_t halves_off(uint32_t r, uint32_t c) {
     return c * 2048u + (r >> 3) * 128u + (r & 7u) * 16u;
