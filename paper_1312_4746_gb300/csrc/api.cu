@@ -684,25 +684,34 @@ TcLaunch cs_tc_launch(cs_ctx* ctx, const LikPlan& L, const float* img, const uin
 }
 
 // Gather and sum; with `sorted` the tensor-core sample order was already
-// enqueued (cs_data_term sorts on the side stream).
+// enqueued (cs_data_term sorts on a side stream). The gather and the
+// tensor-core tile build do not need the distances: with `dist_ready` (the
+// distance transform's completion on another stream) the stream waits for
+// it only before the sum itself.
 static cudaError_t enqueue_sum(cs_ctx* ctx, const LikPlan& L, const float* img,
                                const uint32_t* bitmask, const int32_t* sample_pix,
                                const cs_params* prm, float* neglog, float* post,
-                               cudaStream_t st, bool sorted = false) {
+                               cudaStream_t st, bool sorted = false,
+                               cudaEvent_t dist_ready = nullptr) {
+    TcLaunch T{};
+    if (L.tc_form) {
+        ctx->last_fb_count = L.fb_count;
+        T = cs_tc_launch(ctx, L, img, bitmask, sample_pix, prm, neglog, post);
+        T.stall = ctx->stall == CS_STALL_SUM;  // the timeout-path test hook, one-shot
+        if (T.stall) ctx->stall = CS_STALL_NONE;
+    }
     cudaError_t e;
     {
         StageTimer tm(ctx, CS_STAGE_GATHER, st);
         e = launch_gather(img, L.H, L.W, bitmask, L.k, L.n_labels, L.d_off, sample_pix, L.S,
                           !L.persample, L.t, st);
+        if (e == cudaSuccess && L.tc_form) e = launch_sum_tc_prepare(T, sorted, st);
     }
+    if (e == cudaSuccess && dist_ready) e = cudaStreamWaitEvent(st, dist_ready, 0);
     if (e != cudaSuccess) return e;
     StageTimer tm(ctx, CS_STAGE_SUM, st);
     if (!L.tc_form) return launch_sum_plain(cs_sum_args(L, img, bitmask, prm, neglog, post), st);
-    ctx->last_fb_count = L.fb_count;
-    TcLaunch T = cs_tc_launch(ctx, L, img, bitmask, sample_pix, prm, neglog, post);
-    T.stall = ctx->stall == CS_STALL_SUM;  // the timeout-path test hook, one-shot
-    if (T.stall) ctx->stall = CS_STALL_NONE;
-    return launch_sum_tc(T, sorted, st);
+    return launch_sum_tc_run(T, st);
 }
 
 extern "C" {
@@ -905,10 +914,10 @@ cs_status cs_data_term(cs_ctx* ctx, const float* img, int H, int W, const float*
             if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
         }
         if (e == cudaSuccess) e = enqueue_codes(ctx, a, st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join, 0);
         if (e == cudaSuccess && L.tc_form) e = cudaStreamWaitEvent(st, ctx->ev_join2, 0);
         if (e == cudaSuccess)
-            e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st, L.tc_form);
+            e = enqueue_sum(ctx, L, img, a.bitmask, sample_pix, prm, neglog, post, st, L.tc_form,
+                            ctx->ev_join);
         if (e == cudaSuccess && smooth) {
             SmoothArgs sa{img, H, W, omega, k, prm->p, mask, sample_pix, L.S, (float)prm->iota_sigma,
                           iota_smp, L.d_off, reps, n_labels, L.d2, (float)prm->alpha,

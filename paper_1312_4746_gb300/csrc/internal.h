@@ -456,9 +456,11 @@ cudaError_t launch_tc_prepare(const TcLaunch& L, cudaStream_t st);
 bool tc_sum_shape(int k, bool tex8, bool persample, int variant, int* shape);
 cudaError_t launch_tc_sum(const TcImage* descs, int n_images, const TcSumParams& p,
                           cudaStream_t st);
-// Preparation (the tiles only when `sorted`) and the sum, for a single image
-// (L.desc must be set).
-cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st);
+// For a single image (L.desc must be set): the preparation (Morton sort and
+// tile build, or the tile build alone when `sorted`), which needs the
+// gathered sample tables but not the distances, then the sum.
+cudaError_t launch_sum_tc_prepare(const TcLaunch& L, bool sorted, cudaStream_t st);
+cudaError_t launch_sum_tc_run(const TcLaunch& L, cudaStream_t st);
 
 // Validation and planning helpers shared by the entry points.
 cs_status cs_check_image(cs_ctx* ctx, const char* fn, int H, int W, int k);

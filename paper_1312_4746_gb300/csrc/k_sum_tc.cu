@@ -1546,13 +1546,15 @@ bool tc_sum_shape(int k, bool tex8, bool persample, int variant, int* shape) {
            }) == cudaSuccess;
 }
 
-cudaError_t launch_sum_tc(const TcLaunch& L, bool sorted, cudaStream_t st) {
+cudaError_t launch_sum_tc_prepare(const TcLaunch& L, bool sorted, cudaStream_t st) {
     TcLaunch one = L;
     one.first_item = 0;
     one.pix_off = 0;
     one.first_ptile = 0;
-    cudaError_t e = sorted ? launch_tc_tiles(one, st) : launch_tc_prepare(one, st);
-    if (e != cudaSuccess) return e;
+    return sorted ? launch_tc_tiles(one, st) : launch_tc_prepare(one, st);
+}
+
+cudaError_t launch_sum_tc_run(const TcLaunch& L, cudaStream_t st) {
     TcSumParams p{L.k,       L.tex8,  L.persample, L.alpha,      L.d_min, L.kappa_beta,
                   L.sigma_c2, L.d_err, L.n_sm,      L.fb_list,    L.fb_count,
                   L.H * L.W,  L.l_tol, L.rho_var,   L.wait_ns,    L.stall};
