@@ -421,9 +421,10 @@ cs_status cs_unsup_data_term(cs_ctx* ctx, const float* img, int H, int W, const 
 /*
  * The whole data term in one call: patches, codes and co-support bitmasks of
  * every pixel (as cs_codes) followed by the likelihoods (as cs_likelihood).
- * The scribble distance transform depends only on the samples; it runs on a
- * context-owned stream concurrently with the codes and is joined (CUDA
- * events) before the sum. Arguments as in cs_codes / cs_likelihood; bitmask
+ * The scribble distance transform and the tensor-core sample order depend
+ * only on the samples; they run on two context-owned streams concurrently
+ * with the codes. The sample order is joined (CUDA events) before the
+ * tensor-core tile build, the distances only before the sum. Arguments as in cs_codes / cs_likelihood; bitmask
  * (DEVICE P x ceil(k/32) uint32) and dist2 may be NULL, in which case they
  * live in scratch. Capturable in a CUDA graph once a first call has sized
  * the scratch (the call allocates only when the scratch must grow).
@@ -666,7 +667,8 @@ cs_status cs_unit_rates(cs_ctx* ctx, double* out, double* clock_mhz);
  * its stream around each stage it launches:
  *   CS_STAGE_CODES   patches, codes, bitmasks and the FP64 guard pass
  *   CS_STAGE_DIST    exact scribble distance transform
- *   CS_STAGE_GATHER  sample tables and majority co-supports
+ *   CS_STAGE_GATHER  sample tables and majority co-supports (and, in the
+ *                    tensor-core forms, the sample tiles' operand layout)
  *   CS_STAGE_SUM     the pixel x sample likelihood sum and label normalisation
  *   CS_STAGE_SURROGATE  the surrogate network over all pixels
  *   CS_STAGE_TRAIN   the surrogate network's training steps (forward,
