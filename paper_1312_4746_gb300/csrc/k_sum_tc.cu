@@ -14,14 +14,15 @@
 // receives all of it from tcgen05 MMAs: the texture sum (an exact integer,
 // 2 b_x.b_j - |b_j|, so TSM = |b_x| minus it) from FP8 (e4m3, values 0 and
 // +-1) or BF16 MMAs over whole 32-code (16-code) slabs, the last few codes
-// (k mod 32 or k mod 16, when at most EXT_MAX) riding in spare columns of
+// (k mod 32 or k mod 16, when at most EXT_MAX) riding in the second half of
 // the second location slab as BF16 +-1 / 0; the colour part from a 16-wide
 // BF16 MMA over hi/lo splits of both factors (relative error about 2^-17);
 // the location part from two 16-wide BF16 MMAs whose sample side is exact
 // (2u in two bf16 pieces per axis, |u|^2 in four) and whose pixel side
 // holds three-piece splits of -f x' and f (relative error below 2^-24). The
 // sample side of the location is formed per (pixel tile, sample tile) by the
-// producer from the sample positions; the pixel side per label by the
+// producer from the sample positions (the rest of the sample side is laid
+// out once per call and bulk-copied); the pixel side per label by the
 // epilogue. In the factorised form D1 holds the colour and location parts
 // with Bt = 1.
 //
@@ -655,7 +656,7 @@ __global__ void __launch_bounds__((Cfg<TEX8, KS, PERSAMPLE, SOLO>::THREADS),
                 if (!ok) break;
                 uint8_t* st = ring + s * C::stage_bytes;
                 const int nvalid = min(BN, m_i - (T - T0) * BN);
-                // the copy first, so that it lands while the location slabs
+                // the copy first, so that it lands while the location rows
                 // are written; the arrival follows them
                 if (pw == 0 && lane == 0) {
                     tc::mbar_expect_tx(full + s, C::copy_bytes);
