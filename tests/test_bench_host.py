@@ -1,7 +1,8 @@
 """Host logic of bench.py without a GPU: the whole-job numbers of a
 multi-rank run (max over ranks, pairs of all ranks) through a real
 world-size-2 process group on the gloo backend, the per-rank workload seeds
-of the weak-scaling run, and the reference arm's rank-0-only rule."""
+of the weak-scaling run, the reference arm's rank-0-only rule and the JSON
+line it prints."""
 import io
 import os
 import socket
@@ -85,3 +86,34 @@ def test_reference_arm_other_ranks_print_nothing(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(A())
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line(monkeypatch):
+    """Rank 0 of the reference arm prints one JSON line with the contract's
+    keys: the oracle's rate is the line's value, its cpu_baseline and its
+    end-to-end figure (no host-device copies)."""
+    import json
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class A:
+        steps, warmup, ref_pixels = 2, 1, 16
+
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(A())
+    lines = [l for l in buf.getvalue().splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["unit"] == "pairs/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "16 random pixels" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == bench.WORKLOAD_NAME
